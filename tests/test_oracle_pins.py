@@ -1,0 +1,313 @@
+"""Pins of the CPU oracle to facts the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each test checks it against a
+printed worked example, brute force over all arrangements, a textbook closed
+form, or an invariant.  The plausible mistakes these catch: a wrong pivot rank
+(Fig. 1, Sec. 5, brute force), a swapped left/right side (brute force,
+planted errors), a wrong split dimension (Sec. 5 uses both dimensions; widest
+brute force), a broken tie rule (tie-heavy brute force, signed zero), a wrong
+subtree size (recursive definition), a dropped payload (bytewise checks).
+"""
+import itertools
+import math
+import random
+
+import numpy as np
+import pytest
+
+from oracle import emulator, oracle
+from paper_2211_00120_gb300 import synth
+from tests.golden_io import fig1, walkthrough
+
+RR, WIDEST = oracle.ROUND_ROBIN, oracle.WIDEST
+
+
+# ---------------------------------------------------------------- helpers --
+def fkey(v):
+    v = float(v)
+    return (v, 0 if math.copysign(1.0, v) < 0 else 1)
+
+
+def strict_less(pts, a, b, d):
+    return (fkey(pts[a, d]), a) < (fkey(pts[b, d]), b)
+
+
+def level(i):
+    return (i + 1).bit_length() - 1
+
+
+def dims_of_arrangement(pts, order, k, mode):
+    """Split dimension of every node of the arrangement ``order`` (node ->
+    original index): round robin by level, or widest extent of the scene box
+    clipped top-down by the ancestors' planes."""
+    n = len(order)
+    if mode == RR:
+        return [level(i) % k for i in range(n)]
+    lo = [min((pts[i, d] for i in range(n)), key=fkey) for d in range(k)]
+    hi = [max((pts[i, d] for i in range(n)), key=fkey) for d in range(k)]
+    dims = [0] * n
+    boxes = {0: (list(lo), list(hi))}
+    for s in range(n):
+        blo, bhi = boxes[s]
+        ext = [np.float32(bhi[d]) - np.float32(blo[d]) for d in range(k)]
+        best = 0
+        for d in range(1, k):
+            if ext[d] > ext[best]:
+                best = d
+        dims[s] = best
+        x = pts[order[s], best]
+        boxes[2 * s + 1] = (list(blo), bhi[:best] + [x] + bhi[best + 1:])
+        boxes[2 * s + 2] = (blo[:best] + [x] + blo[best + 1:], list(bhi))
+    return dims
+
+
+def is_valid(pts, order, k, mode):
+    n = len(order)
+    dims = dims_of_arrangement(pts, order, k, mode)
+    for i in range(1, n):
+        child = i
+        p = (i - 1) // 2
+        while True:
+            d = dims[p]
+            if child == 2 * p + 1:
+                if not strict_less(pts, order[i], order[p], d):
+                    return False
+            elif not strict_less(pts, order[p], order[i], d):
+                return False
+            if p == 0:
+                break
+            child, p = p, (p - 1) // 2
+    return True
+
+
+def tie_heavy(rng, n, k, values=(0.0, 1.0, 2.0)):
+    return np.array([[rng.choice(values) for _ in range(k)] for _ in range(n)], dtype=np.float32)
+
+
+# ------------------------------------------------------- paper's examples --
+def test_fig1_six_points():
+    pts, expected = fig1()
+    out, orig = oracle.build(pts, k=2, mode=RR)
+    np.testing.assert_array_equal(out, expected)
+    np.testing.assert_array_equal(pts[orig], expected)
+
+
+def test_sec5_walkthrough_final_array():
+    blocks = walkthrough()
+    _, _, _, x0, y0 = blocks[0]
+    pts = np.array([x0, y0], dtype=np.float32).T.copy()
+    out, _ = oracle.build(pts, k=2, mode=RR)
+    step, _, _, xf, yf = blocks[-1]
+    assert step == "final"
+    np.testing.assert_array_equal(out[:, 0], np.array(xf, dtype=np.float32))
+    np.testing.assert_array_equal(out[:, 1], np.array(yf, dtype=np.float32))
+
+
+def test_sec5_walkthrough_every_step_of_the_level_loop():
+    """The emulator of the paper's level loop reproduces every printed table
+    (tags and coordinates after each sort and each tag update)."""
+    blocks = walkthrough()
+    _, _, _, x0, y0 = blocks[0]
+    pts = np.array([x0, y0], dtype=np.float32).T.copy()
+    seen = []
+
+    def trace(step, l, tags, order):
+        seen.append((step, l, list(tags), [int(pts[o, 0]) for o in order],
+                     [int(pts[o, 1]) for o in order]))
+
+    emulator.emulate(pts, 2, emulator.ROUND_ROBIN, trace)
+    assert seen == [tuple(b) for b in blocks[1:]]
+
+
+# ---------------------------------------------------------- brute force --
+@pytest.mark.parametrize("mode", [RR, WIDEST])
+def test_bruteforce_unique_valid_arrangement(mode):
+    """Over all N! arrangements of tie-heavy inputs (N <= 7), exactly one
+    satisfies the strict k-d condition, and it is the oracle's."""
+    rng = random.Random(1234 + mode)
+    cases = 0
+    for n in range(1, 8):
+        reps = 3 if n == 7 else 8
+        for _ in range(reps):
+            k = rng.randint(1, 3)
+            pts = tie_heavy(rng, n, k) if rng.random() < 0.7 else \
+                np.array([[rng.uniform(-3, 3) for _ in range(k)] for _ in range(n)], np.float32)
+            valid = [p for p in itertools.permutations(range(n)) if is_valid(pts, p, k, mode)]
+            assert len(valid) == 1, (n, k, pts)
+            _, orig = oracle.build(pts, k, mode)
+            assert tuple(int(o) for o in orig) == valid[0]
+            cases += 1
+    assert cases > 40
+
+
+def test_bruteforce_n8_distinct():
+    rng = random.Random(77)
+    for mode in (RR, WIDEST):
+        pts = np.array([[rng.uniform(0, 1) for _ in range(3)] for _ in range(8)], np.float32)
+        valid = [p for p in itertools.permutations(range(8)) if is_valid(pts, p, 3, mode)]
+        assert len(valid) == 1
+        _, orig = oracle.build(pts, 3, mode)
+        assert tuple(int(o) for o in orig) == valid[0]
+
+
+# ------------------------------------------------------- closed forms --
+def eytzinger(sorted_vals):
+    n = len(sorted_vals)
+    out = [None] * n
+    it = iter(sorted_vals)
+
+    def inorder(s):
+        if s >= n:
+            return
+        inorder(2 * s + 1)
+        out[s] = next(it)
+        inorder(2 * s + 2)
+
+    inorder(0)
+    return out
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 8, 10, 31, 100, 257, 1000])
+def test_k1_is_sorted_array_in_level_order(n):
+    """k = 1: the tree is the sorted array laid out in level order (the
+    textbook Eytzinger layout), for both split modes."""
+    rng = np.random.default_rng(n)
+    pts = rng.integers(0, max(2, n // 3), size=(n, 1)).astype(np.float32)
+    ranked = sorted(range(n), key=lambda i: (fkey(pts[i, 0]), i))
+    want = eytzinger(ranked)
+    for mode in (RR, WIDEST):
+        _, orig = oracle.build(pts, 1, mode)
+        assert list(orig) == want
+
+
+def test_subtree_size_counting_matches_recursive_definition():
+    for n in range(0, 300):
+        memo = {}
+
+        def rec(s):
+            if s >= n:
+                return 0
+            if s not in memo:
+                memo[s] = 1 + rec(2 * s + 1) + rec(2 * s + 2)
+            return memo[s]
+
+        for s in range(n + 3):
+            assert oracle.subtree_size(s, n) == rec(s)
+
+
+def test_paper_ss_and_sb_formulas_match_counting():
+    """Sec. 4.1 / 4.2 in O(1) equal the counted subtree size and the segment
+    begin F(l) + sum of left siblings' sizes, for all s and N <= 1100."""
+    for n in range(1, 1100):
+        L = n.bit_length()
+        for l in range(L):
+            acc = (1 << l) - 1
+            for s in range((1 << l) - 1, min(n, (1 << (l + 1)) - 1)):
+                assert emulator.ss(s, n) == oracle.subtree_size(s, n)
+                assert emulator.sb(s, l, n) == acc
+                acc += oracle.subtree_size(s, n)
+
+
+def test_literal_c_precedence_reading_of_ss_is_wrong():
+    bad = sum(emulator.ss_literal(s, n) != oracle.subtree_size(s, n)
+              for n in range(2, 300) for s in range(n))
+    assert bad > 0
+
+
+# ------------------------------------------------- algorithm agreement --
+@pytest.mark.parametrize("mode", [RR, WIDEST])
+def test_emulator_of_level_loop_matches_recursive_oracle(mode):
+    rng = random.Random(99 + mode)
+    for _ in range(300):
+        n = rng.randint(1, 70)
+        k = rng.randint(1, 4)
+        if rng.random() < 0.5:
+            pts = tie_heavy(rng, n, k, values=(-1.0, -0.0, 0.0, 0.5, 1.0))
+        else:
+            pts = np.array([[rng.gauss(0, 1) * (d + 1) for d in range(k)] for _ in range(n)],
+                           np.float32)
+        _, orig = oracle.build(pts, k, mode)
+        assert list(emulator.emulate(pts, k, mode)) == list(orig)
+
+
+# ------------------------------------------------------------ invariants --
+@pytest.mark.parametrize("mode", [RR, WIDEST])
+@pytest.mark.parametrize("gen", ["uniform", "mixed", "aniso"])
+def test_checker_accepts_oracle_output_and_catches_planted_errors(mode, gen):
+    n = 5000
+    if gen == "uniform":
+        pts = synth.uniform(n, 3, seed=5)
+    elif gen == "mixed":
+        pts = synth.mixed(n, 3, seed=6)
+    else:
+        pts = synth.aniso_float4(n, seed=7)
+    out, orig = oracle.build(pts, 3, mode)
+    assert oracle.check(pts, out, orig, 3, mode) == -1
+    # the output is a permutation of the input
+    assert sorted(orig.tolist()) == list(range(n))
+    # planted: swap two nodes (records and indices together)
+    o2, g2 = out.copy(), orig.copy()
+    o2[[10, 2000]] = o2[[2000, 10]]
+    g2[[10, 2000]] = g2[[2000, 10]]
+    assert oracle.check(pts, o2, g2, 3, mode) >= 0
+    # planted: a coordinate nudged by one ulp
+    o3 = out.copy()
+    o3[123, 0] = np.nextafter(o3[123, 0], np.float32(np.inf))
+    assert oracle.check(pts, o3, orig, 3, mode) == 123
+    # planted: index list that is not a permutation
+    g4 = orig.copy()
+    g4[5] = g4[6]
+    assert oracle.check(pts, out, g4, 3, mode) >= 0
+
+
+def test_perfect_tree_and_small_edge_sizes():
+    for n in [0, 1, 2, 3, 4, 7, 15, 16, 17, 63, 64, 65]:
+        pts = synth.uniform(n, 3, seed=n)
+        out, orig = oracle.build(pts, 3, RR)
+        assert oracle.check(pts, out, orig, 3, RR) == -1
+        if n:
+            assert sorted(orig.tolist()) == list(range(n))
+
+
+def test_signed_zero_orders_below_positive_zero():
+    pts = np.array([[0.0], [-0.0], [0.0]], dtype=np.float32)
+    _, orig = oracle.build(pts, 1, RR)
+    # strict order: (-0,1) < (+0,0) < (+0,2); root = rank ss(1) = 1 -> index 0
+    assert list(orig) == [0, 1, 2]
+
+
+def test_nan_is_rejected():
+    pts = synth.uniform(50, 3, seed=1)
+    pts[17, 2] = np.nan
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.build(pts, 3, RR)
+    assert e.value.code == oracle.NAN_INPUT
+
+
+def test_payload_moves_bytewise_and_is_never_compared():
+    base = synth.uniform(3000, 3, seed=4)
+    pts = synth.with_stride(base, 6)
+    out, orig = oracle.build(pts, 3, RR)
+    _, orig_plain = oracle.build(base, 3, RR)
+    assert list(orig) == list(orig_plain)
+    assert out.view(np.uint32).tobytes() == pts[orig].view(np.uint32).tobytes()
+
+
+def test_widest_k1_equals_round_robin_and_dominant_axis_splits_first():
+    pts = synth.uniform(500, 1, seed=2)
+    assert list(oracle.build(pts, 1, WIDEST)[1]) == list(oracle.build(pts, 1, RR)[1])
+    box = synth.aniso_float4(2000, seed=3)  # x extent 100, z 10, y 1
+    out, orig = oracle.build(box, 3, WIDEST)
+    xs = box[:, 0]
+    # root splits x at the rank ss(1) element
+    rank = sorted(range(2000), key=lambda i: (fkey(xs[i]), i))
+    assert orig[0] == rank[oracle.subtree_size(1, 2000)]
+
+
+def test_single_node_selector_matches_full_build():
+    for mode in (RR, WIDEST):
+        pts = synth.mixed(4000, 3, seed=11)
+        _, orig = oracle.build(pts, 3, mode)
+        rng = random.Random(mode)
+        for s in [0, 1, 2, 3999] + [rng.randrange(4000) for _ in range(30)]:
+            assert oracle.node(pts, 3, mode, s) == orig[s]
