@@ -1,0 +1,162 @@
+/*
+ * kdb.h -- C ABI of the GB300 (sm_103a) left-balanced k-d tree builder.
+ *
+ * The operation is the one defined in Wald, "GPU-friendly, Parallel, and
+ * (Almost-)In-Place Construction of Left-Balanced k-d Trees" (arXiv
+ * 2211.00120): given N k-dimensional points, permute them so that the array
+ * is a left-balanced, complete k-d tree in level order -- node i at record i,
+ * children of i at 2i+1 and 2i+2 (Sec. 2) -- where every node is >= all nodes
+ * of its left subtree and <= all nodes of its right subtree in its split
+ * dimension (Sec. 1).  The split dimension is level mod k (round robin,
+ * Sec. 2) or the dimension of widest extent of the subtree's domain, the
+ * scene box clipped by the ancestors' planes (split-widest, Sec. 6).
+ *
+ * The build follows the paper's method: O(log N) iterations, each a
+ * whole-array sort by (subtree tag, split coordinate) and a per-point tag
+ * update (Sec. 3), followed by one placement of the records (Sec. 3.2, 7.1).
+ *
+ * Conventions shared by every call:
+ *   - Records: N records of stride_bytes each, the k coordinates are float32
+ *     at byte offsets 0, 4, ..., 4(k-1); bytes after 4k are payload that is
+ *     moved with the record and never read as a coordinate.  1 <= k <= 8,
+ *     stride_bytes >= 4k and a multiple of 4, the base 4-byte aligned.
+ *   - 0 <= N <= 2^31 - 1 (the paper's tags are 32-bit ints, Sec. 3).
+ *   - Ties: points are ordered by (coordinate, original index), -0.0 before
+ *     +0.0, so the tree is unique (the paper's less() in Sec. 3.1 leaves equal
+ *     keys unordered).  NaN coordinates are rejected.
+ *   - Device pointers are CUDA device (or managed) memory owned by the
+ *     caller; "h_" pointers are host memory.  The library never frees caller
+ *     memory and keeps no pointer to it after a call returns.
+ *   - Streams: work is ordered on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream).  Calls that return device-detected errors synchronise
+ *     the stream before returning, as stated per call.
+ *   - Errors: argument errors return KDB_ERR_INVALID_ARGUMENT before anything
+ *     is enqueued.  If a device error is detected (NaN input, a bounded wait
+ *     that ran out, an internal consistency check) the records are left
+ *     untouched: the final placement is skipped on the device.
+ *   - Thread safety: calls on different streams may run concurrently; each
+ *     call uses its own workspace.
+ */
+#ifndef KDB_H
+#define KDB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define KDB_API __attribute__((visibility("default")))
+#else
+#define KDB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t / CUstream. */
+typedef struct CUstream_st* kdb_stream_t;
+
+typedef enum {
+  KDB_SPLIT_ROUND_ROBIN = 0,   /* dimension = level mod k (Sec. 2) */
+  KDB_SPLIT_WIDEST_EXTENT = 1  /* widest side of the clipped domain (Sec. 6) */
+} kdb_split_mode;
+
+typedef enum {
+  KDB_OK = 0,
+  KDB_ERR_INVALID_ARGUMENT = 1,
+  KDB_ERR_OUT_OF_MEMORY = 2,
+  KDB_ERR_CUDA = 3,
+  KDB_ERR_NAN_INPUT = 4,
+  KDB_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+  KDB_ERR_NOT_A_KD_TREE = 6,  /* returned by kdb_validate only */
+  KDB_ERR_INTERNAL = 7        /* a device-side consistency check failed */
+} kdb_status;
+
+/* Static, NUL-terminated description of a status code. */
+KDB_API const char* kdb_status_string(kdb_status status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+KDB_API int kdb_version(void);
+
+/*
+ * kdb_build -- build the tree in place (Sec. 3.2, parallelKDTreeBuild).
+ *   d_points      device, in/out: N records, permuted in place into level
+ *                 order.
+ *   n, k, stride_bytes, mode: as above.
+ * Allocates its workspace from a library-owned stream-ordered pool, runs on
+ * `stream`, synchronises `stream` and returns the device status.  N <= 1
+ * returns KDB_OK immediately.
+ */
+KDB_API kdb_status kdb_build(void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
+                     kdb_stream_t stream);
+
+/*
+ * kdb_workspace_size -- bytes of device workspace kdb_build_ex needs for
+ * this problem (0 for N <= 1).  Returns 0 for invalid arguments too.
+ */
+KDB_API size_t kdb_workspace_size(int64_t n, int k, int stride_bytes, kdb_split_mode mode);
+
+/*
+ * kdb_build_ex -- kdb_build with caller-provided workspace and extra outputs.
+ *   d_workspace     device, >= kdb_workspace_size() bytes, 256-byte aligned,
+ *                   or NULL to use the library pool.  Owned by the caller; its
+ *                   contents on entry do not matter.
+ *   d_out_orig_index  device int32[N] or NULL: original index (position in
+ *                   the input) of the record stored at each node.
+ *   d_out_split_dim device uint8[N] or NULL: split dimension of each node.
+ * Synchronises `stream` and returns the device status.
+ */
+KDB_API kdb_status kdb_build_ex(void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
+                        void* d_workspace, size_t workspace_bytes, int32_t* d_out_orig_index,
+                        uint8_t* d_out_split_dim, kdb_stream_t stream);
+
+/*
+ * kdb_build_batched -- build num_sets independent trees in one pipeline.
+ *   d_points    device, in/out: the sets back to back; set b is records
+ *               [h_offsets[b], h_offsets[b+1]) and is permuted in place into
+ *               its own level-order tree.
+ *   h_offsets   host int64[num_sets+1], non-decreasing, h_offsets[0] = 0,
+ *               every set size <= 2^31 - 1.
+ * Ties use the index within the set, so every set's output equals a
+ * kdb_build of that set alone.  Synchronises `stream`.
+ */
+KDB_API kdb_status kdb_build_batched(void* d_points, const int64_t* h_offsets, int num_sets, int k,
+                             int stride_bytes, kdb_split_mode mode, kdb_stream_t stream);
+
+/*
+ * kdb_build_host -- kdb_build for records in host memory: copies them to the
+ * device, builds, and copies the tree back into h_points on `stream` (pinned
+ * host memory gives asynchronous copies).  Synchronises `stream`.
+ */
+KDB_API kdb_status kdb_build_host(void* h_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
+                          kdb_stream_t stream);
+
+/*
+ * kdb_validate -- check the k-d condition of a level-order tree (Sec. 1):
+ * for every node i and every ancestor p with split dimension d, x_d(i) <=
+ * x_d(p) if i is in p's left subtree and >= if in the right one, under the
+ * total order with -0.0 < +0.0.  For the widest mode the dimensions are
+ * recomputed top-down from the tree's own planes (Sec. 6).
+ *   h_first_bad_node  host, out: smallest violating node, or -1.
+ * Returns KDB_OK or KDB_ERR_NOT_A_KD_TREE.  Synchronous.
+ */
+KDB_API kdb_status kdb_validate(const void* d_points, int64_t n, int k, int stride_bytes,
+                        kdb_split_mode mode, int64_t* h_first_bad_node, kdb_stream_t stream);
+
+/*
+ * Fault injection for tests (host-side; never faults a GPU):
+ *   KDB_FAULT_ALLOC       the next workspace allocation reports failure;
+ *   KDB_FAULT_LOOKBACK    the next build's radix passes wait on a status value
+ *                         that no block ever writes, so each bounded wait runs
+ *                         out after about `arg` microseconds and the build
+ *                         returns KDB_ERR_TIMEOUT.
+ * Returns the previous fault setting.  Not thread-safe; tests only.
+ */
+enum { KDB_FAULT_NONE = 0, KDB_FAULT_ALLOC = 1, KDB_FAULT_LOOKBACK = 2 };
+KDB_API int kdb_debug_inject_fault(int fault, int64_t arg);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KDB_H */

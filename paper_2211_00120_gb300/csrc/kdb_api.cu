@@ -1,0 +1,717 @@
+// kdb_api.cu -- host driver of the build and the C ABI declared in kdb.h.
+//
+// The level loop (Sec. 3.2, parallelKDTreeBuild):
+//   prepass      one read of the records: coordinate keys, NaN check, digit
+//                histograms, scene boxes (widest mode, Sec. 6);
+//   rank sorts   per dimension, a stable LSD radix sort of the coordinate keys
+//                from input order, so equal coordinates keep index order; its
+//                last pass writes each point's rank in that dimension.  The
+//                rank is then a strict stand-in for (coordinate, index) in
+//                every later key;
+//   level l      key = (set, subtree, rank in the split dimension), radix sort
+//                of the level's live items (Sec. 3.1), the tag update of
+//                Sec. 3.2 fused into the last pass; widest mode then derives
+//                the next level's split dimensions;
+//   placement    the records are permuted in place by the node -> original
+//                index array (one int32 per point).
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/kdb.h"
+#include "kdb_launch.h"
+#include "kdb_onesweep.cuh"
+
+namespace kdb {
+namespace {
+
+// ---------------------------------------------------------------- faults --
+int g_fault = KDB_FAULT_NONE;
+int64_t g_fault_arg = 0;
+constexpr uint64_t kDefaultWaitNs = 4000000000ull;  // a look-back wait gives up after 4 s
+
+// ------------------------------------------------------------------ pools --
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+int g_sms[64] = {};
+
+kdb_status device_setup(int* dev, cudaMemPool_t* pool, int* sms) {
+  if (cudaGetDevice(dev) != cudaSuccess || *dev < 0 || *dev >= 64) {
+    cudaGetLastError();
+    return KDB_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[*dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = *dev;
+    cudaMemPool_t p;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return KDB_ERR_CUDA;
+    }
+    uint64_t keep = ~0ull;  // keep freed blocks for the next build
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[*dev] = p;
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, *dev);
+    g_sms[*dev] = n > 0 ? n : 1;
+  }
+  *pool = g_pools[*dev];
+  *sms = g_sms[*dev];
+  return KDB_OK;
+}
+
+kdb_status pool_alloc(void** p, size_t bytes, cudaMemPool_t pool, cudaStream_t st) {
+  *p = nullptr;
+  if (bytes == 0) return KDB_OK;
+  if (g_fault == KDB_FAULT_ALLOC) {
+    g_fault = KDB_FAULT_NONE;
+    return KDB_ERR_OUT_OF_MEMORY;
+  }
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? KDB_ERR_OUT_OF_MEMORY : KDB_ERR_CUDA;
+  }
+  return KDB_OK;
+}
+
+// ------------------------------------------------------------------- plan --
+inline int ceil_div_i(int a, int b) { return (a + b - 1) / b; }
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Plan {
+  std::vector<SetInfo> sets;
+  uint32_t total = 0;
+  int k = 0, stride = 0, mode = 0;
+  int Lmax = 0;        // most levels of any set
+  int rb = 0;          // bits of a rank
+  int set_bits = 0;    // bits of a set id in the rank-sort keys (0 for one set)
+  int rank_passes = 0;
+  bool singletons = false;  // a set of one record (its node is its record)
+  bool too_wide = false;    // (set, subtree, rank) needs more than 64 bits
+  std::vector<std::vector<ActiveEntry>> act;  // per level l = 0 .. Lmax-2
+  std::vector<uint32_t> items;                // per level
+  std::vector<int> passes;                    // per level
+  std::vector<uint32_t> box_slots;            // per level (widest)
+  uint32_t max_items = 0, max_boxes = 0;
+  int total_passes = 0;
+
+  // workspace layout (byte offsets)
+  size_t o_keysA, o_keysB, o_valsA, o_valsB, o_ckeys, o_ranks, o_perm, o_dims, o_boxA, o_boxB,
+      o_status, o_hist, o_tickets, o_err, o_bbox, o_stage, o_sets, o_act, bytes;
+  std::vector<size_t> act_off;  // element offset of each level's active list in the table
+};
+
+void make_plan(Plan& P) {
+  uint32_t nmax = 0;
+  for (const SetInfo& s : P.sets) {
+    nmax = std::max(nmax, s.n);
+    if (s.n == 1) P.singletons = true;
+  }
+  P.Lmax = nmax ? num_levels(nmax) : 0;
+  P.rb = bits_for(nmax);
+  const uint32_t ns = (uint32_t)P.sets.size();
+  P.set_bits = ns > 1 ? bits_for(ns) : 0;
+  P.rank_passes = ceil_div_i(32 + P.set_bits, 8);
+  const int levels = std::max(0, P.Lmax - 1);
+  P.act.assign(levels, {});
+  P.items.assign(levels, 0);
+  P.passes.assign(levels, 0);
+  P.box_slots.assign(levels, 0);
+  for (int l = 0; l < levels; ++l) {
+    uint32_t base = 0;
+    for (uint32_t b = 0; b < ns; ++b) {
+      const uint32_t n = P.sets[b].n;
+      if (n < 2 || num_levels(n) < l + 2) continue;
+      ActiveEntry e;
+      e.set = b;
+      e.base = base;
+      e.next = -1;
+      e.box0 = (uint32_t)P.act[l].size() << l;
+      base += n - full_nodes(l);
+      P.act[l].push_back(e);
+    }
+    P.items[l] = base;
+    const uint32_t na = (uint32_t)P.act[l].size();
+    const int abits = na > 1 ? bits_for(na) : 0;
+    if (abits + l + P.rb > 64) P.too_wide = true;  // packed key would not fit 64 bits
+    P.passes[l] = ceil_div_i(abits + l + P.rb, 8);
+    if (P.passes[l] < 1) P.passes[l] = 1;
+    P.box_slots[l] = na << l;
+    P.max_items = std::max(P.max_items, base);
+    P.max_boxes = std::max(P.max_boxes, P.box_slots[l]);
+    P.total_passes += P.passes[l];
+  }
+  for (int l = 0; l + 1 < levels; ++l) {
+    size_t j = 0;
+    for (ActiveEntry& e : P.act[l]) {
+      while (j < P.act[l + 1].size() && P.act[l + 1][j].set < e.set) ++j;
+      if (j < P.act[l + 1].size() && P.act[l + 1][j].set == e.set) e.next = (int32_t)j;
+    }
+  }
+  P.total_passes += P.k * P.rank_passes;
+
+  const uint64_t T = P.total;
+  const size_t ksz = P.sets.size() > 1 ? 8 : 4;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  P.o_keysA = take(T * 8);
+  P.o_keysB = take(T * 8);
+  P.o_valsA = take(T * 4);
+  P.o_valsB = take(T * 4);
+  P.o_ckeys = take(T * P.k * ksz);
+  P.o_ranks = take(T * P.k * 4);
+  P.o_perm = take(T * 4);
+  P.o_dims = take(T);
+  const size_t box_bytes = P.mode == KDB_SPLIT_WIDEST_EXTENT ? (size_t)P.max_boxes * 2 * P.k * 4 : 0;
+  P.o_boxA = take(box_bytes);
+  P.o_boxB = take(box_bytes);
+  const size_t tiles = (std::max<uint64_t>(T, P.max_items) + kSortTile - 1) / kSortTile;
+  P.o_status = take(tiles * kRadixBins * 8);
+  P.o_hist = take((size_t)P.total_passes * kRadixBins * 4);
+  P.o_tickets = take((size_t)P.total_passes * 4);
+  P.o_err = take(4);
+  P.o_bbox = take(P.sets.size() * 2 * P.k * 4);
+  P.o_stage = take(((T + 31) / 32) * (size_t)P.stride);
+  P.o_sets = take(P.sets.size() * sizeof(SetInfo));
+  size_t nact = 0;
+  P.act_off.assign(levels, 0);
+  for (int l = 0; l < levels; ++l) {
+    P.act_off[l] = nact;
+    nact += P.act[l].size();
+  }
+  P.o_act = take(std::max<size_t>(nact, 1) * sizeof(ActiveEntry));
+  P.bytes = o;
+}
+
+kdb_status check_common(int64_t n, int k, int stride) {
+  if (n < 0 || n > 2147483647LL) return KDB_ERR_INVALID_ARGUMENT;
+  if (k < 1 || k > kMaxK) return KDB_ERR_INVALID_ARGUMENT;
+  if (stride < 4 * k || stride % 4 != 0) return KDB_ERR_INVALID_ARGUMENT;
+  return KDB_OK;
+}
+
+kdb_status check_mode(kdb_split_mode mode) {
+  return (mode == KDB_SPLIT_ROUND_ROBIN || mode == KDB_SPLIT_WIDEST_EXTENT)
+             ? KDB_OK
+             : KDB_ERR_INVALID_ARGUMENT;
+}
+
+#define KDB_CK(call)                      \
+  do {                                    \
+    cudaError_t e_ = (call);              \
+    if (e_ != cudaSuccess) {              \
+      cudaGetLastError();                 \
+      return KDB_ERR_CUDA;                \
+    }                                     \
+  } while (0)
+
+template <typename T>
+T* at(void* ws, size_t off) {
+  return reinterpret_cast<T*>(static_cast<unsigned char*>(ws) + off);
+}
+
+// Enqueues the whole build on `st`.  Does not synchronise.
+kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
+                         int32_t* out_orig, uint8_t* out_dim, cudaStream_t st) {
+  const uint32_t T = P.total;
+  const int k = P.k;
+  uint64_t* keysA = at<uint64_t>(ws, P.o_keysA);
+  uint64_t* keysB = at<uint64_t>(ws, P.o_keysB);
+  uint32_t* valsA = at<uint32_t>(ws, P.o_valsA);
+  uint32_t* valsB = at<uint32_t>(ws, P.o_valsB);
+  uint32_t* ranks = at<uint32_t>(ws, P.o_ranks);
+  uint32_t* perm = at<uint32_t>(ws, P.o_perm);
+  uint8_t* dims = at<uint8_t>(ws, P.o_dims);
+  float* boxA = at<float>(ws, P.o_boxA);
+  float* boxB = at<float>(ws, P.o_boxB);
+  uint64_t* status = at<uint64_t>(ws, P.o_status);
+  uint32_t* hist = at<uint32_t>(ws, P.o_hist);
+  uint32_t* tickets = at<uint32_t>(ws, P.o_tickets);
+  uint32_t* err = at<uint32_t>(ws, P.o_err);
+  uint32_t* bbox = at<uint32_t>(ws, P.o_bbox);
+  SetInfo* d_sets = at<SetInfo>(ws, P.o_sets);
+  ActiveEntry* d_act = at<ActiveEntry>(ws, P.o_act);
+  const bool multi = P.sets.size() > 1;
+  const bool widest = P.mode == KDB_SPLIT_WIDEST_EXTENT;
+
+  // tables and zeroed state: look-back words, histograms, tickets, error word
+  KDB_CK(cudaMemcpyAsync(d_sets, P.sets.data(), P.sets.size() * sizeof(SetInfo),
+                         cudaMemcpyHostToDevice, st));
+  {
+    std::vector<ActiveEntry> flat;
+    for (const auto& v : P.act) flat.insert(flat.end(), v.begin(), v.end());
+    if (!flat.empty())
+      KDB_CK(cudaMemcpyAsync(d_act, flat.data(), flat.size() * sizeof(ActiveEntry),
+                             cudaMemcpyHostToDevice, st));
+    // pageable source: the copy has completed when cudaMemcpyAsync returns
+  }
+  KDB_CK(cudaMemsetAsync(status, 0, P.o_hist - P.o_status, st));
+  KDB_CK(cudaMemsetAsync(hist, 0, P.o_bbox - P.o_hist, st));  // hist, tickets, err
+  if (widest) {
+    std::vector<uint32_t> init(P.sets.size() * 2 * k);
+    for (size_t b = 0; b < P.sets.size(); ++b)
+      for (int d = 0; d < k; ++d) {
+        init[b * 2 * k + d] = 0xFFFFFFFFu;
+        init[b * 2 * k + k + d] = 0u;
+      }
+    KDB_CK(cudaMemcpyAsync(bbox, init.data(), init.size() * 4, cudaMemcpyHostToDevice, st));
+  }
+  if (out_dim || widest) KDB_CK(cudaMemsetAsync(dims, 0, T, st));
+
+  const uint64_t wait_ns =
+      g_fault == KDB_FAULT_LOOKBACK ? (uint64_t)std::max<int64_t>(g_fault_arg, 1) * 1000ull
+                                    : kDefaultWaitNs;
+  const bool fault_lb = g_fault == KDB_FAULT_LOOKBACK;
+  if (fault_lb) g_fault = KDB_FAULT_NONE;
+  int g = 0;  // pass counter within the build
+  auto ctl = [&](uint32_t n, int shift, const uint32_t* h) {
+    PassCtl c;
+    c.n = n;
+    c.shift = shift;
+    c.hist = h;
+    c.status = status;
+    c.ticket = tickets + g;
+    c.epoch = (uint32_t)(g + 1);
+    c.wait_epoch = fault_lb ? (uint32_t)(g + 1) + 0x10000000u : c.epoch;
+    c.wait_ns = wait_ns;
+    c.err = err;
+    ++g;
+    return c;
+  };
+
+  // ---- prepass
+  PrepassArgs pa;
+  pa.pts = pts;
+  pa.total = T;
+  pa.k = k;
+  pa.stride = P.stride;
+  pa.sets = d_sets;
+  pa.nsets = (uint32_t)P.sets.size();
+  pa.keys32 = multi ? nullptr : at<uint32_t>(ws, P.o_ckeys);
+  pa.keys64 = multi ? at<uint64_t>(ws, P.o_ckeys) : nullptr;
+  pa.hist = hist;
+  pa.passes = P.rank_passes;
+  pa.bbox = widest ? bbox : nullptr;
+  pa.err = err;
+  KDB_CK(launch_prepass(pa, sms, st));
+  uint32_t* hcur = hist + (size_t)k * P.rank_passes * kRadixBins;
+
+  // ---- per-dimension ranks
+  for (int d = 0; d < k; ++d) {
+    const uint32_t* hd = hist + (size_t)d * P.rank_passes * kRadixBins;
+    if (!multi) {
+      const uint32_t* kin = at<uint32_t>(ws, P.o_ckeys) + (size_t)d * T;
+      const uint32_t* vin = nullptr;
+      uint32_t* kb[2] = {reinterpret_cast<uint32_t*>(keysA), reinterpret_cast<uint32_t*>(keysB)};
+      uint32_t* vb[2] = {valsA, valsB};
+      for (int p = 0; p < P.rank_passes; ++p) {
+        PassCtl c = ctl(T, 8 * p, hd + p * kRadixBins);
+        if (p + 1 == P.rank_passes) {
+          KDB_CK(pass_u32_rank(kin, vin, ranks + (size_t)d * T, c, st));
+        } else {
+          KDB_CK(pass_u32_pingpong(kin, vin, kb[p & 1], vb[p & 1], c, st));
+          kin = kb[p & 1];
+          vin = vb[p & 1];
+        }
+      }
+    } else {
+      const uint64_t* kin = at<uint64_t>(ws, P.o_ckeys) + (size_t)d * T;
+      const uint32_t* vin = nullptr;
+      uint64_t* kb[2] = {keysA, keysB};
+      uint32_t* vb[2] = {valsA, valsB};
+      for (int p = 0; p < P.rank_passes; ++p) {
+        PassCtl c = ctl(T, 8 * p, hd + p * kRadixBins);
+        if (p + 1 == P.rank_passes) {
+          KDB_CK(pass_u64_rank(kin, vin, ranks + (size_t)d * T, d_sets, 32, c, st));
+        } else {
+          KDB_CK(pass_u64_pingpong(kin, vin, kb[p & 1], vb[p & 1], c, st));
+          kin = kb[p & 1];
+          vin = vb[p & 1];
+        }
+      }
+    }
+  }
+
+  if (P.singletons) {
+    // a one-record set is already its own tree: identity entries in perm
+    // (every other entry is written by the level loop)
+    std::vector<uint32_t> ids;
+    for (const SetInfo& s : P.sets)
+      if (s.n == 1) ids.push_back(s.off);
+    // few and small: write them one by one from a host table
+    for (uint32_t id : ids) KDB_CK(cudaMemcpyAsync(perm + id, &id, 4, cudaMemcpyHostToDevice, st));
+  }
+
+  // ---- level loop
+  const int levels = (int)P.act.size();
+  if (widest && levels > 0)
+    KDB_CK(launch_widest_root(d_sets, d_act + P.act_off[0], (uint32_t)P.act[0].size(), bbox, k,
+                              boxA, dims, st));
+  const uint32_t* vals_cur = nullptr;  // level 0: original order
+  for (int l = 0; l < levels; ++l) {
+    LevelCtx x;
+    x.sets = d_sets;
+    x.act = d_act + P.act_off[l];
+    x.act_next = l + 1 < levels ? d_act + P.act_off[l + 1] : nullptr;
+    x.nact = (uint32_t)P.act[l].size();
+    x.l = l;
+    x.rb = P.rb;
+    const uint32_t n = P.items[l];
+    // the buffer not holding vals_cur receives the level's first outputs
+    uint32_t* vfree = vals_cur == valsA ? valsB : valsA;
+    LevelKeyArgs ka;
+    ka.x = x;
+    ka.items = n;
+    ka.vals = vals_cur;
+    ka.vals_out = vfree;  // level 0 only
+    ka.ranks = ranks;
+    ka.total = T;
+    ka.k = k;
+    ka.mode = P.mode;
+    ka.dims = dims;
+    ka.keys_out = keysA;
+    ka.hist = hcur;
+    ka.passes = P.passes[l];
+    KDB_CK(launch_level_keys(ka, sms, st));
+    const uint64_t* kin = keysA;
+    const uint32_t* vin = vals_cur ? vals_cur : vfree;
+    uint64_t* kout = keysB;
+    uint32_t* vout = vin == valsA ? valsB : valsA;
+    for (int p = 0; p < P.passes[l]; ++p) {
+      PassCtl c = ctl(n, 8 * p, hcur + p * kRadixBins);
+      if (p + 1 == P.passes[l]) {
+        KDB_CK(pass_u64_update(kin, vin, x, perm, vout, c, st));
+        vals_cur = vout;
+      } else {
+        KDB_CK(pass_u64_pingpong(kin, vin, kout, vout, c, st));
+        const uint64_t* kt = kin;
+        kin = kout;
+        kout = const_cast<uint64_t*>(kt);
+        const uint32_t* vt = vin;
+        vin = vout;
+        vout = const_cast<uint32_t*>(vt);
+      }
+    }
+    hcur += (size_t)P.passes[l] * kRadixBins;
+    if (widest) {
+      WidestArgs wa;
+      wa.x = x;
+      wa.pts = pts;
+      wa.k = k;
+      wa.stride = P.stride;
+      wa.perm = perm;
+      wa.boxes_in = (l & 1) ? boxB : boxA;
+      wa.boxes_out = (l & 1) ? boxA : boxB;
+      wa.dims = dims;
+      wa.total_threads = x.nact << l;
+      KDB_CK(launch_widest_children(wa, st));
+    }
+  }
+
+  // ---- placement
+  if (out_dim && !widest) KDB_CK(launch_rr_dims(dims, d_sets, (uint32_t)P.sets.size(), T, k, st));
+  PermuteArgs pm;
+  pm.pts = pts;
+  pm.total = T;
+  pm.stride = P.stride;
+  pm.perm = perm;
+  pm.stage = at<unsigned char>(ws, P.o_stage);
+  pm.err = err;
+  KDB_CK(launch_permute(pm, sms, st));
+  if (out_orig) KDB_CK(launch_unmark(perm, out_orig, T, st));
+  if (out_dim) KDB_CK(cudaMemcpyAsync(out_dim, dims, T, cudaMemcpyDeviceToDevice, st));
+  return KDB_OK;
+}
+
+kdb_status finish(const Plan& P, void* ws, cudaStream_t st) {
+  uint32_t h_err = 0;
+  KDB_CK(cudaMemcpyAsync(&h_err, at<uint32_t>(ws, P.o_err), 4, cudaMemcpyDeviceToHost, st));
+  KDB_CK(cudaStreamSynchronize(st));
+  if (h_err & ERR_NAN) return KDB_ERR_NAN_INPUT;
+  if (h_err & ERR_TIMEOUT) return KDB_ERR_TIMEOUT;
+  if (h_err & ERR_INTERNAL) return KDB_ERR_INTERNAL;
+  return KDB_OK;
+}
+
+kdb_status run(Plan& P, unsigned char* pts, void* user_ws, size_t user_bytes, int32_t* out_orig,
+               uint8_t* out_dim, cudaStream_t st) {
+  make_plan(P);
+  if (P.too_wide) return KDB_ERR_INVALID_ARGUMENT;
+  int dev, sms;
+  cudaMemPool_t pool;
+  kdb_status s = device_setup(&dev, &pool, &sms);
+  if (s != KDB_OK) return s;
+  void* ws = user_ws;
+  if (ws) {
+    if (user_bytes < P.bytes || (reinterpret_cast<uintptr_t>(ws) & 255)) return KDB_ERR_INVALID_ARGUMENT;
+  } else {
+    s = pool_alloc(&ws, P.bytes, pool, st);
+    if (s != KDB_OK) return s;
+  }
+  s = enqueue_build(P, pts, ws, sms, out_orig, out_dim, st);
+  kdb_status f = finish(P, ws, st);
+  if (!user_ws) {
+    cudaFreeAsync(ws, st);
+    cudaStreamSynchronize(st);
+  }
+  return s != KDB_OK ? s : f;
+}
+
+}  // namespace
+}  // namespace kdb
+
+using namespace kdb;
+
+extern "C" {
+
+const char* kdb_status_string(kdb_status s) {
+  switch (s) {
+    case KDB_OK: return "ok";
+    case KDB_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case KDB_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case KDB_ERR_CUDA: return "CUDA error";
+    case KDB_ERR_NAN_INPUT: return "NaN coordinate in input";
+    case KDB_ERR_TIMEOUT: return "bounded device wait timed out";
+    case KDB_ERR_NOT_A_KD_TREE: return "not a k-d tree";
+    case KDB_ERR_INTERNAL: return "internal consistency check failed";
+  }
+  return "unknown status";
+}
+
+int kdb_version(void) { return 100; }
+
+int kdb_debug_inject_fault(int fault, int64_t arg) {
+  const int prev = g_fault;
+  g_fault = fault;
+  g_fault_arg = arg;
+  return prev;
+}
+
+size_t kdb_workspace_size(int64_t n, int k, int stride_bytes, kdb_split_mode mode) {
+  if (check_common(n, k, stride_bytes) != KDB_OK || check_mode(mode) != KDB_OK || n <= 1) return 0;
+  Plan P;
+  P.sets.push_back(SetInfo{0u, (uint32_t)n});
+  P.total = (uint32_t)n;
+  P.k = k;
+  P.stride = stride_bytes;
+  P.mode = mode;
+  make_plan(P);
+  return P.bytes;
+}
+
+kdb_status kdb_build_ex(void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
+                        void* d_workspace, size_t workspace_bytes, int32_t* d_out_orig_index,
+                        uint8_t* d_out_split_dim, kdb_stream_t stream) {
+  kdb_status s = check_common(n, k, stride_bytes);
+  if (s == KDB_OK) s = check_mode(mode);
+  if (s != KDB_OK) return s;
+  if (n > 0 && (!d_points || (reinterpret_cast<uintptr_t>(d_points) & 3))) return KDB_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (n <= 1) {
+    if (n == 1) {
+      int32_t zero = 0;
+      uint8_t z8 = 0;
+      if (d_out_orig_index) KDB_CK(cudaMemcpyAsync(d_out_orig_index, &zero, 4, cudaMemcpyHostToDevice, st));
+      if (d_out_split_dim) KDB_CK(cudaMemcpyAsync(d_out_split_dim, &z8, 1, cudaMemcpyHostToDevice, st));
+      KDB_CK(cudaStreamSynchronize(st));
+    }
+    return KDB_OK;
+  }
+  Plan P;
+  P.sets.push_back(SetInfo{0u, (uint32_t)n});
+  P.total = (uint32_t)n;
+  P.k = k;
+  P.stride = stride_bytes;
+  P.mode = mode;
+  return run(P, static_cast<unsigned char*>(d_points), d_workspace, workspace_bytes,
+             d_out_orig_index, d_out_split_dim, st);
+}
+
+kdb_status kdb_build(void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
+                     kdb_stream_t stream) {
+  return kdb_build_ex(d_points, n, k, stride_bytes, mode, nullptr, 0, nullptr, nullptr, stream);
+}
+
+kdb_status kdb_build_batched(void* d_points, const int64_t* h_offsets, int num_sets, int k,
+                             int stride_bytes, kdb_split_mode mode, kdb_stream_t stream) {
+  if (num_sets < 0 || (num_sets > 0 && !h_offsets)) return KDB_ERR_INVALID_ARGUMENT;
+  if (num_sets == 0) return KDB_OK;
+  if (h_offsets[0] != 0) return KDB_ERR_INVALID_ARGUMENT;
+  const int64_t total = h_offsets[num_sets];
+  kdb_status s = check_common(total, k, stride_bytes);
+  if (s == KDB_OK) s = check_mode(mode);
+  if (s != KDB_OK) return s;
+  if (total > 0 && (!d_points || (reinterpret_cast<uintptr_t>(d_points) & 3))) return KDB_ERR_INVALID_ARGUMENT;
+  Plan P;
+  P.sets.reserve(num_sets);
+  for (int b = 0; b < num_sets; ++b) {
+    if (h_offsets[b + 1] < h_offsets[b]) return KDB_ERR_INVALID_ARGUMENT;
+    P.sets.push_back(SetInfo{(uint32_t)h_offsets[b], (uint32_t)(h_offsets[b + 1] - h_offsets[b])});
+  }
+  if (total <= 1) return KDB_OK;
+  P.total = (uint32_t)total;
+  P.k = k;
+  P.stride = stride_bytes;
+  P.mode = mode;
+  return run(P, static_cast<unsigned char*>(d_points), nullptr, 0, nullptr, nullptr,
+             reinterpret_cast<cudaStream_t>(stream));
+}
+
+kdb_status kdb_build_host(void* h_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
+                          kdb_stream_t stream) {
+  kdb_status s = check_common(n, k, stride_bytes);
+  if (s == KDB_OK) s = check_mode(mode);
+  if (s != KDB_OK) return s;
+  if (n <= 1) return KDB_OK;
+  if (!h_points) return KDB_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int dev, sms;
+  cudaMemPool_t pool;
+  s = device_setup(&dev, &pool, &sms);
+  if (s != KDB_OK) return s;
+  const size_t bytes = (size_t)n * stride_bytes;
+  void* d = nullptr;
+  s = pool_alloc(&d, bytes, pool, st);
+  if (s != KDB_OK) return s;
+  if (cudaMemcpyAsync(d, h_points, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeAsync(d, st);
+    return KDB_ERR_CUDA;
+  }
+  s = kdb_build_ex(d, n, k, stride_bytes, mode, nullptr, 0, nullptr, nullptr, stream);
+  if (s == KDB_OK &&
+      cudaMemcpyAsync(h_points, d, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+    cudaGetLastError();
+    s = KDB_ERR_CUDA;
+  }
+  cudaFreeAsync(d, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    if (s == KDB_OK) s = KDB_ERR_CUDA;
+  }
+  return s;
+}
+
+kdb_status kdb_validate(const void* d_points, int64_t n, int k, int stride_bytes,
+                        kdb_split_mode mode, int64_t* h_first_bad_node, kdb_stream_t stream) {
+  kdb_status s = check_common(n, k, stride_bytes);
+  if (s == KDB_OK) s = check_mode(mode);
+  if (s != KDB_OK) return s;
+  if (h_first_bad_node) *h_first_bad_node = -1;
+  if (n <= 1) return KDB_OK;
+  if (!d_points || (reinterpret_cast<uintptr_t>(d_points) & 3)) return KDB_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int dev, sms;
+  cudaMemPool_t pool;
+  s = device_setup(&dev, &pool, &sms);
+  if (s != KDB_OK) return s;
+  const uint32_t N = (uint32_t)n;
+  const bool widest = mode == KDB_SPLIT_WIDEST_EXTENT;
+  const int L = num_levels(N);
+  // single-set tables for the dimension pass (widest mode)
+  std::vector<ActiveEntry> act(std::max(1, L - 1));
+  for (int l = 0; l < (int)act.size(); ++l) {
+    act[l].set = 0;
+    act[l].base = 0;
+    act[l].next = (l + 1 < (int)act.size()) ? 0 : -1;
+    act[l].box0 = 0;
+  }
+  const size_t box_bytes = widest ? ((size_t)1 << std::max(0, L - 1)) * 2 * k * 4 : 0;
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    size_t a = o;
+    o = align256(o + b);
+    return a;
+  };
+  const size_t o_bad = take(4), o_err = take(4), o_bbox = take(2 * k * 4), o_sets = take(sizeof(SetInfo)),
+               o_act = take(act.size() * sizeof(ActiveEntry)), o_dims = take(widest ? N : 0),
+               o_bA = take(box_bytes), o_bB = take(box_bytes);
+  void* ws = nullptr;
+  s = pool_alloc(&ws, o, pool, st);
+  if (s != KDB_OK) return s;
+  uint32_t* bad = at<uint32_t>(ws, o_bad);
+  kdb_status result = KDB_OK;
+  do {
+    if (cudaMemsetAsync(bad, 0xFF, 4, st) != cudaSuccess) { result = KDB_ERR_CUDA; break; }
+    uint8_t* dims = nullptr;
+    if (widest) {
+      SetInfo one{0u, N};
+      std::vector<uint32_t> init(2 * k);
+      for (int d = 0; d < k; ++d) {
+        init[d] = 0xFFFFFFFFu;
+        init[k + d] = 0u;
+      }
+      dims = at<uint8_t>(ws, o_dims);
+      if (cudaMemcpyAsync(at<void>(ws, o_sets), &one, sizeof one, cudaMemcpyHostToDevice, st) ||
+          cudaMemcpyAsync(at<void>(ws, o_act), act.data(), act.size() * sizeof(ActiveEntry),
+                          cudaMemcpyHostToDevice, st) ||
+          cudaMemcpyAsync(at<void>(ws, o_bbox), init.data(), init.size() * 4,
+                          cudaMemcpyHostToDevice, st) ||
+          cudaMemsetAsync(at<void>(ws, o_err), 0, 4, st) || cudaMemsetAsync(dims, 0, N, st)) {
+        result = KDB_ERR_CUDA;
+        break;
+      }
+      PrepassArgs pa{};
+      pa.pts = static_cast<const unsigned char*>(d_points);
+      pa.total = N;
+      pa.k = k;
+      pa.stride = stride_bytes;
+      pa.sets = at<SetInfo>(ws, o_sets);
+      pa.nsets = 1;
+      pa.bbox = at<uint32_t>(ws, o_bbox);
+      pa.err = at<uint32_t>(ws, o_err);
+      if (launch_prepass(pa, sms, st) != cudaSuccess) { result = KDB_ERR_CUDA; break; }
+      ActiveEntry* d_act = at<ActiveEntry>(ws, o_act);
+      if (launch_widest_root(pa.sets, d_act, 1, pa.bbox, k, at<float>(ws, o_bA), dims, st) !=
+          cudaSuccess) { result = KDB_ERR_CUDA; break; }
+      for (int l = 0; l + 1 < L; ++l) {
+        WidestArgs wa;
+        wa.x.sets = pa.sets;
+        wa.x.act = d_act + l;
+        wa.x.act_next = l + 1 < (int)act.size() ? d_act + l + 1 : nullptr;
+        wa.x.nact = 1;
+        wa.x.l = l;
+        wa.x.rb = 0;
+        wa.pts = pa.pts;
+        wa.k = k;
+        wa.stride = stride_bytes;
+        wa.perm = nullptr;
+        wa.boxes_in = at<float>(ws, (l & 1) ? o_bB : o_bA);
+        wa.boxes_out = at<float>(ws, (l & 1) ? o_bA : o_bB);
+        wa.dims = dims;
+        wa.total_threads = 1u << l;
+        if (launch_widest_children(wa, st) != cudaSuccess) { result = KDB_ERR_CUDA; break; }
+      }
+      if (result != KDB_OK) break;
+    }
+    if (launch_validate(static_cast<const unsigned char*>(d_points), N, k, stride_bytes, mode, dims,
+                        bad, st) != cudaSuccess) { result = KDB_ERR_CUDA; break; }
+    uint32_t h_bad = 0xFFFFFFFFu;
+    if (cudaMemcpyAsync(&h_bad, bad, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) { result = KDB_ERR_CUDA; break; }
+    if (h_bad != 0xFFFFFFFFu) {
+      if (h_first_bad_node) *h_first_bad_node = (int64_t)h_bad;
+      result = KDB_ERR_NOT_A_KD_TREE;
+    }
+  } while (0);
+  if (result == KDB_ERR_CUDA) cudaGetLastError();
+  cudaFreeAsync(ws, st);
+  cudaStreamSynchronize(st);
+  return result;
+}
+
+}  // extern "C"

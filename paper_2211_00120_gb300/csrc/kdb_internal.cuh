@@ -1,0 +1,169 @@
+// kdb_internal.cuh -- shared device/host helpers of the k-d tree builder.
+//
+// Implicit-tree arithmetic of the paper (Wald, arXiv 2211.00120):
+//   level(i) = 31 - clz(i+1), L = numLevels(N) = 32 - clz(N), F(l) = 2^l - 1
+//   (Sec. 2, with the Revision 3 correction of L); subtree size ss(s) in O(1)
+//   (Sec. 4.1); segment begin sb(s,l) in O(1) (Sec. 4.2).  All arithmetic is
+//   unsigned (the paper's ~((~s) << h) is undefined on signed ints).
+//
+// "Compacted" level arrays: after the level-l tag update every node of levels
+// < l+1 is final, so the live points of level l+1 are kept in an array of
+// N - F(l+1) items with the pinned nodes removed.  Segment (subtree) s_rel =
+// s - F(l) of level l starts at sb(s,l) - F(l) in the level-l array.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace kdb {
+
+enum : uint32_t { ERR_NAN = 1u, ERR_TIMEOUT = 2u, ERR_INTERNAL = 4u };
+
+constexpr int kMaxK = 8;
+constexpr int kRadixBins = 256;  // 8-bit radix digits
+constexpr uint32_t kMark = 0x80000000u;  // visited flag in the permutation array
+
+__host__ __device__ inline int clz32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+  return __clz(x);
+#else
+  return x ? __builtin_clz(x) : 32;
+#endif
+}
+
+__host__ __device__ inline int num_levels(uint32_t n) { return 32 - clz32(n); }
+__host__ __device__ inline int level_of(uint32_t i) { return 31 - clz32(i + 1); }
+__host__ __device__ inline uint32_t full_nodes(int l) { return (uint32_t)((1ull << l) - 1); }
+// bits needed to hold values in [0, n)
+__host__ __device__ inline int bits_for(uint64_t n) {
+  int b = 0;
+  while (b < 63 && (1ull << b) < n) ++b;
+  return b;
+}
+
+struct Tree {
+  uint32_t n;  // N
+  int L;       // number of levels
+  uint32_t m;  // nodes on the lowest level, N - F(L-1)
+};
+
+__host__ __device__ inline Tree make_tree(uint32_t n) {
+  Tree t;
+  t.n = n;
+  t.L = n ? num_levels(n) : 0;
+  t.m = n ? n - full_nodes(t.L - 1) : 0;
+  return t;
+}
+
+// ss(s), Sec. 4.1: full inner levels below s plus its share of the lowest
+// level.  0 for nodes outside the tree.
+__host__ __device__ inline uint32_t subtree_size(const Tree& t, uint32_t s) {
+  if (s >= t.n) return 0;
+  const int h = t.L - level_of(s) - 1;
+  const uint64_t w = 1ull << h;
+  const uint64_t fllc = ((uint64_t)s << h) + (w - 1);  // first lowest-level child
+  const uint64_t low = fllc >= t.n ? 0 : ((uint64_t)t.n - fllc < w ? (uint64_t)t.n - fllc : w);
+  return (uint32_t)((w - 1) + low);
+}
+
+// Segment layout of level l (0 <= l <= L-2) in its compacted array.
+// With h = L-l-1 >= 1 every subtree of level l has 2^h - 1 inner nodes and
+// 0..2^h lowest-level nodes; the lowest level is filled from the left, so the
+// first q subtrees are full (2^(h+1)-1), subtree q is partial and the rest
+// are thin (2^h - 1) (Observation 3 together with Sec. 4.2).
+struct LevelLayout {
+  uint32_t m;      // lowest-level nodes of the whole tree
+  int l, h;
+  uint32_t full;   // 2^(h+1) - 1
+  uint32_t thin;   // 2^h - 1
+  uint32_t q;      // number of full subtrees
+  uint32_t a;      // q * full: items covered by the full subtrees
+  uint32_t part;   // size of subtree q (if q < 2^l)
+  uint32_t nseg;   // 2^l
+  uint32_t items;  // N - F(l)
+
+  __host__ __device__ static LevelLayout make(const Tree& t, int l) {
+    LevelLayout y;
+    y.m = t.m;
+    y.l = l;
+    y.h = t.L - l - 1;
+    y.thin = (uint32_t)((1ull << y.h) - 1);
+    y.full = (uint32_t)((1ull << (y.h + 1)) - 1);
+    y.nseg = 1u << l;
+    uint32_t q = t.m >> y.h;
+    y.q = q < y.nseg ? q : y.nseg;
+    y.a = y.q * y.full;
+    y.part = y.thin + (t.m - (y.q << y.h));  // only meaningful if q < nseg
+    y.items = t.n - full_nodes(l);
+    return y;
+  }
+  // sb(F(l) + s_rel, l) - F(l), Sec. 4.2
+  __host__ __device__ uint32_t seg_start(uint32_t s_rel) const {
+    const uint64_t lowest = (uint64_t)s_rel << h;
+    return (uint32_t)((uint64_t)s_rel * thin + (lowest < m ? lowest : m));
+  }
+  // subtree of the item at compacted position j (inverse of seg_start)
+  __host__ __device__ uint32_t seg_of(uint32_t j) const {
+    if (j < a) return j / full;
+    const uint32_t j2 = j - a;
+    if (j2 < part) return q;
+    return q + 1 + (j2 - part) / thin;
+  }
+  // ss(lChild(s)) for s = F(l) + s_rel: size of the left child's subtree,
+  // which is the pivot rank of Observation 1
+  __host__ __device__ uint32_t left_size(uint32_t s_rel) const {
+    // left child is subtree 2*s_rel of level l+1 (h-1 levels below it)
+    const int hc = h - 1;
+    const uint64_t lowest = (uint64_t)(2 * s_rel) << hc;
+    const uint64_t w = 1ull << hc;
+    const uint64_t low = lowest >= m ? 0 : (m - lowest < w ? m - lowest : w);
+    return (uint32_t)((w - 1) + low);
+  }
+};
+
+// Order-preserving map float32 -> uint32: unsigned order of the result is the
+// float order with -0 < +0 (Sec. 7.1 suggests radix keys built from the
+// coordinate bits; this is the usual sign-flip transform).
+__host__ __device__ inline uint32_t float_key(uint32_t bits) {
+  return bits ^ ((bits & 0x80000000u) ? 0xFFFFFFFFu : 0x80000000u);
+}
+__host__ __device__ inline uint32_t key_to_float_bits(uint32_t key) {
+  return key ^ ((key & 0x80000000u) ? 0x80000000u : 0xFFFFFFFFu);
+}
+
+#ifdef __CUDACC__
+__device__ inline uint64_t ld_relaxed_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ inline void st_relaxed_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ inline uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ inline float coord_of(const unsigned char* pts, uint32_t i, int stride, int d) {
+  return *reinterpret_cast<const float*>(pts + (uint64_t)i * (uint32_t)stride + 4u * d);
+}
+#endif
+
+// ---------------------------------------------------------------------------
+// Sets (batched builds).  A single build is a batch of one set.  Per level l
+// the sets that still have a sort to run (L_b - 1 > l) are "active"; their
+// compacted arrays are concatenated in set order.
+struct SetInfo {
+  uint32_t off;  // first record of the set in the caller's array
+  uint32_t n;    // records in the set
+};
+
+struct ActiveEntry {
+  uint32_t set;   // index into the set table
+  uint32_t base;  // start of this set's items in the level's concatenated array
+  int32_t next;   // index of the same set in the next level's active list, -1 if it leaves
+  uint32_t box0;  // first box slot of this set at this level (widest mode)
+};
+
+}  // namespace kdb

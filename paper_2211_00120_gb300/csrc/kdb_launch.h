@@ -1,0 +1,104 @@
+// kdb_launch.h -- host-side launchers of the builder's kernels (internal).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "kdb_internal.cuh"
+
+namespace kdb {
+
+// Everything one level of the build needs to know about its sets.
+struct LevelCtx {
+  const SetInfo* sets;
+  const ActiveEntry* act;       // active sets of level l (device)
+  const ActiveEntry* act_next;  // active sets of level l+1 (device), may be empty
+  uint32_t nact;
+  int l;
+  int rb;  // bits of a rank
+};
+
+// Radix pass geometry (one tile per block).
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+struct PassCtl;
+
+// onesweep passes (kdb_sort.cu)
+cudaError_t pass_u32_pingpong(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
+                              uint32_t* vout, const PassCtl& c, cudaStream_t st);
+cudaError_t pass_u32_rank(const uint32_t* kin, const uint32_t* vin, uint32_t* rank,
+                          const PassCtl& c, cudaStream_t st);
+cudaError_t pass_u64_pingpong(const uint64_t* kin, const uint32_t* vin, uint64_t* kout,
+                              uint32_t* vout, const PassCtl& c, cudaStream_t st);
+cudaError_t pass_u64_rank(const uint64_t* kin, const uint32_t* vin, uint32_t* rank,
+                          const SetInfo* sets, int set_shift, const PassCtl& c, cudaStream_t st);
+cudaError_t pass_u64_update(const uint64_t* kin, const uint32_t* vin, const LevelCtx& x,
+                            uint32_t* perm, uint32_t* vals_next, const PassCtl& c,
+                            cudaStream_t st);
+
+// tree kernels (kdb_tree.cu)
+struct PrepassArgs {
+  const unsigned char* pts;
+  uint32_t total;       // records
+  int k, stride;
+  const SetInfo* sets;  // nsets entries
+  uint32_t nsets;
+  uint32_t* keys32;     // k * total (single set) or nullptr
+  uint64_t* keys64;     // k * total (several sets) or nullptr
+  uint32_t* hist;       // k * passes * 256, or nullptr
+  int passes;
+  uint32_t* bbox;       // nsets * 2k (min keys, then max keys) or nullptr
+  uint32_t* err;
+};
+cudaError_t launch_prepass(const PrepassArgs& a, int num_sms, cudaStream_t st);
+
+struct LevelKeyArgs {
+  LevelCtx x;
+  uint32_t items;           // items in this level's concatenated array
+  const uint32_t* vals;     // original index per item, or nullptr (level 0)
+  uint32_t* vals_out;       // level 0 only: receives the original index per item
+  const uint32_t* ranks;    // k * total
+  uint32_t total;
+  int k, mode;
+  const uint8_t* dims;      // split dimension per node (widest mode)
+  uint64_t* keys_out;
+  uint32_t* hist;           // passes * 256
+  int passes;
+};
+cudaError_t launch_level_keys(const LevelKeyArgs& a, int num_sms, cudaStream_t st);
+
+struct WidestArgs {
+  LevelCtx x;              // x.act is the level whose nodes are split
+  const unsigned char* pts;
+  int k, stride;
+  const uint32_t* perm;    // orig index of each pinned node, or nullptr (points in tree order)
+  const float* boxes_in;   // per active entry: 2^l boxes of 2k floats
+  float* boxes_out;        // per next-level active entry: 2^(l+1) boxes
+  uint8_t* dims;           // per node
+  uint32_t total_threads;  // nact << l
+};
+cudaError_t launch_widest_root(const SetInfo* sets, const ActiveEntry* act0, uint32_t nact,
+                               const uint32_t* bbox, int k, float* boxes0, uint8_t* dims,
+                               cudaStream_t st);
+cudaError_t launch_widest_children(const WidestArgs& a, cudaStream_t st);
+cudaError_t launch_rr_dims(uint8_t* dims, const SetInfo* sets, uint32_t nsets, uint32_t total,
+                           int k, cudaStream_t st);
+
+struct PermuteArgs {
+  unsigned char* pts;
+  uint32_t total;
+  int stride;
+  uint32_t* perm;          // node -> original index, marked on the way
+  unsigned char* stage;    // ceil(total / 32) records
+  uint32_t* err;
+};
+cudaError_t launch_permute(const PermuteArgs& a, int num_sms, cudaStream_t st);
+cudaError_t launch_unmark(const uint32_t* perm, int32_t* out, uint32_t total, cudaStream_t st);
+
+cudaError_t launch_validate(const unsigned char* pts, uint32_t n, int k, int stride, int mode,
+                            const uint8_t* dims, uint32_t* first_bad, cudaStream_t st);
+
+}  // namespace kdb

@@ -1,0 +1,488 @@
+// kdb_tree.cu -- per-level kernels of the k-d tree build other than the sort.
+#include "kdb_launch.h"
+
+namespace kdb {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// first set whose range contains record i (sets sorted by offset)
+__device__ inline uint32_t find_set(const SetInfo* sets, uint32_t nsets, uint32_t i) {
+  uint32_t lo = 0, hi = nsets;  // invariant: answer in [lo, hi)
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (sets[mid].off <= i) lo = mid; else hi = mid;
+  }
+  while (lo + 1 < nsets && sets[lo].off + sets[lo].n <= i) ++lo;  // skip empty sets
+  return lo;
+}
+
+__device__ inline uint32_t find_active(const ActiveEntry* act, uint32_t nact, uint32_t j) {
+  uint32_t lo = 0, hi = nact;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (act[mid].base <= j) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// warp-aggregated shared-memory histogram increment
+__device__ inline void hist_add(uint32_t* h, uint32_t bin, bool ok) {
+  const uint32_t b = ok ? bin : 0xFFFFFFFFu;
+  const uint32_t peers = __match_any_sync(0xffffffffu, b);
+  const int lane = threadIdx.x & 31;
+  if (ok && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(h + bin, (uint32_t)__popc(peers));
+}
+
+// Contiguous chunk of [0, total) for this block, a multiple of blockDim long.
+__device__ inline void block_chunk(uint32_t total, uint32_t* b, uint32_t* e) {
+  const uint64_t per = (((uint64_t)total + gridDim.x - 1) / gridDim.x + blockDim.x - 1) /
+                       blockDim.x * blockDim.x;
+  const uint64_t s = per * blockIdx.x;
+  *b = (uint32_t)(s < total ? s : total);
+  *e = (uint32_t)(s + per < total ? s + per : total);
+}
+
+__device__ inline int widest_of(const float* lo, const float* hi, int k) {
+  int best = 0;
+  float be = __fsub_rn(hi[0], lo[0]);
+  for (int d = 1; d < k; ++d) {
+    const float e = __fsub_rn(hi[d], lo[d]);
+    if (e > be) {
+      be = e;
+      best = d;
+    }
+  }
+  return best;
+}
+
+// ---------------------------------------------------------------------------
+// Prepass: coordinate keys for the per-dimension rank sorts, their digit
+// histograms, the NaN check and (widest mode) each set's scene box, which is
+// the domain of the root (Sec. 6).  One read of every record.
+__global__ void __launch_bounds__(kThreads) prepass_kernel(PrepassArgs a) {
+  extern __shared__ uint32_t s_hist[];
+  const int H = a.hist ? a.k * a.passes * kRadixBins : 0;
+  for (int i = threadIdx.x; i < H; i += blockDim.x) s_hist[i] = 0;
+  __syncthreads();
+  uint32_t beg, end;
+  block_chunk(a.total, &beg, &end);
+  uint32_t lo[kMaxK], hi[kMaxK];
+  for (int d = 0; d < kMaxK; ++d) {
+    lo[d] = 0xFFFFFFFFu;
+    hi[d] = 0u;
+  }
+  bool nan = false;
+  uint32_t cur = 0;
+  bool have = false;
+  if (beg < end && a.nsets > 1) cur = find_set(a.sets, a.nsets, beg + threadIdx.x < end ? beg + threadIdx.x : beg);
+  for (uint32_t base = beg; base < end; base += blockDim.x) {
+    const uint32_t i = base + threadIdx.x;
+    const bool ok = i < end;
+    if (ok && a.nsets > 1) {
+      uint32_t s = cur;
+      while (s + 1 < a.nsets && a.sets[s].off + a.sets[s].n <= i) ++s;
+      if (s != cur && have && a.bbox) {
+        for (int d = 0; d < a.k; ++d) {
+          atomicMin(a.bbox + cur * 2 * a.k + d, lo[d]);
+          atomicMax(a.bbox + cur * 2 * a.k + a.k + d, hi[d]);
+          lo[d] = 0xFFFFFFFFu;
+          hi[d] = 0u;
+        }
+      }
+      cur = s;
+    }
+    have = have || ok;
+    const unsigned char* rec = a.pts + (uint64_t)i * (uint32_t)a.stride;
+    for (int d = 0; d < a.k; ++d) {
+      uint32_t key = 0;
+      if (ok) {
+        const uint32_t bits = *reinterpret_cast<const uint32_t*>(rec + 4 * d);
+        if ((bits & 0x7FFFFFFFu) > 0x7F800000u) nan = true;
+        key = float_key(bits);
+        lo[d] = min(lo[d], key);
+        hi[d] = max(hi[d], key);
+        if (a.keys32) a.keys32[(uint64_t)d * a.total + i] = key;
+        if (a.keys64) a.keys64[(uint64_t)d * a.total + i] = ((uint64_t)cur << 32) | key;
+      }
+      if (a.hist) {
+        const uint64_t k64 = ((uint64_t)cur << 32) | key;
+        for (int p = 0; p < a.passes; ++p)
+          hist_add(s_hist + (d * a.passes + p) * kRadixBins,
+                   (uint32_t)(k64 >> (8 * p)) & (kRadixBins - 1), ok);
+      }
+    }
+  }
+  if (a.bbox) {
+    // warp-combine when the whole warp ended in one set, else per thread
+    const uint32_t tag = have ? cur : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, tag);
+    const int lane = threadIdx.x & 31;
+    for (int d = 0; d < a.k; ++d) {
+      uint32_t l = lo[d], h = hi[d];
+      if (peers == 0xffffffffu) {
+        l = __reduce_min_sync(0xffffffffu, l);
+        h = __reduce_max_sync(0xffffffffu, h);
+        if (lane == 0 && have) {
+          atomicMin(a.bbox + cur * 2 * a.k + d, l);
+          atomicMax(a.bbox + cur * 2 * a.k + a.k + d, h);
+        }
+      } else if (have) {
+        atomicMin(a.bbox + cur * 2 * a.k + d, l);
+        atomicMax(a.bbox + cur * 2 * a.k + a.k + d, h);
+      }
+    }
+  }
+  if (nan) atomicOr(a.err, ERR_NAN);
+  __syncthreads();
+  for (int i = threadIdx.x; i < H; i += blockDim.x)
+    if (s_hist[i]) atomicAdd(a.hist + i, s_hist[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Key of every item of level l: (active set, subtree, rank of the item in the
+// subtree's split dimension).  The subtree of an item is implied by its
+// position in the compacted array (Observation 3 / Sec. 4.2 inverted), so no
+// tag is stored between levels.  Ranks order equal coordinates by original
+// index, which makes the key strict.  Also builds the digit histograms of all
+// passes of the level's sort.
+__global__ void __launch_bounds__(kThreads) level_keys_kernel(LevelKeyArgs a) {
+  __shared__ uint32_t s_hist[8 * kRadixBins];
+  const int H = a.passes * kRadixBins;
+  for (int i = threadIdx.x; i < H; i += blockDim.x) s_hist[i] = 0;
+  __syncthreads();
+  uint32_t beg, end;
+  block_chunk(a.items, &beg, &end);
+  const LevelCtx& x = a.x;
+  uint32_t ai = 0xFFFFFFFFu, aend = 0, abase = 0, soff = 0;
+  LevelLayout y;
+  const uint32_t Fl = full_nodes(x.l);
+  for (uint32_t base = beg; base < end; base += blockDim.x) {
+    const uint32_t j = base + threadIdx.x;
+    const bool ok = j < end;
+    uint64_t key = 0;
+    if (ok) {
+      if (ai == 0xFFFFFFFFu || j >= aend) {
+        ai = (x.nact > 1) ? find_active(x.act, x.nact, j) : 0;
+        const ActiveEntry e = x.act[ai];
+        const SetInfo si = x.sets[e.set];
+        y = LevelLayout::make(make_tree(si.n), x.l);
+        abase = e.base;
+        aend = e.base + y.items;
+        soff = si.off;
+      }
+      const uint32_t jj = j - abase;
+      const uint32_t s_rel = y.seg_of(jj);
+      const uint32_t orig = a.vals ? a.vals[j] : soff + jj;
+      if (!a.vals) a.vals_out[j] = orig;
+      const int d = a.mode == 0 ? x.l % a.k : a.dims[soff + Fl + s_rel];
+      const uint32_t r = a.ranks[(uint64_t)d * a.total + orig];
+      key = ((uint64_t)ai << (x.l + x.rb)) | ((uint64_t)s_rel << x.rb) | r;
+      a.keys_out[j] = key;
+    }
+    for (int p = 0; p < a.passes; ++p)
+      hist_add(s_hist + p * kRadixBins, (uint32_t)(key >> (8 * p)) & (kRadixBins - 1), ok);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < H; i += blockDim.x)
+    if (s_hist[i]) atomicAdd(a.hist + i, s_hist[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Split-widest (Sec. 6).  The domain of the root is the set's scene box; the
+// domain of a child is its parent's domain with one side replaced by the
+// parent's plane (hi = plane for the left child, lo = plane for the right
+// child).  The paper recomputes a new subtree's domain by walking up to the
+// root; here each level keeps the domains of its subtrees and derives the next
+// level's from them, which yields the same boxes (a plane always lies inside
+// its node's domain).  Split dimension = widest side (hi - lo in float32,
+// first dimension wins ties).
+__global__ void widest_root_kernel(const SetInfo* sets, const ActiveEntry* act, uint32_t nact,
+                                   const uint32_t* bbox, int k, float* boxes, uint8_t* dims) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nact) return;
+  const ActiveEntry e = act[i];
+  float lo[kMaxK], hi[kMaxK];
+  for (int d = 0; d < k; ++d) {
+    lo[d] = __uint_as_float(key_to_float_bits(bbox[e.set * 2 * k + d]));
+    hi[d] = __uint_as_float(key_to_float_bits(bbox[e.set * 2 * k + k + d]));
+    boxes[(uint64_t)e.box0 * 2 * k + d] = lo[d];
+    boxes[(uint64_t)e.box0 * 2 * k + k + d] = hi[d];
+  }
+  dims[sets[e.set].off] = (uint8_t)widest_of(lo, hi, k);
+}
+
+__global__ void widest_children_kernel(WidestArgs a) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= a.total_threads) return;
+  const LevelCtx& x = a.x;
+  const uint32_t ei = tid >> x.l;
+  const uint32_t s_rel = tid & ((1u << x.l) - 1u);
+  const ActiveEntry e = x.act[ei];
+  const SetInfo si = x.sets[e.set];
+  const uint32_t s = full_nodes(x.l) + s_rel;
+  const int k = a.k;
+  float lo[kMaxK], hi[kMaxK];
+  const float* bin = a.boxes_in + ((uint64_t)e.box0 + s_rel) * 2 * k;
+  for (int d = 0; d < k; ++d) {
+    lo[d] = bin[d];
+    hi[d] = bin[k + d];
+  }
+  const int d = a.dims[si.off + s];
+  const uint32_t node_rec = a.perm ? a.perm[si.off + s] : si.off + s;
+  const float plane = coord_of(a.pts, node_rec, a.stride, d);
+  const uint32_t c0 = 2 * s + 1;
+  for (int side = 0; side < 2; ++side) {
+    const uint32_t c = c0 + side;
+    if (c >= si.n) break;
+    const float keep = side == 0 ? hi[d] : lo[d];
+    if (side == 0) hi[d] = plane; else lo[d] = plane;
+    a.dims[si.off + c] = (uint8_t)widest_of(lo, hi, k);
+    if (e.next >= 0) {
+      float* bout = a.boxes_out + ((uint64_t)x.act_next[e.next].box0 + 2 * s_rel + side) * 2 * k;
+      for (int dd = 0; dd < k; ++dd) {
+        bout[dd] = lo[dd];
+        bout[k + dd] = hi[dd];
+      }
+    }
+    if (side == 0) hi[d] = keep; else lo[d] = keep;
+  }
+}
+
+__global__ void rr_dims_kernel(uint8_t* dims, const SetInfo* sets, uint32_t nsets, uint32_t total,
+                               int k) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const uint32_t s = nsets > 1 ? find_set(sets, nsets, i) : 0;
+  dims[i] = (uint8_t)(level_of(i - sets[s].off) % k);
+}
+
+// ---------------------------------------------------------------------------
+// Final placement (Sec. 3.2: after the last iteration each point's tag is its
+// node, and the array ends up sorted by tag), done as an almost-in-place
+// permutation of the caller's records: perm[node] = original index is the one
+// int32 per point; the staging area holds one record per 32.
+//
+// perm splits into cycles.  Every block of 32 consecutive nodes designates one
+// "leader" (a hashed offset inside the block).  Phase 1 copies each leader's
+// record aside.  Phase 2 starts one walker per leader: it fills its node from
+// the node perm points to, moves there, and repeats until the next node is a
+// leader, whose saved copy it takes.  Each node is written by exactly one
+// walker, after that walker read it, so walkers never race.  A second round
+// with denser leaders, then a minimum-index rotation, finish cycles that had
+// no leader.  Visited nodes are marked in perm's top bit.
+__device__ inline uint32_t hash32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7FEB352Du;
+  x ^= x >> 15;
+  x *= 0x846CA68Bu;
+  x ^= x >> 16;
+  return x;
+}
+
+__device__ inline uint32_t leader_of_block(uint32_t b, int round, uint32_t group) {
+  return b * group + hash32(b ^ (0x9E3779B9u * (uint32_t)(round + 1))) % group;
+}
+
+__device__ inline bool is_leader(uint32_t node, int round, uint32_t group) {
+  return leader_of_block(node / group, round, group) == node;
+}
+
+__device__ inline void copy_record(unsigned char* dst, const unsigned char* src, int stride) {
+  if ((stride & 15) == 0 && ((((uintptr_t)dst) | ((uintptr_t)src)) & 15) == 0) {
+    for (int o = 0; o < stride; o += 16)
+      *reinterpret_cast<uint4*>(dst + o) = *reinterpret_cast<const uint4*>(src + o);
+  } else {
+    for (int o = 0; o < stride; o += 4)
+      *reinterpret_cast<uint32_t*>(dst + o) = *reinterpret_cast<const uint32_t*>(src + o);
+  }
+}
+
+__global__ void perm_stage_kernel(PermuteArgs a, int round, uint32_t group) {
+  if (*a.err) return;
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nb = (a.total + group - 1) / group;
+  if (b >= nb) return;
+  const uint32_t ld = leader_of_block(b, round, group);
+  if (ld >= a.total || (a.perm[ld] & kMark)) return;
+  copy_record(a.stage + (uint64_t)b * a.stride, a.pts + (uint64_t)ld * a.stride, a.stride);
+}
+
+__global__ void perm_walk_kernel(PermuteArgs a, int round, uint32_t group) {
+  if (*a.err) return;
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nb = (a.total + group - 1) / group;
+  if (b >= nb) return;
+  const uint32_t ld = leader_of_block(b, round, group);
+  if (ld >= a.total || (a.perm[ld] & kMark)) return;
+  uint32_t cur = ld;
+  for (uint32_t steps = 0; steps <= a.total; ++steps) {
+    const uint32_t nxt = a.perm[cur] & ~kMark;
+    if (nxt >= a.total) {
+      atomicOr(a.err, ERR_INTERNAL);
+      return;
+    }
+    unsigned char* dst = a.pts + (uint64_t)cur * a.stride;
+    if (is_leader(nxt, round, group)) {
+      copy_record(dst, a.stage + (uint64_t)(nxt / group) * a.stride, a.stride);
+      a.perm[cur] |= kMark;
+      return;
+    }
+    copy_record(dst, a.pts + (uint64_t)nxt * a.stride, a.stride);
+    a.perm[cur] |= kMark;
+    cur = nxt;
+  }
+  atomicOr(a.err, ERR_INTERNAL);  // longer than any cycle: perm is not a permutation
+}
+
+__global__ void perm_rest_kernel(PermuteArgs a) {
+  if (*a.err) return;
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.total) return;
+  if (a.perm[s] & kMark) return;
+  // the rotation is done by the smallest node of the cycle
+  uint32_t x = a.perm[s] & ~kMark;
+  for (uint32_t steps = 0; x != s; ++steps) {
+    if (x < s) return;
+    if (steps > a.total || x >= a.total) {
+      atomicOr(a.err, ERR_INTERNAL);
+      return;
+    }
+    x = a.perm[x] & ~kMark;
+  }
+  uint4 tmp4[16];
+  unsigned char* tmp = reinterpret_cast<unsigned char*>(tmp4);
+  const bool small = a.stride <= 256;
+  uint32_t cur = s;
+  if (small) copy_record(tmp, a.pts + (uint64_t)s * a.stride, a.stride);
+  // records longer than 256 bytes rotate the other way round: swap along the cycle
+  for (;;) {
+    const uint32_t nxt = a.perm[cur] & ~kMark;
+    if (nxt == s) {
+      if (small) copy_record(a.pts + (uint64_t)cur * a.stride, tmp, a.stride);
+      a.perm[cur] |= kMark;
+      return;
+    }
+    if (small) {
+      copy_record(a.pts + (uint64_t)cur * a.stride, a.pts + (uint64_t)nxt * a.stride, a.stride);
+    } else {
+      uint32_t* p = reinterpret_cast<uint32_t*>(a.pts + (uint64_t)cur * a.stride);
+      uint32_t* q = reinterpret_cast<uint32_t*>(a.pts + (uint64_t)nxt * a.stride);
+      for (int o = 0; o < a.stride / 4; ++o) {
+        const uint32_t t = p[o];
+        p[o] = q[o];
+        q[o] = t;
+      }
+    }
+    a.perm[cur] |= kMark;
+    cur = nxt;
+  }
+}
+
+__global__ void unmark_kernel(const uint32_t* perm, int32_t* out, uint32_t total) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < total) out[i] = (int32_t)(perm[i] & ~kMark);
+}
+
+// ---------------------------------------------------------------------------
+// k-d condition of every node against every ancestor (Sec. 1), in the total
+// order of float_key (-0 < +0); ties are allowed on both sides.
+__global__ void validate_kernel(const unsigned char* pts, uint32_t n, int k, int stride, int mode,
+                                const uint8_t* dims, uint32_t* first_bad) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 || i >= n) return;
+  uint32_t child = i;
+  uint32_t p = (i - 1) / 2;
+  for (;;) {
+    const int d = mode == 0 ? level_of(p) % k : dims[p];
+    const uint32_t ki = float_key(__float_as_uint(coord_of(pts, i, stride, d)));
+    const uint32_t kp = float_key(__float_as_uint(coord_of(pts, p, stride, d)));
+    const bool left = child == 2 * p + 1;
+    if ((left && ki > kp) || (!left && ki < kp)) {
+      atomicMin(first_bad, i);
+      return;
+    }
+    if (p == 0) return;
+    child = p;
+    p = (p - 1) / 2;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers --
+cudaError_t launch_prepass(const PrepassArgs& a, int num_sms, cudaStream_t st) {
+  if (a.total == 0) return cudaSuccess;
+  const size_t smem = a.hist ? (size_t)a.k * a.passes * kRadixBins * sizeof(uint32_t) : 0;
+  cudaError_t e = cudaFuncSetAttribute(prepass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  uint32_t grid = (uint32_t)num_sms * 4;
+  const uint32_t need = (a.total + kThreads - 1) / kThreads;
+  if (grid > need) grid = need;
+  prepass_kernel<<<grid, kThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_level_keys(const LevelKeyArgs& a, int num_sms, cudaStream_t st) {
+  if (a.items == 0) return cudaSuccess;
+  uint32_t grid = (uint32_t)num_sms * 8;
+  const uint32_t need = (a.items + kThreads - 1) / kThreads;
+  if (grid > need) grid = need;
+  level_keys_kernel<<<grid, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widest_root(const SetInfo* sets, const ActiveEntry* act0, uint32_t nact,
+                               const uint32_t* bbox, int k, float* boxes0, uint8_t* dims,
+                               cudaStream_t st) {
+  if (nact == 0) return cudaSuccess;
+  widest_root_kernel<<<(nact + 127) / 128, 128, 0, st>>>(sets, act0, nact, bbox, k, boxes0, dims);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widest_children(const WidestArgs& a, cudaStream_t st) {
+  if (a.total_threads == 0) return cudaSuccess;
+  widest_children_kernel<<<(a.total_threads + kThreads - 1) / kThreads, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rr_dims(uint8_t* dims, const SetInfo* sets, uint32_t nsets, uint32_t total,
+                           int k, cudaStream_t st) {
+  if (total == 0) return cudaSuccess;
+  rr_dims_kernel<<<(total + kThreads - 1) / kThreads, kThreads, 0, st>>>(dims, sets, nsets, total, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute(const PermuteArgs& a, int num_sms, cudaStream_t st) {
+  (void)num_sms;
+  if (a.total == 0) return cudaSuccess;
+  // both rounds use one leader per 32 nodes (the staging area holds
+  // ceil(total/32) records); the second round hashes to other offsets
+  const uint32_t groups[2] = {32, 32};
+  for (int r = 0; r < 2; ++r) {
+    const uint32_t nb = (a.total + groups[r] - 1) / groups[r];
+    const uint32_t grid = (nb + kThreads - 1) / kThreads;
+    perm_stage_kernel<<<grid, kThreads, 0, st>>>(a, r, groups[r]);
+    perm_walk_kernel<<<grid, kThreads, 0, st>>>(a, r, groups[r]);
+  }
+  perm_rest_kernel<<<(a.total + kThreads - 1) / kThreads, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unmark(const uint32_t* perm, int32_t* out, uint32_t total, cudaStream_t st) {
+  if (total == 0) return cudaSuccess;
+  unmark_kernel<<<(total + kThreads - 1) / kThreads, kThreads, 0, st>>>(perm, out, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const unsigned char* pts, uint32_t n, int k, int stride, int mode,
+                            const uint8_t* dims, uint32_t* first_bad, cudaStream_t st) {
+  if (n < 2) return cudaSuccess;
+  validate_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(pts, n, k, stride, mode, dims,
+                                                                        first_bad);
+  return cudaGetLastError();
+}
+
+}  // namespace kdb

@@ -1,0 +1,168 @@
+"""Thin Python binding of the C ABI in ``include/kdb.h``.
+
+Argument marshalling only: every step of the build runs in the CUDA library
+``_build/libkdb.so``.  Device buffers are torch CUDA tensors (PyTorch provides
+device memory and streams); the functions take the tensor's data pointer and
+the current torch stream.  There is no fallback: if the library has not been
+built, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+ROUND_ROBIN = 0
+WIDEST_EXTENT = 1
+
+OK = 0
+ERR_INVALID_ARGUMENT = 1
+ERR_OUT_OF_MEMORY = 2
+ERR_CUDA = 3
+ERR_NAN_INPUT = 4
+ERR_TIMEOUT = 5
+ERR_NOT_A_KD_TREE = 6
+ERR_INTERNAL = 7
+
+FAULT_NONE = 0
+FAULT_ALLOC = 1
+FAULT_LOOKBACK = 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libkdb.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "kdb.h")
+
+_lib = None
+_lock = threading.Lock()
+
+
+class KdbError(RuntimeError):
+    def __init__(self, code: int, call: str):
+        super().__init__(f"{call}: {status_string(code)} ({code})")
+        self.code = code
+
+
+def declared_symbols() -> list[str]:
+    """Names of the entry points declared in include/kdb.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    return re.findall(r"KDB_API\s+[\w\s\*]+?\b(kdb_\w+)\s*\(", text)
+
+
+def load():
+    """Loads the CUDA library; raises if it was not built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"CUDA library {LIB_PATH} is missing; build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+        sig = {
+            "kdb_status_string": ([i32], ctypes.c_char_p),
+            "kdb_version": ([], i32),
+            "kdb_build": ([vp, i64, i32, i32, i32, vp], i32),
+            "kdb_workspace_size": ([i64, i32, i32, i32], sz),
+            "kdb_build_ex": ([vp, i64, i32, i32, i32, vp, sz, vp, vp, vp], i32),
+            "kdb_build_batched": ([vp, vp, i32, i32, i32, i32, vp], i32),
+            "kdb_build_host": ([vp, i64, i32, i32, i32, vp], i32),
+            "kdb_validate": ([vp, i64, i32, i32, i32, ctypes.POINTER(i64), vp], i32),
+            "kdb_debug_inject_fault": ([i32, i64], i32),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def status_string(code: int) -> str:
+    try:
+        return load().kdb_status_string(code).decode()
+    except Exception:  # library not loadable: still give a message
+        return f"status {code}"
+
+
+def _stream(stream) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _records(points):
+    """(pointer, n, stride_bytes) of a 2-D contiguous tensor of 4-byte items."""
+    if points.dim() != 2 or points.element_size() != 4 or not points.is_contiguous():
+        raise ValueError("points must be a contiguous 2-D tensor of 4-byte items (one row per record)")
+    return points.data_ptr(), points.shape[0], 4 * points.shape[1]
+
+
+def _check(rc: int, call: str):
+    if rc != OK:
+        raise KdbError(rc, call)
+
+
+def kdb_version() -> int:
+    return load().kdb_version()
+
+
+def kdb_status_string(code: int) -> str:
+    return status_string(code)
+
+
+def kdb_build(points, k: int, mode: int = ROUND_ROBIN, stream=None) -> None:
+    """Permutes the CUDA tensor ``points`` (rows = records, first k columns
+    float32 coordinates) in place into a left-balanced k-d tree."""
+    ptr, n, stride = _records(points)
+    _check(load().kdb_build(ptr, n, k, stride, mode, _stream(stream)), "kdb_build")
+
+
+def kdb_workspace_size(n: int, k: int, stride_bytes: int, mode: int = ROUND_ROBIN) -> int:
+    return int(load().kdb_workspace_size(n, k, stride_bytes, mode))
+
+
+def kdb_build_ex(points, k: int, mode: int = ROUND_ROBIN, workspace=None, out_orig_index=None,
+                 out_split_dim=None, stream=None) -> None:
+    ptr, n, stride = _records(points)
+    ws = workspace.data_ptr() if workspace is not None else None
+    wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    oi = out_orig_index.data_ptr() if out_orig_index is not None else None
+    od = out_split_dim.data_ptr() if out_split_dim is not None else None
+    _check(load().kdb_build_ex(ptr, n, k, stride, mode, ws, wsb, oi, od, _stream(stream)),
+           "kdb_build_ex")
+
+
+def kdb_build_batched(points, offsets, k: int, mode: int = ROUND_ROBIN, stream=None) -> None:
+    """``offsets``: sequence of num_sets+1 record offsets (host)."""
+    ptr, n, stride = _records(points)
+    offs = (ctypes.c_int64 * len(offsets))(*[int(o) for o in offsets])
+    if offs[len(offsets) - 1] != n:
+        raise ValueError("offsets must end at the number of records")
+    _check(load().kdb_build_batched(ptr, offs, len(offsets) - 1, k, stride, mode, _stream(stream)),
+           "kdb_build_batched")
+
+
+def kdb_build_host(points, k: int, mode: int = ROUND_ROBIN, stream=None) -> None:
+    """``points``: host (CPU, ideally pinned) tensor, permuted in place."""
+    ptr, n, stride = _records(points)
+    _check(load().kdb_build_host(ptr, n, k, stride, mode, _stream(stream)), "kdb_build_host")
+
+
+def kdb_validate(points, k: int, mode: int = ROUND_ROBIN, stream=None) -> int:
+    """Returns -1 if ``points`` is a valid k-d tree, else the first bad node."""
+    ptr, n, stride = _records(points)
+    bad = ctypes.c_int64(-1)
+    rc = load().kdb_validate(ptr, n, k, stride, mode, ctypes.byref(bad), _stream(stream))
+    if rc not in (OK, ERR_NOT_A_KD_TREE):
+        raise KdbError(rc, "kdb_validate")
+    return int(bad.value)
+
+
+def kdb_debug_inject_fault(fault: int, arg: int = 0) -> int:
+    return load().kdb_debug_inject_fault(fault, arg)

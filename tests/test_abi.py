@@ -1,0 +1,69 @@
+"""The C-ABI library builds for sm_103a, loads, and exports exactly what
+include/kdb.h declares.  Only calls that need no GPU are made here: argument
+checking, workspace sizing and status strings."""
+import ctypes
+import subprocess
+
+import pytest
+
+from paper_2211_00120_gb300 import build_lib, kdb
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib.build()
+    return kdb.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = kdb.declared_symbols()
+    assert {"kdb_build", "kdb_build_batched", "kdb_validate", "kdb_build_ex",
+            "kdb_workspace_size", "kdb_status_string", "kdb_build_host"} <= set(declared)
+    out = subprocess.run(["nm", "-D", "--defined-only", kdb.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.split()[-1].startswith("kdb_")}
+    assert exported == set(declared)
+    for name in declared:
+        assert getattr(lib, name) is not None
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        assert lib.kdb_status_string(code)
+    assert lib.kdb_status_string(0) == b"ok"
+    assert lib.kdb_version() >= 100
+
+
+def test_invalid_arguments_are_rejected_before_any_device_work(lib):
+    bad = [
+        (-1, 3, 12),    # negative N
+        (1 << 31, 3, 12),  # N above 2^31-1
+        (10, 0, 12),    # k < 1
+        (10, 9, 36),    # k > 8
+        (10, 3, 8),     # stride < 4k
+        (10, 3, 14),    # stride not a multiple of 4
+    ]
+    for n, k, stride in bad:
+        assert lib.kdb_build(ctypes.c_void_p(16), n, k, stride, 0, None) == kdb.ERR_INVALID_ARGUMENT
+        assert lib.kdb_workspace_size(n, k, stride, 0) == 0
+    assert lib.kdb_build(ctypes.c_void_p(16), 10, 3, 12, 7, None) == kdb.ERR_INVALID_ARGUMENT
+    assert lib.kdb_build(None, 10, 3, 12, 0, None) == kdb.ERR_INVALID_ARGUMENT
+    assert lib.kdb_build(ctypes.c_void_p(18), 10, 3, 12, 0, None) == kdb.ERR_INVALID_ARGUMENT
+    offs = (ctypes.c_int64 * 3)(0, 5, 3)  # decreasing offsets
+    assert lib.kdb_build_batched(ctypes.c_void_p(16), offs, 2, 3, 12, 0, None) == \
+        kdb.ERR_INVALID_ARGUMENT
+
+
+def test_trivial_sizes_need_no_work(lib):
+    # N <= 1 returns immediately (no device call is made for N = 0)
+    assert lib.kdb_build(None, 0, 3, 12, 0, None) == kdb.OK
+    assert lib.kdb_workspace_size(1, 3, 12, 0) == 0
+
+
+def test_workspace_size_grows_with_n(lib):
+    a = lib.kdb_workspace_size(1000, 3, 12, 0)
+    b = lib.kdb_workspace_size(100000, 3, 12, 0)
+    c = lib.kdb_workspace_size(100000, 3, 12, 1)
+    assert 0 < a < b <= c
+    # linear in N: well under 100 bytes per point at these sizes
+    assert b < 100 * 100000

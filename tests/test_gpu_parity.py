@@ -1,0 +1,215 @@
+"""CUDA path against the CPU oracle, through the C ABI.
+
+Every comparison is exact: the build only compares coordinates and moves
+records, so the GPU output must equal the oracle's byte for byte (records and
+original indices).  Sizes span many radix tiles (4096 items) with ragged
+tails; the edge cases are the degenerate ones of the method (N <= 3, perfect
+trees, all points equal, heavy ties, signed zeros, infinities, k = 1, payload
+bytes, empty and one-point sets in a batch).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle
+from paper_2211_00120_gb300 import kdb, synth
+from tests.golden_io import fig1, walkthrough
+
+pytestmark = pytest.mark.gpu
+
+RR, WIDEST = kdb.ROUND_ROBIN, kdb.WIDEST_EXTENT
+
+
+def gpu_build(pts: np.ndarray, k: int, mode: int):
+    d = torch.from_numpy(np.ascontiguousarray(pts)).cuda()
+    orig = torch.empty(pts.shape[0], dtype=torch.int32, device="cuda")
+    kdb.kdb_build_ex(d, k, mode, out_orig_index=orig)
+    torch.cuda.synchronize()
+    return d.cpu().numpy(), orig.cpu().numpy()
+
+
+def assert_same(pts, k, mode):
+    want, worig = oracle.build(pts, k, mode)
+    got, gorig = gpu_build(pts, k, mode)
+    if not np.array_equal(gorig, worig):
+        bad = int(np.flatnonzero(gorig != worig)[0])
+        raise AssertionError(f"N={len(pts)} k={k} mode={mode}: node {bad} holds {gorig[bad]}, "
+                             f"oracle {worig[bad]}")
+    assert got.view(np.uint32).tobytes() == want.view(np.uint32).tobytes()
+
+
+def tie_grid(n, k, levels, seed):
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, levels, size=(n, k)).astype(np.float32)
+
+
+@pytest.mark.parametrize("mode", [RR, WIDEST])
+@pytest.mark.parametrize("n", [2, 3, 5, 10, 31, 32, 100, 1000, 4095, 4096, 4097, 12289, 65537,
+                               300001])
+def test_uniform_float3(n, mode):
+    assert_same(synth.uniform(n, 3, seed=n), 3, mode)
+
+
+@pytest.mark.parametrize("mode", [RR, WIDEST])
+@pytest.mark.parametrize("k", [1, 2, 4, 8])
+def test_dimensions(k, mode):
+    assert_same(synth.uniform(20011, k, seed=k), k, mode)
+
+
+@pytest.mark.parametrize("mode", [RR, WIDEST])
+def test_mixed_with_duplicates(mode):
+    assert_same(synth.mixed(200003, 3, seed=1), 3, mode)
+
+
+@pytest.mark.parametrize("mode", [RR, WIDEST])
+@pytest.mark.parametrize("levels", [1, 2, 3, 50])
+def test_heavy_ties(levels, mode):
+    assert_same(tie_grid(50000, 3, levels, seed=levels), 3, mode)
+
+
+@pytest.mark.parametrize("mode", [RR, WIDEST])
+def test_signed_zero_and_infinities(mode):
+    rng = np.random.default_rng(3)
+    vals = np.array([-np.inf, -1.0, -0.0, 0.0, 1e-42, 1.0, np.inf], dtype=np.float32)
+    pts = vals[rng.integers(0, len(vals), size=(30000, 3))]
+    assert_same(pts, 3, mode)
+
+
+@pytest.mark.parametrize("mode", [RR, WIDEST])
+@pytest.mark.parametrize("stride_floats", [3, 4, 5, 8])
+def test_payload_strides(stride_floats, mode):
+    pts = synth.with_stride(synth.uniform(40000, 3, seed=9), stride_floats)
+    assert_same(pts, 3, mode)
+
+
+def test_perfect_trees():
+    for m in [2, 3, 12, 13, 16]:
+        assert_same(synth.uniform((1 << m) - 1, 3, seed=m), 3, RR)
+
+
+def test_aniso_float4_widest():
+    assert_same(synth.aniso_float4(100003, seed=2), 3, WIDEST)
+
+
+def test_config1_uniform_1000():
+    """N=1000 float3, uniform [0,1)^3, seed 0, round robin."""
+    assert_same(synth.uniform(1000, 3, seed=0), 3, RR)
+
+
+def test_paper_examples_on_gpu():
+    pts, expected = fig1()
+    got, _ = gpu_build(pts, 2, RR)
+    np.testing.assert_array_equal(got, expected)
+    blocks = walkthrough()
+    _, _, _, x0, y0 = blocks[0]
+    pts = np.array([x0, y0], dtype=np.float32).T.copy()
+    got, _ = gpu_build(pts, 2, RR)
+    _, _, _, xf, yf = blocks[-1]
+    np.testing.assert_array_equal(got, np.array([xf, yf], dtype=np.float32).T)
+
+
+def test_split_dims_output():
+    pts = synth.uniform(5000, 3, seed=4)
+    d = torch.from_numpy(pts).cuda()
+    dims = torch.empty(5000, dtype=torch.uint8, device="cuda")
+    kdb.kdb_build_ex(d, 3, RR, out_split_dim=dims)
+    lv = np.floor(np.log2(np.arange(5000) + 1)).astype(np.int64)
+    np.testing.assert_array_equal(dims.cpu().numpy(), lv % 3)
+
+
+def test_user_workspace_and_repeatability():
+    pts = synth.mixed(70001, 3, seed=8)
+    want, _ = oracle.build(pts, 3, WIDEST)
+    nbytes = kdb.kdb_workspace_size(70001, 3, 12, WIDEST)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        d = torch.from_numpy(pts).cuda()
+        kdb.kdb_build_ex(d, 3, WIDEST, workspace=ws)
+        assert np.array_equal(d.cpu().numpy().view(np.uint32), want.view(np.uint32))
+
+
+def test_host_buffer_entry_point():
+    pts = synth.uniform(50000, 3, seed=12)
+    want, _ = oracle.build(pts, 3, RR)
+    h = torch.from_numpy(pts.copy()).pin_memory()
+    kdb.kdb_build_host(h, 3, RR)
+    assert np.array_equal(h.numpy(), want)
+
+
+def test_streams_run_independently():
+    a = synth.uniform(100000, 3, seed=21)
+    b = synth.mixed(100000, 3, seed=22)
+    wa, _ = oracle.build(a, 3, RR)
+    wb, _ = oracle.build(b, 3, WIDEST)
+    da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    kdb.kdb_build(da, 3, RR, stream=s1)
+    kdb.kdb_build(db, 3, WIDEST, stream=s2)
+    torch.cuda.synchronize()
+    assert np.array_equal(da.cpu().numpy(), wa) and np.array_equal(db.cpu().numpy(), wb)
+
+
+@pytest.mark.parametrize("mode", [RR, WIDEST])
+def test_batched_equals_each_set_alone(mode):
+    sizes = [0, 1, 2, 3, 7, 100, 4097, 1, 0, 25000, 999, 65536, 5]
+    sizes += [int(s) for s in synth.lognormal_sizes(40, 100, 20000, seed=3)]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    pts = synth.mixed(int(offs[-1]), 3, seed=4)
+    d = torch.from_numpy(pts).cuda()
+    kdb.kdb_build_batched(d, offs.tolist(), 3, mode)
+    got = d.cpu().numpy()
+    for b in range(len(sizes)):
+        lo, hi = offs[b], offs[b + 1]
+        if hi - lo == 0:
+            continue
+        want, _ = oracle.build(pts[lo:hi], 3, mode)
+        assert np.array_equal(got[lo:hi].view(np.uint32), want.view(np.uint32)), f"set {b}"
+
+
+# ------------------------------------------------------------- validation --
+@pytest.mark.parametrize("mode", [RR, WIDEST])
+def test_validate_accepts_trees_and_rejects_planted_errors(mode):
+    pts = synth.uniform(30000, 3, seed=30)
+    want, _ = oracle.build(pts, 3, mode)
+    d = torch.from_numpy(want).cuda()
+    assert kdb.kdb_validate(d, 3, mode) == -1
+    bad = want.copy()
+    bad[[5, 20000]] = bad[[20000, 5]]
+    assert kdb.kdb_validate(torch.from_numpy(bad).cuda(), 3, mode) >= 0
+    # the unbuilt input is not a tree
+    assert kdb.kdb_validate(torch.from_numpy(pts).cuda(), 3, mode) >= 0
+
+
+# ---------------------------------------------------------------- faults --
+def test_nan_input_is_reported_and_records_untouched():
+    pts = synth.uniform(10000, 3, seed=1)
+    pts[777, 1] = np.nan
+    d = torch.from_numpy(pts).cuda()
+    with pytest.raises(kdb.KdbError) as e:
+        kdb.kdb_build(d, 3, RR)
+    assert e.value.code == kdb.ERR_NAN_INPUT
+    assert np.array_equal(d.cpu().numpy().view(np.uint32), pts.view(np.uint32))
+
+
+def test_allocation_failure_is_reported():
+    pts = synth.uniform(10000, 3, seed=2)
+    d = torch.from_numpy(pts).cuda()
+    kdb.kdb_debug_inject_fault(kdb.FAULT_ALLOC, 0)
+    with pytest.raises(kdb.KdbError) as e:
+        kdb.kdb_build(d, 3, RR)
+    assert e.value.code == kdb.ERR_OUT_OF_MEMORY
+    assert np.array_equal(d.cpu().numpy(), pts)
+
+
+def test_lookback_wait_runs_out_and_context_stays_usable():
+    """The radix passes wait on a look-back value no block ever writes: every
+    bounded wait gives up after ~200 us, the build reports a timeout, leaves
+    the records alone, and the next build works."""
+    pts = synth.uniform(3 * 4096 + 5, 3, seed=3)
+    d = torch.from_numpy(pts).cuda()
+    kdb.kdb_debug_inject_fault(kdb.FAULT_LOOKBACK, 200)
+    with pytest.raises(kdb.KdbError) as e:
+        kdb.kdb_build(d, 3, RR)
+    assert e.value.code == kdb.ERR_TIMEOUT
+    assert np.array_equal(d.cpu().numpy(), pts)
+    assert_same(pts, 3, RR)
