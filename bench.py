@@ -1,0 +1,325 @@
+"""Benchmark of the GB300 k-d tree build.
+
+One step = one complete build (every level of the method plus the final
+placement) of one synthetic point set already resident in device memory.
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead (the
+plain recursive builder the parity tests compare against) on a bounded
+sample of the same workload.
+
+Launch: ``python bench.py [--gpus 1] [--steps K] [--warmup W]``; for N > 1 under
+``torch.distributed.run`` each rank builds its own replica of the workload
+(a single tree does not shard) and rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2211_00120_gb300 import synth  # noqa: E402
+
+METRIC = "Mpts/s k-d build at 1e8 float3, % of HBM roofline; batched vs serial builds/s"
+
+WORKLOADS = {
+    # name: (description, n, k, stride floats, split mode, generator)
+    "uniform_1e8_f3_rr": ("1e8 float3 points, uniform [0,1)^3 (seed 0), round-robin split",
+                          100_000_000, 3, 3, 0, lambda n: synth.uniform(n, 3, seed=0)),
+    "mixed_1e7_f3_rr": ("1e7 float3 points, half uniform, half 64 Gaussian clusters (sigma 0.01), "
+                        "1% exact duplicates (seed 1), round-robin split",
+                        10_000_000, 3, 3, 0, lambda n: synth.mixed(n, 3, seed=1)),
+    "aniso_1e8_f4_widest": ("1e8 float4 points (xyz + payload) uniform in [0,100)x[0,1)x[0,10) "
+                            "(seed 2), widest-extent split",
+                            100_000_000, 3, 4, 1, lambda n: synth.aniso_float4(n, seed=2)),
+}
+RADIX_KINDS = ("radix_pass", "radix_pass_rank", "radix_pass_update")
+KERNEL_SOURCES = ["kdb_onesweep.cuh", "kdb_sort.cu", "kdb_internal.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2211_00120_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_per_launch(n_items_per_launch: float):
+    """DRAM bytes per radix-pass launch from the committed ncu summary, scaled
+    to this launch size; None if absent or taken on another kernel version."""
+    p = os.path.join(ROOT, "profiles", "onesweep_traffic.json")
+    try:
+        with open(p) as f:
+            j = json.load(f)
+    except Exception:
+        return None
+    if j.get("kernel_hash") != kernel_hash():
+        return None
+    return j["dram_bytes_per_item"] * n_items_per_launch
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        rows = [r.split(", ") for r in out.strip().splitlines() if r.count(",") >= 8]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def floor_bytes(n: int, stride_bytes: int) -> float:
+    """Each live record and its one int32 read and written once per level:
+    sum over l = 0 .. L-1 of 2 (S + 4) (N - F(l-1))."""
+    L = n.bit_length()
+    tot = 0.0
+    for l in range(L):
+        prev = (1 << (l - 1)) - 1 if l >= 1 else 0
+        tot += 2.0 * (stride_bytes + 4) * (n - prev)
+    return tot
+
+
+def cpu_baseline(workload: str, target_s: float = 15.0):
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    workload: the first n points of the same generator, n grown until one
+    build takes a few seconds, then repeated to about target_s seconds."""
+    from oracle import oracle
+
+    desc, n_full, k, sf, mode, gen = WORKLOADS[workload]
+    n = 1 << 18
+    pts = gen(n_full if n_full <= (1 << 22) else (1 << 22))
+    while True:
+        sample = np.ascontiguousarray(pts[:n])
+        t0 = time.perf_counter()
+        oracle.build(sample, k, mode)
+        dt = time.perf_counter() - t0
+        if dt > target_s / 4 or n >= pts.shape[0]:
+            break
+        n *= 2
+    reps, total = 1, dt
+    while total < target_s:
+        t0 = time.perf_counter()
+        oracle.build(sample, k, mode)
+        total += time.perf_counter() - t0
+        reps += 1
+    return {"value": reps * n / total / 1e6, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} builds of the first {n} points of the same generator "
+                      f"({desc}); oracle single-threaded, {total:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    desc, n_full, k, sf, mode, gen = WORKLOADS[args.workload]
+    # each step: one oracle build of a bounded sample, so the run stays short
+    n = 1 << 20
+    pts = np.ascontiguousarray(gen(n_full)[:n]) if n_full <= n else gen(n)
+    from oracle import oracle
+
+    for _ in range(args.warmup):
+        oracle.build(pts, k, mode)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.build(pts, k, mode)
+        t.append(time.perf_counter() - t0)
+    ms = 1000.0 * sum(t) / len(t)
+    val = n / (ms / 1000.0) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Mpts/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": desc, "sample_points": n, "k": k,
+                                            "stride_bytes": 4 * sf},
+            "cpu_baseline": {"value": val, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {n} points of the workload per step"},
+            "e2e": {"value": val, "unit": "Mpts/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="uniform_1e8_f3_rr", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="warm-up and one build, nothing timed (for ncu launch lists)")
+    args = ap.parse_args()
+    if args.warmup < 3 and not args.profile_only:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    from paper_2211_00120_gb300 import kdb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    desc, n, k, sf, mode, gen = WORKLOADS[args.workload]
+    host = gen(n)
+    stride = 4 * sf
+    src = torch.from_numpy(host).cuda()
+    work = torch.empty_like(src)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        work.copy_(src)
+        kdb.kdb_build(work, k, mode)
+    torch.cuda.synchronize()
+    if args.profile_only:
+        work.copy_(src)
+        kdb.kdb_build(work, k, mode)
+        torch.cuda.synchronize()
+        return 0
+    bad = kdb.kdb_validate(work, k, mode)
+    if bad != -1:
+        raise SystemExit(f"bench: built array is not a k-d tree (node {bad})")
+
+    sampler = ClockSampler(local)
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = kdb.kdb_launch_count()
+    kdb.kdb_profile_start()
+    for s in range(args.steps):
+        work.copy_(src)  # restore the input (1.2 GB write: also evicts L2)
+        ev[s][0].record(stream)
+        kdb.kdb_build(work, k, mode)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    prof = kdb.kdb_profile_stop()
+    launches = kdb.kdb_launch_count() - launches0
+    clocks = sampler.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n / (ms / 1000.0) / 1e6
+
+    # roofline of the dominant kernel: the onesweep radix pass
+    rad = [p for p in prof if p["name"] in RADIX_KINDS]
+    r_ms = sum(p["ms"] for p in rad)
+    r_bytes = sum(p["bytes"] for p in rad)
+    r_launch = sum(p["launches"] for p in rad)
+    peak, peak_src = measured_peak()
+    achieved = r_bytes / (r_ms / 1000.0) / 1e9 if r_ms > 0 else None
+    build_ms_total = ms
+    kernel_ms = {p["name"]: round(p["ms"] / args.steps, 3) for p in prof}
+    fb = floor_bytes(n, stride)
+    traffic = traffic_per_launch(n * 1.0) if r_launch else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "kernel": "onesweep radix pass (all variants)",
+                "launches_per_step": r_launch / args.steps,
+                "kernel_share_of_step": r_ms / args.steps / build_ms_total,
+                "peak_source": peak_src,
+                "build_floor_frac": fb / (peak * 1e9) / (build_ms_total / 1000.0)}
+
+    e2e = None
+    if not args.no_e2e:
+        h_src = torch.from_numpy(host)
+        h = torch.empty_like(h_src).pin_memory()
+        times = []
+        for _ in range(max(1, args.e2e_steps)):
+            h.copy_(h_src)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            kdb.kdb_build_host(h, k, mode)
+            times.append(time.perf_counter() - t0)
+        e_ms = 1000.0 * sum(times) / len(times)
+        e2e = {"value": world * n / (e_ms / 1000.0) / 1e6, "unit": "Mpts/s",
+               "h2d_bytes_per_step": n * stride, "d2h_bytes_per_step": n * stride,
+               "ms_per_step": e_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": desc, "n_points": n, "k": k, "stride_bytes": stride,
+                           "split": "round_robin" if mode == 0 else "widest_extent",
+                           "parallelism": "replicas" if world > 1 else "single_gpu",
+                           "l2": "input 1.2+ GB > L2, restored by a device copy before each step"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "kernel_ms_per_step": kernel_ms}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -144,6 +144,27 @@ KDB_API kdb_status kdb_validate(const void* d_points, int64_t n, int k, int stri
                         kdb_split_mode mode, int64_t* h_first_bad_node, kdb_stream_t stream);
 
 /*
+ * Profiling of the library's own kernels (tracing for benchmarks).
+ * kdb_profile_start() makes every later build record a CUDA event pair around
+ * each of its kernel launches, on the launch stream; kdb_profile_stop()
+ * waits for those events and fills up to max_entries rows, one per kernel
+ * kind, with the number of launches, their summed device time and their
+ * summed algorithmic bytes (the bytes the kernel's job has to read and write,
+ * not measured traffic).  Returns the number of rows, or -1 on a CUDA error.
+ * kdb_launch_count() is the number of kernels the library has launched in
+ * this process.  Host-side state shared by all threads; for benchmarks.
+ */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double ms;
+  double bytes;
+} kdb_kernel_stat;
+KDB_API void kdb_profile_start(void);
+KDB_API int kdb_profile_stop(kdb_kernel_stat* out, int max_entries);
+KDB_API int64_t kdb_launch_count(void);
+
+/*
  * Fault injection for tests (host-side; never faults a GPU):
  *   KDB_FAULT_ALLOC       the next workspace allocation reports failure;
  *   KDB_FAULT_LOOKBACK    the next build's radix passes wait on a status value

@@ -15,6 +15,7 @@
 //   placement    the records are permuted in place by the node -> original
 //                index array (one int32 per point).
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -32,6 +33,72 @@ namespace {
 int g_fault = KDB_FAULT_NONE;
 int64_t g_fault_arg = 0;
 constexpr uint64_t kDefaultWaitNs = 4000000000ull;  // a look-back wait gives up after 4 s
+
+// -------------------------------------------------------------- profiling --
+enum Kind {
+  K_PREPASS,
+  K_RADIX,
+  K_RADIX_RANK,
+  K_RADIX_UPDATE,
+  K_LEVEL_KEYS,
+  K_WIDEST,
+  K_PLACEMENT,
+  K_VALIDATE,
+  K_COUNT
+};
+const char* const kKindName[K_COUNT] = {"prepass",      "radix_pass",  "radix_pass_rank",
+                                        "radix_pass_update", "level_keys", "widest_dims",
+                                        "placement",    "validate"};
+struct ProfRec {
+  int kind;
+  double bytes;
+  int launches;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_event_pool;
+std::atomic<int64_t> g_launches{0};
+
+cudaEvent_t take_event() {
+  cudaEvent_t e = nullptr;
+  if (!g_event_pool.empty()) {
+    e = g_event_pool.back();
+    g_event_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    e = nullptr;
+  }
+  return e;
+}
+
+// Brackets one launcher call: counts its kernel launches and, while
+// profiling is on, records an event pair around it on the launch stream.
+class Prof {
+ public:
+  Prof(int kind, double bytes, int launches, cudaStream_t st) : st_(st) {
+    g_launches += launches;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return;
+    rec_.kind = kind;
+    rec_.bytes = bytes;
+    rec_.launches = launches;
+    rec_.a = take_event();
+    rec_.b = take_event();
+    if (rec_.a && rec_.b && cudaEventRecord(rec_.a, st_) == cudaSuccess) on_ = true;
+  }
+  ~Prof() {
+    if (!on_) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (cudaEventRecord(rec_.b, st_) == cudaSuccess) g_prof.push_back(rec_);
+  }
+
+ private:
+  cudaStream_t st_;
+  ProfRec rec_{};
+  bool on_ = false;
+};
 
 // ------------------------------------------------------------------ pools --
 std::mutex g_pool_mu;
@@ -307,7 +374,10 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   pa.passes = P.rank_passes;
   pa.bbox = widest ? bbox : nullptr;
   pa.err = err;
-  KDB_CK(launch_prepass(pa, sms, st));
+  {
+    Prof pf(K_PREPASS, (double)T * k * (4.0 + (multi ? 8 : 4)), 1, st);
+    KDB_CK(launch_prepass(pa, sms, st));
+  }
   uint32_t* hcur = hist + (size_t)k * P.rank_passes * kRadixBins;
 
   // ---- per-dimension ranks
@@ -321,8 +391,10 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       for (int p = 0; p < P.rank_passes; ++p) {
         PassCtl c = ctl(T, 8 * p, hd + p * kRadixBins);
         if (p + 1 == P.rank_passes) {
+          Prof pf(K_RADIX_RANK, (double)T * 12, 1, st);
           KDB_CK(pass_u32_rank(kin, vin, ranks + (size_t)d * T, c, st));
         } else {
+          Prof pf(K_RADIX, (double)T * 16, 1, st);
           KDB_CK(pass_u32_pingpong(kin, vin, kb[p & 1], vb[p & 1], c, st));
           kin = kb[p & 1];
           vin = vb[p & 1];
@@ -336,8 +408,10 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       for (int p = 0; p < P.rank_passes; ++p) {
         PassCtl c = ctl(T, 8 * p, hd + p * kRadixBins);
         if (p + 1 == P.rank_passes) {
+          Prof pf(K_RADIX_RANK, (double)T * 16, 1, st);
           KDB_CK(pass_u64_rank(kin, vin, ranks + (size_t)d * T, d_sets, 32, c, st));
         } else {
+          Prof pf(K_RADIX, (double)T * 24, 1, st);
           KDB_CK(pass_u64_pingpong(kin, vin, kb[p & 1], vb[p & 1], c, st));
           kin = kb[p & 1];
           vin = vb[p & 1];
@@ -359,8 +433,11 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   // ---- level loop
   const int levels = (int)P.act.size();
   if (widest && levels > 0)
+  {
+    Prof pf(K_WIDEST, 0.0, 1, st);
     KDB_CK(launch_widest_root(d_sets, d_act + P.act_off[0], (uint32_t)P.act[0].size(), bbox, k,
                               boxA, dims, st));
+  }
   const uint32_t* vals_cur = nullptr;  // level 0: original order
   for (int l = 0; l < levels; ++l) {
     LevelCtx x;
@@ -370,6 +447,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     x.nact = (uint32_t)P.act[l].size();
     x.l = l;
     x.rb = P.rb;
+    x.err = err;
     const uint32_t n = P.items[l];
     // the buffer not holding vals_cur receives the level's first outputs
     uint32_t* vfree = vals_cur == valsA ? valsB : valsA;
@@ -386,7 +464,10 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     ka.keys_out = keysA;
     ka.hist = hcur;
     ka.passes = P.passes[l];
-    KDB_CK(launch_level_keys(ka, sms, st));
+    {
+      Prof pf(K_LEVEL_KEYS, (double)n * 16, 1, st);
+      KDB_CK(launch_level_keys(ka, sms, st));
+    }
     const uint64_t* kin = keysA;
     const uint32_t* vin = vals_cur ? vals_cur : vfree;
     uint64_t* kout = keysB;
@@ -394,10 +475,14 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     for (int p = 0; p < P.passes[l]; ++p) {
       PassCtl c = ctl(n, 8 * p, hcur + p * kRadixBins);
       if (p + 1 == P.passes[l]) {
+        Prof pf(K_RADIX_UPDATE, (double)n * 16, 1, st);
         KDB_CK(pass_u64_update(kin, vin, x, perm, vout, c, st));
         vals_cur = vout;
       } else {
-        KDB_CK(pass_u64_pingpong(kin, vin, kout, vout, c, st));
+        {
+          Prof pf(K_RADIX, (double)n * 24, 1, st);
+          KDB_CK(pass_u64_pingpong(kin, vin, kout, vout, c, st));
+        }
         const uint64_t* kt = kin;
         kin = kout;
         kout = const_cast<uint64_t*>(kt);
@@ -418,12 +503,16 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       wa.boxes_out = (l & 1) ? boxA : boxB;
       wa.dims = dims;
       wa.total_threads = x.nact << l;
+      Prof pf(K_WIDEST, (double)(x.nact << l) * (2 * k * 4 * 3 + 8), 1, st);
       KDB_CK(launch_widest_children(wa, st));
     }
   }
 
   // ---- placement
-  if (out_dim && !widest) KDB_CK(launch_rr_dims(dims, d_sets, (uint32_t)P.sets.size(), T, k, st));
+  if (out_dim && !widest) {
+    Prof pf(K_WIDEST, (double)T, 1, st);
+    KDB_CK(launch_rr_dims(dims, d_sets, (uint32_t)P.sets.size(), T, k, st));
+  }
   PermuteArgs pm;
   pm.pts = pts;
   pm.total = T;
@@ -431,8 +520,14 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   pm.perm = perm;
   pm.stage = at<unsigned char>(ws, P.o_stage);
   pm.err = err;
-  KDB_CK(launch_permute(pm, sms, st));
-  if (out_orig) KDB_CK(launch_unmark(perm, out_orig, T, st));
+  {
+    Prof pf(K_PLACEMENT, (double)T * (4.0 + 2.0 * P.stride), 5, st);
+    KDB_CK(launch_permute(pm, sms, st));
+  }
+  if (out_orig) {
+    Prof pf(K_PLACEMENT, (double)T * 8, 1, st);
+    KDB_CK(launch_unmark(perm, out_orig, T, st));
+  }
   if (out_dim) KDB_CK(cudaMemcpyAsync(out_dim, dims, T, cudaMemcpyDeviceToDevice, st));
   return KDB_OK;
 }
@@ -493,6 +588,53 @@ const char* kdb_status_string(kdb_status s) {
 }
 
 int kdb_version(void) { return 100; }
+
+void kdb_profile_start(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = true;
+}
+
+int kdb_profile_stop(kdb_kernel_stat* out, int max_entries) {
+  std::vector<ProfRec> recs;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = false;
+    recs.swap(g_prof);
+  }
+  kdb_kernel_stat agg[K_COUNT];
+  memset(agg, 0, sizeof agg);
+  bool ok = true;
+  for (const ProfRec& r : recs) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+      cudaGetLastError();
+      ok = false;
+    }
+    agg[r.kind].launches += r.launches;
+    agg[r.kind].ms += ms;
+    agg[r.kind].bytes += r.bytes;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (const ProfRec& r : recs) {
+      g_event_pool.push_back(r.a);
+      g_event_pool.push_back(r.b);
+    }
+  }
+  if (!ok) return -1;
+  int n = 0;
+  for (int kd = 0; kd < K_COUNT; ++kd) {
+    if (!agg[kd].launches) continue;
+    if (out && n < max_entries) {
+      out[n] = agg[kd];
+      snprintf(out[n].name, sizeof out[n].name, "%s", kKindName[kd]);
+    }
+    ++n;
+  }
+  return n < max_entries ? n : max_entries;
+}
+
+int64_t kdb_launch_count(void) { return g_launches.load(); }
 
 int kdb_debug_inject_fault(int fault, int64_t arg) {
   const int prev = g_fault;
@@ -686,6 +828,7 @@ kdb_status kdb_validate(const void* d_points, int64_t n, int k, int stride_bytes
         wa.x.nact = 1;
         wa.x.l = l;
         wa.x.rb = 0;
+        wa.x.err = at<uint32_t>(ws, o_err);
         wa.pts = pa.pts;
         wa.k = k;
         wa.stride = stride_bytes;
@@ -698,6 +841,7 @@ kdb_status kdb_validate(const void* d_points, int64_t n, int k, int stride_bytes
       }
       if (result != KDB_OK) break;
     }
+    g_launches += widest ? L + 1 : 1;  // prepass, widest passes, check
     if (launch_validate(static_cast<const unsigned char*>(d_points), N, k, stride_bytes, mode, dims,
                         bad, st) != cudaSuccess) { result = KDB_ERR_CUDA; break; }
     uint32_t h_bad = 0xFFFFFFFFu;

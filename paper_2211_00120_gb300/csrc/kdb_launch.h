@@ -16,7 +16,8 @@ struct LevelCtx {
   const ActiveEntry* act_next;  // active sets of level l+1 (device), may be empty
   uint32_t nact;
   int l;
-  int rb;  // bits of a rank
+  int rb;         // bits of a rank
+  uint32_t* err;  // device status word: kernels do nothing once it is set
 };
 
 // Radix pass geometry (one tile per block).

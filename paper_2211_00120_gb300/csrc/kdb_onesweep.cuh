@@ -107,11 +107,14 @@ __global__ void __launch_bounds__(THREADS)
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
-    s_tile = atomicAdd(c.ticket, 1u);
-    s_abort = 0;
+    // after any device error the inputs may be garbage: do nothing.  A block
+    // that leaves here has taken no ticket, so no tile ever waits on it.
+    s_abort = *reinterpret_cast<volatile uint32_t*>(c.err) != 0u;
+    if (!s_abort) s_tile = atomicAdd(c.ticket, 1u);
   }
   for (int i = tid; i < WARPS * kRadix; i += THREADS) (&s_whist[0][0])[i] = 0;
   __syncthreads();
+  if (s_abort) return;
   const uint32_t tile = s_tile;
   const uint64_t tbase = (uint64_t)tile * TILE;
   const uint32_t tn = (uint32_t)((uint64_t)c.n - tbase < (uint64_t)TILE ? (uint64_t)c.n - tbase : TILE);

@@ -23,6 +23,10 @@ struct EpiUpdate {
   __device__ void operator()(uint64_t key, uint32_t orig, uint32_t dest) const {
     const uint32_t ai = (uint32_t)(key >> (x.l + x.rb));
     const uint32_t s_rel = (uint32_t)(key >> x.rb) & ((1u << x.l) - 1u);
+    if (ai >= x.nact) {
+      atomicOr(x.err, ERR_INTERNAL);
+      return;
+    }
     const ActiveEntry e = x.act[ai];
     const SetInfo si = x.sets[e.set];
     const Tree t = make_tree(si.n);
@@ -30,6 +34,11 @@ struct EpiUpdate {
     const uint32_t j = dest - e.base;
     const uint32_t q = j - y.seg_start(s_rel);
     const uint32_t pr = y.left_size(s_rel);
+    // the item must lie inside its subtree's segment of its set
+    if (j >= y.items || q >= y.seg_start(s_rel + 1) - y.seg_start(s_rel)) {
+      atomicOr(x.err, ERR_INTERNAL);
+      return;
+    }
     if (q == pr) {
       perm[si.off + full_nodes(x.l) + s_rel] = orig;
       return;

@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(kThreads) prepass_kernel(PrepassArgs a) {
 // passes of the level's sort.
 __global__ void __launch_bounds__(kThreads) level_keys_kernel(LevelKeyArgs a) {
   __shared__ uint32_t s_hist[8 * kRadixBins];
+  if (*reinterpret_cast<volatile uint32_t*>(a.x.err)) return;  // inputs may be garbage
   const int H = a.passes * kRadixBins;
   for (int i = threadIdx.x; i < H; i += blockDim.x) s_hist[i] = 0;
   __syncthreads();
@@ -177,7 +178,12 @@ __global__ void __launch_bounds__(kThreads) level_keys_kernel(LevelKeyArgs a) {
       const uint32_t orig = a.vals ? a.vals[j] : soff + jj;
       if (!a.vals) a.vals_out[j] = orig;
       const int d = a.mode == 0 ? x.l % a.k : a.dims[soff + Fl + s_rel];
-      const uint32_t r = a.ranks[(uint64_t)d * a.total + orig];
+      uint32_t r = 0;
+      if (orig < a.total && d < a.k) {
+        r = a.ranks[(uint64_t)d * a.total + orig];
+      } else {
+        atomicOr(x.err, ERR_INTERNAL);
+      }
       key = ((uint64_t)ai << (x.l + x.rb)) | ((uint64_t)s_rel << x.rb) | r;
       a.keys_out[j] = key;
     }
@@ -217,6 +223,7 @@ __global__ void widest_children_kernel(WidestArgs a) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= a.total_threads) return;
   const LevelCtx& x = a.x;
+  if (x.err && *reinterpret_cast<volatile uint32_t*>(x.err)) return;
   const uint32_t ei = tid >> x.l;
   const uint32_t s_rel = tid & ((1u << x.l) - 1u);
   const ActiveEntry e = x.act[ei];
@@ -231,6 +238,10 @@ __global__ void widest_children_kernel(WidestArgs a) {
   }
   const int d = a.dims[si.off + s];
   const uint32_t node_rec = a.perm ? a.perm[si.off + s] : si.off + s;
+  if (d >= k || node_rec >= si.off + si.n) {
+    if (x.err) atomicOr(x.err, ERR_INTERNAL);
+    return;
+  }
   const float plane = coord_of(a.pts, node_rec, a.stride, d);
   const uint32_t c0 = 2 * s + 1;
   for (int side = 0; side < 2; ++side) {

@@ -37,6 +37,11 @@ _lib = None
 _lock = threading.Lock()
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 class KdbError(RuntimeError):
     def __init__(self, code: int, call: str):
         super().__init__(f"{call}: {status_string(code)} ({code})")
@@ -72,6 +77,9 @@ def load():
             "kdb_build_host": ([vp, i64, i32, i32, i32, vp], i32),
             "kdb_validate": ([vp, i64, i32, i32, i32, ctypes.POINTER(i64), vp], i32),
             "kdb_debug_inject_fault": ([i32, i64], i32),
+            "kdb_profile_start": ([], None),
+            "kdb_profile_stop": ([ctypes.POINTER(KernelStat), i32], i32),
+            "kdb_launch_count": ([], i64),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -166,3 +174,21 @@ def kdb_validate(points, k: int, mode: int = ROUND_ROBIN, stream=None) -> int:
 
 def kdb_debug_inject_fault(fault: int, arg: int = 0) -> int:
     return load().kdb_debug_inject_fault(fault, arg)
+
+
+def kdb_profile_start() -> None:
+    load().kdb_profile_start()
+
+
+def kdb_profile_stop() -> list[dict]:
+    """Per kernel kind: launches, summed device ms, summed algorithmic bytes."""
+    buf = (KernelStat * 16)()
+    n = load().kdb_profile_stop(buf, 16)
+    if n < 0:
+        raise KdbError(ERR_CUDA, "kdb_profile_stop")
+    return [{"name": buf[i].name.decode(), "launches": int(buf[i].launches), "ms": buf[i].ms,
+             "bytes": buf[i].bytes} for i in range(n)]
+
+
+def kdb_launch_count() -> int:
+    return int(load().kdb_launch_count())
