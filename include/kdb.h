@@ -132,6 +132,32 @@ KDB_API kdb_status kdb_build_host(void* h_points, int64_t n, int k, int stride_b
                           kdb_stream_t stream);
 
 /*
+ * kdb_build_noalloc -- kdb_build that allocates no device memory.
+ * The paper has no counterpart; this is a deployment convenience.  Some
+ * callers cannot call cudaMalloc (or a stream-ordered allocator) when they
+ * build: applications whose whole device-memory budget is fixed and reserved
+ * at start-up (for example by another framework's caching allocator), or
+ * latency-critical loops where an allocation could fail or stall at an
+ * unpredictable moment.  This entry point takes its workspace from one
+ * static device array of KDB_NOALLOC_SCRATCH_BYTES compiled into the library;
+ * every GPU that loads the library holds that array until the process exits.
+ *   d_points, n, k, stride_bytes, mode, stream: as for kdb_build.
+ * Limits: n <= KDB_NOALLOC_MAX_POINTS and kdb_workspace_size(n, k,
+ * stride_bytes, mode) <= KDB_NOALLOC_SCRATCH_BYTES; anything larger returns
+ * KDB_ERR_INVALID_ARGUMENT before any work is enqueued.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call uses the same array, which keeps the previous call's contents
+ * (the build clears what must start at zero): calls that overlap on the GPU,
+ * from several streams or host threads, race with each other and must be
+ * serialised by the caller.  Synchronises `stream`.
+ */
+#define KDB_NOALLOC_MAX_POINTS 262144
+#define KDB_NOALLOC_SCRATCH_BYTES (32u << 20)
+KDB_API kdb_status kdb_build_noalloc(void* d_points, int64_t n, int k, int stride_bytes,
+                                     kdb_split_mode mode, kdb_stream_t stream);
+
+/*
  * kdb_validate -- check the k-d condition of a level-order tree (Sec. 1):
  * for every node i and every ancestor p with split dimension d, x_d(i) <=
  * x_d(p) if i is in p's left subtree and >= if in the right one, under the

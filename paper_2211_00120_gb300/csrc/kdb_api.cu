@@ -566,6 +566,28 @@ kdb_status run(Plan& P, unsigned char* pts, void* user_ws, size_t user_bytes, in
   return s != KDB_OK ? s : f;
 }
 
+// ------------------------------------------------------- no-alloc build --
+// Workspace of kdb_build_noalloc: one static device array per GPU that loads
+// the library.  Host code must not use the symbol's host-side address; the
+// device address is looked up once per device with that device current.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[KDB_NOALLOC_SCRATCH_BYTES];
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};
+
+kdb_status noalloc_scratch(int dev, void** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return KDB_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return KDB_OK;
+}
+
 }  // namespace
 }  // namespace kdb
 
@@ -686,6 +708,42 @@ kdb_status kdb_build_ex(void* d_points, int64_t n, int k, int stride_bytes, kdb_
 kdb_status kdb_build(void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
                      kdb_stream_t stream) {
   return kdb_build_ex(d_points, n, k, stride_bytes, mode, nullptr, 0, nullptr, nullptr, stream);
+}
+
+kdb_status kdb_build_noalloc(void* d_points, int64_t n, int k, int stride_bytes,
+                             kdb_split_mode mode, kdb_stream_t stream) {
+  kdb_status s = check_common(n, k, stride_bytes);
+  if (s == KDB_OK) s = check_mode(mode);
+  if (s != KDB_OK) return s;
+  if (n > KDB_NOALLOC_MAX_POINTS) return KDB_ERR_INVALID_ARGUMENT;
+  if (n <= 1) return KDB_OK;
+  if (!d_points || (reinterpret_cast<uintptr_t>(d_points) & 3)) return KDB_ERR_INVALID_ARGUMENT;
+  Plan P;
+  P.sets.push_back(SetInfo{0u, (uint32_t)n});
+  P.total = (uint32_t)n;
+  P.k = k;
+  P.stride = stride_bytes;
+  P.mode = mode;
+  make_plan(P);
+  if (P.too_wide || P.bytes > KDB_NOALLOC_SCRATCH_BYTES) return KDB_ERR_INVALID_ARGUMENT;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return KDB_ERR_CUDA;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return KDB_ERR_CUDA;
+  }
+  void* ws = nullptr;
+  s = noalloc_scratch(dev, &ws);
+  if (s != KDB_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  s = enqueue_build(P, static_cast<unsigned char*>(d_points), ws, sms > 0 ? sms : 1, nullptr,
+                    nullptr, st);
+  kdb_status f = finish(P, ws, st);
+  return s != KDB_OK ? s : f;
 }
 
 kdb_status kdb_build_batched(void* d_points, const int64_t* h_offsets, int num_sets, int k,

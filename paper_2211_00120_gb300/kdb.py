@@ -75,6 +75,7 @@ def load():
             "kdb_build_ex": ([vp, i64, i32, i32, i32, vp, sz, vp, vp, vp], i32),
             "kdb_build_batched": ([vp, vp, i32, i32, i32, i32, vp], i32),
             "kdb_build_host": ([vp, i64, i32, i32, i32, vp], i32),
+            "kdb_build_noalloc": ([vp, i64, i32, i32, i32, vp], i32),
             "kdb_validate": ([vp, i64, i32, i32, i32, ctypes.POINTER(i64), vp], i32),
             "kdb_debug_inject_fault": ([i32, i64], i32),
             "kdb_profile_start": ([], None),
@@ -160,6 +161,18 @@ def kdb_build_host(points, k: int, mode: int = ROUND_ROBIN, stream=None) -> None
     """``points``: host (CPU, ideally pinned) tensor, permuted in place."""
     ptr, n, stride = _records(points)
     _check(load().kdb_build_host(ptr, n, k, stride, mode, _stream(stream)), "kdb_build_host")
+
+
+NOALLOC_MAX_POINTS = 262144
+
+
+def kdb_build_noalloc(points, k: int, mode: int = ROUND_ROBIN, stream=None) -> None:
+    """kdb_build whose workspace is the library's static device array: for
+    callers that cannot allocate device memory when they build.  At most
+    NOALLOC_MAX_POINTS records; calls must not overlap on the GPU."""
+    ptr, n, stride = _records(points)
+    _check(load().kdb_build_noalloc(ptr, n, k, stride, mode, _stream(stream)),
+           "kdb_build_noalloc")
 
 
 def kdb_validate(points, k: int, mode: int = ROUND_ROBIN, stream=None) -> int:
