@@ -153,6 +153,10 @@ kdb_status pool_alloc(void** p, size_t bytes, cudaMemPool_t pool, cudaStream_t s
 
 // ------------------------------------------------------------------- plan --
 inline int ceil_div_i(int a, int b) { return (a + b - 1) / b; }
+// A level sorts segment by segment when every subtree of every active set
+// has at least 2^13 - 1 items (>= one radix tile), i.e. L_b - l - 1 >= 13.
+constexpr int kSegMinLog = 13;
+static_assert((1 << kSegMinLog) - 1 >= kSortTile, "segments must span a tile");
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Plan {
@@ -169,6 +173,9 @@ struct Plan {
   std::vector<uint32_t> items;                // per level
   std::vector<int> passes;                    // per level
   std::vector<uint32_t> box_slots;            // per level (widest)
+  std::vector<char> seg;                      // per level: segmented sort (32-bit rank keys)
+  std::vector<uint32_t> nseg, chunks;         // per segmented level
+  std::vector<size_t> hist_off;               // per level: offset (in u32) into the histograms
   uint32_t max_items = 0, max_boxes = 0;
   int total_passes = 0;
 
@@ -194,8 +201,14 @@ void make_plan(Plan& P) {
   P.items.assign(levels, 0);
   P.passes.assign(levels, 0);
   P.box_slots.assign(levels, 0);
+  P.seg.assign(levels, 0);
+  P.nseg.assign(levels, 0);
+  P.chunks.assign(levels, 0);
+  P.hist_off.assign(levels, 0);
+  size_t hist_words = (size_t)P.k * P.rank_passes * kRadixBins;
   for (int l = 0; l < levels; ++l) {
     uint32_t base = 0;
+    bool all_long = true;  // every segment of every active set >= 2^13 - 1 items
     for (uint32_t b = 0; b < ns; ++b) {
       const uint32_t n = P.sets[b].n;
       if (n < 2 || num_levels(n) < l + 2) continue;
@@ -204,15 +217,35 @@ void make_plan(Plan& P) {
       e.base = base;
       e.next = -1;
       e.box0 = (uint32_t)P.act[l].size() << l;
+      e.chunk0 = 0;
+      e.cps = 0;
       base += n - full_nodes(l);
+      if (num_levels(n) - l - 1 < kSegMinLog) all_long = false;
       P.act[l].push_back(e);
     }
     P.items[l] = base;
     const uint32_t na = (uint32_t)P.act[l].size();
-    const int abits = na > 1 ? bits_for(na) : 0;
-    if (abits + l + P.rb > 64) P.too_wide = true;  // packed key would not fit 64 bits
-    P.passes[l] = ceil_div_i(abits + l + P.rb, 8);
-    if (P.passes[l] < 1) P.passes[l] = 1;
+    P.seg[l] = all_long && na > 0 && P.rb <= 32;
+    P.hist_off[l] = hist_words;
+    if (P.seg[l]) {
+      P.passes[l] = std::max(1, ceil_div_i(P.rb, 8));
+      P.nseg[l] = na << l;
+      uint32_t chunk = 0;
+      for (ActiveEntry& e : P.act[l]) {
+        const int h = num_levels(P.sets[e.set].n) - l - 1;
+        const uint32_t full = (uint32_t)((1ull << (h + 1)) - 1);
+        e.chunk0 = chunk;
+        e.cps = (full + kSegChunk - 1) / kSegChunk;
+        chunk += e.cps << l;
+      }
+      P.chunks[l] = chunk;
+      hist_words += (size_t)P.passes[l] * P.nseg[l] * kRadixBins;
+    } else {
+      const int abits = na > 1 ? bits_for(na) : 0;
+      if (abits + l + P.rb > 64) P.too_wide = true;  // packed key would not fit 64 bits
+      P.passes[l] = std::max(1, ceil_div_i(abits + l + P.rb, 8));
+      hist_words += (size_t)P.passes[l] * kRadixBins;
+    }
     P.box_slots[l] = na << l;
     P.max_items = std::max(P.max_items, base);
     P.max_boxes = std::max(P.max_boxes, P.box_slots[l]);
@@ -248,7 +281,7 @@ void make_plan(Plan& P) {
   P.o_boxB = take(box_bytes);
   const size_t tiles = (std::max<uint64_t>(T, P.max_items) + kSortTile - 1) / kSortTile;
   P.o_status = take(tiles * kRadixBins * 8);
-  P.o_hist = take((size_t)P.total_passes * kRadixBins * 4);
+  P.o_hist = take(hist_words * 4);
   P.o_tickets = take((size_t)P.total_passes * 4);
   P.o_err = take(4);
   P.o_bbox = take(P.sets.size() * 2 * P.k * 4);
@@ -451,6 +484,51 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     const uint32_t n = P.items[l];
     // the buffer not holding vals_cur receives the level's first outputs
     uint32_t* vfree = vals_cur == valsA ? valsB : valsA;
+    hcur = hist + P.hist_off[l];
+    if (P.seg[l]) {
+      SegKeyArgs sa;
+      sa.x = x;
+      sa.chunks = P.chunks[l];
+      sa.vals = vals_cur;
+      sa.vals_out = vfree;
+      sa.ranks = ranks;
+      sa.total = T;
+      sa.k = k;
+      sa.mode = P.mode;
+      sa.dims = dims;
+      sa.keys_out = reinterpret_cast<uint32_t*>(keysA);
+      sa.seg_hist = hcur;
+      sa.nseg = P.nseg[l];
+      sa.passes = P.passes[l];
+      {
+        Prof pf(K_LEVEL_KEYS, (double)n * 12, 1, st);
+        KDB_CK(launch_seg_level_keys(sa, st));
+      }
+      const uint32_t* kin = reinterpret_cast<uint32_t*>(keysA);
+      const uint32_t* vin = vals_cur ? vals_cur : vfree;
+      uint32_t* kout = reinterpret_cast<uint32_t*>(keysB);
+      uint32_t* vout = vin == valsA ? valsB : valsA;
+      for (int p = 0; p < P.passes[l]; ++p) {
+        PassCtl c = ctl(n, 8 * p, nullptr);
+        const uint32_t* sh = hcur + (size_t)p * P.nseg[l] * kRadixBins;
+        if (p + 1 == P.passes[l]) {
+          Prof pf(K_RADIX_UPDATE, (double)n * 12, 1, st);
+          KDB_CK(seg_pass_update(kin, vin, x, sh, perm, vout, c, st));
+          vals_cur = vout;
+        } else {
+          {
+            Prof pf(K_RADIX, (double)n * 16, 1, st);
+            KDB_CK(seg_pass_pingpong(kin, vin, kout, vout, x, sh, c, st));
+          }
+          const uint32_t* kt = kin;
+          kin = kout;
+          kout = const_cast<uint32_t*>(kt);
+          const uint32_t* vt = vin;
+          vin = vout;
+          vout = const_cast<uint32_t*>(vt);
+        }
+      }
+    } else {
     LevelKeyArgs ka;
     ka.x = x;
     ka.items = n;
@@ -491,7 +569,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
         vout = const_cast<uint32_t*>(vt);
       }
     }
-    hcur += (size_t)P.passes[l] * kRadixBins;
+    }
     if (widest) {
       WidestArgs wa;
       wa.x = x;

@@ -164,6 +164,8 @@ struct ActiveEntry {
   uint32_t base;  // start of this set's items in the level's concatenated array
   int32_t next;   // index of the same set in the next level's active list, -1 if it leaves
   uint32_t box0;  // first box slot of this set at this level (widest mode)
+  uint32_t chunk0;  // first key-build chunk of this set (segmented levels)
+  uint32_t cps;     // key-build chunks per subtree segment (segmented levels)
 };
 
 }  // namespace kdb

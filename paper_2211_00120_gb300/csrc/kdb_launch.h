@@ -40,6 +40,15 @@ cudaError_t pass_u64_update(const uint64_t* kin, const uint32_t* vin, const Leve
                             uint32_t* perm, uint32_t* vals_next, const PassCtl& c,
                             cudaStream_t st);
 
+// segmented passes over 32-bit rank keys (kdb_sort.cu); every segment of the
+// level must be at least one tile long
+cudaError_t seg_pass_pingpong(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
+                              uint32_t* vout, const LevelCtx& x, const uint32_t* seg_hist,
+                              const PassCtl& c, cudaStream_t st);
+cudaError_t seg_pass_update(const uint32_t* kin, const uint32_t* vin, const LevelCtx& x,
+                            const uint32_t* seg_hist, uint32_t* perm, uint32_t* vals_next,
+                            const PassCtl& c, cudaStream_t st);
+
 // tree kernels (kdb_tree.cu)
 struct PrepassArgs {
   const unsigned char* pts;
@@ -70,6 +79,25 @@ struct LevelKeyArgs {
   int passes;
 };
 cudaError_t launch_level_keys(const LevelKeyArgs& a, int num_sms, cudaStream_t st);
+
+// Segmented levels: one block per (segment, chunk of kSegChunk items); keys
+// are the 32-bit ranks, histograms are per (pass, segment, digit).
+constexpr uint32_t kSegChunk = 8192;
+struct SegKeyArgs {
+  LevelCtx x;
+  uint32_t chunks;          // total chunks of the level
+  const uint32_t* vals;     // original index per item, or nullptr (level 0)
+  uint32_t* vals_out;       // level 0 only
+  const uint32_t* ranks;
+  uint32_t total;
+  int k, mode;
+  const uint8_t* dims;
+  uint32_t* keys_out;
+  uint32_t* seg_hist;       // [passes][nseg][256]
+  uint32_t nseg;
+  int passes;
+};
+cudaError_t launch_seg_level_keys(const SegKeyArgs& a, cudaStream_t st);
 
 struct WidestArgs {
   LevelCtx x;              // x.act is the level whose nodes are split

@@ -1,6 +1,7 @@
 // kdb_sort.cu -- instantiations of the onesweep pass and the fused tag update.
 #include "kdb_launch.h"
 #include "kdb_onesweep.cuh"
+#include "kdb_segsort.cuh"
 
 namespace kdb {
 
@@ -85,6 +86,32 @@ cudaError_t pass_u64_update(const uint64_t* kin, const uint32_t* vin, const Leve
                             uint32_t* perm, uint32_t* vals_next, const PassCtl& c,
                             cudaStream_t st) {
   return run_pass(kin, vin, EpiUpdate{x, perm, vals_next}, c, st);
+}
+
+template <class Epi>
+static cudaError_t run_seg_pass(const uint32_t* kin, const uint32_t* vin, const LevelCtx& x,
+                                const uint32_t* seg_hist, const Epi& epi, const PassCtl& c,
+                                cudaStream_t st) {
+  if (c.n == 0) return cudaSuccess;
+  auto kern = seg_onesweep_pass<kSortThreads, kSortItems, Epi>;
+  const size_t smem = (size_t)kSortTile * 8;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const uint32_t tiles = (c.n + kSortTile - 1) / kSortTile;
+  kern<<<tiles, kSortThreads, smem, st>>>(kin, vin, c, x, seg_hist, epi);
+  return cudaGetLastError();
+}
+
+cudaError_t seg_pass_pingpong(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
+                              uint32_t* vout, const LevelCtx& x, const uint32_t* seg_hist,
+                              const PassCtl& c, cudaStream_t st) {
+  return run_seg_pass(kin, vin, x, seg_hist, SegEpiPingPong{kout, vout}, c, st);
+}
+
+cudaError_t seg_pass_update(const uint32_t* kin, const uint32_t* vin, const LevelCtx& x,
+                            const uint32_t* seg_hist, uint32_t* perm, uint32_t* vals_next,
+                            const PassCtl& c, cudaStream_t st) {
+  return run_seg_pass(kin, vin, x, seg_hist, SegEpiUpdate{perm, vals_next}, c, st);
 }
 
 }  // namespace kdb

@@ -195,6 +195,58 @@ __global__ void __launch_bounds__(kThreads) level_keys_kernel(LevelKeyArgs a) {
     if (s_hist[i]) atomicAdd(a.hist + i, s_hist[i]);
 }
 
+// Segmented variant: each block owns one chunk of one subtree segment, so the
+// segment is known without a search and the block's digit histograms belong to
+// one segment.  Key = rank of the item in its subtree's split dimension.
+__global__ void __launch_bounds__(kThreads) seg_level_keys_kernel(SegKeyArgs a) {
+  __shared__ uint32_t s_hist[4 * kRadixBins];
+  if (*reinterpret_cast<volatile uint32_t*>(a.x.err)) return;
+  const LevelCtx& x = a.x;
+  const uint32_t g = blockIdx.x;
+  uint32_t ai = 0;
+  {
+    uint32_t lo = 0, hi = x.nact;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (x.act[mid].chunk0 <= g) lo = mid; else hi = mid;
+    }
+    ai = lo;
+  }
+  const ActiveEntry e = x.act[ai];
+  const SetInfo si = x.sets[e.set];
+  const LevelLayout y = LevelLayout::make(make_tree(si.n), x.l);
+  const uint32_t c = g - e.chunk0;
+  const uint32_t s_rel = c / e.cps, ci = c % e.cps;
+  if (s_rel >= y.nseg) return;
+  const uint32_t sbeg = e.base + y.seg_start(s_rel), send = e.base + y.seg_start(s_rel + 1);
+  const uint32_t beg = sbeg + ci * kSegChunk;
+  if (beg >= send) return;
+  const uint32_t end = beg + kSegChunk < send ? beg + kSegChunk : send;
+  const int H = a.passes * kRadixBins;
+  for (int i = threadIdx.x; i < H; i += blockDim.x) s_hist[i] = 0;
+  __syncthreads();
+  const int d = a.mode == 0 ? x.l % a.k : a.dims[si.off + full_nodes(x.l) + s_rel];
+  const uint32_t* rank_d = a.ranks + (uint64_t)(d < a.k ? d : 0) * a.total;
+  for (uint32_t j = beg + threadIdx.x; j < end; j += blockDim.x) {
+    const uint32_t orig = a.vals ? a.vals[j] : si.off + (j - e.base);
+    if (!a.vals) a.vals_out[j] = orig;
+    uint32_t r = 0;
+    if (orig < a.total && d < a.k) r = rank_d[orig];
+    else atomicOr(x.err, ERR_INTERNAL);
+    a.keys_out[j] = r;
+    for (int p = 0; p < a.passes; ++p) atomicAdd(&s_hist[p * kRadixBins + ((r >> (8 * p)) & 0xFF)], 1u);
+  }
+  __syncthreads();
+  const uint32_t gid = (ai << x.l) | s_rel;
+  for (int i = threadIdx.x; i < H; i += blockDim.x) {
+    const uint32_t v = s_hist[i];
+    if (v) {
+      const int p = i / kRadixBins, dg = i % kRadixBins;
+      atomicAdd(a.seg_hist + ((uint64_t)p * a.nseg + gid) * kRadixBins + dg, v);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Split-widest (Sec. 6).  The domain of the root is the set's scene box; the
 // domain of a child is its parent's domain with one side replaced by the
@@ -442,6 +494,12 @@ cudaError_t launch_level_keys(const LevelKeyArgs& a, int num_sms, cudaStream_t s
   const uint32_t need = (a.items + kThreads - 1) / kThreads;
   if (grid > need) grid = need;
   level_keys_kernel<<<grid, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_level_keys(const SegKeyArgs& a, cudaStream_t st) {
+  if (a.chunks == 0) return cudaSuccess;
+  seg_level_keys_kernel<<<a.chunks, kThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

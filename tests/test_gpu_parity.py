@@ -213,3 +213,24 @@ def test_lookback_wait_runs_out_and_context_stays_usable():
     assert e.value.code == kdb.ERR_TIMEOUT
     assert np.array_equal(d.cpu().numpy(), pts)
     assert_same(pts, 3, RR)
+
+
+@pytest.mark.parametrize("mode", [RR, WIDEST])
+def test_batched_large_sets_use_segmented_levels(mode):
+    """All sets long enough that the top levels sort segment by segment."""
+    sizes = [20000, 16383, 70001, 40000, 16384, 131071]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    pts = synth.uniform(int(offs[-1]), 3, seed=8)
+    d = torch.from_numpy(pts).cuda()
+    kdb.kdb_build_batched(d, offs.tolist(), 3, mode)
+    got = d.cpu().numpy()
+    for b in range(len(sizes)):
+        lo, hi = offs[b], offs[b + 1]
+        want, _ = oracle.build(pts[lo:hi], 3, mode)
+        assert np.array_equal(got[lo:hi].view(np.uint32), want.view(np.uint32)), f"set {b}"
+
+
+@pytest.mark.parametrize("mode", [RR, WIDEST])
+def test_large_single_builds_exact(mode):
+    """2^21 + 3 points: 9 segmented levels then the packed-key levels."""
+    assert_same(synth.mixed((1 << 21) + 3, 3, seed=77), 3, mode)
