@@ -44,11 +44,12 @@ enum Kind {
   K_WIDEST,
   K_PLACEMENT,
   K_VALIDATE,
+  K_LOCAL,
   K_COUNT
 };
 const char* const kKindName[K_COUNT] = {"prepass",      "radix_pass",  "radix_pass_rank",
                                         "radix_pass_update", "level_keys", "widest_dims",
-                                        "placement",    "validate"};
+                                        "placement",    "validate",   "local_finish"};
 struct ProfRec {
   int kind;
   double bytes;
@@ -183,7 +184,21 @@ struct Plan {
   size_t o_keysA, o_keysB, o_valsA, o_valsB, o_ckeys, o_ranks, o_perm, o_dims, o_boxA, o_boxB,
       o_status, o_hist, o_tickets, o_err, o_bbox, o_stage, o_sets, o_act, bytes;
   std::vector<size_t> act_off;  // element offset of each level's active list in the table
+  // local finish (k <= kLocalMaxK): subtrees of <= 2^13 - 1 points run on chip
+  bool use_local = false;
+  std::vector<LocalSet> lsets;
+  std::vector<LocalWork> work;
+  uint32_t local_boxes = 0;
+  size_t o_vloc, o_lbox, o_lsets, o_work;
 };
+
+// Levels run on the whole GPU for set b: all of them (packed keys), or, with
+// the local finish, those whose subtrees still hold >= 2^13 - 1 points.
+inline int global_levels(const Plan& P, uint32_t n) {
+  if (n < 2) return 0;
+  const int L = num_levels(n);
+  return P.use_local ? std::max(0, L - kLocalLog) : L - 1;
+}
 
 void make_plan(Plan& P) {
   uint32_t nmax = 0;
@@ -196,7 +211,27 @@ void make_plan(Plan& P) {
   const uint32_t ns = (uint32_t)P.sets.size();
   P.set_bits = ns > 1 ? bits_for(ns) : 0;
   P.rank_passes = ceil_div_i(32 + P.set_bits, 8);
-  const int levels = std::max(0, P.Lmax - 1);
+  P.use_local = P.k <= kLocalMaxK;
+  int levels = 0;
+  for (const SetInfo& si : P.sets) levels = std::max(levels, global_levels(P, si.n));
+  if (P.use_local) {
+    P.lsets.resize(ns);
+    uint32_t lbox = 0;
+    for (uint32_t b = 0; b < ns; ++b) {
+      const SetInfo& si = P.sets[b];
+      LocalSet ls;
+      ls.off = si.off;
+      ls.n = si.n;
+      ls.l0 = global_levels(P, si.n);
+      ls.lbox0 = lbox;
+      if (si.n >= 2) {
+        for (uint32_t r = 0; r < (1u << ls.l0); ++r) P.work.push_back(LocalWork{b, r});
+        if (ls.l0 > 0) lbox += 1u << ls.l0;
+      }
+      P.lsets[b] = ls;
+    }
+    P.local_boxes = lbox;
+  }
   P.act.assign(levels, {});
   P.items.assign(levels, 0);
   P.passes.assign(levels, 0);
@@ -211,7 +246,7 @@ void make_plan(Plan& P) {
     bool all_long = true;  // every segment of every active set >= 2^13 - 1 items
     for (uint32_t b = 0; b < ns; ++b) {
       const uint32_t n = P.sets[b].n;
-      if (n < 2 || num_levels(n) < l + 2) continue;
+      if (l >= global_levels(P, n)) continue;
       ActiveEntry e;
       e.set = b;
       e.base = base;
@@ -294,6 +329,11 @@ void make_plan(Plan& P) {
     nact += P.act[l].size();
   }
   P.o_act = take(std::max<size_t>(nact, 1) * sizeof(ActiveEntry));
+  P.o_vloc = take(P.use_local ? T * 4 : 0);
+  P.o_lbox = take(P.use_local && P.mode == KDB_SPLIT_WIDEST_EXTENT
+                      ? (size_t)P.local_boxes * 2 * P.k * 4 : 0);
+  P.o_lsets = take(P.lsets.size() * sizeof(LocalSet));
+  P.o_work = take(P.work.size() * sizeof(LocalWork));
   P.bytes = o;
 }
 
@@ -359,6 +399,17 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
                              cudaMemcpyHostToDevice, st));
     // pageable source: the copy has completed when cudaMemcpyAsync returns
   }
+  uint32_t* vals_local = at<uint32_t>(ws, P.o_vloc);
+  float* boxes_local = at<float>(ws, P.o_lbox);
+  LocalSet* d_lsets = at<LocalSet>(ws, P.o_lsets);
+  LocalWork* d_work = at<LocalWork>(ws, P.o_work);
+  if (P.use_local) {
+    KDB_CK(cudaMemcpyAsync(d_lsets, P.lsets.data(), P.lsets.size() * sizeof(LocalSet),
+                           cudaMemcpyHostToDevice, st));
+    if (!P.work.empty())
+      KDB_CK(cudaMemcpyAsync(d_work, P.work.data(), P.work.size() * sizeof(LocalWork),
+                             cudaMemcpyHostToDevice, st));
+  }
   KDB_CK(cudaMemsetAsync(status, 0, P.o_hist - P.o_status, st));
   KDB_CK(cudaMemsetAsync(hist, 0, P.o_bbox - P.o_hist, st));  // hist, tickets, err
   if (widest) {
@@ -379,7 +430,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   if (fault_lb) g_fault = KDB_FAULT_NONE;
   int g = 0;  // pass counter within the build
   auto ctl = [&](uint32_t n, int shift, const uint32_t* h) {
-    PassCtl c;
+    PassCtl c{};
     c.n = n;
     c.shift = shift;
     c.hist = h;
@@ -394,7 +445,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   };
 
   // ---- prepass
-  PrepassArgs pa;
+  PrepassArgs pa{};
   pa.pts = pts;
   pa.total = T;
   pa.k = k;
@@ -473,7 +524,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   }
   const uint32_t* vals_cur = nullptr;  // level 0: original order
   for (int l = 0; l < levels; ++l) {
-    LevelCtx x;
+    LevelCtx x{};
     x.sets = d_sets;
     x.act = d_act + P.act_off[l];
     x.act_next = l + 1 < levels ? d_act + P.act_off[l + 1] : nullptr;
@@ -481,12 +532,14 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     x.l = l;
     x.rb = P.rb;
     x.err = err;
+    x.local_next = P.use_local ? 1 : 0;
+    x.vals_local = vals_local;
     const uint32_t n = P.items[l];
     // the buffer not holding vals_cur receives the level's first outputs
     uint32_t* vfree = vals_cur == valsA ? valsB : valsA;
     hcur = hist + P.hist_off[l];
     if (P.seg[l]) {
-      SegKeyArgs sa;
+      SegKeyArgs sa{};
       sa.x = x;
       sa.chunks = P.chunks[l];
       sa.vals = vals_cur;
@@ -529,7 +582,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
         }
       }
     } else {
-    LevelKeyArgs ka;
+    LevelKeyArgs ka{};
     ka.x = x;
     ka.items = n;
     ka.vals = vals_cur;
@@ -571,7 +624,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     }
     }
     if (widest) {
-      WidestArgs wa;
+      WidestArgs wa{};
       wa.x = x;
       wa.pts = pts;
       wa.k = k;
@@ -581,9 +634,33 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       wa.boxes_out = (l & 1) ? boxA : boxB;
       wa.dims = dims;
       wa.total_threads = x.nact << l;
+      wa.boxes_local = boxes_local;
+      wa.lsets = P.use_local ? d_lsets : nullptr;
       Prof pf(K_WIDEST, (double)(x.nact << l) * (2 * k * 4 * 3 + 8), 1, st);
       KDB_CK(launch_widest_children(wa, st));
     }
+  }
+
+  // ---- subtrees small enough for one block: all remaining levels on chip
+  if (P.use_local && !P.work.empty()) {
+    LocalArgs la{};
+    la.work = d_work;
+    la.nwork = (uint32_t)P.work.size();
+    la.lsets = d_lsets;
+    la.vals_local = vals_local;
+    la.ranks = ranks;
+    la.total = T;
+    la.k = k;
+    la.mode = P.mode;
+    la.pts = pts;
+    la.stride = P.stride;
+    la.boxes_local = boxes_local;
+    la.bbox = bbox;
+    la.dims = dims;
+    la.perm = perm;
+    la.err = err;
+    Prof pf(K_LOCAL, (double)T * (4.0 + 4.0 * k + 4.0), 1, st);
+    KDB_CK(launch_local_finish(la, st));
   }
 
   // ---- placement
@@ -591,7 +668,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     Prof pf(K_WIDEST, (double)T, 1, st);
     KDB_CK(launch_rr_dims(dims, d_sets, (uint32_t)P.sets.size(), T, k, st));
   }
-  PermuteArgs pm;
+  PermuteArgs pm{};
   pm.pts = pts;
   pm.total = T;
   pm.stride = P.stride;
@@ -957,7 +1034,7 @@ kdb_status kdb_validate(const void* d_points, int64_t n, int k, int stride_bytes
       if (launch_widest_root(pa.sets, d_act, 1, pa.bbox, k, at<float>(ws, o_bA), dims, st) !=
           cudaSuccess) { result = KDB_ERR_CUDA; break; }
       for (int l = 0; l + 1 < L; ++l) {
-        WidestArgs wa;
+        WidestArgs wa{};
         wa.x.sets = pa.sets;
         wa.x.act = d_act + l;
         wa.x.act_next = l + 1 < (int)act.size() ? d_act + l + 1 : nullptr;

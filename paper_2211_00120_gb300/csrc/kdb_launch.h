@@ -16,9 +16,45 @@ struct LevelCtx {
   const ActiveEntry* act_next;  // active sets of level l+1 (device), may be empty
   uint32_t nact;
   int l;
-  int rb;         // bits of a rank
-  uint32_t* err;  // device status word: kernels do nothing once it is set
+  int rb;          // bits of a rank
+  uint32_t* err;   // device status word: kernels do nothing once it is set
+  int local_next;  // 1: a set that leaves the active list goes to the local finish
+  uint32_t* vals_local;  // per set at its first record: the local level's items
 };
+
+// Local finish of small subtrees (kdb_local.cu).
+constexpr int kLocalThreads = 1024;
+constexpr int kLocalLog = 13;                     // subtrees of <= 2^13 - 1 points
+constexpr int kLocalCap = 1 << kLocalLog;         // 8192
+constexpr int kLocalMax = kLocalCap - 1;
+constexpr int kLocalMaxK = 4;                     // shared-memory budget: k + 1 lists
+struct LocalSet {
+  uint32_t off, n;
+  int l0;          // level at which the set's subtrees are finished locally
+  uint32_t lbox0;  // first slot of its subtrees' domains in the local box array
+};
+struct LocalWork {
+  uint32_t set;
+  uint32_t s_rel;  // subtree index on level l0 of that set
+};
+struct LocalArgs {
+  const LocalWork* work;
+  uint32_t nwork;
+  const LocalSet* lsets;
+  const uint32_t* vals_local;
+  const uint32_t* ranks;
+  uint32_t total;
+  int k, mode;
+  const unsigned char* pts;
+  int stride;
+  const float* boxes_local;  // widest: domain of each local root with l0 > 0
+  const uint32_t* bbox;      // widest: scene box keys per set (roots with l0 = 0)
+  uint8_t* dims;
+  uint32_t* perm;
+  uint32_t* err;
+};
+size_t local_smem_bytes(int k);
+cudaError_t launch_local_finish(const LocalArgs& a, cudaStream_t st);
 
 // Radix pass geometry (one tile per block).
 constexpr int kSortThreads = 256;
@@ -108,6 +144,8 @@ struct WidestArgs {
   float* boxes_out;        // per next-level active entry: 2^(l+1) boxes
   uint8_t* dims;           // per node
   uint32_t total_threads;  // nact << l
+  float* boxes_local;      // domains of the roots of local subtrees (sets leaving)
+  const LocalSet* lsets;   // their slots (nullptr: no local finish)
 };
 cudaError_t launch_widest_root(const SetInfo* sets, const ActiveEntry* act0, uint32_t nact,
                                const uint32_t* bbox, int k, float* boxes0, uint8_t* dims,

@@ -30,9 +30,10 @@ struct TileSegs {
   uint32_t pr[2];     // pivot rank ss(lChild(s)) (Observation 1)
   uint32_t ebase[2];  // first position of the segment's set in this level
   uint32_t node[2];   // first slot of the set in perm + F(l) + srel: node s
-  uint32_t child0[2]; // where the set's children go: next level's base, or the
-                      // set's lowest-level slot F(l+1) in perm
-  int32_t next[2];    // set's entry in the next level's active list, or -1
+  uint32_t child0[2]; // where the set's children go: next level's base, the
+                      // set's first record (local level array), or its
+                      // lowest-level slot F(l+1) in perm
+  int32_t next[2];    // 0: next level's array, 1: perm (lowest level), 2: local array
 };
 
 __device__ inline void fill_update_info(const LevelCtx& x, TileSegs& ts, int i) {
@@ -42,8 +43,16 @@ __device__ inline void fill_update_info(const LevelCtx& x, TileSegs& ts, int i) 
   ts.pr[i] = y.left_size(ts.srel[i]);
   ts.ebase[i] = e.base;
   ts.node[i] = si.off + full_nodes(x.l) + ts.srel[i];
-  ts.next[i] = e.next;
-  ts.child0[i] = e.next >= 0 ? x.act_next[e.next].base : si.off + full_nodes(x.l + 1);
+  if (e.next >= 0) {
+    ts.next[i] = 0;
+    ts.child0[i] = x.act_next[e.next].base;
+  } else if (x.local_next) {
+    ts.next[i] = 2;
+    ts.child0[i] = si.off;
+  } else {
+    ts.next[i] = 1;
+    ts.child0[i] = si.off + full_nodes(x.l + 1);
+  }
 }
 
 __device__ inline uint32_t find_active_entry(const ActiveEntry* act, uint32_t nact, uint32_t j) {
@@ -271,6 +280,7 @@ struct SegEpiUpdate {
   static constexpr bool kNeedsUpdateInfo = true;
   uint32_t* perm;
   uint32_t* vals_next;
+  uint32_t* vals_local;
   __device__ void operator()(uint32_t, uint32_t orig, uint32_t dest, uint32_t seg,
                              const TileSegs& ts) const {
     const uint32_t q = dest - ts.start[seg];
@@ -280,10 +290,8 @@ struct SegEpiUpdate {
       return;
     }
     const uint32_t jn = dest - ts.ebase[seg] - ts.srel[seg] - (q > pr ? 1u : 0u);
-    if (ts.next[seg] < 0)
-      perm[ts.child0[seg] + jn] = orig;
-    else
-      vals_next[ts.child0[seg] + jn] = orig;
+    uint32_t* out = ts.next[seg] == 0 ? vals_next : (ts.next[seg] == 1 ? perm : vals_local);
+    out[ts.child0[seg] + jn] = orig;
   }
 };
 

@@ -111,7 +111,7 @@ cudaError_t seg_pass_pingpong(const uint32_t* kin, const uint32_t* vin, uint32_t
 cudaError_t seg_pass_update(const uint32_t* kin, const uint32_t* vin, const LevelCtx& x,
                             const uint32_t* seg_hist, uint32_t* perm, uint32_t* vals_next,
                             const PassCtl& c, cudaStream_t st) {
-  return run_seg_pass(kin, vin, x, seg_hist, SegEpiUpdate{perm, vals_next}, c, st);
+  return run_seg_pass(kin, vin, x, seg_hist, SegEpiUpdate{perm, vals_next, x.vals_local}, c, st);
 }
 
 }  // namespace kdb

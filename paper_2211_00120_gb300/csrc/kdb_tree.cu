@@ -302,8 +302,12 @@ __global__ void widest_children_kernel(WidestArgs a) {
     const float keep = side == 0 ? hi[d] : lo[d];
     if (side == 0) hi[d] = plane; else lo[d] = plane;
     a.dims[si.off + c] = (uint8_t)widest_of(lo, hi, k);
-    if (e.next >= 0) {
-      float* bout = a.boxes_out + ((uint64_t)x.act_next[e.next].box0 + 2 * s_rel + side) * 2 * k;
+    float* bout = nullptr;
+    if (e.next >= 0)
+      bout = a.boxes_out + ((uint64_t)x.act_next[e.next].box0 + 2 * s_rel + side) * 2 * k;
+    else if (a.lsets)  // the child is the root of a subtree finished locally
+      bout = a.boxes_local + ((uint64_t)a.lsets[e.set].lbox0 + 2 * s_rel + side) * 2 * k;
+    if (bout) {
       for (int dd = 0; dd < k; ++dd) {
         bout[dd] = lo[dd];
         bout[k + dd] = hi[dd];
