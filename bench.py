@@ -197,6 +197,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--points", type=int, default=0,
+                    help="override the workload's number of points (small profiling cases)")
     ap.add_argument("--profile-only", action="store_true",
                     help="warm-up and one build, nothing timed (for ncu launch lists)")
     args = ap.parse_args()
@@ -219,6 +221,9 @@ def main():
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     desc, n, k, sf, mode, gen = WORKLOADS[args.workload]
+    if args.points:
+        n = args.points
+        desc = f"{desc} [first {n} points]"
     host = gen(n)
     stride = 4 * sf
     src = torch.from_numpy(host).cuda()

@@ -157,7 +157,7 @@ inline int ceil_div_i(int a, int b) { return (a + b - 1) / b; }
 // A level sorts segment by segment when every subtree of every active set
 // has at least 2^13 - 1 items (>= one radix tile), i.e. L_b - l - 1 >= 13.
 constexpr int kSegMinLog = 13;
-static_assert((1 << kSegMinLog) - 1 >= kSortTile, "segments must span a tile");
+static_assert((1 << kSegMinLog) - 1 >= kSegTile, "segments must span a tile");
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Plan {
@@ -189,7 +189,8 @@ struct Plan {
   std::vector<LocalSet> lsets;
   std::vector<LocalWork> work;
   uint32_t local_boxes = 0;
-  size_t o_vloc, o_lbox, o_lsets, o_work;
+  size_t o_vloc, o_lbox, o_lsets, o_work, o_whole;
+  uint64_t kstride = 0;  // elements between two dimensions' coordinate keys
 };
 
 // Levels run on the whole GPU for set b: all of them (packed keys), or, with
@@ -307,14 +308,17 @@ void make_plan(Plan& P) {
   P.o_keysB = take(T * 8);
   P.o_valsA = take(T * 4);
   P.o_valsB = take(T * 4);
-  P.o_ckeys = take(T * P.k * ksz);
+  P.kstride = (T + 63) & ~uint64_t(63);  // per-dimension key arrays start 256-byte aligned
+  P.o_ckeys = take(P.kstride * P.k * ksz);
   P.o_ranks = take(T * P.k * 4);
   P.o_perm = take(T * 4);
   P.o_dims = take(T);
   const size_t box_bytes = P.mode == KDB_SPLIT_WIDEST_EXTENT ? (size_t)P.max_boxes * 2 * P.k * 4 : 0;
   P.o_boxA = take(box_bytes);
   P.o_boxB = take(box_bytes);
-  const size_t tiles = (std::max<uint64_t>(T, P.max_items) + kSortTile - 1) / kSortTile;
+  const size_t tiles =
+      (std::max<uint64_t>(T, P.max_items) + std::min(kSortTile, kSegTile) - 1) /
+      std::min(kSortTile, kSegTile);
   P.o_status = take(tiles * kRadixBins * 8);
   P.o_hist = take(hist_words * 4);
   P.o_tickets = take((size_t)P.total_passes * 4);
@@ -334,6 +338,7 @@ void make_plan(Plan& P) {
                       ? (size_t)P.local_boxes * 2 * P.k * 4 : 0);
   P.o_lsets = take(P.lsets.size() * sizeof(LocalSet));
   P.o_work = take(P.work.size() * sizeof(LocalWork));
+  P.o_whole = take(sizeof(ActiveEntry));  // one segment spanning the whole array
   P.bytes = o;
 }
 
@@ -410,6 +415,14 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       KDB_CK(cudaMemcpyAsync(d_work, P.work.data(), P.work.size() * sizeof(LocalWork),
                              cudaMemcpyHostToDevice, st));
   }
+  ActiveEntry* d_whole = at<ActiveEntry>(ws, P.o_whole);
+  {
+    ActiveEntry w{};
+    w.set = 0;
+    w.base = 0;
+    w.next = -1;
+    KDB_CK(cudaMemcpyAsync(d_whole, &w, sizeof w, cudaMemcpyHostToDevice, st));
+  }
   KDB_CK(cudaMemsetAsync(status, 0, P.o_hist - P.o_status, st));
   KDB_CK(cudaMemsetAsync(hist, 0, P.o_bbox - P.o_hist, st));  // hist, tickets, err
   if (widest) {
@@ -454,6 +467,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   pa.nsets = (uint32_t)P.sets.size();
   pa.keys32 = multi ? nullptr : at<uint32_t>(ws, P.o_ckeys);
   pa.keys64 = multi ? at<uint64_t>(ws, P.o_ckeys) : nullptr;
+  pa.kstride = P.kstride;
   pa.hist = hist;
   pa.passes = P.rank_passes;
   pa.bbox = widest ? bbox : nullptr;
@@ -468,24 +482,32 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   for (int d = 0; d < k; ++d) {
     const uint32_t* hd = hist + (size_t)d * P.rank_passes * kRadixBins;
     if (!multi) {
-      const uint32_t* kin = at<uint32_t>(ws, P.o_ckeys) + (size_t)d * T;
+      // one set: the segmented pass with a single segment spanning the array
+      LevelCtx wx{};
+      wx.sets = d_sets;
+      wx.act = d_whole;
+      wx.nact = 1;
+      wx.l = 0;
+      wx.err = err;
+      const uint32_t* kin = at<uint32_t>(ws, P.o_ckeys) + (size_t)d * P.kstride;
       const uint32_t* vin = nullptr;
       uint32_t* kb[2] = {reinterpret_cast<uint32_t*>(keysA), reinterpret_cast<uint32_t*>(keysB)};
       uint32_t* vb[2] = {valsA, valsB};
       for (int p = 0; p < P.rank_passes; ++p) {
-        PassCtl c = ctl(T, 8 * p, hd + p * kRadixBins);
+        PassCtl c = ctl(T, 8 * p, nullptr);
+        const uint32_t* hp = hd + p * kRadixBins;
         if (p + 1 == P.rank_passes) {
           Prof pf(K_RADIX_RANK, (double)T * 12, 1, st);
-          KDB_CK(pass_u32_rank(kin, vin, ranks + (size_t)d * T, c, st));
+          KDB_CK(seg_pass_rank(kin, vin, wx, hp, ranks + (size_t)d * T, c, st));
         } else {
           Prof pf(K_RADIX, (double)T * 16, 1, st);
-          KDB_CK(pass_u32_pingpong(kin, vin, kb[p & 1], vb[p & 1], c, st));
+          KDB_CK(seg_pass_pingpong(kin, vin, kb[p & 1], vb[p & 1], wx, hp, c, st));
           kin = kb[p & 1];
           vin = vb[p & 1];
         }
       }
     } else {
-      const uint64_t* kin = at<uint64_t>(ws, P.o_ckeys) + (size_t)d * T;
+      const uint64_t* kin = at<uint64_t>(ws, P.o_ckeys) + (size_t)d * P.kstride;
       const uint32_t* vin = nullptr;
       uint64_t* kb[2] = {keysA, keysB};
       uint32_t* vb[2] = {valsA, valsB};

@@ -60,6 +60,14 @@ cudaError_t launch_local_finish(const LocalArgs& a, cudaStream_t st);
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;
+// Segmented passes: 256 threads x 15 items = 3840 < 2^13 - 1, the shortest
+// subtree segment of a segmented level, so a tile touches at most two
+// segments; three blocks per SM.
+constexpr int kSegThreads = 256;
+constexpr int kSegItems = 15;
+constexpr int kSegMinBlocks = 3;
+constexpr int kSegTile = kSegThreads * kSegItems;
+size_t seg_pass_smem();
 
 struct PassCtl;
 
@@ -84,6 +92,10 @@ cudaError_t seg_pass_pingpong(const uint32_t* kin, const uint32_t* vin, uint32_t
 cudaError_t seg_pass_update(const uint32_t* kin, const uint32_t* vin, const LevelCtx& x,
                             const uint32_t* seg_hist, uint32_t* perm, uint32_t* vals_next,
                             const PassCtl& c, cudaStream_t st);
+// last pass of a one-set rank sort (x describes one segment: the whole array)
+cudaError_t seg_pass_rank(const uint32_t* kin, const uint32_t* vin, const LevelCtx& x,
+                          const uint32_t* seg_hist, uint32_t* rank, const PassCtl& c,
+                          cudaStream_t st);
 
 // tree kernels (kdb_tree.cu)
 struct PrepassArgs {
@@ -94,6 +106,7 @@ struct PrepassArgs {
   uint32_t nsets;
   uint32_t* keys32;     // k * total (single set) or nullptr
   uint64_t* keys64;     // k * total (several sets) or nullptr
+  uint64_t kstride;     // elements between two dimensions' keys (>= total)
   uint32_t* hist;       // k * passes * 256, or nullptr
   int passes;
   uint32_t* bbox;       // nsets * 2k (min keys, then max keys) or nullptr

@@ -11,13 +11,14 @@
 //   2. rank each key among equal digits inside its warp with __match_any_sync
 //      (warp-level multi-split), per-warp digit counters in shared memory;
 //   3. tile-wide digit counts and offsets by a block scan;
-//   4. decoupled look-back: for every digit, publish this tile's count, add up
-//      the counts of earlier tiles until one with an inclusive prefix is
-//      found, publish the inclusive prefix.  Each wait is bounded by a time
-//      limit; on expiry the tile records ERR_TIMEOUT, publishes a prefix so
-//      that later tiles do not wait on it, and writes nothing;
-//   5. stage the tile in shared memory in digit order, then write it out with
-//      consecutive threads on consecutive positions of each digit's run.
+//   4. publish the tile's digit counts, stage the tile in shared memory in
+//      digit order, then decoupled look-back: add up the counts of earlier
+//      tiles (16 per round trip) until one with an inclusive prefix is found,
+//      publish the inclusive prefix.  Each wait is bounded by a time limit; on
+//      expiry the tile records ERR_TIMEOUT, publishes a prefix so that later
+//      tiles do not wait on it, and writes nothing;
+//   5. write the tile out with consecutive threads on consecutive positions
+//      of each digit's run.
 // The epilogue object decides what is written for each (key, value, dest).
 #pragma once
 
@@ -81,6 +82,54 @@ __device__ inline uint32_t block_excl_scan(uint32_t v, uint32_t* s_tmp, uint32_t
   *total = s_tmp[THREADS / 32 - 1];
   __syncthreads();
   return before + x - v;
+}
+
+// Look back from tile-1 for digit `tid`: adds predecessors' counts until one
+// carries an inclusive prefix.  WIN predecessor words are read per round trip,
+// so the inclusive-prefix frontier moves WIN tiles per L2 round trip instead
+// of one.  Returns false if a wait ran past c.wait_ns.
+template <int WIN>
+__device__ inline bool look_back(const PassCtl& c, uint32_t tile, int tid, uint32_t* prefix) {
+  int64_t t = (int64_t)tile - 1;
+  uint32_t acc = 0;
+  bool waiting = false;
+  uint64_t t0 = 0;
+  for (;;) {
+    uint64_t w[WIN];
+#pragma unroll
+    for (int i = 0; i < WIN; ++i)
+      w[i] = (t - i >= 0) ? ld_relaxed_u64(c.status + (uint64_t)(t - i) * kRadix + tid)
+                          : lb_pack(kFlagPre, c.wait_epoch, 0);
+    int used = 0;
+    bool done = false;
+#pragma unroll
+    for (int i = 0; i < WIN; ++i) {
+      if (done || used < i) break;
+      const uint64_t x = w[i];
+      const uint32_t ep = (uint32_t)(x >> 32) & 0x3FFFFFFFu;
+      if (ep != c.wait_epoch || (x >> 62) == 0) break;  // not published yet
+      acc += (uint32_t)x;
+      ++used;
+      if ((x >> 62) == 2 || t - i == 0) done = true;
+    }
+    if (done) {
+      *prefix = acc;
+      return true;
+    }
+    if (used > 0) {
+      t -= used;
+      waiting = false;
+      continue;
+    }
+    const uint64_t now = global_timer_ns();
+    if (!waiting) {
+      waiting = true;
+      t0 = now;
+    } else if (now - t0 > c.wait_ns) {
+      *prefix = acc;
+      return false;
+    }
+  }
 }
 
 template <typename K, int THREADS, int ITEMS>
@@ -166,49 +215,14 @@ __global__ void __launch_bounds__(THREADS)
   const uint32_t bstart =
       block_excl_scan<THREADS>(tid < kRadix ? c.hist[tid] : 0u, s_scan, &dummy);
 
-  // 4. decoupled look-back, one thread per digit
+  // 4. publish this tile's counts, stage the tile in digit order (tile-local
+  //    positions need no global prefix), then look back
   if (tid < kRadix) {
     s_toff[tid] = toff;
-    uint64_t* mine = c.status + (uint64_t)tile * kRadix + tid;
-    uint32_t prefix = 0;
-    if (tile == 0) {
-      st_relaxed_u64(mine, lb_pack(kFlagPre, c.epoch, cnt));
-    } else {
-      st_relaxed_u64(mine, lb_pack(kFlagAgg, c.epoch, cnt));
-      int64_t t = (int64_t)tile - 1;
-      bool waiting = false, expired = false;
-      uint64_t t0 = 0;
-      for (;;) {
-        const uint64_t w = ld_relaxed_u64(c.status + (uint64_t)t * kRadix + tid);
-        const uint32_t ep = (uint32_t)(w >> 32) & 0x3FFFFFFFu;
-        if (ep == c.wait_epoch && (w >> 62) != 0) {
-          prefix += (uint32_t)w;
-          if ((w >> 62) == 2 || t == 0) break;
-          --t;
-          waiting = false;
-          continue;
-        }
-        const uint64_t now = global_timer_ns();
-        if (!waiting) {
-          waiting = true;
-          t0 = now;
-        } else if (now - t0 > c.wait_ns) {
-          expired = true;
-          break;
-        }
-      }
-      if (expired) {
-        atomicOr(c.err, ERR_TIMEOUT);
-        s_abort = 1;
-      }
-      st_relaxed_u64(mine, lb_pack(kFlagPre, c.epoch, prefix + cnt));
-    }
-    s_gbase[tid] = bstart + prefix - toff;  // modulo 2^32: dest = s_gbase[d] + p
+    st_relaxed_u64(c.status + (uint64_t)tile * kRadix + tid,
+                   lb_pack(tile == 0 ? kFlagPre : kFlagAgg, c.epoch, cnt));
   }
   __syncthreads();
-  if (s_abort) return;
-
-  // 5. stage in digit order, then write out
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const uint32_t p = wbase + i * 32 + lane;
@@ -219,7 +233,22 @@ __global__ void __launch_bounds__(THREADS)
       s_vals[pos] = val[i];
     }
   }
+  if (tid < kRadix) {
+    uint32_t prefix = 0;
+    if (tile > 0) {
+      if (!look_back<16>(c, tile, tid, &prefix)) {
+        atomicOr(c.err, ERR_TIMEOUT);
+        s_abort = 1;
+      }
+      st_relaxed_u64(c.status + (uint64_t)tile * kRadix + tid,
+                     lb_pack(kFlagPre, c.epoch, prefix + cnt));
+    }
+    s_gbase[tid] = bstart + prefix - toff;  // modulo 2^32: dest = s_gbase[d] + p
+  }
   __syncthreads();
+  if (s_abort) return;
+
+  // 5. write out: consecutive threads on consecutive slots of each digit's run
   for (uint32_t p = tid; p < tn; p += THREADS) {
     const K k = s_keys[p];
     const uint32_t d = digit_of(k, c.shift);

@@ -77,22 +77,56 @@ __device__ inline void segment_at(const LevelCtx& x, uint32_t j, uint32_t* ai, u
   *end = e.base + y.seg_start(s + 1);
 }
 
-template <int THREADS, int ITEMS, class Epi>
-__global__ void __launch_bounds__(THREADS)
+// Exclusive block scan of one 64-bit value per thread (any multiple of 32
+// threads up to 1024).
+template <int THREADS>
+__device__ inline uint64_t block_excl_scan64(uint64_t v, uint64_t* s_tmp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_tmp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t w = lane < THREADS / 32 ? s_tmp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < THREADS / 32) s_tmp[lane] = w;
+  }
+  __syncthreads();
+  const uint64_t r = (warp ? s_tmp[warp - 1] : 0) + x - v;
+  __syncthreads();
+  return r;
+}
+
+// Bound on waiting for the tile's bulk copy; after it the block records a
+// timeout, waits the same again for the copy to land, and leaves.
+constexpr uint64_t kCopyWaitNs = 2000000000ull;
+
+template <int THREADS, int ITEMS, int MINB, class Epi>
+__global__ void __launch_bounds__(THREADS, MINB)
     seg_onesweep_pass(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                       PassCtl c, LevelCtx x, const uint32_t* __restrict__ seg_hist, Epi epi) {
-  static_assert(THREADS == kRadix, "one thread per digit");
+  static_assert(THREADS >= kRadix && THREADS % 32 == 0, "a thread per digit");
+  static_assert((THREADS * ITEMS) % 4 == 0, "tiles start on 16-byte boundaries");
   constexpr int WARPS = THREADS / 32;
   constexpr int TILE = THREADS * ITEMS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint32_t* s_keys = reinterpret_cast<uint32_t*>(smem_raw);
-  uint32_t* s_vals = s_keys + TILE;
-  __shared__ uint32_t s_whist[WARPS][2 * kRadix];
-  __shared__ uint32_t s_gbase[2 * kRadix];
-  __shared__ uint32_t s_toff[2 * kRadix];  // tile offset of each bin (A bins, then B bins)
-  __shared__ uint32_t s_toffB0;  // first staged position of segment B
-  __shared__ uint32_t s_scan[WARPS];
-  __shared__ uint32_t s_tile, s_abort;
+  constexpr int BINS = 2 * kRadix;  // (segment A or B) x digit
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint32_t* s_keys = reinterpret_cast<uint32_t*>(smem_raw);          // tile in, then out
+  uint32_t* s_vals = s_keys + TILE;                                   // tile in, then out
+  uint16_t* s_whist = reinterpret_cast<uint16_t*>(s_vals + TILE);     // [BINS][WARPS]
+  __shared__ uint32_t s_gbase[BINS];
+  __shared__ uint32_t s_toff[BINS];
+  __shared__ uint64_t s_scan64[WARPS];
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ uint32_t s_tile, s_abort, s_totA;
   __shared__ TileSegs s_ts;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -103,12 +137,21 @@ __global__ void __launch_bounds__(THREADS)
       s_tile = tile;
       const uint32_t tb = tile * (uint32_t)TILE;
       const uint32_t tn = c.n - tb < (uint32_t)TILE ? c.n - tb : (uint32_t)TILE;
-      uint32_t a, s, st, en;
-      segment_at(x, tb, &a, &s, &st, &en);
+      // 1. the tile's keys and values to shared memory by bulk copy (whole
+      //    16-byte groups; the last 0-3 items are loaded below)
+      const uint32_t nal = tn & ~3u;
+      mbar_init(&s_bar, 1);
+      mbar_expect_tx(&s_bar, nal * 4u * (vals_in ? 2u : 1u));
+      if (nal) {
+        bulk_g2s(s_keys, keys_in + tb, nal * 4u, &s_bar);
+        if (vals_in) bulk_g2s(s_vals, vals_in + tb, nal * 4u, &s_bar);
+      }
+      uint32_t a, sr, st, en;
+      segment_at(x, tb, &a, &sr, &st, &en);
       s_ts.ai[0] = a;
-      s_ts.srel[0] = s;
+      s_ts.srel[0] = sr;
       s_ts.start[0] = st;
-      s_ts.gid[0] = (a << x.l) | s;
+      s_ts.gid[0] = (a << x.l) | sr;
       s_ts.bpos = tn;
       if (en < tb + tn) {  // the tile reaches into the next segment
         uint32_t a2, s2, st2, en2;
@@ -121,7 +164,7 @@ __global__ void __launch_bounds__(THREADS)
         if (en2 < tb + tn) s_abort = 2;  // a segment shorter than a tile: not allowed here
       } else {
         s_ts.ai[1] = a;
-        s_ts.srel[1] = s;
+        s_ts.srel[1] = sr;
         s_ts.start[1] = st;
         s_ts.gid[1] = s_ts.gid[0];
       }
@@ -131,123 +174,138 @@ __global__ void __launch_bounds__(THREADS)
       }
     }
   }
-  for (int i = tid; i < WARPS * 2 * kRadix; i += THREADS) (&s_whist[0][0])[i] = 0;
+  for (int i = tid; i < BINS * WARPS / 2; i += THREADS) reinterpret_cast<uint32_t*>(s_whist)[i] = 0;
   __syncthreads();
   if (s_abort == 1) return;
-  if (s_abort == 2) {
-    // cannot happen with the level plan; record it and publish so no tile waits
-    if (tid == 0) atomicOr(c.err, ERR_INTERNAL);
-  }
+  if (s_abort == 2 && tid == 0) atomicOr(c.err, ERR_INTERNAL);
   const uint32_t tile = s_tile;
   const uint32_t tb = tile * (uint32_t)TILE;
   const uint32_t tn = c.n - tb < (uint32_t)TILE ? c.n - tb : (uint32_t)TILE;
+  const uint32_t nal = tn & ~3u;
+  if (tid < (int)(tn - nal)) {
+    s_keys[nal + tid] = keys_in[tb + nal + tid];
+    if (vals_in) s_vals[nal + tid] = vals_in[tb + nal + tid];
+  }
+  if (!vals_in)
+    for (uint32_t p = tid; p < tn; p += THREADS) s_vals[p] = tb + p;
+  {
+    bool waiting = false, late = false;
+    uint64_t t0 = 0;
+    while (!mbar_try_wait(&s_bar, 0)) {
+      const uint64_t now = global_timer_ns();
+      if (!waiting) {
+        waiting = true;
+        t0 = now;
+      } else if (now - t0 > (late ? 2 : 1) * kCopyWaitNs) {
+        if (late) break;  // give up; the error is recorded below
+        late = true;
+        atomicOr(c.err, ERR_TIMEOUT);
+      }
+    }
+    if (late) s_abort = 1;
+  }
+  __syncthreads();
+  if (s_abort == 1) return;
   const uint32_t bpos = s_ts.bpos;
   const bool hasB = bpos < tn;
   const bool a_cont = s_ts.start[0] < tb;  // segment A began in an earlier tile
   const uint32_t wbase = (uint32_t)warp * 32 * ITEMS;
 
-  uint32_t key[ITEMS], val[ITEMS], rnk[ITEMS];
-#pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const uint32_t p = wbase + i * 32 + lane;
-    if (p < tn) {
-      key[i] = keys_in[tb + p];
-      val[i] = vals_in[tb + p];
-    }
-  }
+  // 2. rank within the warp among equal (segment, digit), in input order
+  uint32_t key[ITEMS];
   const uint32_t lt = (1u << lane) - 1u;
+  uint32_t rnk[ITEMS];
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const uint32_t p = wbase + i * 32 + lane;
     const bool ok = p < tn;
+    key[i] = ok ? s_keys[p] : 0u;
     const uint32_t bin =
-        ok ? (((p >= bpos) ? (uint32_t)kRadix : 0u) | digit_of(key[i], c.shift)) : 2u * kRadix;
+        ok ? (((p >= bpos) ? (uint32_t)kRadix : 0u) | digit_of(key[i], c.shift)) : (uint32_t)BINS;
     const uint32_t peers = __match_any_sync(0xffffffffu, bin);
     uint32_t before = 0;
-    if (ok) before = s_whist[warp][bin];
+    if (ok) before = s_whist[bin * WARPS + warp];
     __syncwarp();
-    if (ok) {
-      rnk[i] = before + __popc(peers & lt);
-      if ((peers & lt) == 0) s_whist[warp][bin] = before + __popc(peers);
-    }
+    rnk[i] = before + __popc(peers & lt);
+    if (ok && (peers & lt) == 0) s_whist[bin * WARPS + warp] = (uint16_t)(before + __popc(peers));
     __syncwarp();
   }
   __syncthreads();
 
-  // per bin (thread tid owns digit tid of A and of B)
+  // 3. tile counts per bin; publish them for the tile's last segment at once
   uint32_t cA = 0, cB = 0;
+  if (tid < kRadix) {
 #pragma unroll
-  for (int w = 0; w < WARPS; ++w) {
-    const uint32_t ta = s_whist[w][tid], tb2 = s_whist[w][kRadix + tid];
-    s_whist[w][tid] = cA;
-    s_whist[w][kRadix + tid] = cB;
-    cA += ta;
-    cB += tb2;
-  }
-  uint32_t totA, totB, d0;
-  const uint32_t toffA = block_excl_scan<THREADS>(cA, s_scan, &totA);
-  const uint32_t toffB = block_excl_scan<THREADS>(cB, s_scan, &totB) + totA;
-  const uint32_t hA = seg_hist[(uint64_t)s_ts.gid[0] * kRadix + tid];
-  const uint32_t hB = hasB ? seg_hist[(uint64_t)s_ts.gid[1] * kRadix + tid] : 0u;
-  const uint32_t bA = block_excl_scan<THREADS>(hA, s_scan, &d0);
-  const uint32_t bB = block_excl_scan<THREADS>(hB, s_scan, &d0);
-
-  // look-back for segment A's digit prefixes; publish for the tile's last segment
-  uint64_t* mine = c.status + (uint64_t)tile * kRadix + tid;
-  uint32_t prefA = 0;
-  if (hasB || !a_cont) st_relaxed_u64(mine, lb_pack(kFlagPre, c.epoch, hasB ? cB : cA));
-  else st_relaxed_u64(mine, lb_pack(kFlagAgg, c.epoch, cA));
-  if (a_cont && s_abort == 0) {
-    int64_t t = (int64_t)tile - 1;
-    bool waiting = false, expired = false;
-    uint64_t t0 = 0;
-    for (;;) {
-      const uint64_t w = ld_relaxed_u64(c.status + (uint64_t)t * kRadix + tid);
-      const uint32_t ep = (uint32_t)(w >> 32) & 0x3FFFFFFFu;
-      if (ep == c.wait_epoch && (w >> 62) != 0) {
-        prefA += (uint32_t)w;
-        if ((w >> 62) == 2 || t == 0) break;
-        --t;
-        waiting = false;
-        continue;
-      }
-      const uint64_t now = global_timer_ns();
-      if (!waiting) {
-        waiting = true;
-        t0 = now;
-      } else if (now - t0 > c.wait_ns) {
-        expired = true;
-        break;
-      }
+    for (int w = 0; w < WARPS; ++w) {
+      const uint32_t ta = s_whist[tid * WARPS + w], tb2 = s_whist[(kRadix + tid) * WARPS + w];
+      s_whist[tid * WARPS + w] = (uint16_t)cA;
+      s_whist[(kRadix + tid) * WARPS + w] = (uint16_t)cB;
+      cA += ta;
+      cB += tb2;
     }
-    if (expired) {
-      atomicOr(c.err, ERR_TIMEOUT);
-      s_abort = 1;
-    }
-    if (!hasB) st_relaxed_u64(mine, lb_pack(kFlagPre, c.epoch, prefA + cA));
+    uint64_t* mine = c.status + (uint64_t)tile * kRadix + tid;
+    if (hasB || !a_cont) st_relaxed_u64(mine, lb_pack(kFlagPre, c.epoch, hasB ? cB : cA));
+    else st_relaxed_u64(mine, lb_pack(kFlagAgg, c.epoch, cA));
   }
-  s_toff[tid] = toffA;
-  s_toff[kRadix + tid] = toffB;
-  s_gbase[tid] = s_ts.start[0] + bA + prefA - toffA;
-  s_gbase[kRadix + tid] = s_ts.start[1] + bB - toffB;
-  if (tid == 0) s_toffB0 = totA;
+  // 4. tile offsets of the bins (A bins, then B bins) and the segments' digit
+  //    starts, two 64-bit scans
+  uint32_t hA = 0, hB = 0;
+  if (tid < kRadix) {
+    hA = seg_hist[(uint64_t)s_ts.gid[0] * kRadix + tid];
+    hB = hasB ? seg_hist[(uint64_t)s_ts.gid[1] * kRadix + tid] : 0u;
+  }
+  const uint64_t tsc = block_excl_scan64<THREADS>((uint64_t)cA | ((uint64_t)cB << 32), s_scan64);
+  const uint64_t hsc = block_excl_scan64<THREADS>((uint64_t)hA | ((uint64_t)hB << 32), s_scan64);
+  if (tid == kRadix - 1) s_totA = (uint32_t)tsc + cA;
   __syncthreads();
-  if (s_abort) return;
-
+  uint32_t toffA = 0, toffB = 0;
+  if (tid < kRadix) {
+    toffA = (uint32_t)tsc;
+    toffB = (uint32_t)(tsc >> 32) + s_totA;
+    s_toff[tid] = toffA;
+    s_toff[kRadix + tid] = toffB;
+  }
+  uint32_t val[ITEMS];
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t p = wbase + i * 32 + lane;
+    val[i] = p < tn ? s_vals[p] : 0u;
+  }
+  __syncthreads();  // the input tile is consumed: its buffers take the output
+  // 5. stage keys and values in bin order (tile-local positions need no
+  //    global prefix)
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const uint32_t p = wbase + i * 32 + lane;
     if (p < tn) {
       const uint32_t bin = ((p >= bpos) ? (uint32_t)kRadix : 0u) | digit_of(key[i], c.shift);
-      const uint32_t pos = s_toff[bin] + s_whist[warp][bin] + rnk[i];
+      const uint32_t pos = s_toff[bin] + s_whist[bin * WARPS + warp] + rnk[i];
       s_keys[pos] = key[i];
       s_vals[pos] = val[i];
     }
   }
+  // 6. look-back for segment A's digit prefixes
+  if (tid < kRadix) {
+    uint32_t prefA = 0;
+    if (a_cont && s_abort == 0) {
+      if (!look_back<16>(c, tile, tid, &prefA)) {
+        atomicOr(c.err, ERR_TIMEOUT);
+        s_abort = 1;
+      }
+      if (!hasB) st_relaxed_u64(c.status + (uint64_t)tile * kRadix + tid,
+                                lb_pack(kFlagPre, c.epoch, prefA + cA));
+    }
+    s_gbase[tid] = s_ts.start[0] + (uint32_t)hsc + prefA - toffA;
+    s_gbase[kRadix + tid] = s_ts.start[1] + (uint32_t)(hsc >> 32) - toffB;
+  }
   __syncthreads();
+  if (s_abort) return;
+
+  // 7. write out: consecutive threads on consecutive slots of each bin's run
+  const uint32_t totA = s_totA;
   for (uint32_t p = tid; p < tn; p += THREADS) {
     const uint32_t k = s_keys[p];
-    const uint32_t seg = p >= s_toffB0 ? 1u : 0u;
+    const uint32_t seg = p >= totA ? 1u : 0u;
     const uint32_t bin = (seg ? (uint32_t)kRadix : 0u) | digit_of(k, c.shift);
     const uint32_t dest = s_gbase[bin] + p;
     if (dest >= c.n) {
@@ -276,6 +334,16 @@ struct SegEpiPingPong {
 // into the next level's compacted array (one pinned item removed per earlier
 // subtree, plus this subtree's own pivot for right children).  On a set's last
 // sorted level the children are lowest-level nodes and go to their slots.
+// Last pass of a per-dimension rank sort over one set: the sorted position of
+// an item is its rank in that dimension.
+struct SegEpiRank {
+  static constexpr bool kNeedsUpdateInfo = false;
+  uint32_t* rank;
+  __device__ void operator()(uint32_t, uint32_t v, uint32_t dest, uint32_t, const TileSegs&) const {
+    rank[v] = dest;
+  }
+};
+
 struct SegEpiUpdate {
   static constexpr bool kNeedsUpdateInfo = true;
   uint32_t* perm;

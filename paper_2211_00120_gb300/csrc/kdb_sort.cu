@@ -93,12 +93,12 @@ static cudaError_t run_seg_pass(const uint32_t* kin, const uint32_t* vin, const 
                                 const uint32_t* seg_hist, const Epi& epi, const PassCtl& c,
                                 cudaStream_t st) {
   if (c.n == 0) return cudaSuccess;
-  auto kern = seg_onesweep_pass<kSortThreads, kSortItems, Epi>;
-  const size_t smem = (size_t)kSortTile * 8;
+  auto kern = seg_onesweep_pass<kSegThreads, kSegItems, kSegMinBlocks, Epi>;
+  const size_t smem = seg_pass_smem();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const uint32_t tiles = (c.n + kSortTile - 1) / kSortTile;
-  kern<<<tiles, kSortThreads, smem, st>>>(kin, vin, c, x, seg_hist, epi);
+  const uint32_t tiles = (c.n + kSegTile - 1) / kSegTile;
+  kern<<<tiles, kSegThreads, smem, st>>>(kin, vin, c, x, seg_hist, epi);
   return cudaGetLastError();
 }
 
@@ -106,6 +106,16 @@ cudaError_t seg_pass_pingpong(const uint32_t* kin, const uint32_t* vin, uint32_t
                               uint32_t* vout, const LevelCtx& x, const uint32_t* seg_hist,
                               const PassCtl& c, cudaStream_t st) {
   return run_seg_pass(kin, vin, x, seg_hist, SegEpiPingPong{kout, vout}, c, st);
+}
+
+size_t seg_pass_smem() {
+  return (size_t)kSegTile * 8 + (size_t)2 * kRadix * (kSegThreads / 32) * 2;
+}
+
+cudaError_t seg_pass_rank(const uint32_t* kin, const uint32_t* vin, const LevelCtx& x,
+                          const uint32_t* seg_hist, uint32_t* rank, const PassCtl& c,
+                          cudaStream_t st) {
+  return run_seg_pass(kin, vin, x, seg_hist, SegEpiRank{rank}, c, st);
 }
 
 cudaError_t seg_pass_update(const uint32_t* kin, const uint32_t* vin, const LevelCtx& x,

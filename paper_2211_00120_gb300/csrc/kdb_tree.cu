@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(kThreads) prepass_kernel(PrepassArgs a) {
         key = float_key(bits);
         lo[d] = min(lo[d], key);
         hi[d] = max(hi[d], key);
-        if (a.keys32) a.keys32[(uint64_t)d * a.total + i] = key;
-        if (a.keys64) a.keys64[(uint64_t)d * a.total + i] = ((uint64_t)cur << 32) | key;
+        if (a.keys32) a.keys32[(uint64_t)d * a.kstride + i] = key;
+        if (a.keys64) a.keys64[(uint64_t)d * a.kstride + i] = ((uint64_t)cur << 32) | key;
       }
       if (a.hist) {
         const uint64_t k64 = ((uint64_t)cur << 32) | key;
