@@ -153,7 +153,7 @@ KDB_API kdb_status kdb_build_host(void* h_points, int64_t n, int k, int stride_b
  * serialised by the caller.  Synchronises `stream`.
  */
 #define KDB_NOALLOC_MAX_POINTS 262144
-#define KDB_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define KDB_NOALLOC_SCRATCH_BYTES (64u << 20)
 KDB_API kdb_status kdb_build_noalloc(void* d_points, int64_t n, int k, int stride_bytes,
                                      kdb_split_mode mode, kdb_stream_t stream);
 

@@ -45,11 +45,15 @@ enum Kind {
   K_PLACEMENT,
   K_VALIDATE,
   K_LOCAL,
+  K_PARTITION,
+  K_PIVOT,
+  K_LISTS,
   K_COUNT
 };
 const char* const kKindName[K_COUNT] = {"prepass",      "radix_pass",  "radix_pass_rank",
                                         "radix_pass_update", "level_keys", "widest_dims",
-                                        "placement",    "validate",   "local_finish"};
+                                        "placement",    "validate",   "local_finish",
+                                        "partition_pass", "pivots",     "build_lists"};
 struct ProfRec {
   int kind;
   double bytes;
@@ -190,6 +194,10 @@ struct Plan {
   std::vector<LocalWork> work;
   uint32_t local_boxes = 0;
   size_t o_vloc, o_lbox, o_lsets, o_work, o_whole;
+  // presorted lists (k <= 3): one list of 16-byte entries per dimension
+  bool use_lists = false;
+  size_t o_rows, o_sorted, o_lists, o_ents, o_piv;
+  uint32_t max_nseg = 0;
   uint64_t kstride = 0;  // elements between two dimensions' coordinate keys
 };
 
@@ -213,6 +221,7 @@ void make_plan(Plan& P) {
   P.set_bits = ns > 1 ? bits_for(ns) : 0;
   P.rank_passes = ceil_div_i(32 + P.set_bits, 8);
   P.use_local = P.k <= kLocalMaxK;
+  P.use_lists = P.use_local && P.k <= 3;
   int levels = 0;
   for (const SetInfo& si : P.sets) levels = std::max(levels, global_levels(P, si.n));
   if (P.use_local) {
@@ -263,7 +272,10 @@ void make_plan(Plan& P) {
     const uint32_t na = (uint32_t)P.act[l].size();
     P.seg[l] = all_long && na > 0 && P.rb <= 32;
     P.hist_off[l] = hist_words;
-    if (P.seg[l]) {
+    P.max_nseg = std::max(P.max_nseg, na << l);
+    if (P.use_lists) {
+      P.passes[l] = P.k;  // one partition pass per list
+    } else if (P.seg[l]) {
       P.passes[l] = std::max(1, ceil_div_i(P.rb, 8));
       P.nseg[l] = na << l;
       uint32_t chunk = 0;
@@ -304,13 +316,15 @@ void make_plan(Plan& P) {
     o = align256(o + bytes);
     return at;
   };
-  P.o_keysA = take(T * 8);
-  P.o_keysB = take(T * 8);
+  // 64-bit keys: several sets' rank sorts, or packed level keys; else 32-bit
+  const size_t kb = (P.sets.size() > 1 || !P.use_lists) ? 8 : 4;
+  P.o_keysA = take(T * kb);
+  P.o_keysB = take(T * kb);
   P.o_valsA = take(T * 4);
   P.o_valsB = take(T * 4);
   P.kstride = (T + 63) & ~uint64_t(63);  // per-dimension key arrays start 256-byte aligned
   P.o_ckeys = take(P.kstride * P.k * ksz);
-  P.o_ranks = take(T * P.k * 4);
+  P.o_ranks = take(P.use_lists ? 0 : T * P.k * 4);
   P.o_perm = take(T * 4);
   P.o_dims = take(T);
   const size_t box_bytes = P.mode == KDB_SPLIT_WIDEST_EXTENT ? (size_t)P.max_boxes * 2 * P.k * 4 : 0;
@@ -333,12 +347,18 @@ void make_plan(Plan& P) {
     nact += P.act[l].size();
   }
   P.o_act = take(std::max<size_t>(nact, 1) * sizeof(ActiveEntry));
-  P.o_vloc = take(P.use_local ? T * 4 : 0);
+  P.o_vloc = take(P.use_local && !P.use_lists ? T * 4 : 0);
   P.o_lbox = take(P.use_local && P.mode == KDB_SPLIT_WIDEST_EXTENT
                       ? (size_t)P.local_boxes * 2 * P.k * 4 : 0);
   P.o_lsets = take(P.lsets.size() * sizeof(LocalSet));
   P.o_work = take(P.work.size() * sizeof(LocalWork));
   P.o_whole = take(sizeof(ActiveEntry));  // one segment spanning the whole array
+  const bool L = P.use_lists, G = L && levels > 0;  // G: there are global levels
+  P.o_rows = take(L ? T * 16 : 0);
+  P.o_sorted = take(G ? P.kstride * P.k * 4 : 0);
+  P.o_lists = take(G ? T * 16 * 2 * P.k : 0);
+  P.o_ents = take(G ? T * 16 : 0);
+  P.o_piv = take(L ? (size_t)std::max<uint32_t>(P.max_nseg, 1) * 4 : 0);
   P.bytes = o;
 }
 
@@ -479,6 +499,19 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   uint32_t* hcur = hist + (size_t)k * P.rank_passes * kRadixBins;
 
   // ---- per-dimension ranks
+  uint32_t* rows = at<uint32_t>(ws, P.o_rows);
+  uint32_t* sorted = at<uint32_t>(ws, P.o_sorted);
+  auto rank_out = [&](int d) {
+    RankOut o{};
+    o.d = d;
+    if (P.use_lists) {
+      o.rows = rows;
+      if (!P.act.empty()) o.sorted = sorted + (size_t)d * P.kstride;
+    } else {
+      o.rank = ranks + (size_t)d * T;
+    }
+    return o;
+  };
   for (int d = 0; d < k; ++d) {
     const uint32_t* hd = hist + (size_t)d * P.rank_passes * kRadixBins;
     if (!multi) {
@@ -497,8 +530,8 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
         PassCtl c = ctl(T, 8 * p, nullptr);
         const uint32_t* hp = hd + p * kRadixBins;
         if (p + 1 == P.rank_passes) {
-          Prof pf(K_RADIX_RANK, (double)T * 12, 1, st);
-          KDB_CK(seg_pass_rank(kin, vin, wx, hp, ranks + (size_t)d * T, c, st));
+          Prof pf(K_RADIX_RANK, (double)T * (P.use_lists ? 16 : 12), 1, st);
+          KDB_CK(seg_pass_rank(kin, vin, wx, hp, rank_out(d), c, st));
         } else {
           Prof pf(K_RADIX, (double)T * 16, 1, st);
           KDB_CK(seg_pass_pingpong(kin, vin, kb[p & 1], vb[p & 1], wx, hp, c, st));
@@ -514,8 +547,8 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       for (int p = 0; p < P.rank_passes; ++p) {
         PassCtl c = ctl(T, 8 * p, hd + p * kRadixBins);
         if (p + 1 == P.rank_passes) {
-          Prof pf(K_RADIX_RANK, (double)T * 16, 1, st);
-          KDB_CK(pass_u64_rank(kin, vin, ranks + (size_t)d * T, d_sets, 32, c, st));
+          Prof pf(K_RADIX_RANK, (double)T * (P.use_lists ? 20 : 16), 1, st);
+          KDB_CK(pass_u64_rank(kin, vin, rank_out(d), d_sets, 32, c, st));
         } else {
           Prof pf(K_RADIX, (double)T * 24, 1, st);
           KDB_CK(pass_u64_pingpong(kin, vin, kb[p & 1], vb[p & 1], c, st));
@@ -545,6 +578,32 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
                               boxA, dims, st));
   }
   const uint32_t* vals_cur = nullptr;  // level 0: original order
+  uint4* lcur[3] = {nullptr, nullptr, nullptr};
+  uint4* lnext[3] = {nullptr, nullptr, nullptr};
+  uint4* ents_local = at<uint4>(ws, P.o_ents);
+  uint32_t* piv = at<uint32_t>(ws, P.o_piv);
+  if (P.use_lists) {
+    for (int d = 0; d < k; ++d) {
+      lcur[d] = at<uint4>(ws, P.o_lists) + (size_t)(2 * d) * T;
+      lnext[d] = at<uint4>(ws, P.o_lists) + (size_t)(2 * d + 1) * T;
+    }
+    if (levels > 0) {
+      ListBuildArgs lb{};
+      lb.x.sets = d_sets;
+      lb.x.act = d_act + P.act_off[0];
+      lb.x.nact = (uint32_t)P.act[0].size();
+      lb.x.err = err;
+      lb.items = P.items[0];
+      lb.rows = rows;
+      lb.sorted = sorted;
+      lb.kstride = P.kstride;
+      lb.total = T;
+      lb.k = k;
+      for (int d = 0; d < k; ++d) lb.lists[d] = lcur[d];
+      Prof pf(K_LISTS, (double)P.items[0] * k * (4.0 + 16.0 + 16.0), 1, st);
+      KDB_CK(launch_build_lists(lb, st));
+    }
+  }
   for (int l = 0; l < levels; ++l) {
     LevelCtx x{};
     x.sets = d_sets;
@@ -560,7 +619,52 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     // the buffer not holding vals_cur receives the level's first outputs
     uint32_t* vfree = vals_cur == valsA ? valsB : valsA;
     hcur = hist + P.hist_off[l];
-    if (P.seg[l]) {
+    if (P.use_lists) {
+      PivotArgs pv{};
+      pv.x = x;
+      for (int d = 0; d < k; ++d) pv.lists[d] = lcur[d];
+      pv.items = n;
+      pv.piv = piv;
+      pv.perm = perm;
+      pv.dims = dims;
+      pv.k = k;
+      pv.mode = P.mode;
+      {
+        Prof pf(K_PIVOT, (double)(x.nact << l) * 20, 1, st);
+        KDB_CK(launch_pivots(pv, st));
+      }
+      bool all_leave = true;  // every set goes to the local finish after this level
+      for (const ActiveEntry& e : P.act[l]) all_leave = all_leave && e.next < 0;
+      const uint32_t next_items = l + 1 < levels ? P.items[l + 1] : 0;
+      for (int d = 0; d < k; ++d) {
+        if (all_leave && P.mode == 0 && d != l % k) {
+          ++g;  // keep the ticket / epoch numbering of the plan
+          continue;
+        }
+        PassCtl c = ctl(n, 0, nullptr);
+        PartArgs pa2{};
+        pa2.x = x;
+        pa2.in = lcur[d];
+        pa2.out_next = lnext[d];
+        pa2.out_local = ents_local;
+        pa2.piv = piv;
+        pa2.dims = dims;
+        pa2.k = k;
+        pa2.mode = P.mode;
+        pa2.dlist = d;
+        pa2.n = n;
+        pa2.next_items = next_items;
+        pa2.total = T;
+        pa2.status = c.status;
+        pa2.ticket = c.ticket;
+        pa2.epoch = c.epoch;
+        pa2.wait_epoch = c.wait_epoch;
+        pa2.wait_ns = c.wait_ns;
+        Prof pf(K_PARTITION, (double)n * 32, 1, st);
+        KDB_CK(launch_partition(pa2, st));
+      }
+      for (int d = 0; d < k; ++d) std::swap(lcur[d], lnext[d]);
+    } else if (P.seg[l]) {
       SegKeyArgs sa{};
       sa.x = x;
       sa.chunks = P.chunks[l];
@@ -670,7 +774,9 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     la.nwork = (uint32_t)P.work.size();
     la.lsets = d_lsets;
     la.vals_local = vals_local;
-    la.ranks = ranks;
+    la.ents_local = P.use_lists ? ents_local : nullptr;
+    la.rows = P.use_lists ? reinterpret_cast<const uint4*>(rows) : nullptr;
+    la.ranks = P.use_lists ? nullptr : ranks;
     la.total = T;
     la.k = k;
     la.mode = P.mode;

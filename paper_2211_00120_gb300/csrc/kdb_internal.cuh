@@ -189,6 +189,22 @@ struct SetInfo {
   uint32_t n;    // records in the set
 };
 
+// Outputs of the last pass of a per-dimension rank sort.
+struct RankOut {
+  uint32_t* rank;    // rank[item] in this dimension (one array per dimension), or nullptr
+  uint32_t* rows;    // rank rows rows[4*item + d], rows[4*item + 3] = item (k <= 3), or nullptr
+  uint32_t* sorted;  // sorted[position] = item, or nullptr
+  int d;             // this dimension
+  __device__ void put(uint32_t item, uint32_t r, uint32_t pos) const {
+    if (rank) rank[item] = r;
+    if (rows) {
+      rows[4u * item + d] = r;
+      if (d == 0) rows[4u * item + 3] = item;
+    }
+    if (sorted) sorted[pos] = item;
+  }
+};
+
 struct ActiveEntry {
   uint32_t set;   // index into the set table
   uint32_t base;  // start of this set's items in the level's concatenated array

@@ -22,6 +22,49 @@ struct LevelCtx {
   uint32_t* vals_local;  // per set at its first record: the local level's items
 };
 
+// Presorted-list levels (kdb_part.cu), k <= 3: one 16-byte entry per point
+// (ranks in dimensions 0..2, original index), one list per dimension.
+constexpr int kPartThreads = 256;
+constexpr int kPartItems = 15;
+constexpr int kPartTile = kPartThreads * kPartItems;  // < 2^13 - 1: <= two segments a tile
+struct ListBuildArgs {
+  LevelCtx x;               // level 0
+  uint32_t items;           // items of level 0
+  const uint32_t* rows;     // rank rows, 4 words per point
+  const uint32_t* sorted;   // per dimension: points in sorted order (stride kstride)
+  uint64_t kstride;
+  uint32_t total;
+  int k;
+  uint4* lists[3];
+};
+struct PivotArgs {
+  LevelCtx x;
+  const uint4* lists[3];    // this level's lists
+  uint32_t items;
+  uint32_t* piv;            // out: pivot rank per segment (ai << l | s_rel)
+  uint32_t* perm;           // out: node -> original index
+  const uint8_t* dims;      // widest: split dimension per node
+  int k, mode;
+};
+struct PartArgs {
+  LevelCtx x;
+  const uint4* in;          // this level's list sorted by dimension dlist
+  uint4* out_next;          // next level's list
+  uint4* out_local;         // entries for the local finish (sets leaving)
+  const uint32_t* piv;
+  const uint8_t* dims;
+  int k, mode, dlist;
+  uint32_t n, next_items, total;
+  uint64_t* status;         // one look-back word per tile
+  uint32_t* ticket;
+  uint32_t epoch, wait_epoch;
+  uint64_t wait_ns;
+};
+size_t partition_smem();
+cudaError_t launch_build_lists(const ListBuildArgs& a, cudaStream_t st);
+cudaError_t launch_pivots(const PivotArgs& a, cudaStream_t st);
+cudaError_t launch_partition(const PartArgs& a, cudaStream_t st);
+
 // Local finish of small subtrees (kdb_local.cu).
 constexpr int kLocalThreads = 1024;
 constexpr int kLocalLog = 13;                     // subtrees of <= 2^13 - 1 points
@@ -41,7 +84,9 @@ struct LocalArgs {
   const LocalWork* work;
   uint32_t nwork;
   const LocalSet* lsets;
-  const uint32_t* vals_local;
+  const uint32_t* vals_local;   // original indices (rank arrays gathered), or
+  const uint4* ents_local;      // entries (k <= 3): ranks and original index
+  const uint4* rows;            // entries in input order (sets local from level 0)
   const uint32_t* ranks;
   uint32_t total;
   int k, mode;
@@ -72,13 +117,9 @@ size_t seg_pass_smem();
 struct PassCtl;
 
 // onesweep passes (kdb_sort.cu)
-cudaError_t pass_u32_pingpong(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
-                              uint32_t* vout, const PassCtl& c, cudaStream_t st);
-cudaError_t pass_u32_rank(const uint32_t* kin, const uint32_t* vin, uint32_t* rank,
-                          const PassCtl& c, cudaStream_t st);
 cudaError_t pass_u64_pingpong(const uint64_t* kin, const uint32_t* vin, uint64_t* kout,
                               uint32_t* vout, const PassCtl& c, cudaStream_t st);
-cudaError_t pass_u64_rank(const uint64_t* kin, const uint32_t* vin, uint32_t* rank,
+cudaError_t pass_u64_rank(const uint64_t* kin, const uint32_t* vin, const RankOut& out,
                           const SetInfo* sets, int set_shift, const PassCtl& c, cudaStream_t st);
 cudaError_t pass_u64_update(const uint64_t* kin, const uint32_t* vin, const LevelCtx& x,
                             uint32_t* perm, uint32_t* vals_next, const PassCtl& c,
@@ -94,7 +135,7 @@ cudaError_t seg_pass_update(const uint32_t* kin, const uint32_t* vin, const Leve
                             const PassCtl& c, cudaStream_t st);
 // last pass of a one-set rank sort (x describes one segment: the whole array)
 cudaError_t seg_pass_rank(const uint32_t* kin, const uint32_t* vin, const LevelCtx& x,
-                          const uint32_t* seg_hist, uint32_t* rank, const PassCtl& c,
+                          const uint32_t* seg_hist, const RankOut& out, const PassCtl& c,
                           cudaStream_t st);
 
 // tree kernels (kdb_tree.cu)

@@ -190,8 +190,11 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     return;
   }
   if (threadIdx.x == 0) s_bad = 0;
+  // entries (k <= 3) carry every rank; otherwise ranks are gathered
+  const uint4* ents = nullptr;
+  if (a.ents_local) ents = l0 > 0 ? a.ents_local + ls.off + start0 : a.rows + ls.off;
   for (uint32_t i = threadIdx.x; i < m; i += T)
-    s_orig[i] = l0 > 0 ? a.vals_local[ls.off + start0 + i] : ls.off + i;
+    s_orig[i] = ents ? ents[i].w : (l0 > 0 ? a.vals_local[ls.off + start0 + i] : ls.off + i);
   if (threadIdx.x <= (unsigned)k) s_list_of[threadIdx.x] = threadIdx.x;
   __syncthreads();
 
@@ -206,14 +209,19 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
       for (uint32_t i = threadIdx.x; i < m; i += T) list[i] = (uint16_t)i;
       continue;
     }
-    const uint32_t* rank_d = a.ranks + (size_t)d * a.total;
+    const uint32_t* rank_d = a.ranks ? a.ranks + (size_t)d * a.total : nullptr;
     uint32_t lo = 0xFFFFFFFFu, hi = 0;
     for (uint32_t i = threadIdx.x; i < kLocalCap; i += T) {
       uint32_t r = 0xFFFFFFFFu;
       if (i < m) {
-        const uint32_t o = s_orig[i];
-        if (o < a.total) r = rank_d[o];
-        else s_bad = 1;
+        if (ents) {
+          const uint4 e = ents[i];
+          r = d == 0 ? e.x : (d == 1 ? e.y : e.z);
+        } else {
+          const uint32_t o = s_orig[i];
+          if (o < a.total) r = rank_d[o];
+          else s_bad = 1;
+        }
         lo = min(lo, r);
         hi = max(hi, r);
       }

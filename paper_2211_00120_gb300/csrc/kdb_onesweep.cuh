@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(THREADS)
   static_assert(THREADS >= kRadix && THREADS % 32 == 0, "one thread per digit");
   constexpr int WARPS = THREADS / 32;
   constexpr int TILE = THREADS * ITEMS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   K* s_keys = reinterpret_cast<K*>(smem_raw);
   uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + TILE);
   __shared__ uint32_t s_whist[WARPS][kRadix];
@@ -276,13 +276,13 @@ struct EpiPingPong {
 // item, less its set's first sorted position, is its rank in that dimension.
 template <typename K>
 struct EpiRank {
-  uint32_t* rank;          // rank[item] for this dimension
+  RankOut out;
   const SetInfo* sets;     // nullptr for a single set starting at 0
   int set_shift;           // set id = key >> set_shift (multi-set keys)
   __device__ void operator()(K k, uint32_t v, uint32_t dest) const {
     uint32_t base = 0;
     if (sets) base = sets[(uint32_t)((uint64_t)k >> set_shift)].off;
-    rank[v] = dest - base;
+    out.put(v, dest - base, dest);
   }
 };
 

@@ -338,9 +338,9 @@ struct SegEpiPingPong {
 // an item is its rank in that dimension.
 struct SegEpiRank {
   static constexpr bool kNeedsUpdateInfo = false;
-  uint32_t* rank;
+  RankOut out;
   __device__ void operator()(uint32_t, uint32_t v, uint32_t dest, uint32_t, const TileSegs&) const {
-    rank[v] = dest;
+    out.put(v, dest, dest);
   }
 };
 

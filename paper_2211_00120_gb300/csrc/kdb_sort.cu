@@ -66,21 +66,13 @@ static cudaError_t run_pass(const K* kin, const uint32_t* vin, const Epi& epi, c
   return cudaGetLastError();
 }
 
-cudaError_t pass_u32_pingpong(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
-                              uint32_t* vout, const PassCtl& c, cudaStream_t st) {
-  return run_pass(kin, vin, EpiPingPong<uint32_t>{kout, vout}, c, st);
-}
-cudaError_t pass_u32_rank(const uint32_t* kin, const uint32_t* vin, uint32_t* rank,
-                          const PassCtl& c, cudaStream_t st) {
-  return run_pass(kin, vin, EpiRank<uint32_t>{rank, nullptr, 0}, c, st);
-}
 cudaError_t pass_u64_pingpong(const uint64_t* kin, const uint32_t* vin, uint64_t* kout,
                               uint32_t* vout, const PassCtl& c, cudaStream_t st) {
   return run_pass(kin, vin, EpiPingPong<uint64_t>{kout, vout}, c, st);
 }
-cudaError_t pass_u64_rank(const uint64_t* kin, const uint32_t* vin, uint32_t* rank,
+cudaError_t pass_u64_rank(const uint64_t* kin, const uint32_t* vin, const RankOut& out,
                           const SetInfo* sets, int set_shift, const PassCtl& c, cudaStream_t st) {
-  return run_pass(kin, vin, EpiRank<uint64_t>{rank, sets, set_shift}, c, st);
+  return run_pass(kin, vin, EpiRank<uint64_t>{out, sets, set_shift}, c, st);
 }
 cudaError_t pass_u64_update(const uint64_t* kin, const uint32_t* vin, const LevelCtx& x,
                             uint32_t* perm, uint32_t* vals_next, const PassCtl& c,
@@ -113,9 +105,9 @@ size_t seg_pass_smem() {
 }
 
 cudaError_t seg_pass_rank(const uint32_t* kin, const uint32_t* vin, const LevelCtx& x,
-                          const uint32_t* seg_hist, uint32_t* rank, const PassCtl& c,
+                          const uint32_t* seg_hist, const RankOut& out, const PassCtl& c,
                           cudaStream_t st) {
-  return run_seg_pass(kin, vin, x, seg_hist, SegEpiRank{rank}, c, st);
+  return run_seg_pass(kin, vin, x, seg_hist, SegEpiRank{out}, c, st);
 }
 
 cudaError_t seg_pass_update(const uint32_t* kin, const uint32_t* vin, const LevelCtx& x,

@@ -35,8 +35,9 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     with pytest.raises(kdb.KdbError) as e:
         kdb.kdb_build_noalloc(pts, 3, kdb.ROUND_ROBIN)
     assert e.value.code == kdb.ERR_INVALID_ARGUMENT
-    # within the point limit but a workspace larger than the static array
-    wide = torch.zeros((kdb.NOALLOC_MAX_POINTS, 8), dtype=torch.float32, device="cuda")
+    # within the point limit but a workspace larger than the static array:
+    # 8 KiB records make the placement's staging area alone 64 MiB
+    wide = torch.zeros((kdb.NOALLOC_MAX_POINTS, 2048), dtype=torch.float32, device="cuda")
     with pytest.raises(kdb.KdbError) as e:
-        kdb.kdb_build_noalloc(wide, 8, kdb.WIDEST_EXTENT)
+        kdb.kdb_build_noalloc(wide, 3, kdb.WIDEST_EXTENT)
     assert e.value.code == kdb.ERR_INVALID_ARGUMENT
