@@ -42,15 +42,19 @@ WORKLOADS = {
                             "(seed 2), widest-extent split",
                             100_000_000, 3, 4, 1, lambda n: synth.aniso_float4(n, seed=2)),
 }
-RADIX_KINDS = ("radix_pass", "radix_pass_rank", "radix_pass_update")
-KERNEL_SOURCES = ["kdb_onesweep.cuh", "kdb_sort.cu", "kdb_internal.cuh"]
+# algorithmic bytes per item of each kernel kind (matches the library's
+# profiling counters): used to turn a launch's bytes into items
+BYTES_PER_ITEM = {"partition_pass": 32.0, "radix_pass": 16.0}
 
 
 def kernel_hash() -> str:
+    """Hash of every CUDA source: a stored ncu traffic figure is only reused
+    while the kernels are exactly the ones it was measured on."""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2211_00120_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    d = os.path.join(ROOT, "paper_2211_00120_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -64,10 +68,12 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def traffic_per_launch(n_items_per_launch: float):
-    """DRAM bytes per radix-pass launch from the committed ncu summary, scaled
-    to this launch size; None if absent or taken on another kernel version."""
-    p = os.path.join(ROOT, "profiles", "onesweep_traffic.json")
+def traffic_per_launch(kind: str, n_items_per_launch: float):
+    """DRAM bytes per launch of `kind` from the committed ncu summary
+    (profiles/<kind>_traffic.json, measured on a smaller case and scaled by
+    the items a launch processes); None if absent or measured on other
+    kernel sources."""
+    p = os.path.join(ROOT, "profiles", f"{kind}_traffic.json")
     try:
         with open(p) as f:
             j = json.load(f)
@@ -270,22 +276,24 @@ def main():
         ms = float(t.item())
     value = world * n / (ms / 1000.0) / 1e6
 
-    # roofline of the dominant kernel: the onesweep radix pass
-    rad = [p for p in prof if p["name"] in RADIX_KINDS]
-    r_ms = sum(p["ms"] for p in rad)
-    r_bytes = sum(p["bytes"] for p in rad)
-    r_launch = sum(p["launches"] for p in rad)
+    # roofline of the dominant kernel (largest share of the step): its
+    # algorithmic bytes over its own CUDA-event time in the timed steps
+    dom = max(prof, key=lambda p: p["ms"])
     peak, peak_src = measured_peak()
-    achieved = r_bytes / (r_ms / 1000.0) / 1e9 if r_ms > 0 else None
+    achieved = dom["bytes"] / (dom["ms"] / 1000.0) / 1e9 if dom["ms"] > 0 else None
     build_ms_total = ms
     kernel_ms = {p["name"]: round(p["ms"] / args.steps, 3) for p in prof}
     fb = floor_bytes(n, stride)
-    traffic = traffic_per_launch(n * 1.0) if r_launch else None
+    traffic = None
+    if dom["name"] in BYTES_PER_ITEM and dom["launches"]:
+        items = dom["bytes"] / BYTES_PER_ITEM[dom["name"]] / dom["launches"]
+        traffic = traffic_per_launch(dom["name"], items)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "kernel": "onesweep radix pass (all variants)",
-                "launches_per_step": r_launch / args.steps,
-                "kernel_share_of_step": r_ms / args.steps / build_ms_total,
+                "kernel": dom["name"],
+                "launches_per_step": dom["launches"] / args.steps,
+                "kernel_share_of_step": dom["ms"] / args.steps / build_ms_total,
+                "algorithmic_bytes_per_launch": dom["bytes"] / max(dom["launches"], 1),
                 "peak_source": peak_src,
                 "build_floor_frac": fb / (peak * 1e9) / (build_ms_total / 1000.0)}
 

@@ -107,10 +107,19 @@ __global__ void __launch_bounds__(kThreads) prepass_kernel(PrepassArgs a) {
         if (a.keys64) a.keys64[(uint64_t)d * a.kstride + i] = ((uint64_t)cur << 32) | key;
       }
       if (a.hist) {
+        // low digits spread over many bins: plain shared atomics; the top
+        // float digit and the set-id digits repeat within a warp, so those
+        // are aggregated per warp first
         const uint64_t k64 = ((uint64_t)cur << 32) | key;
-        for (int p = 0; p < a.passes; ++p)
-          hist_add(s_hist + (d * a.passes + p) * kRadixBins,
-                   (uint32_t)(k64 >> (8 * p)) & (kRadixBins - 1), ok);
+        for (int p = 0; p < a.passes; ++p) {
+          uint32_t* h = s_hist + (d * a.passes + p) * kRadixBins;
+          const uint32_t bin = (uint32_t)(k64 >> (8 * p)) & (kRadixBins - 1);
+          if (p < 3) {
+            if (ok) atomicAdd(h + bin, 1u);
+          } else {
+            hist_add(h, bin, ok);
+          }
+        }
       }
     }
   }
@@ -384,8 +393,8 @@ __global__ void perm_walk_kernel(PermuteArgs a, int round, uint32_t group) {
   const uint32_t ld = leader_of_block(b, round, group);
   if (ld >= a.total || (a.perm[ld] & kMark)) return;
   uint32_t cur = ld;
+  uint32_t nxt = a.perm[cur] & ~kMark;
   for (uint32_t steps = 0; steps <= a.total; ++steps) {
-    const uint32_t nxt = a.perm[cur] & ~kMark;
     if (nxt >= a.total) {
       atomicOr(a.err, ERR_INTERNAL);
       return;
@@ -393,12 +402,16 @@ __global__ void perm_walk_kernel(PermuteArgs a, int round, uint32_t group) {
     unsigned char* dst = a.pts + (uint64_t)cur * a.stride;
     if (is_leader(nxt, round, group)) {
       copy_record(dst, a.stage + (uint64_t)(nxt / group) * a.stride, a.stride);
-      a.perm[cur] |= kMark;
+      a.perm[cur] = nxt | kMark;
       return;
     }
+    // the next link is read together with the record, so a step costs one
+    // memory latency, not two
+    const uint32_t after = a.perm[nxt] & ~kMark;
     copy_record(dst, a.pts + (uint64_t)nxt * a.stride, a.stride);
-    a.perm[cur] |= kMark;
+    a.perm[cur] = nxt | kMark;
     cur = nxt;
+    nxt = after;
   }
   atomicOr(a.err, ERR_INTERNAL);  // longer than any cycle: perm is not a permutation
 }
