@@ -338,7 +338,7 @@ void make_plan(Plan& P) {
   P.o_tickets = take((size_t)P.total_passes * 4);
   P.o_err = take(4);
   P.o_bbox = take(P.sets.size() * 2 * P.k * 4);
-  P.o_stage = take(((T + 31) / 32) * (size_t)P.stride);
+  P.o_stage = take(((T + kPermGroup - 1) / kPermGroup) * (size_t)P.stride);
   P.o_sets = take(P.sets.size() * sizeof(SetInfo));
   size_t nact = 0;
   P.act_off.assign(levels, 0);

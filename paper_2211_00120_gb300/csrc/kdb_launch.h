@@ -208,12 +208,15 @@ cudaError_t launch_widest_children(const WidestArgs& a, cudaStream_t st);
 cudaError_t launch_rr_dims(uint8_t* dims, const SetInfo* sets, uint32_t nsets, uint32_t total,
                            int k, cudaStream_t st);
 
+// Placement: one cycle leader (and one staged record) per kPermGroup nodes.
+constexpr uint32_t kPermGroup = 16;
+
 struct PermuteArgs {
   unsigned char* pts;
   uint32_t total;
   int stride;
   uint32_t* perm;          // node -> original index, marked on the way
-  unsigned char* stage;    // ceil(total / 32) records
+  unsigned char* stage;    // ceil(total / kPermGroup) records
   uint32_t* err;
 };
 cudaError_t launch_permute(const PermuteArgs& a, int num_sms, cudaStream_t st);

@@ -160,6 +160,8 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
   __shared__ uint32_t s_bad;
   if (*reinterpret_cast<volatile uint32_t*>(a.err)) return;
   const int k = a.k;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
   uint32_t* s_orig = reinterpret_cast<uint32_t*>(sm);                      // kLocalCap
   uint16_t* s_lists = reinterpret_cast<uint16_t*>(s_orig + kLocalCap);     // (k+1) * cap
   unsigned char* s_area = reinterpret_cast<unsigned char*>(s_lists + (size_t)(k + 1) * kLocalCap);
@@ -272,6 +274,113 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     if (L == tree.L - 1) {
       const uint32_t c0 = ((s0 + 1) << j) - 1;
       nn = c0 >= tree.n ? 0 : min(nodes, tree.n - c0);
+    }
+    if (nodes >= (uint32_t)W) {
+      // Deep depths: every subtree is owned by one warp (or, when subtrees
+      // average fewer than 8 points, by one thread).  Segment bounds and
+      // pivot ranks come from the O(1) layout formulas; the owner marks its
+      // subtree's sides and partitions its subtree's part of every list, so a
+      // depth needs one block barrier per list.
+      const bool per_thread = mj < 8u * nn;
+      const uint32_t own0 = per_thread ? threadIdx.x : (uint32_t)warp;
+      const uint32_t ownstep = per_thread ? (uint32_t)T : (uint32_t)W;
+      const uint32_t c0 = ((s0 + 1) << j) - 1;
+      const int drr = L % k;
+      const bool lowest = L == tree.L - 1;
+      for (uint32_t t = own0; t < nn; t += ownstep) {
+        const uint32_t crel = first + t;
+        const uint32_t st = yj.seg_start(crel) - base;
+        const uint32_t sz = yj.seg_start(crel + 1) - yj.seg_start(crel);
+        const uint32_t pr = yj.h >= 1 ? yj.left_size(crel) : 0u;
+        const uint32_t loc = nodes - 1 + t;  // local level-order index
+        int d = drr;
+        if (a.mode == 1) {  // widest: the node's domain from the planes above it
+          float lo[kMaxK], hi[kMaxK];
+          for (int dd = 0; dd < k; ++dd) {
+            lo[dd] = s_box[dd];
+            hi[dd] = s_box[kMaxK + dd];
+          }
+          for (int i = 0; i < j; ++i) {
+            const uint32_t la = (1u << i) - 1 + (t >> (j - i));
+            const int da = s_ldim[la];
+            const float xv = s_lplane[la];
+            if (((t >> (j - 1 - i)) & 1u) == 0) hi[da] = xv; else lo[da] = xv;
+          }
+          d = widest_dim(lo, hi, k);
+        }
+        const uint16_t* list = s_lists + (size_t)s_list_of[d] * kLocalCap;
+        if (per_thread || lane == 0) {
+          const uint32_t o = s_orig[list[st + pr]];
+          a.perm[ls.off + c0 + t] = o;
+          if (a.mode == 1) {
+            s_ldim[loc] = (uint8_t)d;
+            s_lplane[loc] = coord_of(a.pts, o, a.stride, d);
+            a.dims[ls.off + c0 + t] = (uint8_t)d;
+          }
+        }
+        for (uint32_t q = per_thread ? 0u : (uint32_t)lane; q < sz; q += per_thread ? 1u : 32u)
+          s_side[list[st + q]] = q < pr ? 0 : (q == pr ? 2 : 1);
+      }
+      __syncthreads();
+      if (lowest) break;
+      const uint32_t mn = mj - nn;
+      const int depth_left = tree.L - 1 - (L + 1);
+      for (int dd = 0; dd < k; ++dd) {
+        if (a.mode == 0) {
+          bool need = false;
+          for (int jj = 0; jj <= depth_left && !need; ++jj) need = ((L + 1 + jj) % k) == dd;
+          if (!need) continue;
+        }
+        const uint16_t* src = s_lists + (size_t)s_list_of[dd] * kLocalCap;
+        uint16_t* dst = s_lists + (size_t)s_list_of[k] * kLocalCap;
+        for (uint32_t t = own0; t < nn; t += ownstep) {
+          const uint32_t crel = first + t;
+          const uint32_t st = yj.seg_start(crel) - base;
+          const uint32_t sz = yj.seg_start(crel + 1) - yj.seg_start(crel);
+          const uint32_t pr = yj.left_size(crel);
+          const uint32_t nl = st - t, nr = st - t + pr;
+          uint32_t cl = 0, cr = 0;
+          if (per_thread) {
+            for (uint32_t q = 0; q < sz; ++q) {
+              const uint16_t it = src[st + q];
+              const uint8_t sd = s_side[it];
+              if (sd == 0) dst[nl + cl++] = it;
+              else if (sd == 1) dst[nr + cr++] = it;
+            }
+            if (nl + cl > mn || nr + cr > mn) s_bad = 1;
+          } else {
+            for (uint32_t q0 = 0; q0 < sz; q0 += 32) {
+              const uint32_t q = q0 + lane;
+              uint16_t it = 0;
+              uint8_t sd = 3;
+              if (q < sz) {
+                it = src[st + q];
+                sd = s_side[it];
+              }
+              const uint32_t bl = __ballot_sync(0xffffffffu, sd == 0);
+              const uint32_t br = __ballot_sync(0xffffffffu, sd == 1);
+              uint32_t np = 0xFFFFFFFFu;
+              if (sd == 0) np = nl + cl + __popc(bl & lt);
+              if (sd == 1) np = nr + cr + __popc(br & lt);
+              if (sd <= 1) {
+                if (np < mn) dst[np] = it;
+                else s_bad = 1;
+              }
+              cl += __popc(bl);
+              cr += __popc(br);
+            }
+          }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          const int t2 = s_list_of[dd];
+          s_list_of[dd] = s_list_of[k];
+          s_list_of[k] = t2;
+        }
+        __syncthreads();
+      }
+      mj = mn;
+      continue;
     }
     // per node: segment start, pivot rank, lefts before it
     for (uint32_t t = threadIdx.x; t < nn; t += T) {

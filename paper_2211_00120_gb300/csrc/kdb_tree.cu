@@ -338,9 +338,9 @@ __global__ void rr_dims_kernel(uint8_t* dims, const SetInfo* sets, uint32_t nset
 // Final placement (Sec. 3.2: after the last iteration each point's tag is its
 // node, and the array ends up sorted by tag), done as an almost-in-place
 // permutation of the caller's records: perm[node] = original index is the one
-// int32 per point; the staging area holds one record per 32.
+// int32 per point; the staging area holds one record per kPermGroup nodes.
 //
-// perm splits into cycles.  Every block of 32 consecutive nodes designates one
+// perm splits into cycles.  Every block of kPermGroup consecutive nodes designates one
 // "leader" (a hashed offset inside the block).  Phase 1 copies each leader's
 // record aside.  Phase 2 starts one walker per leader: it fills its node from
 // the node perm points to, moves there, and repeats until the next node is a
@@ -544,9 +544,9 @@ cudaError_t launch_rr_dims(uint8_t* dims, const SetInfo* sets, uint32_t nsets, u
 cudaError_t launch_permute(const PermuteArgs& a, int num_sms, cudaStream_t st) {
   (void)num_sms;
   if (a.total == 0) return cudaSuccess;
-  // both rounds use one leader per 32 nodes (the staging area holds
-  // ceil(total/32) records); the second round hashes to other offsets
-  const uint32_t groups[2] = {32, 32};
+  // both rounds use one leader per kPermGroup nodes (the staging area holds
+  // ceil(total / kPermGroup) records); the second round hashes to other offsets
+  const uint32_t groups[2] = {kPermGroup, kPermGroup};
   for (int r = 0; r < 2; ++r) {
     const uint32_t nb = (a.total + groups[r] - 1) / groups[r];
     const uint32_t grid = (nb + kThreads - 1) / kThreads;
