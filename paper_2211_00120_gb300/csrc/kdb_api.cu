@@ -196,7 +196,8 @@ struct Plan {
   size_t o_vloc, o_lbox, o_lsets, o_work, o_whole;
   // presorted lists (k <= 3): one list of 16-byte entries per dimension
   bool use_lists = false;
-  size_t o_rows, o_sorted, o_lists, o_ents, o_piv;
+  size_t o_rows, o_lists, o_ents, o_piv, o_l0;
+  size_t rec_hist_off = 0;  // record-sort histograms (in u32, inside the histogram area)
   uint32_t max_nseg = 0;
   uint64_t kstride = 0;  // elements between two dimensions' coordinate keys
 };
@@ -250,7 +251,9 @@ void make_plan(Plan& P) {
   P.nseg.assign(levels, 0);
   P.chunks.assign(levels, 0);
   P.hist_off.assign(levels, 0);
-  size_t hist_words = (size_t)P.k * P.rank_passes * kRadixBins;
+  // list mode sorts 16-byte entries per set (histograms added below); the
+  // other modes rank every dimension first
+  size_t hist_words = P.use_lists ? 0 : (size_t)P.k * P.rank_passes * kRadixBins;
   for (int l = 0; l < levels; ++l) {
     uint32_t base = 0;
     bool all_long = true;  // every segment of every active set >= 2^13 - 1 items
@@ -275,6 +278,17 @@ void make_plan(Plan& P) {
     P.max_nseg = std::max(P.max_nseg, na << l);
     if (P.use_lists) {
       P.passes[l] = P.k;  // one partition pass per list
+      if (l == 0) {       // per-set chunks of the level-0 histograms
+        uint32_t chunk = 0;
+        for (ActiveEntry& e : P.act[0]) {
+          e.chunk0 = chunk;
+          e.cps = (P.sets[e.set].n + kSegChunk - 1) / kSegChunk;
+          chunk += e.cps;
+        }
+        P.chunks[0] = chunk;
+        P.rec_hist_off = hist_words;
+        hist_words += (size_t)P.k * 4 * na * kRadixBins;
+      }
     } else if (P.seg[l]) {
       P.passes[l] = std::max(1, ceil_div_i(P.rb, 8));
       P.nseg[l] = na << l;
@@ -306,7 +320,7 @@ void make_plan(Plan& P) {
       if (j < P.act[l + 1].size() && P.act[l + 1][j].set == e.set) e.next = (int32_t)j;
     }
   }
-  P.total_passes += P.k * P.rank_passes;
+  P.total_passes += P.k * (P.use_lists ? 4 : P.rank_passes);
 
   const uint64_t T = P.total;
   const size_t ksz = P.sets.size() > 1 ? 8 : 4;
@@ -317,13 +331,14 @@ void make_plan(Plan& P) {
     return at;
   };
   // 64-bit keys: several sets' rank sorts, or packed level keys; else 32-bit
-  const size_t kb = (P.sets.size() > 1 || !P.use_lists) ? 8 : 4;
+  // rank sorts and packed-key levels (not used in list mode)
+  const size_t kb = P.use_lists ? 0 : 8;
   P.o_keysA = take(T * kb);
   P.o_keysB = take(T * kb);
-  P.o_valsA = take(T * 4);
-  P.o_valsB = take(T * 4);
+  P.o_valsA = take(P.use_lists ? 0 : T * 4);
+  P.o_valsB = take(P.use_lists ? 0 : T * 4);
   P.kstride = (T + 63) & ~uint64_t(63);  // per-dimension key arrays start 256-byte aligned
-  P.o_ckeys = take(P.kstride * P.k * ksz);
+  P.o_ckeys = take(P.use_lists ? 0 : P.kstride * P.k * ksz);
   P.o_ranks = take(P.use_lists ? 0 : T * P.k * 4);
   P.o_perm = take(T * 4);
   P.o_dims = take(T);
@@ -354,11 +369,11 @@ void make_plan(Plan& P) {
   P.o_work = take(P.work.size() * sizeof(LocalWork));
   P.o_whole = take(sizeof(ActiveEntry));  // one segment spanning the whole array
   const bool L = P.use_lists, G = L && levels > 0;  // G: there are global levels
-  P.o_rows = take(L ? T * 16 : 0);
-  P.o_sorted = take(G ? P.kstride * P.k * 4 : 0);
-  P.o_lists = take(G ? T * 16 * 2 * P.k : 0);
-  P.o_ents = take(G ? T * 16 : 0);
-  P.o_piv = take(L ? (size_t)std::max<uint32_t>(P.max_nseg, 1) * 4 : 0);
+  P.o_rows = take(L ? T * 16 : 0);                   // entries in input order
+  P.o_lists = take(G ? T * 16 * 2 * P.k : 0);        // per dimension, double-buffered
+  P.o_ents = take(G ? T * 16 : 0);                   // entries handed to the local finish
+  P.o_piv = take(L ? (size_t)std::max<uint32_t>(P.max_nseg, 1) * 8 : 0);
+  P.o_l0 = take(G && P.sets.size() > 1 ? T * 16 : 0);  // level-0 array of several sets
   P.bytes = o;
 }
 
@@ -485,34 +500,32 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   pa.stride = P.stride;
   pa.sets = d_sets;
   pa.nsets = (uint32_t)P.sets.size();
-  pa.keys32 = multi ? nullptr : at<uint32_t>(ws, P.o_ckeys);
-  pa.keys64 = multi ? at<uint64_t>(ws, P.o_ckeys) : nullptr;
-  pa.kstride = P.kstride;
-  pa.hist = hist;
-  pa.passes = P.rank_passes;
+  uint4* ents0 = at<uint4>(ws, P.o_rows);
+  if (P.use_lists) {
+    pa.ents = ents0;
+  } else {
+    pa.keys32 = multi ? nullptr : at<uint32_t>(ws, P.o_ckeys);
+    pa.keys64 = multi ? at<uint64_t>(ws, P.o_ckeys) : nullptr;
+    pa.kstride = P.kstride;
+    pa.hist = hist;
+    pa.passes = P.rank_passes;
+  }
   pa.bbox = widest ? bbox : nullptr;
   pa.err = err;
   {
-    Prof pf(K_PREPASS, (double)T * k * (4.0 + (multi ? 8 : 4)), 1, st);
+    Prof pf(K_PREPASS, P.use_lists ? (double)T * (4.0 * k + 16.0) : (double)T * k * (4.0 + (multi ? 8 : 4)), 1, st);
     KDB_CK(launch_prepass(pa, sms, st));
   }
   uint32_t* hcur = hist + (size_t)k * P.rank_passes * kRadixBins;
 
-  // ---- per-dimension ranks
-  uint32_t* rows = at<uint32_t>(ws, P.o_rows);
-  uint32_t* sorted = at<uint32_t>(ws, P.o_sorted);
+  // ---- per-dimension ranks (packed-key levels, k >= 4)
   auto rank_out = [&](int d) {
     RankOut o{};
     o.d = d;
-    if (P.use_lists) {
-      o.rows = rows;
-      if (!P.act.empty()) o.sorted = sorted + (size_t)d * P.kstride;
-    } else {
-      o.rank = ranks + (size_t)d * T;
-    }
+    o.rank = ranks + (size_t)d * T;
     return o;
   };
-  for (int d = 0; d < k; ++d) {
+  for (int d = 0; d < (P.use_lists ? 0 : k); ++d) {
     const uint32_t* hd = hist + (size_t)d * P.rank_passes * kRadixBins;
     if (!multi) {
       // one set: the segmented pass with a single segment spanning the array
@@ -530,7 +543,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
         PassCtl c = ctl(T, 8 * p, nullptr);
         const uint32_t* hp = hd + p * kRadixBins;
         if (p + 1 == P.rank_passes) {
-          Prof pf(K_RADIX_RANK, (double)T * (P.use_lists ? 16 : 12), 1, st);
+          Prof pf(K_RADIX_RANK, (double)T * 12, 1, st);
           KDB_CK(seg_pass_rank(kin, vin, wx, hp, rank_out(d), c, st));
         } else {
           Prof pf(K_RADIX, (double)T * 16, 1, st);
@@ -547,7 +560,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       for (int p = 0; p < P.rank_passes; ++p) {
         PassCtl c = ctl(T, 8 * p, hd + p * kRadixBins);
         if (p + 1 == P.rank_passes) {
-          Prof pf(K_RADIX_RANK, (double)T * (P.use_lists ? 20 : 16), 1, st);
+          Prof pf(K_RADIX_RANK, (double)T * 16, 1, st);
           KDB_CK(pass_u64_rank(kin, vin, rank_out(d), d_sets, 32, c, st));
         } else {
           Prof pf(K_RADIX, (double)T * 24, 1, st);
@@ -581,27 +594,57 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   uint4* lcur[3] = {nullptr, nullptr, nullptr};
   uint4* lnext[3] = {nullptr, nullptr, nullptr};
   uint4* ents_local = at<uint4>(ws, P.o_ents);
-  uint32_t* piv = at<uint32_t>(ws, P.o_piv);
+  uint2* piv = at<uint2>(ws, P.o_piv);
   if (P.use_lists) {
     for (int d = 0; d < k; ++d) {
       lcur[d] = at<uint4>(ws, P.o_lists) + (size_t)(2 * d) * T;
       lnext[d] = at<uint4>(ws, P.o_lists) + (size_t)(2 * d + 1) * T;
     }
     if (levels > 0) {
-      ListBuildArgs lb{};
-      lb.x.sets = d_sets;
-      lb.x.act = d_act + P.act_off[0];
-      lb.x.nact = (uint32_t)P.act[0].size();
-      lb.x.err = err;
-      lb.items = P.items[0];
-      lb.rows = rows;
-      lb.sorted = sorted;
-      lb.kstride = P.kstride;
-      lb.total = T;
-      lb.k = k;
-      for (int d = 0; d < k; ++d) lb.lists[d] = lcur[d];
-      Prof pf(K_LISTS, (double)P.items[0] * k * (4.0 + 16.0 + 16.0), 1, st);
-      KDB_CK(launch_build_lists(lb, st));
+      // level-0 lists: per dimension a stable LSD radix sort of the entries
+      // by the coordinate key, from input order (so ties keep index order)
+      LevelCtx x0{};
+      x0.sets = d_sets;
+      x0.act = d_act + P.act_off[0];
+      x0.nact = (uint32_t)P.act[0].size();
+      x0.l = 0;
+      x0.err = err;
+      const uint32_t n0 = P.items[0];
+      const uint4* l0 = ents0;
+      if (multi) {
+        ListBuildArgs lb{};
+        lb.x = x0;
+        lb.items = n0;
+        lb.ents = ents0;
+        lb.out = at<uint4>(ws, P.o_l0);
+        lb.total = T;
+        Prof pf(K_LISTS, (double)n0 * 32, 1, st);
+        KDB_CK(launch_gather_level0(lb, st));
+        l0 = lb.out;
+      }
+      RecHistArgs rh{};
+      rh.x = x0;
+      rh.chunks = P.chunks[0];
+      rh.ents = l0;
+      rh.hist = hist + P.rec_hist_off;
+      rh.nseg = x0.nact;
+      rh.k = k;
+      {
+        Prof pf(K_LISTS, (double)n0 * 16, 1, st);
+        KDB_CK(launch_rec_hist(rh, st));
+      }
+      uint4* tmp[2] = {lnext[0], ents_local};  // free until the level loop uses them
+      for (int d = 0; d < k; ++d) {
+        const uint4* in = l0;
+        for (int p = 0; p < 4; ++p) {
+          uint4* out = p == 3 ? lcur[d] : tmp[p & 1];
+          PassCtl c = ctl(n0, 8 * p, nullptr);
+          const uint32_t* sh = rh.hist + ((size_t)(d * 4 + p) * x0.nact) * kRadixBins;
+          Prof pf(K_RADIX, (double)n0 * 32, 1, st);
+          KDB_CK(launch_rec_sort_pass(in, out, c, x0, sh, d, st));
+          in = out;
+        }
+      }
     }
   }
   for (int l = 0; l < levels; ++l) {
@@ -775,7 +818,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     la.lsets = d_lsets;
     la.vals_local = vals_local;
     la.ents_local = P.use_lists ? ents_local : nullptr;
-    la.rows = P.use_lists ? reinterpret_cast<const uint4*>(rows) : nullptr;
+    la.rows = P.use_lists ? ents0 : nullptr;
     la.ranks = P.use_lists ? nullptr : ranks;
     la.total = T;
     la.k = k;

@@ -22,26 +22,36 @@ struct LevelCtx {
   uint32_t* vals_local;  // per set at its first record: the local level's items
 };
 
+struct PassCtl;
+
 // Presorted-list levels (kdb_part.cu), k <= 3: one 16-byte entry per point
-// (ranks in dimensions 0..2, original index), one list per dimension.
+// (order-preserving keys of coordinates 0..2, original index), one list per
+// dimension.
 constexpr int kPartThreads = 256;
 constexpr int kPartItems = 15;
 constexpr int kPartTile = kPartThreads * kPartItems;  // < 2^13 - 1: <= two segments a tile
-struct ListBuildArgs {
+constexpr int kRecThreads = 256;
+constexpr int kRecItems = 15;
+struct ListBuildArgs {      // level-0 array of several sets
   LevelCtx x;               // level 0
-  uint32_t items;           // items of level 0
-  const uint32_t* rows;     // rank rows, 4 words per point
-  const uint32_t* sorted;   // per dimension: points in sorted order (stride kstride)
-  uint64_t kstride;
+  uint32_t items;
+  const uint4* ents;        // entries in input order
+  uint4* out;
   uint32_t total;
+};
+struct RecHistArgs {        // digit histograms per (dimension, pass, set)
+  LevelCtx x;               // level 0 (chunk0 / cps filled in)
+  uint32_t chunks;
+  const uint4* ents;        // level-0 array
+  uint32_t* hist;           // [k*4][nseg][256]
+  uint32_t nseg;
   int k;
-  uint4* lists[3];
 };
 struct PivotArgs {
   LevelCtx x;
   const uint4* lists[3];    // this level's lists
   uint32_t items;
-  uint32_t* piv;            // out: pivot rank per segment (ai << l | s_rel)
+  uint2* piv;               // out: pivot (key, original index) per segment
   uint32_t* perm;           // out: node -> original index
   const uint8_t* dims;      // widest: split dimension per node
   int k, mode;
@@ -51,7 +61,7 @@ struct PartArgs {
   const uint4* in;          // this level's list sorted by dimension dlist
   uint4* out_next;          // next level's list
   uint4* out_local;         // entries for the local finish (sets leaving)
-  const uint32_t* piv;
+  const uint2* piv;
   const uint8_t* dims;
   int k, mode, dlist;
   uint32_t n, next_items, total;
@@ -61,7 +71,11 @@ struct PartArgs {
   uint64_t wait_ns;
 };
 size_t partition_smem();
-cudaError_t launch_build_lists(const ListBuildArgs& a, cudaStream_t st);
+size_t rec_sort_smem();
+cudaError_t launch_gather_level0(const ListBuildArgs& a, cudaStream_t st);
+cudaError_t launch_rec_hist(const RecHistArgs& a, cudaStream_t st);
+cudaError_t launch_rec_sort_pass(const uint4* in, uint4* out, const PassCtl& c, const LevelCtx& x,
+                                 const uint32_t* seg_hist, int d, cudaStream_t st);
 cudaError_t launch_pivots(const PivotArgs& a, cudaStream_t st);
 cudaError_t launch_partition(const PartArgs& a, cudaStream_t st);
 
@@ -85,7 +99,7 @@ struct LocalArgs {
   uint32_t nwork;
   const LocalSet* lsets;
   const uint32_t* vals_local;   // original indices (rank arrays gathered), or
-  const uint4* ents_local;      // entries (k <= 3): ranks and original index
+  const uint4* ents_local;      // entries (k <= 3): coordinate keys and original index
   const uint4* rows;            // entries in input order (sets local from level 0)
   const uint32_t* ranks;
   uint32_t total;
@@ -114,7 +128,6 @@ constexpr int kSegMinBlocks = 3;
 constexpr int kSegTile = kSegThreads * kSegItems;
 size_t seg_pass_smem();
 
-struct PassCtl;
 
 // onesweep passes (kdb_sort.cu)
 cudaError_t pass_u64_pingpong(const uint64_t* kin, const uint32_t* vin, uint64_t* kout,
@@ -148,6 +161,7 @@ struct PrepassArgs {
   uint32_t* keys32;     // k * total (single set) or nullptr
   uint64_t* keys64;     // k * total (several sets) or nullptr
   uint64_t kstride;     // elements between two dimensions' keys (>= total)
+  uint4* ents;          // k <= 3: entries (keys of dims 0..2, index) or nullptr
   uint32_t* hist;       // k * passes * 256, or nullptr
   int passes;
   uint32_t* bbox;       // nsets * 2k (min keys, then max keys) or nullptr

@@ -23,6 +23,13 @@ namespace {
 
 constexpr int T = kLocalThreads;
 constexpr int W = T / 32;
+// nodes per level of a subtree finished by one warp (see the warp phase)
+constexpr int kWarpTab = 1 << (kLocalLog - 1 - 5);
+static_assert(W == 32, "the warp phase starts at the first depth with >= 32 subtrees");
+// level-phase scratch: side + 3 node tables + dims + planes + warp tables
+static_assert(kLocalCap + 3 * 2 * (kLocalCap / 2 + 8) + kLocalCap + 4 * kLocalCap +
+                      W * 2 * kWarpTab * 2 <= 12 * kLocalCap,
+              "level-phase scratch fits the sort area");
 
 __device__ inline int widest_dim(const float* lo, const float* hi, int k) {
   int best = 0;
@@ -205,25 +212,79 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
   if (l0 > 0) dpar = a.mode == 0 ? (l0 - 1) % k : a.dims[ls.off + (s0 - 1) / 2];
   // the spare list slot holds the radix counters while the lists are built
   uint16_t* s_wh = s_lists + (size_t)k * kLocalCap;
+  if (ents) {
+    // Lists ordered by (key_d, original index).  The items arrive ordered so
+    // in the parent's split dimension (on a set's level 0: by index).  For
+    // the other dimensions the items are put in index order once, then
+    // sorted stably by key from that order.
+    int todo[kMaxK];
+    int nt = 0;
+    for (int d = 0; d < k; ++d)
+      if (d != dpar) todo[nt++] = d;
+    if (dpar >= 0) {
+      uint16_t* list = s_lists + (size_t)dpar * kLocalCap;
+      for (uint32_t i = threadIdx.x; i < m; i += T) list[i] = (uint16_t)i;
+    }
+    if (nt > 0) {
+      uint16_t* ord = s_lists + (size_t)todo[nt - 1] * kLocalCap;  // index order
+      if (l0 > 0) {
+        uint32_t lo = 0xFFFFFFFFu, hi = 0;
+        for (uint32_t i = threadIdx.x; i < m; i += T) {
+          lo = min(lo, s_orig[i]);
+          hi = max(hi, s_orig[i]);
+        }
+        lo = block_min(lo, s_w);
+        hi = block_max(hi, s_w);
+        for (uint32_t i = threadIdx.x; i < m; i += T) {
+          s_ka[i] = s_orig[i] - lo;
+          s_ia[i] = (uint16_t)i;
+        }
+        __syncthreads();
+        const int passes = (bits_for((uint64_t)(hi - lo) + 1) + 7) / 8;
+        const uint16_t* sorted = smem_radix_sort(s_ka, s_ia, s_kb, s_ib, s_wh, m, passes, s_w);
+        for (uint32_t i = threadIdx.x; i < m; i += T) ord[i] = sorted[i];
+      } else {
+        for (uint32_t i = threadIdx.x; i < m; i += T) ord[i] = (uint16_t)i;
+      }
+      __syncthreads();
+      for (int q = 0; q < nt; ++q) {
+        const int d = todo[q];
+        uint32_t lo = 0xFFFFFFFFu, hi = 0;
+        for (uint32_t i = threadIdx.x; i < m; i += T) {
+          const uint16_t it = ord[i];
+          const uint4 e = ents[it];
+          const uint32_t key = d == 0 ? e.x : (d == 1 ? e.y : e.z);
+          s_ka[i] = key;
+          s_ia[i] = it;
+          lo = min(lo, key);
+          hi = max(hi, key);
+        }
+        lo = block_min(lo, s_w);
+        hi = block_max(hi, s_w);
+        for (uint32_t i = threadIdx.x; i < m; i += T) s_ka[i] -= lo;
+        __syncthreads();
+        const int passes = (bits_for((uint64_t)(hi - lo) + 1) + 7) / 8;
+        const uint16_t* sorted = smem_radix_sort(s_ka, s_ia, s_kb, s_ib, s_wh, m, passes, s_w);
+        uint16_t* list = s_lists + (size_t)d * kLocalCap;
+        for (uint32_t i = threadIdx.x; i < m; i += T) list[i] = sorted[i];
+        __syncthreads();
+      }
+    }
+  } else {
   for (int d = 0; d < k; ++d) {
     uint16_t* list = s_lists + (size_t)d * kLocalCap;
     if (d == dpar) {
       for (uint32_t i = threadIdx.x; i < m; i += T) list[i] = (uint16_t)i;
       continue;
     }
-    const uint32_t* rank_d = a.ranks ? a.ranks + (size_t)d * a.total : nullptr;
+    const uint32_t* rank_d = a.ranks + (size_t)d * a.total;
     uint32_t lo = 0xFFFFFFFFu, hi = 0;
     for (uint32_t i = threadIdx.x; i < kLocalCap; i += T) {
       uint32_t r = 0xFFFFFFFFu;
       if (i < m) {
-        if (ents) {
-          const uint4 e = ents[i];
-          r = d == 0 ? e.x : (d == 1 ? e.y : e.z);
-        } else {
-          const uint32_t o = s_orig[i];
-          if (o < a.total) r = rank_d[o];
-          else s_bad = 1;
-        }
+        const uint32_t o = s_orig[i];
+        if (o < a.total) r = rank_d[o];
+        else s_bad = 1;
         lo = min(lo, r);
         hi = max(hi, r);
       }
@@ -238,6 +299,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     const uint16_t* sorted = smem_radix_sort(s_ka, s_ia, s_kb, s_ib, s_wh, m, passes, s_w);
     for (uint32_t i = threadIdx.x; i < m; i += T) list[i] = sorted[i];
     __syncthreads();
+  }
   }
 
   // domain of the subtree root (widest mode)
@@ -276,111 +338,131 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
       nn = c0 >= tree.n ? 0 : min(nodes, tree.n - c0);
     }
     if (nodes >= (uint32_t)W) {
-      // Deep depths: every subtree is owned by one warp (or, when subtrees
-      // average fewer than 8 points, by one thread).  Segment bounds and
-      // pivot ranks come from the O(1) layout formulas; the owner marks its
-      // subtree's sides and partitions its subtree's part of every list, so a
-      // depth needs one block barrier per list.
-      const bool per_thread = mj < 8u * nn;
-      const uint32_t own0 = per_thread ? threadIdx.x : (uint32_t)warp;
-      const uint32_t ownstep = per_thread ? (uint32_t)T : (uint32_t)W;
+      // From here on every subtree of this depth is finished by one warp,
+      // independently of the others.  Within its subtree a warp keeps each
+      // node's points in the node's in-order range: the left child takes
+      // [start, start + pr), the pivot's slot stays empty, the right child
+      // takes (start + pr, start + size).  Ranges of different warps never
+      // overlap, so warps need no block barrier and each keeps its own list
+      // rotation.
+      // a warp's subtree has at most 2^(kLocalLog-5) - 1 points, so at most
+      // kWarpTab nodes on any of its levels; two tables per warp
       const uint32_t c0 = ((s0 + 1) << j) - 1;
-      const int drr = L % k;
-      const bool lowest = L == tree.L - 1;
-      for (uint32_t t = own0; t < nn; t += ownstep) {
-        const uint32_t crel = first + t;
-        const uint32_t st = yj.seg_start(crel) - base;
-        const uint32_t sz = yj.seg_start(crel + 1) - yj.seg_start(crel);
-        const uint32_t pr = yj.h >= 1 ? yj.left_size(crel) : 0u;
-        const uint32_t loc = nodes - 1 + t;  // local level-order index
-        int d = drr;
-        if (a.mode == 1) {  // widest: the node's domain from the planes above it
-          float lo[kMaxK], hi[kMaxK];
+      uint16_t* tabs = reinterpret_cast<uint16_t*>(s_lplane + kLocalCap) + (size_t)warp * 2 * kWarpTab;
+      for (uint32_t t = warp; t < nn; t += W) {
+        int slot[kMaxK + 1];
+        for (int q = 0; q <= k; ++q) slot[q] = s_list_of[q];
+        uint16_t* ta = tabs;
+        uint16_t* tb2 = tabs + kWarpTab;
+        const uint32_t root = c0 + t;
+        if (lane == 0) ta[0] = (uint16_t)(yj.seg_start(first + t) - base);
+        __syncwarp();
+        for (int i = 0;; ++i) {
+          const int Li = L + i;
+          if (Li > tree.L - 1) break;
+          const uint32_t cf = ((root + 1) << i) - 1;  // first node of sub-depth i
+          if (cf >= tree.n) break;
+          const uint32_t cnt = min(1u << i, tree.n - cf);
+          const bool lowest = Li == tree.L - 1;
+          const uint32_t jj = j + i;                    // depth below s0
+          const uint32_t loc0 = (1u << jj) - 1 + (t << i);  // local index of node cf
+          const bool coop = cnt <= 8;  // few nodes: the warp shares each node's items
+          // pins, sides, widest dimensions
+          for (uint32_t u = coop ? 0u : (uint32_t)lane; u < cnt; u += coop ? 1u : 32u) {
+            const uint32_t node = cf + u;
+            const uint32_t st = ta[u];
+            const uint32_t sz = subtree_size(tree, node);
+            const uint32_t pr = subtree_size(tree, 2 * node + 1);
+            int d = Li % k;
+            if (a.mode == 1) {
+              float lo[kMaxK], hi[kMaxK];
+              for (int dd = 0; dd < k; ++dd) {
+                lo[dd] = s_box[dd];
+                hi[dd] = s_box[kMaxK + dd];
+              }
+              const uint32_t tt = (t << i) + u;  // index among depth-jj nodes of s0
+              for (uint32_t e = 0; e < jj; ++e) {
+                const uint32_t la = (1u << e) - 1 + (tt >> (jj - e));
+                const int da = s_ldim[la];
+                const float xv = s_lplane[la];
+                if (((tt >> (jj - 1 - e)) & 1u) == 0) hi[da] = xv; else lo[da] = xv;
+              }
+              d = widest_dim(lo, hi, k);
+            }
+            const uint16_t* list = s_lists + (size_t)slot[d] * kLocalCap;
+            if (!coop || lane == 0) {
+              const uint32_t o = s_orig[list[st + pr]];
+              a.perm[ls.off + node] = o;
+              if (a.mode == 1) {
+                s_ldim[loc0 + u] = (uint8_t)d;
+                s_lplane[loc0 + u] = coord_of(a.pts, o, a.stride, d);
+                a.dims[ls.off + node] = (uint8_t)d;
+              }
+            }
+            for (uint32_t q = coop ? (uint32_t)lane : 0u; q < sz; q += coop ? 32u : 1u)
+              s_side[list[st + q]] = q < pr ? 0 : (q == pr ? 2 : 1);
+          }
+          __syncwarp();
+          if (lowest) break;
+          const int depth_left = tree.L - 1 - (Li + 1);
           for (int dd = 0; dd < k; ++dd) {
-            lo[dd] = s_box[dd];
-            hi[dd] = s_box[kMaxK + dd];
-          }
-          for (int i = 0; i < j; ++i) {
-            const uint32_t la = (1u << i) - 1 + (t >> (j - i));
-            const int da = s_ldim[la];
-            const float xv = s_lplane[la];
-            if (((t >> (j - 1 - i)) & 1u) == 0) hi[da] = xv; else lo[da] = xv;
-          }
-          d = widest_dim(lo, hi, k);
-        }
-        const uint16_t* list = s_lists + (size_t)s_list_of[d] * kLocalCap;
-        if (per_thread || lane == 0) {
-          const uint32_t o = s_orig[list[st + pr]];
-          a.perm[ls.off + c0 + t] = o;
-          if (a.mode == 1) {
-            s_ldim[loc] = (uint8_t)d;
-            s_lplane[loc] = coord_of(a.pts, o, a.stride, d);
-            a.dims[ls.off + c0 + t] = (uint8_t)d;
-          }
-        }
-        for (uint32_t q = per_thread ? 0u : (uint32_t)lane; q < sz; q += per_thread ? 1u : 32u)
-          s_side[list[st + q]] = q < pr ? 0 : (q == pr ? 2 : 1);
-      }
-      __syncthreads();
-      if (lowest) break;
-      const uint32_t mn = mj - nn;
-      const int depth_left = tree.L - 1 - (L + 1);
-      for (int dd = 0; dd < k; ++dd) {
-        if (a.mode == 0) {
-          bool need = false;
-          for (int jj = 0; jj <= depth_left && !need; ++jj) need = ((L + 1 + jj) % k) == dd;
-          if (!need) continue;
-        }
-        const uint16_t* src = s_lists + (size_t)s_list_of[dd] * kLocalCap;
-        uint16_t* dst = s_lists + (size_t)s_list_of[k] * kLocalCap;
-        for (uint32_t t = own0; t < nn; t += ownstep) {
-          const uint32_t crel = first + t;
-          const uint32_t st = yj.seg_start(crel) - base;
-          const uint32_t sz = yj.seg_start(crel + 1) - yj.seg_start(crel);
-          const uint32_t pr = yj.left_size(crel);
-          const uint32_t nl = st - t, nr = st - t + pr;
-          uint32_t cl = 0, cr = 0;
-          if (per_thread) {
-            for (uint32_t q = 0; q < sz; ++q) {
-              const uint16_t it = src[st + q];
-              const uint8_t sd = s_side[it];
-              if (sd == 0) dst[nl + cl++] = it;
-              else if (sd == 1) dst[nr + cr++] = it;
+            if (a.mode == 0) {
+              bool need = false;
+              for (int q = 0; q <= depth_left && !need; ++q) need = ((Li + 1 + q) % k) == dd;
+              if (!need) continue;
             }
-            if (nl + cl > mn || nr + cr > mn) s_bad = 1;
-          } else {
-            for (uint32_t q0 = 0; q0 < sz; q0 += 32) {
-              const uint32_t q = q0 + lane;
-              uint16_t it = 0;
-              uint8_t sd = 3;
-              if (q < sz) {
-                it = src[st + q];
-                sd = s_side[it];
+            const uint16_t* src = s_lists + (size_t)slot[dd] * kLocalCap;
+            uint16_t* dst = s_lists + (size_t)slot[k] * kLocalCap;
+            for (uint32_t u = coop ? 0u : (uint32_t)lane; u < cnt; u += coop ? 1u : 32u) {
+              const uint32_t node = cf + u;
+              const uint32_t st = ta[u];
+              const uint32_t sz = subtree_size(tree, node);
+              const uint32_t pr = subtree_size(tree, 2 * node + 1);
+              uint32_t cl = 0, cr = 0;
+              if (coop) {
+                for (uint32_t q0 = 0; q0 < sz; q0 += 32) {
+                  const uint32_t q = q0 + lane;
+                  uint16_t it = 0;
+                  uint8_t sd = 3;
+                  if (q < sz) {
+                    it = src[st + q];
+                    sd = s_side[it];
+                  }
+                  const uint32_t bl = __ballot_sync(0xffffffffu, sd == 0);
+                  const uint32_t br = __ballot_sync(0xffffffffu, sd == 1);
+                  if (sd == 0) dst[st + cl + __popc(bl & lt)] = it;
+                  if (sd == 1) dst[st + pr + 1 + cr + __popc(br & lt)] = it;
+                  cl += __popc(bl);
+                  cr += __popc(br);
+                }
+              } else {
+                for (uint32_t q = 0; q < sz; ++q) {
+                  const uint16_t it = src[st + q];
+                  const uint8_t sd = s_side[it];
+                  if (sd == 0) dst[st + cl++] = it;
+                  else if (sd == 1) dst[st + pr + 1 + cr++] = it;
+                }
               }
-              const uint32_t bl = __ballot_sync(0xffffffffu, sd == 0);
-              const uint32_t br = __ballot_sync(0xffffffffu, sd == 1);
-              uint32_t np = 0xFFFFFFFFu;
-              if (sd == 0) np = nl + cl + __popc(bl & lt);
-              if (sd == 1) np = nr + cr + __popc(br & lt);
-              if (sd <= 1) {
-                if (np < mn) dst[np] = it;
-                else s_bad = 1;
-              }
-              cl += __popc(bl);
-              cr += __popc(br);
             }
+            __syncwarp();
+            const int t2 = slot[dd];
+            slot[dd] = slot[k];
+            slot[k] = t2;
           }
+          // children's ranges: left starts where the node starts, right after the pivot
+          for (uint32_t u = lane; u < cnt; u += 32) {
+            const uint32_t st = ta[u];
+            const uint32_t pr = subtree_size(tree, 2 * (cf + u) + 1);
+            tb2[2 * u] = (uint16_t)st;
+            tb2[2 * u + 1] = (uint16_t)(st + pr + 1);
+          }
+          __syncwarp();
+          uint16_t* tt2 = ta;
+          ta = tb2;
+          tb2 = tt2;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          const int t2 = s_list_of[dd];
-          s_list_of[dd] = s_list_of[k];
-          s_list_of[k] = t2;
-        }
-        __syncthreads();
       }
-      mj = mn;
-      continue;
+      break;
     }
     // per node: segment start, pivot rank, lefts before it
     for (uint32_t t = threadIdx.x; t < nn; t += T) {

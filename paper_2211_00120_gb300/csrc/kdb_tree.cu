@@ -95,12 +95,14 @@ __global__ void __launch_bounds__(kThreads) prepass_kernel(PrepassArgs a) {
     }
     have = have || ok;
     const unsigned char* rec = a.pts + (uint64_t)i * (uint32_t)a.stride;
+    uint32_t ek[3] = {0u, 0u, 0u};
     for (int d = 0; d < a.k; ++d) {
       uint32_t key = 0;
       if (ok) {
         const uint32_t bits = *reinterpret_cast<const uint32_t*>(rec + 4 * d);
         if ((bits & 0x7FFFFFFFu) > 0x7F800000u) nan = true;
         key = float_key(bits);
+        if (d < 3) ek[d] = key;
         lo[d] = min(lo[d], key);
         hi[d] = max(hi[d], key);
         if (a.keys32) a.keys32[(uint64_t)d * a.kstride + i] = key;
@@ -122,6 +124,7 @@ __global__ void __launch_bounds__(kThreads) prepass_kernel(PrepassArgs a) {
         }
       }
     }
+    if (a.ents && ok) a.ents[i] = make_uint4(ek[0], ek[1], ek[2], i);
   }
   if (a.bbox) {
     // warp-combine when the whole warp ended in one set, else per thread
