@@ -27,7 +27,7 @@ struct PassCtl;
 // Presorted-list levels (kdb_part.cu), k <= 3: one 16-byte entry per point
 // (order-preserving keys of coordinates 0..2, original index), one list per
 // dimension.
-constexpr int kPartThreads = 256;
+constexpr int kPartThreads = 128;
 constexpr int kPartItems = 15;
 constexpr int kPartTile = kPartThreads * kPartItems;  // < 2^13 - 1: <= two segments a tile
 constexpr int kRecThreads = 256;

@@ -381,7 +381,7 @@ __device__ inline bool warp_look_back(const PartArgs& a, uint32_t tile, uint32_t
   }
 }
 
-__global__ void __launch_bounds__(PT, 3) partition_kernel(PartArgs a) {
+__global__ void __launch_bounds__(PT, 6) partition_kernel(PartArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint4* s_in = reinterpret_cast<uint4*>(smem_raw);
   __shared__ __align__(8) uint64_t s_bar;
