@@ -16,6 +16,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -47,15 +48,30 @@ WORKLOADS = {
 BYTES_PER_ITEM = {"partition_pass": 32.0, "radix_pass": 16.0}
 
 
-def kernel_hash() -> str:
-    """Hash of every CUDA source: a stored ncu traffic figure is only reused
-    while the kernels are exactly the ones it was measured on."""
-    h = hashlib.sha256()
+# the source file that defines each kernel kind of the k <= 3 path
+KIND_SOURCE = {"partition_pass": "kdb_part.cu", "radix_pass": "kdb_lists.cu",
+               "pivots": "kdb_part.cu", "build_lists": "kdb_lists.cu",
+               "local_finish": "kdb_local.cu", "placement": "kdb_tree.cu",
+               "prepass": "kdb_tree.cu"}
+
+
+def kernel_hash(kind: str) -> str:
+    """Hash of the source file defining kernel kind `kind` and every header it
+    includes: a stored ncu traffic figure is only reused while that kernel is
+    exactly the one it was measured on."""
     d = os.path.join(ROOT, "paper_2211_00120_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    h = hashlib.sha256()
+    todo, seen = [KIND_SOURCE.get(kind, "")], set()
+    while todo:
+        f = todo.pop()
+        if f in seen or not os.path.isfile(os.path.join(d, f)):
+            continue
+        seen.add(f)
         with open(os.path.join(d, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
-    return h.hexdigest()[:16]
+            text = fh.read()
+        h.update(f.encode() + text)
+        todo += re.findall(r'#include "([^"/]+)"', text.decode())
+    return h.hexdigest()[:16] if seen else ""
 
 
 def measured_peak():
@@ -79,7 +95,7 @@ def traffic_per_launch(kind: str, n_items_per_launch: float):
             j = json.load(f)
     except Exception:
         return None
-    if j.get("kernel_hash") != kernel_hash():
+    if not j.get("kernel_hash") or j["kernel_hash"] != kernel_hash(kind):
         return None
     return j["dram_bytes_per_item"] * n_items_per_launch
 

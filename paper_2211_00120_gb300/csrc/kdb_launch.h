@@ -30,8 +30,6 @@ struct PassCtl;
 constexpr int kPartThreads = 128;
 constexpr int kPartItems = 15;
 constexpr int kPartTile = kPartThreads * kPartItems;  // < 2^13 - 1: <= two segments a tile
-constexpr int kRecThreads = 256;
-constexpr int kRecItems = 15;
 struct ListBuildArgs {      // level-0 array of several sets
   LevelCtx x;               // level 0
   uint32_t items;

@@ -1,0 +1,284 @@
+// kdb_lists.cu -- the level-0 sorted lists of the k <= 3 path.
+//
+// Every point is carried as a 16-byte entry: the order-preserving keys of its
+// coordinates in dimensions 0..2 and its original index.  Comparing entries by
+// (key_d, original index) is the paper's less() in dimension d (Sec. 3.1)
+// with the tie rule.
+//
+// For every dimension d, list d is a stable LSD radix sort of the entries by
+// key_d (4 passes of 8-bit digits, each a segmented onesweep pass over 16-byte
+// records, one segment per set) starting from input order, which leaves list d
+// sorted by (key_d, original index): the order the level-0 sort produces when
+// d is the root's split dimension.
+#include "kdb_launch.h"
+#include "kdb_segsort.cuh"
+
+namespace kdb {
+namespace {
+
+__device__ inline uint32_t comp(const uint4& e, int d) {
+  return d == 0 ? e.x : (d == 1 ? e.y : e.z);
+}
+// ---------------------------------------------------------------------------
+// Level-0 array of several sets: the entries of the sets that run global
+// levels, back to back (a single set uses the input entries directly).
+__global__ void gather_level0_kernel(ListBuildArgs a) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.items) return;
+  if (*reinterpret_cast<volatile uint32_t*>(a.x.err)) return;
+  const uint32_t ai = a.x.nact > 1 ? find_active_entry(a.x.act, a.x.nact, j) : 0;
+  const ActiveEntry e = a.x.act[ai];
+  const uint32_t src = a.x.sets[e.set].off + (j - e.base);
+  if (src >= a.total) {
+    atomicOr(a.x.err, ERR_INTERNAL);
+    return;
+  }
+  a.out[j] = a.ents[src];
+}
+
+// Digit histograms of every (dimension, pass, segment) of the level-0 array;
+// one block per chunk of one segment (a set).
+__global__ void __launch_bounds__(256) rec_hist_kernel(RecHistArgs a) {
+  __shared__ uint32_t s_hist[3 * 4 * kRadixBins];
+  if (*reinterpret_cast<volatile uint32_t*>(a.x.err)) return;
+  const LevelCtx& x = a.x;
+  const uint32_t g = blockIdx.x;
+  uint32_t ai = 0;
+  {
+    uint32_t lo = 0, hi = x.nact;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (x.act[mid].chunk0 <= g) lo = mid; else hi = mid;
+    }
+    ai = lo;
+  }
+  const ActiveEntry e = x.act[ai];
+  const uint32_t n = x.sets[e.set].n;  // level 0: the whole set is one segment
+  const uint32_t beg = e.base + (g - e.chunk0) * kSegChunk;
+  const uint32_t end = min(e.base + n, beg + kSegChunk);
+  if (beg >= end) return;
+  const int H = a.k * 4 * kRadixBins;
+  for (int i = threadIdx.x; i < H; i += blockDim.x) s_hist[i] = 0;
+  __syncthreads();
+  for (uint32_t j = beg + threadIdx.x; j < end; j += blockDim.x) {
+    const uint4 en = a.ents[j];
+    for (int d = 0; d < a.k; ++d) {
+      const uint32_t key = comp(en, d);
+      for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[(d * 4 + p) * kRadixBins + ((key >> (8 * p)) & 255u)], 1u);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < H; i += blockDim.x) {
+    const uint32_t v = s_hist[i];
+    if (v) {
+      const int dp = i / kRadixBins, dg = i % kRadixBins;  // dp = d * 4 + p
+      atomicAdd(a.hist + ((uint64_t)dp * a.nseg + ai) * kRadixBins + dg, v);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One stable LSD pass over 16-byte entries by digit (key_d >> shift) & 255,
+// every set its own segment.  The tile's records are staged by bulk copy; only
+// their slot order is staged for the write-out, which reads the records from
+// shared memory in digit order and writes each digit's run contiguously.
+constexpr int RT = 256;  // threads of a record-sort block
+constexpr int RI = 15;   // entries per thread
+constexpr int RTILE = RT * RI;
+constexpr int RW = RT / 32;
+
+__global__ void __launch_bounds__(RT, 2)
+    rec_sort_pass(const uint4* __restrict__ in, uint4* __restrict__ out, PassCtl c, LevelCtx x,
+                  const uint32_t* __restrict__ seg_hist, int d) {
+  constexpr int BINS = 2 * kRadix;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint4* s_rec = reinterpret_cast<uint4*>(smem_raw);
+  uint16_t* s_slot = reinterpret_cast<uint16_t*>(s_rec + RTILE);
+  uint16_t* s_whist = s_slot + RTILE;  // [BINS][RW]
+  __shared__ uint32_t s_gbase[BINS];
+  __shared__ uint32_t s_toff[BINS];
+  __shared__ uint64_t s_scan64[RW];
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ uint32_t s_tile, s_abort, s_totA;
+  __shared__ TileSegs s_ts;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    s_abort = *reinterpret_cast<volatile uint32_t*>(c.err) != 0u;
+    if (!s_abort) {
+      const uint32_t tile = atomicAdd(c.ticket, 1u);
+      s_tile = tile;
+      const uint32_t tb = tile * (uint32_t)RTILE;
+      const uint32_t tn = c.n - tb < (uint32_t)RTILE ? c.n - tb : (uint32_t)RTILE;
+      mbar_init(&s_bar, 1);
+      mbar_expect_tx(&s_bar, tn * 16u);
+      bulk_g2s(s_rec, in + tb, tn * 16u, &s_bar);
+      uint32_t a, sr, st, en;
+      segment_at(x, tb, &a, &sr, &st, &en);
+      s_ts.ai[0] = a;
+      s_ts.srel[0] = sr;
+      s_ts.start[0] = st;
+      s_ts.gid[0] = a;  // level 0: one segment per set
+      s_ts.bpos = tn;
+      if (en < tb + tn) {
+        uint32_t a2, s2, st2, en2;
+        segment_at(x, en, &a2, &s2, &st2, &en2);
+        s_ts.ai[1] = a2;
+        s_ts.srel[1] = s2;
+        s_ts.start[1] = st2;
+        s_ts.gid[1] = a2;
+        s_ts.bpos = en - tb;
+        if (en2 < tb + tn) s_abort = 2;
+      } else {
+        s_ts.ai[1] = a;
+        s_ts.srel[1] = sr;
+        s_ts.start[1] = st;
+        s_ts.gid[1] = a;
+      }
+    }
+  }
+  for (int i = tid; i < BINS * RW / 2; i += RT) reinterpret_cast<uint32_t*>(s_whist)[i] = 0;
+  __syncthreads();
+  if (s_abort == 1) return;
+  if (s_abort == 2 && tid == 0) atomicOr(c.err, ERR_INTERNAL);
+  const uint32_t tile = s_tile;
+  const uint32_t tb = tile * (uint32_t)RTILE;
+  const uint32_t tn = c.n - tb < (uint32_t)RTILE ? c.n - tb : (uint32_t)RTILE;
+  {
+    bool waiting = false, late = false;
+    uint64_t t0 = 0;
+    while (!mbar_try_wait(&s_bar, 0)) {
+      const uint64_t now = global_timer_ns();
+      if (!waiting) {
+        waiting = true;
+        t0 = now;
+      } else if (now - t0 > (late ? 2 : 1) * kCopyWaitNs) {
+        if (late) break;
+        late = true;
+        atomicOr(c.err, ERR_TIMEOUT);
+      }
+    }
+    if (late) s_abort = 1;
+  }
+  __syncthreads();
+  if (s_abort == 1) return;
+  const uint32_t bpos = s_ts.bpos;
+  const bool hasB = bpos < tn;
+  const bool a_cont = s_ts.start[0] < tb;
+  const uint32_t wbase = (uint32_t)warp * 32 * RI;
+  const uint32_t lt = (1u << lane) - 1u;
+
+  uint16_t bins[RI];
+  uint16_t rnk[RI];
+#pragma unroll
+  for (int i = 0; i < RI; ++i) {
+    const uint32_t p = wbase + i * 32 + lane;
+    const bool ok = p < tn;
+    uint32_t bin = BINS;
+    if (ok) bin = ((p >= bpos) ? (uint32_t)kRadix : 0u) | ((comp(s_rec[p], d) >> c.shift) & 255u);
+    const uint32_t peers = __match_any_sync(0xffffffffu, bin);
+    uint32_t before = 0;
+    if (ok) before = s_whist[bin * RW + warp];
+    __syncwarp();
+    rnk[i] = (uint16_t)(before + __popc(peers & lt));
+    if (ok && (peers & lt) == 0) s_whist[bin * RW + warp] = (uint16_t)(before + __popc(peers));
+    bins[i] = (uint16_t)bin;
+    __syncwarp();
+  }
+  __syncthreads();
+  uint32_t cA = 0, cB = 0;
+  if (tid < kRadix) {
+#pragma unroll
+    for (int w = 0; w < RW; ++w) {
+      const uint32_t ta = s_whist[tid * RW + w], tb2 = s_whist[(kRadix + tid) * RW + w];
+      s_whist[tid * RW + w] = (uint16_t)cA;
+      s_whist[(kRadix + tid) * RW + w] = (uint16_t)cB;
+      cA += ta;
+      cB += tb2;
+    }
+    uint64_t* mine = c.status + (uint64_t)tile * kRadix + tid;
+    if (hasB || !a_cont) st_relaxed_u64(mine, lb_pack(kFlagPre, c.epoch, hasB ? cB : cA));
+    else st_relaxed_u64(mine, lb_pack(kFlagAgg, c.epoch, cA));
+  }
+  uint32_t hA = 0, hB = 0;
+  if (tid < kRadix) {
+    hA = seg_hist[(uint64_t)s_ts.gid[0] * kRadix + tid];
+    hB = hasB ? seg_hist[(uint64_t)s_ts.gid[1] * kRadix + tid] : 0u;
+  }
+  const uint64_t tsc = block_excl_scan64<RT>((uint64_t)cA | ((uint64_t)cB << 32), s_scan64);
+  const uint64_t hsc = block_excl_scan64<RT>((uint64_t)hA | ((uint64_t)hB << 32), s_scan64);
+  if (tid == kRadix - 1) s_totA = (uint32_t)tsc + cA;
+  __syncthreads();
+  uint32_t toffA = 0, toffB = 0;
+  if (tid < kRadix) {
+    toffA = (uint32_t)tsc;
+    toffB = (uint32_t)(tsc >> 32) + s_totA;
+    s_toff[tid] = toffA;
+    s_toff[kRadix + tid] = toffB;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < RI; ++i) {
+    const uint32_t p = wbase + i * 32 + lane;
+    if (p < tn) {
+      const uint32_t bin = bins[i];
+      s_slot[s_toff[bin] + s_whist[bin * RW + warp] + rnk[i]] = (uint16_t)p;
+    }
+  }
+  if (tid < kRadix) {
+    uint32_t prefA = 0;
+    if (a_cont && s_abort == 0) {
+      if (!look_back<16>(c, tile, tid, &prefA)) {
+        atomicOr(c.err, ERR_TIMEOUT);
+        s_abort = 1;
+      }
+      if (!hasB) st_relaxed_u64(c.status + (uint64_t)tile * kRadix + tid,
+                                lb_pack(kFlagPre, c.epoch, prefA + cA));
+    }
+    s_gbase[tid] = s_ts.start[0] + (uint32_t)hsc + prefA - toffA;
+    s_gbase[kRadix + tid] = s_ts.start[1] + (uint32_t)(hsc >> 32) - toffB;
+  }
+  __syncthreads();
+  if (s_abort) return;
+  const uint32_t totA = s_totA;
+  for (uint32_t sl = tid; sl < tn; sl += RT) {
+    const uint4 rec = s_rec[s_slot[sl]];
+    const uint32_t bin = (sl >= totA ? (uint32_t)kRadix : 0u) | ((comp(rec, d) >> c.shift) & 255u);
+    const uint32_t dest = s_gbase[bin] + sl;
+    if (dest >= c.n) {
+      atomicOr(c.err, ERR_INTERNAL);
+      continue;
+    }
+    out[dest] = rec;
+  }
+}
+
+}  // namespace
+
+size_t rec_sort_smem() { return (size_t)RTILE * 18 + (size_t)2 * kRadix * RW * 2; }
+
+cudaError_t launch_gather_level0(const ListBuildArgs& a, cudaStream_t st) {
+  if (a.items == 0) return cudaSuccess;
+  gather_level0_kernel<<<(a.items + 255) / 256, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rec_hist(const RecHistArgs& a, cudaStream_t st) {
+  if (a.chunks == 0) return cudaSuccess;
+  rec_hist_kernel<<<a.chunks, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rec_sort_pass(const uint4* in, uint4* out, const PassCtl& c, const LevelCtx& x,
+                                 const uint32_t* seg_hist, int d, cudaStream_t st) {
+  if (c.n == 0) return cudaSuccess;
+  const size_t smem = rec_sort_smem();
+  cudaError_t e =
+      cudaFuncSetAttribute(rec_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const uint32_t tiles = (c.n + RTILE - 1) / RTILE;
+  rec_sort_pass<<<tiles, RT, smem, st>>>(in, out, c, x, seg_hist, d);
+  return cudaGetLastError();
+}
+
+}  // namespace kdb
