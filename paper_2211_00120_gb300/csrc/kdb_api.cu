@@ -196,7 +196,7 @@ struct Plan {
   size_t o_vloc, o_lbox, o_lsets, o_work, o_whole;
   // presorted lists (k <= 3): one list of 16-byte entries per dimension
   bool use_lists = false;
-  size_t o_rows, o_lists, o_ents, o_piv, o_l0;
+  size_t o_rows, o_lists, o_lorig, o_piv, o_l0;
   size_t rec_hist_off = 0;  // record-sort histograms (in u32, inside the histogram area)
   uint32_t max_nseg = 0;
   uint64_t kstride = 0;  // elements between two dimensions' coordinate keys
@@ -371,7 +371,7 @@ void make_plan(Plan& P) {
   const bool L = P.use_lists, G = L && levels > 0;  // G: there are global levels
   P.o_rows = take(L ? T * 16 : 0);                   // entries in input order
   P.o_lists = take(G ? T * 16 * 2 * P.k : 0);        // per dimension, double-buffered
-  P.o_ents = take(G ? T * 16 : 0);                   // entries handed to the local finish
+  P.o_lorig = take(G ? T * 4 * P.k : 0);             // lists handed to the local finish
   P.o_piv = take(L ? (size_t)std::max<uint32_t>(P.max_nseg, 1) * 8 : 0);
   P.o_l0 = take(G && P.sets.size() > 1 ? T * 16 : 0);  // level-0 array of several sets
   P.bytes = o;
@@ -593,7 +593,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   const uint32_t* vals_cur = nullptr;  // level 0: original order
   uint4* lcur[3] = {nullptr, nullptr, nullptr};
   uint4* lnext[3] = {nullptr, nullptr, nullptr};
-  uint4* ents_local = at<uint4>(ws, P.o_ents);
+  uint32_t* lorig = at<uint32_t>(ws, P.o_lorig);
   uint2* piv = at<uint2>(ws, P.o_piv);
   if (P.use_lists) {
     for (int d = 0; d < k; ++d) {
@@ -633,11 +633,11 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
         Prof pf(K_LISTS, (double)n0 * 16, 1, st);
         KDB_CK(launch_rec_hist(rh, st));
       }
-      uint4* tmp[2] = {lnext[0], ents_local};  // free until the level loop uses them
       for (int d = 0; d < k; ++d) {
         const uint4* in = l0;
         for (int p = 0; p < 4; ++p) {
-          uint4* out = p == 3 ? lcur[d] : tmp[p & 1];
+          // ping-pong between the dimension's two list buffers, ending in lcur
+          uint4* out = (p & 1) ? lcur[d] : lnext[d];
           PassCtl c = ctl(n0, 8 * p, nullptr);
           const uint32_t* sh = rh.hist + ((size_t)(d * 4 + p) * x0.nact) * kRadixBins;
           Prof pf(K_RADIX, (double)n0 * 32, 1, st);
@@ -676,20 +676,14 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
         Prof pf(K_PIVOT, (double)(x.nact << l) * 20, 1, st);
         KDB_CK(launch_pivots(pv, st));
       }
-      bool all_leave = true;  // every set goes to the local finish after this level
-      for (const ActiveEntry& e : P.act[l]) all_leave = all_leave && e.next < 0;
       const uint32_t next_items = l + 1 < levels ? P.items[l + 1] : 0;
       for (int d = 0; d < k; ++d) {
-        if (all_leave && P.mode == 0 && d != l % k) {
-          ++g;  // keep the ticket / epoch numbering of the plan
-          continue;
-        }
         PassCtl c = ctl(n, 0, nullptr);
         PartArgs pa2{};
         pa2.x = x;
         pa2.in = lcur[d];
         pa2.out_next = lnext[d];
-        pa2.out_local = ents_local;
+        pa2.out_lorig = lorig;
         pa2.piv = piv;
         pa2.dims = dims;
         pa2.k = k;
@@ -817,7 +811,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     la.nwork = (uint32_t)P.work.size();
     la.lsets = d_lsets;
     la.vals_local = vals_local;
-    la.ents_local = P.use_lists ? ents_local : nullptr;
+    la.lorig = P.use_lists ? lorig : nullptr;
     la.rows = P.use_lists ? ents0 : nullptr;
     la.ranks = P.use_lists ? nullptr : ranks;
     la.total = T;

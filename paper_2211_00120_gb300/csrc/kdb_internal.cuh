@@ -119,6 +119,18 @@ struct LevelLayout {
     const uint64_t low = lowest >= m ? 0 : (m - lowest < w ? m - lowest : w);
     return (uint32_t)((w - 1) + low);
   }
+  // sum of left_size(u) over u < x (h >= 1): every left child holds w - 1
+  // upper nodes plus its share of the lowest level, which fills left to right
+  __host__ __device__ uint32_t left_before(uint32_t x) const {
+    const uint64_t w = 1ull << (h - 1);
+    const uint64_t full = (uint64_t)m >> h;  // left children whose part of the lowest level is full
+    uint64_t low = (x < full ? x : full) * w;
+    if (x > full) {
+      const uint64_t rest = (uint64_t)m - 2 * w * full;
+      low += rest < w ? rest : w;
+    }
+    return (uint32_t)((uint64_t)x * (w - 1) + low);
+  }
 };
 
 // Order-preserving map float32 -> uint32: unsigned order of the result is the

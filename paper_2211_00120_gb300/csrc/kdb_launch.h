@@ -58,7 +58,8 @@ struct PartArgs {
   LevelCtx x;
   const uint4* in;          // this level's list sorted by dimension dlist
   uint4* out_next;          // next level's list
-  uint4* out_local;         // entries for the local finish (sets leaving)
+  uint32_t* out_lorig;      // original indices for the local finish (sets leaving),
+                            // one array of `total` per list
   const uint2* piv;
   const uint8_t* dims;
   int k, mode, dlist;
@@ -97,7 +98,8 @@ struct LocalArgs {
   uint32_t nwork;
   const LocalSet* lsets;
   const uint32_t* vals_local;   // original indices (rank arrays gathered), or
-  const uint4* ents_local;      // entries (k <= 3): coordinate keys and original index
+  const uint32_t* lorig;        // k <= 3: per dimension the original indices of the
+                                // items leaving the global levels, in list order
   const uint4* rows;            // entries in input order (sets local from level 0)
   const uint32_t* ranks;
   uint32_t total;

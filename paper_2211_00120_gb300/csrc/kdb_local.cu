@@ -6,16 +6,21 @@
 //
 // Inside the block, each level still performs the paper's step: order every
 // sub-segment by (tag, coordinate) (Sec. 3.1) and apply the tag update
-// (Sec. 3.2).  The order is kept as k lists, one per dimension, each holding
-// the block's points sorted by (sub-segment, rank in that dimension).  For a
-// level with split dimension d, the list of d *is* the sorted order the tag
-// update needs: in sub-segment t the point at rank ss(lChild) is pinned
-// (Observation 1), lower ranks go left, higher ranks right.  Every list is
-// then partitioned stably by that outcome, which leaves each child's points
-// sorted by (child, rank) -- the next level's sort order -- without sorting
-// again.  The lists are built once: the list of the parent's dimension comes
-// in order (the items arrive sorted by it), the others are radix-sorted in
-// shared memory.
+// (Sec. 3.2).  The order is kept as k lists of local ids, one per dimension,
+// each sorted by (sub-segment, key_d, original index).  For a level with split
+// dimension d, the list of d *is* the sorted order the tag update needs: in
+// sub-segment t the point at rank ss(lChild) is pinned (Observation 1), lower
+// ranks go left, higher ranks right.  One pass over that list writes, per
+// point, its side and the closed-form start of its run on the next level (the
+// sub-segment sizes of Sec. 4); every list is then partitioned stably by side
+// with warp ballots, which leaves each child's points sorted by (child, key,
+// index) -- the next level's sort order -- without sorting again.  Once a
+// depth has at least 32 sub-segments, each warp finishes its own subtrees
+// without block barriers.
+//
+// The lists arrive from the global passes already in order (as original
+// indices); a set small enough to start here builds them from its entries by
+// radix sorts in shared memory.
 #include "kdb_launch.h"
 
 namespace kdb {
@@ -23,13 +28,13 @@ namespace {
 
 constexpr int T = kLocalThreads;
 constexpr int W = T / 32;
-// nodes per level of a subtree finished by one warp (see the warp phase)
-constexpr int kWarpTab = 1 << (kLocalLog - 1 - 5);
 static_assert(W == 32, "the warp phase starts at the first depth with >= 32 subtrees");
-// level-phase scratch: side + 3 node tables + dims + planes + warp tables
-static_assert(kLocalCap + 3 * 2 * (kLocalCap / 2 + 8) + kLocalCap + 4 * kLocalCap +
-                      W * 2 * kWarpTab * 2 <= 12 * kLocalCap,
-              "level-phase scratch fits the sort area");
+// scratch area (12 bytes per item): the setup's sort buffers (4 + 4 + 2 + 2)
+// or hash table (2 slots per item of 4 + 2 bytes); the levels' info words,
+// split dimensions and planes (2 + 1 + 4)
+static_assert(2 * kLocalCap * 4 + 2 * kLocalCap * 2 <= 12 * kLocalCap, "hash table fits");
+static_assert(kLocalCap * (2 + 1 + 4) <= 12 * kLocalCap, "level scratch fits");
+static_assert(kLocalCap <= (1 << 14), "info words hold 14-bit offsets");
 
 __device__ inline int widest_dim(const float* lo, const float* hi, int k) {
   int best = 0;
@@ -159,11 +164,77 @@ __device__ uint16_t* smem_radix_sort(uint32_t* ka, uint16_t* ia, uint32_t* kb, u
   return ia;
 }
 
+// Slot of list d among the k + 1 list buffers, packed 4 bits per dimension
+// (the last one is the spare that receives a partition).
+__device__ inline int slot_of(uint32_t slots, int d) { return (int)((slots >> (4 * d)) & 15u); }
+__device__ inline uint32_t swap_slots(uint32_t slots, int d, int k) {
+  const uint32_t a = (slots >> (4 * d)) & 15u, b = (slots >> (4 * k)) & 15u;
+  slots &= ~((15u << (4 * d)) | (15u << (4 * k)));
+  return slots | (b << (4 * d)) | (a << (4 * k));
+}
+
+// Segments [f, f + cnt) of one level of the set's tree (relative indices on
+// that level), handled by one thread group.  Positions are local: position 0
+// is the first item of the block's own subtree on this level.
+struct Range {
+  LevelLayout y;
+  uint32_t tfirst;  // first segment of the block's subtree on this level
+  uint32_t base;    // y.seg_start(tfirst)
+  uint32_t f;       // first segment of the range
+  uint32_t p0, p1;  // local positions of the range's items
+  uint32_t lb0;     // y.left_before(f)
+  uint32_t nb;      // local position of the range's first item on the next level
+};
+
+__device__ inline Range make_range(const LevelLayout& y, uint32_t tfirst, uint32_t f, uint32_t cnt) {
+  Range r;
+  r.y = y;
+  r.tfirst = tfirst;
+  r.base = y.seg_start(tfirst);
+  r.f = f;
+  r.p0 = y.seg_start(f) - r.base;
+  r.p1 = y.seg_start(f + cnt) - r.base;
+  r.lb0 = y.h >= 1 ? y.left_before(f) : 0u;
+  // the next level holds every item of this level but the pinned ones, in
+  // segment order: items before the range's first child = items before f
+  // minus the f pivots above them
+  r.nb = (y.seg_start(f) - f) - (r.base - tfirst);
+  return r;
+}
+
+// Tag update of the item at local position p (Sec. 3.2 with Observation 1):
+// in its segment t it is left of the pivot (side 0), the pivot (2) or right
+// (1).  Returns the item's position on the next level minus its rank among
+// the range's items of the same side: left items of the range go, in list
+// order, after the right items of the range's earlier segments; right items
+// after the left items of the earlier segments and of t itself.
+__device__ inline uint32_t classify(const Range& r, uint32_t p, uint32_t* t_out, uint32_t* side) {
+  const uint32_t t = r.y.seg_of(r.base + p);
+  const uint32_t st = r.y.seg_start(t) - r.base;
+  const uint32_t q = p - st;
+  uint32_t pr = 0, sl = 0;
+  if (r.y.h >= 1) {
+    pr = r.y.left_size(t);
+    sl = r.y.left_before(t) - r.lb0;
+  }
+  const uint32_t sr = (st - r.p0) - (t - r.f) - sl;
+  *t_out = t;
+  if (q < pr) {
+    *side = 0;
+    return r.nb + sr;
+  }
+  if (q == pr) {
+    *side = 2;
+    return 0;
+  }
+  *side = 1;
+  return r.nb + sl + pr;
+}
+
 __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ uint32_t s_w[W];
   __shared__ float s_box[2 * kMaxK];
-  __shared__ int s_list_of[kMaxK + 1];  // physical list slot of each dimension, + spare
   __shared__ uint32_t s_bad;
   if (*reinterpret_cast<volatile uint32_t*>(a.err)) return;
   const int k = a.k;
@@ -172,18 +243,17 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
   uint32_t* s_orig = reinterpret_cast<uint32_t*>(sm);                      // kLocalCap
   uint16_t* s_lists = reinterpret_cast<uint16_t*>(s_orig + kLocalCap);     // (k+1) * cap
   unsigned char* s_area = reinterpret_cast<unsigned char*>(s_lists + (size_t)(k + 1) * kLocalCap);
-  // sort phase view of the scratch area
+  // setup view of the scratch area: radix sort buffers, or the hash table
   uint32_t* s_ka = reinterpret_cast<uint32_t*>(s_area);
   uint32_t* s_kb = s_ka + kLocalCap;
   uint16_t* s_ia = reinterpret_cast<uint16_t*>(s_kb + kLocalCap);
   uint16_t* s_ib = s_ia + kLocalCap;
-  // level phase view of the scratch area
-  uint8_t* s_side = s_area;                                                  // cap
-  uint16_t* s_tstart = reinterpret_cast<uint16_t*>(s_area + kLocalCap);      // cap/2 + 1
-  uint16_t* s_tpr = s_tstart + kLocalCap / 2 + 8;                            // cap/2
-  uint16_t* s_tpl = s_tpr + kLocalCap / 2 + 8;                               // cap/2
-  uint8_t* s_ldim = reinterpret_cast<uint8_t*>(s_tpl + kLocalCap / 2 + 8);   // cap
-  float* s_lplane = reinterpret_cast<float*>(s_ldim + kLocalCap);            // cap
+  uint32_t* s_hkey = reinterpret_cast<uint32_t*>(s_area);                  // 2 * cap
+  uint16_t* s_hval = reinterpret_cast<uint16_t*>(s_hkey + 2 * kLocalCap);  // 2 * cap
+  // level view of the scratch area
+  uint16_t* s_info = reinterpret_cast<uint16_t*>(s_area);                  // cap
+  uint8_t* s_ldim = reinterpret_cast<uint8_t*>(s_info + kLocalCap);        // cap
+  float* s_lplane = reinterpret_cast<float*>(s_ldim + kLocalCap);          // cap
 
   const LocalWork wk = a.work[blockIdx.x];
   const LocalSet ls = a.lsets[wk.set];
@@ -199,107 +269,130 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     return;
   }
   if (threadIdx.x == 0) s_bad = 0;
-  // entries (k <= 3) carry every rank; otherwise ranks are gathered
-  const uint4* ents = nullptr;
-  if (a.ents_local) ents = l0 > 0 ? a.ents_local + ls.off + start0 : a.rows + ls.off;
-  for (uint32_t i = threadIdx.x; i < m; i += T)
-    s_orig[i] = ents ? ents[i].w : (l0 > 0 ? a.vals_local[ls.off + start0 + i] : ls.off + i);
-  if (threadIdx.x <= (unsigned)k) s_list_of[threadIdx.x] = threadIdx.x;
   __syncthreads();
 
-  // dimension the items arrive sorted by: the parent's split dimension
-  int dpar = -1;
+  // ---- the k lists: local ids 0..m-1 ordered by (key_d, original index)
+  int dpar = -1;  // dimension the items arrive sorted by (the parent's split)
   if (l0 > 0) dpar = a.mode == 0 ? (l0 - 1) % k : a.dims[ls.off + (s0 - 1) / 2];
-  // the spare list slot holds the radix counters while the lists are built
-  uint16_t* s_wh = s_lists + (size_t)k * kLocalCap;
-  if (ents) {
-    // Lists ordered by (key_d, original index).  The items arrive ordered so
-    // in the parent's split dimension (on a set's level 0: by index).  For
-    // the other dimensions the items are put in index order once, then
-    // sorted stably by key from that order.
-    int todo[kMaxK];
-    int nt = 0;
-    for (int d = 0; d < k; ++d)
-      if (d != dpar) todo[nt++] = d;
-    if (dpar >= 0) {
-      uint16_t* list = s_lists + (size_t)dpar * kLocalCap;
-      for (uint32_t i = threadIdx.x; i < m; i += T) list[i] = (uint16_t)i;
+  uint16_t* s_wh = s_lists + (size_t)k * kLocalCap;  // radix counters (spare list slot)
+  if (a.lorig && l0 > 0) {
+    // The global passes hand over every list of the subtree as original
+    // indices, already in order.  Local id = position in list 0; the other
+    // lists are translated through a hash table original index -> local id.
+    const uint32_t* lo0 = a.lorig + ls.off + start0;
+    constexpr uint32_t HM = 2 * kLocalCap - 1;
+    for (uint32_t i = threadIdx.x; i < 2 * kLocalCap; i += T) s_hkey[i] = 0xFFFFFFFFu;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < m; i += T) {
+      uint32_t o = lo0[i];
+      if (o >= a.total) {
+        s_bad = 1;
+        o = 0;
+      }
+      s_orig[i] = o;
+      s_lists[i] = (uint16_t)i;
+      uint32_t h = (o * 0x9E3779B1u) >> (32 - (kLocalLog + 1));
+      bool done = false;
+      for (uint32_t probe = 0; probe <= HM && !done; ++probe) {
+        const uint32_t prev = atomicCAS(&s_hkey[h], 0xFFFFFFFFu, o);
+        if (prev == 0xFFFFFFFFu) {
+          s_hval[h] = (uint16_t)i;
+          done = true;
+        } else if (prev == o) {
+          break;  // an original index twice: corrupt input lists
+        }
+        h = (h + 1) & HM;
+      }
+      if (!done) s_bad = 1;
     }
-    if (nt > 0) {
-      uint16_t* ord = s_lists + (size_t)todo[nt - 1] * kLocalCap;  // index order
-      if (l0 > 0) {
-        uint32_t lo = 0xFFFFFFFFu, hi = 0;
-        for (uint32_t i = threadIdx.x; i < m; i += T) {
-          lo = min(lo, s_orig[i]);
-          hi = max(hi, s_orig[i]);
+    __syncthreads();
+    for (int d = 1; d < k; ++d) {
+      const uint32_t* lod = a.lorig + (size_t)d * a.total + ls.off + start0;
+      uint16_t* list = s_lists + (size_t)d * kLocalCap;
+      for (uint32_t i = threadIdx.x; i < m; i += T) {
+        const uint32_t o = lod[i];
+        uint32_t h = (o * 0x9E3779B1u) >> (32 - (kLocalLog + 1));
+        uint32_t id = 0xFFFFFFFFu;
+        for (uint32_t probe = 0; probe <= HM; ++probe) {
+          const uint32_t key = s_hkey[h];
+          if (key == o) {
+            id = s_hval[h];
+            break;
+          }
+          if (key == 0xFFFFFFFFu) break;
+          h = (h + 1) & HM;
         }
-        lo = block_min(lo, s_w);
-        hi = block_max(hi, s_w);
-        for (uint32_t i = threadIdx.x; i < m; i += T) {
-          s_ka[i] = s_orig[i] - lo;
-          s_ia[i] = (uint16_t)i;
+        if (id >= m) {
+          s_bad = 1;
+          id = 0;
         }
-        __syncthreads();
-        const int passes = (bits_for((uint64_t)(hi - lo) + 1) + 7) / 8;
-        const uint16_t* sorted = smem_radix_sort(s_ka, s_ia, s_kb, s_ib, s_wh, m, passes, s_w);
-        for (uint32_t i = threadIdx.x; i < m; i += T) ord[i] = sorted[i];
-      } else {
-        for (uint32_t i = threadIdx.x; i < m; i += T) ord[i] = (uint16_t)i;
+        list[i] = (uint16_t)id;
       }
+    }
+    __syncthreads();
+  } else if (a.rows) {
+    // a set finished locally from its level 0: entries in input order carry
+    // the keys; every list is a stable key sort from index order
+    const uint4* ents = a.rows + ls.off;
+    for (uint32_t i = threadIdx.x; i < m; i += T) {
+      const uint32_t o = ents[i].w;
+      if (o >= a.total) s_bad = 1;
+      s_orig[i] = o < a.total ? o : 0u;
+    }
+    for (int d = 0; d < k; ++d) {
+      uint32_t lo = 0xFFFFFFFFu, hi = 0;
+      for (uint32_t i = threadIdx.x; i < m; i += T) {
+        const uint4 e = ents[i];
+        const uint32_t key = d == 0 ? e.x : (d == 1 ? e.y : e.z);
+        s_ka[i] = key;
+        s_ia[i] = (uint16_t)i;
+        lo = min(lo, key);
+        hi = max(hi, key);
+      }
+      lo = block_min(lo, s_w);
+      hi = block_max(hi, s_w);
+      for (uint32_t i = threadIdx.x; i < m; i += T) s_ka[i] -= lo;
       __syncthreads();
-      for (int q = 0; q < nt; ++q) {
-        const int d = todo[q];
-        uint32_t lo = 0xFFFFFFFFu, hi = 0;
-        for (uint32_t i = threadIdx.x; i < m; i += T) {
-          const uint16_t it = ord[i];
-          const uint4 e = ents[it];
-          const uint32_t key = d == 0 ? e.x : (d == 1 ? e.y : e.z);
-          s_ka[i] = key;
-          s_ia[i] = it;
-          lo = min(lo, key);
-          hi = max(hi, key);
-        }
-        lo = block_min(lo, s_w);
-        hi = block_max(hi, s_w);
-        for (uint32_t i = threadIdx.x; i < m; i += T) s_ka[i] -= lo;
-        __syncthreads();
-        const int passes = (bits_for((uint64_t)(hi - lo) + 1) + 7) / 8;
-        const uint16_t* sorted = smem_radix_sort(s_ka, s_ia, s_kb, s_ib, s_wh, m, passes, s_w);
-        uint16_t* list = s_lists + (size_t)d * kLocalCap;
-        for (uint32_t i = threadIdx.x; i < m; i += T) list[i] = sorted[i];
-        __syncthreads();
-      }
+      const int passes = (bits_for((uint64_t)(hi - lo) + 1) + 7) / 8;
+      const uint16_t* sorted = smem_radix_sort(s_ka, s_ia, s_kb, s_ib, s_wh, m, passes, s_w);
+      uint16_t* list = s_lists + (size_t)d * kLocalCap;
+      for (uint32_t i = threadIdx.x; i < m; i += T) list[i] = sorted[i];
+      __syncthreads();
     }
   } else {
-  for (int d = 0; d < k; ++d) {
-    uint16_t* list = s_lists + (size_t)d * kLocalCap;
-    if (d == dpar) {
-      for (uint32_t i = threadIdx.x; i < m; i += T) list[i] = (uint16_t)i;
-      continue;
-    }
-    const uint32_t* rank_d = a.ranks + (size_t)d * a.total;
-    uint32_t lo = 0xFFFFFFFFu, hi = 0;
-    for (uint32_t i = threadIdx.x; i < kLocalCap; i += T) {
-      uint32_t r = 0xFFFFFFFFu;
-      if (i < m) {
-        const uint32_t o = s_orig[i];
-        if (o < a.total) r = rank_d[o];
-        else s_bad = 1;
-        lo = min(lo, r);
-        hi = max(hi, r);
+    // rank arrays (k > 3): the items arrive in the parent's order
+    for (uint32_t i = threadIdx.x; i < m; i += T)
+      s_orig[i] = l0 > 0 ? a.vals_local[ls.off + start0 + i] : ls.off + i;
+    __syncthreads();
+    for (int d = 0; d < k; ++d) {
+      uint16_t* list = s_lists + (size_t)d * kLocalCap;
+      if (d == dpar) {
+        for (uint32_t i = threadIdx.x; i < m; i += T) list[i] = (uint16_t)i;
+        continue;
       }
-      s_ka[i] = r;
-      s_ia[i] = (uint16_t)i;
+      const uint32_t* rank_d = a.ranks + (size_t)d * a.total;
+      uint32_t lo = 0xFFFFFFFFu, hi = 0;
+      for (uint32_t i = threadIdx.x; i < kLocalCap; i += T) {
+        uint32_t r = 0xFFFFFFFFu;
+        if (i < m) {
+          const uint32_t o = s_orig[i];
+          if (o < a.total) r = rank_d[o];
+          else s_bad = 1;
+          lo = min(lo, r);
+          hi = max(hi, r);
+        }
+        s_ka[i] = r;
+        s_ia[i] = (uint16_t)i;
+      }
+      lo = block_min(lo, s_w);
+      hi = block_max(hi, s_w);
+      for (uint32_t i = threadIdx.x; i < m; i += T) s_ka[i] -= lo;
+      __syncthreads();
+      const int passes = (bits_for((uint64_t)(hi - lo) + 1) + 7) / 8;
+      const uint16_t* sorted = smem_radix_sort(s_ka, s_ia, s_kb, s_ib, s_wh, m, passes, s_w);
+      for (uint32_t i = threadIdx.x; i < m; i += T) list[i] = sorted[i];
+      __syncthreads();
     }
-    lo = block_min(lo, s_w);
-    hi = block_max(hi, s_w);
-    for (uint32_t i = threadIdx.x; i < m; i += T) s_ka[i] -= lo;
-    __syncthreads();
-    const int passes = (bits_for((uint64_t)(hi - lo) + 1) + 7) / 8;
-    const uint16_t* sorted = smem_radix_sort(s_ka, s_ia, s_kb, s_ib, s_wh, m, passes, s_w);
-    for (uint32_t i = threadIdx.x; i < m; i += T) list[i] = sorted[i];
-    __syncthreads();
-  }
   }
 
   // domain of the subtree root (widest mode)
@@ -323,284 +416,193 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
   }
   __syncthreads();
 
-  uint32_t mj = m;  // live items at this depth
-  for (int j = 0;; ++j) {
-    const int L = l0 + j;  // level of this depth in the set's tree
-    if (L > tree.L - 1 || mj == 0) break;
-    const LevelLayout yj = LevelLayout::make(tree, L);
-    const uint32_t first = (((s0 + 1) << j) - 1) - full_nodes(L);  // subtree rel index of t = 0
-    const uint32_t nodes = 1u << j;
-    const uint32_t base = yj.seg_start(first);
-    // nodes of this depth that exist (only the lowest level can be partial)
-    uint32_t nn = nodes;
-    if (L == tree.L - 1) {
-      const uint32_t c0 = ((s0 + 1) << j) - 1;
-      nn = c0 >= tree.n ? 0 : min(nodes, tree.n - c0);
+  const bool widest = a.mode == 1;
+  // split dimension of node tl (index among the block's nodes at depth jj):
+  // widest side of its domain, the root's domain clipped by the planes of
+  // its ancestors inside the block (Sec. 6)
+  auto node_dim = [&](uint32_t jj, uint32_t tl) -> int {
+    float lo[kMaxK], hi[kMaxK];
+    for (int d = 0; d < k; ++d) {
+      lo[d] = s_box[d];
+      hi[d] = s_box[kMaxK + d];
     }
+    for (uint32_t e = 0; e < jj; ++e) {
+      const uint32_t la = (1u << e) - 1 + (tl >> (jj - e));
+      const int da = s_ldim[la];
+      const float xv = s_lplane[la];
+      if (((tl >> (jj - 1 - e)) & 1u) == 0) hi[da] = xv; else lo[da] = xv;
+    }
+    return widest_dim(lo, hi, k);
+  };
+  // is list d read on a level below level L (round robin)?
+  auto needed = [&](int L, int d) -> bool {
+    if (widest) return true;
+    for (int q = L + 1; q <= tree.L - 1; ++q)
+      if (q % k == d) return true;
+    return false;
+  };
+  // mark every item of range r (info word: side << 14 | next-level offset),
+  // pin the pivots, record the planes.  The range's items are stored from
+  // list position sb on.
+  auto info_pass = [&](const Range& r, uint32_t jj, int L, uint32_t slots, uint32_t sb, uint32_t g0,
+                       uint32_t gs) {
+    const int drr = L % k;
+    const uint32_t dbase = (1u << jj) - 1;  // local index of the first node at depth jj
+    for (uint32_t p = r.p0 + g0; p < r.p1; p += gs) {
+      uint32_t t, side;
+      const uint32_t off = classify(r, p, &t, &side);
+      const uint32_t tl = t - r.tfirst;
+      const int d = widest ? s_ldim[dbase + tl] : drr;
+      const uint32_t it = s_lists[(size_t)slot_of(slots, d) * kLocalCap + (p - r.p0 + sb)];
+      if (it >= m || off >= kLocalCap) {
+        s_bad = 1;
+        continue;
+      }
+      if (side == 2) {
+        const uint32_t o = s_orig[it];
+        a.perm[ls.off + full_nodes(L) + t] = o;
+        if (widest) s_lplane[dbase + tl] = coord_of(a.pts, o, a.stride, d);
+      }
+      s_info[it] = (uint16_t)((side << 14) | off);
+    }
+  };
+
+  uint32_t slots = 0;
+  for (int q = 0; q <= k; ++q) slots |= (uint32_t)q << (4 * q);
+  constexpr int PER = kLocalCap / T;  // positions per thread in a block-wide partition
+
+  for (uint32_t j = 0;; ++j) {
+    const int L = l0 + (int)j;
+    if (L > tree.L - 1) break;
+    const LevelLayout yj = LevelLayout::make(tree, L);
+    const uint32_t nodes = 1u << j;
+    const uint32_t first = wk.s_rel << j;
     if (nodes >= (uint32_t)W) {
-      // From here on every subtree of this depth is finished by one warp,
-      // independently of the others.  Within its subtree a warp keeps each
-      // node's points in the node's in-order range: the left child takes
-      // [start, start + pr), the pivot's slot stays empty, the right child
-      // takes (start + pr, start + size).  Ranges of different warps never
-      // overlap, so warps need no block barrier and each keeps its own list
-      // rotation.
-      // a warp's subtree has at most 2^(kLocalLog-5) - 1 points, so at most
-      // kWarpTab nodes on any of its levels; two tables per warp
-      const uint32_t c0 = ((s0 + 1) << j) - 1;
-      uint16_t* tabs = reinterpret_cast<uint16_t*>(s_lplane + kLocalCap) + (size_t)warp * 2 * kWarpTab;
-      for (uint32_t t = warp; t < nn; t += W) {
-        int slot[kMaxK + 1];
-        for (int q = 0; q <= k; ++q) slot[q] = s_list_of[q];
-        uint16_t* ta = tabs;
-        uint16_t* tb2 = tabs + kWarpTab;
-        const uint32_t root = c0 + t;
-        if (lane == 0) ta[0] = (uint16_t)(yj.seg_start(first + t) - base);
-        __syncwarp();
-        for (int i = 0;; ++i) {
-          const int Li = L + i;
+      // From here every subtree of depth j is finished by one warp.  On every
+      // later level the warp keeps its subtree's items from the subtree's
+      // start at depth j on (the set of items only shrinks), so no other
+      // warp touches them and warps need no block barrier.
+      for (uint32_t tw = warp; tw < nodes; tw += W) {
+        uint32_t wslots = slots;
+        const uint32_t sb = yj.seg_start(first + tw) - yj.seg_start(first);
+        for (uint32_t i = 0;; ++i) {
+          const int Li = L + (int)i;
           if (Li > tree.L - 1) break;
-          const uint32_t cf = ((root + 1) << i) - 1;  // first node of sub-depth i
-          if (cf >= tree.n) break;
-          const uint32_t cnt = min(1u << i, tree.n - cf);
-          const bool lowest = Li == tree.L - 1;
-          const uint32_t jj = j + i;                    // depth below s0
-          const uint32_t loc0 = (1u << jj) - 1 + (t << i);  // local index of node cf
-          const bool coop = cnt <= 8;  // few nodes: the warp shares each node's items
-          // pins, sides, widest dimensions
-          for (uint32_t u = coop ? 0u : (uint32_t)lane; u < cnt; u += coop ? 1u : 32u) {
-            const uint32_t node = cf + u;
-            const uint32_t st = ta[u];
-            const uint32_t sz = subtree_size(tree, node);
-            const uint32_t pr = subtree_size(tree, 2 * node + 1);
-            int d = Li % k;
-            if (a.mode == 1) {
-              float lo[kMaxK], hi[kMaxK];
-              for (int dd = 0; dd < k; ++dd) {
-                lo[dd] = s_box[dd];
-                hi[dd] = s_box[kMaxK + dd];
-              }
-              const uint32_t tt = (t << i) + u;  // index among depth-jj nodes of s0
-              for (uint32_t e = 0; e < jj; ++e) {
-                const uint32_t la = (1u << e) - 1 + (tt >> (jj - e));
-                const int da = s_ldim[la];
-                const float xv = s_lplane[la];
-                if (((tt >> (jj - 1 - e)) & 1u) == 0) hi[da] = xv; else lo[da] = xv;
-              }
-              d = widest_dim(lo, hi, k);
-            }
-            const uint16_t* list = s_lists + (size_t)slot[d] * kLocalCap;
-            if (!coop || lane == 0) {
-              const uint32_t o = s_orig[list[st + pr]];
-              a.perm[ls.off + node] = o;
-              if (a.mode == 1) {
-                s_ldim[loc0 + u] = (uint8_t)d;
-                s_lplane[loc0 + u] = coord_of(a.pts, o, a.stride, d);
-                a.dims[ls.off + node] = (uint8_t)d;
-              }
-            }
-            for (uint32_t q = coop ? (uint32_t)lane : 0u; q < sz; q += coop ? 32u : 1u)
-              s_side[list[st + q]] = q < pr ? 0 : (q == pr ? 2 : 1);
-          }
-          __syncwarp();
-          if (lowest) break;
-          const int depth_left = tree.L - 1 - (Li + 1);
-          for (int dd = 0; dd < k; ++dd) {
-            if (a.mode == 0) {
-              bool need = false;
-              for (int q = 0; q <= depth_left && !need; ++q) need = ((Li + 1 + q) % k) == dd;
-              if (!need) continue;
-            }
-            const uint16_t* src = s_lists + (size_t)slot[dd] * kLocalCap;
-            uint16_t* dst = s_lists + (size_t)slot[k] * kLocalCap;
-            for (uint32_t u = coop ? 0u : (uint32_t)lane; u < cnt; u += coop ? 1u : 32u) {
-              const uint32_t node = cf + u;
-              const uint32_t st = ta[u];
-              const uint32_t sz = subtree_size(tree, node);
-              const uint32_t pr = subtree_size(tree, 2 * node + 1);
-              uint32_t cl = 0, cr = 0;
-              if (coop) {
-                for (uint32_t q0 = 0; q0 < sz; q0 += 32) {
-                  const uint32_t q = q0 + lane;
-                  uint16_t it = 0;
-                  uint8_t sd = 3;
-                  if (q < sz) {
-                    it = src[st + q];
-                    sd = s_side[it];
-                  }
-                  const uint32_t bl = __ballot_sync(0xffffffffu, sd == 0);
-                  const uint32_t br = __ballot_sync(0xffffffffu, sd == 1);
-                  if (sd == 0) dst[st + cl + __popc(bl & lt)] = it;
-                  if (sd == 1) dst[st + pr + 1 + cr + __popc(br & lt)] = it;
-                  cl += __popc(bl);
-                  cr += __popc(br);
-                }
-              } else {
-                for (uint32_t q = 0; q < sz; ++q) {
-                  const uint16_t it = src[st + q];
-                  const uint8_t sd = s_side[it];
-                  if (sd == 0) dst[st + cl++] = it;
-                  else if (sd == 1) dst[st + pr + 1 + cr++] = it;
-                }
-              }
+          const LevelLayout yi = LevelLayout::make(tree, Li);
+          const uint32_t jj = j + i;
+          const uint32_t firsti = wk.s_rel << jj;
+          const uint32_t cnt = 1u << i;
+          const Range r = make_range(yi, firsti, firsti + (tw << i), cnt);
+          if (r.p0 >= r.p1) break;
+          if (widest) {
+            for (uint32_t u = lane; u < cnt; u += 32) {
+              const uint32_t tl = (tw << i) + u;
+              const uint32_t node = full_nodes(Li) + firsti + tl;
+              if (node >= tree.n) continue;
+              const int d = node_dim(jj, tl);
+              s_ldim[(1u << jj) - 1 + tl] = (uint8_t)d;
+              a.dims[ls.off + node] = (uint8_t)d;
             }
             __syncwarp();
-            const int t2 = slot[dd];
-            slot[dd] = slot[k];
-            slot[k] = t2;
           }
-          // children's ranges: left starts where the node starts, right after the pivot
-          for (uint32_t u = lane; u < cnt; u += 32) {
-            const uint32_t st = ta[u];
-            const uint32_t pr = subtree_size(tree, 2 * (cf + u) + 1);
-            tb2[2 * u] = (uint16_t)st;
-            tb2[2 * u + 1] = (uint16_t)(st + pr + 1);
-          }
+          info_pass(r, jj, Li, wslots, sb, lane, 32);
           __syncwarp();
-          uint16_t* tt2 = ta;
-          ta = tb2;
-          tb2 = tt2;
+          if (Li == tree.L - 1) break;
+          const uint32_t lim = r.nb + (r.p1 - r.p0) - cnt;  // end of the range's next-level items
+          for (int d = 0; d < k; ++d) {
+            if (!needed(Li, d)) continue;
+            const uint16_t* src = s_lists + (size_t)slot_of(wslots, d) * kLocalCap;
+            uint16_t* dst = s_lists + (size_t)slot_of(wslots, k) * kLocalCap;
+            uint32_t cl = 0, cr = 0;
+            for (uint32_t b = r.p0; b < r.p1; b += 32) {
+              const uint32_t p = b + lane;
+              uint32_t it = 0, v = 3u << 14;
+              if (p < r.p1) {
+                it = src[p - r.p0 + sb];
+                v = s_info[it];
+              }
+              const uint32_t side = v >> 14;
+              const uint32_t bl = __ballot_sync(0xffffffffu, side == 0);
+              const uint32_t br = __ballot_sync(0xffffffffu, side == 1);
+              if (side < 2) {
+                const uint32_t np =
+                    (v & 0x3FFFu) + (side == 0 ? cl + __popc(bl & lt) : cr + __popc(br & lt));
+                if (np >= r.nb && np < lim) dst[np - r.nb + sb] = (uint16_t)it;
+                else s_bad = 1;
+              }
+              cl += __popc(bl);
+              cr += __popc(br);
+            }
+            __syncwarp();
+            wslots = swap_slots(wslots, d, k);
+          }
         }
       }
       break;
     }
-    // per node: segment start, pivot rank, lefts before it
-    for (uint32_t t = threadIdx.x; t < nn; t += T) {
-      s_tstart[t] = (uint16_t)(yj.seg_start(first + t) - base);
-      s_tpr[t] = (uint16_t)(yj.h >= 1 ? yj.left_size(first + t) : 0u);
-    }
-    if (threadIdx.x == 0) s_tstart[nn] = (uint16_t)mj;
-    __syncthreads();
-    {
-      // exclusive scan of the pivot ranks over the nodes (<= 4 per thread)
-      const uint32_t per = (nn + T - 1) / T;
-      const uint32_t t0 = threadIdx.x * per;
-      uint32_t v[4] = {0, 0, 0, 0}, sum = 0;
-      for (uint32_t q = 0; q < per && q < 4; ++q)
-        if (t0 + q < nn) {
-          v[q] = s_tpr[t0 + q];
-          sum += v[q];
-        }
-      uint32_t run = scan_excl(sum, s_w, nullptr);
-      for (uint32_t q = 0; q < per && q < 4; ++q)
-        if (t0 + q < nn) {
-          s_tpl[t0 + q] = (uint16_t)run;
-          run += v[q];
-        }
-    }
-    // split dimension of every node of this depth (widest: clipped domain)
-    if (a.mode == 1 && j > 0) {
-      for (uint32_t t = threadIdx.x; t < nn; t += T) {
-        float lo[kMaxK], hi[kMaxK];
-        for (int d = 0; d < k; ++d) {
-          lo[d] = s_box[d];
-          hi[d] = s_box[kMaxK + d];
-        }
-        for (int i = 0; i < j; ++i) {
-          const uint32_t ti = t >> (j - i);
-          const uint32_t loc = (1u << i) - 1 + ti;
-          const int da = s_ldim[loc];
-          const float x = s_lplane[loc];
-          if (((t >> (j - 1 - i)) & 1u) == 0) hi[da] = x; else lo[da] = x;
-        }
-        const int dd = widest_dim(lo, hi, k);
-        s_ldim[(1u << j) - 1 + t] = (uint8_t)dd;
-        a.dims[ls.off + ((s0 + 1) << j) - 1 + t] = (uint8_t)dd;
+    const Range r = make_range(yj, first, first, nodes);
+    const uint32_t mj = r.p1;
+    if (widest && j > 0) {
+      for (uint32_t tl = threadIdx.x; tl < nodes; tl += T) {
+        const uint32_t node = full_nodes(L) + first + tl;
+        if (node >= tree.n) continue;
+        const int d = node_dim(j, tl);
+        s_ldim[(1u << j) - 1 + tl] = (uint8_t)d;
+        a.dims[ls.off + node] = (uint8_t)d;
       }
+      __syncthreads();
     }
-    __syncthreads();
-    const int drr = L % k;
-    // pin the pivots; mark every item left / pivot / right
-    for (uint32_t t = threadIdx.x; t < nn; t += T) {
-      const int d = a.mode == 0 ? drr : s_ldim[(1u << j) - 1 + t];
-      const uint16_t* list = s_lists + (size_t)s_list_of[d] * kLocalCap;
-      const uint32_t it = list[s_tstart[t] + s_tpr[t]];
-      const uint32_t o = s_orig[it];
-      a.perm[ls.off + ((s0 + 1) << j) - 1 + t] = o;
-      if (a.mode == 1) s_lplane[(1u << j) - 1 + t] = coord_of(a.pts, o, a.stride, d);
-    }
-    {
-      const uint32_t per = (mj + T - 1) / T;
-      const uint32_t p0 = threadIdx.x * per, p1 = min(p0 + per, mj);
-      uint32_t t = 0;
-      if (p0 < p1) {
-        uint32_t lo = 0, hi = nn;
-        while (hi - lo > 1) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (s_tstart[mid] <= p0) lo = mid; else hi = mid;
-        }
-        t = lo;
-      }
-      for (uint32_t p = p0; p < p1; ++p) {
-        while (t + 1 < nn && s_tstart[t + 1] <= p) ++t;
-        const int d = a.mode == 0 ? drr : s_ldim[(1u << j) - 1 + t];
-        const uint16_t* list = s_lists + (size_t)s_list_of[d] * kLocalCap;
-        const uint32_t q = p - s_tstart[t], pr = s_tpr[t];
-        s_side[list[p]] = q < pr ? 0 : (q == pr ? 2 : 1);
-      }
-    }
+    info_pass(r, j, L, slots, 0, threadIdx.x, T);
     __syncthreads();
     if (L == tree.L - 1) break;  // lowest level: every item was pinned
-    // stable partition of every list still needed into the next depth's order
-    const uint32_t mn = mj - nn;
-    const int depth_left = tree.L - 1 - (L + 1);  // levels after the next one
+    const uint32_t mn = mj - nodes;
+    // stable partition of every list still needed into the next level's
+    // order: each warp ranks a contiguous chunk with ballots, one block
+    // exchange of the warps' counts, then every item is written
+    const uint32_t chunk = ((mj + W * 32 - 1) / (W * 32)) * 32;
     for (int d = 0; d < k; ++d) {
-      if (a.mode == 0) {
-        bool need = false;
-        for (int jj = 0; jj <= depth_left && !need; ++jj) need = ((L + 1 + jj) % k) == d;
-        if (!need) continue;
-      }
-      const int src_slot = s_list_of[d], dst_slot = s_list_of[k];
-      const uint16_t* src = s_lists + (size_t)src_slot * kLocalCap;
-      uint16_t* dst = s_lists + (size_t)dst_slot * kLocalCap;
-      const uint32_t per = (mj + T - 1) / T;
-      const uint32_t p0 = threadIdx.x * per, p1 = min(p0 + per, mj);
-      uint32_t cnt = 0;  // lefts in the low half, rights in the high half
-      for (uint32_t p = p0; p < p1; ++p) {
-        const uint8_t sd = s_side[src[p]];
-        cnt += sd == 0 ? 1u : (sd == 1 ? 0x10000u : 0u);
-      }
-      uint32_t run = scan_excl(cnt, s_w, nullptr);
-      uint32_t gl = run & 0xFFFFu, gr = run >> 16;
-      uint32_t t = 0;
-      if (p0 < p1) {
-        uint32_t lo = 0, hi = nn;
-        while (hi - lo > 1) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (s_tstart[mid] <= p0) lo = mid; else hi = mid;
+      if (!needed(L, d)) continue;
+      const uint16_t* src = s_lists + (size_t)slot_of(slots, d) * kLocalCap;
+      uint16_t* dst = s_lists + (size_t)slot_of(slots, k) * kLocalCap;
+      uint32_t its[PER], vs[PER];
+      uint32_t cl = 0, cr = 0;
+      const uint32_t c0 = (uint32_t)warp * chunk;
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const uint32_t p = c0 + (uint32_t)q * 32 + lane;
+        uint32_t it = 0, v = 3u << 14;
+        if ((uint32_t)q * 32 < chunk && p < mj) {
+          it = src[p];
+          v = s_info[it];
         }
-        t = lo;
+        const uint32_t side = v >> 14;
+        const uint32_t bl = __ballot_sync(0xffffffffu, side == 0);
+        const uint32_t br = __ballot_sync(0xffffffffu, side == 1);
+        const uint32_t rank = side == 0 ? cl + __popc(bl & lt) : cr + __popc(br & lt);
+        its[q] = it | (rank << 16);
+        vs[q] = v;
+        cl += __popc(bl);
+        cr += __popc(br);
       }
-      for (uint32_t p = p0; p < p1; ++p) {
-        while (t + 1 < nn && s_tstart[t + 1] <= p) ++t;
-        const uint16_t it = src[p];
-        const uint8_t sd = s_side[it];
-        if (sd == 2) continue;
-        const uint32_t ts = s_tstart[t], pr = s_tpr[t], pl = s_tpl[t];
-        uint32_t np;
-        if (sd == 0) {
-          np = ts - t + (gl - pl);
-          ++gl;
-        } else {
-          np = ts - t + pr + (gr - (ts - t - pl));
-          ++gr;
-        }
-        if (np < mn) dst[np] = it;
+      if (lane == 0) s_w[warp] = cl | (cr << 16);
+      __syncthreads();
+      const uint32_t before = __reduce_add_sync(0xffffffffu, lane < warp ? s_w[lane] : 0u);
+      const uint32_t wl = before & 0xFFFFu, wr = before >> 16;
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const uint32_t side = vs[q] >> 14;
+        if (side > 1) continue;
+        const uint32_t np = (vs[q] & 0x3FFFu) + (side == 0 ? wl : wr) + (its[q] >> 16);
+        if (np < mn) dst[np] = (uint16_t)(its[q] & 0xFFFFu);
         else s_bad = 1;
       }
       __syncthreads();
-      if (threadIdx.x == 0) {
-        s_list_of[d] = dst_slot;
-        s_list_of[k] = src_slot;
-      }
-      __syncthreads();
+      slots = swap_slots(slots, d, k);
     }
-    mj = mn;
   }
   __syncthreads();
   if (threadIdx.x == 0 && s_bad) atomicOr(a.err, ERR_INTERNAL);
 }
-
 }  // namespace
 
 size_t local_smem_bytes(int k) {

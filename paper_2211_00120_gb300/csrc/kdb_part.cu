@@ -70,7 +70,7 @@ struct PartSeg {
   uint32_t pk, po;  // pivot (key, original index)
   int dsplit;       // split dimension
   uint32_t csL, csR;  // first output position of the left / right child
-  int mode;         // 0: next level's list, 1: local entries, 2: not needed
+  int mode;         // 0: next level's list, 1: original indices for the local finish
 };
 
 __device__ inline void part_seg_info(const PartArgs& a, uint32_t ai, uint32_t srel, uint32_t start,
@@ -91,9 +91,9 @@ __device__ inline void part_seg_info(const PartArgs& a, uint32_t ai, uint32_t sr
     ps->mode = 0;
     child0 = x.act_next[e.next].base;
   } else {
-    // the set continues in the local finish, which needs only the list of
-    // the parent's split dimension
-    ps->mode = ps->dsplit == a.dlist ? 1 : 2;
+    // the set continues in the local finish, which takes every list in
+    // order as original indices
+    ps->mode = 1;
     child0 = si.off;
   }
   ps->csL = child0 + (start - e.base) - srel;
@@ -292,18 +292,17 @@ __global__ void __launch_bounds__(PT, 6) partition_kernel(PartArgs a) {
     if (!(cd & 0x80000000u) || side > 1) continue;
     const bool isB = (cd >> 28) & 1u;
     const PartSeg& sg = isB ? sB : sA;
-    if (sg.mode == 2) continue;
     const uint32_t rank = cd & 0x0FFFFFFFu;
     uint32_t pos;
     if (side == 0) pos = sg.csL + (isB ? 0u : prefL) + s_woff[warp][isB ? 2 : 0] + rank;
     else pos = sg.csR + (isB ? 0u : prefR) + s_woff[warp][isB ? 3 : 1] + rank;
-    uint4* out = sg.mode == 0 ? a.out_next : a.out_local;
     const uint32_t lim = sg.mode == 0 ? a.next_items : a.total;
     if (pos >= lim) {
       atomicOr(x.err, ERR_INTERNAL);
       continue;
     }
-    out[pos] = s_in[wbase + i * 32 + lane];
+    if (sg.mode == 0) a.out_next[pos] = s_in[wbase + i * 32 + lane];
+    else a.out_lorig[(size_t)a.dlist * a.total + pos] = s_in[wbase + i * 32 + lane].w;
   }
 }
 }  // namespace

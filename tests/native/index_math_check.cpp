@@ -40,8 +40,13 @@ int main(int argc, char** argv) {
       const kdb::LevelLayout y = kdb::LevelLayout::make(t, l);
       const long long F = (1LL << l) - 1;
       if ((long long)y.items != n - F) { printf("FAIL items n=%lld l=%d\n", n, l); return 1; }
-      long long pos = 0;
+      long long pos = 0, lefts = 0;
       for (long long sr = 0; sr < (1LL << l); ++sr) {
+        if (y.h >= 1 && (long long)y.left_before((uint32_t)sr) != lefts) {
+          printf("FAIL left_before n=%lld l=%d s_rel=%lld\n", n, l, sr);
+          return 1;
+        }
+        lefts += counted_size(2 * (F + sr) + 1, n);
         const long long s = F + sr;
         const long long size = counted_size(s, n);
         if ((long long)y.seg_start((uint32_t)sr) != pos) {
@@ -61,6 +66,10 @@ int main(int argc, char** argv) {
         ++cases;
       }
       if (pos != n - F) { printf("FAIL total n=%lld l=%d\n", n, l); return 1; }
+      if (y.h >= 1 && (long long)y.left_before((uint32_t)(1LL << l)) != lefts) {
+        printf("FAIL left_before end n=%lld l=%d\n", n, l);
+        return 1;
+      }
     }
   }
   // float_key is monotone and -0 < +0
