@@ -313,6 +313,23 @@ def main():
                 "peak_source": peak_src,
                 "build_floor_frac": fb / (peak * 1e9) / (build_ms_total / 1000.0)}
 
+    # the paper's almost-in-place placement (one int32 per point) on the same
+    # builds, for comparison with the default gather through spare workspace
+    prev = kdb.kdb_set_placement(kdb.PLACEMENT_IN_PLACE)
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(3)]
+    kdb.kdb_profile_start()
+    for e0, e1 in ev2:
+        work.copy_(src)
+        e0.record(stream)
+        kdb.kdb_build(work, k, mode)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    prof_ip = {p["name"]: p["ms"] / len(ev2) for p in kdb.kdb_profile_stop()}
+    kdb.kdb_set_placement(prev)
+    in_place = {"ms_per_step": sum(a.elapsed_time(b) for a, b in ev2) / len(ev2),
+                "placement_ms": round(prof_ip.get("placement", 0.0), 3), "steps": len(ev2)}
+
     e2e = None
     if not args.no_e2e:
         h_src = torch.from_numpy(host)
@@ -343,7 +360,8 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single_gpu",
                            "l2": "input 1.2+ GB > L2, restored by a device copy before each step"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "kernel_ms_per_step": kernel_ms}
+                "clocks": clocks, "kernel_ms_per_step": kernel_ms,
+                "placement_in_place": in_place}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -158,6 +158,25 @@ KDB_API kdb_status kdb_build_noalloc(void* d_points, int64_t n, int k, int strid
                                      kdb_split_mode mode, kdb_stream_t stream);
 
 /*
+ * kdb_set_placement -- how the final placement moves the records into level
+ * order (Sec. 3.2, 7.1).  Both settings give identical output.
+ *   KDB_PLACEMENT_AUTO      (default) when the part of the build's workspace
+ *                           that is no longer needed at that point can hold
+ *                           the N records, gather them there in node order
+ *                           and copy them back (two coalesced passes);
+ *                           otherwise as KDB_PLACEMENT_IN_PLACE.
+ *   KDB_PLACEMENT_IN_PLACE  the almost-in-place permutation: cycles of the
+ *                           node -> original-index array (one int32 per
+ *                           point) are walked from one leader per 16 nodes,
+ *                           whose records wait in a staging area of N/16
+ *                           records.
+ * Process-wide; read when a build is enqueued.  Returns the previous setting;
+ * any other value leaves the setting unchanged.
+ */
+typedef enum { KDB_PLACEMENT_AUTO = 0, KDB_PLACEMENT_IN_PLACE = 1 } kdb_placement;
+KDB_API kdb_placement kdb_set_placement(kdb_placement placement);
+
+/*
  * kdb_validate -- check the k-d condition of a level-order tree (Sec. 1):
  * for every node i and every ancestor p with split dimension d, x_d(i) <=
  * x_d(p) if i is in p's left subtree and >= if in the right one, under the

@@ -65,6 +65,7 @@ bool g_prof_on = false;
 std::vector<ProfRec> g_prof;
 std::vector<cudaEvent_t> g_event_pool;
 std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_placement{KDB_PLACEMENT_AUTO};
 
 cudaEvent_t take_event() {
   cudaEvent_t e = nullptr;
@@ -197,6 +198,7 @@ struct Plan {
   // presorted lists (k <= 3): one list of 16-byte entries per dimension
   bool use_lists = false;
   size_t o_rows, o_lists, o_lorig, o_piv, o_l0;
+  size_t o_gather = 0, gather_bytes = 0;  // placement through spare workspace
   size_t rec_hist_off = 0;  // record-sort histograms (in u32, inside the histogram area)
   uint32_t max_nseg = 0;
   uint64_t kstride = 0;  // elements between two dimensions' coordinate keys
@@ -375,6 +377,10 @@ void make_plan(Plan& P) {
   P.o_piv = take(L ? (size_t)std::max<uint32_t>(P.max_nseg, 1) * 8 : 0);
   P.o_l0 = take(G && P.sets.size() > 1 ? T * 16 : 0);  // level-0 array of several sets
   P.bytes = o;
+  // workspace that is dead once the local finish has run, one contiguous
+  // range: the placement may gather the records into it
+  P.o_gather = L ? P.o_rows : P.o_keysA;
+  P.gather_bytes = (L ? P.o_piv : P.o_perm) - P.o_gather;
 }
 
 kdb_status check_common(int64_t n, int k, int stride) {
@@ -840,7 +846,10 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   pm.perm = perm;
   pm.stage = at<unsigned char>(ws, P.o_stage);
   pm.err = err;
-  {
+  if (g_placement.load() == KDB_PLACEMENT_AUTO && (size_t)T * P.stride <= P.gather_bytes) {
+    Prof pf(K_PLACEMENT, (double)T * (4.0 + 4.0 * P.stride), 2, st);
+    KDB_CK(launch_place_gather(pm, at<unsigned char>(ws, P.o_gather), sms, st));
+  } else {
     Prof pf(K_PLACEMENT, (double)T * (4.0 + 2.0 * P.stride), 5, st);
     KDB_CK(launch_permute(pm, sms, st));
   }
@@ -977,6 +986,12 @@ int kdb_profile_stop(kdb_kernel_stat* out, int max_entries) {
 }
 
 int64_t kdb_launch_count(void) { return g_launches.load(); }
+
+kdb_placement kdb_set_placement(kdb_placement placement) {
+  if (placement != KDB_PLACEMENT_AUTO && placement != KDB_PLACEMENT_IN_PLACE)
+    return (kdb_placement)g_placement.load();
+  return (kdb_placement)g_placement.exchange(placement);
+}
 
 int kdb_debug_inject_fault(int fault, int64_t arg) {
   const int prev = g_fault;

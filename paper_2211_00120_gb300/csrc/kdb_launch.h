@@ -234,6 +234,7 @@ struct PermuteArgs {
   uint32_t* err;
 };
 cudaError_t launch_permute(const PermuteArgs& a, int num_sms, cudaStream_t st);
+cudaError_t launch_place_gather(const PermuteArgs& a, unsigned char* tmp, int num_sms, cudaStream_t st);
 cudaError_t launch_unmark(const uint32_t* perm, int32_t* out, uint32_t total, cudaStream_t st);
 
 cudaError_t launch_validate(const unsigned char* pts, uint32_t n, int k, int stride, int mode,

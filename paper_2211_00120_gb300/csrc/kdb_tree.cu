@@ -1,4 +1,6 @@
 // kdb_tree.cu -- per-level kernels of the k-d tree build other than the sort.
+#include <algorithm>
+
 #include "kdb_launch.h"
 
 namespace kdb {
@@ -463,6 +465,55 @@ __global__ void perm_rest_kernel(PermuteArgs a) {
   }
 }
 
+// Placement through spare workspace: tmp[i] = record of node i (its original
+// position perm[i]), then one coalesced copy back.  Same result as the cycle
+// walk; used when the workspace that is dead by now can hold the records.
+constexpr int kGatherStage = 64;  // records up to this stride are staged per block
+__global__ void __launch_bounds__(kThreads) place_gather_kernel(PermuteArgs a, unsigned char* tmp) {
+  __shared__ __align__(16) uint32_t s_rec[kThreads * kGatherStage / 4];
+  if (*reinterpret_cast<volatile uint32_t*>(a.err)) return;
+  const uint32_t i0 = blockIdx.x * kThreads;
+  const uint32_t i = i0 + threadIdx.x;
+  const int words = a.stride / 4;
+  uint32_t src = 0;
+  bool ok = i < a.total;
+  if (ok) {
+    src = a.perm[i] & ~kMark;
+    if (src >= a.total) {
+      atomicOr(a.err, ERR_INTERNAL);
+      ok = false;
+    }
+  }
+  if (a.stride > kGatherStage) {
+    if (ok) copy_record(tmp + (uint64_t)i * a.stride, a.pts + (uint64_t)src * a.stride, a.stride);
+    return;
+  }
+  if (ok) {
+    const uint32_t* r = reinterpret_cast<const uint32_t*>(a.pts + (uint64_t)src * a.stride);
+    for (int w = 0; w < words; ++w) s_rec[threadIdx.x * words + w] = r[w];
+  }
+  __syncthreads();
+  // the block's records are contiguous in tmp: write them word by word
+  const uint32_t n = min((uint32_t)kThreads, a.total - i0);
+  uint32_t* out = reinterpret_cast<uint32_t*>(tmp + (uint64_t)i0 * a.stride);
+  for (uint32_t w = threadIdx.x; w < n * (uint32_t)words; w += kThreads) out[w] = s_rec[w];
+}
+
+__global__ void place_copy_back_kernel(PermuteArgs a, const unsigned char* tmp, uint64_t bytes) {
+  if (*reinterpret_cast<volatile uint32_t*>(a.err)) return;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (((reinterpret_cast<uintptr_t>(a.pts) | reinterpret_cast<uintptr_t>(tmp) | bytes) & 15) == 0) {
+    const uint4* s = reinterpret_cast<const uint4*>(tmp);
+    uint4* d = reinterpret_cast<uint4*>(a.pts);
+    for (uint64_t q = t0; q < bytes / 16; q += stride) d[q] = s[q];
+  } else {
+    const uint32_t* s = reinterpret_cast<const uint32_t*>(tmp);
+    uint32_t* d = reinterpret_cast<uint32_t*>(a.pts);
+    for (uint64_t q = t0; q < bytes / 4; q += stride) d[q] = s[q];
+  }
+}
+
 __global__ void unmark_kernel(const uint32_t* perm, int32_t* out, uint32_t total) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < total) out[i] = (int32_t)(perm[i] & ~kMark);
@@ -557,6 +608,16 @@ cudaError_t launch_permute(const PermuteArgs& a, int num_sms, cudaStream_t st) {
     perm_walk_kernel<<<grid, kThreads, 0, st>>>(a, r, groups[r]);
   }
   perm_rest_kernel<<<(a.total + kThreads - 1) / kThreads, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_place_gather(const PermuteArgs& a, unsigned char* tmp, int num_sms, cudaStream_t st) {
+  if (a.total == 0) return cudaSuccess;
+  place_gather_kernel<<<(a.total + kThreads - 1) / kThreads, kThreads, 0, st>>>(a, tmp);
+  const uint64_t bytes = (uint64_t)a.total * a.stride;
+  const uint64_t want = (bytes / 16 + kThreads - 1) / kThreads;
+  const uint32_t grid = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(want, 1), (uint64_t)num_sms * 8);
+  place_copy_back_kernel<<<grid, kThreads, 0, st>>>(a, tmp, bytes);
   return cudaGetLastError();
 }
 

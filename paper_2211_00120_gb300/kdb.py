@@ -25,6 +25,9 @@ ERR_TIMEOUT = 5
 ERR_NOT_A_KD_TREE = 6
 ERR_INTERNAL = 7
 
+PLACEMENT_AUTO = 0
+PLACEMENT_IN_PLACE = 1
+
 FAULT_NONE = 0
 FAULT_ALLOC = 1
 FAULT_LOOKBACK = 2
@@ -78,6 +81,7 @@ def load():
             "kdb_build_noalloc": ([vp, i64, i32, i32, i32, vp], i32),
             "kdb_validate": ([vp, i64, i32, i32, i32, ctypes.POINTER(i64), vp], i32),
             "kdb_debug_inject_fault": ([i32, i64], i32),
+            "kdb_set_placement": ([i32], i32),
             "kdb_profile_start": ([], None),
             "kdb_profile_stop": ([ctypes.POINTER(KernelStat), i32], i32),
             "kdb_launch_count": ([], i64),
@@ -183,6 +187,12 @@ def kdb_validate(points, k: int, mode: int = ROUND_ROBIN, stream=None) -> int:
     if rc not in (OK, ERR_NOT_A_KD_TREE):
         raise KdbError(rc, "kdb_validate")
     return int(bad.value)
+
+
+def kdb_set_placement(placement: int) -> int:
+    """Process-wide placement setting (PLACEMENT_AUTO / PLACEMENT_IN_PLACE);
+    returns the previous one."""
+    return load().kdb_set_placement(placement)
 
 
 def kdb_debug_inject_fault(fault: int, arg: int = 0) -> int:

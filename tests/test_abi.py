@@ -69,3 +69,13 @@ def test_workspace_size_grows_with_n(lib):
     # 16-byte entries, double-buffered, dominate)
     assert b < 256 * 100000
     assert lib.kdb_workspace_size(1000000, 3, 12, 0) < 10 * b
+
+
+def test_placement_setting_round_trips(lib):
+    prev = kdb.kdb_set_placement(kdb.PLACEMENT_IN_PLACE)
+    try:
+        assert prev == kdb.PLACEMENT_AUTO
+        assert kdb.kdb_set_placement(7) == kdb.PLACEMENT_IN_PLACE  # invalid: unchanged
+        assert kdb.kdb_set_placement(kdb.PLACEMENT_AUTO) == kdb.PLACEMENT_IN_PLACE
+    finally:
+        kdb.kdb_set_placement(kdb.PLACEMENT_AUTO)

@@ -234,3 +234,46 @@ def test_batched_large_sets_use_segmented_levels(mode):
 def test_large_single_builds_exact(mode):
     """2^21 + 3 points: 9 segmented levels then the packed-key levels."""
     assert_same(synth.mixed((1 << 21) + 3, 3, seed=77), 3, mode)
+
+
+# -------------------------------------------------------------- placement --
+PLACEMENT_CASES = {
+    # name: (points, k, mode); record widths on both sides of the spare
+    # workspace the gather placement needs
+    "float3_rr": (lambda: synth.uniform(300001, 3, seed=51), 3, RR),
+    "float4_widest": (lambda: synth.aniso_float4(200003, seed=52), 3, WIDEST),
+    "stride8_rr": (lambda: synth.with_stride(synth.uniform(70001, 3, seed=53), 8), 3, RR),
+    "stride40_widest": (lambda: synth.with_stride(synth.uniform(50001, 3, seed=54), 40), 3, WIDEST),
+    "k4_rr": (lambda: synth.uniform(90001, 4, seed=55), 4, RR),
+    "k1_small": (lambda: synth.uniform(5000, 1, seed=56), 1, RR),
+}
+
+
+@pytest.mark.parametrize("placement", [kdb.PLACEMENT_AUTO, kdb.PLACEMENT_IN_PLACE])
+@pytest.mark.parametrize("case", sorted(PLACEMENT_CASES))
+def test_placement_modes_agree_with_oracle(case, placement):
+    gen, k, mode = PLACEMENT_CASES[case]
+    prev = kdb.kdb_set_placement(placement)
+    try:
+        assert_same(gen(), k, mode)
+    finally:
+        kdb.kdb_set_placement(prev)
+
+
+@pytest.mark.parametrize("placement", [kdb.PLACEMENT_AUTO, kdb.PLACEMENT_IN_PLACE])
+def test_placement_modes_batched(placement):
+    sizes = [3, 70001, 0, 5000, 16384, 1, 40000]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    pts = synth.mixed(int(offs[-1]), 3, seed=57)
+    prev = kdb.kdb_set_placement(placement)
+    try:
+        d = torch.from_numpy(pts).cuda()
+        kdb.kdb_build_batched(d, offs.tolist(), 3, RR)
+        got = d.cpu().numpy()
+    finally:
+        kdb.kdb_set_placement(prev)
+    for b in range(len(sizes)):
+        lo, hi = offs[b], offs[b + 1]
+        if hi > lo:
+            want, _ = oracle.build(pts[lo:hi], 3, RR)
+            assert np.array_equal(got[lo:hi].view(np.uint32), want.view(np.uint32)), f"set {b}"
