@@ -350,7 +350,8 @@ void make_plan(Plan& P) {
   const size_t tiles =
       (std::max<uint64_t>(T, P.max_items) + std::min(kSortTile, kSegTile) - 1) /
       std::min(kSortTile, kSegTile);
-  P.o_status = take(tiles * kRadixBins * 8);
+  const size_t part_tiles = (std::max<uint64_t>(T, P.max_items) + kPartTile - 1) / kPartTile;
+  P.o_status = take(std::max(tiles * kRadixBins, part_tiles * kLiftBins) * 8);
   P.o_hist = take(hist_words * 4);
   P.o_tickets = take((size_t)P.total_passes * 4);
   P.o_err = take(4);
@@ -374,7 +375,7 @@ void make_plan(Plan& P) {
   P.o_rows = take(L ? T * 16 : 0);                   // entries in input order
   P.o_lists = take(G ? T * 16 * 2 * P.k : 0);        // per dimension, double-buffered
   P.o_lorig = take(G ? T * 4 * P.k : 0);             // lists handed to the local finish
-  P.o_piv = take(L ? (size_t)std::max<uint32_t>(P.max_nseg, 1) * 8 : 0);
+  P.o_piv = take(L ? (size_t)kLiftMax * std::max<uint32_t>(P.max_nseg, 1) * 8 : 0);  // last 3 levels
   P.o_l0 = take(G && P.sets.size() > 1 ? T * 16 : 0);  // level-0 array of several sets
   P.bytes = o;
   // workspace that is dead once the local finish has run, one contiguous
@@ -600,7 +601,59 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   uint4* lcur[3] = {nullptr, nullptr, nullptr};
   uint4* lnext[3] = {nullptr, nullptr, nullptr};
   uint32_t* lorig = at<uint32_t>(ws, P.o_lorig);
-  uint2* piv = at<uint2>(ws, P.o_piv);
+  // pivots of the last kLiftMax levels, level q in slot q % kLiftMax
+  uint2* piv_ring[kLiftMax];
+  for (int i = 0; i < kLiftMax; ++i)
+    piv_ring[i] = at<uint2>(ws, P.o_piv) + (size_t)i * std::max<uint32_t>(P.max_nseg, 1);
+  // Round robin over one set: a list is read only on the levels that split
+  // in its dimension, so it is advanced lazily, several levels in one pass,
+  // just before those levels (lat[d]: the level list d is sorted for).
+  const bool lazy = P.use_lists && P.mode == KDB_SPLIT_ROUND_ROBIN && P.sets.size() == 1;
+  int lat[3] = {0, 0, 0};
+  auto level_ctx = [&](int l) {
+    LevelCtx x{};
+    x.sets = d_sets;
+    x.act = d_act + P.act_off[l];
+    x.act_next = l + 1 < levels ? d_act + P.act_off[l + 1] : nullptr;
+    x.nact = (uint32_t)P.act[l].size();
+    x.l = l;
+    x.rb = P.rb;
+    x.err = err;
+    x.local_next = P.use_local ? 1 : 0;
+    x.vals_local = vals_local;
+    return x;
+  };
+  // advance list d from level p to level q (the local finish's level if
+  // handoff), with the pivots of levels p .. q-1
+  auto lift = [&](int d, int p, int q, bool handoff) -> cudaError_t {
+    PassCtl c = ctl(P.items[p], 0, nullptr);
+    PartArgs pa{};
+    pa.x = level_ctx(p);
+    pa.act_out = q < levels ? d_act + P.act_off[q] : nullptr;
+    pa.b = q - p;
+    pa.handoff = handoff ? 1 : 0;
+    pa.in = lcur[d];
+    pa.out_next = lnext[d];
+    pa.out_lorig = lorig;
+    for (int e = 0; e < q - p; ++e) pa.piv[e] = piv_ring[(p + e) % kLiftMax];
+    pa.dims = dims;
+    pa.k = k;
+    pa.mode = P.mode;
+    pa.dlist = d;
+    pa.n = P.items[p];
+    pa.next_items = q < levels ? P.items[q] : 0;
+    pa.total = T;
+    pa.status = c.status;
+    pa.ticket = c.ticket;
+    pa.epoch = c.epoch;
+    pa.wait_epoch = c.wait_epoch;
+    pa.wait_ns = c.wait_ns;
+    Prof pf(K_PARTITION, (double)P.items[p] * 32, 1, st);
+    cudaError_t e = launch_partition(pa, st);
+    std::swap(lcur[d], lnext[d]);
+    lat[d] = q;
+    return e;
+  };
   if (P.use_lists) {
     for (int d = 0; d < k; ++d) {
       lcur[d] = at<uint4>(ws, P.o_lists) + (size_t)(2 * d) * T;
@@ -669,11 +722,12 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     uint32_t* vfree = vals_cur == valsA ? valsB : valsA;
     hcur = hist + P.hist_off[l];
     if (P.use_lists) {
+      if (lazy && lat[l % k] < l) KDB_CK(lift(l % k, lat[l % k], l, false));
       PivotArgs pv{};
       pv.x = x;
       for (int d = 0; d < k; ++d) pv.lists[d] = lcur[d];
       pv.items = n;
-      pv.piv = piv;
+      pv.piv = piv_ring[l % kLiftMax];
       pv.perm = perm;
       pv.dims = dims;
       pv.k = k;
@@ -682,31 +736,9 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
         Prof pf(K_PIVOT, (double)(x.nact << l) * 20, 1, st);
         KDB_CK(launch_pivots(pv, st));
       }
-      const uint32_t next_items = l + 1 < levels ? P.items[l + 1] : 0;
-      for (int d = 0; d < k; ++d) {
-        PassCtl c = ctl(n, 0, nullptr);
-        PartArgs pa2{};
-        pa2.x = x;
-        pa2.in = lcur[d];
-        pa2.out_next = lnext[d];
-        pa2.out_lorig = lorig;
-        pa2.piv = piv;
-        pa2.dims = dims;
-        pa2.k = k;
-        pa2.mode = P.mode;
-        pa2.dlist = d;
-        pa2.n = n;
-        pa2.next_items = next_items;
-        pa2.total = T;
-        pa2.status = c.status;
-        pa2.ticket = c.ticket;
-        pa2.epoch = c.epoch;
-        pa2.wait_epoch = c.wait_epoch;
-        pa2.wait_ns = c.wait_ns;
-        Prof pf(K_PARTITION, (double)n * 32, 1, st);
-        KDB_CK(launch_partition(pa2, st));
-      }
-      for (int d = 0; d < k; ++d) std::swap(lcur[d], lnext[d]);
+      // every list follows the level (sets leaving hand their lists over)
+      if (!lazy)
+        for (int d = 0; d < k; ++d) KDB_CK(lift(d, l, l + 1, false));
     } else if (P.seg[l]) {
       SegKeyArgs sa{};
       sa.x = x;
@@ -809,6 +841,9 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       KDB_CK(launch_widest_children(wa, st));
     }
   }
+
+  if (lazy && levels > 0)  // hand every list over to the local finish
+    for (int d = 0; d < k; ++d) KDB_CK(lift(d, lat[d], levels, true));
 
   // ---- subtrees small enough for one block: all remaining levels on chip
   if (P.use_local && !P.work.empty()) {

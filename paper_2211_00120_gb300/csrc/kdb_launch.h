@@ -54,17 +54,23 @@ struct PivotArgs {
   const uint8_t* dims;      // widest: split dimension per node
   int k, mode;
 };
+// One partition pass advances a list by 1..kLiftMax levels at once.
+constexpr int kLiftMax = 3;
+constexpr int kLiftBins = 1 << kLiftMax;  // descendants of a segment kLiftMax levels down
 struct PartArgs {
-  LevelCtx x;
-  const uint4* in;          // this level's list sorted by dimension dlist
-  uint4* out_next;          // next level's list
+  LevelCtx x;               // level p, the input list's level
+  const ActiveEntry* act_out;  // active sets of level p + b
+  int b;                    // levels to advance, 1..kLiftMax (b > 1: one active set)
+  int handoff;              // 1: every set goes to the local finish at level p + b
+  const uint4* in;          // list sorted by (tag on level p, key_dlist, index)
+  uint4* out_next;          // the list on level p + b
   uint32_t* out_lorig;      // original indices for the local finish (sets leaving),
                             // one array of `total` per list
-  const uint2* piv;
+  const uint2* piv[kLiftMax];  // pivots (key, index) of levels p .. p + b - 1
   const uint8_t* dims;
   int k, mode, dlist;
   uint32_t n, next_items, total;
-  uint64_t* status;         // one look-back word per tile
+  uint64_t* status;         // kLiftBins look-back words per tile
   uint32_t* ticket;
   uint32_t epoch, wait_epoch;
   uint64_t wait_ns;

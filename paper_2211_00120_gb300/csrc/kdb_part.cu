@@ -63,97 +63,117 @@ constexpr int PT = kPartThreads;
 constexpr int PI = kPartItems;
 constexpr int PTILE = PT * PI;
 constexpr int PW = PT / 32;
+constexpr int NB = 2 * kLiftBins;  // bins of a tile: (segment A or B) x child
+static_assert(kLiftMax == 3, "pivot tables hold depth-3 subtrees");
 
-struct PartSeg {
-  uint32_t start;   // first position of the segment in this level's array
-  uint32_t ai, srel;
-  uint32_t pk, po;  // pivot (key, original index)
-  int dsplit;       // split dimension
-  uint32_t csL, csR;  // first output position of the left / right child
-  int mode;         // 0: next level's list, 1: original indices for the local finish
+struct LiftSeg {
+  uint32_t start;              // first position of the segment in the level-p array
+  uint32_t cs[kLiftBins];      // first output position of each child's run
+  uint32_t pk[kLiftBins - 1];  // pivots of the segment's first b levels, heap order
+  uint32_t po[kLiftBins - 1];
+  uint8_t dim[kLiftBins - 1];  // their split dimensions
+  int mode;                    // 0: next level's list, 1: original indices for the local finish
 };
 
-__device__ inline void part_seg_info(const PartArgs& a, uint32_t ai, uint32_t srel, uint32_t start,
-                                     PartSeg* ps) {
+__device__ inline void lift_seg_info(const PartArgs& a, uint32_t ai, uint32_t srel, uint32_t start,
+                                     LiftSeg* ps) {
   const LevelCtx& x = a.x;
   const ActiveEntry e = x.act[ai];
   const SetInfo si = x.sets[e.set];
-  const LevelLayout y = LevelLayout::make(make_tree(si.n), x.l);
+  const Tree tree = make_tree(si.n);
   ps->start = start;
-  ps->ai = ai;
-  ps->srel = srel;
-  const uint2 pv = a.piv[(ai << x.l) | srel];
-  ps->pk = pv.x;
-  ps->po = pv.y;
-  ps->dsplit = a.mode == 0 ? x.l % a.k : a.dims[si.off + full_nodes(x.l) + srel];
-  uint32_t child0;
-  if (e.next >= 0) {
-    ps->mode = 0;
-    child0 = x.act_next[e.next].base;
-  } else {
-    // the set continues in the local finish, which takes every list in
-    // order as original indices
-    ps->mode = 1;
-    child0 = si.off;
+  ps->mode = (a.handoff || e.next < 0) ? 1 : 0;
+  uint32_t base_out;
+  if (ps->mode == 1) base_out = si.off;
+  else base_out = a.act_out[a.b == 1 ? (uint32_t)e.next : 0u].base;
+  const LevelLayout yo = LevelLayout::make(tree, x.l + a.b);
+  const uint32_t nb = 1u << a.b;
+  for (uint32_t c = 0; c < nb; ++c) ps->cs[c] = base_out + yo.seg_start((srel << a.b) + c);
+  for (uint32_t h = 0; h + 1 < nb; ++h) {
+    const int e2 = 31 - __clz(h + 1);  // depth of heap node h below the segment
+    const uint32_t rel = (srel << e2) + (h + 1 - (1u << e2));
+    const int lq = x.l + e2;
+    const uint2 pv = a.piv[e2][(ai << lq) | rel];
+    ps->pk[h] = pv.x;
+    ps->po[h] = pv.y;
+    ps->dim[h] = (uint8_t)(a.mode == 0 ? lq % a.k : a.dims[si.off + full_nodes(lq) + rel]);
   }
-  ps->csL = child0 + (start - e.base) - srel;
-  ps->csR = ps->csL + y.left_size(srel);
 }
 
-// Warp-parallel look-back: the lanes read the words of the 32 preceding
-// tiles; values of consecutive published words are added until the nearest
-// inclusive prefix.  Returns false if a wait ran past c.wait_ns.
-__device__ inline bool warp_look_back(const PartArgs& a, uint32_t tile, uint32_t* prefix) {
+// Warp-parallel decoupled look-back over nb bins: lane group g (32 / nb
+// lanes) reads bin g of the words of as many preceding tiles at a time and
+// adds published values up to the nearest inclusive prefix.  Writes the
+// exclusive prefix of every bin to s_pref; false if a wait ran past wait_ns.
+__device__ inline bool warp_look_back_bins(const PartArgs& a, uint32_t tile, int nbin,
+                                           uint32_t* s_pref) {
   const int lane = threadIdx.x & 31;
-  int64_t t = (int64_t)tile - 1;  // newest predecessor not yet consumed
+  const int lpb = 32 / nbin;
+  const int g = lane / lpb, j = lane % lpb;
+  const uint32_t gmask = lpb == 32 ? 0xffffffffu : (((1u << lpb) - 1u) << (g * lpb));
+  int64_t t = (int64_t)tile - 1;  // newest predecessor not yet consumed (group-uniform)
   uint32_t acc = 0;
-  bool waiting = false;
+  bool done = false, ok = true, waiting = false;
   uint64_t t0 = 0;
   for (;;) {
-    const int64_t mine = t - lane;
-    uint64_t w = mine >= 0 ? ld_relaxed_u64(a.status + mine) : lb_pack(kFlagPre, a.wait_epoch, 0);
+    const int64_t mine = t - j;
+    uint64_t w = lb_pack(kFlagPre, a.wait_epoch, 0);
+    if (!done && mine >= 0) w = ld_relaxed_u64(a.status + (uint64_t)mine * kLiftBins + g);
     const uint32_t ep = (uint32_t)(w >> 32) & 0x3FFFFFFFu;
-    const bool ready = ep == a.wait_epoch && (w >> 62) != 0;
-    const bool pre = ready && (w >> 62) == 2;
-    const uint32_t notready = __ballot_sync(0xffffffffu, !ready);
-    const uint32_t pres = __ballot_sync(0xffffffffu, pre);
-    const int first_nr = notready ? __ffs(notready) - 1 : 32;
-    const int first_pre = pres ? __ffs(pres) - 1 : 32;
-    if (first_pre < first_nr) {  // everything up to the prefix is published
-      const uint32_t v = lane <= first_pre ? (uint32_t)w : 0u;
-      *prefix = acc + __reduce_add_sync(0xffffffffu, v);
-      return true;
+    const bool ready = done || (ep == a.wait_epoch && (w >> 62) != 0);
+    const bool pre = !done && ready && (w >> 62) == 2;
+    const uint32_t nr = __ballot_sync(0xffffffffu, !ready) & gmask;
+    const uint32_t pr = __ballot_sync(0xffffffffu, pre) & gmask;
+    const int fnr = nr ? __ffs(nr) - 1 - g * lpb : lpb;
+    const int fpr = pr ? __ffs(pr) - 1 - g * lpb : lpb;
+    const uint32_t v = done ? 0u : (uint32_t)w;
+    uint32_t s1 = j <= fpr ? v : 0u, s2 = j < fnr ? v : 0u;
+    for (int o = 1; o < lpb; o <<= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     }
-    if (first_nr > 0) {  // consume the published aggregates and move on
-      const uint32_t v = lane < first_nr ? (uint32_t)w : 0u;
-      acc += __reduce_add_sync(0xffffffffu, v);
-      t -= first_nr;
-      waiting = false;
-      continue;
+    if (!done) {
+      if (fpr < fnr) {  // everything up to the prefix is published
+        acc += s1;
+        done = true;
+      } else if (fnr > 0) {  // consume the published aggregates and move on
+        acc += s2;
+        t -= fnr;
+        waiting = false;
+      } else {
+        const uint64_t now = global_timer_ns();
+        if (!waiting) {
+          waiting = true;
+          t0 = now;
+        } else if (now - t0 > a.wait_ns) {
+          ok = false;
+          done = true;
+        }
+      }
     }
-    const uint64_t now = global_timer_ns();
-    if (!waiting) {
-      waiting = true;
-      t0 = now;
-    } else if (now - t0 > a.wait_ns) {
-      *prefix = acc;
-      return false;
-    }
+    if (__all_sync(0xffffffffu, done)) break;
   }
+  if (j == 0) s_pref[g] = acc;
+  return __all_sync(0xffffffffu, ok);
 }
 
+// One pass that advances list dlist by b levels (1 <= b <= 3): the tag update
+// of Sec. 3.2 applied b times with the pivots of levels p .. p+b-1, and the
+// list re-sorted by the new tag.  The list is sorted by (tag_p, key, index),
+// so the new order is a stable split of every segment into its 2^b
+// descendants' runs; items pinned on the way are dropped.
 __global__ void __launch_bounds__(PT, 6) partition_kernel(PartArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint4* s_in = reinterpret_cast<uint4*>(smem_raw);
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ uint32_t s_tile, s_abort, s_bpos, s_acont;
-  __shared__ PartSeg s_seg[2];
-  __shared__ uint32_t s_wcnt[PW][6];  // per warp: LA RA LB RB PA PB
-  __shared__ uint32_t s_woff[PW][4];
-  __shared__ uint32_t s_prefL, s_prefP;
+  __shared__ LiftSeg s_seg[2];
+  __shared__ uint32_t s_wcnt[PW][NB];  // per warp and bin: items, then exclusive offsets
+  __shared__ uint32_t s_tcnt[NB];      // tile totals per bin
+  __shared__ uint32_t s_prefA[kLiftBins];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const LevelCtx& x = a.x;
+  const int nbin = 1 << a.b;
   if (tid == 0) {
     s_abort = *reinterpret_cast<volatile uint32_t*>(x.err) != 0u;
     if (!s_abort) {
@@ -166,13 +186,13 @@ __global__ void __launch_bounds__(PT, 6) partition_kernel(PartArgs a) {
       bulk_g2s(s_in, a.in + tb, tn * 16u, &s_bar);
       uint32_t ai, sr, st, en;
       segment_at(x, tb, &ai, &sr, &st, &en);
-      part_seg_info(a, ai, sr, st, &s_seg[0]);
+      lift_seg_info(a, ai, sr, st, &s_seg[0]);
       s_acont = st < tb;
       s_bpos = tn;
       if (en < tb + tn) {
         uint32_t a2, s2, st2, en2;
         segment_at(x, en, &a2, &s2, &st2, &en2);
-        part_seg_info(a, a2, s2, st2, &s_seg[1]);
+        lift_seg_info(a, a2, s2, st2, &s_seg[1]);
         s_bpos = en - tb;
         if (en2 < tb + tn) s_abort = 2;  // a segment shorter than a tile: not allowed
       } else {
@@ -180,9 +200,13 @@ __global__ void __launch_bounds__(PT, 6) partition_kernel(PartArgs a) {
       }
     }
   }
+  for (int i = tid; i < PW * NB; i += PT) (&s_wcnt[0][0])[i] = 0;
   __syncthreads();
   if (s_abort == 1) return;
-  if (s_abort == 2 && tid == 0) atomicOr(x.err, ERR_INTERNAL);
+  if (s_abort == 2) {
+    if (tid == 0) atomicOr(x.err, ERR_INTERNAL);
+    return;
+  }
   const uint32_t tile = s_tile;
   const uint32_t tb = tile * (uint32_t)PTILE;
   const uint32_t tn = a.n - tb < (uint32_t)PTILE ? a.n - tb : (uint32_t)PTILE;
@@ -206,103 +230,97 @@ __global__ void __launch_bounds__(PT, 6) partition_kernel(PartArgs a) {
   if (s_abort == 1) return;
   const uint32_t bpos = s_bpos;
   const bool hasB = bpos < tn;
-  const PartSeg sA = s_seg[0], sB = s_seg[1];
 
-  // classify every item and rank it among its warp's items of the same
-  // (segment, side), in list order
+  // classify every item (child path or pinned) and rank it among its warp's
+  // items of the same (segment, child), in list order
   const uint32_t lt = (1u << lane) - 1u;
-  uint32_t code[PI];  // bit 31: valid, bits 29-30: side (0 L, 1 R, 2 pivot), bit 28: B, low: rank
-  uint32_t cnt[6] = {0, 0, 0, 0, 0, 0};
+  uint16_t bins[PI];
+  uint16_t rnk[PI];
   const uint32_t wbase = (uint32_t)warp * 32 * PI;
 #pragma unroll
   for (int i = 0; i < PI; ++i) {
     const uint32_t p = wbase + i * 32 + lane;
-    const bool ok = p < tn;
-    const bool isB = p >= bpos;
-    uint32_t side = 3;
-    if (ok) {
-      const PartSeg& sg = isB ? sB : sA;
+    uint32_t bin = NB;  // not written: out of range or pinned
+    if (p < tn) {
+      const uint32_t sg = p >= bpos ? 1u : 0u;
+      const LiftSeg& S = s_seg[sg];
       const uint4 en = s_in[p];
-      const uint32_t key = comp(en, sg.dsplit);
-      side = before(key, en.w, sg.pk, sg.po) ? 0u : ((key == sg.pk && en.w == sg.po) ? 2u : 1u);
+      uint32_t h = 0;
+      bool pinned = false;
+      for (int e2 = 0; e2 < a.b; ++e2) {
+        const uint32_t key = comp(en, S.dim[h]);
+        const uint32_t pk = S.pk[h], po = S.po[h];
+        if (key == pk && en.w == po) {
+          pinned = true;
+          break;
+        }
+        h = 2 * h + (before(key, en.w, pk, po) ? 1u : 2u);
+      }
+      if (!pinned) bin = sg * kLiftBins + (h - (uint32_t)(nbin - 1));
     }
-    const uint32_t bLA = __ballot_sync(0xffffffffu, ok && !isB && side == 0);
-    const uint32_t bRA = __ballot_sync(0xffffffffu, ok && !isB && side == 1);
-    const uint32_t bLB = __ballot_sync(0xffffffffu, ok && isB && side == 0);
-    const uint32_t bRB = __ballot_sync(0xffffffffu, ok && isB && side == 1);
-    const uint32_t bPA = __ballot_sync(0xffffffffu, ok && !isB && side == 2);
-    const uint32_t bPB = __ballot_sync(0xffffffffu, ok && isB && side == 2);
-    uint32_t rank = 0;
-    if (side == 0) rank = (isB ? cnt[2] + __popc(bLB & lt) : cnt[0] + __popc(bLA & lt));
-    if (side == 1) rank = (isB ? cnt[3] + __popc(bRB & lt) : cnt[1] + __popc(bRA & lt));
-    code[i] = (ok ? 0x80000000u : 0u) | (side << 29) | (isB ? 0x10000000u : 0u) | rank;
-    cnt[0] += __popc(bLA);
-    cnt[1] += __popc(bRA);
-    cnt[2] += __popc(bLB);
-    cnt[3] += __popc(bRB);
-    cnt[4] += __popc(bPA);
-    cnt[5] += __popc(bPB);
+    const uint32_t peers = __match_any_sync(0xffffffffu, bin);
+    uint32_t prev = 0;
+    if (bin < NB) prev = s_wcnt[warp][bin];
+    __syncwarp();
+    rnk[i] = (uint16_t)(prev + __popc(peers & lt));
+    if (bin < NB && (peers & lt) == 0) s_wcnt[warp][bin] = prev + __popc(peers);
+    bins[i] = (uint16_t)bin;
+    __syncwarp();
   }
-  if (lane == 0)
-    for (int q = 0; q < 6; ++q) s_wcnt[warp][q] = cnt[q];
   __syncthreads();
-  if (tid == 0) {
-    uint32_t run[4] = {0, 0, 0, 0}, pa = 0, pb = 0;
+  if (tid < NB) {
+    uint32_t run = 0;
+#pragma unroll
     for (int w = 0; w < PW; ++w) {
-      for (int q = 0; q < 4; ++q) {
-        s_woff[w][q] = run[q];
-        run[q] += s_wcnt[w][q];
-      }
-      pa += s_wcnt[w][4];
-      pb += s_wcnt[w][5];
+      const uint32_t c = s_wcnt[w][tid];
+      s_wcnt[w][tid] = run;
+      run += c;
     }
-    // publish this tile's counts for its last segment: 2 * lefts + pivots
-    uint64_t* mine = a.status + tile;
-    if (hasB) st_relaxed_u64(mine, lb_pack(kFlagPre, a.epoch, 2 * run[2] + pb));
-    else if (!s_acont) st_relaxed_u64(mine, lb_pack(kFlagPre, a.epoch, 2 * run[0] + pa));
-    else st_relaxed_u64(mine, lb_pack(kFlagAgg, a.epoch, 2 * run[0] + pa));
-    s_prefL = run[0];  // tile totals, replaced by the prefix below
-    s_prefP = pa;
+    s_tcnt[tid] = run;
   }
   __syncthreads();
+  // publish the counts of this tile's last segment: B's (which starts here),
+  // or A's -- an inclusive prefix if A starts here, else an aggregate
+  const bool a_cont = s_acont != 0;
+  if (tid < nbin) {
+    uint64_t* mine = a.status + (uint64_t)tile * kLiftBins + tid;
+    if (hasB) st_relaxed_u64(mine, lb_pack(kFlagPre, a.epoch, s_tcnt[kLiftBins + tid]));
+    else st_relaxed_u64(mine, lb_pack(a_cont ? kFlagAgg : kFlagPre, a.epoch, s_tcnt[tid]));
+  }
   if (warp == 0) {
-    uint32_t v = 0;
     bool ok = true;
-    if (s_acont) ok = warp_look_back(a, tile, &v);
-    if (lane == 0) {
-      if (!ok) {
-        atomicOr(x.err, ERR_TIMEOUT);
-        s_abort = 1;
-      }
-      if (s_acont && !hasB)
-        st_relaxed_u64(a.status + tile, lb_pack(kFlagPre, a.epoch, v + 2 * s_prefL + s_prefP));
-      s_prefL = v >> 1;
-      s_prefP = v & 1u;
+    if (a_cont) ok = warp_look_back_bins(a, tile, nbin, s_prefA);
+    else if (lane < kLiftBins) s_prefA[lane] = 0;
+    __syncwarp();
+    if (lane < nbin) {
+      if (a_cont && !hasB)
+        st_relaxed_u64(a.status + (uint64_t)tile * kLiftBins + lane,
+                       lb_pack(kFlagPre, a.epoch, s_prefA[lane] + s_tcnt[lane]));
+    }
+    if (!ok && lane == 0) {
+      atomicOr(x.err, ERR_TIMEOUT);
+      s_abort = 1;
     }
   }
   __syncthreads();
   if (s_abort) return;
 
   // write every child's run in order
-  const uint32_t prefL = s_prefL, prefR = (tb - sA.start) - s_prefL - s_prefP;
 #pragma unroll
   for (int i = 0; i < PI; ++i) {
-    const uint32_t cd = code[i];
-    const uint32_t side = (cd >> 29) & 3u;
-    if (!(cd & 0x80000000u) || side > 1) continue;
-    const bool isB = (cd >> 28) & 1u;
-    const PartSeg& sg = isB ? sB : sA;
-    const uint32_t rank = cd & 0x0FFFFFFFu;
-    uint32_t pos;
-    if (side == 0) pos = sg.csL + (isB ? 0u : prefL) + s_woff[warp][isB ? 2 : 0] + rank;
-    else pos = sg.csR + (isB ? 0u : prefR) + s_woff[warp][isB ? 3 : 1] + rank;
-    const uint32_t lim = sg.mode == 0 ? a.next_items : a.total;
+    const uint32_t bin = bins[i];
+    if (bin >= NB) continue;
+    const uint32_t sg = bin / kLiftBins, c = bin % kLiftBins;
+    const LiftSeg& S = s_seg[sg];
+    const uint32_t pos = S.cs[c] + (sg ? 0u : s_prefA[c]) + s_wcnt[warp][bin] + rnk[i];
+    const uint32_t lim = S.mode == 0 ? a.next_items : a.total;
     if (pos >= lim) {
       atomicOr(x.err, ERR_INTERNAL);
       continue;
     }
-    if (sg.mode == 0) a.out_next[pos] = s_in[wbase + i * 32 + lane];
-    else a.out_lorig[(size_t)a.dlist * a.total + pos] = s_in[wbase + i * 32 + lane].w;
+    const uint4 en = s_in[wbase + i * 32 + lane];
+    if (S.mode == 0) a.out_next[pos] = en;
+    else a.out_lorig[(size_t)a.dlist * a.total + pos] = en.w;
   }
 }
 }  // namespace
