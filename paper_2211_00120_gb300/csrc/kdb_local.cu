@@ -173,52 +173,107 @@ __device__ inline uint32_t swap_slots(uint32_t slots, int d, int k) {
   return slots | (b << (4 * d)) | (a << (4 * k));
 }
 
-// Segments [f, f + cnt) of one level of the set's tree (relative indices on
-// that level), handled by one thread group.  Positions are local: position 0
-// is the first item of the block's own subtree on this level.
-struct Range {
-  LevelLayout y;
-  uint32_t tfirst;  // first segment of the block's subtree on this level
-  uint32_t base;    // y.seg_start(tfirst)
-  uint32_t f;       // first segment of the range
-  uint32_t p0, p1;  // local positions of the range's items
-  uint32_t lb0;     // y.left_before(f)
-  uint32_t nb;      // local position of the range's first item on the next level
+// q = n / d for n < 2^13 and 1 <= d < 2^13 by a multiply-high with
+// M = floor((2^32 - 1) / d) + 1: the error term n (M - 2^32/d) / 2^32 is below
+// 2^-19, less than the gap 1/d between n/d and the next integer.
+__device__ inline uint32_t div_magic(uint32_t d) { return d <= 1 ? 0u : 0xFFFFFFFFu / d + 1u; }
+__device__ inline uint32_t div_small(uint32_t n, uint32_t d, uint32_t magic) {
+  return d <= 1 ? n * d : __umulhi(n, magic);
+}
+
+// The block's subtree on one level of the set's tree, in block-local terms:
+// segment u = the block's u-th subtree on that level, positions counted from
+// the block's first item on that level.  Same closed forms as the set's
+// layout (Sec. 4.1, 4.2) with the lowest-level nodes that fall inside the
+// block's subtree; every value is below 2^13, so all of it is 32-bit.
+struct Local {
+  uint32_t h;        // levels below this one
+  uint32_t thin;     // 2^h - 1: a subtree without lowest-level nodes
+  uint32_t full;     // 2^(h+1) - 1
+  uint32_t mb;       // lowest-level nodes inside the block's subtree
+  uint32_t qb;       // full segments
+  uint32_t a;        // items in the full segments
+  uint32_t part;     // size of segment qb
+  uint32_t w;        // 2^(h-1): lowest-level width of a left child (h >= 1)
+  uint32_t mfull, mthin;
 };
 
-__device__ inline Range make_range(const LevelLayout& y, uint32_t tfirst, uint32_t f, uint32_t cnt) {
+__device__ inline Local make_local(const Tree& tree, int L, uint32_t tfirst, uint32_t nodes) {
+  Local y;
+  y.h = (uint32_t)(tree.L - L - 1);
+  y.thin = (1u << y.h) - 1u;
+  y.full = 2u * y.thin + 1u;
+  const uint64_t lo = (uint64_t)tfirst << y.h;  // first lowest-level slot of the block
+  const uint64_t room = (uint64_t)nodes << y.h;
+  y.mb = tree.m > lo ? (uint32_t)min((uint64_t)tree.m - lo, room) : 0u;
+  y.qb = min(y.mb >> y.h, nodes);
+  y.a = y.qb * y.full;
+  y.part = y.thin + (y.mb - (y.qb << y.h));
+  y.w = y.h >= 1 ? 1u << (y.h - 1) : 0u;
+  y.mfull = div_magic(y.full);
+  y.mthin = div_magic(y.thin);
+  return y;
+}
+__device__ inline uint32_t l_start(const Local& y, uint32_t u) { return u * y.thin + min(u << y.h, y.mb); }
+__device__ inline uint32_t l_seg_of(const Local& y, uint32_t p) {
+  if (p < y.a) return div_small(p, y.full, y.mfull);
+  const uint32_t p2 = p - y.a;
+  if (p2 < y.part) return y.qb;
+  return y.qb + 1u + div_small(p2 - y.part, y.thin, y.mthin);
+}
+__device__ inline uint32_t l_left(const Local& y, uint32_t u) {  // h >= 1
+  const uint32_t lowest = (2u * u) << (y.h - 1);
+  const uint32_t low = lowest >= y.mb ? 0u : min(y.mb - lowest, y.w);
+  return (y.w - 1u) + low;
+}
+__device__ inline uint32_t l_left_before(const Local& y, uint32_t u) {  // h >= 1
+  const uint32_t fb = y.mb >> y.h;
+  uint32_t low = min(u, fb) * y.w;
+  if (u > fb) low += min(y.mb - fb * (2u * y.w), y.w);
+  return u * (y.w - 1u) + low;
+}
+
+// Segments [uf, uf + cnt) of one level handled by one thread group.
+struct Range {
+  Local y;
+  uint32_t uf;       // first segment
+  uint32_t p0, p1;   // positions of the range's items
+  uint32_t lb0;      // lefts before uf
+  uint32_t nb;       // position of the range's first item on the next level
+};
+
+__device__ inline Range make_range(const Local& y, uint32_t uf, uint32_t cnt) {
   Range r;
   r.y = y;
-  r.tfirst = tfirst;
-  r.base = y.seg_start(tfirst);
-  r.f = f;
-  r.p0 = y.seg_start(f) - r.base;
-  r.p1 = y.seg_start(f + cnt) - r.base;
-  r.lb0 = y.h >= 1 ? y.left_before(f) : 0u;
+  r.uf = uf;
+  r.p0 = l_start(y, uf);
+  r.p1 = l_start(y, uf + cnt);
+  r.lb0 = y.h >= 1 ? l_left_before(y, uf) : 0u;
   // the next level holds every item of this level but the pinned ones, in
-  // segment order: items before the range's first child = items before f
-  // minus the f pivots above them
-  r.nb = (y.seg_start(f) - f) - (r.base - tfirst);
+  // segment order: items before the range's first child = items before uf
+  // minus the uf pivots above them
+  r.nb = r.p0 - uf;
   return r;
 }
 
-// Tag update of the item at local position p (Sec. 3.2 with Observation 1):
-// in its segment t it is left of the pivot (side 0), the pivot (2) or right
-// (1).  Returns the item's position on the next level minus its rank among
-// the range's items of the same side: left items of the range go, in list
-// order, after the right items of the range's earlier segments; right items
-// after the left items of the earlier segments and of t itself.
-__device__ inline uint32_t classify(const Range& r, uint32_t p, uint32_t* t_out, uint32_t* side) {
-  const uint32_t t = r.y.seg_of(r.base + p);
-  const uint32_t st = r.y.seg_start(t) - r.base;
+// Tag update of the item at position p (Sec. 3.2 with Observation 1): in its
+// segment u it is left of the pivot (side 0), the pivot (2) or right (1).
+// Returns the item's position on the next level minus its rank among the
+// range's items of the same side: left items of the range go, in list order,
+// after the right items of the range's earlier segments; right items after
+// the left items of the earlier segments and of u itself.
+__device__ inline uint32_t classify(const Range& r, uint32_t p, uint32_t* u_out, uint32_t* side) {
+  const Local& y = r.y;
+  const uint32_t u = l_seg_of(y, p);
+  const uint32_t st = l_start(y, u);
   const uint32_t q = p - st;
   uint32_t pr = 0, sl = 0;
-  if (r.y.h >= 1) {
-    pr = r.y.left_size(t);
-    sl = r.y.left_before(t) - r.lb0;
+  if (y.h >= 1) {
+    pr = l_left(y, u);
+    sl = l_left_before(y, u) - r.lb0;
   }
-  const uint32_t sr = (st - r.p0) - (t - r.f) - sl;
-  *t_out = t;
+  const uint32_t sr = (st - r.p0) - (u - r.uf) - sl;
+  *u_out = u;
   if (q < pr) {
     *side = 0;
     return r.nb + sr;
@@ -434,24 +489,40 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     }
     return widest_dim(lo, hi, k);
   };
-  // is list d read on a level below level L (round robin)?
-  auto needed = [&](int L, int d) -> bool {
-    if (widest) return true;
-    for (int q = L + 1; q <= tree.L - 1; ++q)
-      if (q % k == d) return true;
-    return false;
-  };
+  // per depth jj below the block's root (level l0 + jj): the block's layout,
+  // the round-robin split dimension and the lists read on deeper levels,
+  // computed once
+  __shared__ Local s_lay[kLocalLog + 1];
+  __shared__ uint8_t s_drr[kLocalLog + 1], s_need[kLocalLog + 1];
+  const int depths = tree.L - l0;  // levels l0 .. tree.L - 1
+  if (depths > kLocalLog + 1) {
+    if (threadIdx.x == 0) atomicOr(a.err, ERR_INTERNAL);
+    return;
+  }
+  if (threadIdx.x < (unsigned)depths) {
+    const int jj = threadIdx.x, L = l0 + jj;
+    s_lay[jj] = make_local(tree, L, wk.s_rel << jj, 1u << jj);
+    const int dr = L % k;
+    s_drr[jj] = (uint8_t)dr;
+    uint32_t need = widest ? (1u << k) - 1u : 0u;
+    int md = dr + 1 == k ? 0 : dr + 1;
+    for (int q = L + 1, c = 0; q <= tree.L - 1 && c < k; ++q, ++c) {
+      need |= 1u << md;
+      md = md + 1 == k ? 0 : md + 1;
+    }
+    s_need[jj] = (uint8_t)need;
+  }
+  __syncthreads();
   // mark every item of range r (info word: side << 14 | next-level offset),
   // pin the pivots, record the planes.  The range's items are stored from
   // list position sb on.
   auto info_pass = [&](const Range& r, uint32_t jj, int L, uint32_t slots, uint32_t sb, uint32_t g0,
                        uint32_t gs) {
-    const int drr = L % k;
+    const int drr = s_drr[jj];
     const uint32_t dbase = (1u << jj) - 1;  // local index of the first node at depth jj
     for (uint32_t p = r.p0 + g0; p < r.p1; p += gs) {
-      uint32_t t, side;
-      const uint32_t off = classify(r, p, &t, &side);
-      const uint32_t tl = t - r.tfirst;
+      uint32_t tl, side;
+      const uint32_t off = classify(r, p, &tl, &side);
       const int d = widest ? s_ldim[dbase + tl] : drr;
       const uint32_t it = s_lists[(size_t)slot_of(slots, d) * kLocalCap + (p - r.p0 + sb)];
       if (it >= m || off >= kLocalCap) {
@@ -460,7 +531,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
       }
       if (side == 2) {
         const uint32_t o = s_orig[it];
-        a.perm[ls.off + full_nodes(L) + t] = o;
+        a.perm[ls.off + full_nodes(L) + (wk.s_rel << jj) + tl] = o;
         if (widest) s_lplane[dbase + tl] = coord_of(a.pts, o, a.stride, d);
       }
       s_info[it] = (uint16_t)((side << 14) | off);
@@ -474,9 +545,9 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
   for (uint32_t j = 0;; ++j) {
     const int L = l0 + (int)j;
     if (L > tree.L - 1) break;
-    const LevelLayout yj = LevelLayout::make(tree, L);
     const uint32_t nodes = 1u << j;
     const uint32_t first = wk.s_rel << j;
+    const Local& yj = s_lay[j];
     if (nodes >= (uint32_t)W) {
       // From here every subtree of depth j is finished by one warp.  On every
       // later level the warp keeps its subtree's items from the subtree's
@@ -484,15 +555,14 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
       // warp touches them and warps need no block barrier.
       for (uint32_t tw = warp; tw < nodes; tw += W) {
         uint32_t wslots = slots;
-        const uint32_t sb = yj.seg_start(first + tw) - yj.seg_start(first);
+        const uint32_t sb = l_start(yj, tw);
         for (uint32_t i = 0;; ++i) {
           const int Li = L + (int)i;
           if (Li > tree.L - 1) break;
-          const LevelLayout yi = LevelLayout::make(tree, Li);
           const uint32_t jj = j + i;
           const uint32_t firsti = wk.s_rel << jj;
           const uint32_t cnt = 1u << i;
-          const Range r = make_range(yi, firsti, firsti + (tw << i), cnt);
+          const Range r = make_range(s_lay[jj], tw << i, cnt);
           if (r.p0 >= r.p1) break;
           if (widest) {
             for (uint32_t u = lane; u < cnt; u += 32) {
@@ -510,7 +580,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
           if (Li == tree.L - 1) break;
           const uint32_t lim = r.nb + (r.p1 - r.p0) - cnt;  // end of the range's next-level items
           for (int d = 0; d < k; ++d) {
-            if (!needed(Li, d)) continue;
+            if (!((s_need[jj] >> d) & 1u)) continue;
             const uint16_t* src = s_lists + (size_t)slot_of(wslots, d) * kLocalCap;
             uint16_t* dst = s_lists + (size_t)slot_of(wslots, k) * kLocalCap;
             uint32_t cl = 0, cr = 0;
@@ -540,7 +610,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
       }
       break;
     }
-    const Range r = make_range(yj, first, first, nodes);
+    const Range r = make_range(yj, 0, nodes);
     const uint32_t mj = r.p1;
     if (widest && j > 0) {
       for (uint32_t tl = threadIdx.x; tl < nodes; tl += T) {
@@ -561,7 +631,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     // exchange of the warps' counts, then every item is written
     const uint32_t chunk = ((mj + W * 32 - 1) / (W * 32)) * 32;
     for (int d = 0; d < k; ++d) {
-      if (!needed(L, d)) continue;
+      if (!((s_need[j] >> d) & 1u)) continue;
       const uint16_t* src = s_lists + (size_t)slot_of(slots, d) * kLocalCap;
       uint16_t* dst = s_lists + (size_t)slot_of(slots, k) * kLocalCap;
       uint32_t its[PER], vs[PER];
