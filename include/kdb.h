@@ -216,9 +216,12 @@ KDB_API int64_t kdb_launch_count(void);
  *                         that no block ever writes, so each bounded wait runs
  *                         out after about `arg` microseconds and the build
  *                         returns KDB_ERR_TIMEOUT.
+ *   KDB_FAULT_LOOKBACK_PARTITION  the same for the next build's per-level
+ *                         partition passes only, which run after the first
+ *                         pivots have been placed.
  * Returns the previous fault setting.  Not thread-safe; tests only.
  */
-enum { KDB_FAULT_NONE = 0, KDB_FAULT_ALLOC = 1, KDB_FAULT_LOOKBACK = 2 };
+enum { KDB_FAULT_NONE = 0, KDB_FAULT_ALLOC = 1, KDB_FAULT_LOOKBACK = 2, KDB_FAULT_LOOKBACK_PARTITION = 3 };
 KDB_API int kdb_debug_inject_fault(int fault, int64_t arg);
 
 #ifdef __cplusplus

@@ -198,6 +198,8 @@ struct Plan {
   // presorted lists (k <= 3): one list of 16-byte entries per dimension
   bool use_lists = false;
   size_t o_rows, o_lists, o_lorig, o_piv, o_l0;
+  size_t o_lents = 0;        // list 0 handed to the local finish as entries
+  bool can_direct = false;   // records (stride 4k) can be written from their entries
   size_t o_gather = 0, gather_bytes = 0;  // placement through spare workspace
   size_t rec_hist_off = 0;  // record-sort histograms (in u32, inside the histogram area)
   uint32_t max_nseg = 0;
@@ -377,6 +379,8 @@ void make_plan(Plan& P) {
   P.o_lorig = take(G ? T * 4 * P.k : 0);             // lists handed to the local finish
   P.o_piv = take(L ? (size_t)kLiftMax * std::max<uint32_t>(P.max_nseg, 1) * 8 : 0);  // last 3 levels
   P.o_l0 = take(G && P.sets.size() > 1 ? T * 16 : 0);  // level-0 array of several sets
+  P.can_direct = L && P.stride == 4 * P.k;
+  P.o_lents = take(P.can_direct && G ? T * 16 : 0);
   P.bytes = o;
   // workspace that is dead once the local finish has run, one contiguous
   // range: the placement may gather the records into it
@@ -479,10 +483,12 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   if (out_dim || widest) KDB_CK(cudaMemsetAsync(dims, 0, T, st));
 
   const uint64_t wait_ns =
-      g_fault == KDB_FAULT_LOOKBACK ? (uint64_t)std::max<int64_t>(g_fault_arg, 1) * 1000ull
-                                    : kDefaultWaitNs;
+      (g_fault == KDB_FAULT_LOOKBACK || g_fault == KDB_FAULT_LOOKBACK_PARTITION)
+          ? (uint64_t)std::max<int64_t>(g_fault_arg, 1) * 1000ull
+          : kDefaultWaitNs;
   const bool fault_lb = g_fault == KDB_FAULT_LOOKBACK;
-  if (fault_lb) g_fault = KDB_FAULT_NONE;
+  const bool fault_part = g_fault == KDB_FAULT_LOOKBACK_PARTITION;
+  if (fault_lb || fault_part) g_fault = KDB_FAULT_NONE;
   int g = 0;  // pass counter within the build
   auto ctl = [&](uint32_t n, int shift, const uint32_t* h) {
     PassCtl c{};
@@ -609,6 +615,11 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   // in its dimension, so it is advanced lazily, several levels in one pass,
   // just before those levels (lat[d]: the level list d is sorted for).
   const bool lazy = P.use_lists && P.mode == KDB_SPLIT_ROUND_ROBIN && P.sets.size() == 1;
+  // Records without payload are written straight to their nodes from the
+  // entries (which hold every coordinate bit) as the nodes are pinned; the
+  // caller's array is not read after the prepass, and no placement is left.
+  const bool direct = P.can_direct && g_placement.load() == KDB_PLACEMENT_AUTO;
+  uint4* lents = direct ? at<uint4>(ws, P.o_lents) : nullptr;
   int lat[3] = {0, 0, 0};
   auto level_ctx = [&](int l) {
     LevelCtx x{};
@@ -627,6 +638,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   // handoff), with the pivots of levels p .. q-1
   auto lift = [&](int d, int p, int q, bool handoff) -> cudaError_t {
     PassCtl c = ctl(P.items[p], 0, nullptr);
+    if (fault_part) c.wait_epoch = c.epoch + 0x10000000u;
     PartArgs pa{};
     pa.x = level_ctx(p);
     pa.act_out = q < levels ? d_act + P.act_off[q] : nullptr;
@@ -635,6 +647,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     pa.in = lcur[d];
     pa.out_next = lnext[d];
     pa.out_lorig = lorig;
+    pa.out_lents = lents;
     for (int e = 0; e < q - p; ++e) pa.piv[e] = piv_ring[(p + e) % kLiftMax];
     pa.dims = dims;
     pa.k = k;
@@ -732,6 +745,8 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       pv.dims = dims;
       pv.k = k;
       pv.mode = P.mode;
+      pv.pts_out = direct ? pts : nullptr;
+      pv.stride = P.stride;
       {
         Prof pf(K_PIVOT, (double)(x.nact << l) * 20, 1, st);
         KDB_CK(launch_pivots(pv, st));
@@ -830,7 +845,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       wa.pts = pts;
       wa.k = k;
       wa.stride = P.stride;
-      wa.perm = perm;
+      wa.perm = direct ? nullptr : perm;  // direct: the pivot's record is already at its node
       wa.boxes_in = (l & 1) ? boxB : boxA;
       wa.boxes_out = (l & 1) ? boxA : boxB;
       wa.dims = dims;
@@ -865,6 +880,8 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     la.dims = dims;
     la.perm = perm;
     la.err = err;
+    la.lents = lents;
+    la.pts_out = direct ? pts : nullptr;
     Prof pf(K_LOCAL, (double)T * (4.0 + 4.0 * k + 4.0), 1, st);
     KDB_CK(launch_local_finish(la, st));
   }
@@ -881,7 +898,11 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   pm.perm = perm;
   pm.stage = at<unsigned char>(ws, P.o_stage);
   pm.err = err;
-  if (g_placement.load() == KDB_PLACEMENT_AUTO && (size_t)T * P.stride <= P.gather_bytes) {
+  if (direct) {
+    // every record is at its node already; put the input back if the build failed
+    Prof pf(K_PLACEMENT, 0.0, 1, st);
+    KDB_CK(launch_restore(pts, ents0, T, k, err, st));
+  } else if (g_placement.load() == KDB_PLACEMENT_AUTO && (size_t)T * P.stride <= P.gather_bytes) {
     Prof pf(K_PLACEMENT, (double)T * (4.0 + 4.0 * P.stride), 2, st);
     KDB_CK(launch_place_gather(pm, at<unsigned char>(ws, P.o_gather), sms, st));
   } else {

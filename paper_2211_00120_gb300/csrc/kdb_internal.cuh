@@ -142,6 +142,16 @@ __host__ __device__ inline uint32_t float_key(uint32_t bits) {
 __host__ __device__ inline uint32_t key_to_float_bits(uint32_t key) {
   return key ^ ((key & 0x80000000u) ? 0x80000000u : 0xFFFFFFFFu);
 }
+#ifdef __CUDACC__
+// The record of a point from its entry (k <= 3 coordinate keys, no payload):
+// the key map is a bijection, so the bits are the input's.
+__device__ inline void write_record_from_entry(unsigned char* rec, const uint4& e, int k) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(rec);
+  r[0] = key_to_float_bits(e.x);
+  if (k > 1) r[1] = key_to_float_bits(e.y);
+  if (k > 2) r[2] = key_to_float_bits(e.z);
+}
+#endif
 
 #ifdef __CUDACC__
 __device__ inline uint64_t ld_relaxed_u64(const uint64_t* p) {

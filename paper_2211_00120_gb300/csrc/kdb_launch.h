@@ -53,6 +53,8 @@ struct PivotArgs {
   uint32_t* perm;           // out: node -> original index
   const uint8_t* dims;      // widest: split dimension per node
   int k, mode;
+  unsigned char* pts_out;   // records written directly at their nodes (stride = 4k), or nullptr
+  int stride;
 };
 // One partition pass advances a list by 1..kLiftMax levels at once.
 constexpr int kLiftMax = 3;
@@ -66,6 +68,7 @@ struct PartArgs {
   uint4* out_next;          // the list on level p + b
   uint32_t* out_lorig;      // original indices for the local finish (sets leaving),
                             // one array of `total` per list
+  uint4* out_lents;         // if set: list 0 is handed over as whole entries here
   const uint2* piv[kLiftMax];  // pivots (key, index) of levels p .. p + b - 1
   const uint8_t* dims;
   int k, mode, dlist;
@@ -106,6 +109,7 @@ struct LocalArgs {
   const uint32_t* vals_local;   // original indices (rank arrays gathered), or
   const uint32_t* lorig;        // k <= 3: per dimension the original indices of the
                                 // items leaving the global levels, in list order
+  const uint4* lents;           // if set: list 0 as whole entries (replaces lorig[0])
   const uint4* rows;            // entries in input order (sets local from level 0)
   const uint32_t* ranks;
   uint32_t total;
@@ -117,6 +121,7 @@ struct LocalArgs {
   uint8_t* dims;
   uint32_t* perm;
   uint32_t* err;
+  unsigned char* pts_out;    // records written directly at their nodes (stride = 4k), or nullptr
 };
 size_t local_smem_bytes(int k);
 cudaError_t launch_local_finish(const LocalArgs& a, cudaStream_t st);
@@ -241,6 +246,10 @@ struct PermuteArgs {
 };
 cudaError_t launch_permute(const PermuteArgs& a, int num_sms, cudaStream_t st);
 cudaError_t launch_place_gather(const PermuteArgs& a, unsigned char* tmp, int num_sms, cudaStream_t st);
+// Records of stride 4k rebuilt from their entries (input order) if the build
+// failed after writing records directly at their nodes.
+cudaError_t launch_restore(unsigned char* pts, const uint4* ents, uint32_t total, int k, const uint32_t* err,
+                           cudaStream_t st);
 cudaError_t launch_unmark(const uint32_t* perm, int32_t* out, uint32_t total, cudaStream_t st);
 
 cudaError_t launch_validate(const unsigned char* pts, uint32_t n, int k, int stride, int mode,

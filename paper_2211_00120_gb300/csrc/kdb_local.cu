@@ -335,11 +335,12 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     // indices, already in order.  Local id = position in list 0; the other
     // lists are translated through a hash table original index -> local id.
     const uint32_t* lo0 = a.lorig + ls.off + start0;
+    const uint4* le0 = a.lents ? a.lents + ls.off + start0 : nullptr;  // list 0 as entries
     constexpr uint32_t HM = 2 * kLocalCap - 1;
     for (uint32_t i = threadIdx.x; i < 2 * kLocalCap; i += T) s_hkey[i] = 0xFFFFFFFFu;
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < m; i += T) {
-      uint32_t o = lo0[i];
+      uint32_t o = le0 ? le0[i].w : lo0[i];
       if (o >= a.total) {
         s_bad = 1;
         o = 0;
@@ -472,6 +473,9 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
   __syncthreads();
 
   const bool widest = a.mode == 1;
+  // records written directly at their nodes: the entry of each local id
+  const uint4* ent_of = nullptr;
+  if (a.pts_out) ent_of = l0 > 0 ? a.lents + ls.off + start0 : a.rows + ls.off;
   // split dimension of node tl (index among the block's nodes at depth jj):
   // widest side of its domain, the root's domain clipped by the planes of
   // its ancestors inside the block (Sec. 6)
@@ -531,8 +535,16 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
       }
       if (side == 2) {
         const uint32_t o = s_orig[it];
-        a.perm[ls.off + full_nodes(L) + (wk.s_rel << jj) + tl] = o;
-        if (widest) s_lplane[dbase + tl] = coord_of(a.pts, o, a.stride, d);
+        const uint32_t node = ls.off + full_nodes(L) + (wk.s_rel << jj) + tl;
+        a.perm[node] = o;
+        if (ent_of) {  // the record goes straight to its node
+          const uint4 e = ent_of[it];
+          write_record_from_entry(a.pts_out + (uint64_t)node * a.stride, e, k);
+          if (widest)
+            s_lplane[dbase + tl] = __uint_as_float(key_to_float_bits(d == 0 ? e.x : (d == 1 ? e.y : e.z)));
+        } else if (widest) {
+          s_lplane[dbase + tl] = coord_of(a.pts, o, a.stride, d);
+        }
       }
       s_info[it] = (uint16_t)((side << 14) | off);
     }

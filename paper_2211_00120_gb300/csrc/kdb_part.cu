@@ -56,6 +56,7 @@ __global__ void pivot_kernel(PivotArgs a) {
   const uint4 ent = a.lists[d][pos];
   a.piv[gid] = make_uint2(comp(ent, d), ent.w);
   a.perm[si.off + node] = ent.w;
+  if (a.pts_out) write_record_from_entry(a.pts_out + (uint64_t)(si.off + node) * a.stride, ent, a.k);
 }
 
 // ---------------------------------------------------------------------------
@@ -320,6 +321,7 @@ __global__ void __launch_bounds__(PT, 6) partition_kernel(PartArgs a) {
     }
     const uint4 en = s_in[wbase + i * 32 + lane];
     if (S.mode == 0) a.out_next[pos] = en;
+    else if (a.out_lents && a.dlist == 0) a.out_lents[pos] = en;
     else a.out_lorig[(size_t)a.dlist * a.total + pos] = en.w;
   }
 }

@@ -514,6 +514,15 @@ __global__ void place_copy_back_kernel(PermuteArgs a, const unsigned char* tmp, 
   }
 }
 
+// After a failed build that wrote records at their nodes: put every record
+// back from its entry, so the caller's array is as it was.
+__global__ void restore_kernel(unsigned char* pts, const uint4* ents, uint32_t total, int k,
+                               const uint32_t* err) {
+  if (*reinterpret_cast<const volatile uint32_t*>(err) == 0) return;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
+    write_record_from_entry(pts + (uint64_t)i * (4 * k), ents[i], k);
+}
+
 __global__ void unmark_kernel(const uint32_t* perm, int32_t* out, uint32_t total) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < total) out[i] = (int32_t)(perm[i] & ~kMark);
@@ -618,6 +627,15 @@ cudaError_t launch_place_gather(const PermuteArgs& a, unsigned char* tmp, int nu
   const uint64_t want = (bytes / 16 + kThreads - 1) / kThreads;
   const uint32_t grid = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(want, 1), (uint64_t)num_sms * 8);
   place_copy_back_kernel<<<grid, kThreads, 0, st>>>(a, tmp, bytes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restore(unsigned char* pts, const uint4* ents, uint32_t total, int k, const uint32_t* err,
+                           cudaStream_t st) {
+  if (total == 0) return cudaSuccess;
+  // a small grid: the kernel usually finds no error and returns at once
+  const uint32_t grid = std::min<uint32_t>((total + kThreads - 1) / kThreads, 1024);
+  restore_kernel<<<grid, kThreads, 0, st>>>(pts, ents, total, k, err);
   return cudaGetLastError();
 }
 

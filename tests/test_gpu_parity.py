@@ -277,3 +277,23 @@ def test_placement_modes_batched(placement):
         if hi > lo:
             want, _ = oracle.build(pts[lo:hi], 3, RR)
             assert np.array_equal(got[lo:hi].view(np.uint32), want.view(np.uint32)), f"set {b}"
+
+
+@pytest.mark.parametrize("placement", [kdb.PLACEMENT_AUTO, kdb.PLACEMENT_IN_PLACE])
+def test_failure_after_first_pivots_leaves_records_untouched(placement):
+    """A partition pass times out after the root's record was already written
+    at its node (records without payload go straight to their nodes): the
+    build reports the timeout, the caller's array is exactly the input again,
+    and the next build works."""
+    pts = synth.uniform(100003, 3, seed=61)
+    d = torch.from_numpy(pts).cuda()
+    prev = kdb.kdb_set_placement(placement)
+    try:
+        kdb.kdb_debug_inject_fault(kdb.FAULT_LOOKBACK_PARTITION, 200)
+        with pytest.raises(kdb.KdbError) as e:
+            kdb.kdb_build(d, 3, RR)
+        assert e.value.code == kdb.ERR_TIMEOUT
+        assert np.array_equal(d.cpu().numpy().view(np.uint32), pts.view(np.uint32))
+        assert_same(pts, 3, RR)
+    finally:
+        kdb.kdb_set_placement(prev)
