@@ -649,11 +649,13 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
       uint32_t its[PER], vs[PER];
       uint32_t cl = 0, cr = 0;
       const uint32_t c0 = (uint32_t)warp * chunk;
+      const int rounds = (int)(chunk / 32);  // block-uniform
 #pragma unroll
       for (int q = 0; q < PER; ++q) {
+        if (q >= rounds) break;
         const uint32_t p = c0 + (uint32_t)q * 32 + lane;
         uint32_t it = 0, v = 3u << 14;
-        if ((uint32_t)q * 32 < chunk && p < mj) {
+        if (p < mj) {
           it = src[p];
           v = s_info[it];
         }
@@ -672,6 +674,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
       const uint32_t wl = before & 0xFFFFu, wr = before >> 16;
 #pragma unroll
       for (int q = 0; q < PER; ++q) {
+        if (q >= rounds) break;
         const uint32_t side = vs[q] >> 14;
         if (side > 1) continue;
         const uint32_t np = (vs[q] & 0x3FFFu) + (side == 0 ? wl : wr) + (its[q] >> 16);
