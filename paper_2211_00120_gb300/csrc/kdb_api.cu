@@ -349,9 +349,11 @@ void make_plan(Plan& P) {
   const size_t box_bytes = P.mode == KDB_SPLIT_WIDEST_EXTENT ? (size_t)P.max_boxes * 2 * P.k * 4 : 0;
   P.o_boxA = take(box_bytes);
   P.o_boxB = take(box_bytes);
-  const size_t tiles =
-      (std::max<uint64_t>(T, P.max_items) + std::min(kSortTile, kSegTile) - 1) /
-      std::min(kSortTile, kSegTile);
+  // look-back words: 256 per tile of the radix passes (the smallest of their
+  // tiles), kLiftBins per partition tile
+  const uint64_t min_tile =
+      std::min<uint64_t>(std::min(kSortTile, kSegTile), (uint64_t)rec_sort_tile());
+  const size_t tiles = (std::max<uint64_t>(T, P.max_items) + min_tile - 1) / min_tile;
   const size_t part_tiles = (std::max<uint64_t>(T, P.max_items) + kPartTile - 1) / kPartTile;
   P.o_status = take(std::max(tiles * kRadixBins, part_tiles * kLiftBins) * 8);
   P.o_hist = take(hist_words * 4);
@@ -501,6 +503,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     c.wait_epoch = fault_lb ? (uint32_t)(g + 1) + 0x10000000u : c.epoch;
     c.wait_ns = wait_ns;
     c.err = err;
+    c.status_words = (P.o_hist - P.o_status) / 8;
     ++g;
     return c;
   };
@@ -661,6 +664,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     pa.epoch = c.epoch;
     pa.wait_epoch = c.wait_epoch;
     pa.wait_ns = c.wait_ns;
+    pa.status_words = c.status_words;
     Prof pf(K_PARTITION, (double)P.items[p] * 32, 1, st);
     cudaError_t e = launch_partition(pa, st);
     std::swap(lcur[d], lnext[d]);

@@ -77,9 +77,11 @@ struct PartArgs {
   uint32_t* ticket;
   uint32_t epoch, wait_epoch;
   uint64_t wait_ns;
+  uint64_t status_words;    // capacity of status
 };
 size_t partition_smem();
 size_t rec_sort_smem();
+uint32_t rec_sort_tile();  // entries per record-sort tile (one look-back word per digit each)
 cudaError_t launch_gather_level0(const ListBuildArgs& a, cudaStream_t st);
 cudaError_t launch_rec_hist(const RecHistArgs& a, cudaStream_t st);
 cudaError_t launch_rec_sort_pass(const uint4* in, uint4* out, const PassCtl& c, const LevelCtx& x,

@@ -83,18 +83,18 @@ __global__ void __launch_bounds__(256) rec_hist_kernel(RecHistArgs a) {
 // their slot order is staged for the write-out, which reads the records from
 // shared memory in digit order and writes each digit's run contiguously.
 constexpr int RT = 256;  // threads of a record-sort block
-constexpr int RI = 15;   // entries per thread
+constexpr int RI = 13;   // entries per thread: 3328 a tile, three blocks per SM
 constexpr int RTILE = RT * RI;
 constexpr int RW = RT / 32;
 
-__global__ void __launch_bounds__(RT, 2)
+__global__ void __launch_bounds__(RT, 3)
     rec_sort_pass(const uint4* __restrict__ in, uint4* __restrict__ out, PassCtl c, LevelCtx x,
                   const uint32_t* __restrict__ seg_hist, int d) {
   constexpr int BINS = 2 * kRadix;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint4* s_rec = reinterpret_cast<uint4*>(smem_raw);
   uint16_t* s_slot = reinterpret_cast<uint16_t*>(s_rec + RTILE);
-  uint16_t* s_whist = s_slot + RTILE;  // [BINS][RW]
+  uint16_t* s_whist = s_slot + RTILE;  // [RW][BINS]: a warp's digits on distinct banks
   __shared__ uint32_t s_gbase[BINS];
   __shared__ uint32_t s_toff[BINS];
   __shared__ uint64_t s_scan64[RW];
@@ -106,8 +106,14 @@ __global__ void __launch_bounds__(RT, 2)
   if (tid == 0) {
     s_abort = *reinterpret_cast<volatile uint32_t*>(c.err) != 0u;
     if (!s_abort) {
-      const uint32_t tile = atomicAdd(c.ticket, 1u);
-      s_tile = tile;
+      s_tile = atomicAdd(c.ticket, 1u);
+      if ((uint64_t)(s_tile + 1) * kRadix > c.status_words) {  // the last tiles: no tile waits on them
+        atomicOr(c.err, ERR_INTERNAL);
+        s_abort = 1;
+      }
+    }
+    if (!s_abort) {
+      const uint32_t tile = s_tile;
       const uint32_t tb = tile * (uint32_t)RTILE;
       const uint32_t tn = c.n - tb < (uint32_t)RTILE ? c.n - tb : (uint32_t)RTILE;
       mbar_init(&s_bar, 1);
@@ -178,10 +184,10 @@ __global__ void __launch_bounds__(RT, 2)
     if (ok) bin = ((p >= bpos) ? (uint32_t)kRadix : 0u) | ((comp(s_rec[p], d) >> c.shift) & 255u);
     const uint32_t peers = __match_any_sync(0xffffffffu, bin);
     uint32_t before = 0;
-    if (ok) before = s_whist[bin * RW + warp];
+    if (ok) before = s_whist[warp * BINS + bin];
     __syncwarp();
     rnk[i] = (uint16_t)(before + __popc(peers & lt));
-    if (ok && (peers & lt) == 0) s_whist[bin * RW + warp] = (uint16_t)(before + __popc(peers));
+    if (ok && (peers & lt) == 0) s_whist[warp * BINS + bin] = (uint16_t)(before + __popc(peers));
     bins[i] = (uint16_t)bin;
     __syncwarp();
   }
@@ -190,9 +196,9 @@ __global__ void __launch_bounds__(RT, 2)
   if (tid < kRadix) {
 #pragma unroll
     for (int w = 0; w < RW; ++w) {
-      const uint32_t ta = s_whist[tid * RW + w], tb2 = s_whist[(kRadix + tid) * RW + w];
-      s_whist[tid * RW + w] = (uint16_t)cA;
-      s_whist[(kRadix + tid) * RW + w] = (uint16_t)cB;
+      const uint32_t ta = s_whist[w * BINS + tid], tb2 = s_whist[w * BINS + kRadix + tid];
+      s_whist[w * BINS + tid] = (uint16_t)cA;
+      s_whist[w * BINS + kRadix + tid] = (uint16_t)cB;
       cA += ta;
       cB += tb2;
     }
@@ -222,7 +228,7 @@ __global__ void __launch_bounds__(RT, 2)
     const uint32_t p = wbase + i * 32 + lane;
     if (p < tn) {
       const uint32_t bin = bins[i];
-      s_slot[s_toff[bin] + s_whist[bin * RW + warp] + rnk[i]] = (uint16_t)p;
+      s_slot[s_toff[bin] + s_whist[warp * BINS + bin] + rnk[i]] = (uint16_t)p;
     }
   }
   if (tid < kRadix) {
@@ -256,6 +262,7 @@ __global__ void __launch_bounds__(RT, 2)
 }  // namespace
 
 size_t rec_sort_smem() { return (size_t)RTILE * 18 + (size_t)2 * kRadix * RW * 2; }
+uint32_t rec_sort_tile() { return (uint32_t)RTILE; }
 
 cudaError_t launch_gather_level0(const ListBuildArgs& a, cudaStream_t st) {
   if (a.items == 0) return cudaSuccess;

@@ -40,6 +40,7 @@ struct PassCtl {
   uint32_t wait_epoch;    // epoch waited for (== epoch unless a fault is injected)
   uint64_t wait_ns;       // bound on one look-back wait
   uint32_t* err;          // device status word
+  uint64_t status_words;  // capacity of status: a tile whose words lie beyond it does nothing
 };
 
 // look-back word: [63:62] flag, [61:32] epoch, [31:0] count
@@ -159,7 +160,14 @@ __global__ void __launch_bounds__(THREADS)
     // after any device error the inputs may be garbage: do nothing.  A block
     // that leaves here has taken no ticket, so no tile ever waits on it.
     s_abort = *reinterpret_cast<volatile uint32_t*>(c.err) != 0u;
-    if (!s_abort) s_tile = atomicAdd(c.ticket, 1u);
+    if (!s_abort) {
+      s_tile = atomicAdd(c.ticket, 1u);
+      // the last tiles: no tile waits on them
+      if ((uint64_t)(s_tile + 1) * kRadix > c.status_words) {
+        atomicOr(c.err, ERR_INTERNAL);
+        s_abort = 1;
+      }
+    }
   }
   for (int i = tid; i < WARPS * kRadix; i += THREADS) (&s_whist[0][0])[i] = 0;
   __syncthreads();

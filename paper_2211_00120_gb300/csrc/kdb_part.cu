@@ -178,8 +178,14 @@ __global__ void __launch_bounds__(PT, 6) partition_kernel(PartArgs a) {
   if (tid == 0) {
     s_abort = *reinterpret_cast<volatile uint32_t*>(x.err) != 0u;
     if (!s_abort) {
-      const uint32_t tile = atomicAdd(a.ticket, 1u);
-      s_tile = tile;
+      s_tile = atomicAdd(a.ticket, 1u);
+      if ((uint64_t)(s_tile + 1) * kLiftBins > a.status_words) {  // the last tiles: no tile waits on them
+        atomicOr(x.err, ERR_INTERNAL);
+        s_abort = 1;
+      }
+    }
+    if (!s_abort) {
+      const uint32_t tile = s_tile;
       const uint32_t tb = tile * (uint32_t)PTILE;
       const uint32_t tn = a.n - tb < (uint32_t)PTILE ? a.n - tb : (uint32_t)PTILE;
       mbar_init(&s_bar, 1);
@@ -203,11 +209,7 @@ __global__ void __launch_bounds__(PT, 6) partition_kernel(PartArgs a) {
   }
   for (int i = tid; i < PW * NB; i += PT) (&s_wcnt[0][0])[i] = 0;
   __syncthreads();
-  if (s_abort == 1) return;
-  if (s_abort == 2) {
-    if (tid == 0) atomicOr(x.err, ERR_INTERNAL);
-    return;
-  }
+  if (s_abort == 1) return;  // no copy was issued
   const uint32_t tile = s_tile;
   const uint32_t tb = tile * (uint32_t)PTILE;
   const uint32_t tn = a.n - tb < (uint32_t)PTILE ? a.n - tb : (uint32_t)PTILE;
@@ -229,6 +231,10 @@ __global__ void __launch_bounds__(PT, 6) partition_kernel(PartArgs a) {
   }
   __syncthreads();
   if (s_abort == 1) return;
+  if (s_abort == 2) {  // the copy has landed; nothing else is in flight
+    if (tid == 0) atomicOr(x.err, ERR_INTERNAL);
+    return;
+  }
   const uint32_t bpos = s_bpos;
   const bool hasB = bpos < tn;
 

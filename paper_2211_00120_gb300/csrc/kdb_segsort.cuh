@@ -133,8 +133,14 @@ __global__ void __launch_bounds__(THREADS, MINB)
   if (tid == 0) {
     s_abort = *reinterpret_cast<volatile uint32_t*>(c.err) != 0u;
     if (!s_abort) {
-      const uint32_t tile = atomicAdd(c.ticket, 1u);
-      s_tile = tile;
+      s_tile = atomicAdd(c.ticket, 1u);
+      if ((uint64_t)(s_tile + 1) * kRadix > c.status_words) {  // the last tiles: no tile waits on them
+        atomicOr(c.err, ERR_INTERNAL);
+        s_abort = 1;
+      }
+    }
+    if (!s_abort) {
+      const uint32_t tile = s_tile;
       const uint32_t tb = tile * (uint32_t)TILE;
       const uint32_t tn = c.n - tb < (uint32_t)TILE ? c.n - tb : (uint32_t)TILE;
       // 1. the tile's keys and values to shared memory by bulk copy (whole
