@@ -28,7 +28,7 @@ struct PassCtl;
 // (order-preserving keys of coordinates 0..2, original index), one list per
 // dimension.
 constexpr int kPartThreads = 128;
-constexpr int kPartItems = 15;
+constexpr int kPartItems = 13;
 constexpr int kPartTile = kPartThreads * kPartItems;  // < 2^13 - 1: <= two segments a tile
 struct ListBuildArgs {      // level-0 array of several sets
   LevelCtx x;               // level 0
