@@ -177,6 +177,61 @@ def cpu_baseline(workload: str, target_s: float = 15.0):
                       f"({desc}); oracle single-threaded, {total:.1f} s"}
 
 
+def batched_vs_serial(sets: int = 4096, lo: int = 100, hi: int = 1_000_000, seed: int = 3,
+                      steps: int = 3):
+    """Many independent float3 sets (sizes log-uniform in [lo, hi], uniform
+    points, round robin) built by one kdb_build_batched call against one
+    kdb_build call per set, on the same device-resident array: builds/s of
+    each, and whether the outputs are identical."""
+    import torch
+    from paper_2211_00120_gb300 import kdb
+    sizes = synth.lognormal_sizes(sets, lo, hi, seed=seed)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(offs[-1])
+    src = torch.from_numpy(synth.uniform(n, 3, seed=seed)).cuda()
+    work = torch.empty_like(src)
+    stream = torch.cuda.current_stream()
+    off_list = offs.tolist()
+
+    def batched():
+        kdb.kdb_build_batched(work, off_list, 3, kdb.ROUND_ROBIN)
+
+    def serial():
+        for b in range(sets):
+            if off_list[b + 1] > off_list[b]:
+                kdb.kdb_build(work[off_list[b]:off_list[b + 1]], 3, kdb.ROUND_ROBIN)
+
+    def timed(fn):
+        times = []
+        for _ in range(steps):
+            work.copy_(src)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return statistics.median(times)
+
+    work.copy_(src)
+    batched()  # warm-up (pool, first launches)
+    out_b = work.clone()
+    work.copy_(src)
+    serial()
+    equal = bool(torch.equal(work.view(torch.int32), out_b.view(torch.int32)))
+    tb = timed(batched)
+    ts = timed(serial)
+    del src, work, out_b
+    torch.cuda.empty_cache()
+    return {"workload": f"{sets} float3 sets, sizes log-uniform in [{lo}, {hi}] (seed {seed}), "
+                        f"{n} points uniform in [0,1)^3, round robin",
+            "points": n, "batched_ms": tb, "serial_ms": ts,
+            "batched_builds_per_s": sets / (tb / 1000.0), "serial_builds_per_s": sets / (ts / 1000.0),
+            "batched_mpts_per_s": n / (tb / 1000.0) / 1e6, "speedup": ts / tb,
+            "equal_output": equal, "steps": steps,
+            "timing": "CUDA events around the whole call (serial: 4096 synchronous kdb_build calls)"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -219,6 +274,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched vs serial measurement")
     ap.add_argument("--points", type=int, default=0,
                     help="override the workload's number of points (small profiling cases)")
     ap.add_argument("--profile-only", action="store_true",
@@ -346,6 +403,12 @@ def main():
                "h2d_bytes_per_step": n * stride, "d2h_bytes_per_step": n * stride,
                "ms_per_step": e_ms}
 
+    batched = None
+    if not args.no_batched:
+        del src, work
+        torch.cuda.empty_cache()
+        batched = batched_vs_serial()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)
@@ -361,7 +424,7 @@ def main():
                            "l2": "input 1.2+ GB > L2, restored by a device copy before each step"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "kernel_ms_per_step": kernel_ms,
-                "placement_in_place": in_place}
+                "placement_in_place": in_place, "batched": batched}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
