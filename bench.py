@@ -178,26 +178,34 @@ def cpu_baseline(workload: str, target_s: float = 15.0):
 
 
 def batched_vs_serial(sets: int = 4096, lo: int = 100, hi: int = 1_000_000, seed: int = 3,
-                      steps: int = 3):
+                      steps: int = 3, world: int = 1, rank: int = 0, dist=None):
     """Many independent float3 sets (sizes log-uniform in [lo, hi], uniform
     points, round robin) built by one kdb_build_batched call against one
     kdb_build call per set, on the same device-resident array: builds/s of
-    each, and whether the outputs are identical."""
+    each, and whether the outputs are identical.  With several ranks every
+    rank takes its LPT share of the sets (no exchange); times are the max
+    over ranks."""
     import torch
-    from paper_2211_00120_gb300 import kdb
-    sizes = synth.lognormal_sizes(sets, lo, hi, seed=seed)
+    from paper_2211_00120_gb300 import kdb, shard
+    sizes_all = synth.lognormal_sizes(sets, lo, hi, seed=seed)
+    offs_all = np.concatenate([[0], np.cumsum(sizes_all)]).astype(np.int64)
+    n_all = int(offs_all[-1])
+    mine = shard.lpt_shards([int(v) for v in sizes_all], world)[rank]
+    sizes = sizes_all[mine]
     offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
-    n = int(offs[-1])
-    src = torch.from_numpy(synth.uniform(n, 3, seed=seed)).cuda()
+    rows = [synth.uniform_rows(int(offs_all[b]), int(sizes_all[b]), 3, seed=seed) for b in mine]
+    host = np.concatenate(rows) if rows else np.zeros((0, 3), np.float32)
+    src = torch.from_numpy(host).cuda()
     work = torch.empty_like(src)
     stream = torch.cuda.current_stream()
     off_list = offs.tolist()
+    nsets = len(mine)
 
     def batched():
         kdb.kdb_build_batched(work, off_list, 3, kdb.ROUND_ROBIN)
 
     def serial():
-        for b in range(sets):
+        for b in range(nsets):
             if off_list[b + 1] > off_list[b]:
                 kdb.kdb_build(work[off_list[b]:off_list[b + 1]], 3, kdb.ROUND_ROBIN)
 
@@ -223,8 +231,14 @@ def batched_vs_serial(sets: int = 4096, lo: int = 100, hi: int = 1_000_000, seed
     ts = timed(serial)
     del src, work, out_b
     torch.cuda.empty_cache()
+    if dist is not None:
+        t = torch.tensor([tb, ts, 0.0 if equal else 1.0], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tb, ts, equal = float(t[0]), float(t[1]), float(t[2]) == 0.0
+    n = n_all
     return {"workload": f"{sets} float3 sets, sizes log-uniform in [{lo}, {hi}] (seed {seed}), "
                         f"{n} points uniform in [0,1)^3, round robin",
+            "ranks": world, "sharding": "LPT by points x levels, no exchange" if world > 1 else None,
             "points": n, "batched_ms": tb, "serial_ms": ts,
             "batched_builds_per_s": sets / (tb / 1000.0), "serial_builds_per_s": sets / (ts / 1000.0),
             "batched_mpts_per_s": n / (tb / 1000.0) / 1e6, "speedup": ts / tb,
@@ -407,7 +421,7 @@ def main():
     if not args.no_batched:
         del src, work
         torch.cuda.empty_cache()
-        batched = batched_vs_serial()
+        batched = batched_vs_serial(world=world, rank=rank, dist=dist)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

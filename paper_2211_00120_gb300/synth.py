@@ -73,6 +73,11 @@ def uniform(n: int, k: int = 3, seed: int = 0, stream: int = 0) -> np.ndarray:
     return out
 
 
+def uniform_rows(start: int, n: int, k: int = 3, seed: int = 0, stream: int = 0) -> np.ndarray:
+    """Rows [start, start + n) of uniform(., k, seed, stream), drawn alone."""
+    return unit_f32(u64(seed, stream, n * k, start * k)).reshape(n, k)
+
+
 def _gauss(seed: int, stream: int, n: int) -> np.ndarray:
     """n standard normals (float64) by Box-Muller."""
     a = u64(seed, stream, n)
