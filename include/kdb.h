@@ -158,6 +158,44 @@ KDB_API kdb_status kdb_build_noalloc(void* d_points, int64_t n, int k, int strid
                                      kdb_split_mode mode, kdb_stream_t stream);
 
 /*
+ * Plans: a build prepared once and enqueued many times, for repeated builds
+ * of the same shape and for CUDA-graph capture.  The paper has no
+ * counterpart; this is a deployment convenience.
+ *
+ * kdb_plan_create -- plans builds of num_sets sets laid out as for
+ * kdb_build_batched (h_offsets: host int64[num_sets+1], h_offsets[0] = 0,
+ * non-decreasing; num_sets = 1 and {0, N} for a single tree), with k,
+ * stride_bytes and mode as for kdb_build.  Allocates the plan's device
+ * workspace (kdb_plan_workspace_bytes) on the current device, copies its
+ * tables there, and runs one build on zero-filled points so that every
+ * kernel is loaded and configured.  Synchronous.  *out_plan is NULL on error.
+ *
+ * kdb_plan_enqueue -- enqueues one build of d_points (device, in/out, the
+ * planned layout) on `stream` and returns without synchronising.  It
+ * allocates nothing, synchronises nothing and reads no host memory: only
+ * kernels and memsets on `stream`, so it may be captured into a CUDA graph
+ * (in any capture mode) and the graph replayed on new point data.  The
+ * current device must be the plan's.  Builds of one plan share its
+ * workspace: enqueue them in one stream order.  Returns
+ * KDB_ERR_INVALID_ARGUMENT or KDB_ERR_CUDA for launch problems; device
+ * errors (NaN, timeouts) are read with kdb_plan_status.  On a device error
+ * the records are left as they were (as for kdb_build).
+ *
+ * kdb_plan_status -- synchronises `stream` and returns the device status of
+ * the plan's last build enqueued before that point.
+ *
+ * kdb_plan_destroy -- frees the plan (NULL is ignored); the caller makes
+ * sure no enqueued build of it is still running.
+ */
+typedef struct kdb_plan_st* kdb_plan;
+KDB_API kdb_status kdb_plan_create(const int64_t* h_offsets, int num_sets, int k, int stride_bytes,
+                                   kdb_split_mode mode, kdb_plan* out_plan);
+KDB_API kdb_status kdb_plan_enqueue(kdb_plan plan, void* d_points, kdb_stream_t stream);
+KDB_API kdb_status kdb_plan_status(kdb_plan plan, kdb_stream_t stream);
+KDB_API size_t kdb_plan_workspace_bytes(kdb_plan plan);
+KDB_API void kdb_plan_destroy(kdb_plan plan);
+
+/*
  * kdb_set_placement -- how the final placement moves the records into level
  * order (Sec. 3.2, 7.1).  Both settings give identical output.
  *   KDB_PLACEMENT_AUTO      (default) when the part of the build's workspace

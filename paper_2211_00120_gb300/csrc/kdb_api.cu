@@ -20,6 +20,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "../../include/kdb.h"
@@ -66,6 +67,14 @@ std::vector<ProfRec> g_prof;
 std::vector<cudaEvent_t> g_event_pool;
 std::atomic<int64_t> g_launches{0};
 std::atomic<int> g_placement{KDB_PLACEMENT_AUTO};
+
+struct SmemAttr {
+  int dev;
+  const void* func;
+  size_t bytes;
+};
+std::mutex g_attr_mu;
+std::vector<SmemAttr> g_attr;
 
 cudaEvent_t take_event() {
   cudaEvent_t e = nullptr;
@@ -417,9 +426,39 @@ T* at(void* ws, size_t off) {
   return reinterpret_cast<T*>(static_cast<unsigned char*>(ws) + off);
 }
 
-// Enqueues the whole build on `st`.  Does not synchronise.
+// Copies the plan's tables (sets, active lists, local work) into the
+// workspace; with sync, from the host synchronously (plans made once).
+kdb_status upload_tables(const Plan& P, void* ws, cudaStream_t st, bool sync) {
+  auto copy = [&](void* dst, const void* src, size_t bytes) {
+    return sync ? cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice)
+                : cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  KDB_CK(copy(at<SetInfo>(ws, P.o_sets), P.sets.data(), P.sets.size() * sizeof(SetInfo)));
+  std::vector<ActiveEntry> flat;
+  for (const auto& v : P.act) flat.insert(flat.end(), v.begin(), v.end());
+  if (!flat.empty())
+    KDB_CK(copy(at<ActiveEntry>(ws, P.o_act), flat.data(), flat.size() * sizeof(ActiveEntry)));
+  // pageable sources: each copy has completed when the call returns
+  if (P.use_local) {
+    KDB_CK(copy(at<LocalSet>(ws, P.o_lsets), P.lsets.data(), P.lsets.size() * sizeof(LocalSet)));
+    if (!P.work.empty())
+      KDB_CK(copy(at<LocalWork>(ws, P.o_work), P.work.data(), P.work.size() * sizeof(LocalWork)));
+  }
+  ActiveEntry w{};
+  w.set = 0;
+  w.base = 0;
+  w.next = -1;
+  KDB_CK(copy(at<ActiveEntry>(ws, P.o_whole), &w, sizeof w));
+  return KDB_OK;
+}
+
+// Enqueues the whole build on `st`.  Does not synchronise.  With
+// tables_ready the plan's tables are already in the workspace: then only
+// kernels and memsets are enqueued (no host memory is read), so the call can
+// be captured into a CUDA graph.
 kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
-                         int32_t* out_orig, uint8_t* out_dim, cudaStream_t st) {
+                         int32_t* out_orig, uint8_t* out_dim, cudaStream_t st,
+                         bool tables_ready = false) {
   const uint32_t T = P.total;
   const int k = P.k;
   uint64_t* keysA = at<uint64_t>(ws, P.o_keysA);
@@ -442,46 +481,18 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   const bool widest = P.mode == KDB_SPLIT_WIDEST_EXTENT;
 
   // tables and zeroed state: look-back words, histograms, tickets, error word
-  KDB_CK(cudaMemcpyAsync(d_sets, P.sets.data(), P.sets.size() * sizeof(SetInfo),
-                         cudaMemcpyHostToDevice, st));
-  {
-    std::vector<ActiveEntry> flat;
-    for (const auto& v : P.act) flat.insert(flat.end(), v.begin(), v.end());
-    if (!flat.empty())
-      KDB_CK(cudaMemcpyAsync(d_act, flat.data(), flat.size() * sizeof(ActiveEntry),
-                             cudaMemcpyHostToDevice, st));
-    // pageable source: the copy has completed when cudaMemcpyAsync returns
+  if (!tables_ready) {
+    kdb_status s = upload_tables(P, ws, st, false);
+    if (s != KDB_OK) return s;
   }
   uint32_t* vals_local = at<uint32_t>(ws, P.o_vloc);
   float* boxes_local = at<float>(ws, P.o_lbox);
   LocalSet* d_lsets = at<LocalSet>(ws, P.o_lsets);
   LocalWork* d_work = at<LocalWork>(ws, P.o_work);
-  if (P.use_local) {
-    KDB_CK(cudaMemcpyAsync(d_lsets, P.lsets.data(), P.lsets.size() * sizeof(LocalSet),
-                           cudaMemcpyHostToDevice, st));
-    if (!P.work.empty())
-      KDB_CK(cudaMemcpyAsync(d_work, P.work.data(), P.work.size() * sizeof(LocalWork),
-                             cudaMemcpyHostToDevice, st));
-  }
   ActiveEntry* d_whole = at<ActiveEntry>(ws, P.o_whole);
-  {
-    ActiveEntry w{};
-    w.set = 0;
-    w.base = 0;
-    w.next = -1;
-    KDB_CK(cudaMemcpyAsync(d_whole, &w, sizeof w, cudaMemcpyHostToDevice, st));
-  }
   KDB_CK(cudaMemsetAsync(status, 0, P.o_hist - P.o_status, st));
   KDB_CK(cudaMemsetAsync(hist, 0, P.o_bbox - P.o_hist, st));  // hist, tickets, err
-  if (widest) {
-    std::vector<uint32_t> init(P.sets.size() * 2 * k);
-    for (size_t b = 0; b < P.sets.size(); ++b)
-      for (int d = 0; d < k; ++d) {
-        init[b * 2 * k + d] = 0xFFFFFFFFu;
-        init[b * 2 * k + k + d] = 0u;
-      }
-    KDB_CK(cudaMemcpyAsync(bbox, init.data(), init.size() * 4, cudaMemcpyHostToDevice, st));
-  }
+  if (widest) KDB_CK(launch_init_bbox(bbox, (uint32_t)P.sets.size(), k, st));
   if (out_dim || widest) KDB_CK(cudaMemsetAsync(dims, 0, T, st));
 
   const uint64_t wait_ns =
@@ -978,6 +989,32 @@ kdb_status noalloc_scratch(int dev, void** out) {
 }
 
 }  // namespace
+
+// A build prepared once and enqueued many times (kdb_plan_*).
+struct PlanObj {
+  Plan P;
+  void* ws = nullptr;
+  int dev = 0, sms = 1;
+  uint32_t* h_err = nullptr;  // pinned
+  bool trivial = false;       // N <= 1 in every set: nothing to do
+};
+
+cudaError_t ensure_smem(const void* func, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  for (SmemAttr& a : g_attr) {
+    if (a.dev != dev || a.func != func) continue;
+    if (a.bytes >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) a.bytes = bytes;
+    return e;
+  }
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) g_attr.push_back({dev, func, bytes});
+  return e;
+}
 }  // namespace kdb
 
 using namespace kdb;
@@ -1164,6 +1201,115 @@ kdb_status kdb_build_batched(void* d_points, const int64_t* h_offsets, int num_s
   P.mode = mode;
   return run(P, static_cast<unsigned char*>(d_points), nullptr, 0, nullptr, nullptr,
              reinterpret_cast<cudaStream_t>(stream));
+}
+
+kdb_status kdb_plan_create(const int64_t* h_offsets, int num_sets, int k, int stride_bytes,
+                           kdb_split_mode mode, kdb_plan* out_plan) {
+  using kdb::PlanObj;
+  if (!out_plan) return KDB_ERR_INVALID_ARGUMENT;
+  *out_plan = nullptr;
+  if (num_sets < 1 || !h_offsets || h_offsets[0] != 0) return KDB_ERR_INVALID_ARGUMENT;
+  const int64_t total = h_offsets[num_sets];
+  kdb_status s = kdb::check_common(total, k, stride_bytes);
+  if (s == KDB_OK) s = kdb::check_mode(mode);
+  if (s != KDB_OK) return s;
+  PlanObj* po = new (std::nothrow) PlanObj();
+  if (!po) return KDB_ERR_OUT_OF_MEMORY;
+  kdb::Plan& P = po->P;
+  for (int b = 0; b < num_sets; ++b) {
+    if (h_offsets[b + 1] < h_offsets[b]) {
+      delete po;
+      return KDB_ERR_INVALID_ARGUMENT;
+    }
+    P.sets.push_back(kdb::SetInfo{(uint32_t)h_offsets[b], (uint32_t)(h_offsets[b + 1] - h_offsets[b])});
+  }
+  P.total = (uint32_t)total;
+  P.k = k;
+  P.stride = stride_bytes;
+  P.mode = mode;
+  po->trivial = total <= 1;
+  if (po->trivial) {
+    *out_plan = reinterpret_cast<kdb_plan>(po);
+    return KDB_OK;
+  }
+  kdb::make_plan(P);
+  cudaMemPool_t pool;
+  s = P.too_wide ? KDB_ERR_INVALID_ARGUMENT : kdb::device_setup(&po->dev, &pool, &po->sms);
+  void* pts = nullptr;
+  if (s == KDB_OK && (cudaMalloc(&po->ws, P.bytes) != cudaSuccess ||
+                      cudaMallocHost(reinterpret_cast<void**>(&po->h_err), 4) != cudaSuccess)) {
+    cudaGetLastError();
+    s = KDB_ERR_OUT_OF_MEMORY;
+  }
+  if (s == KDB_OK) s = kdb::upload_tables(P, po->ws, nullptr, true);
+  // one build on all-zero points outside any capture: loads every kernel and
+  // sets its attributes, so that later enqueues only launch
+  if (s == KDB_OK) {
+    if (cudaMalloc(&pts, (size_t)total * stride_bytes) != cudaSuccess ||
+        cudaMemset(pts, 0, (size_t)total * stride_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      s = KDB_ERR_OUT_OF_MEMORY;
+    }
+  }
+  if (s == KDB_OK) {
+    s = kdb::enqueue_build(P, static_cast<unsigned char*>(pts), po->ws, po->sms, nullptr, nullptr,
+                           nullptr, true);
+    kdb_status f = kdb::finish(P, po->ws, nullptr);
+    if (s == KDB_OK) s = f;
+  }
+  if (pts) cudaFree(pts);
+  if (s != KDB_OK) {
+    kdb_plan_destroy(reinterpret_cast<kdb_plan>(po));
+    return s;
+  }
+  *out_plan = reinterpret_cast<kdb_plan>(po);
+  return KDB_OK;
+}
+
+kdb_status kdb_plan_enqueue(kdb_plan plan, void* d_points, kdb_stream_t stream) {
+  kdb::PlanObj* po = reinterpret_cast<kdb::PlanObj*>(plan);
+  if (!po) return KDB_ERR_INVALID_ARGUMENT;
+  if (po->trivial) return KDB_OK;
+  if (!d_points || (reinterpret_cast<uintptr_t>(d_points) & 3)) return KDB_ERR_INVALID_ARGUMENT;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != po->dev) {
+    cudaGetLastError();
+    return KDB_ERR_INVALID_ARGUMENT;
+  }
+  return kdb::enqueue_build(po->P, static_cast<unsigned char*>(d_points), po->ws, po->sms, nullptr,
+                            nullptr, reinterpret_cast<cudaStream_t>(stream), true);
+}
+
+kdb_status kdb_plan_status(kdb_plan plan, kdb_stream_t stream) {
+  kdb::PlanObj* po = reinterpret_cast<kdb::PlanObj*>(plan);
+  if (!po) return KDB_ERR_INVALID_ARGUMENT;
+  if (po->trivial) return KDB_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(po->h_err, kdb::at<uint32_t>(po->ws, po->P.o_err), 4, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return KDB_ERR_CUDA;
+  }
+  const uint32_t e = *po->h_err;
+  if (e & kdb::ERR_NAN) return KDB_ERR_NAN_INPUT;
+  if (e & kdb::ERR_TIMEOUT) return KDB_ERR_TIMEOUT;
+  if (e & kdb::ERR_INTERNAL) return KDB_ERR_INTERNAL;
+  return KDB_OK;
+}
+
+size_t kdb_plan_workspace_bytes(kdb_plan plan) {
+  const kdb::PlanObj* po = reinterpret_cast<const kdb::PlanObj*>(plan);
+  return po && !po->trivial ? po->P.bytes : 0;
+}
+
+void kdb_plan_destroy(kdb_plan plan) {
+  kdb::PlanObj* po = reinterpret_cast<kdb::PlanObj*>(plan);
+  if (!po) return;
+  if (po->ws) cudaFree(po->ws);
+  if (po->h_err) cudaFreeHost(po->h_err);
+  cudaGetLastError();
+  delete po;
 }
 
 kdb_status kdb_build_host(void* h_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,

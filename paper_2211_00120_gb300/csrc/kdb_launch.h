@@ -24,6 +24,11 @@ struct LevelCtx {
 
 struct PassCtl;
 
+// Raises a kernel's dynamic shared-memory limit on the current device if it
+// is below `bytes`; remembers what it set, so that later launches (also
+// inside a stream capture) make no attribute call.
+cudaError_t ensure_smem(const void* func, size_t bytes);
+
 // Presorted-list levels (kdb_part.cu), k <= 3: one 16-byte entry per point
 // (order-preserving keys of coordinates 0..2, original index), one list per
 // dimension.
@@ -252,6 +257,7 @@ cudaError_t launch_place_gather(const PermuteArgs& a, unsigned char* tmp, int nu
 // failed after writing records directly at their nodes.
 cudaError_t launch_restore(unsigned char* pts, const uint4* ents, uint32_t total, int k, const uint32_t* err,
                            cudaStream_t st);
+cudaError_t launch_init_bbox(uint32_t* bbox, uint32_t nsets, int k, cudaStream_t st);
 cudaError_t launch_unmark(const uint32_t* perm, int32_t* out, uint32_t total, cudaStream_t st);
 
 cudaError_t launch_validate(const unsigned char* pts, uint32_t n, int k, int stride, int mode,

@@ -281,7 +281,7 @@ cudaError_t launch_rec_sort_pass(const uint4* in, uint4* out, const PassCtl& c, 
   if (c.n == 0) return cudaSuccess;
   const size_t smem = rec_sort_smem();
   cudaError_t e =
-      cudaFuncSetAttribute(rec_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      ensure_smem((const void*)rec_sort_pass, smem);
   if (e != cudaSuccess) return e;
   const uint32_t tiles = (c.n + RTILE - 1) / RTILE;
   rec_sort_pass<<<tiles, RT, smem, st>>>(in, out, c, x, seg_hist, d);

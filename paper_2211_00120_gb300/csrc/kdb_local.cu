@@ -697,8 +697,7 @@ size_t local_smem_bytes(int k) {
 cudaError_t launch_local_finish(const LocalArgs& a, cudaStream_t st) {
   if (a.nwork == 0) return cudaSuccess;
   const size_t smem = local_smem_bytes(a.k);
-  cudaError_t e = cudaFuncSetAttribute(local_finish_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem((const void*)local_finish_kernel, smem);
   if (e != cudaSuccess) return e;
   local_finish_kernel<<<a.nwork, T, smem, st>>>(a);
   return cudaGetLastError();

@@ -346,7 +346,7 @@ cudaError_t launch_partition(const PartArgs& a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
   const size_t smem = partition_smem();
   cudaError_t e =
-      cudaFuncSetAttribute(partition_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      ensure_smem((const void*)partition_kernel, smem);
   if (e != cudaSuccess) return e;
   const uint32_t tiles = (a.n + PTILE - 1) / PTILE;
   partition_kernel<<<tiles, PT, smem, st>>>(a);

@@ -58,8 +58,8 @@ static cudaError_t run_pass(const K* kin, const uint32_t* vin, const Epi& epi, c
   if (c.n == 0) return cudaSuccess;
   auto kern = onesweep_pass<K, kSortThreads, kSortItems, Epi>;
   const size_t smem = OnesweepShape<K, kSortThreads, kSortItems>::kDynSmem;
-  // set on every call: the attribute belongs to the current device
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the attribute belongs to the current device; set once per device
+  cudaError_t e = ensure_smem((const void*)kern, smem);
   if (e != cudaSuccess) return e;
   const uint32_t tiles = (c.n + kSortTile - 1) / kSortTile;
   kern<<<tiles, kSortThreads, smem, st>>>(kin, vin, c, epi);
@@ -87,7 +87,7 @@ static cudaError_t run_seg_pass(const uint32_t* kin, const uint32_t* vin, const 
   if (c.n == 0) return cudaSuccess;
   auto kern = seg_onesweep_pass<kSegThreads, kSegItems, kSegMinBlocks, Epi>;
   const size_t smem = seg_pass_smem();
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem((const void*)kern, smem);
   if (e != cudaSuccess) return e;
   const uint32_t tiles = (c.n + kSegTile - 1) / kSegTile;
   kern<<<tiles, kSegThreads, smem, st>>>(kin, vin, c, x, seg_hist, epi);

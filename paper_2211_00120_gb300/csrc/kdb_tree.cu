@@ -523,6 +523,13 @@ __global__ void restore_kernel(unsigned char* pts, const uint4* ents, uint32_t t
     write_record_from_entry(pts + (uint64_t)i * (4 * k), ents[i], k);
 }
 
+// Scene-box accumulators of every set: lower keys at the top, upper at zero.
+__global__ void init_bbox_kernel(uint32_t* bbox, uint32_t nsets, int k) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nsets * 2 * (uint32_t)k) return;
+  bbox[i] = (i % (2 * (uint32_t)k)) < (uint32_t)k ? 0xFFFFFFFFu : 0u;
+}
+
 __global__ void unmark_kernel(const uint32_t* perm, int32_t* out, uint32_t total) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < total) out[i] = (int32_t)(perm[i] & ~kMark);
@@ -558,8 +565,7 @@ __global__ void validate_kernel(const unsigned char* pts, uint32_t n, int k, int
 cudaError_t launch_prepass(const PrepassArgs& a, int num_sms, cudaStream_t st) {
   if (a.total == 0) return cudaSuccess;
   const size_t smem = a.hist ? (size_t)a.k * a.passes * kRadixBins * sizeof(uint32_t) : 0;
-  cudaError_t e = cudaFuncSetAttribute(prepass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = ensure_smem((const void*)prepass_kernel, smem);
   if (e != cudaSuccess) return e;
   uint32_t grid = (uint32_t)num_sms * 4;
   const uint32_t need = (a.total + kThreads - 1) / kThreads;
@@ -636,6 +642,13 @@ cudaError_t launch_restore(unsigned char* pts, const uint4* ents, uint32_t total
   // a small grid: the kernel usually finds no error and returns at once
   const uint32_t grid = std::min<uint32_t>((total + kThreads - 1) / kThreads, 1024);
   restore_kernel<<<grid, kThreads, 0, st>>>(pts, ents, total, k, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_bbox(uint32_t* bbox, uint32_t nsets, int k, cudaStream_t st) {
+  const uint32_t n = nsets * 2 * (uint32_t)k;
+  if (n == 0) return cudaSuccess;
+  init_bbox_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(bbox, nsets, k);
   return cudaGetLastError();
 }
 

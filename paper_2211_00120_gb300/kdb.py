@@ -83,6 +83,11 @@ def load():
             "kdb_validate": ([vp, i64, i32, i32, i32, ctypes.POINTER(i64), vp], i32),
             "kdb_debug_inject_fault": ([i32, i64], i32),
             "kdb_set_placement": ([i32], i32),
+            "kdb_plan_create": ([vp, i32, i32, i32, i32, ctypes.POINTER(vp)], i32),
+            "kdb_plan_enqueue": ([vp, vp, vp], i32),
+            "kdb_plan_status": ([vp, vp], i32),
+            "kdb_plan_workspace_bytes": ([vp], sz),
+            "kdb_plan_destroy": ([vp], None),
             "kdb_profile_start": ([], None),
             "kdb_profile_stop": ([ctypes.POINTER(KernelStat), i32], i32),
             "kdb_launch_count": ([], i64),
@@ -188,6 +193,47 @@ def kdb_validate(points, k: int, mode: int = ROUND_ROBIN, stream=None) -> int:
     if rc not in (OK, ERR_NOT_A_KD_TREE):
         raise KdbError(rc, "kdb_validate")
     return int(bad.value)
+
+
+class Plan:
+    """A build prepared once (kdb_plan_create) and enqueued many times; the
+    enqueue is capture-safe (CUDA graphs).  ``offsets``: record offsets of the
+    sets (num_sets + 1 entries), or a single point count."""
+
+    def __init__(self, offsets, k: int, stride_bytes: int, mode: int = ROUND_ROBIN):
+        if isinstance(offsets, int):
+            offsets = [0, offsets]
+        self.offsets = [int(o) for o in offsets]
+        offs = (ctypes.c_int64 * len(self.offsets))(*self.offsets)
+        h = ctypes.c_void_p()
+        _check(load().kdb_plan_create(offs, len(self.offsets) - 1, k, stride_bytes, mode,
+                                      ctypes.byref(h)), "kdb_plan_create")
+        self._h = h
+        self.k, self.stride, self.mode = k, stride_bytes, mode
+
+    def enqueue(self, points, stream=None) -> None:
+        ptr, n, stride = _records(points)
+        if n != self.offsets[-1] or stride != self.stride:
+            raise ValueError("points do not match the plan's layout")
+        _check(load().kdb_plan_enqueue(self._h, ptr, _stream(stream)), "kdb_plan_enqueue")
+
+    def status(self, stream=None) -> None:
+        _check(load().kdb_plan_status(self._h, _stream(stream)), "kdb_plan_status")
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(load().kdb_plan_workspace_bytes(self._h))
+
+    def close(self) -> None:
+        if self._h:
+            load().kdb_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kdb_set_placement(placement: int) -> int:
