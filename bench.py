@@ -229,17 +229,34 @@ def batched_vs_serial(sets: int = 4096, lo: int = 100, hi: int = 1_000_000, seed
     equal = bool(torch.equal(work.view(torch.int32), out_b.view(torch.int32)))
     tb = timed(batched)
     ts = timed(serial)
+    # the same batched build from a plan captured into one CUDA graph
+    plan = kdb.Plan(off_list, 3, 12, kdb.ROUND_ROBIN)
+    cap = torch.cuda.Stream()
+    cap.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(graph, stream=cap):
+            plan.enqueue(work, stream=cap)
+    stream.wait_stream(cap)
+    work.copy_(src)
+    graph.replay()
+    plan.status()
+    equal = equal and bool(torch.equal(work.view(torch.int32), out_b.view(torch.int32)))
+    tg = timed(graph.replay)
+    del graph
+    plan.close()
     del src, work, out_b
     torch.cuda.empty_cache()
     if dist is not None:
-        t = torch.tensor([tb, ts, 0.0 if equal else 1.0], device="cuda")
+        t = torch.tensor([tb, ts, tg, 0.0 if equal else 1.0], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tb, ts, equal = float(t[0]), float(t[1]), float(t[2]) == 0.0
+        tb, ts, tg, equal = float(t[0]), float(t[1]), float(t[2]), float(t[3]) == 0.0
     n = n_all
     return {"workload": f"{sets} float3 sets, sizes log-uniform in [{lo}, {hi}] (seed {seed}), "
                         f"{n} points uniform in [0,1)^3, round robin",
             "ranks": world, "sharding": "LPT by points x levels, no exchange" if world > 1 else None,
-            "points": n, "batched_ms": tb, "serial_ms": ts,
+            "points": n, "batched_ms": tb, "serial_ms": ts, "graph_ms": tg,
+            "graph_builds_per_s": sets / (tg / 1000.0),
             "batched_builds_per_s": sets / (tb / 1000.0), "serial_builds_per_s": sets / (ts / 1000.0),
             "batched_mpts_per_s": n / (tb / 1000.0) / 1e6, "speedup": ts / tb,
             "equal_output": equal, "steps": steps,
