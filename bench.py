@@ -263,6 +263,102 @@ def batched_vs_serial(sets: int = 4096, lo: int = 100, hi: int = 1_000_000, seed
             "timing": "CUDA events around the whole call (serial: 4096 synchronous kdb_build calls)"}
 
 
+def serving(rate: float = 2000.0, duration_s: float = 5.0, lo: int = 1000, hi: int = 10_000_000,
+            budget_gb: float = 40.0, seed: int = 4, inflight: int = 3, pool_log: int = 24):
+    """The build server under a Poisson stream of requests: sizes log-uniform
+    in [lo, hi], float3 or float4 records, uniform or clustered points (fair
+    coins), every request copied in from pinned host memory and its tree
+    copied back out.  The payloads are slices of four pre-generated pinned
+    pools, so host generation is not timed.  Reports builds/s and latency
+    percentiles (submit to copy-back done) at the offered rate; if that rate
+    saturates the server, again at 80% of the throughput it reached; and the
+    same requests served one at a time (one stream, one request per batch)."""
+    import torch
+    from paper_2211_00120_gb300 import kdb
+
+    P = 1 << pool_log
+    pools = {}
+    for f4 in (False, True):
+        for cl in (False, True):
+            base = synth.mixed(P, 3, seed=60 + cl) if cl else synth.uniform(P, 3, seed=60)
+            if f4:
+                arr = np.empty((P, 4), dtype=np.float32)
+                arr[:, :3] = base
+                arr[:, 3] = np.arange(P, dtype=np.uint32).view(np.float32)
+            else:
+                arr = base
+            pools[(f4, cl)] = (torch.from_numpy(arr).pin_memory(),
+                               torch.empty(arr.shape, dtype=torch.float32).pin_memory())
+    t_arr, sizes, f4s, cls, where = synth.poisson_requests(rate, duration_s, lo, hi, seed=seed)
+    sizes = np.minimum(sizes, P)
+    reqs = []
+    for i in range(len(t_arr)):
+        n = int(sizes[i])
+        off = int(where[i] * (P - n + 1))
+        src, dst = pools[(bool(f4s[i]), bool(cls[i]))]
+        reqs.append((float(t_arr[i]), src[off:off + n], dst[off:off + n]))
+
+    def run(scale: float, count: int, **cfg):
+        """Replays the first `count` requests with arrival times / scale."""
+        srv = kdb.Server(budget_bytes=int(budget_gb * (1 << 30)), **cfg)
+        done, late = {}, 0.0
+        t0 = time.perf_counter()
+        for t, src, dst in reqs[:count]:
+            target = t0 + t / scale
+            while True:
+                d = target - time.perf_counter()
+                if d <= 0:
+                    break
+                if d > 0.0006:
+                    time.sleep(d - 0.0004)
+            late = max(late, time.perf_counter() - target)
+            srv.submit(src, 3, kdb.ROUND_ROBIN, out=dst)
+            for r in srv.poll(0):
+                done[r["id"]] = r
+        while len(done) < count:
+            for r in srv.poll(200):
+                done[r["id"]] = r
+        st = srv.stats()
+        srv.close()
+        rs = list(done.values())
+        bad = sum(1 for r in rs if r["status"] != kdb.OK)
+        first = min(r["submit_s"] for r in rs)
+        last = max(r["done_s"] for r in rs)
+        lat = np.array([r["done_s"] - r["submit_s"] for r in rs]) * 1e3
+        pts = sum(r["n"] for r in rs)
+        offered = count / (reqs[count - 1][0] / scale) if count > 1 else None
+        achieved = count / (last - first)
+        return {"offered_builds_per_s": offered, "builds_per_s": achieved,
+                "mpts_per_s": pts / (last - first) / 1e6, "requests": count, "failed": bad,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "saturated": bool(offered and achieved < 0.95 * offered),
+                "batches": st["batches"], "max_batch_requests": st["max_batch_requests"],
+                "max_inflight_batches": st["max_inflight_batches"],
+                "max_used_gb": st["max_used_bytes"] / 2**30, "max_submit_lateness_ms": late * 1e3}
+
+    nreq = len(reqs)
+    out = {"workload": f"Poisson arrivals at {rate:g} req/s for {duration_s:g} s ({nreq} requests, "
+                       f"seed {seed}), sizes log-uniform in [{lo}, {hi}], float3/float4 and "
+                       f"uniform/clustered 50/50, round robin, {budget_gb:g} GB budget",
+           "latency": "submit to the end of the copy back to pinned host memory (server clock)",
+           "inflight_batches": inflight}
+    out["offered"] = run(1.0, nreq, max_inflight_batches=inflight)
+    if out["offered"]["saturated"]:
+        scale = 0.8 * out["offered"]["builds_per_s"] / rate
+        out["at_80pct_of_max"] = run(scale, nreq, max_inflight_batches=inflight)
+    # the same stream served one request at a time: 2 s of arrivals
+    m = int(np.searchsorted(t_arr, 2.0))
+    one = run(1.0, m, max_inflight_batches=1, max_batch_requests=1)
+    cb = run(1.0, m, max_inflight_batches=inflight)
+    out["one_at_a_time_vs_batched"] = {"requests": m, "one_at_a_time_builds_per_s": one["builds_per_s"],
+                                       "batched_builds_per_s": cb["builds_per_s"],
+                                       "one_at_a_time_p50_ms": one["p50_ms"],
+                                       "batched_p50_ms": cb["p50_ms"],
+                                       "speedup": cb["builds_per_s"] / one["builds_per_s"]}
+    del pools, reqs
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -307,6 +403,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched vs serial measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="only the serving measurement (prints its JSON object)")
     ap.add_argument("--points", type=int, default=0,
                     help="override the workload's number of points (small profiling cases)")
     ap.add_argument("--profile-only", action="store_true",
@@ -330,6 +429,9 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.serving_only:
+        print(json.dumps(serving()), flush=True)
+        return 0
     desc, n, k, sf, mode, gen = WORKLOADS[args.workload]
     if args.points:
         n = args.points
@@ -440,6 +542,10 @@ def main():
         torch.cuda.empty_cache()
         batched = batched_vs_serial(world=world, rank=rank, dist=dist)
 
+    served = None
+    if world == 1 and not args.no_serving:
+        served = serving()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)
@@ -455,7 +561,7 @@ def main():
                            "l2": "input 1.2+ GB > L2, restored by a device copy before each step"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "kernel_ms_per_step": kernel_ms,
-                "placement_in_place": in_place, "batched": batched}
+                "placement_in_place": in_place, "batched": batched, "serving": served}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

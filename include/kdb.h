@@ -124,6 +124,33 @@ KDB_API kdb_status kdb_build_batched(void* d_points, const int64_t* h_offsets, i
                              int stride_bytes, kdb_split_mode mode, kdb_stream_t stream);
 
 /*
+ * kdb_build_batched_async -- kdb_build_batched that only enqueues: the same
+ * build of num_sets independent trees (h_offsets, k, stride_bytes, mode as
+ * for kdb_build_batched), with caller workspace and no synchronisation.
+ * The paper has no batched build; each set is the paper's build (Sec. 3.2)
+ * and its output equals a kdb_build of that set alone.
+ *   d_workspace     device, >= kdb_batched_workspace_size() bytes for the
+ *                   same arguments, 256-byte aligned, owned by the caller;
+ *                   its contents on entry do not matter.  A call uses it
+ *                   until the enqueued work has finished.
+ *   d_error_word    device uint32 or NULL: receives, in stream order, the
+ *                   build's device error flags (0 = success); map it with
+ *                   kdb_error_word_status.
+ * Host memory is read only during the call (the set table is copied into
+ * the workspace on `stream`), so h_offsets may be reused at once.  Returns
+ * argument and launch errors; device errors (NaN input, timeouts) arrive in
+ * d_error_word, and then every set's records are left as they were.
+ */
+KDB_API size_t kdb_batched_workspace_size(const int64_t* h_offsets, int num_sets, int k,
+                                          int stride_bytes, kdb_split_mode mode);
+KDB_API kdb_status kdb_build_batched_async(void* d_points, const int64_t* h_offsets, int num_sets,
+                                           int k, int stride_bytes, kdb_split_mode mode,
+                                           void* d_workspace, size_t workspace_bytes,
+                                           uint32_t* d_error_word, kdb_stream_t stream);
+/* Status of a device error word written by kdb_build_batched_async. */
+KDB_API kdb_status kdb_error_word_status(uint32_t word);
+
+/*
  * kdb_build_host -- kdb_build for records in host memory: copies them to the
  * device, builds, and copies the tree back into h_points on `stream` (pinned
  * host memory gives asynchronous copies).  Synchronises `stream`.
@@ -194,6 +221,71 @@ KDB_API kdb_status kdb_plan_enqueue(kdb_plan plan, void* d_points, kdb_stream_t 
 KDB_API kdb_status kdb_plan_status(kdb_plan plan, kdb_stream_t stream);
 KDB_API size_t kdb_plan_workspace_bytes(kdb_plan plan);
 KDB_API void kdb_plan_destroy(kdb_plan plan);
+
+/*
+ * Build server: requests accepted as they arrive and built on one GPU by
+ * continuous batching.  The paper has no counterpart; each request is the
+ * paper's build (Sec. 3.2) of its own point set, bit-identical to kdb_build
+ * of that set alone, whatever it was batched with.
+ *
+ * A worker thread owns max_inflight_batches CUDA streams.  Whenever one is
+ * free, the queued requests with the head request's layout (k, stride_bytes,
+ * mode) are taken in arrival order, as many as fit in the free part of the
+ * device-memory budget (points plus build workspace) and the caps, and are
+ * enqueued as one batch: copies in, one kdb_build_batched_async, copies out.
+ * Requests arriving meanwhile go to the next free stream, so batches overlap
+ * on the device.  The budget is reserved from the device when the server is
+ * created and stays reserved until it is destroyed.  A batch that fails on
+ * the device (NaN input, a timeout) leaves the records untouched; each of its
+ * requests is then run again alone, so only the failing request fails.
+ *
+ * kdb_server_create -- on the current device; fails with
+ *   KDB_ERR_OUT_OF_MEMORY if budget_bytes exceeds the free device memory.
+ * kdb_server_submit -- queues one build.  h_points: host, n records as for
+ *   kdb_build (pinned memory gives asynchronous copies; pageable memory
+ *   works but serialises the copies); read when the request's batch starts,
+ *   so it must stay valid and unchanged until the result is polled.  h_out:
+ *   host, n records, receives the tree (may equal h_points; NULL = no copy
+ *   back).  *out_id receives the request id.  Returns
+ *   KDB_ERR_INVALID_ARGUMENT for bad arguments and KDB_ERR_OUT_OF_MEMORY if
+ *   the request alone exceeds the budget; nothing is queued then.
+ * kdb_server_poll -- moves up to max_results finished requests into out,
+ *   waiting up to timeout_ms (0: no wait, < 0: until one is there) for the
+ *   first.  Returns the count (-1 for bad arguments).  Times are seconds
+ *   since the server was created: submit, admission into a batch, and the end
+ *   of the batch's copy out.
+ * kdb_server_get_stats -- counters since creation.
+ * kdb_server_destroy -- builds everything still queued, waits for it, frees
+ *   the server.  Results not yet polled are dropped.
+ * Submit, poll and stats may be called from any thread.
+ */
+typedef struct kdb_server_st* kdb_server;
+typedef struct {
+  size_t budget_bytes;         /* device memory for in-flight batches */
+  int max_inflight_batches;    /* streams, 1 .. 16 */
+  int max_batch_requests;      /* >= 1 */
+  int64_t max_batch_points;    /* >= 1; a single larger request still runs */
+} kdb_server_config;
+typedef struct {
+  int64_t id;
+  kdb_status status;
+  int64_t n;
+  double submit_s, admit_s, done_s;
+} kdb_request_result;
+typedef struct {
+  int64_t submitted, completed, failed;
+  int64_t batches, retried_alone;
+  int64_t max_batch_requests, max_inflight_batches;
+  int64_t queued, inflight_requests;
+  size_t budget_bytes, used_bytes, max_used_bytes;
+} kdb_server_stats;
+KDB_API kdb_status kdb_server_create(const kdb_server_config* config, kdb_server* out_server);
+KDB_API kdb_status kdb_server_submit(kdb_server server, const void* h_points, void* h_out, int64_t n,
+                                     int k, int stride_bytes, kdb_split_mode mode, int64_t* out_id);
+KDB_API int kdb_server_poll(kdb_server server, kdb_request_result* out, int max_results,
+                            int timeout_ms);
+KDB_API kdb_status kdb_server_get_stats(kdb_server server, kdb_server_stats* out);
+KDB_API kdb_status kdb_server_destroy(kdb_server server);
 
 /*
  * kdb_set_placement -- how the final placement moves the records into level

@@ -1203,6 +1203,77 @@ kdb_status kdb_build_batched(void* d_points, const int64_t* h_offsets, int num_s
              reinterpret_cast<cudaStream_t>(stream));
 }
 
+namespace kdb {
+namespace {
+// The sets of a batched call as a plan (make_plan not yet run); checks the
+// arguments shared by the batched entry points.
+kdb_status batched_sets(Plan& P, const int64_t* h_offsets, int num_sets, int k, int stride_bytes,
+                        kdb_split_mode mode) {
+  if (num_sets < 1 || !h_offsets || h_offsets[0] != 0) return KDB_ERR_INVALID_ARGUMENT;
+  const int64_t total = h_offsets[num_sets];
+  kdb_status s = check_common(total, k, stride_bytes);
+  if (s == KDB_OK) s = check_mode(mode);
+  if (s != KDB_OK) return s;
+  P.sets.reserve(num_sets);
+  for (int b = 0; b < num_sets; ++b) {
+    if (h_offsets[b + 1] < h_offsets[b]) return KDB_ERR_INVALID_ARGUMENT;
+    P.sets.push_back(SetInfo{(uint32_t)h_offsets[b], (uint32_t)(h_offsets[b + 1] - h_offsets[b])});
+  }
+  P.total = (uint32_t)total;
+  P.k = k;
+  P.stride = stride_bytes;
+  P.mode = mode;
+  return KDB_OK;
+}
+}  // namespace
+}  // namespace kdb
+
+size_t kdb_batched_workspace_size(const int64_t* h_offsets, int num_sets, int k, int stride_bytes,
+                                  kdb_split_mode mode) {
+  kdb::Plan P;
+  if (kdb::batched_sets(P, h_offsets, num_sets, k, stride_bytes, mode) != KDB_OK || P.total <= 1)
+    return 0;
+  kdb::make_plan(P);
+  return P.too_wide ? 0 : P.bytes;
+}
+
+kdb_status kdb_build_batched_async(void* d_points, const int64_t* h_offsets, int num_sets, int k,
+                                   int stride_bytes, kdb_split_mode mode, void* d_workspace,
+                                   size_t workspace_bytes, uint32_t* d_error_word,
+                                   kdb_stream_t stream) {
+  kdb::Plan P;
+  kdb_status s = kdb::batched_sets(P, h_offsets, num_sets, k, stride_bytes, mode);
+  if (s != KDB_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (P.total <= 1) {
+    if (d_error_word) KDB_CK(cudaMemsetAsync(d_error_word, 0, 4, st));
+    return KDB_OK;
+  }
+  if (!d_points || (reinterpret_cast<uintptr_t>(d_points) & 3)) return KDB_ERR_INVALID_ARGUMENT;
+  kdb::make_plan(P);
+  if (P.too_wide) return KDB_ERR_INVALID_ARGUMENT;
+  if (!d_workspace || workspace_bytes < P.bytes || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
+    return KDB_ERR_INVALID_ARGUMENT;
+  int dev, sms;
+  cudaMemPool_t pool;
+  s = kdb::device_setup(&dev, &pool, &sms);
+  if (s != KDB_OK) return s;
+  s = kdb::enqueue_build(P, static_cast<unsigned char*>(d_points), d_workspace, sms, nullptr, nullptr,
+                         st);
+  if (s != KDB_OK) return s;
+  if (d_error_word)
+    KDB_CK(cudaMemcpyAsync(d_error_word, kdb::at<uint32_t>(d_workspace, P.o_err), 4,
+                           cudaMemcpyDeviceToDevice, st));
+  return KDB_OK;
+}
+
+kdb_status kdb_error_word_status(uint32_t word) {
+  if (word & kdb::ERR_NAN) return KDB_ERR_NAN_INPUT;
+  if (word & kdb::ERR_TIMEOUT) return KDB_ERR_TIMEOUT;
+  if (word) return KDB_ERR_INTERNAL;
+  return KDB_OK;
+}
+
 kdb_status kdb_plan_create(const int64_t* h_offsets, int num_sets, int k, int stride_bytes,
                            kdb_split_mode mode, kdb_plan* out_plan) {
   using kdb::PlanObj;

@@ -46,6 +46,24 @@ class KernelStat(ctypes.Structure):
                 ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_inflight_batches", ctypes.c_int),
+                ("max_batch_requests", ctypes.c_int), ("max_batch_points", ctypes.c_int64)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int), ("n", ctypes.c_int64),
+                ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in
+                ("submitted", "completed", "failed", "batches", "retried_alone",
+                 "max_batch_requests", "max_inflight_batches", "queued", "inflight_requests")] + \
+               [(f, ctypes.c_size_t) for f in ("budget_bytes", "used_bytes", "max_used_bytes")]
+
+
 class KdbError(RuntimeError):
     def __init__(self, code: int, call: str):
         super().__init__(f"{call}: {status_string(code)} ({code})")
@@ -91,6 +109,14 @@ def load():
             "kdb_profile_start": ([], None),
             "kdb_profile_stop": ([ctypes.POINTER(KernelStat), i32], i32),
             "kdb_launch_count": ([], i64),
+            "kdb_batched_workspace_size": ([vp, i32, i32, i32, i32], sz),
+            "kdb_build_batched_async": ([vp, vp, i32, i32, i32, i32, vp, sz, vp, vp], i32),
+            "kdb_error_word_status": ([ctypes.c_uint32], i32),
+            "kdb_server_create": ([ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)], i32),
+            "kdb_server_submit": ([vp, vp, vp, i64, i32, i32, i32, ctypes.POINTER(i64)], i32),
+            "kdb_server_poll": ([vp, ctypes.POINTER(RequestResult), i32, i32], i32),
+            "kdb_server_get_stats": ([vp, ctypes.POINTER(ServerStats)], i32),
+            "kdb_server_destroy": ([vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -228,6 +254,93 @@ class Plan:
         if self._h:
             load().kdb_plan_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kdb_batched_workspace_size(offsets, k: int, stride_bytes: int, mode: int = ROUND_ROBIN) -> int:
+    offs = (ctypes.c_int64 * len(offsets))(*[int(o) for o in offsets])
+    return int(load().kdb_batched_workspace_size(offs, len(offsets) - 1, k, stride_bytes, mode))
+
+
+def kdb_build_batched_async(points, offsets, k: int, mode: int, workspace, error_word,
+                            stream=None) -> None:
+    """Enqueues a batched build with caller workspace (CUDA uint8 tensor) and a
+    device error word (CUDA int32 tensor of one element, or None)."""
+    ptr, n, stride = _records(points)
+    offs = (ctypes.c_int64 * len(offsets))(*[int(o) for o in offsets])
+    if offs[len(offsets) - 1] != n:
+        raise ValueError("offsets must end at the number of records")
+    ew = error_word.data_ptr() if error_word is not None else None
+    _check(load().kdb_build_batched_async(ptr, offs, len(offsets) - 1, k, stride, mode,
+                                          workspace.data_ptr(),
+                                          workspace.numel() * workspace.element_size(), ew,
+                                          _stream(stream)), "kdb_build_batched_async")
+
+
+def kdb_error_word_status(word: int) -> int:
+    return int(load().kdb_error_word_status(word & 0xFFFFFFFF))
+
+
+class Server:
+    """The library's build server (kdb_server_*): requests are submitted as
+    host tensors and built on the current device by continuous batching.
+    Keeps a reference to each request's tensors until its result is polled."""
+
+    def __init__(self, budget_bytes: int, max_inflight_batches: int = 3,
+                 max_batch_requests: int = 4096, max_batch_points: int = 1 << 26):
+        cfg = ServerConfig(int(budget_bytes), int(max_inflight_batches), int(max_batch_requests),
+                           int(max_batch_points))
+        h = ctypes.c_void_p()
+        _check(load().kdb_server_create(ctypes.byref(cfg), ctypes.byref(h)), "kdb_server_create")
+        self._h = h
+        self._keep = {}
+        self._res = (RequestResult * 256)()
+
+    def submit(self, points, k: int, mode: int = ROUND_ROBIN, out=None) -> int:
+        """``points``: CPU tensor (rows = records; pinned for asynchronous
+        copies); ``out``: CPU tensor of the same shape for the tree, or None
+        to build in place."""
+        if points.is_cuda:
+            raise ValueError("Server.submit takes host tensors")
+        ptr, n, stride = _records(points)
+        dst = points if out is None else out
+        if dst.shape != points.shape or dst.dtype != points.dtype or not dst.is_contiguous():
+            raise ValueError("out must be a contiguous tensor shaped like points")
+        rid = ctypes.c_int64(-1)
+        _check(load().kdb_server_submit(self._h, ptr, dst.data_ptr(), n, k, stride, mode,
+                                        ctypes.byref(rid)), "kdb_server_submit")
+        self._keep[rid.value] = (points, dst)
+        return int(rid.value)
+
+    def poll(self, timeout_ms: int = 0, max_results: int = 256) -> list[dict]:
+        m = min(max_results, len(self._res))
+        n = load().kdb_server_poll(self._h, self._res, m, int(timeout_ms))
+        if n < 0:
+            raise KdbError(ERR_INVALID_ARGUMENT, "kdb_server_poll")
+        out = []
+        for i in range(n):
+            r = self._res[i]
+            self._keep.pop(int(r.id), None)
+            out.append({"id": int(r.id), "status": int(r.status), "n": int(r.n),
+                        "submit_s": r.submit_s, "admit_s": r.admit_s, "done_s": r.done_s})
+        return out
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load().kdb_server_get_stats(self._h, ctypes.byref(st)), "kdb_server_get_stats")
+        return {f: int(getattr(st, f)) for f, _ in ServerStats._fields_}
+
+    def close(self) -> None:
+        if self._h:
+            rc = load().kdb_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+            _check(rc, "kdb_server_destroy")
 
     def __del__(self):
         try:

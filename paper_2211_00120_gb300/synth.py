@@ -142,3 +142,22 @@ def with_stride(points: np.ndarray, stride_floats: int, payload_seed: int = 99) 
         bits = (u64(payload_seed, 40, n * (stride_floats - k)) >> np.uint64(32)).astype(np.uint32)
         out[:, k:] = bits.reshape(n, stride_floats - k).view(np.float32)
     return out
+
+
+def poisson_requests(rate: float, duration_s: float, lo: float, hi: float, seed: int = 4):
+    """A Poisson stream of build requests: arrival times (seconds, exponential
+    gaps of mean 1/rate, up to duration_s), sizes log-uniform in [lo, hi], and
+    per request two fair coins: float4 records (else float3) and clustered
+    points (else uniform)."""
+    m = int(rate * duration_s * 1.2 + 64)
+    gaps = -np.log(1.0 - unit_f64(u64(seed, 50, m))) / rate
+    t = np.cumsum(gaps)
+    t = t[t < duration_s]
+    c = len(t)
+    u = unit_f64(u64(seed, 51, c))
+    sizes = np.floor(np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))).astype(np.int64)
+    coins = u64(seed, 52, c)
+    float4 = (coins & np.uint64(1)).astype(bool)
+    clustered = ((coins >> np.uint64(1)) & np.uint64(1)).astype(bool)
+    where = unit_f64(u64(seed, 53, c))  # position of the request's points in a pool
+    return t, sizes, float4, clustered, where

@@ -1,0 +1,156 @@
+"""The build server (kdb_server_*): requests accepted as they arrive and built
+by continuous batching.  Every result must equal the same set built alone by
+kdb_build, bit for bit, whatever it was batched with; batches overlap on the
+device; a failing request fails alone; the memory budget holds."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2211_00120_gb300 import kdb, synth
+
+pytestmark = pytest.mark.gpu
+
+RR, WIDEST = kdb.ROUND_ROBIN, kdb.WIDEST_EXTENT
+
+
+def alone(pts: np.ndarray, k: int, mode: int) -> np.ndarray:
+    d = torch.from_numpy(pts).cuda()
+    kdb.kdb_build(d, k, mode)
+    return d.cpu().numpy()
+
+
+def pinned(a: np.ndarray) -> torch.Tensor:
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+
+
+def drain(srv, count: int, timeout_s: float = 120.0) -> dict:
+    done = {}
+    t_end = time.time() + timeout_s
+    while len(done) < count:
+        assert time.time() < t_end, f"server finished {len(done)} of {count} requests"
+        for r in srv.poll(timeout_ms=100):
+            done[r["id"]] = r
+    return done
+
+
+def request_mix(rng, count: int):
+    """float3 / float4 records, uniform or clustered points, both split modes,
+    sizes log-uniform in [1e3, 2e5]."""
+    out = []
+    for i in range(count):
+        n = int(np.exp(rng.uniform(np.log(1e3), np.log(2e5))))
+        f4 = bool(rng.integers(2))
+        clustered = bool(rng.integers(2))
+        mode = int(rng.integers(2))
+        seed = 100 + i
+        if f4:
+            pts = synth.aniso_float4(n, seed=seed)
+            if clustered:
+                pts[:, :3] = synth.mixed(n, 3, seed=seed)
+        else:
+            pts = synth.mixed(n, 3, seed=seed) if clustered else synth.uniform(n, 3, seed=seed)
+        out.append((pts, 3, mode))
+    return out
+
+
+def test_server_results_equal_alone_and_batches_overlap():
+    srv = kdb.Server(budget_bytes=16 << 30, max_inflight_batches=3)
+    rng = np.random.default_rng(7)
+    # a large float4 widest-extent build first: no later request shares its
+    # layout, so it runs in a batch of its own while the others arrive
+    big = synth.aniso_float4(50_000_000, seed=9)
+    reqs = [(big, 3, WIDEST)] + [r for r in request_mix(rng, 40) if r[0].shape[1] == 3 or r[2] == RR]
+    ins = [pinned(p) for p, _, _ in reqs]
+    outs = [torch.empty_like(t).pin_memory() for t in ins]
+    ids = [srv.submit(ins[i], reqs[i][1], reqs[i][2], out=outs[i]) for i in range(len(reqs))]
+    done = drain(srv, len(ids))
+    st = srv.stats()
+    srv.close()
+    for i, rid in enumerate(ids):
+        assert done[rid]["status"] == kdb.OK
+        pts, k, mode = reqs[i]
+        want = alone(pts, k, mode)
+        assert np.array_equal(outs[i].numpy().view(np.uint32), want.view(np.uint32)), f"request {i}"
+    assert st["completed"] == len(ids) and st["failed"] == 0
+    assert st["max_batch_requests"] >= 2          # requests were batched
+    assert st["max_inflight_batches"] >= 2        # batches were in flight together
+    assert st["max_used_bytes"] <= st["budget_bytes"]
+    # small requests that arrived after the big one finished before it: their
+    # batches ran while it was on the device
+    big_done = done[ids[0]]["done_s"]
+    assert any(done[r]["done_s"] < big_done for r in ids[1:])
+
+
+def test_server_nan_request_fails_alone():
+    srv = kdb.Server(budget_bytes=4 << 30, max_inflight_batches=1)
+    blocker = pinned(synth.uniform(4_000_000, 3, seed=1))
+    sets = [synth.mixed(5000 + 1000 * i, 3, seed=20 + i) for i in range(6)]
+    sets[3][17, 1] = np.nan
+    ins = [pinned(s) for s in sets]
+    outs = [torch.empty_like(t).pin_memory() for t in ins]
+    srv.submit(blocker, 3, RR)
+    # queued while the blocker runs, so they form one batch, which fails on
+    # the NaN and is rerun request by request
+    ids = [srv.submit(ins[i], 3, RR, out=outs[i]) for i in range(len(sets))]
+    done = drain(srv, len(ids) + 1)
+    st = srv.stats()
+    srv.close()
+    for i, rid in enumerate(ids):
+        if i == 3:
+            assert done[rid]["status"] == kdb.ERR_NAN_INPUT
+            continue
+        assert done[rid]["status"] == kdb.OK
+        assert np.array_equal(outs[i].numpy().view(np.uint32), alone(sets[i], 3, RR).view(np.uint32))
+    assert st["failed"] == 1
+    assert st["retried_alone"] >= 2
+
+
+def test_server_admission_by_budget():
+    budget = 256 << 20
+    srv = kdb.Server(budget_bytes=budget, max_inflight_batches=4)
+    # one request larger than the whole budget is refused at submit
+    too_big = pinned(synth.uniform(2_000_000, 3, seed=3))
+    with pytest.raises(kdb.KdbError) as e:
+        srv.submit(too_big, 3, RR)
+    assert e.value.code == kdb.ERR_OUT_OF_MEMORY
+    with pytest.raises(kdb.KdbError) as e:
+        srv.submit(pinned(synth.uniform(100, 3, seed=3)), 0, RR)
+    assert e.value.code == kdb.ERR_INVALID_ARGUMENT
+    # many requests that together exceed the budget: admitted as memory frees
+    sets = [synth.uniform(200_000, 3, seed=40 + i) for i in range(24)]
+    ins = [pinned(s) for s in sets]
+    ids = [srv.submit(t, 3, RR) for t in ins]  # built in place
+    done = drain(srv, len(ids))
+    st = srv.stats()
+    srv.close()
+    assert all(done[r]["status"] == kdb.OK for r in ids)
+    assert st["max_used_bytes"] <= budget
+    assert st["batches"] >= 2
+    for i in (0, 11, 23):
+        assert np.array_equal(ins[i].numpy().view(np.uint32), alone(sets[i], 3, RR).view(np.uint32))
+
+
+def test_batched_async_with_caller_workspace_equals_batched():
+    sizes = [1, 0, 5000, 130_001, 77]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64).tolist()
+    pts = synth.mixed(offs[-1], 3, seed=8)
+    ref = torch.from_numpy(pts).cuda()
+    kdb.kdb_build_batched(ref, offs, 3, WIDEST)
+    d = torch.from_numpy(pts).cuda()
+    ws = torch.empty(kdb.kdb_batched_workspace_size(offs, 3, 12, WIDEST), dtype=torch.uint8,
+                     device="cuda")
+    err = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    kdb.kdb_build_batched_async(d, offs, 3, WIDEST, ws, err)
+    torch.cuda.synchronize()
+    assert kdb.kdb_error_word_status(int(err.item())) == kdb.OK
+    assert torch.equal(d.view(torch.int32), ref.view(torch.int32))
+    # a NaN comes back through the error word, records untouched
+    bad = pts.copy()
+    bad[offs[3] + 5, 0] = np.nan
+    d = torch.from_numpy(bad).cuda()
+    kdb.kdb_build_batched_async(d, offs, 3, WIDEST, ws, err)
+    torch.cuda.synchronize()
+    assert kdb.kdb_error_word_status(int(err.item())) == kdb.ERR_NAN_INPUT
+    assert np.array_equal(d.cpu().numpy().view(np.uint32), bad.view(np.uint32))
