@@ -451,6 +451,15 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     }
   }
 
+  // every list slot holds a local id below m at every position below m, the
+  // spare slot included (it served as radix counters above): list reads stay
+  // in range even if a consistency check has failed
+  {
+    uint16_t* spare = s_lists + (size_t)k * kLocalCap;
+    for (uint32_t i = threadIdx.x; i < m; i += T) spare[i] = 0;
+  }
+  __syncthreads();
+
   // domain of the subtree root (widest mode)
   if (a.mode == 1 && threadIdx.x == 0) {
     if (l0 == 0) {
