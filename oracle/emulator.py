@@ -23,6 +23,11 @@ Readings where the paper is silent or garbled:
     the left side and ``lo = max(lo, x)`` on the right;
   * widest dimension: argmax of hi-lo in float32 with a strict '>' from d=0.
 
+A third split rule, which the paper does not have, is emulated as well:
+``WIDEST_TIGHT`` takes the widest side of each subtree's tight bounding box,
+the min/max over the points that carry the subtree's tag after the update (a
+segmented reduction over each tag's points).
+
 It is the emulator of the paper's algorithm, not the oracle proper (that is the
 recursive builder in ``kd_oracle.c``); tests check the two against each other.
 """
@@ -34,6 +39,7 @@ import numpy as np
 
 ROUND_ROBIN = 0
 WIDEST = 1
+WIDEST_TIGHT = 2
 
 
 def num_levels(n: int) -> int:
@@ -112,7 +118,7 @@ def emulate(points: np.ndarray, k: int, mode: int = ROUND_ROBIN, trace=None):
     arr = [[0, i] for i in range(n)]  # [tag, original index]
     L = num_levels(n)
     dims = {}
-    if mode == WIDEST:
+    if mode in (WIDEST, WIDEST_TIGHT):
         lo = [min((coords[i][d] for i in range(n)), key=_fkey) for d in range(k)]
         hi = [max((coords[i][d] for i in range(n)), key=_fkey) for d in range(k)]
         scene = (lo, hi)
@@ -161,6 +167,16 @@ def emulate(points: np.ndarray, k: int, mode: int = ROUND_ROBIN, trace=None):
                     # iteration's sort it sits at array slot p
                     clip(coords[arr[p][1]], dims[p], t == 2 * p + 1)
                     t = p
+                dims[child] = _widest(blo, bhi)
+        if mode == WIDEST_TIGHT:
+            # each new subtree's box: min / max over the points now tagged with it
+            members = {}
+            for tag, o in arr:
+                members.setdefault(tag, []).append(o)
+            for child, _, _ in new_subtrees:
+                ms = members[child]
+                blo = [min((coords[o][d] for o in ms), key=_fkey) for d in range(k)]
+                bhi = [max((coords[o][d] for o in ms), key=_fkey) for d in range(k)]
                 dims[child] = _widest(blo, bhi)
         if trace:
             trace("update", l, [e[0] for e in arr], [e[1] for e in arr])

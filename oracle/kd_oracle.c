@@ -16,7 +16,10 @@
  *   its right subtree in its split dimension (Sec. 1).  The split dimension is
  *   level mod k for round robin (Sec. 2) or, for the split-widest extension,
  *   the dimension in which the subtree's domain is widest, the domain being
- *   the scene bounding box clipped by every ancestor's plane (Sec. 6).
+ *   the scene bounding box clipped by every ancestor's plane (Sec. 6).  A
+ *   third mode, which the paper does not have, takes the widest side of the
+ *   subtree's tight bounding box instead (the box of the subtree's own
+ *   points, not its domain); it gives other trees than Sec. 6.
  *
  *   Observation 1 (Sec. 2.1) says that once a subtree's points are sorted in
  *   its split dimension, the point at rank ss(lChild(s)) is node s, lower
@@ -32,7 +35,8 @@
  *   - NaN coordinates are rejected (KDO_NAN);
  *   - the widest dimension is argmax over d of (hi[d] - lo[d]) computed in
  *     float32, scanned from d = 0 with a strict '>', so the lowest dimension
- *     wins ties;
+ *     wins ties; box corners are the smallest and largest coordinate under
+ *     the strict order (-0.0 below +0.0);
  *   - subtree sizes are counted level by level here, not with the paper's
  *     O(1) formula (Sec. 4.1), so that the two can be checked against each
  *     other.
@@ -49,7 +53,7 @@
 #include <string.h>
 
 enum { KDO_OK = 0, KDO_INVALID = 1, KDO_NOMEM = 2, KDO_NAN = 4, KDO_NOT_KD = 6 };
-enum { KDO_ROUND_ROBIN = 0, KDO_WIDEST = 1 };
+enum { KDO_ROUND_ROBIN = 0, KDO_WIDEST = 1, KDO_WIDEST_TIGHT = 2 };
 
 typedef struct {
   const unsigned char* base; /* first record */
@@ -134,6 +138,20 @@ static void scene_box(const pointset* P, int64_t N, float* lo, float* hi) {
   }
 }
 
+/* Tight bounding box of the records S[0..n), n >= 1. */
+static void tight_box(const pointset* P, const int64_t* S, int64_t n, float* lo, float* hi) {
+  for (int d = 0; d < P->k; ++d) {
+    float l = coord(P, S[0], d), h = l;
+    for (int64_t i = 1; i < n; ++i) {
+      float v = coord(P, S[i], d);
+      if (cmp_key(v, 0, l, 0) < 0) l = v;
+      if (cmp_key(v, 0, h, 0) > 0) h = v;
+    }
+    lo[d] = l;
+    hi[d] = h;
+  }
+}
+
 typedef struct {
   const pointset* P;
   int64_t N;
@@ -148,7 +166,16 @@ static void build_rec(build_ctx* C, int64_t* S, int64_t n, int64_t s, int depth,
                       const float* lo, const float* hi) {
   if (n == 0) return;
   const int k = C->P->k;
-  int d = (C->mode == KDO_ROUND_ROBIN) ? depth % k : widest_dim(lo, hi, k);
+  int d;
+  if (C->mode == KDO_ROUND_ROBIN) {
+    d = depth % k;
+  } else if (C->mode == KDO_WIDEST) {
+    d = widest_dim(lo, hi, k);
+  } else { /* widest side of the box of this subtree's own points */
+    float tlo[KDO_MAXK], thi[KDO_MAXK];
+    tight_box(C->P, S, n, tlo, thi);
+    d = widest_dim(tlo, thi, k);
+  }
   merge_sort_idx(C->P, d, S, C->tmp, n);
   int64_t p = kdo_subtree_size(2 * s + 1, C->N); /* Observation 1 */
   C->orig_of_node[s] = (int32_t)S[p];
@@ -167,7 +194,7 @@ static int check_args(const void* points, int64_t N, int k, int stride, int mode
   if (N < 0 || N > 2147483647LL) return KDO_INVALID;
   if (k < 1 || k > KDO_MAXK) return KDO_INVALID;
   if (stride < 4 * k || (stride % 4) != 0) return KDO_INVALID;
-  if (mode != KDO_ROUND_ROBIN && mode != KDO_WIDEST) return KDO_INVALID;
+  if (mode != KDO_ROUND_ROBIN && mode != KDO_WIDEST && mode != KDO_WIDEST_TIGHT) return KDO_INVALID;
   if (N > 0 && points == NULL) return KDO_INVALID;
   return KDO_OK;
 }
@@ -217,7 +244,8 @@ int kdo_build(const void* points, int64_t N, int k, int stride, int mode,
  *       (x_d(i), orig(i)) < (x_d(p), orig(p)) if i lies in p's left subtree
  *       and > if in the right one, with d = p's split dimension.  For the
  *       widest mode the dimensions are recomputed top-down from the built
- *       tree's own planes and the scene box.
+ *       tree's own planes and the scene box; for the tight-box mode from
+ *       the box of each node's subtree in the built tree.
  * Because the left-balanced shape is implicit in the array layout and the
  * valid arrangement is unique under the strict order, (1) and (2) together
  * are equivalent to equality with kdo_build.  *first_bad receives the first
@@ -248,6 +276,19 @@ int kdo_check(const void* in_points, const void* out_points, const int32_t* orig
         for (int64_t t = s + 1; t > 1; t >>= 1) ++lvl;
         dim[s] = (unsigned char)(lvl % k);
       }
+    } else if (mode == KDO_WIDEST_TIGHT) {
+      /* the records of node s's subtree, gathered by walking its levels */
+      int64_t* sub = (int64_t*)malloc((size_t)N * sizeof *sub);
+      if (!sub) { free(seen); free(dim); return KDO_NOMEM; }
+      for (int64_t s = 0; s < N; ++s) {
+        int64_t cnt = 0;
+        for (int64_t first = s, width = 1; first < N; first = 2 * first + 1, width *= 2)
+          for (int64_t t = first; t < first + width && t < N; ++t) sub[cnt++] = t;
+        float lo[KDO_MAXK], hi[KDO_MAXK];
+        tight_box(&Out, sub, cnt, lo, hi);
+        dim[s] = (unsigned char)widest_dim(lo, hi, k);
+      }
+      free(sub);
     } else {
       /* top-down: the domain of node s is the scene box clipped by the
          planes of its ancestors; walk the path from the root each time */
@@ -346,7 +387,16 @@ int kdo_node(const void* points, int64_t N, int k, int stride, int mode, int64_t
   int lvl = 0;
   for (int j = depth; j >= 0; --j) {
     s = path[j];
-    int d = (mode == KDO_ROUND_ROBIN) ? lvl % k : widest_dim(lo, hi, k);
+    int d;
+    if (mode == KDO_ROUND_ROBIN) {
+      d = lvl % k;
+    } else if (mode == KDO_WIDEST) {
+      d = widest_dim(lo, hi, k);
+    } else {
+      float tlo[KDO_MAXK], thi[KDO_MAXK];
+      tight_box(&P, S + off, n, tlo, thi);
+      d = widest_dim(tlo, thi, k);
+    }
     int64_t p = kdo_subtree_size(2 * s + 1, N);
     quickselect(&P, d, S + off, n, p);
     if (j == 0) {

@@ -21,6 +21,7 @@ import numpy as np
 
 ROUND_ROBIN = 0
 WIDEST = 1
+WIDEST_TIGHT = 2  # widest side of the subtree's own (tight) bounding box
 
 OK = 0
 INVALID = 1

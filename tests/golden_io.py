@@ -34,3 +34,13 @@ def fig1():
         name, *pts = ln.split()
         d[name] = np.array([[float(c) for c in p.split(",")] for p in pts], dtype=np.float32)
     return d["input"], d["expected"]
+
+
+def tight_box():
+    """The hand-derived tight-box example: (input, expected, expected with the
+    clipped domain of Sec. 6)."""
+    d = {}
+    for ln in _lines("tight_box.txt"):
+        name, *pts = ln.split()
+        d[name] = np.array([[float(c) for c in p.split(",")] for p in pts], dtype=np.float32)
+    return d["input"], d["expected"], d["expected_clipped"]

@@ -17,9 +17,9 @@ import pytest
 
 from oracle import emulator, oracle
 from paper_2211_00120_gb300 import synth
-from tests.golden_io import fig1, walkthrough
+from tests.golden_io import fig1, tight_box, walkthrough
 
-RR, WIDEST = oracle.ROUND_ROBIN, oracle.WIDEST
+RR, WIDEST, TIGHT = oracle.ROUND_ROBIN, oracle.WIDEST, oracle.WIDEST_TIGHT
 
 
 # ---------------------------------------------------------------- helpers --
@@ -43,6 +43,25 @@ def dims_of_arrangement(pts, order, k, mode):
     n = len(order)
     if mode == RR:
         return [level(i) % k for i in range(n)]
+    if mode == TIGHT:
+        # widest side of the box of the points in node s's subtree
+        dims = []
+        for s in range(n):
+            sub, frontier = [], [s]
+            while frontier:
+                t = frontier.pop()
+                if t < n:
+                    sub.append(order[t])
+                    frontier += [2 * t + 1, 2 * t + 2]
+            lo = [min((pts[o, d] for o in sub), key=fkey) for d in range(k)]
+            hi = [max((pts[o, d] for o in sub), key=fkey) for d in range(k)]
+            ext = [np.float32(hi[d]) - np.float32(lo[d]) for d in range(k)]
+            best = 0
+            for d in range(1, k):
+                if ext[d] > ext[best]:
+                    best = d
+            dims.append(best)
+        return dims
     lo = [min((pts[i, d] for i in range(n)), key=fkey) for d in range(k)]
     hi = [max((pts[i, d] for i in range(n)), key=fkey) for d in range(k)]
     dims = [0] * n
@@ -120,7 +139,7 @@ def test_sec5_walkthrough_every_step_of_the_level_loop():
 
 
 # ---------------------------------------------------------- brute force --
-@pytest.mark.parametrize("mode", [RR, WIDEST])
+@pytest.mark.parametrize("mode", [RR, WIDEST, TIGHT])
 def test_bruteforce_unique_valid_arrangement(mode):
     """Over all N! arrangements of tie-heavy inputs (N <= 7), exactly one
     satisfies the strict k-d condition, and it is the oracle's."""
@@ -142,7 +161,7 @@ def test_bruteforce_unique_valid_arrangement(mode):
 
 def test_bruteforce_n8_distinct():
     rng = random.Random(77)
-    for mode in (RR, WIDEST):
+    for mode in (RR, WIDEST, TIGHT):
         pts = np.array([[rng.uniform(0, 1) for _ in range(3)] for _ in range(8)], np.float32)
         valid = [p for p in itertools.permutations(range(8)) if is_valid(pts, p, 3, mode)]
         assert len(valid) == 1
@@ -175,7 +194,7 @@ def test_k1_is_sorted_array_in_level_order(n):
     pts = rng.integers(0, max(2, n // 3), size=(n, 1)).astype(np.float32)
     ranked = sorted(range(n), key=lambda i: (fkey(pts[i, 0]), i))
     want = eytzinger(ranked)
-    for mode in (RR, WIDEST):
+    for mode in (RR, WIDEST, TIGHT):
         _, orig = oracle.build(pts, 1, mode)
         assert list(orig) == want
 
@@ -215,7 +234,7 @@ def test_literal_c_precedence_reading_of_ss_is_wrong():
 
 
 # ------------------------------------------------- algorithm agreement --
-@pytest.mark.parametrize("mode", [RR, WIDEST])
+@pytest.mark.parametrize("mode", [RR, WIDEST, TIGHT])
 def test_emulator_of_level_loop_matches_recursive_oracle(mode):
     rng = random.Random(99 + mode)
     for _ in range(300):
@@ -231,7 +250,7 @@ def test_emulator_of_level_loop_matches_recursive_oracle(mode):
 
 
 # ------------------------------------------------------------ invariants --
-@pytest.mark.parametrize("mode", [RR, WIDEST])
+@pytest.mark.parametrize("mode", [RR, WIDEST, TIGHT])
 @pytest.mark.parametrize("gen", ["uniform", "mixed", "aniso"])
 def test_checker_accepts_oracle_output_and_catches_planted_errors(mode, gen):
     n = 5000
@@ -305,9 +324,29 @@ def test_widest_k1_equals_round_robin_and_dominant_axis_splits_first():
 
 
 def test_single_node_selector_matches_full_build():
-    for mode in (RR, WIDEST):
+    for mode in (RR, WIDEST, TIGHT):
         pts = synth.mixed(4000, 3, seed=11)
         _, orig = oracle.build(pts, 3, mode)
         rng = random.Random(mode)
         for s in [0, 1, 2, 3999] + [rng.randrange(4000) for _ in range(30)]:
             assert oracle.node(pts, 3, mode, s) == orig[s]
+
+
+def test_tight_box_hand_example_and_difference_from_clipped_domain():
+    """The hand-derived 7-point example (tests/golden/tight_box.txt): the
+    tight-box rule and the clipped domain of Sec. 6 pick different dimensions
+    at node 2, and each checker rejects the other rule's tree."""
+    pts, want, want_clipped = tight_box()
+
+    def as_orig(expected):
+        return [next(i for i in range(len(pts)) if (pts[i] == row).all()) for row in expected]
+
+    out, orig = oracle.build(pts, 2, TIGHT)
+    assert list(orig) == as_orig(want)
+    _, orig_c = oracle.build(pts, 2, WIDEST)
+    assert list(orig_c) == as_orig(want_clipped)
+    assert oracle.check(pts, out, orig, 2, TIGHT) == -1
+    assert oracle.check(pts, out, orig, 2, WIDEST) >= 0
+    out_c = pts[orig_c]
+    assert oracle.check(pts, out_c, orig_c, 2, TIGHT) >= 0
+
