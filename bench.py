@@ -42,6 +42,9 @@ WORKLOADS = {
     "aniso_1e8_f4_widest": ("1e8 float4 points (xyz + payload) uniform in [0,100)x[0,1)x[0,10) "
                             "(seed 2), widest-extent split",
                             100_000_000, 3, 4, 1, lambda n: synth.aniso_float4(n, seed=2)),
+    "aniso_1e8_f4_tight": ("1e8 float4 points (xyz + payload) uniform in [0,100)x[0,1)x[0,10) "
+                           "(seed 2), widest side of each subtree's tight box",
+                           100_000_000, 3, 4, 2, lambda n: synth.aniso_float4(n, seed=2)),
 }
 # algorithmic bytes per item of each kernel kind (matches the library's
 # profiling counters): used to turn a launch's bytes into items
@@ -556,7 +559,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": desc, "n_points": n, "k": k, "stride_bytes": stride,
-                           "split": "round_robin" if mode == 0 else "widest_extent",
+                           "split": ["round_robin", "widest_extent", "widest_tight_box"][mode],
                            "parallelism": "replicas" if world > 1 else "single_gpu",
                            "l2": "input 1.2+ GB > L2, restored by a device copy before each step"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

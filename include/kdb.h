@@ -58,7 +58,12 @@ typedef struct CUstream_st* kdb_stream_t;
 
 typedef enum {
   KDB_SPLIT_ROUND_ROBIN = 0,   /* dimension = level mod k (Sec. 2) */
-  KDB_SPLIT_WIDEST_EXTENT = 1  /* widest side of the clipped domain (Sec. 6) */
+  KDB_SPLIT_WIDEST_EXTENT = 1, /* widest side of the clipped domain (Sec. 6) */
+  /* widest side of the subtree's tight bounding box, the box of its own
+     points (a rule the paper does not have; Sec. 6 uses the domain instead):
+     same extent arithmetic, corners under the strict order.  k <= 3 only;
+     other k return KDB_ERR_INVALID_ARGUMENT. */
+  KDB_SPLIT_WIDEST_TIGHT = 2
 } kdb_split_mode;
 
 typedef enum {

@@ -208,6 +208,7 @@ struct Plan {
   bool use_lists = false;
   size_t o_rows, o_lists, o_lorig, o_piv, o_l0;
   size_t o_lents = 0;        // list 0 handed to the local finish as entries
+  bool has_lents = false;
   bool can_direct = false;   // records (stride 4k) can be written from their entries
   size_t o_gather = 0, gather_bytes = 0;  // placement through spare workspace
   size_t rec_hist_off = 0;  // record-sort histograms (in u32, inside the histogram area)
@@ -236,6 +237,7 @@ void make_plan(Plan& P) {
   P.rank_passes = ceil_div_i(32 + P.set_bits, 8);
   P.use_local = P.k <= kLocalMaxK;
   P.use_lists = P.use_local && P.k <= 3;
+  if (P.mode == KDB_SPLIT_WIDEST_TIGHT && !P.use_lists) P.too_wide = true;  // not supported
   int levels = 0;
   for (const SetInfo& si : P.sets) levels = std::max(levels, global_levels(P, si.n));
   if (P.use_local) {
@@ -391,7 +393,10 @@ void make_plan(Plan& P) {
   P.o_piv = take(L ? (size_t)kLiftMax * std::max<uint32_t>(P.max_nseg, 1) * 8 : 0);  // last 3 levels
   P.o_l0 = take(G && P.sets.size() > 1 ? T * 16 : 0);  // level-0 array of several sets
   P.can_direct = L && P.stride == 4 * P.k;
-  P.o_lents = take(P.can_direct && G ? T * 16 : 0);
+  // list 0 handed over as entries: records written from them (stride 4k),
+  // and the keys of the tight-box rule in the local finish
+  P.has_lents = (P.can_direct || P.mode == KDB_SPLIT_WIDEST_TIGHT) && G;
+  P.o_lents = take(P.has_lents ? T * 16 : 0);
   P.bytes = o;
   // workspace that is dead once the local finish has run, one contiguous
   // range: the placement may gather the records into it
@@ -407,9 +412,15 @@ kdb_status check_common(int64_t n, int k, int stride) {
 }
 
 kdb_status check_mode(kdb_split_mode mode) {
-  return (mode == KDB_SPLIT_ROUND_ROBIN || mode == KDB_SPLIT_WIDEST_EXTENT)
+  return (mode == KDB_SPLIT_ROUND_ROBIN || mode == KDB_SPLIT_WIDEST_EXTENT ||
+          mode == KDB_SPLIT_WIDEST_TIGHT)
              ? KDB_OK
              : KDB_ERR_INVALID_ARGUMENT;
+}
+// The tight-box rule runs on the presorted lists only (k <= 3).
+kdb_status check_mode_k(kdb_split_mode mode, int k) {
+  if (check_mode(mode) != KDB_OK) return KDB_ERR_INVALID_ARGUMENT;
+  return mode == KDB_SPLIT_WIDEST_TIGHT && k > 3 ? KDB_ERR_INVALID_ARGUMENT : KDB_OK;
 }
 
 #define KDB_CK(call)                      \
@@ -479,6 +490,8 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   ActiveEntry* d_act = at<ActiveEntry>(ws, P.o_act);
   const bool multi = P.sets.size() > 1;
   const bool widest = P.mode == KDB_SPLIT_WIDEST_EXTENT;
+  const bool tight = P.mode == KDB_SPLIT_WIDEST_TIGHT;
+  const bool bydim = widest || tight;  // split dimension stored per node
 
   // tables and zeroed state: look-back words, histograms, tickets, error word
   if (!tables_ready) {
@@ -492,8 +505,8 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   ActiveEntry* d_whole = at<ActiveEntry>(ws, P.o_whole);
   KDB_CK(cudaMemsetAsync(status, 0, P.o_hist - P.o_status, st));
   KDB_CK(cudaMemsetAsync(hist, 0, P.o_bbox - P.o_hist, st));  // hist, tickets, err
-  if (widest) KDB_CK(launch_init_bbox(bbox, (uint32_t)P.sets.size(), k, st));
-  if (out_dim || widest) KDB_CK(cudaMemsetAsync(dims, 0, T, st));
+  if (bydim) KDB_CK(launch_init_bbox(bbox, (uint32_t)P.sets.size(), k, st));
+  if (out_dim || bydim) KDB_CK(cudaMemsetAsync(dims, 0, T, st));
 
   const uint64_t wait_ns =
       (g_fault == KDB_FAULT_LOOKBACK || g_fault == KDB_FAULT_LOOKBACK_PARTITION)
@@ -537,7 +550,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     pa.hist = hist;
     pa.passes = P.rank_passes;
   }
-  pa.bbox = widest ? bbox : nullptr;
+  pa.bbox = bydim ? bbox : nullptr;  // the root's domain and its tight box alike
   pa.err = err;
   {
     Prof pf(K_PREPASS, P.use_lists ? (double)T * (4.0 * k + 16.0) : (double)T * k * (4.0 + (multi ? 8 : 4)), 1, st);
@@ -611,11 +624,11 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
 
   // ---- level loop
   const int levels = (int)P.act.size();
-  if (widest && levels > 0)
+  if (bydim && levels > 0)
   {
     Prof pf(K_WIDEST, 0.0, 1, st);
     KDB_CK(launch_widest_root(d_sets, d_act + P.act_off[0], (uint32_t)P.act[0].size(), bbox, k,
-                              boxA, dims, st));
+                              widest ? boxA : nullptr, dims, st));
   }
   const uint32_t* vals_cur = nullptr;  // level 0: original order
   uint4* lcur[3] = {nullptr, nullptr, nullptr};
@@ -633,7 +646,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   // entries (which hold every coordinate bit) as the nodes are pinned; the
   // caller's array is not read after the prepass, and no placement is left.
   const bool direct = P.can_direct && g_placement.load() == KDB_PLACEMENT_AUTO;
-  uint4* lents = direct ? at<uint4>(ws, P.o_lents) : nullptr;
+  uint4* lents = P.has_lents && (direct || tight) ? at<uint4>(ws, P.o_lents) : nullptr;
   int lat[3] = {0, 0, 0};
   auto level_ctx = [&](int l) {
     LevelCtx x{};
@@ -769,6 +782,18 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       // every list follows the level (sets leaving hand their lists over)
       if (!lazy)
         for (int d = 0; d < k; ++d) KDB_CK(lift(d, l, l + 1, false));
+      if (tight && l + 1 < levels) {
+        // split dimensions of level l + 1 from the first and last entries of
+        // every subtree in each list
+        TightArgs ta{};
+        ta.x = x;
+        for (int d = 0; d < k; ++d) ta.lists[d] = lcur[d];
+        ta.items_next = P.items[l + 1];
+        ta.dims = dims;
+        ta.k = k;
+        Prof pf(K_WIDEST, (double)(x.nact << (l + 1)) * (2.0 * 16 * k + 1), 1, st);
+        KDB_CK(launch_tight_children(ta, st));
+      }
     } else if (P.seg[l]) {
       SegKeyArgs sa{};
       sa.x = x;
@@ -902,7 +927,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   }
 
   // ---- placement
-  if (out_dim && !widest) {
+  if (out_dim && !bydim) {
     Prof pf(K_WIDEST, (double)T, 1, st);
     KDB_CK(launch_rr_dims(dims, d_sets, (uint32_t)P.sets.size(), T, k, st));
   }
@@ -1098,7 +1123,7 @@ int kdb_debug_inject_fault(int fault, int64_t arg) {
 }
 
 size_t kdb_workspace_size(int64_t n, int k, int stride_bytes, kdb_split_mode mode) {
-  if (check_common(n, k, stride_bytes) != KDB_OK || check_mode(mode) != KDB_OK || n <= 1) return 0;
+  if (check_common(n, k, stride_bytes) != KDB_OK || check_mode_k(mode, k) != KDB_OK || n <= 1) return 0;
   Plan P;
   P.sets.push_back(SetInfo{0u, (uint32_t)n});
   P.total = (uint32_t)n;
@@ -1113,7 +1138,7 @@ kdb_status kdb_build_ex(void* d_points, int64_t n, int k, int stride_bytes, kdb_
                         void* d_workspace, size_t workspace_bytes, int32_t* d_out_orig_index,
                         uint8_t* d_out_split_dim, kdb_stream_t stream) {
   kdb_status s = check_common(n, k, stride_bytes);
-  if (s == KDB_OK) s = check_mode(mode);
+  if (s == KDB_OK) s = check_mode_k(mode, k);
   if (s != KDB_OK) return s;
   if (n > 0 && (!d_points || (reinterpret_cast<uintptr_t>(d_points) & 3))) return KDB_ERR_INVALID_ARGUMENT;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -1145,7 +1170,7 @@ kdb_status kdb_build(void* d_points, int64_t n, int k, int stride_bytes, kdb_spl
 kdb_status kdb_build_noalloc(void* d_points, int64_t n, int k, int stride_bytes,
                              kdb_split_mode mode, kdb_stream_t stream) {
   kdb_status s = check_common(n, k, stride_bytes);
-  if (s == KDB_OK) s = check_mode(mode);
+  if (s == KDB_OK) s = check_mode_k(mode, k);
   if (s != KDB_OK) return s;
   if (n > KDB_NOALLOC_MAX_POINTS) return KDB_ERR_INVALID_ARGUMENT;
   if (n <= 1) return KDB_OK;
@@ -1185,7 +1210,7 @@ kdb_status kdb_build_batched(void* d_points, const int64_t* h_offsets, int num_s
   if (h_offsets[0] != 0) return KDB_ERR_INVALID_ARGUMENT;
   const int64_t total = h_offsets[num_sets];
   kdb_status s = check_common(total, k, stride_bytes);
-  if (s == KDB_OK) s = check_mode(mode);
+  if (s == KDB_OK) s = check_mode_k(mode, k);
   if (s != KDB_OK) return s;
   if (total > 0 && (!d_points || (reinterpret_cast<uintptr_t>(d_points) & 3))) return KDB_ERR_INVALID_ARGUMENT;
   Plan P;
@@ -1212,7 +1237,7 @@ kdb_status batched_sets(Plan& P, const int64_t* h_offsets, int num_sets, int k, 
   if (num_sets < 1 || !h_offsets || h_offsets[0] != 0) return KDB_ERR_INVALID_ARGUMENT;
   const int64_t total = h_offsets[num_sets];
   kdb_status s = check_common(total, k, stride_bytes);
-  if (s == KDB_OK) s = check_mode(mode);
+  if (s == KDB_OK) s = check_mode_k(mode, k);
   if (s != KDB_OK) return s;
   P.sets.reserve(num_sets);
   for (int b = 0; b < num_sets; ++b) {
@@ -1282,7 +1307,7 @@ kdb_status kdb_plan_create(const int64_t* h_offsets, int num_sets, int k, int st
   if (num_sets < 1 || !h_offsets || h_offsets[0] != 0) return KDB_ERR_INVALID_ARGUMENT;
   const int64_t total = h_offsets[num_sets];
   kdb_status s = kdb::check_common(total, k, stride_bytes);
-  if (s == KDB_OK) s = kdb::check_mode(mode);
+  if (s == KDB_OK) s = kdb::check_mode_k(mode, k);
   if (s != KDB_OK) return s;
   PlanObj* po = new (std::nothrow) PlanObj();
   if (!po) return KDB_ERR_OUT_OF_MEMORY;
@@ -1386,7 +1411,7 @@ void kdb_plan_destroy(kdb_plan plan) {
 kdb_status kdb_build_host(void* h_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
                           kdb_stream_t stream) {
   kdb_status s = check_common(n, k, stride_bytes);
-  if (s == KDB_OK) s = check_mode(mode);
+  if (s == KDB_OK) s = check_mode_k(mode, k);
   if (s != KDB_OK) return s;
   if (n <= 1) return KDB_OK;
   if (!h_points) return KDB_ERR_INVALID_ARGUMENT;
@@ -1421,7 +1446,7 @@ kdb_status kdb_build_host(void* h_points, int64_t n, int k, int stride_bytes, kd
 kdb_status kdb_validate(const void* d_points, int64_t n, int k, int stride_bytes,
                         kdb_split_mode mode, int64_t* h_first_bad_node, kdb_stream_t stream) {
   kdb_status s = check_common(n, k, stride_bytes);
-  if (s == KDB_OK) s = check_mode(mode);
+  if (s == KDB_OK) s = check_mode_k(mode, k);
   if (s != KDB_OK) return s;
   if (h_first_bad_node) *h_first_bad_node = -1;
   if (n <= 1) return KDB_OK;
@@ -1433,6 +1458,7 @@ kdb_status kdb_validate(const void* d_points, int64_t n, int k, int stride_bytes
   if (s != KDB_OK) return s;
   const uint32_t N = (uint32_t)n;
   const bool widest = mode == KDB_SPLIT_WIDEST_EXTENT;
+  const bool tight = mode == KDB_SPLIT_WIDEST_TIGHT;
   const int L = num_levels(N);
   // single-set tables for the dimension pass (widest mode)
   std::vector<ActiveEntry> act(std::max(1, L - 1));
@@ -1450,8 +1476,9 @@ kdb_status kdb_validate(const void* d_points, int64_t n, int k, int stride_bytes
     return a;
   };
   const size_t o_bad = take(4), o_err = take(4), o_bbox = take(2 * k * 4), o_sets = take(sizeof(SetInfo)),
-               o_act = take(act.size() * sizeof(ActiveEntry)), o_dims = take(widest ? N : 0),
-               o_bA = take(box_bytes), o_bB = take(box_bytes);
+               o_act = take(act.size() * sizeof(ActiveEntry)), o_dims = take(widest || tight ? N : 0),
+               o_bA = take(box_bytes), o_bB = take(box_bytes),
+               o_tbox = take(tight ? (size_t)N * 2 * k * 4 : 0);
   void* ws = nullptr;
   s = pool_alloc(&ws, o, pool, st);
   if (s != KDB_OK) return s;
@@ -1511,7 +1538,15 @@ kdb_status kdb_validate(const void* d_points, int64_t n, int k, int stride_bytes
       }
       if (result != KDB_OK) break;
     }
-    g_launches += widest ? L + 1 : 1;  // prepass, widest passes, check
+    if (tight) {
+      dims = at<uint8_t>(ws, o_dims);
+      if (launch_tight_validate_dims(static_cast<const unsigned char*>(d_points), N, k, stride_bytes,
+                                     at<uint32_t>(ws, o_tbox), dims, st) != cudaSuccess) {
+        result = KDB_ERR_CUDA;
+        break;
+      }
+    }
+    g_launches += widest || tight ? L + 1 : 1;  // prepass / boxes, dimension passes, check
     if (launch_validate(static_cast<const unsigned char*>(d_points), N, k, stride_bytes, mode, dims,
                         bad, st) != cudaSuccess) { result = KDB_ERR_CUDA; break; }
     uint32_t h_bad = 0xFFFFFFFFu;

@@ -61,6 +61,17 @@ struct PivotArgs {
   unsigned char* pts_out;   // records written directly at their nodes (stride = 4k), or nullptr
   int stride;
 };
+// Tight-box split rule: split dimension of every subtree of level l + 1 of
+// the sets that stay on the global levels, from their first and last entries
+// in each list of level l + 1 (kdb_part.cu).
+struct TightArgs {
+  LevelCtx x;               // level l (x.act, x.act_next)
+  const uint4* lists[3];    // the lists of level l + 1
+  uint32_t items_next;      // items of level l + 1
+  uint8_t* dims;
+  int k;
+};
+cudaError_t launch_tight_children(const TightArgs& a, cudaStream_t st);
 // One partition pass advances a list by 1..kLiftMax levels at once.
 constexpr int kLiftMax = 3;
 constexpr int kLiftBins = 1 << kLiftMax;  // descendants of a segment kLiftMax levels down
@@ -237,6 +248,9 @@ cudaError_t launch_widest_root(const SetInfo* sets, const ActiveEntry* act0, uin
                                const uint32_t* bbox, int k, float* boxes0, uint8_t* dims,
                                cudaStream_t st);
 cudaError_t launch_widest_children(const WidestArgs& a, cudaStream_t st);
+// validator, tight-box rule: per-node subtree boxes (n x 2k keys) and dims
+cudaError_t launch_tight_validate_dims(const unsigned char* pts, uint32_t n, int k, int stride,
+                                       uint32_t* box, uint8_t* dims, cudaStream_t st);
 cudaError_t launch_rr_dims(uint8_t* dims, const SetInfo* sets, uint32_t nsets, uint32_t total,
                            int k, cudaStream_t st);
 

@@ -481,10 +481,19 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
   }
   __syncthreads();
 
-  const bool widest = a.mode == 1;
+  const bool widest = a.mode == 1;  // widest side of the clipped domain (Sec. 6)
+  const bool tight = a.mode == 2;   // widest side of the subtree's own box
+  const bool bydim = widest || tight;
   // records written directly at their nodes: the entry of each local id
   const uint4* ent_of = nullptr;
   if (a.pts_out) ent_of = l0 > 0 ? a.lents + ls.off + start0 : a.rows + ls.off;
+  // keys of each local id (tight-box rule: list 0 is handed over as entries)
+  const uint4* key_of = nullptr;
+  if (tight) key_of = l0 > 0 ? a.lents + ls.off + start0 : a.rows + ls.off;
+  if (tight && !key_of) {
+    if (threadIdx.x == 0) atomicOr(a.err, ERR_INTERNAL);
+    return;
+  }
   // split dimension of node tl (index among the block's nodes at depth jj):
   // widest side of its domain, the root's domain clipped by the planes of
   // its ancestors inside the block (Sec. 6)
@@ -502,6 +511,25 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     }
     return widest_dim(lo, hi, k);
   };
+  // split dimension under the tight-box rule of the node whose items sit at
+  // list positions [q0, q1): each list is sorted by key within the node, so
+  // its first and last items hold the node's smallest and largest key
+  auto tight_dim = [&](uint32_t sl, uint32_t q0, uint32_t q1) -> int {
+    int best = 0;
+    float be = 0.0f;
+    for (int d = 0; d < k; ++d) {
+      const uint16_t* list = s_lists + (size_t)slot_of(sl, d) * kLocalCap;
+      const uint4 e0 = key_of[list[q0]], e1 = key_of[list[q1 - 1]];
+      const float lo = __uint_as_float(key_to_float_bits(d == 0 ? e0.x : (d == 1 ? e0.y : e0.z)));
+      const float hi = __uint_as_float(key_to_float_bits(d == 0 ? e1.x : (d == 1 ? e1.y : e1.z)));
+      const float ext = __fsub_rn(hi, lo);
+      if (d == 0 || ext > be) {
+        be = ext;
+        best = d;
+      }
+    }
+    return best;
+  };
   // per depth jj below the block's root (level l0 + jj): the block's layout,
   // the round-robin split dimension and the lists read on deeper levels,
   // computed once
@@ -517,7 +545,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     s_lay[jj] = make_local(tree, L, wk.s_rel << jj, 1u << jj);
     const int dr = L % k;
     s_drr[jj] = (uint8_t)dr;
-    uint32_t need = widest ? (1u << k) - 1u : 0u;
+    uint32_t need = bydim ? (1u << k) - 1u : 0u;
     int md = dr + 1 == k ? 0 : dr + 1;
     for (int q = L + 1, c = 0; q <= tree.L - 1 && c < k; ++q, ++c) {
       need |= 1u << md;
@@ -536,7 +564,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     for (uint32_t p = r.p0 + g0; p < r.p1; p += gs) {
       uint32_t tl, side;
       const uint32_t off = classify(r, p, &tl, &side);
-      const int d = widest ? s_ldim[dbase + tl] : drr;
+      const int d = bydim ? s_ldim[dbase + tl] : drr;
       const uint32_t it = s_lists[(size_t)slot_of(slots, d) * kLocalCap + (p - r.p0 + sb)];
       if (it >= m || off >= kLocalCap) {
         s_bad = 1;
@@ -585,12 +613,14 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
           const uint32_t cnt = 1u << i;
           const Range r = make_range(s_lay[jj], tw << i, cnt);
           if (r.p0 >= r.p1) break;
-          if (widest) {
+          if (bydim) {
             for (uint32_t u = lane; u < cnt; u += 32) {
               const uint32_t tl = (tw << i) + u;
               const uint32_t node = full_nodes(Li) + firsti + tl;
               if (node >= tree.n) continue;
-              const int d = node_dim(jj, tl);
+              const int d = widest ? node_dim(jj, tl)
+                                   : tight_dim(wslots, l_start(s_lay[jj], tl) - r.p0 + sb,
+                                               l_start(s_lay[jj], tl + 1) - r.p0 + sb);
               s_ldim[(1u << jj) - 1 + tl] = (uint8_t)d;
               a.dims[ls.off + node] = (uint8_t)d;
             }
@@ -633,11 +663,11 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     }
     const Range r = make_range(yj, 0, nodes);
     const uint32_t mj = r.p1;
-    if (widest && j > 0) {
+    if ((widest && j > 0) || tight) {
       for (uint32_t tl = threadIdx.x; tl < nodes; tl += T) {
         const uint32_t node = full_nodes(L) + first + tl;
         if (node >= tree.n) continue;
-        const int d = node_dim(j, tl);
+        const int d = widest ? node_dim(j, tl) : tight_dim(slots, l_start(yj, tl), l_start(yj, tl + 1));
         s_ldim[(1u << j) - 1 + tl] = (uint8_t)d;
         a.dims[ls.off + node] = (uint8_t)d;
       }

@@ -60,6 +60,47 @@ __global__ void pivot_kernel(PivotArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Tight-box rule: split dimension of subtree c of level l + 1 = the widest
+// side of the box of its points.  List d of level l + 1 is sorted by
+// (subtree, key_d, index), so the subtree's smallest and largest key_d are
+// its first and last entries: the per-subtree min/max reduction costs two
+// reads per dimension.  Extent arithmetic as for the clipped domain: float32
+// hi - lo, strict '>' from dimension 0.
+__global__ void tight_children_kernel(TightArgs a) {
+  const LevelCtx& x = a.x;
+  const int lc = x.l + 1;
+  const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (x.nact << lc)) return;
+  if (*reinterpret_cast<volatile uint32_t*>(x.err)) return;
+  const uint32_t ei = gid >> lc, c_rel = gid & ((1u << lc) - 1u);
+  const ActiveEntry e = x.act[ei];
+  if (e.next < 0) return;  // the set's next level runs in the local finish
+  const SetInfo si = x.sets[e.set];
+  const Tree tree = make_tree(si.n);
+  const uint32_t node = full_nodes(lc) + c_rel;
+  if (node >= si.n) return;
+  const LevelLayout y = LevelLayout::make(tree, lc);
+  const uint32_t base = x.act_next[e.next].base;
+  const uint32_t first = base + y.seg_start(c_rel), end = base + y.seg_start(c_rel + 1);
+  if (end <= first || end > a.items_next) {
+    atomicOr(x.err, ERR_INTERNAL);
+    return;
+  }
+  int best = 0;
+  float be = 0.0f;
+  for (int d = 0; d < a.k; ++d) {
+    const float lo = __uint_as_float(key_to_float_bits(comp(a.lists[d][first], d)));
+    const float hi = __uint_as_float(key_to_float_bits(comp(a.lists[d][end - 1], d)));
+    const float ext = __fsub_rn(hi, lo);
+    if (d == 0 || ext > be) {
+      be = ext;
+      best = d;
+    }
+  }
+  a.dims[si.off + node] = (uint8_t)best;
+}
+
+// ---------------------------------------------------------------------------
 constexpr int PT = kPartThreads;
 constexpr int PI = kPartItems;
 constexpr int PTILE = PT * PI;
@@ -339,6 +380,13 @@ cudaError_t launch_pivots(const PivotArgs& a, cudaStream_t st) {
   const uint32_t nseg = a.x.nact << a.x.l;
   if (nseg == 0) return cudaSuccess;
   pivot_kernel<<<(nseg + 255) / 256, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tight_children(const TightArgs& a, cudaStream_t st) {
+  const uint32_t n = a.x.nact << (a.x.l + 1);
+  if (n == 0) return cudaSuccess;
+  tight_children_kernel<<<(n + 255) / 256, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -279,8 +279,10 @@ __global__ void widest_root_kernel(const SetInfo* sets, const ActiveEntry* act, 
   for (int d = 0; d < k; ++d) {
     lo[d] = __uint_as_float(key_to_float_bits(bbox[e.set * 2 * k + d]));
     hi[d] = __uint_as_float(key_to_float_bits(bbox[e.set * 2 * k + k + d]));
-    boxes[(uint64_t)e.box0 * 2 * k + d] = lo[d];
-    boxes[(uint64_t)e.box0 * 2 * k + k + d] = hi[d];
+    if (boxes) {  // the root's domain, for the clipped-domain rule
+      boxes[(uint64_t)e.box0 * 2 * k + d] = lo[d];
+      boxes[(uint64_t)e.box0 * 2 * k + k + d] = hi[d];
+    }
   }
   dims[sets[e.set].off] = (uint8_t)widest_of(lo, hi, k);
 }
@@ -538,6 +540,31 @@ __global__ void unmark_kernel(const uint32_t* perm, int32_t* out, uint32_t total
 // ---------------------------------------------------------------------------
 // k-d condition of every node against every ancestor (Sec. 1), in the total
 // order of float_key (-0 < +0); ties are allowed on both sides.
+// Tight-box rule in the validator: the box of node i's subtree is its own
+// point joined with its children's boxes, built bottom-up one level per launch
+// (keys, so that min / max follow the strict order); the node's dimension is
+// the widest side of that box.
+__global__ void tight_box_level_kernel(const unsigned char* pts, uint32_t n, int k, int stride, int l,
+                                       uint32_t* box, uint8_t* dims) {
+  const uint64_t i = (uint64_t)full_nodes(l) + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= n || i >= (uint64_t)full_nodes(l + 1)) return;
+  uint32_t lo[kMaxK], hi[kMaxK];
+  for (int d = 0; d < k; ++d) lo[d] = hi[d] = float_key(__float_as_uint(coord_of(pts, (uint32_t)i, stride, d)));
+  for (uint64_t c = 2 * i + 1; c <= 2 * i + 2 && c < n; ++c)
+    for (int d = 0; d < k; ++d) {
+      lo[d] = min(lo[d], box[c * 2 * k + d]);
+      hi[d] = max(hi[d], box[c * 2 * k + k + d]);
+    }
+  float flo[kMaxK], fhi[kMaxK];
+  for (int d = 0; d < k; ++d) {
+    box[i * 2 * k + d] = lo[d];
+    box[i * 2 * k + k + d] = hi[d];
+    flo[d] = __uint_as_float(key_to_float_bits(lo[d]));
+    fhi[d] = __uint_as_float(key_to_float_bits(hi[d]));
+  }
+  dims[i] = (uint8_t)widest_of(flo, fhi, k);
+}
+
 __global__ void validate_kernel(const unsigned char* pts, uint32_t n, int k, int stride, int mode,
                                 const uint8_t* dims, uint32_t* first_bad) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -595,6 +622,19 @@ cudaError_t launch_widest_root(const SetInfo* sets, const ActiveEntry* act0, uin
   if (nact == 0) return cudaSuccess;
   widest_root_kernel<<<(nact + 127) / 128, 128, 0, st>>>(sets, act0, nact, bbox, k, boxes0, dims);
   return cudaGetLastError();
+}
+
+cudaError_t launch_tight_validate_dims(const unsigned char* pts, uint32_t n, int k, int stride,
+                                       uint32_t* box, uint8_t* dims, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  for (int l = num_levels(n) - 1; l >= 0; --l) {
+    const uint32_t cnt = std::min<uint64_t>((uint64_t)n, (uint64_t)full_nodes(l + 1)) - full_nodes(l);
+    tight_box_level_kernel<<<(cnt + kThreads - 1) / kThreads, kThreads, 0, st>>>(pts, n, k, stride, l,
+                                                                                   box, dims);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_widest_children(const WidestArgs& a, cudaStream_t st) {

@@ -15,6 +15,7 @@ import threading
 
 ROUND_ROBIN = 0
 WIDEST_EXTENT = 1
+WIDEST_TIGHT = 2  # widest side of the subtree's own bounding box (k <= 3)
 
 OK = 0
 ERR_INVALID_ARGUMENT = 1

@@ -24,7 +24,7 @@ from paper_2211_00120_gb300 import kdb, synth
 
 pytestmark = pytest.mark.gpu
 
-RR, WIDEST = kdb.ROUND_ROBIN, kdb.WIDEST_EXTENT
+RR, WIDEST, TIGHT = kdb.ROUND_ROBIN, kdb.WIDEST_EXTENT, kdb.WIDEST_TIGHT
 
 
 def build_like_bench(pts: np.ndarray, k: int, mode: int):
@@ -51,6 +51,16 @@ def test_mixed_1e7_round_robin_equals_oracle():
     pts = synth.mixed(10_000_000, 3, seed=1)
     got, gorig = build_like_bench(pts, 3, RR)
     want, worig = oracle.build(pts, 3, RR)
+    if not np.array_equal(gorig, worig):
+        bad = int(np.flatnonzero(gorig != worig)[0])
+        raise AssertionError(f"node {bad} holds {gorig[bad]}, oracle {worig[bad]}")
+    assert got.view(np.uint32).tobytes() == want.view(np.uint32).tobytes()
+
+
+def test_mixed_1e7_tight_box_equals_oracle():
+    pts = synth.mixed(10_000_000, 3, seed=1)
+    got, gorig = build_like_bench(pts, 3, TIGHT)
+    want, worig = oracle.build(pts, 3, TIGHT)
     if not np.array_equal(gorig, worig):
         bad = int(np.flatnonzero(gorig != worig)[0])
         raise AssertionError(f"node {bad} holds {gorig[bad]}, oracle {worig[bad]}")
