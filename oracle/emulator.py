@@ -97,7 +97,10 @@ def _fkey(v: float):
 
 
 def _widest(lo, hi) -> int:
-    ext = [np.float32(h) - np.float32(lo_) for lo_, h in zip(lo, hi)]
+    if all(isinstance(v, int) for v in list(lo) + list(hi)):
+        ext = [h - lo_ for lo_, h in zip(lo, hi)]  # int32 coordinates: exact
+    else:
+        ext = [np.float32(h) - np.float32(lo_) for lo_, h in zip(lo, hi)]
     best = 0
     for d in range(1, len(ext)):
         if ext[d] > ext[best]:
@@ -110,11 +113,13 @@ def emulate(points: np.ndarray, k: int, mode: int = ROUND_ROBIN, trace=None):
     float32 coordinates).  Returns the original index of the point at each
     node.  ``trace(step, l, tags, order)`` is called after every sort and
     every update (step in {"sort", "update", "final"})."""
-    P = np.asarray(points, dtype=np.float32)
+    ints = np.asarray(points).dtype == np.int32  # int32 coordinates (Sec. 5 uses int2)
+    P = np.asarray(points) if ints else np.asarray(points, dtype=np.float32)
     n = P.shape[0]
     if n == 0:
         return np.zeros(0, dtype=np.int64)
-    coords = [[float(P[i, d]) for d in range(k)] for i in range(n)]
+    conv = int if ints else float
+    coords = [[conv(P[i, d]) for d in range(k)] for i in range(n)]
     arr = [[0, i] for i in range(n)]  # [tag, original index]
     L = num_levels(n)
     dims = {}

@@ -33,6 +33,11 @@
  *     tree is unique; -0.0 orders before +0.0 (the paper compares with '<'
  *     and is silent on equal keys);
  *   - NaN coordinates are rejected (KDO_NAN);
+ *   - coordinates are float32 unless the mode argument carries KDO_INT32
+ *     (the paper's int1 / int2 data, Table 1 and Sec. 5): then they are int32,
+ *     ordered as integers, and box extents are exact 64-bit differences.  The
+ *     clipped-domain rule is float-only here (its planes clip a float box);
+ *     int32 with it is refused as an invalid argument;
  *   - the widest dimension is argmax over d of (hi[d] - lo[d]) computed in
  *     float32, scanned from d = 0 with a strict '>', so the lowest dimension
  *     wins ties; box corners are the smallest and largest coordinate under
@@ -54,15 +59,24 @@
 
 enum { KDO_OK = 0, KDO_INVALID = 1, KDO_NOMEM = 2, KDO_NAN = 4, KDO_NOT_KD = 6 };
 enum { KDO_ROUND_ROBIN = 0, KDO_WIDEST = 1, KDO_WIDEST_TIGHT = 2 };
+enum { KDO_INT32 = 0x100 }; /* flag in the mode argument: int32 coordinates */
+#define KDO_MAXK 8
 
 typedef struct {
   const unsigned char* base; /* first record */
   int64_t stride;            /* bytes between records */
-  int k;                     /* coordinates per record (float32 at offsets 0,4,..) */
+  int k;                     /* coordinates per record (4-byte items at offsets 0,4,..) */
+  int ints;                  /* 1: int32 coordinates, 0: float32 */
 } pointset;
 
 static float coord(const pointset* P, int64_t i, int d) {
   float v;
+  memcpy(&v, P->base + i * P->stride + 4 * (int64_t)d, sizeof v);
+  return v;
+}
+
+static int32_t icoord(const pointset* P, int64_t i, int d) {
+  int32_t v;
   memcpy(&v, P->base + i * P->stride + 4 * (int64_t)d, sizeof v);
   return v;
 }
@@ -80,6 +94,17 @@ static int cmp_key(float a, int64_t ia, float b, int64_t ib) {
   return 0;
 }
 
+/* Strict total order of records a and b in dimension d: by coordinate (as
+ * float32 with -0 < +0, or as int32), then by original index. */
+static int cmp_rec(const pointset* P, int64_t a, int64_t b, int d) {
+  if (P->ints) {
+    int32_t x = icoord(P, a, d), y = icoord(P, b, d);
+    if (x != y) return x < y ? -1 : 1;
+    return a < b ? -1 : (a > b ? 1 : 0);
+  }
+  return cmp_key(coord(P, a, d), a, coord(P, b, d), b);
+}
+
 /* ---------------- plain merge sort of an index list by one dimension ----- */
 static void merge_sort_idx(const pointset* P, int d, int64_t* a, int64_t* tmp, int64_t n) {
   if (n < 2) return;
@@ -88,7 +113,7 @@ static void merge_sort_idx(const pointset* P, int d, int64_t* a, int64_t* tmp, i
   merge_sort_idx(P, d, a + h, tmp, n - h);
   int64_t i = 0, j = h, o = 0;
   while (i < h && j < n) {
-    if (cmp_key(coord(P, a[j], d), a[j], coord(P, a[i], d), a[i]) < 0)
+    if (cmp_rec(P, a[j], a[i], d) < 0)
       tmp[o++] = a[j++];
     else
       tmp[o++] = a[i++];
@@ -138,7 +163,7 @@ static void scene_box(const pointset* P, int64_t N, float* lo, float* hi) {
   }
 }
 
-/* Tight bounding box of the records S[0..n), n >= 1. */
+/* Tight bounding box of the records S[0..n), n >= 1 (float32 coordinates). */
 static void tight_box(const pointset* P, const int64_t* S, int64_t n, float* lo, float* hi) {
   for (int d = 0; d < P->k; ++d) {
     float l = coord(P, S[0], d), h = l;
@@ -152,6 +177,30 @@ static void tight_box(const pointset* P, const int64_t* S, int64_t n, float* lo,
   }
 }
 
+/* Widest side of the tight box of S[0..n): float32 extents as widest_dim,
+ * or for int32 coordinates the exact 64-bit extents max - min, scanned the
+ * same way (strict '>' from d = 0). */
+static int tight_widest(const pointset* P, const int64_t* S, int64_t n) {
+  if (!P->ints) {
+    float lo[KDO_MAXK], hi[KDO_MAXK];
+    tight_box(P, S, n, lo, hi);
+    return widest_dim(lo, hi, P->k);
+  }
+  int best = 0;
+  int64_t bestExt = 0;
+  for (int d = 0; d < P->k; ++d) {
+    int32_t l = icoord(P, S[0], d), h = l;
+    for (int64_t i = 1; i < n; ++i) {
+      int32_t v = icoord(P, S[i], d);
+      if (v < l) l = v;
+      if (v > h) h = v;
+    }
+    int64_t e = (int64_t)h - (int64_t)l;
+    if (d == 0 || e > bestExt) { bestExt = e; best = d; }
+  }
+  return best;
+}
+
 typedef struct {
   const pointset* P;
   int64_t N;
@@ -159,8 +208,6 @@ typedef struct {
   int64_t* tmp;
   int32_t* orig_of_node; /* output: original index stored at node s */
 } build_ctx;
-
-#define KDO_MAXK 8
 
 static void build_rec(build_ctx* C, int64_t* S, int64_t n, int64_t s, int depth,
                       const float* lo, const float* hi) {
@@ -172,14 +219,12 @@ static void build_rec(build_ctx* C, int64_t* S, int64_t n, int64_t s, int depth,
   } else if (C->mode == KDO_WIDEST) {
     d = widest_dim(lo, hi, k);
   } else { /* widest side of the box of this subtree's own points */
-    float tlo[KDO_MAXK], thi[KDO_MAXK];
-    tight_box(C->P, S, n, tlo, thi);
-    d = widest_dim(tlo, thi, k);
+    d = tight_widest(C->P, S, n);
   }
   merge_sort_idx(C->P, d, S, C->tmp, n);
   int64_t p = kdo_subtree_size(2 * s + 1, C->N); /* Observation 1 */
   C->orig_of_node[s] = (int32_t)S[p];
-  float x = coord(C->P, S[p], d);
+  float x = C->P->ints ? 0.0f : coord(C->P, S[p], d); /* plane (clipped-domain rule only) */
   float clo[KDO_MAXK], chi[KDO_MAXK];
   memcpy(clo, lo, sizeof(float) * k);
   memcpy(chi, hi, sizeof(float) * k);
@@ -194,12 +239,16 @@ static int check_args(const void* points, int64_t N, int k, int stride, int mode
   if (N < 0 || N > 2147483647LL) return KDO_INVALID;
   if (k < 1 || k > KDO_MAXK) return KDO_INVALID;
   if (stride < 4 * k || (stride % 4) != 0) return KDO_INVALID;
-  if (mode != KDO_ROUND_ROBIN && mode != KDO_WIDEST && mode != KDO_WIDEST_TIGHT) return KDO_INVALID;
+  if (mode & ~(0xFF | KDO_INT32)) return KDO_INVALID;
+  int split = mode & 0xFF;
+  if (split != KDO_ROUND_ROBIN && split != KDO_WIDEST && split != KDO_WIDEST_TIGHT) return KDO_INVALID;
+  if ((mode & KDO_INT32) && split == KDO_WIDEST) return KDO_INVALID;
   if (N > 0 && points == NULL) return KDO_INVALID;
   return KDO_OK;
 }
 
 static int has_nan(const pointset* P, int64_t N) {
+  if (P->ints) return 0;
   for (int64_t i = 0; i < N; ++i)
     for (int d = 0; d < P->k; ++d)
       if (isnan(coord(P, i, d))) return 1;
@@ -214,15 +263,16 @@ int kdo_build(const void* points, int64_t N, int k, int stride, int mode,
   int rc = check_args(points, N, k, stride, mode);
   if (rc) return rc;
   if (N == 0) return KDO_OK;
-  pointset P = {(const unsigned char*)points, stride, k};
+  pointset P = {(const unsigned char*)points, stride, k, (mode & KDO_INT32) != 0};
+  mode &= 0xFF;
   if (has_nan(&P, N)) return KDO_NAN;
   int64_t* S = (int64_t*)malloc((size_t)N * sizeof *S);
   int64_t* tmp = (int64_t*)malloc((size_t)N * sizeof *tmp);
   int32_t* orig = (int32_t*)malloc((size_t)N * sizeof *orig);
   if (!S || !tmp || !orig) { free(S); free(tmp); free(orig); return KDO_NOMEM; }
   for (int64_t i = 0; i < N; ++i) S[i] = i;
-  float lo[KDO_MAXK], hi[KDO_MAXK];
-  scene_box(&P, N, lo, hi);
+  float lo[KDO_MAXK] = {0}, hi[KDO_MAXK] = {0};
+  if (!P.ints) scene_box(&P, N, lo, hi);
   build_ctx C = {&P, N, mode, tmp, orig};
   build_rec(&C, S, N, 0, 0, lo, hi);
   if (out_points) {
@@ -257,8 +307,9 @@ int kdo_check(const void* in_points, const void* out_points, const int32_t* orig
   if (first_bad) *first_bad = -1;
   if (rc) return rc;
   if (N == 0) return KDO_OK;
-  pointset In = {(const unsigned char*)in_points, stride, k};
-  pointset Out = {(const unsigned char*)out_points, stride, k};
+  pointset In = {(const unsigned char*)in_points, stride, k, (mode & KDO_INT32) != 0};
+  pointset Out = {(const unsigned char*)out_points, stride, k, (mode & KDO_INT32) != 0};
+  mode &= 0xFF;
   unsigned char* seen = (unsigned char*)calloc((size_t)N, 1);
   unsigned char* dim = (unsigned char*)malloc((size_t)N);
   if (!seen || !dim) { free(seen); free(dim); return KDO_NOMEM; }
@@ -284,9 +335,7 @@ int kdo_check(const void* in_points, const void* out_points, const int32_t* orig
         int64_t cnt = 0;
         for (int64_t first = s, width = 1; first < N; first = 2 * first + 1, width *= 2)
           for (int64_t t = first; t < first + width && t < N; ++t) sub[cnt++] = t;
-        float lo[KDO_MAXK], hi[KDO_MAXK];
-        tight_box(&Out, sub, cnt, lo, hi);
-        dim[s] = (unsigned char)widest_dim(lo, hi, k);
+        dim[s] = (unsigned char)tight_widest(&Out, sub, cnt);
       }
       free(sub);
     } else {
@@ -316,7 +365,14 @@ int kdo_check(const void* in_points, const void* out_points, const int32_t* orig
       int64_t child = i;
       for (int64_t p = (i - 1) / 2;; p = (p - 1) / 2) {
         int d = dim[p];
-        int c = cmp_key(coord(&Out, i, d), orig[i], coord(&Out, p, d), orig[p]);
+        /* the strict order on (coordinate, original index) of the two nodes */
+        int c;
+        if (Out.ints) {
+          int32_t xi = icoord(&Out, i, d), xp = icoord(&Out, p, d);
+          c = xi != xp ? (xi < xp ? -1 : 1) : (orig[i] < orig[p] ? -1 : (orig[i] > orig[p] ? 1 : 0));
+        } else {
+          c = cmp_key(coord(&Out, i, d), orig[i], coord(&Out, p, d), orig[p]);
+        }
         int left = (child == 2 * p + 1);
         if ((left && c >= 0) || (!left && c <= 0)) { bad = i; break; }
         child = p;
@@ -350,12 +406,11 @@ static void quickselect(const pointset* P, int d, int64_t* a, int64_t n, int64_t
   while (lo < hi) {
     int64_t pi = lo + (int64_t)(lcg_next(&st) % (uint64_t)(hi - lo + 1));
     int64_t piv = a[pi];
-    float pv = coord(P, piv, d);
     a[pi] = a[hi];
     a[hi] = piv;
     int64_t store = lo;
     for (int64_t i = lo; i < hi; ++i) {
-      if (cmp_key(coord(P, a[i], d), a[i], pv, piv) < 0) {
+      if (cmp_rec(P, a[i], piv, d) < 0) {
         int64_t t = a[i]; a[i] = a[store]; a[store] = t;
         ++store;
       }
@@ -372,13 +427,14 @@ int kdo_node(const void* points, int64_t N, int k, int stride, int mode, int64_t
   int rc = check_args(points, N, k, stride, mode);
   if (rc) return rc;
   if (node < 0 || node >= N || !out_orig) return KDO_INVALID;
-  pointset P = {(const unsigned char*)points, stride, k};
+  pointset P = {(const unsigned char*)points, stride, k, (mode & KDO_INT32) != 0};
+  mode &= 0xFF;
   if (has_nan(&P, N)) return KDO_NAN;
   int64_t* S = (int64_t*)malloc((size_t)N * sizeof *S);
   if (!S) return KDO_NOMEM;
   for (int64_t i = 0; i < N; ++i) S[i] = i;
-  float lo[KDO_MAXK], hi[KDO_MAXK];
-  scene_box(&P, N, lo, hi);
+  float lo[KDO_MAXK] = {0}, hi[KDO_MAXK] = {0};
+  if (!P.ints) scene_box(&P, N, lo, hi);
   int64_t path[64];
   int depth = 0;
   for (int64_t t = node; t > 0; t = (t - 1) / 2) path[depth++] = t;
@@ -393,9 +449,7 @@ int kdo_node(const void* points, int64_t N, int k, int stride, int mode, int64_t
     } else if (mode == KDO_WIDEST) {
       d = widest_dim(lo, hi, k);
     } else {
-      float tlo[KDO_MAXK], thi[KDO_MAXK];
-      tight_box(&P, S + off, n, tlo, thi);
-      d = widest_dim(tlo, thi, k);
+      d = tight_widest(&P, S + off, n);
     }
     int64_t p = kdo_subtree_size(2 * s + 1, N);
     quickselect(&P, d, S + off, n, p);
@@ -403,7 +457,7 @@ int kdo_node(const void* points, int64_t N, int k, int stride, int mode, int64_t
       *out_orig = (int32_t)S[off + p];
       break;
     }
-    float x = coord(&P, S[off + p], d);
+    float x = P.ints ? 0.0f : coord(&P, S[off + p], d);
     if (path[j - 1] == 2 * s + 1) {
       hi[d] = x;
       n = p;

@@ -7,8 +7,10 @@ module compiles it with gcc on first use (or when ``compile_oracle()`` is
 called from the build step) and exposes numpy-level functions.
 
 Records are passed as 2-D C-contiguous numpy arrays with 4-byte items (one row
-per record, row bytes = stride); the first ``k`` columns are float32
-coordinates and any further columns are payload that is moved, never compared.
+per record, row bytes = stride); the first ``k`` columns are the coordinates
+and any further columns are payload that is moved, never compared.  An int32
+array has int32 coordinates (the oracle's INT32 mode flag is set from the
+dtype); any other 4-byte dtype is read as float32.
 """
 from __future__ import annotations
 
@@ -22,6 +24,7 @@ import numpy as np
 ROUND_ROBIN = 0
 WIDEST = 1
 WIDEST_TIGHT = 2  # widest side of the subtree's own (tight) bounding box
+INT32 = 0x100     # mode flag: int32 coordinates
 
 OK = 0
 INVALID = 1
@@ -73,6 +76,10 @@ def _records(points: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(points)
 
 
+def _mode(points: np.ndarray, mode: int) -> int:
+    return mode | (INT32 if points.dtype == np.int32 else 0)
+
+
 class OracleError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what} returned {code}")
@@ -85,7 +92,8 @@ def build(points: np.ndarray, k: int, mode: int = ROUND_ROBIN):
     n, w = pts.shape
     out = np.empty_like(pts)
     orig = np.empty(n, dtype=np.int32)
-    rc = _load().kdo_build(pts.ctypes.data, n, k, 4 * w, mode, out.ctypes.data, orig.ctypes.data)
+    rc = _load().kdo_build(pts.ctypes.data, n, k, 4 * w, _mode(pts, mode), out.ctypes.data,
+                           orig.ctypes.data)
     if rc != OK:
         raise OracleError(rc, "kdo_build")
     return out, orig
@@ -101,7 +109,7 @@ def check(in_points: np.ndarray, out_points: np.ndarray, orig: np.ndarray, k: in
         raise ValueError("shape mismatch")
     bad = ctypes.c_int64(-1)
     rc = _load().kdo_check(a.ctypes.data, b.ctypes.data, o.ctypes.data, a.shape[0], k,
-                           4 * a.shape[1], mode, ctypes.byref(bad))
+                           4 * a.shape[1], _mode(a, mode), ctypes.byref(bad))
     if rc not in (OK, NOT_KD):
         raise OracleError(rc, "kdo_check")
     return int(bad.value)
@@ -111,7 +119,7 @@ def node(points: np.ndarray, k: int, mode: int, s: int) -> int:
     """Original index of the record that belongs at node ``s``."""
     pts = _records(points)
     out = ctypes.c_int32(-1)
-    rc = _load().kdo_node(pts.ctypes.data, pts.shape[0], k, 4 * pts.shape[1], mode, s,
+    rc = _load().kdo_node(pts.ctypes.data, pts.shape[0], k, 4 * pts.shape[1], _mode(pts, mode), s,
                           ctypes.byref(out))
     if rc != OK:
         raise OracleError(rc, "kdo_node")

@@ -24,8 +24,16 @@ RR, WIDEST, TIGHT = oracle.ROUND_ROBIN, oracle.WIDEST, oracle.WIDEST_TIGHT
 
 # ---------------------------------------------------------------- helpers --
 def fkey(v):
+    if isinstance(v, (int, np.integer)):
+        return (int(v), 1)  # int32 coordinates: plain integer order
     v = float(v)
     return (v, 0 if math.copysign(1.0, v) < 0 else 1)
+
+
+def extent(lo, hi):
+    if isinstance(lo, (int, np.integer)):
+        return int(hi) - int(lo)  # exact for int32 coordinates
+    return np.float32(hi) - np.float32(lo)
 
 
 def strict_less(pts, a, b, d):
@@ -55,7 +63,7 @@ def dims_of_arrangement(pts, order, k, mode):
                     frontier += [2 * t + 1, 2 * t + 2]
             lo = [min((pts[o, d] for o in sub), key=fkey) for d in range(k)]
             hi = [max((pts[o, d] for o in sub), key=fkey) for d in range(k)]
-            ext = [np.float32(hi[d]) - np.float32(lo[d]) for d in range(k)]
+            ext = [extent(lo[d], hi[d]) for d in range(k)]
             best = 0
             for d in range(1, k):
                 if ext[d] > ext[best]:
@@ -350,3 +358,93 @@ def test_tight_box_hand_example_and_difference_from_clipped_domain():
     out_c = pts[orig_c]
     assert oracle.check(pts, out_c, orig_c, 2, TIGHT) >= 0
 
+
+
+# ------------------------------------------------------- int32 coordinates --
+INT_EDGE = [-2**31, -2**31 + 1, -1, 0, 1, 2**24, 2**24 + 1, 2**31 - 2, 2**31 - 1]
+
+
+def int_points(rng, n, k):
+    """int32 coordinates with the extremes and pairs that float32 cannot tell
+    apart (2^24 and 2^24 + 1; 2^31 - 2 and 2^31 - 1)."""
+    return np.array([[rng.choice(INT_EDGE) for _ in range(k)] for _ in range(n)], dtype=np.int32)
+
+
+def test_sec5_walkthrough_as_int2_points():
+    """Sec. 5's points are int2: built as int32 coordinates the oracle gives the
+    final array the paper prints, and the emulator every intermediate state."""
+    blocks = walkthrough()
+    _, _, _, x0, y0 = blocks[0]
+    pts = np.array([x0, y0], dtype=np.int32).T.copy()
+    out, orig = oracle.build(pts, 2, RR)
+    _, _, _, xf, yf = blocks[-1]
+    np.testing.assert_array_equal(out, np.array([xf, yf], dtype=np.int32).T)
+    seen = []
+
+    def trace(step, l, tags, order):
+        seen.append((step, l, list(tags), [int(pts[o, 0]) for o in order],
+                     [int(pts[o, 1]) for o in order]))
+
+    emulator.emulate(pts, 2, RR, trace)
+    assert seen == [tuple(b) for b in blocks[1:]]
+
+
+@pytest.mark.parametrize("mode", [RR, TIGHT])
+def test_int32_bruteforce_unique_valid_arrangement(mode):
+    rng = random.Random(4321 + mode)
+    for n in range(1, 8):
+        for _ in range(4 if n == 7 else 8):
+            k = rng.randint(1, 3)
+            pts = int_points(rng, n, k)
+            valid = [p for p in itertools.permutations(range(n)) if is_valid(pts, p, k, mode)]
+            assert len(valid) == 1, (n, k, pts)
+            _, orig = oracle.build(pts, k, mode)
+            assert tuple(int(o) for o in orig) == valid[0]
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 100, 1000])
+def test_int32_k1_is_sorted_array_in_level_order(n):
+    rng = random.Random(n)
+    pts = int_points(rng, n, 1)
+    ranked = sorted(range(n), key=lambda i: (int(pts[i, 0]), i))
+    for mode in (RR, TIGHT):
+        assert list(oracle.build(pts, 1, mode)[1]) == eytzinger(ranked)
+
+
+@pytest.mark.parametrize("mode", [RR, TIGHT])
+def test_int32_emulator_matches_oracle_and_checker(mode):
+    rng = random.Random(55 + mode)
+    for _ in range(150):
+        n = rng.randint(1, 60)
+        k = rng.randint(1, 3)
+        pts = int_points(rng, n, k) if rng.random() < 0.5 else \
+            np.array([[rng.randint(-50, 50) for _ in range(k)] for _ in range(n)], np.int32)
+        out, orig = oracle.build(pts, k, mode)
+        assert list(emulator.emulate(pts, k, mode)) == list(orig)
+        assert oracle.check(pts, out, orig, k, mode) == -1
+    # planted: a coordinate changed by one
+    pts = synth_ints(5000, 3, seed=8)
+    out, orig = oracle.build(pts, 3, mode)
+    o2 = out.copy()
+    o2[77, 1] += 1
+    assert oracle.check(pts, o2, orig, 3, mode) >= 0
+
+
+def synth_ints(n, k, seed):
+    rng = np.random.default_rng(seed)
+    return rng.integers(-2**31, 2**31, size=(n, k), dtype=np.int64).astype(np.int32)
+
+
+@pytest.mark.parametrize("mode", [RR, TIGHT])
+def test_int32_equals_float32_on_values_both_represent_exactly(mode):
+    """Integers below 2^24 in magnitude are exact in float32 and order the same
+    way, so the int32 tree and the float32 tree of the same values agree."""
+    rng = np.random.default_rng(9)
+    ints = rng.integers(-2**24 + 1, 2**24, size=(3000, 3)).astype(np.int32)
+    assert list(oracle.build(ints, 3, mode)[1]) == list(oracle.build(ints.astype(np.float32), 3, mode)[1])
+
+
+def test_int32_with_the_clipped_domain_rule_is_refused():
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.build(synth_ints(10, 3, seed=1), 3, WIDEST)
+    assert e.value.code == oracle.INVALID
