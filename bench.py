@@ -42,6 +42,9 @@ WORKLOADS = {
     "aniso_1e8_f4_widest": ("1e8 float4 points (xyz + payload) uniform in [0,100)x[0,1)x[0,10) "
                             "(seed 2), widest-extent split",
                             100_000_000, 3, 4, 1, lambda n: synth.aniso_float4(n, seed=2)),
+    "int1_1e8_rr": ("1e8 int32 points, k = 1 (the paper's int1 data), uniform over the int32 "
+                    "range (seed 0), round-robin split",
+                    100_000_000, 1, 1, 0, lambda n: synth.int32_uniform(n, 1, seed=0)),
     "aniso_1e8_f4_tight": ("1e8 float4 points (xyz + payload) uniform in [0,100)x[0,1)x[0,10) "
                            "(seed 2), widest side of each subtree's tight box",
                            100_000_000, 3, 4, 2, lambda n: synth.aniso_float4(n, seed=2)),

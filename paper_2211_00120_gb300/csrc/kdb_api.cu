@@ -177,7 +177,8 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Plan {
   std::vector<SetInfo> sets;
   uint32_t total = 0;
-  int k = 0, stride = 0, mode = 0;
+  int k = 0, stride = 0, mode = 0;  // mode: the split rule (low byte of the mode argument)
+  bool ints = false;                // int32 coordinates (KDB_COORDS_INT32)
   int Lmax = 0;        // most levels of any set
   int rb = 0;          // bits of a rank
   int set_bits = 0;    // bits of a set id in the rank-sort keys (0 for one set)
@@ -411,17 +412,26 @@ kdb_status check_common(int64_t n, int k, int stride) {
   return KDB_OK;
 }
 
+// The mode argument: a split rule in the low byte, optionally OR'ed with
+// KDB_COORDS_INT32.
 kdb_status check_mode(kdb_split_mode mode) {
-  return (mode == KDB_SPLIT_ROUND_ROBIN || mode == KDB_SPLIT_WIDEST_EXTENT ||
-          mode == KDB_SPLIT_WIDEST_TIGHT)
-             ? KDB_OK
-             : KDB_ERR_INVALID_ARGUMENT;
+  const int m = (int)mode;
+  if (m & ~(0xFF | KDB_COORDS_INT32)) return KDB_ERR_INVALID_ARGUMENT;
+  const int split = m & 0xFF;
+  if (split != KDB_SPLIT_ROUND_ROBIN && split != KDB_SPLIT_WIDEST_EXTENT &&
+      split != KDB_SPLIT_WIDEST_TIGHT)
+    return KDB_ERR_INVALID_ARGUMENT;
+  // the clipped-domain rule clips float boxes: float32 coordinates only
+  if ((m & KDB_COORDS_INT32) && split == KDB_SPLIT_WIDEST_EXTENT) return KDB_ERR_INVALID_ARGUMENT;
+  return KDB_OK;
 }
 // The tight-box rule runs on the presorted lists only (k <= 3).
 kdb_status check_mode_k(kdb_split_mode mode, int k) {
   if (check_mode(mode) != KDB_OK) return KDB_ERR_INVALID_ARGUMENT;
-  return mode == KDB_SPLIT_WIDEST_TIGHT && k > 3 ? KDB_ERR_INVALID_ARGUMENT : KDB_OK;
+  return ((int)mode & 0xFF) == KDB_SPLIT_WIDEST_TIGHT && k > 3 ? KDB_ERR_INVALID_ARGUMENT : KDB_OK;
 }
+inline int split_of(int mode) { return mode & 0xFF; }
+inline bool ints_of(int mode) { return (mode & KDB_COORDS_INT32) != 0; }
 
 #define KDB_CK(call)                      \
   do {                                    \
@@ -552,6 +562,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   }
   pa.bbox = bydim ? bbox : nullptr;  // the root's domain and its tight box alike
   pa.err = err;
+  pa.ints = P.ints;
   {
     Prof pf(K_PREPASS, P.use_lists ? (double)T * (4.0 * k + 16.0) : (double)T * k * (4.0 + (multi ? 8 : 4)), 1, st);
     KDB_CK(launch_prepass(pa, sms, st));
@@ -628,7 +639,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   {
     Prof pf(K_WIDEST, 0.0, 1, st);
     KDB_CK(launch_widest_root(d_sets, d_act + P.act_off[0], (uint32_t)P.act[0].size(), bbox, k,
-                              widest ? boxA : nullptr, dims, st));
+                              widest ? boxA : nullptr, dims, P.ints, st));
   }
   const uint32_t* vals_cur = nullptr;  // level 0: original order
   uint4* lcur[3] = {nullptr, nullptr, nullptr};
@@ -775,6 +786,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       pv.mode = P.mode;
       pv.pts_out = direct ? pts : nullptr;
       pv.stride = P.stride;
+      pv.ints = P.ints;
       {
         Prof pf(K_PIVOT, (double)(x.nact << l) * 20, 1, st);
         KDB_CK(launch_pivots(pv, st));
@@ -791,6 +803,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
         ta.items_next = P.items[l + 1];
         ta.dims = dims;
         ta.k = k;
+        ta.ints = P.ints;
         Prof pf(K_WIDEST, (double)(x.nact << (l + 1)) * (2.0 * 16 * k + 1), 1, st);
         KDB_CK(launch_tight_children(ta, st));
       }
@@ -922,6 +935,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     la.err = err;
     la.lents = lents;
     la.pts_out = direct ? pts : nullptr;
+    la.ints = P.ints;
     Prof pf(K_LOCAL, (double)T * (4.0 + 4.0 * k + 4.0), 1, st);
     KDB_CK(launch_local_finish(la, st));
   }
@@ -941,7 +955,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   if (direct) {
     // every record is at its node already; put the input back if the build failed
     Prof pf(K_PLACEMENT, 0.0, 1, st);
-    KDB_CK(launch_restore(pts, ents0, T, k, err, st));
+    KDB_CK(launch_restore(pts, ents0, T, k, err, P.ints, st));
   } else if (g_placement.load() == KDB_PLACEMENT_AUTO && (size_t)T * P.stride <= P.gather_bytes) {
     Prof pf(K_PLACEMENT, (double)T * (4.0 + 4.0 * P.stride), 2, st);
     KDB_CK(launch_place_gather(pm, at<unsigned char>(ws, P.o_gather), sms, st));
@@ -1129,7 +1143,8 @@ size_t kdb_workspace_size(int64_t n, int k, int stride_bytes, kdb_split_mode mod
   P.total = (uint32_t)n;
   P.k = k;
   P.stride = stride_bytes;
-  P.mode = mode;
+  P.mode = split_of(mode);
+  P.ints = ints_of(mode);
   make_plan(P);
   return P.bytes;
 }
@@ -1157,7 +1172,8 @@ kdb_status kdb_build_ex(void* d_points, int64_t n, int k, int stride_bytes, kdb_
   P.total = (uint32_t)n;
   P.k = k;
   P.stride = stride_bytes;
-  P.mode = mode;
+  P.mode = split_of(mode);
+  P.ints = ints_of(mode);
   return run(P, static_cast<unsigned char*>(d_points), d_workspace, workspace_bytes,
              d_out_orig_index, d_out_split_dim, st);
 }
@@ -1180,7 +1196,8 @@ kdb_status kdb_build_noalloc(void* d_points, int64_t n, int k, int stride_bytes,
   P.total = (uint32_t)n;
   P.k = k;
   P.stride = stride_bytes;
-  P.mode = mode;
+  P.mode = split_of(mode);
+  P.ints = ints_of(mode);
   make_plan(P);
   if (P.too_wide || P.bytes > KDB_NOALLOC_SCRATCH_BYTES) return KDB_ERR_INVALID_ARGUMENT;
   int dev = 0;
@@ -1223,7 +1240,8 @@ kdb_status kdb_build_batched(void* d_points, const int64_t* h_offsets, int num_s
   P.total = (uint32_t)total;
   P.k = k;
   P.stride = stride_bytes;
-  P.mode = mode;
+  P.mode = split_of(mode);
+  P.ints = ints_of(mode);
   return run(P, static_cast<unsigned char*>(d_points), nullptr, 0, nullptr, nullptr,
              reinterpret_cast<cudaStream_t>(stream));
 }
@@ -1247,7 +1265,8 @@ kdb_status batched_sets(Plan& P, const int64_t* h_offsets, int num_sets, int k, 
   P.total = (uint32_t)total;
   P.k = k;
   P.stride = stride_bytes;
-  P.mode = mode;
+  P.mode = split_of(mode);
+  P.ints = ints_of(mode);
   return KDB_OK;
 }
 }  // namespace
@@ -1322,7 +1341,8 @@ kdb_status kdb_plan_create(const int64_t* h_offsets, int num_sets, int k, int st
   P.total = (uint32_t)total;
   P.k = k;
   P.stride = stride_bytes;
-  P.mode = mode;
+  P.mode = split_of(mode);
+  P.ints = ints_of(mode);
   po->trivial = total <= 1;
   if (po->trivial) {
     *out_plan = reinterpret_cast<kdb_plan>(po);
@@ -1457,8 +1477,9 @@ kdb_status kdb_validate(const void* d_points, int64_t n, int k, int stride_bytes
   s = device_setup(&dev, &pool, &sms);
   if (s != KDB_OK) return s;
   const uint32_t N = (uint32_t)n;
-  const bool widest = mode == KDB_SPLIT_WIDEST_EXTENT;
-  const bool tight = mode == KDB_SPLIT_WIDEST_TIGHT;
+  const bool widest = split_of(mode) == KDB_SPLIT_WIDEST_EXTENT;
+  const bool tight = split_of(mode) == KDB_SPLIT_WIDEST_TIGHT;
+  const bool ints = ints_of(mode);
   const int L = num_levels(N);
   // single-set tables for the dimension pass (widest mode)
   std::vector<ActiveEntry> act(std::max(1, L - 1));
@@ -1515,7 +1536,7 @@ kdb_status kdb_validate(const void* d_points, int64_t n, int k, int stride_bytes
       pa.err = at<uint32_t>(ws, o_err);
       if (launch_prepass(pa, sms, st) != cudaSuccess) { result = KDB_ERR_CUDA; break; }
       ActiveEntry* d_act = at<ActiveEntry>(ws, o_act);
-      if (launch_widest_root(pa.sets, d_act, 1, pa.bbox, k, at<float>(ws, o_bA), dims, st) !=
+      if (launch_widest_root(pa.sets, d_act, 1, pa.bbox, k, at<float>(ws, o_bA), dims, false, st) !=
           cudaSuccess) { result = KDB_ERR_CUDA; break; }
       for (int l = 0; l + 1 < L; ++l) {
         WidestArgs wa{};
@@ -1541,7 +1562,7 @@ kdb_status kdb_validate(const void* d_points, int64_t n, int k, int stride_bytes
     if (tight) {
       dims = at<uint8_t>(ws, o_dims);
       if (launch_tight_validate_dims(static_cast<const unsigned char*>(d_points), N, k, stride_bytes,
-                                     at<uint32_t>(ws, o_tbox), dims, st) != cudaSuccess) {
+                                     at<uint32_t>(ws, o_tbox), dims, ints, st) != cudaSuccess) {
         result = KDB_ERR_CUDA;
         break;
       }

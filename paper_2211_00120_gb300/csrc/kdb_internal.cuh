@@ -142,14 +142,50 @@ __host__ __device__ inline uint32_t float_key(uint32_t bits) {
 __host__ __device__ inline uint32_t key_to_float_bits(uint32_t key) {
   return key ^ ((key & 0x80000000u) ? 0x80000000u : 0xFFFFFFFFu);
 }
+// int32 coordinates: two's complement order is the unsigned order of the
+// bits with the sign bit flipped.
+__host__ __device__ inline uint32_t coord_key(uint32_t bits, bool ints) {
+  return ints ? bits ^ 0x80000000u : float_key(bits);
+}
+__host__ __device__ inline uint32_t key_to_coord_bits(uint32_t key, bool ints) {
+  return ints ? key ^ 0x80000000u : key_to_float_bits(key);
+}
 #ifdef __CUDACC__
 // The record of a point from its entry (k <= 3 coordinate keys, no payload):
 // the key map is a bijection, so the bits are the input's.
-__device__ inline void write_record_from_entry(unsigned char* rec, const uint4& e, int k) {
+__device__ inline void write_record_from_entry(unsigned char* rec, const uint4& e, int k, bool ints) {
   uint32_t* r = reinterpret_cast<uint32_t*>(rec);
-  r[0] = key_to_float_bits(e.x);
-  if (k > 1) r[1] = key_to_float_bits(e.y);
-  if (k > 2) r[2] = key_to_float_bits(e.z);
+  r[0] = key_to_coord_bits(e.x, ints);
+  if (k > 1) r[1] = key_to_coord_bits(e.y, ints);
+  if (k > 2) r[2] = key_to_coord_bits(e.z, ints);
+}
+// Widest side of a box whose corners are coordinate keys: float32 extents
+// hi - lo (round to nearest, no contraction) or, for int32 coordinates, exact
+// 64-bit differences; scanned from d = 0 with a strict '>', so the lowest
+// dimension wins ties (an extent that is NaN, inf - inf, never wins).
+__device__ inline int widest_of_keys(const uint32_t* lo, const uint32_t* hi, int k, bool ints) {
+  int best = 0;
+  if (ints) {
+    int64_t be = 0;
+    for (int d = 0; d < k; ++d) {
+      const int64_t e = (int64_t)(int32_t)(hi[d] ^ 0x80000000u) - (int64_t)(int32_t)(lo[d] ^ 0x80000000u);
+      if (d == 0 || e > be) {
+        be = e;
+        best = d;
+      }
+    }
+    return best;
+  }
+  float be = 0.0f;
+  for (int d = 0; d < k; ++d) {
+    const float e = __fsub_rn(__uint_as_float(key_to_float_bits(hi[d])),
+                              __uint_as_float(key_to_float_bits(lo[d])));
+    if (d == 0 || e > be) {
+      be = e;
+      best = d;
+    }
+  }
+  return best;
 }
 #endif
 

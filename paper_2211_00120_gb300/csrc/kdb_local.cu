@@ -286,6 +286,9 @@ __device__ inline uint32_t classify(const Range& r, uint32_t p, uint32_t* u_out,
   return r.nb + sl + pr;
 }
 
+// kMode: the split rule (0 round robin, 1 clipped domain, 2 tight box), a
+// template argument so that each rule's kernel carries only its own code.
+template <int kMode>
 __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ uint32_t s_w[W];
@@ -328,7 +331,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
 
   // ---- the k lists: local ids 0..m-1 ordered by (key_d, original index)
   int dpar = -1;  // dimension the items arrive sorted by (the parent's split)
-  if (l0 > 0) dpar = a.mode == 0 ? (l0 - 1) % k : a.dims[ls.off + (s0 - 1) / 2];
+  if (l0 > 0) dpar = kMode == 0 ? (l0 - 1) % k : a.dims[ls.off + (s0 - 1) / 2];
   uint16_t* s_wh = s_lists + (size_t)k * kLocalCap;  // radix counters (spare list slot)
   if (a.lorig && l0 > 0) {
     // The global passes hand over every list of the subtree as original
@@ -461,7 +464,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
   __syncthreads();
 
   // domain of the subtree root (widest mode)
-  if (a.mode == 1 && threadIdx.x == 0) {
+  if (kMode == 1 && threadIdx.x == 0) {
     if (l0 == 0) {
       for (int d = 0; d < k; ++d) {
         s_box[d] = __uint_as_float(key_to_float_bits(a.bbox[wk.set * 2 * k + d]));
@@ -481,9 +484,9 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
   }
   __syncthreads();
 
-  const bool widest = a.mode == 1;  // widest side of the clipped domain (Sec. 6)
-  const bool tight = a.mode == 2;   // widest side of the subtree's own box
-  const bool bydim = widest || tight;
+  constexpr bool widest = kMode == 1;  // widest side of the clipped domain (Sec. 6)
+  constexpr bool tight = kMode == 2;   // widest side of the subtree's own box
+  constexpr bool bydim = widest || tight;
   // records written directly at their nodes: the entry of each local id
   const uint4* ent_of = nullptr;
   if (a.pts_out) ent_of = l0 > 0 ? a.lents + ls.off + start0 : a.rows + ls.off;
@@ -515,20 +518,14 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
   // list positions [q0, q1): each list is sorted by key within the node, so
   // its first and last items hold the node's smallest and largest key
   auto tight_dim = [&](uint32_t sl, uint32_t q0, uint32_t q1) -> int {
-    int best = 0;
-    float be = 0.0f;
+    uint32_t lo[3], hi[3];
     for (int d = 0; d < k; ++d) {
       const uint16_t* list = s_lists + (size_t)slot_of(sl, d) * kLocalCap;
       const uint4 e0 = key_of[list[q0]], e1 = key_of[list[q1 - 1]];
-      const float lo = __uint_as_float(key_to_float_bits(d == 0 ? e0.x : (d == 1 ? e0.y : e0.z)));
-      const float hi = __uint_as_float(key_to_float_bits(d == 0 ? e1.x : (d == 1 ? e1.y : e1.z)));
-      const float ext = __fsub_rn(hi, lo);
-      if (d == 0 || ext > be) {
-        be = ext;
-        best = d;
-      }
+      lo[d] = d == 0 ? e0.x : (d == 1 ? e0.y : e0.z);
+      hi[d] = d == 0 ? e1.x : (d == 1 ? e1.y : e1.z);
     }
-    return best;
+    return widest_of_keys(lo, hi, k, a.ints);
   };
   // per depth jj below the block's root (level l0 + jj): the block's layout,
   // the round-robin split dimension and the lists read on deeper levels,
@@ -576,7 +573,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
         a.perm[node] = o;
         if (ent_of) {  // the record goes straight to its node
           const uint4 e = ent_of[it];
-          write_record_from_entry(a.pts_out + (uint64_t)node * a.stride, e, k);
+          write_record_from_entry(a.pts_out + (uint64_t)node * a.stride, e, k, a.ints);
           if (widest)
             s_lplane[dbase + tl] = __uint_as_float(key_to_float_bits(d == 0 ? e.x : (d == 1 ? e.y : e.z)));
         } else if (widest) {
@@ -736,9 +733,14 @@ size_t local_smem_bytes(int k) {
 cudaError_t launch_local_finish(const LocalArgs& a, cudaStream_t st) {
   if (a.nwork == 0) return cudaSuccess;
   const size_t smem = local_smem_bytes(a.k);
-  cudaError_t e = ensure_smem((const void*)local_finish_kernel, smem);
+  const void* fn = a.mode == 1   ? (const void*)local_finish_kernel<1>
+                   : a.mode == 2 ? (const void*)local_finish_kernel<2>
+                                 : (const void*)local_finish_kernel<0>;
+  cudaError_t e = ensure_smem(fn, smem);
   if (e != cudaSuccess) return e;
-  local_finish_kernel<<<a.nwork, T, smem, st>>>(a);
+  if (a.mode == 1) local_finish_kernel<1><<<a.nwork, T, smem, st>>>(a);
+  else if (a.mode == 2) local_finish_kernel<2><<<a.nwork, T, smem, st>>>(a);
+  else local_finish_kernel<0><<<a.nwork, T, smem, st>>>(a);
   return cudaGetLastError();
 }
 

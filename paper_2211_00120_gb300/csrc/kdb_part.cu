@@ -56,7 +56,7 @@ __global__ void pivot_kernel(PivotArgs a) {
   const uint4 ent = a.lists[d][pos];
   a.piv[gid] = make_uint2(comp(ent, d), ent.w);
   a.perm[si.off + node] = ent.w;
-  if (a.pts_out) write_record_from_entry(a.pts_out + (uint64_t)(si.off + node) * a.stride, ent, a.k);
+  if (a.pts_out) write_record_from_entry(a.pts_out + (uint64_t)(si.off + node) * a.stride, ent, a.k, a.ints);
 }
 
 // ---------------------------------------------------------------------------
@@ -65,7 +65,7 @@ __global__ void pivot_kernel(PivotArgs a) {
 // (subtree, key_d, index), so the subtree's smallest and largest key_d are
 // its first and last entries: the per-subtree min/max reduction costs two
 // reads per dimension.  Extent arithmetic as for the clipped domain: float32
-// hi - lo, strict '>' from dimension 0.
+// hi - lo (exact differences for int32 coordinates), strict '>' from d = 0.
 __global__ void tight_children_kernel(TightArgs a) {
   const LevelCtx& x = a.x;
   const int lc = x.l + 1;
@@ -86,18 +86,12 @@ __global__ void tight_children_kernel(TightArgs a) {
     atomicOr(x.err, ERR_INTERNAL);
     return;
   }
-  int best = 0;
-  float be = 0.0f;
+  uint32_t lo[3], hi[3];
   for (int d = 0; d < a.k; ++d) {
-    const float lo = __uint_as_float(key_to_float_bits(comp(a.lists[d][first], d)));
-    const float hi = __uint_as_float(key_to_float_bits(comp(a.lists[d][end - 1], d)));
-    const float ext = __fsub_rn(hi, lo);
-    if (d == 0 || ext > be) {
-      be = ext;
-      best = d;
-    }
+    lo[d] = comp(a.lists[d][first], d);
+    hi[d] = comp(a.lists[d][end - 1], d);
   }
-  a.dims[si.off + node] = (uint8_t)best;
+  a.dims[si.off + node] = (uint8_t)widest_of_keys(lo, hi, a.k, a.ints);
 }
 
 // ---------------------------------------------------------------------------

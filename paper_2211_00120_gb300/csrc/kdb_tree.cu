@@ -102,8 +102,8 @@ __global__ void __launch_bounds__(kThreads) prepass_kernel(PrepassArgs a) {
       uint32_t key = 0;
       if (ok) {
         const uint32_t bits = *reinterpret_cast<const uint32_t*>(rec + 4 * d);
-        if ((bits & 0x7FFFFFFFu) > 0x7F800000u) nan = true;
-        key = float_key(bits);
+        if (!a.ints && (bits & 0x7FFFFFFFu) > 0x7F800000u) nan = true;
+        key = coord_key(bits, a.ints);
         if (d < 3) ek[d] = key;
         lo[d] = min(lo[d], key);
         hi[d] = max(hi[d], key);
@@ -271,20 +271,18 @@ __global__ void __launch_bounds__(kThreads) seg_level_keys_kernel(SegKeyArgs a) 
 // its node's domain).  Split dimension = widest side (hi - lo in float32,
 // first dimension wins ties).
 __global__ void widest_root_kernel(const SetInfo* sets, const ActiveEntry* act, uint32_t nact,
-                                   const uint32_t* bbox, int k, float* boxes, uint8_t* dims) {
+                                   const uint32_t* bbox, int k, float* boxes, uint8_t* dims, bool ints) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nact) return;
   const ActiveEntry e = act[i];
-  float lo[kMaxK], hi[kMaxK];
-  for (int d = 0; d < k; ++d) {
-    lo[d] = __uint_as_float(key_to_float_bits(bbox[e.set * 2 * k + d]));
-    hi[d] = __uint_as_float(key_to_float_bits(bbox[e.set * 2 * k + k + d]));
-    if (boxes) {  // the root's domain, for the clipped-domain rule
-      boxes[(uint64_t)e.box0 * 2 * k + d] = lo[d];
-      boxes[(uint64_t)e.box0 * 2 * k + k + d] = hi[d];
+  const uint32_t* lo = bbox + e.set * 2 * k;  // the scene box: the root's domain and its tight box
+  const uint32_t* hi = lo + k;
+  if (boxes)  // the root's domain, for the clipped-domain rule (float32 only)
+    for (int d = 0; d < k; ++d) {
+      boxes[(uint64_t)e.box0 * 2 * k + d] = __uint_as_float(key_to_float_bits(lo[d]));
+      boxes[(uint64_t)e.box0 * 2 * k + k + d] = __uint_as_float(key_to_float_bits(hi[d]));
     }
-  }
-  dims[sets[e.set].off] = (uint8_t)widest_of(lo, hi, k);
+  dims[sets[e.set].off] = (uint8_t)widest_of_keys(lo, hi, k, ints);
 }
 
 __global__ void widest_children_kernel(WidestArgs a) {
@@ -519,10 +517,10 @@ __global__ void place_copy_back_kernel(PermuteArgs a, const unsigned char* tmp, 
 // After a failed build that wrote records at their nodes: put every record
 // back from its entry, so the caller's array is as it was.
 __global__ void restore_kernel(unsigned char* pts, const uint4* ents, uint32_t total, int k,
-                               const uint32_t* err) {
+                               const uint32_t* err, bool ints) {
   if (*reinterpret_cast<const volatile uint32_t*>(err) == 0) return;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
-    write_record_from_entry(pts + (uint64_t)i * (4 * k), ents[i], k);
+    write_record_from_entry(pts + (uint64_t)i * (4 * k), ents[i], k, ints);
 }
 
 // Scene-box accumulators of every set: lower keys at the top, upper at zero.
@@ -545,24 +543,22 @@ __global__ void unmark_kernel(const uint32_t* perm, int32_t* out, uint32_t total
 // (keys, so that min / max follow the strict order); the node's dimension is
 // the widest side of that box.
 __global__ void tight_box_level_kernel(const unsigned char* pts, uint32_t n, int k, int stride, int l,
-                                       uint32_t* box, uint8_t* dims) {
+                                       uint32_t* box, uint8_t* dims, bool ints) {
   const uint64_t i = (uint64_t)full_nodes(l) + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i >= n || i >= (uint64_t)full_nodes(l + 1)) return;
   uint32_t lo[kMaxK], hi[kMaxK];
-  for (int d = 0; d < k; ++d) lo[d] = hi[d] = float_key(__float_as_uint(coord_of(pts, (uint32_t)i, stride, d)));
+  for (int d = 0; d < k; ++d)
+    lo[d] = hi[d] = coord_key(__float_as_uint(coord_of(pts, (uint32_t)i, stride, d)), ints);
   for (uint64_t c = 2 * i + 1; c <= 2 * i + 2 && c < n; ++c)
     for (int d = 0; d < k; ++d) {
       lo[d] = min(lo[d], box[c * 2 * k + d]);
       hi[d] = max(hi[d], box[c * 2 * k + k + d]);
     }
-  float flo[kMaxK], fhi[kMaxK];
   for (int d = 0; d < k; ++d) {
     box[i * 2 * k + d] = lo[d];
     box[i * 2 * k + k + d] = hi[d];
-    flo[d] = __uint_as_float(key_to_float_bits(lo[d]));
-    fhi[d] = __uint_as_float(key_to_float_bits(hi[d]));
   }
-  dims[i] = (uint8_t)widest_of(flo, fhi, k);
+  dims[i] = (uint8_t)widest_of_keys(lo, hi, k, ints);
 }
 
 __global__ void validate_kernel(const unsigned char* pts, uint32_t n, int k, int stride, int mode,
@@ -571,10 +567,11 @@ __global__ void validate_kernel(const unsigned char* pts, uint32_t n, int k, int
   if (i == 0 || i >= n) return;
   uint32_t child = i;
   uint32_t p = (i - 1) / 2;
+  const bool ints = (mode & 0x100) != 0;  // int32 coordinates
   for (;;) {
-    const int d = mode == 0 ? level_of(p) % k : dims[p];
-    const uint32_t ki = float_key(__float_as_uint(coord_of(pts, i, stride, d)));
-    const uint32_t kp = float_key(__float_as_uint(coord_of(pts, p, stride, d)));
+    const int d = (mode & 0xFF) == 0 ? level_of(p) % k : dims[p];
+    const uint32_t ki = coord_key(__float_as_uint(coord_of(pts, i, stride, d)), ints);
+    const uint32_t kp = coord_key(__float_as_uint(coord_of(pts, p, stride, d)), ints);
     const bool left = child == 2 * p + 1;
     if ((left && ki > kp) || (!left && ki < kp)) {
       atomicMin(first_bad, i);
@@ -617,20 +614,20 @@ cudaError_t launch_seg_level_keys(const SegKeyArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_widest_root(const SetInfo* sets, const ActiveEntry* act0, uint32_t nact,
-                               const uint32_t* bbox, int k, float* boxes0, uint8_t* dims,
+                               const uint32_t* bbox, int k, float* boxes0, uint8_t* dims, bool ints,
                                cudaStream_t st) {
   if (nact == 0) return cudaSuccess;
-  widest_root_kernel<<<(nact + 127) / 128, 128, 0, st>>>(sets, act0, nact, bbox, k, boxes0, dims);
+  widest_root_kernel<<<(nact + 127) / 128, 128, 0, st>>>(sets, act0, nact, bbox, k, boxes0, dims, ints);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tight_validate_dims(const unsigned char* pts, uint32_t n, int k, int stride,
-                                       uint32_t* box, uint8_t* dims, cudaStream_t st) {
+                                       uint32_t* box, uint8_t* dims, bool ints, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   for (int l = num_levels(n) - 1; l >= 0; --l) {
     const uint32_t cnt = std::min<uint64_t>((uint64_t)n, (uint64_t)full_nodes(l + 1)) - full_nodes(l);
     tight_box_level_kernel<<<(cnt + kThreads - 1) / kThreads, kThreads, 0, st>>>(pts, n, k, stride, l,
-                                                                                   box, dims);
+                                                                                   box, dims, ints);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -677,11 +674,11 @@ cudaError_t launch_place_gather(const PermuteArgs& a, unsigned char* tmp, int nu
 }
 
 cudaError_t launch_restore(unsigned char* pts, const uint4* ents, uint32_t total, int k, const uint32_t* err,
-                           cudaStream_t st) {
+                           bool ints, cudaStream_t st) {
   if (total == 0) return cudaSuccess;
   // a small grid: the kernel usually finds no error and returns at once
   const uint32_t grid = std::min<uint32_t>((total + kThreads - 1) / kThreads, 1024);
-  restore_kernel<<<grid, kThreads, 0, st>>>(pts, ents, total, k, err);
+  restore_kernel<<<grid, kThreads, 0, st>>>(pts, ents, total, k, err, ints);
   return cudaGetLastError();
 }
 

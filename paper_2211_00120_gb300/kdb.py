@@ -16,6 +16,7 @@ import threading
 ROUND_ROBIN = 0
 WIDEST_EXTENT = 1
 WIDEST_TIGHT = 2  # widest side of the subtree's own bounding box (k <= 3)
+COORDS_INT32 = 0x100  # mode flag: int32 coordinates (set from an int32 tensor's dtype)
 
 OK = 0
 ERR_INVALID_ARGUMENT = 1
@@ -149,6 +150,13 @@ def _records(points):
     return points.data_ptr(), points.shape[0], 4 * points.shape[1]
 
 
+def _mode(points, mode: int) -> int:
+    """The mode argument: the split rule, plus COORDS_INT32 for int32 records."""
+    import torch
+
+    return mode | (COORDS_INT32 if points.dtype == torch.int32 else 0)
+
+
 def _check(rc: int, call: str):
     if rc != OK:
         raise KdbError(rc, call)
@@ -166,7 +174,7 @@ def kdb_build(points, k: int, mode: int = ROUND_ROBIN, stream=None) -> None:
     """Permutes the CUDA tensor ``points`` (rows = records, first k columns
     float32 coordinates) in place into a left-balanced k-d tree."""
     ptr, n, stride = _records(points)
-    _check(load().kdb_build(ptr, n, k, stride, mode, _stream(stream)), "kdb_build")
+    _check(load().kdb_build(ptr, n, k, stride, _mode(points, mode), _stream(stream)), "kdb_build")
 
 
 def kdb_workspace_size(n: int, k: int, stride_bytes: int, mode: int = ROUND_ROBIN) -> int:
@@ -180,8 +188,8 @@ def kdb_build_ex(points, k: int, mode: int = ROUND_ROBIN, workspace=None, out_or
     wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
     oi = out_orig_index.data_ptr() if out_orig_index is not None else None
     od = out_split_dim.data_ptr() if out_split_dim is not None else None
-    _check(load().kdb_build_ex(ptr, n, k, stride, mode, ws, wsb, oi, od, _stream(stream)),
-           "kdb_build_ex")
+    _check(load().kdb_build_ex(ptr, n, k, stride, _mode(points, mode), ws, wsb, oi, od,
+                               _stream(stream)), "kdb_build_ex")
 
 
 def kdb_build_batched(points, offsets, k: int, mode: int = ROUND_ROBIN, stream=None) -> None:
@@ -190,14 +198,15 @@ def kdb_build_batched(points, offsets, k: int, mode: int = ROUND_ROBIN, stream=N
     offs = (ctypes.c_int64 * len(offsets))(*[int(o) for o in offsets])
     if offs[len(offsets) - 1] != n:
         raise ValueError("offsets must end at the number of records")
-    _check(load().kdb_build_batched(ptr, offs, len(offsets) - 1, k, stride, mode, _stream(stream)),
-           "kdb_build_batched")
+    _check(load().kdb_build_batched(ptr, offs, len(offsets) - 1, k, stride, _mode(points, mode),
+                                    _stream(stream)), "kdb_build_batched")
 
 
 def kdb_build_host(points, k: int, mode: int = ROUND_ROBIN, stream=None) -> None:
     """``points``: host (CPU, ideally pinned) tensor, permuted in place."""
     ptr, n, stride = _records(points)
-    _check(load().kdb_build_host(ptr, n, k, stride, mode, _stream(stream)), "kdb_build_host")
+    _check(load().kdb_build_host(ptr, n, k, stride, _mode(points, mode), _stream(stream)),
+           "kdb_build_host")
 
 
 NOALLOC_MAX_POINTS = 262144
@@ -208,7 +217,7 @@ def kdb_build_noalloc(points, k: int, mode: int = ROUND_ROBIN, stream=None) -> N
     callers that cannot allocate device memory when they build.  At most
     NOALLOC_MAX_POINTS records; calls must not overlap on the GPU."""
     ptr, n, stride = _records(points)
-    _check(load().kdb_build_noalloc(ptr, n, k, stride, mode, _stream(stream)),
+    _check(load().kdb_build_noalloc(ptr, n, k, stride, _mode(points, mode), _stream(stream)),
            "kdb_build_noalloc")
 
 
@@ -216,7 +225,7 @@ def kdb_validate(points, k: int, mode: int = ROUND_ROBIN, stream=None) -> int:
     """Returns -1 if ``points`` is a valid k-d tree, else the first bad node."""
     ptr, n, stride = _records(points)
     bad = ctypes.c_int64(-1)
-    rc = load().kdb_validate(ptr, n, k, stride, mode, ctypes.byref(bad), _stream(stream))
+    rc = load().kdb_validate(ptr, n, k, stride, _mode(points, mode), ctypes.byref(bad), _stream(stream))
     if rc not in (OK, ERR_NOT_A_KD_TREE):
         raise KdbError(rc, "kdb_validate")
     return int(bad.value)
@@ -277,7 +286,7 @@ def kdb_build_batched_async(points, offsets, k: int, mode: int, workspace, error
     if offs[len(offsets) - 1] != n:
         raise ValueError("offsets must end at the number of records")
     ew = error_word.data_ptr() if error_word is not None else None
-    _check(load().kdb_build_batched_async(ptr, offs, len(offsets) - 1, k, stride, mode,
+    _check(load().kdb_build_batched_async(ptr, offs, len(offsets) - 1, k, stride, _mode(points, mode),
                                           workspace.data_ptr(),
                                           workspace.numel() * workspace.element_size(), ew,
                                           _stream(stream)), "kdb_build_batched_async")
@@ -313,8 +322,8 @@ class Server:
         if dst.shape != points.shape or dst.dtype != points.dtype or not dst.is_contiguous():
             raise ValueError("out must be a contiguous tensor shaped like points")
         rid = ctypes.c_int64(-1)
-        _check(load().kdb_server_submit(self._h, ptr, dst.data_ptr(), n, k, stride, mode,
-                                        ctypes.byref(rid)), "kdb_server_submit")
+        _check(load().kdb_server_submit(self._h, ptr, dst.data_ptr(), n, k, stride,
+                                        _mode(points, mode), ctypes.byref(rid)), "kdb_server_submit")
         self._keep[rid.value] = (points, dst)
         return int(rid.value)
 

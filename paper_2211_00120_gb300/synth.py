@@ -161,3 +161,15 @@ def poisson_requests(rate: float, duration_s: float, lo: float, hi: float, seed:
     clustered = ((coins >> np.uint64(1)) & np.uint64(1)).astype(bool)
     where = unit_f64(u64(seed, 53, c))  # position of the request's points in a pool
     return t, sizes, float4, clustered, where
+
+
+def int32_uniform(n: int, k: int = 1, seed: int = 0, stream: int = 60) -> np.ndarray:
+    """(n, k) int32, i.i.d. uniform over the whole int32 range (the top 32 bits
+    of each SplitMix64 draw)."""
+    out = np.empty((n, k), dtype=np.int32)
+    chunk = 1 << 24
+    for s in range(0, n, chunk):
+        m = min(chunk, n - s)
+        out[s:s + m] = (u64(seed, stream, m * k, s * k) >> np.uint64(32)).astype(np.uint32).view(
+            np.int32).reshape(m, k)
+    return out
