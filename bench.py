@@ -183,6 +183,25 @@ def cpu_baseline(workload: str, target_s: float = 15.0):
                       f"({desc}); oracle single-threaded, {total:.1f} s"}
 
 
+def cpu_parallel_baseline(workload: str, log2_points: int = 24):
+    """The paper's level loop ported to host threads (oracle/paper_cpu.c, one
+    thread per core) on a bounded sample: the first 2^log2_points points of
+    the workload's generator."""
+    from oracle import paper_cpu
+
+    desc, n_full, k, sf, mode, gen = WORKLOADS[workload]
+    n = min(n_full, 1 << log2_points)
+    pts = gen(n)
+    paper_cpu.build(pts[:4096], k, mode)  # load the library
+    t0 = time.perf_counter()
+    paper_cpu.build(pts, k, mode)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt / 1e6, "unit": "Mpts/s", "cores": paper_cpu.cores(),
+            "kind": "paper level loop on host threads (parallel sort per level + tag update)",
+            "sample": f"one build of the first {n} points of the same generator ({desc}), "
+                      f"{dt:.1f} s"}
+
+
 def batched_vs_serial(sets: int = 4096, lo: int = 100, hi: int = 1_000_000, seed: int = 3,
                       steps: int = 3, world: int = 1, rank: int = 0, dist=None):
     """Many independent float3 sets (sizes log-uniform in [lo, hi], uniform
@@ -552,9 +571,10 @@ def main():
     if world == 1 and not args.no_serving:
         served = serving()
 
-    cpu = None
+    cpu = cpu_par = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)
+        cpu_par = cpu_parallel_baseline(args.workload)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": world,
@@ -565,7 +585,8 @@ def main():
                            "split": ["round_robin", "widest_extent", "widest_tight_box"][mode],
                            "parallelism": "replicas" if world > 1 else "single_gpu",
                            "l2": "input 1.2+ GB > L2, restored by a device copy before each step"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_parallel": cpu_par,
+                "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "kernel_ms_per_step": kernel_ms,
                 "placement_in_place": in_place, "batched": batched, "serving": served}
         print(json.dumps(line), flush=True)
