@@ -691,6 +691,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     pa.k = k;
     pa.mode = P.mode;
     pa.dlist = d;
+    pa.pos_first = P.mode == KDB_SPLIT_ROUND_ROBIN && p % k == d ? 1 : 0;
     pa.n = P.items[p];
     pa.next_items = q < levels ? P.items[q] : 0;
     pa.total = T;

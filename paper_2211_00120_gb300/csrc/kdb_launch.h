@@ -81,6 +81,8 @@ struct PartArgs {
   LevelCtx x;               // level p, the input list's level
   const ActiveEntry* act_out;  // active sets of level p + b
   int b;                    // levels to advance, 1..kLiftMax (b > 1: one active set)
+  int pos_first;            // 1: the list is in level p's split order (its dimension is
+                            // level p's), so the first level goes by position
   int handoff;              // 1: every set goes to the local finish at level p + b
   const uint4* in;          // list sorted by (tag on level p, key_dlist, index)
   uint4* out_next;          // the list on level p + b

@@ -104,6 +104,7 @@ static_assert(kLiftMax == 3, "pivot tables hold depth-3 subtrees");
 
 struct LiftSeg {
   uint32_t start;              // first position of the segment in the level-p array
+  uint32_t left0;              // ss(lChild) of the segment's root: its pivot's rank
   uint32_t cs[kLiftBins];      // first output position of each child's run
   uint32_t pk[kLiftBins - 1];  // pivots of the segment's first b levels, heap order
   uint32_t po[kLiftBins - 1];
@@ -122,6 +123,7 @@ __device__ inline void lift_seg_info(const PartArgs& a, uint32_t ai, uint32_t sr
   uint32_t base_out;
   if (ps->mode == 1) base_out = si.off;
   else base_out = a.act_out[a.b == 1 ? (uint32_t)e.next : 0u].base;
+  ps->left0 = LevelLayout::make(tree, x.l).left_size(srel);
   const LevelLayout yo = LevelLayout::make(tree, x.l + a.b);
   const uint32_t nb = 1u << a.b;
   for (uint32_t c = 0; c < nb; ++c) ps->cs[c] = base_out + yo.seg_start((srel << a.b) + c);
@@ -289,7 +291,16 @@ __global__ void __launch_bounds__(PT, 8) partition_kernel(PartArgs a) {
       const uint4 en = s_in[p];
       uint32_t h = 0;
       bool pinned = false;
-      for (int e2 = 0; e2 < a.b; ++e2) {
+      int e2 = 0;
+      if (a.pos_first) {
+        // the list is in the split order of level p: the item's rank in its
+        // segment decides its side (Observation 1), no comparison needed
+        const uint32_t q = tb + p - S.start;
+        pinned = q == S.left0;
+        h = q < S.left0 ? 1u : 2u;
+        e2 = 1;
+      }
+      for (; e2 < a.b && !pinned; ++e2) {
         const uint32_t key = comp(en, S.dim[h]);
         const uint32_t pk = S.pk[h], po = S.po[h];
         if (key == pk && en.w == po) {
