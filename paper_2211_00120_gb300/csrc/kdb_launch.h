@@ -32,8 +32,23 @@ cudaError_t ensure_smem(const void* func, size_t bytes);
 // Presorted-list levels (kdb_part.cu), k <= 3: one 16-byte entry per point
 // (order-preserving keys of coordinates 0..2, original index), one list per
 // dimension.
-constexpr int kPartThreads = 128;
-constexpr int kPartItems = 13;
+// Partition tile shape (threads x items per thread) and resident blocks per
+// SM; compile-time options so that a sweep can try other shapes.
+// Measured at 1e8 float3 round robin (16 partition launches): 256 x 13 at
+// four blocks per SM 11.1 ms; 128 x 13 at eight 12.2 ms; 128 x 11 at eight
+// 13.2 ms; 512 x 13 at two 11.1 ms; 256 x 16 at three 11.9 ms.
+#ifndef KDB_PART_THREADS
+#define KDB_PART_THREADS 256
+#endif
+#ifndef KDB_PART_ITEMS
+#define KDB_PART_ITEMS 13
+#endif
+#ifndef KDB_PART_BLOCKS
+#define KDB_PART_BLOCKS 4
+#endif
+constexpr int kPartThreads = KDB_PART_THREADS;
+constexpr int kPartItems = KDB_PART_ITEMS;
+constexpr int kPartBlocksPerSM = KDB_PART_BLOCKS;
 constexpr int kPartTile = kPartThreads * kPartItems;  // < 2^13 - 1: <= two segments a tile
 struct ListBuildArgs {      // level-0 array of several sets
   LevelCtx x;               // level 0

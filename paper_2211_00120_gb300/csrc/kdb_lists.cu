@@ -82,12 +82,23 @@ __global__ void __launch_bounds__(256) rec_hist_kernel(RecHistArgs a) {
 // every set its own segment.  The tile's records are staged by bulk copy; only
 // their slot order is staged for the write-out, which reads the records from
 // shared memory in digit order and writes each digit's run contiguously.
-constexpr int RT = 256;  // threads of a record-sort block
-constexpr int RI = 13;   // entries per thread: 3328 a tile, three blocks per SM
+// Record-sort tile shape and resident blocks per SM (compile-time options so
+// that a sweep can try other shapes).
+#ifndef KDB_REC_THREADS
+#define KDB_REC_THREADS 256
+#endif
+#ifndef KDB_REC_ITEMS
+#define KDB_REC_ITEMS 13
+#endif
+#ifndef KDB_REC_BLOCKS
+#define KDB_REC_BLOCKS 3
+#endif
+constexpr int RT = KDB_REC_THREADS;  // threads of a record-sort block
+constexpr int RI = KDB_REC_ITEMS;    // entries per thread: 3328 a tile, three blocks per SM
 constexpr int RTILE = RT * RI;
 constexpr int RW = RT / 32;
 
-__global__ void __launch_bounds__(RT, 3)
+__global__ void __launch_bounds__(RT, KDB_REC_BLOCKS)
     rec_sort_pass(const uint4* __restrict__ in, uint4* __restrict__ out, PassCtl c, LevelCtx x,
                   const uint32_t* __restrict__ seg_hist, int d) {
   constexpr int BINS = 2 * kRadix;

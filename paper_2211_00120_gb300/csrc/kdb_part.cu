@@ -199,7 +199,7 @@ __device__ inline bool warp_look_back_bins(const PartArgs& a, uint32_t tile, int
 // list re-sorted by the new tag.  The list is sorted by (tag_p, key, index),
 // so the new order is a stable split of every segment into its 2^b
 // descendants' runs; items pinned on the way are dropped.
-__global__ void __launch_bounds__(PT, 8) partition_kernel(PartArgs a) {
+__global__ void __launch_bounds__(PT, kPartBlocksPerSM) partition_kernel(PartArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint4* s_in = reinterpret_cast<uint4*>(smem_raw);
   __shared__ __align__(8) uint64_t s_bar;
