@@ -51,7 +51,7 @@ WORKLOADS = {
 }
 # algorithmic bytes per item of each kernel kind (matches the library's
 # profiling counters): used to turn a launch's bytes into items
-BYTES_PER_ITEM = {"partition_pass": 32.0, "radix_pass": 16.0}
+BYTES_PER_ITEM = {"partition_pass": 32.0, "radix_pass": 32.0}
 
 
 # the source file that defines each kernel kind of the k <= 3 path
@@ -88,6 +88,67 @@ def measured_peak():
         return float(j["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def issue_peak_ginst(device: int = 0):
+    """Warp-instruction issue peak of the GPU in G warp-instructions/s: four
+    schedulers per SM, one instruction each per cycle, at the maximum SM clock
+    of the measured peaks file (the clock the bench's runs hold)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+        src = "4 x SMs x measured max SM clock"
+    except Exception:
+        mhz, src = 2070.0, "4 x SMs x nominal max SM clock"
+    return 4.0 * sms * mhz * 1e6 / 1e9, src
+
+
+def stored_counters(name: str, kind: str):
+    """A committed ncu summary (profiles/<name>.json) if it was taken on the
+    current sources of kernel kind `kind`, else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", name + ".json")) as f:
+            j = json.load(f)
+    except Exception:
+        return None
+    return j if j.get("kernel_hash") == kernel_hash(kind) else None
+
+
+def kernel_roofline(p: dict, steps: int, points: int, peak_gbs: float, peak_src: str):
+    """Roofline entry of one kernel kind from the library's profiling rows:
+    HBM-bound kinds against the copy peak (algorithmic bytes / CUDA-event
+    time), the issue-bound local finish against the warp-instruction issue
+    peak (instructions from the stored ncu count)."""
+    ms = p["ms"]
+    if ms <= 0:
+        return None
+    if p["name"] == "local_finish":
+        c = stored_counters("local_finish_instructions", "local_finish")
+        peak, src = issue_peak_ginst()
+        if c is None:
+            return {"kernel": "local_finish", "bound": "alu", "achieved": None, "peak": peak,
+                    "unit": "Gwarp-inst/s", "frac": None, "traffic": None, "peak_source": src,
+                    "ms_per_step": ms / steps}
+        inst = c["warp_instructions_per_point"] * points * steps
+        ach = inst / (ms / 1000.0) / 1e9
+        return {"kernel": "local_finish", "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "Gwarp-inst/s", "frac": ach / peak,
+                "traffic": c["dram_bytes_per_point"] * points * p["launches"] / max(p["launches"], 1),
+                "warp_instructions_per_point": c["warp_instructions_per_point"],
+                "peak_source": src, "ms_per_step": ms / steps,
+                "launches_per_step": p["launches"] / steps}
+    ach = p["bytes"] / (ms / 1000.0) / 1e9
+    traffic = None
+    if p["name"] in BYTES_PER_ITEM and p["launches"]:
+        items = p["bytes"] / BYTES_PER_ITEM[p["name"]] / p["launches"]
+        traffic = traffic_per_launch(p["name"], items)
+    return {"kernel": p["name"], "bound": "hbm", "achieved": ach, "peak": peak_gbs, "unit": "GB/s",
+            "frac": ach / peak_gbs, "traffic": traffic, "peak_source": peak_src,
+            "ms_per_step": ms / steps, "launches_per_step": p["launches"] / steps,
+            "algorithmic_bytes_per_launch": p["bytes"] / max(p["launches"], 1)}
 
 
 def traffic_per_launch(kind: str, n_items_per_launch: float):
@@ -507,26 +568,21 @@ def main():
         ms = float(t.item())
     value = world * n / (ms / 1000.0) / 1e6
 
-    # roofline of the dominant kernel (largest share of the step): its
-    # algorithmic bytes over its own CUDA-event time in the timed steps
-    dom = max(prof, key=lambda p: p["ms"])
+    # roofline of the dominant kernel (largest share of the step), each kernel
+    # against its own bound: the sort passes against the HBM copy peak
+    # (algorithmic bytes over their CUDA-event time in the timed steps), the
+    # issue-bound local finish against the warp-instruction issue peak
     peak, peak_src = measured_peak()
-    achieved = dom["bytes"] / (dom["ms"] / 1000.0) / 1e9 if dom["ms"] > 0 else None
     build_ms_total = ms
     kernel_ms = {p["name"]: round(p["ms"] / args.steps, 3) for p in prof}
     fb = floor_bytes(n, stride)
-    traffic = None
-    if dom["name"] in BYTES_PER_ITEM and dom["launches"]:
-        items = dom["bytes"] / BYTES_PER_ITEM[dom["name"]] / dom["launches"]
-        traffic = traffic_per_launch(dom["name"], items)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "kernel": dom["name"],
-                "launches_per_step": dom["launches"] / args.steps,
-                "kernel_share_of_step": dom["ms"] / args.steps / build_ms_total,
-                "algorithmic_bytes_per_launch": dom["bytes"] / max(dom["launches"], 1),
-                "peak_source": peak_src,
-                "build_floor_frac": fb / (peak * 1e9) / (build_ms_total / 1000.0)}
+    per_kernel = [r for r in (kernel_roofline(p, args.steps, n, peak, peak_src) for p in prof
+                              if p["name"] in ("partition_pass", "radix_pass", "local_finish")) if r]
+    dom = max(prof, key=lambda p: p["ms"])
+    roofline = kernel_roofline(dom, args.steps, n, peak, peak_src) or {}
+    roofline["kernel_share_of_step"] = dom["ms"] / args.steps / build_ms_total
+    roofline["build_floor_frac"] = fb / (peak * 1e9) / (build_ms_total / 1000.0)
+    roofline["kernels"] = per_kernel
 
     # the paper's almost-in-place placement (one int32 per point) on the same
     # builds, for comparison with the default gather through spare workspace
