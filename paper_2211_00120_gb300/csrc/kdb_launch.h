@@ -126,7 +126,10 @@ cudaError_t launch_partition(const PartArgs& a, cudaStream_t st);
 
 // Local finish of small subtrees (kdb_local.cu).
 constexpr int kLocalThreads = 1024;
-constexpr int kLocalLog = 13;                     // subtrees of <= 2^13 - 1 points
+#ifndef KDB_LOCAL_LOG
+#define KDB_LOCAL_LOG 13
+#endif
+constexpr int kLocalLog = KDB_LOCAL_LOG;          // subtrees of <= 2^13 - 1 points
 constexpr int kLocalCap = 1 << kLocalLog;         // 8192
 constexpr int kLocalMax = kLocalCap - 1;
 constexpr int kLocalMaxK = 4;                     // shared-memory budget: k + 1 lists

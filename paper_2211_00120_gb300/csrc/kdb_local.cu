@@ -173,14 +173,6 @@ __device__ inline uint32_t swap_slots(uint32_t slots, int d, int k) {
   return slots | (b << (4 * d)) | (a << (4 * k));
 }
 
-// q = n / d for n < 2^13 and 1 <= d < 2^13 by a multiply-high with
-// M = floor((2^32 - 1) / d) + 1: the error term n (M - 2^32/d) / 2^32 is below
-// 2^-19, less than the gap 1/d between n/d and the next integer.
-__device__ inline uint32_t div_magic(uint32_t d) { return d <= 1 ? 0u : 0xFFFFFFFFu / d + 1u; }
-__device__ inline uint32_t div_small(uint32_t n, uint32_t d, uint32_t magic) {
-  return d <= 1 ? n * d : __umulhi(n, magic);
-}
-
 // The block's subtree on one level of the set's tree, in block-local terms:
 // segment u = the block's u-th subtree on that level, positions counted from
 // the block's first item on that level.  Same closed forms as the set's
@@ -191,11 +183,7 @@ struct Local {
   uint32_t thin;     // 2^h - 1: a subtree without lowest-level nodes
   uint32_t full;     // 2^(h+1) - 1
   uint32_t mb;       // lowest-level nodes inside the block's subtree
-  uint32_t qb;       // full segments
-  uint32_t a;        // items in the full segments
-  uint32_t part;     // size of segment qb
   uint32_t w;        // 2^(h-1): lowest-level width of a left child (h >= 1)
-  uint32_t mfull, mthin;
 };
 
 __device__ inline Local make_local(const Tree& tree, int L, uint32_t tfirst, uint32_t nodes) {
@@ -206,21 +194,10 @@ __device__ inline Local make_local(const Tree& tree, int L, uint32_t tfirst, uin
   const uint64_t lo = (uint64_t)tfirst << y.h;  // first lowest-level slot of the block
   const uint64_t room = (uint64_t)nodes << y.h;
   y.mb = tree.m > lo ? (uint32_t)min((uint64_t)tree.m - lo, room) : 0u;
-  y.qb = min(y.mb >> y.h, nodes);
-  y.a = y.qb * y.full;
-  y.part = y.thin + (y.mb - (y.qb << y.h));
   y.w = y.h >= 1 ? 1u << (y.h - 1) : 0u;
-  y.mfull = div_magic(y.full);
-  y.mthin = div_magic(y.thin);
   return y;
 }
 __device__ inline uint32_t l_start(const Local& y, uint32_t u) { return u * y.thin + min(u << y.h, y.mb); }
-__device__ inline uint32_t l_seg_of(const Local& y, uint32_t p) {
-  if (p < y.a) return div_small(p, y.full, y.mfull);
-  const uint32_t p2 = p - y.a;
-  if (p2 < y.part) return y.qb;
-  return y.qb + 1u + div_small(p2 - y.part, y.thin, y.mthin);
-}
 __device__ inline uint32_t l_left(const Local& y, uint32_t u) {  // h >= 1
   const uint32_t lowest = (2u * u) << (y.h - 1);
   const uint32_t low = lowest >= y.mb ? 0u : min(y.mb - lowest, y.w);
@@ -254,36 +231,6 @@ __device__ inline Range make_range(const Local& y, uint32_t uf, uint32_t cnt) {
   // minus the uf pivots above them
   r.nb = r.p0 - uf;
   return r;
-}
-
-// Tag update of the item at position p (Sec. 3.2 with Observation 1): in its
-// segment u it is left of the pivot (side 0), the pivot (2) or right (1).
-// Returns the item's position on the next level minus its rank among the
-// range's items of the same side: left items of the range go, in list order,
-// after the right items of the range's earlier segments; right items after
-// the left items of the earlier segments and of u itself.
-__device__ inline uint32_t classify(const Range& r, uint32_t p, uint32_t* u_out, uint32_t* side) {
-  const Local& y = r.y;
-  const uint32_t u = l_seg_of(y, p);
-  const uint32_t st = l_start(y, u);
-  const uint32_t q = p - st;
-  uint32_t pr = 0, sl = 0;
-  if (y.h >= 1) {
-    pr = l_left(y, u);
-    sl = l_left_before(y, u) - r.lb0;
-  }
-  const uint32_t sr = (st - r.p0) - (u - r.uf) - sl;
-  *u_out = u;
-  if (q < pr) {
-    *side = 0;
-    return r.nb + sr;
-  }
-  if (q == pr) {
-    *side = 2;
-    return 0;
-  }
-  *side = 1;
-  return r.nb + sl + pr;
 }
 
 // kMode: the split rule (0 round robin, 1 clipped domain, 2 tight box), a
@@ -551,36 +498,68 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     s_need[jj] = (uint8_t)need;
   }
   __syncthreads();
-  // mark every item of range r (info word: side << 14 | next-level offset),
-  // pin the pivots, record the planes.  The range's items are stored from
-  // list position sb on.
-  auto info_pass = [&](const Range& r, uint32_t jj, int L, uint32_t slots, uint32_t sb, uint32_t g0,
-                       uint32_t gs) {
+  // Tag update of depth jj (Sec. 3.2 with Observation 1) for the segments
+  // [r.uf, r.uf + cnt) of range r: in its segment the item at rank pr (the
+  // left subtree's size) is pinned as the node, lower ranks go left, higher
+  // ranks right.  Each item gets an info word (side << 14 | offset); the
+  // offset is its position on the next level minus its rank among the
+  // range's items of the same side in list order: left items of a segment go
+  // after the right items of the range's earlier segments, right items after
+  // the left items of the earlier segments and of the segment itself.  The
+  // pivots are pinned and (clipped-domain rule) their planes recorded.  The
+  // range's items are stored from list position sb on.
+  //
+  // The `gs` threads of a group (g0 = index in the group) take whole
+  // segments: with at least as many threads as segments, 2^x threads share
+  // one segment; with fewer, each thread takes every gs-th segment.  Either
+  // way a segment's constants (start, pivot rank, next-level offsets of its
+  // two sides, from the closed forms of Sec. 4) are computed once per thread
+  // and segment, not once per item.
+  auto info_pass = [&](const Range& r, uint32_t cnt, uint32_t jj, int L, uint32_t slots, uint32_t sb,
+                       uint32_t g0, uint32_t gs) {
     const int drr = s_drr[jj];
     const uint32_t dbase = (1u << jj) - 1;  // local index of the first node at depth jj
-    for (uint32_t p = r.p0 + g0; p < r.p1; p += gs) {
-      uint32_t tl, side;
-      const uint32_t off = classify(r, p, &tl, &side);
+    const Local& y = r.y;
+    const uint32_t tps = gs >= cnt ? gs / cnt : 1u;  // threads per segment
+    const uint32_t u0 = gs >= cnt ? g0 / tps : g0, ustep = gs >= cnt ? cnt : gs;
+    const uint32_t t0 = gs >= cnt ? g0 % tps : 0u;
+    for (uint32_t uu = u0; uu < cnt; uu += ustep) {
+      const uint32_t tl = r.uf + uu;
+      const uint32_t st = l_start(y, tl), en = l_start(y, tl + 1);
+      uint32_t pr = 0, sl = 0;
+      if (y.h >= 1) {
+        pr = l_left(y, tl);
+        sl = l_left_before(y, tl) - r.lb0;
+      }
+      const uint32_t sr = (st - r.p0) - uu - sl;
+      const uint32_t offl = r.nb + sr, offr = r.nb + sl + pr;
       const int d = bydim ? s_ldim[dbase + tl] : drr;
-      const uint32_t it = s_lists[(size_t)slot_of(slots, d) * kLocalCap + (p - r.p0 + sb)];
-      if (it >= m || off >= kLocalCap) {
-        s_bad = 1;
-        continue;
-      }
-      if (side == 2) {
-        const uint32_t o = s_orig[it];
-        const uint32_t node = ls.off + full_nodes(L) + (wk.s_rel << jj) + tl;
-        a.perm[node] = o;
-        if (ent_of) {  // the record goes straight to its node
-          const uint4 e = ent_of[it];
-          write_record_from_entry(a.pts_out + (uint64_t)node * a.stride, e, k, a.ints);
-          if (widest)
-            s_lplane[dbase + tl] = __uint_as_float(key_to_float_bits(d == 0 ? e.x : (d == 1 ? e.y : e.z)));
-        } else if (widest) {
-          s_lplane[dbase + tl] = coord_of(a.pts, o, a.stride, d);
+      const uint16_t* list = s_lists + (size_t)slot_of(slots, d) * kLocalCap;
+      for (uint32_t p = st + t0; p < en; p += tps) {
+        const uint32_t q = p - st;
+        const uint32_t side = q < pr ? 0u : (q == pr ? 2u : 1u);
+        const uint32_t off = side == 0 ? offl : (side == 1 ? offr : 0u);
+        const uint32_t it = list[p - r.p0 + sb];
+        if (it >= m || off >= kLocalCap) {
+          s_bad = 1;
+          continue;
         }
+        if (side == 2) {
+          const uint32_t o = s_orig[it];
+          const uint32_t node = ls.off + full_nodes(L) + (wk.s_rel << jj) + tl;
+          a.perm[node] = o;
+          if (ent_of) {  // the record goes straight to its node
+            const uint4 e = ent_of[it];
+            write_record_from_entry(a.pts_out + (uint64_t)node * a.stride, e, k, a.ints);
+            if (widest)
+              s_lplane[dbase + tl] =
+                  __uint_as_float(key_to_float_bits(d == 0 ? e.x : (d == 1 ? e.y : e.z)));
+          } else if (widest) {
+            s_lplane[dbase + tl] = coord_of(a.pts, o, a.stride, d);
+          }
+        }
+        s_info[it] = (uint16_t)((side << 14) | off);
       }
-      s_info[it] = (uint16_t)((side << 14) | off);
     }
   };
 
@@ -623,7 +602,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
             }
             __syncwarp();
           }
-          info_pass(r, jj, Li, wslots, sb, lane, 32);
+          info_pass(r, cnt, jj, Li, wslots, sb, lane, 32);
           __syncwarp();
           if (Li == tree.L - 1) break;
           const uint32_t lim = r.nb + (r.p1 - r.p0) - cnt;  // end of the range's next-level items
@@ -670,7 +649,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
       }
       __syncthreads();
     }
-    info_pass(r, j, L, slots, 0, threadIdx.x, T);
+    info_pass(r, nodes, j, L, slots, 0, threadIdx.x, T);
     __syncthreads();
     if (L == tree.L - 1) break;  // lowest level: every item was pinned
     const uint32_t mn = mj - nodes;
