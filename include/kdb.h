@@ -170,7 +170,11 @@ KDB_API kdb_status kdb_error_word_status(uint32_t word);
 /*
  * kdb_build_host -- kdb_build for records in host memory: copies them to the
  * device, builds, and copies the tree back into h_points on `stream` (pinned
- * host memory gives asynchronous copies).  Synchronises `stream`.
+ * host memory gives asynchronous copies).  The copy to the device goes in
+ * chunks (of at least 64 MiB, at most 8) on a stream of the call's own, and
+ * the build's first pass over each chunk starts as soon as that chunk has
+ * landed.  On a device error (NaN input, ...) h_points is left as it was.
+ * Synchronises `stream`.
  */
 KDB_API kdb_status kdb_build_host(void* h_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
                           kdb_stream_t stream);

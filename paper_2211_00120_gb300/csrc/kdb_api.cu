@@ -477,9 +477,18 @@ kdb_status upload_tables(const Plan& P, void* ws, cudaStream_t st, bool sync) {
 // tables_ready the plan's tables are already in the workspace: then only
 // kernels and memsets are enqueued (no host memory is read), so the call can
 // be captured into a CUDA graph.
+// Records that arrive from host memory during the build: chunk c is copied
+// to the device on stream `cs` and event ev[c] marks its arrival.
+struct HostFeed {
+  const unsigned char* h = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev[8] = {};
+  int chunks = 0;
+};
+
 kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
                          int32_t* out_orig, uint8_t* out_dim, cudaStream_t st,
-                         bool tables_ready = false) {
+                         bool tables_ready = false, const HostFeed* feed = nullptr) {
   const uint32_t T = P.total;
   const int k = P.k;
   uint64_t* keysA = at<uint64_t>(ws, P.o_keysA);
@@ -564,8 +573,28 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   pa.err = err;
   pa.ints = P.ints;
   {
-    Prof pf(K_PREPASS, P.use_lists ? (double)T * (4.0 * k + 16.0) : (double)T * k * (4.0 + (multi ? 8 : 4)), 1, st);
-    KDB_CK(launch_prepass(pa, sms, st));
+    Prof pf(K_PREPASS, P.use_lists ? (double)T * (4.0 * k + 16.0) : (double)T * k * (4.0 + (multi ? 8 : 4)),
+            feed ? feed->chunks : 1, st);
+    if (!feed) {
+      KDB_CK(launch_prepass(pa, sms, st));
+    } else {
+      // the records come from host memory in chunks: the copy of chunk c + 1
+      // (on the feed's stream) overlaps the prepass of chunk c
+      for (int c = 0; c < feed->chunks; ++c) {
+        const uint32_t b = (uint32_t)((uint64_t)T * c / feed->chunks);
+        const uint32_t e = (uint32_t)((uint64_t)T * (c + 1) / feed->chunks);
+        KDB_CK(cudaMemcpyAsync(pts + (size_t)b * P.stride, feed->h + (size_t)b * P.stride,
+                               (size_t)(e - b) * P.stride, cudaMemcpyHostToDevice, feed->cs));
+        KDB_CK(cudaEventRecord(feed->ev[c], feed->cs));
+      }
+      for (int c = 0; c < feed->chunks; ++c) {
+        pa.beg = (uint32_t)((uint64_t)T * c / feed->chunks);
+        pa.end = (uint32_t)((uint64_t)T * (c + 1) / feed->chunks);
+        KDB_CK(cudaStreamWaitEvent(st, feed->ev[c], 0));
+        if (pa.end > pa.beg) KDB_CK(launch_prepass(pa, sms, st));
+      }
+      pa.beg = pa.end = 0;
+    }
   }
   uint32_t* hcur = hist + (size_t)k * P.rank_passes * kRadixBins;
 
@@ -1441,26 +1470,54 @@ kdb_status kdb_build_host(void* h_points, int64_t n, int k, int stride_bytes, kd
   cudaMemPool_t pool;
   s = device_setup(&dev, &pool, &sms);
   if (s != KDB_OK) return s;
+  Plan P;
+  P.sets.push_back(SetInfo{0u, (uint32_t)n});
+  P.total = (uint32_t)n;
+  P.k = k;
+  P.stride = stride_bytes;
+  P.mode = split_of(mode);
+  P.ints = ints_of(mode);
+  make_plan(P);
+  if (P.too_wide) return KDB_ERR_INVALID_ARGUMENT;
   const size_t bytes = (size_t)n * stride_bytes;
   void* d = nullptr;
+  void* ws = nullptr;
   s = pool_alloc(&d, bytes, pool, st);
-  if (s != KDB_OK) return s;
-  if (cudaMemcpyAsync(d, h_points, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-    cudaGetLastError();
-    cudaFreeAsync(d, st);
-    return KDB_ERR_CUDA;
+  if (s == KDB_OK) s = pool_alloc(&ws, P.bytes, pool, st);
+  // the records go to the device in chunks on a second stream, so that the
+  // prepass of each chunk overlaps the copy of the next
+  HostFeed feed;
+  feed.h = static_cast<const unsigned char*>(h_points);
+  feed.chunks = (int)std::min<size_t>(8, std::max<size_t>(1, bytes >> 26));  // >= 64 MiB a chunk
+  cudaEvent_t ready = nullptr;
+  bool made = s == KDB_OK && cudaStreamCreateWithFlags(&feed.cs, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess;
+  for (int c = 0; made && c < feed.chunks; ++c)
+    made = cudaEventCreateWithFlags(&feed.ev[c], cudaEventDisableTiming) == cudaSuccess;
+  if (s == KDB_OK && !made) s = KDB_ERR_CUDA;
+  if (s == KDB_OK) {
+    // the copies may start once the allocations on `st` are done
+    if (cudaEventRecord(ready, st) != cudaSuccess || cudaStreamWaitEvent(feed.cs, ready, 0) != cudaSuccess)
+      s = KDB_ERR_CUDA;
   }
-  s = kdb_build_ex(d, n, k, stride_bytes, mode, nullptr, 0, nullptr, nullptr, stream);
+  if (s == KDB_OK) s = enqueue_build(P, static_cast<unsigned char*>(d), ws, sms, nullptr, nullptr, st, false,
+                                     &feed);
+  if (s == KDB_OK) s = finish(P, ws, st);
   if (s == KDB_OK &&
-      cudaMemcpyAsync(h_points, d, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
-    cudaGetLastError();
+      cudaMemcpyAsync(h_points, d, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     s = KDB_ERR_CUDA;
-  }
-  cudaFreeAsync(d, st);
+  if (s != KDB_OK) cudaGetLastError();
+  if (feed.cs) cudaStreamSynchronize(feed.cs);  // no copy left in flight
+  if (ws) cudaFreeAsync(ws, st);
+  if (d) cudaFreeAsync(d, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     if (s == KDB_OK) s = KDB_ERR_CUDA;
   }
+  for (int c = 0; c < feed.chunks; ++c)
+    if (feed.ev[c]) cudaEventDestroy(feed.ev[c]);
+  if (ready) cudaEventDestroy(ready);
+  if (feed.cs) cudaStreamDestroy(feed.cs);
   return s;
 }
 

@@ -219,6 +219,7 @@ struct PrepassArgs {
   uint32_t* bbox;       // nsets * 2k (min keys, then max keys) or nullptr
   uint32_t* err;
   bool ints;            // int32 coordinates (else float32)
+  uint32_t beg, end;    // records [beg, end) of this launch (end = 0: all of them)
 };
 cudaError_t launch_prepass(const PrepassArgs& a, int num_sms, cudaStream_t st);
 

@@ -68,8 +68,12 @@ __global__ void __launch_bounds__(kThreads) prepass_kernel(PrepassArgs a) {
   const int H = a.hist ? a.k * a.passes * kRadixBins : 0;
   for (int i = threadIdx.x; i < H; i += blockDim.x) s_hist[i] = 0;
   __syncthreads();
+  // the launch's records [r0, r1), split into one chunk per block
+  const uint32_t r0 = a.end ? a.beg : 0u, r1 = a.end ? a.end : a.total;
   uint32_t beg, end;
-  block_chunk(a.total, &beg, &end);
+  block_chunk(r1 - r0, &beg, &end);
+  beg += r0;
+  end += r0;
   uint32_t lo[kMaxK], hi[kMaxK];
   for (int d = 0; d < kMaxK; ++d) {
     lo[d] = 0xFFFFFFFFu;
@@ -587,12 +591,13 @@ __global__ void validate_kernel(const unsigned char* pts, uint32_t n, int k, int
 
 // ------------------------------------------------------------- launchers --
 cudaError_t launch_prepass(const PrepassArgs& a, int num_sms, cudaStream_t st) {
-  if (a.total == 0) return cudaSuccess;
+  const uint32_t count = a.end ? a.end - a.beg : a.total;
+  if (count == 0) return cudaSuccess;
   const size_t smem = a.hist ? (size_t)a.k * a.passes * kRadixBins * sizeof(uint32_t) : 0;
   cudaError_t e = ensure_smem((const void*)prepass_kernel, smem);
   if (e != cudaSuccess) return e;
   uint32_t grid = (uint32_t)num_sms * 4;
-  const uint32_t need = (a.total + kThreads - 1) / kThreads;
+  const uint32_t need = (count + kThreads - 1) / kThreads;
   if (grid > need) grid = need;
   prepass_kernel<<<grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();

@@ -136,6 +136,26 @@ def test_host_buffer_entry_point():
     assert np.array_equal(h.numpy(), want)
 
 
+@pytest.mark.parametrize("mode", [RR, WIDEST])
+def test_host_buffer_copied_in_chunks(mode):
+    """12M float3 records (144 MB): the copy to the device goes in two chunks
+    overlapped with the first pass; the tree equals the device build's, and a
+    NaN leaves the host records as they were."""
+    pts = synth.mixed(12_000_000, 3, seed=13)
+    d = torch.from_numpy(pts).cuda()
+    kdb.kdb_build(d, 3, mode)
+    h = torch.from_numpy(pts.copy()).pin_memory()
+    kdb.kdb_build_host(h, 3, mode)
+    assert torch.equal(h.view(torch.int32), d.cpu().view(torch.int32))
+    bad = pts.copy()
+    bad[11_999_000, 1] = np.nan  # in the last chunk
+    hb = torch.from_numpy(bad.copy()).pin_memory()
+    with pytest.raises(kdb.KdbError) as e:
+        kdb.kdb_build_host(hb, 3, mode)
+    assert e.value.code == kdb.ERR_NAN_INPUT
+    assert np.array_equal(hb.numpy().view(np.uint32), bad.view(np.uint32))
+
+
 def test_streams_run_independently():
     a = synth.uniform(100000, 3, seed=21)
     b = synth.mixed(100000, 3, seed=22)
