@@ -117,7 +117,8 @@ def stored_counters(name: str, kind: str):
     return j if j.get("kernel_hash") == kernel_hash(kind) else None
 
 
-def kernel_roofline(p: dict, steps: int, points: int, peak_gbs: float, peak_src: str):
+def kernel_roofline(p: dict, steps: int, points: int, peak_gbs: float, peak_src: str,
+                    shapes: dict):
     """Roofline entry of one kernel kind from the library's profiling rows:
     HBM-bound kinds against the copy peak (algorithmic bytes / CUDA-event
     time), the issue-bound local finish against the warp-instruction issue
@@ -144,18 +145,18 @@ def kernel_roofline(p: dict, steps: int, points: int, peak_gbs: float, peak_src:
     traffic = None
     if p["name"] in BYTES_PER_ITEM and p["launches"]:
         items = p["bytes"] / BYTES_PER_ITEM[p["name"]] / p["launches"]
-        traffic = traffic_per_launch(p["name"], items)
+        traffic = traffic_per_launch(p["name"], items, shapes)
     return {"kernel": p["name"], "bound": "hbm", "achieved": ach, "peak": peak_gbs, "unit": "GB/s",
             "frac": ach / peak_gbs, "traffic": traffic, "peak_source": peak_src,
             "ms_per_step": ms / steps, "launches_per_step": p["launches"] / steps,
             "algorithmic_bytes_per_launch": p["bytes"] / max(p["launches"], 1)}
 
 
-def traffic_per_launch(kind: str, n_items_per_launch: float):
+def traffic_per_launch(kind: str, n_items_per_launch: float, shapes: dict):
     """DRAM bytes per launch of `kind` from the committed ncu summary
     (profiles/<kind>_traffic.json, measured on a smaller case and scaled by
-    the items a launch processes); None if absent or measured on other
-    kernel sources."""
+    the items a launch processes); None if absent, measured on other kernel
+    sources, or with another tile shape than the one in use."""
     p = os.path.join(ROOT, "profiles", f"{kind}_traffic.json")
     try:
         with open(p) as f:
@@ -163,6 +164,9 @@ def traffic_per_launch(kind: str, n_items_per_launch: float):
     except Exception:
         return None
     if not j.get("kernel_hash") or j["kernel_hash"] != kernel_hash(kind):
+        return None
+    shape = shapes.get({"partition_pass": "partition", "radix_pass": "radix"}.get(kind, ""))
+    if shape is not None and list(j.get("tile_shape", [])) != list(shape):
         return None
     return j["dram_bytes_per_item"] * n_items_per_launch
 
@@ -494,6 +498,10 @@ def main():
                     help="only the serving measurement (prints its JSON object)")
     ap.add_argument("--points", type=int, default=0,
                     help="override the workload's number of points (small profiling cases)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default tile shapes instead of timing the compiled ones first")
+    ap.add_argument("--tuning", default="",
+                    help="partition,radix tile-shape indices to use (skips the autotuner)")
     ap.add_argument("--profile-only", action="store_true",
                     help="warm-up and one build, nothing timed (for ncu launch lists)")
     args = ap.parse_args()
@@ -527,6 +535,23 @@ def main():
     src = torch.from_numpy(host).cuda()
     work = torch.empty_like(src)
     stream = torch.cuda.current_stream()
+
+    # tile shapes of the two sort kernels: timed on this workload before the
+    # warm-up (kdb_autotune builds a copy of the points), or given
+    autotune = None
+    if args.tuning:
+        kdb.kdb_set_tuning(*(int(v) for v in args.tuning.split(",")))
+    elif not args.no_autotune and not args.profile_only:
+        r = kdb.kdb_autotune(src, k, mode, reps=3)
+        autotune = {"best": list(r["best"]), "best_ms": r["best_ms"],
+                    "ms": {f"{p},{q}": round(v, 3) for (p, q), v in sorted(r["ms"].items())}}
+    tuning = kdb.kdb_get_tuning()
+    shapes = {"partition": kdb.kdb_tuning_shapes(kdb.TUNE_PARTITION)[tuning[0]],
+              "radix": kdb.kdb_tuning_shapes(kdb.TUNE_RADIX)[tuning[1]]}
+    tuned = {"indices": list(tuning),
+             "partition_shape": list(shapes["partition"]), "radix_shape": list(shapes["radix"]),
+             "shape_fields": ["threads", "items_per_thread", "blocks_per_sm"],
+             "autotune": autotune}
 
     for _ in range(args.warmup):
         work.copy_(src)
@@ -576,10 +601,11 @@ def main():
     build_ms_total = ms
     kernel_ms = {p["name"]: round(p["ms"] / args.steps, 3) for p in prof}
     fb = floor_bytes(n, stride)
-    per_kernel = [r for r in (kernel_roofline(p, args.steps, n, peak, peak_src) for p in prof
+    per_kernel = [r for r in (kernel_roofline(p, args.steps, n, peak, peak_src, shapes)
+                              for p in prof
                               if p["name"] in ("partition_pass", "radix_pass", "local_finish")) if r]
     dom = max(prof, key=lambda p: p["ms"])
-    roofline = kernel_roofline(dom, args.steps, n, peak, peak_src) or {}
+    roofline = kernel_roofline(dom, args.steps, n, peak, peak_src, shapes) or {}
     roofline["kernel_share_of_step"] = dom["ms"] / args.steps / build_ms_total
     roofline["build_floor_frac"] = fb / (peak * 1e9) / (build_ms_total / 1000.0)
     roofline["kernels"] = per_kernel
@@ -644,7 +670,8 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_parallel": cpu_par,
                 "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "kernel_ms_per_step": kernel_ms,
-                "placement_in_place": in_place, "batched": batched, "serving": served}
+                "placement_in_place": in_place, "tuning": tuned, "batched": batched,
+                "serving": served}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -328,6 +328,54 @@ typedef enum { KDB_PLACEMENT_AUTO = 0, KDB_PLACEMENT_IN_PLACE = 1 } kdb_placemen
 KDB_API kdb_placement kdb_set_placement(kdb_placement placement);
 
 /*
+ * Tile shapes of the two sort kernels of the per-dimension-list path (k <= 3):
+ *   KDB_TUNE_PARTITION  the per-level stable split (the sorts of Sec. 3.1
+ *                       that follow level 0, Observation 1 fused in);
+ *   KDB_TUNE_RADIX      the passes of the level-0 sort.
+ * The library carries a few compiled shapes of each.  A shape is threads per
+ * block, entries per thread and resident blocks per SM.  The setting only
+ * changes speed: every shape gives bit-identical output.
+ *
+ * kdb_tuning_shape_count -- number of shapes of `kernel`, or -1 for an
+ *   unknown kernel.
+ * kdb_tuning_shape       -- shape `index` of `kernel` (host out-pointers, each
+ *   may be NULL).  KDB_ERR_INVALID_ARGUMENT for an unknown kernel or index.
+ * kdb_get_tuning / kdb_set_tuning -- the process-wide setting, read when a
+ *   build is enqueued (a captured graph keeps the shapes it was captured
+ *   with).  Default {0, 0}.  kdb_set_tuning returns KDB_ERR_INVALID_ARGUMENT
+ *   and changes nothing if an index is out of range.
+ * kdb_autotune -- times every pair of shapes on the caller's points and keeps
+ *   the fastest pair as the process-wide setting.
+ *     d_points    device, in: n points as for kdb_build; read only (each
+ *                 trial builds a copy).
+ *     reps        timed builds per pair, 1..64; a pair's time is the median.
+ *     out_best    host, out (may be NULL): the chosen pair.
+ *     out_best_ms host, out (may be NULL): its median build time.
+ *     h_ms        host, out (may be NULL): kdb_tuning_shape_count(PARTITION)
+ *                 x kdb_tuning_shape_count(RADIX) medians, partition shape
+ *                 major; -1 for pairs not timed.  Where the build does not
+ *                 use the tuned kernels (k > 3, or n too small for a global
+ *                 level) only the current setting is timed and kept.
+ *   Allocates a copy of the points and a workspace from the device's memory
+ *   pool and frees them before returning.  Synchronous.  Returns the first
+ *   build error, KDB_ERR_OUT_OF_MEMORY, or KDB_ERR_INVALID_ARGUMENT for bad
+ *   arguments (as kdb_build, plus n < 2 or reps out of range).
+ */
+enum { KDB_TUNE_PARTITION = 0, KDB_TUNE_RADIX = 1 };
+typedef struct {
+  int32_t partition_shape;
+  int32_t radix_shape;
+} kdb_tuning;
+KDB_API int kdb_tuning_shape_count(int kernel);
+KDB_API kdb_status kdb_tuning_shape(int kernel, int index, int* threads, int* items_per_thread,
+                                    int* blocks_per_sm);
+KDB_API kdb_status kdb_get_tuning(kdb_tuning* out);
+KDB_API kdb_status kdb_set_tuning(const kdb_tuning* tuning);
+KDB_API kdb_status kdb_autotune(const void* d_points, int64_t n, int k, int stride_bytes,
+                                kdb_split_mode mode, int reps, kdb_tuning* out_best,
+                                float* out_best_ms, float* h_ms, kdb_stream_t stream);
+
+/*
  * kdb_validate -- check the k-d condition of a level-order tree (Sec. 1):
  * for every node i and every ancestor p with split dimension d, x_d(i) <=
  * x_d(p) if i is in p's left subtree and >= if in the right one, under the

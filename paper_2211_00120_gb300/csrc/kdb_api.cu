@@ -67,6 +67,7 @@ std::vector<ProfRec> g_prof;
 std::vector<cudaEvent_t> g_event_pool;
 std::atomic<int64_t> g_launches{0};
 std::atomic<int> g_placement{KDB_PLACEMENT_AUTO};
+std::atomic<int> g_part_shape{0}, g_rec_shape{0};  // tile shapes of the two sort kernels
 
 struct SmemAttr {
   int dev;
@@ -185,6 +186,7 @@ struct Plan {
   int rank_passes = 0;
   bool singletons = false;  // a set of one record (its node is its record)
   bool too_wide = false;    // (set, subtree, rank) needs more than 64 bits
+  int part_shape = -1, rec_shape = -1;  // tile shapes; -1: the process-wide setting
   std::vector<std::vector<ActiveEntry>> act;  // per level l = 0 .. Lmax-2
   std::vector<uint32_t> items;                // per level
   std::vector<int> passes;                    // per level
@@ -491,6 +493,8 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
                          bool tables_ready = false, const HostFeed* feed = nullptr) {
   const uint32_t T = P.total;
   const int k = P.k;
+  const int part_shape = P.part_shape >= 0 ? P.part_shape : g_part_shape.load();
+  const int rec_shape = P.rec_shape >= 0 ? P.rec_shape : g_rec_shape.load();
   uint64_t* keysA = at<uint64_t>(ws, P.o_keysA);
   uint64_t* keysB = at<uint64_t>(ws, P.o_keysB);
   uint32_t* valsA = at<uint32_t>(ws, P.o_valsA);
@@ -731,6 +735,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     pa.wait_ns = c.wait_ns;
     pa.status_words = c.status_words;
     Prof pf(K_PARTITION, (double)P.items[p] * 32, 1, st);
+    pa.shape = part_shape;
     cudaError_t e = launch_partition(pa, st);
     std::swap(lcur[d], lnext[d]);
     lat[d] = q;
@@ -782,7 +787,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
           PassCtl c = ctl(n0, 8 * p, nullptr);
           const uint32_t* sh = rh.hist + ((size_t)(d * 4 + p) * x0.nact) * kRadixBins;
           Prof pf(K_RADIX, (double)n0 * 32, 1, st);
-          KDB_CK(launch_rec_sort_pass(in, out, c, x0, sh, d, st));
+          KDB_CK(launch_rec_sort_pass(in, out, c, x0, sh, d, rec_shape, st));
           in = out;
         }
       }
@@ -1157,6 +1162,117 @@ kdb_placement kdb_set_placement(kdb_placement placement) {
   if (placement != KDB_PLACEMENT_AUTO && placement != KDB_PLACEMENT_IN_PLACE)
     return (kdb_placement)g_placement.load();
   return (kdb_placement)g_placement.exchange(placement);
+}
+
+int kdb_tuning_shape_count(int kernel) {
+  if (kernel == KDB_TUNE_PARTITION) return kPartShapes;
+  if (kernel == KDB_TUNE_RADIX) return kRecShapes;
+  return -1;
+}
+
+kdb_status kdb_tuning_shape(int kernel, int index, int* threads, int* items_per_thread,
+                            int* blocks_per_sm) {
+  const int count = kdb_tuning_shape_count(kernel);
+  if (count < 0 || index < 0 || index >= count) return KDB_ERR_INVALID_ARGUMENT;
+  const TileShape& sh = kernel == KDB_TUNE_PARTITION ? kPartShape[index] : kRecShape[index];
+  if (threads) *threads = sh.threads;
+  if (items_per_thread) *items_per_thread = sh.items;
+  if (blocks_per_sm) *blocks_per_sm = sh.blocks;
+  return KDB_OK;
+}
+
+kdb_status kdb_get_tuning(kdb_tuning* out) {
+  if (!out) return KDB_ERR_INVALID_ARGUMENT;
+  out->partition_shape = g_part_shape.load();
+  out->radix_shape = g_rec_shape.load();
+  return KDB_OK;
+}
+
+kdb_status kdb_set_tuning(const kdb_tuning* t) {
+  if (!t || t->partition_shape < 0 || t->partition_shape >= kPartShapes || t->radix_shape < 0 ||
+      t->radix_shape >= kRecShapes)
+    return KDB_ERR_INVALID_ARGUMENT;
+  g_part_shape.store(t->partition_shape);
+  g_rec_shape.store(t->radix_shape);
+  return KDB_OK;
+}
+
+kdb_status kdb_autotune(const void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
+                        int reps, kdb_tuning* out_best, float* out_best_ms, float* h_ms,
+                        kdb_stream_t stream) {
+  kdb_status s = check_common(n, k, stride_bytes);
+  if (s == KDB_OK) s = check_mode_k(mode, k);
+  if (s != KDB_OK) return s;
+  if (n < 2 || reps < 1 || reps > 64 || !d_points || (reinterpret_cast<uintptr_t>(d_points) & 3))
+    return KDB_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Plan P;
+  P.sets.push_back(SetInfo{0u, (uint32_t)n});
+  P.total = (uint32_t)n;
+  P.k = k;
+  P.stride = stride_bytes;
+  P.mode = split_of(mode);
+  P.ints = ints_of(mode);
+  make_plan(P);
+  if (P.too_wide) return KDB_ERR_INVALID_ARGUMENT;
+  int dev, sms;
+  cudaMemPool_t pool;
+  s = device_setup(&dev, &pool, &sms);
+  if (s != KDB_OK) return s;
+  const size_t pts_bytes = (size_t)n * stride_bytes;
+  void *copy = nullptr, *ws = nullptr;
+  s = pool_alloc(&copy, pts_bytes, pool, st);
+  if (s == KDB_OK) s = pool_alloc(&ws, P.bytes, pool, st);
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (s == KDB_OK && (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess))
+    s = KDB_ERR_CUDA;
+  // the tuned kernels run only on the list path with at least one global level
+  const bool tuned = P.use_lists && !P.act.empty();
+  const kdb_tuning cur{g_part_shape.load(), g_rec_shape.load()};
+  const int np = kPartShapes, nr = kRecShapes;
+  std::vector<float> med(np * nr, -1.0f);
+  std::vector<float> t(reps);
+  for (int c = 0; c < np * nr && s == KDB_OK; ++c) {
+    const int ps = c / nr, rs = c % nr;
+    if (!tuned && (ps != cur.partition_shape || rs != cur.radix_shape)) continue;
+    P.part_shape = ps;
+    P.rec_shape = rs;
+    for (int r = -1; r < reps && s == KDB_OK; ++r) {  // r = -1: untimed first build
+      if (cudaMemcpyAsync(copy, d_points, pts_bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+          cudaEventRecord(ev[0], st) != cudaSuccess) {
+        s = KDB_ERR_CUDA;
+        break;
+      }
+      s = enqueue_build(P, static_cast<unsigned char*>(copy), ws, sms, nullptr, nullptr, st);
+      if (cudaEventRecord(ev[1], st) != cudaSuccess && s == KDB_OK) s = KDB_ERR_CUDA;
+      const kdb_status f = finish(P, ws, st);
+      if (s == KDB_OK) s = f;
+      float ms = 0.0f;
+      if (s == KDB_OK && cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) s = KDB_ERR_CUDA;
+      if (r >= 0) t[r] = ms;
+    }
+    if (s == KDB_OK) {
+      std::sort(t.begin(), t.end());
+      med[c] = t[reps / 2];
+    }
+  }
+  int best = -1;
+  for (int c = 0; c < np * nr; ++c)
+    if (med[c] >= 0.0f && (best < 0 || med[c] < med[best])) best = c;
+  if (s == KDB_OK && best >= 0) {
+    const kdb_tuning b{best / nr, best % nr};
+    kdb_set_tuning(&b);
+    if (out_best) *out_best = b;
+    if (out_best_ms) *out_best_ms = med[best];
+    if (h_ms) std::copy(med.begin(), med.end(), h_ms);
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  if (copy) cudaFreeAsync(copy, st);
+  if (ws) cudaFreeAsync(ws, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && s == KDB_OK) s = KDB_ERR_CUDA;
+  cudaGetLastError();
+  return s;
 }
 
 int kdb_debug_inject_fault(int fault, int64_t arg) {

@@ -32,24 +32,26 @@ cudaError_t ensure_smem(const void* func, size_t bytes);
 // Presorted-list levels (kdb_part.cu), k <= 3: one 16-byte entry per point
 // (order-preserving keys of coordinates 0..2, original index), one list per
 // dimension.
-// Partition tile shape (threads x items per thread) and resident blocks per
-// SM; compile-time options so that a sweep can try other shapes.
-// Measured at 1e8 float3 round robin (16 partition launches): 256 x 13 at
-// four blocks per SM 11.1 ms; 128 x 13 at eight 12.2 ms; 128 x 11 at eight
-// 13.2 ms; 512 x 13 at two 11.1 ms; 256 x 16 at three 11.9 ms.
-#ifndef KDB_PART_THREADS
-#define KDB_PART_THREADS 256
-#endif
-#ifndef KDB_PART_ITEMS
-#define KDB_PART_ITEMS 13
-#endif
-#ifndef KDB_PART_BLOCKS
-#define KDB_PART_BLOCKS 4
-#endif
-constexpr int kPartThreads = KDB_PART_THREADS;
-constexpr int kPartItems = KDB_PART_ITEMS;
-constexpr int kPartBlocksPerSM = KDB_PART_BLOCKS;
-constexpr int kPartTile = kPartThreads * kPartItems;  // < 2^13 - 1: <= two segments a tile
+// Tile shapes of the two sort kernels: threads x items per thread at a
+// number of resident blocks per SM.  Each kernel is compiled for a few
+// measured shapes; the autotuner (kdb_autotune) times them on a problem and
+// keeps the fastest, shape 0 being the default.  Measured at 1e8 float3
+// round robin: partition 256 x 13 at four blocks per SM 11.1 ms, 512 x 13 at
+// two 11.1 ms, 128 x 13 at eight 12.2 ms; record sort 256 x 13 at three
+// 11.7 ms, 256 x 9 at four 11.9 ms.
+struct TileShape {
+  int threads, items, blocks;
+};
+constexpr int kPartShapes = 3;
+constexpr TileShape kPartShape[kPartShapes] = {{256, 13, 4}, {512, 13, 2}, {128, 13, 8}};
+constexpr int kRecShapes = 2;
+constexpr TileShape kRecShape[kRecShapes] = {{256, 13, 3}, {256, 9, 4}};
+// smallest tile of each kernel: the look-back buffers are sized for it.  A
+// partition tile stays below 2^13 - 1 entries, so it holds at most two
+// segments of a global level.
+constexpr int kPartTile = 128 * 13;
+constexpr int kRecTileMin = 256 * 9;
+static_assert(512 * 13 < (1 << 13) - 1, "partition tiles hold at most two segments");
 struct ListBuildArgs {      // level-0 array of several sets
   LevelCtx x;               // level 0
   uint32_t items;
@@ -98,6 +100,7 @@ struct PartArgs {
   int b;                    // levels to advance, 1..kLiftMax (b > 1: one active set)
   int pos_first;            // 1: the list is in level p's split order (its dimension is
                             // level p's), so the first level goes by position
+  int shape;                // tile shape: index into kPartShape
   int handoff;              // 1: every set goes to the local finish at level p + b
   const uint4* in;          // list sorted by (tag on level p, key_dlist, index)
   uint4* out_next;          // the list on level p + b
@@ -114,13 +117,13 @@ struct PartArgs {
   uint64_t wait_ns;
   uint64_t status_words;    // capacity of status
 };
-size_t partition_smem();
-size_t rec_sort_smem();
-uint32_t rec_sort_tile();  // entries per record-sort tile (one look-back word per digit each)
+size_t partition_smem(int shape);
+size_t rec_sort_smem(int shape);
+uint32_t rec_sort_tile();  // entries of the smallest record-sort tile (one look-back word per digit each)
 cudaError_t launch_gather_level0(const ListBuildArgs& a, cudaStream_t st);
 cudaError_t launch_rec_hist(const RecHistArgs& a, cudaStream_t st);
 cudaError_t launch_rec_sort_pass(const uint4* in, uint4* out, const PassCtl& c, const LevelCtx& x,
-                                 const uint32_t* seg_hist, int d, cudaStream_t st);
+                                 const uint32_t* seg_hist, int d, int shape, cudaStream_t st);
 cudaError_t launch_pivots(const PivotArgs& a, cudaStream_t st);
 cudaError_t launch_partition(const PartArgs& a, cudaStream_t st);
 

@@ -82,26 +82,15 @@ __global__ void __launch_bounds__(256) rec_hist_kernel(RecHistArgs a) {
 // every set its own segment.  The tile's records are staged by bulk copy; only
 // their slot order is staged for the write-out, which reads the records from
 // shared memory in digit order and writes each digit's run contiguously.
-// Record-sort tile shape and resident blocks per SM (compile-time options so
-// that a sweep can try other shapes).
-#ifndef KDB_REC_THREADS
-#define KDB_REC_THREADS 256
-#endif
-#ifndef KDB_REC_ITEMS
-#define KDB_REC_ITEMS 13
-#endif
-#ifndef KDB_REC_BLOCKS
-#define KDB_REC_BLOCKS 3
-#endif
-constexpr int RT = KDB_REC_THREADS;  // threads of a record-sort block
-constexpr int RI = KDB_REC_ITEMS;    // entries per thread: 3328 a tile, three blocks per SM
-constexpr int RTILE = RT * RI;
-constexpr int RW = RT / 32;
-
-__global__ void __launch_bounds__(RT, KDB_REC_BLOCKS)
+// The tile shape (threads RT, entries per thread RI, resident blocks RB) is a
+// template parameter; the shapes built are listed in kRecShape.
+template <int RT, int RI, int RB>
+__global__ void __launch_bounds__(RT, RB)
     rec_sort_pass(const uint4* __restrict__ in, uint4* __restrict__ out, PassCtl c, LevelCtx x,
                   const uint32_t* __restrict__ seg_hist, int d) {
   constexpr int BINS = 2 * kRadix;
+  constexpr int RTILE = RT * RI;
+  constexpr int RW = RT / 32;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint4* s_rec = reinterpret_cast<uint4*>(smem_raw);
   uint16_t* s_slot = reinterpret_cast<uint16_t*>(s_rec + RTILE);
@@ -272,8 +261,11 @@ __global__ void __launch_bounds__(RT, KDB_REC_BLOCKS)
 
 }  // namespace
 
-size_t rec_sort_smem() { return (size_t)RTILE * 18 + (size_t)2 * kRadix * RW * 2; }
-uint32_t rec_sort_tile() { return (uint32_t)RTILE; }
+size_t rec_sort_smem(int shape) {
+  const TileShape& sh = kRecShape[shape];
+  return (size_t)sh.threads * sh.items * 18 + (size_t)2 * kRadix * (sh.threads / 32) * 2;
+}
+uint32_t rec_sort_tile() { return (uint32_t)kRecTileMin; }
 
 cudaError_t launch_gather_level0(const ListBuildArgs& a, cudaStream_t st) {
   if (a.items == 0) return cudaSuccess;
@@ -287,16 +279,26 @@ cudaError_t launch_rec_hist(const RecHistArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_rec_sort_pass(const uint4* in, uint4* out, const PassCtl& c, const LevelCtx& x,
-                                 const uint32_t* seg_hist, int d, cudaStream_t st) {
-  if (c.n == 0) return cudaSuccess;
-  const size_t smem = rec_sort_smem();
-  cudaError_t e =
-      ensure_smem((const void*)rec_sort_pass, smem);
+template <int S>
+cudaError_t launch_rec_sort_shape(const uint4* in, uint4* out, const PassCtl& c, const LevelCtx& x,
+                                  const uint32_t* seg_hist, int d, cudaStream_t st) {
+  constexpr TileShape sh = kRecShape[S];
+  const size_t smem = rec_sort_smem(S);
+  cudaError_t e = ensure_smem((const void*)rec_sort_pass<sh.threads, sh.items, sh.blocks>, smem);
   if (e != cudaSuccess) return e;
-  const uint32_t tiles = (c.n + RTILE - 1) / RTILE;
-  rec_sort_pass<<<tiles, RT, smem, st>>>(in, out, c, x, seg_hist, d);
+  const uint32_t tile = (uint32_t)(sh.threads * sh.items);
+  const uint32_t tiles = (c.n + tile - 1) / tile;
+  rec_sort_pass<sh.threads, sh.items, sh.blocks><<<tiles, sh.threads, smem, st>>>(in, out, c, x,
+                                                                                   seg_hist, d);
   return cudaGetLastError();
+}
+
+cudaError_t launch_rec_sort_pass(const uint4* in, uint4* out, const PassCtl& c, const LevelCtx& x,
+                                 const uint32_t* seg_hist, int d, int shape, cudaStream_t st) {
+  if (c.n == 0) return cudaSuccess;
+  static_assert(kRecShapes == 2, "one launcher per shape");
+  if (shape == 1) return launch_rec_sort_shape<1>(in, out, c, x, seg_hist, d, st);
+  return launch_rec_sort_shape<0>(in, out, c, x, seg_hist, d, st);
 }
 
 }  // namespace kdb

@@ -95,10 +95,6 @@ __global__ void tight_children_kernel(TightArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-constexpr int PT = kPartThreads;
-constexpr int PI = kPartItems;
-constexpr int PTILE = PT * PI;
-constexpr int PW = PT / 32;
 constexpr int NB = 2 * kLiftBins;  // bins of a tile: (segment A or B) x child
 static_assert(kLiftMax == 3, "pivot tables hold depth-3 subtrees");
 
@@ -199,7 +195,10 @@ __device__ inline bool warp_look_back_bins(const PartArgs& a, uint32_t tile, int
 // list re-sorted by the new tag.  The list is sorted by (tag_p, key, index),
 // so the new order is a stable split of every segment into its 2^b
 // descendants' runs; items pinned on the way are dropped.
-__global__ void __launch_bounds__(PT, kPartBlocksPerSM) partition_kernel(PartArgs a) {
+template <int PT, int PI, int PB>
+__global__ void __launch_bounds__(PT, PB) partition_kernel(PartArgs a) {
+  constexpr int PTILE = PT * PI;
+  constexpr int PW = PT / 32;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint4* s_in = reinterpret_cast<uint4*>(smem_raw);
   __shared__ __align__(8) uint64_t s_bar;
@@ -379,7 +378,9 @@ __global__ void __launch_bounds__(PT, kPartBlocksPerSM) partition_kernel(PartArg
 }
 }  // namespace
 
-size_t partition_smem() { return (size_t)PTILE * 16; }
+size_t partition_smem(int shape) {
+  return (size_t)kPartShape[shape].threads * kPartShape[shape].items * 16;
+}
 
 cudaError_t launch_pivots(const PivotArgs& a, cudaStream_t st) {
   const uint32_t nseg = a.x.nact << a.x.l;
@@ -395,15 +396,26 @@ cudaError_t launch_tight_children(const TightArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int S>
+cudaError_t launch_partition_shape(const PartArgs& a, cudaStream_t st) {
+  constexpr TileShape sh = kPartShape[S];
+  const size_t smem = partition_smem(S);
+  cudaError_t e = ensure_smem((const void*)partition_kernel<sh.threads, sh.items, sh.blocks>, smem);
+  if (e != cudaSuccess) return e;
+  const uint32_t tile = (uint32_t)(sh.threads * sh.items);
+  const uint32_t tiles = (a.n + tile - 1) / tile;
+  partition_kernel<sh.threads, sh.items, sh.blocks><<<tiles, sh.threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_partition(const PartArgs& a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
-  const size_t smem = partition_smem();
-  cudaError_t e =
-      ensure_smem((const void*)partition_kernel, smem);
-  if (e != cudaSuccess) return e;
-  const uint32_t tiles = (a.n + PTILE - 1) / PTILE;
-  partition_kernel<<<tiles, PT, smem, st>>>(a);
-  return cudaGetLastError();
+  static_assert(kPartShapes == 3, "one launcher per shape");
+  switch (a.shape) {
+    case 1: return launch_partition_shape<1>(a, st);
+    case 2: return launch_partition_shape<2>(a, st);
+    default: return launch_partition_shape<0>(a, st);
+  }
 }
 
 }  // namespace kdb

@@ -30,6 +30,9 @@ ERR_INTERNAL = 7
 PLACEMENT_AUTO = 0
 PLACEMENT_IN_PLACE = 1
 
+TUNE_PARTITION = 0
+TUNE_RADIX = 1
+
 FAULT_NONE = 0
 FAULT_ALLOC = 1
 FAULT_LOOKBACK = 2
@@ -64,6 +67,10 @@ class ServerStats(ctypes.Structure):
                 ("submitted", "completed", "failed", "batches", "retried_alone",
                  "max_batch_requests", "max_inflight_batches", "queued", "inflight_requests")] + \
                [(f, ctypes.c_size_t) for f in ("budget_bytes", "used_bytes", "max_used_bytes")]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("partition_shape", ctypes.c_int32), ("radix_shape", ctypes.c_int32)]
 
 
 class KdbError(RuntimeError):
@@ -103,6 +110,13 @@ def load():
             "kdb_validate": ([vp, i64, i32, i32, i32, ctypes.POINTER(i64), vp], i32),
             "kdb_debug_inject_fault": ([i32, i64], i32),
             "kdb_set_placement": ([i32], i32),
+            "kdb_tuning_shape_count": ([i32], i32),
+            "kdb_tuning_shape": ([i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                  ctypes.POINTER(i32)], i32),
+            "kdb_get_tuning": ([ctypes.POINTER(Tuning)], i32),
+            "kdb_set_tuning": ([ctypes.POINTER(Tuning)], i32),
+            "kdb_autotune": ([vp, i64, i32, i32, i32, i32, ctypes.POINTER(Tuning),
+                              ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), vp], i32),
             "kdb_plan_create": ([vp, i32, i32, i32, i32, ctypes.POINTER(vp)], i32),
             "kdb_plan_enqueue": ([vp, vp, vp], i32),
             "kdb_plan_status": ([vp, vp], i32),
@@ -363,6 +377,51 @@ def kdb_set_placement(placement: int) -> int:
     """Process-wide placement setting (PLACEMENT_AUTO / PLACEMENT_IN_PLACE);
     returns the previous one."""
     return load().kdb_set_placement(placement)
+
+
+def kdb_tuning_shapes(kernel: int) -> list[tuple[int, int, int]]:
+    """(threads, items per thread, blocks per SM) of each compiled shape of
+    ``kernel`` (TUNE_PARTITION or TUNE_RADIX)."""
+    lib = load()
+    count = lib.kdb_tuning_shape_count(kernel)
+    if count < 0:
+        raise KdbError(ERR_INVALID_ARGUMENT, "kdb_tuning_shape_count")
+    out = []
+    for i in range(count):
+        t, it, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib.kdb_tuning_shape(kernel, i, ctypes.byref(t), ctypes.byref(it), ctypes.byref(b)),
+               "kdb_tuning_shape")
+        out.append((t.value, it.value, b.value))
+    return out
+
+
+def kdb_get_tuning() -> tuple[int, int]:
+    """Process-wide (partition shape, radix shape)."""
+    t = Tuning()
+    _check(load().kdb_get_tuning(ctypes.byref(t)), "kdb_get_tuning")
+    return t.partition_shape, t.radix_shape
+
+
+def kdb_set_tuning(partition_shape: int, radix_shape: int) -> None:
+    t = Tuning(partition_shape, radix_shape)
+    _check(load().kdb_set_tuning(ctypes.byref(t)), "kdb_set_tuning")
+
+
+def kdb_autotune(points, k: int, mode: int = ROUND_ROBIN, reps: int = 3, stream=None) -> dict:
+    """Times every pair of tile shapes on a copy of ``points`` and keeps the
+    fastest as the process-wide setting.  Returns {"best": (p, r), "best_ms":
+    median ms, "ms": {(p, r): median ms}} (pairs not timed are left out)."""
+    ptr, n, stride = _records(points)
+    lib = load()
+    npart = lib.kdb_tuning_shape_count(TUNE_PARTITION)
+    nrad = lib.kdb_tuning_shape_count(TUNE_RADIX)
+    best = Tuning()
+    best_ms = ctypes.c_float()
+    ms = (ctypes.c_float * (npart * nrad))()
+    _check(lib.kdb_autotune(ptr, n, k, stride, _mode(points, mode), reps, ctypes.byref(best),
+                            ctypes.byref(best_ms), ms, _stream(stream)), "kdb_autotune")
+    table = {(c // nrad, c % nrad): ms[c] for c in range(npart * nrad) if ms[c] >= 0}
+    return {"best": (best.partition_shape, best.radix_shape), "best_ms": best_ms.value, "ms": table}
 
 
 def kdb_debug_inject_fault(fault: int, arg: int = 0) -> int:

@@ -79,3 +79,28 @@ def test_placement_setting_round_trips(lib):
         assert kdb.kdb_set_placement(kdb.PLACEMENT_AUTO) == kdb.PLACEMENT_IN_PLACE
     finally:
         kdb.kdb_set_placement(kdb.PLACEMENT_AUTO)
+
+
+def test_tuning_shapes_and_setting_round_trip(lib):
+    part = kdb.kdb_tuning_shapes(kdb.TUNE_PARTITION)
+    rad = kdb.kdb_tuning_shapes(kdb.TUNE_RADIX)
+    assert len(part) >= 2 and len(rad) >= 2
+    for threads, items, blocks in part + rad:
+        assert threads % 32 == 0 and items > 0 and blocks > 0
+        # a tile of either sort kernel spans at most two subtrees of a global
+        # level (subtrees there hold at least 2^13 - 1 points)
+        assert threads * items < (1 << 13) - 1
+    assert part[0] == (256, 13, 4) and rad[0] == (256, 13, 3)  # the defaults
+    assert lib.kdb_tuning_shape_count(9) == -1
+    assert lib.kdb_tuning_shape(kdb.TUNE_RADIX, len(rad), None, None, None) == kdb.ERR_INVALID_ARGUMENT
+    assert kdb.kdb_get_tuning() == (0, 0)
+    try:
+        kdb.kdb_set_tuning(len(part) - 1, len(rad) - 1)
+        assert kdb.kdb_get_tuning() == (len(part) - 1, len(rad) - 1)
+        with pytest.raises(kdb.KdbError):
+            kdb.kdb_set_tuning(len(part), 0)  # out of range: unchanged
+        with pytest.raises(kdb.KdbError):
+            kdb.kdb_set_tuning(0, -1)
+        assert kdb.kdb_get_tuning() == (len(part) - 1, len(rad) - 1)
+    finally:
+        kdb.kdb_set_tuning(0, 0)

@@ -1,0 +1,118 @@
+"""Tile shapes of the two sort kernels (kdb_set_tuning, kdb_autotune): every
+compiled shape pair must give the oracle's output bit for bit, since a shape
+only changes how a pass is cut into tiles, not what it computes."""
+import functools
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle
+from paper_2211_00120_gb300 import kdb, synth
+from tests.test_gpu_parity import gpu_build, tie_grid
+
+pytestmark = pytest.mark.gpu
+
+PAIRS = list(itertools.product(range(len(kdb.kdb_tuning_shapes(kdb.TUNE_PARTITION))),
+                               range(len(kdb.kdb_tuning_shapes(kdb.TUNE_RADIX)))))
+
+
+@pytest.fixture(autouse=True)
+def default_tuning_after():
+    yield
+    kdb.kdb_set_tuning(0, 0)
+
+
+CASES = {
+    # several tiles of every shape and a ragged tail, two to five global levels
+    "uniform3": lambda: synth.uniform(300001, 3, seed=17),
+    "mixed2": lambda: synth.mixed(65537, 2, seed=5),
+    "ties3": lambda: tie_grid(120011, 3, 7, seed=3),
+    "int1": lambda: synth.int32_uniform(200003, 1, seed=8),
+}
+MODES = [oracle.ROUND_ROBIN, oracle.WIDEST, oracle.WIDEST_TIGHT]
+
+
+@functools.lru_cache(maxsize=None)
+def case(name):
+    return CASES[name]()
+
+
+@functools.lru_cache(maxsize=None)
+def want(name, k, mode):
+    return oracle.build(case(name), k, mode)
+
+
+def check(name, k, mode):
+    pts = case(name)
+    wpts, worig = want(name, k, mode)
+    got, gorig = gpu_build(pts, k, mode)
+    if not np.array_equal(gorig, worig):
+        bad = int(np.flatnonzero(gorig != worig)[0])
+        raise AssertionError(f"{name} mode={mode} tuning={kdb.kdb_get_tuning()}: node {bad} holds "
+                             f"{gorig[bad]}, oracle {worig[bad]}")
+    assert got.view(np.uint32).tobytes() == wpts.view(np.uint32).tobytes()
+
+
+@pytest.mark.parametrize("pair", PAIRS)
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("name", ["uniform3", "mixed2", "ties3"])
+def test_every_shape_pair_matches_the_oracle(name, mode, pair):
+    k = case(name).shape[1]
+    kdb.kdb_set_tuning(*pair)
+    check(name, k, mode)
+
+
+@pytest.mark.parametrize("pair", PAIRS)
+def test_every_shape_pair_int32(pair):
+    kdb.kdb_set_tuning(*pair)
+    check("int1", 1, oracle.ROUND_ROBIN)
+
+
+@pytest.mark.parametrize("pair", PAIRS[1:])
+def test_batched_sets_under_other_shapes(pair):
+    sizes = [9000, 1, 40000, 8191, 8192, 130001, 2, 17000]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    pts = synth.uniform(int(offs[-1]), 3, seed=23)
+    kdb.kdb_set_tuning(*pair)
+    d = torch.from_numpy(pts.copy()).cuda()
+    kdb.kdb_build_batched(d, offs, 3, kdb.ROUND_ROBIN)
+    got = d.cpu().numpy()
+    for a, b in zip(offs[:-1], offs[1:]):
+        w, _ = oracle.build(pts[a:b], 3, oracle.ROUND_ROBIN)
+        assert got[a:b].view(np.uint32).tobytes() == w.view(np.uint32).tobytes()
+
+
+def test_autotune_keeps_the_fastest_pair_and_leaves_points_alone():
+    pts = synth.uniform(2_000_000, 3, seed=31)
+    d = torch.from_numpy(pts).cuda()
+    r = kdb.kdb_autotune(d, 3, kdb.ROUND_ROBIN, reps=3)
+    assert set(r["ms"]) == set(PAIRS)
+    assert all(v > 0 for v in r["ms"].values())
+    assert r["best"] in PAIRS and r["best_ms"] == min(r["ms"].values())
+    assert kdb.kdb_get_tuning() == r["best"]
+    assert torch.equal(d.cpu(), torch.from_numpy(pts))  # read only
+    # a build under the kept setting is still the oracle's tree
+    got, _ = gpu_build(pts, 3, kdb.ROUND_ROBIN)
+    w, _ = oracle.build(pts, 3, oracle.ROUND_ROBIN)
+    assert got.view(np.uint32).tobytes() == w.view(np.uint32).tobytes()
+
+
+def test_autotune_times_only_the_current_pair_where_nothing_is_tuned():
+    kdb.kdb_set_tuning(*PAIRS[-1])
+    # k = 4 builds without the per-dimension lists; 5000 points need no global level
+    for pts, k in [(synth.uniform(300000, 4, seed=2), 4), (synth.uniform(5000, 3, seed=2), 3)]:
+        r = kdb.kdb_autotune(torch.from_numpy(pts).cuda(), k, kdb.ROUND_ROBIN, reps=1)
+        assert list(r["ms"]) == [PAIRS[-1]] and r["best"] == PAIRS[-1]
+
+
+def test_autotune_refuses_bad_arguments():
+    d = torch.from_numpy(synth.uniform(1000, 3, seed=1)).cuda()
+    for reps in (0, 65):
+        with pytest.raises(kdb.KdbError) as e:
+            kdb.kdb_autotune(d, 3, kdb.ROUND_ROBIN, reps=reps)
+        assert e.value.code == kdb.ERR_INVALID_ARGUMENT
+    with pytest.raises(kdb.KdbError):
+        kdb.kdb_autotune(d[:1], 3, kdb.ROUND_ROBIN)
+    assert kdb.kdb_get_tuning() == (0, 0)
