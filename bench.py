@@ -166,9 +166,10 @@ def traffic_per_launch(kind: str, n_items_per_launch: float, shapes: dict):
     if not j.get("kernel_hash") or j["kernel_hash"] != kernel_hash(kind):
         return None
     shape = shapes.get({"partition_pass": "partition", "radix_pass": "radix"}.get(kind, ""))
-    if shape is not None and list(j.get("tile_shape", [])) != list(shape):
-        return None
-    return j["dram_bytes_per_item"] * n_items_per_launch
+    if shape is None:
+        return j["dram_bytes_per_item"] * n_items_per_launch
+    per_item = j.get("by_shape", {}).get("x".join(str(v) for v in shape))
+    return None if per_item is None else per_item * n_items_per_launch
 
 
 class ClockSampler:
