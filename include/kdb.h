@@ -374,6 +374,16 @@ KDB_API kdb_status kdb_set_tuning(const kdb_tuning* tuning);
 KDB_API kdb_status kdb_autotune(const void* d_points, int64_t n, int k, int stride_bytes,
                                 kdb_split_mode mode, int reps, kdb_tuning* out_best,
                                 float* out_best_ms, float* h_ms, kdb_stream_t stream);
+/*
+ * kdb_save_tuning / kdb_load_tuning -- the process-wide setting as a small
+ * JSON file: {"partition": [threads, items, blocks], "radix": [threads, items,
+ * blocks]}.  Shapes are stored by value, so a file from a library with other
+ * compiled shapes is refused on load (KDB_ERR_INVALID_ARGUMENT, setting
+ * unchanged), as are unreadable or malformed files.  Saving returns
+ * KDB_ERR_INVALID_ARGUMENT if the file cannot be written.  Host only.
+ */
+KDB_API kdb_status kdb_save_tuning(const char* path);
+KDB_API kdb_status kdb_load_tuning(const char* path);
 
 /*
  * kdb_validate -- check the k-d condition of a level-order tree (Sec. 1):

@@ -21,6 +21,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/kdb.h"
@@ -1195,6 +1196,66 @@ kdb_status kdb_set_tuning(const kdb_tuning* t) {
   g_part_shape.store(t->partition_shape);
   g_rec_shape.store(t->radix_shape);
   return KDB_OK;
+}
+
+kdb_status kdb_save_tuning(const char* path) {
+  if (!path) return KDB_ERR_INVALID_ARGUMENT;
+  const TileShape& p = kPartShape[g_part_shape.load()];
+  const TileShape& r = kRecShape[g_rec_shape.load()];
+  FILE* f = fopen(path, "w");
+  if (!f) return KDB_ERR_INVALID_ARGUMENT;
+  const int w = fprintf(f, "{\"partition\": [%d, %d, %d], \"radix\": [%d, %d, %d]}\n", p.threads,
+                        p.items, p.blocks, r.threads, r.items, r.blocks);
+  return (fclose(f) == 0 && w > 0) ? KDB_OK : KDB_ERR_INVALID_ARGUMENT;
+}
+
+namespace {
+// The three integers of the array that follows "key": in a JSON text; false
+// if the key is missing or the value is not an array of three integers.
+bool json_shape(const std::string& text, const char* key, TileShape* out) {
+  const std::string k = std::string("\"") + key + "\"";
+  size_t at = text.find(k);
+  if (at == std::string::npos) return false;
+  at = text.find_first_not_of(" \t\r\n", at + k.size());
+  if (at == std::string::npos || text[at] != ':') return false;
+  at = text.find_first_not_of(" \t\r\n", at + 1);
+  if (at == std::string::npos || text[at] != '[') return false;
+  const char* c = text.c_str() + at + 1;
+  int v[3];
+  for (int i = 0; i < 3; ++i) {
+    char* end = nullptr;
+    const long x = strtol(c, &end, 10);
+    if (end == c || x < 1 || x > 4096) return false;
+    v[i] = (int)x;
+    while (*end == ' ' || *end == '\t' || *end == '\r' || *end == '\n') ++end;
+    if (*end != (i < 2 ? ',' : ']')) return false;
+    c = end + 1;
+  }
+  *out = TileShape{v[0], v[1], v[2]};
+  return true;
+}
+
+int shape_index(const TileShape* table, int count, const TileShape& s) {
+  for (int i = 0; i < count; ++i)
+    if (table[i].threads == s.threads && table[i].items == s.items && table[i].blocks == s.blocks)
+      return i;
+  return -1;
+}
+}  // namespace
+
+kdb_status kdb_load_tuning(const char* path) {
+  if (!path) return KDB_ERR_INVALID_ARGUMENT;
+  FILE* f = fopen(path, "r");
+  if (!f) return KDB_ERR_INVALID_ARGUMENT;
+  std::string text;
+  char buf[512];
+  size_t got;
+  while ((got = fread(buf, 1, sizeof buf, f)) > 0 && text.size() < 65536) text.append(buf, got);
+  fclose(f);
+  TileShape p, r;
+  if (!json_shape(text, "partition", &p) || !json_shape(text, "radix", &r)) return KDB_ERR_INVALID_ARGUMENT;
+  const kdb_tuning t{shape_index(kPartShape, kPartShapes, p), shape_index(kRecShape, kRecShapes, r)};
+  return kdb_set_tuning(&t);  // refuses a shape this library does not carry
 }
 
 kdb_status kdb_autotune(const void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,

@@ -115,6 +115,8 @@ def load():
                                   ctypes.POINTER(i32)], i32),
             "kdb_get_tuning": ([ctypes.POINTER(Tuning)], i32),
             "kdb_set_tuning": ([ctypes.POINTER(Tuning)], i32),
+            "kdb_save_tuning": ([ctypes.c_char_p], i32),
+            "kdb_load_tuning": ([ctypes.c_char_p], i32),
             "kdb_autotune": ([vp, i64, i32, i32, i32, i32, ctypes.POINTER(Tuning),
                               ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), vp], i32),
             "kdb_plan_create": ([vp, i32, i32, i32, i32, ctypes.POINTER(vp)], i32),
@@ -405,6 +407,16 @@ def kdb_get_tuning() -> tuple[int, int]:
 def kdb_set_tuning(partition_shape: int, radix_shape: int) -> None:
     t = Tuning(partition_shape, radix_shape)
     _check(load().kdb_set_tuning(ctypes.byref(t)), "kdb_set_tuning")
+
+
+def kdb_save_tuning(path: str) -> None:
+    """Writes the process-wide tile shapes to a JSON file."""
+    _check(load().kdb_save_tuning(os.fsencode(path)), "kdb_save_tuning")
+
+
+def kdb_load_tuning(path: str) -> None:
+    """Sets the process-wide tile shapes from a file written by kdb_save_tuning."""
+    _check(load().kdb_load_tuning(os.fsencode(path)), "kdb_load_tuning")
 
 
 def kdb_autotune(points, k: int, mode: int = ROUND_ROBIN, reps: int = 3, stream=None) -> dict:

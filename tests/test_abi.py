@@ -2,6 +2,7 @@
 include/kdb.h declares.  Only calls that need no GPU are made here: argument
 checking, workspace sizing and status strings."""
 import ctypes
+import json
 import subprocess
 
 import pytest
@@ -102,5 +103,40 @@ def test_tuning_shapes_and_setting_round_trip(lib):
         with pytest.raises(kdb.KdbError):
             kdb.kdb_set_tuning(0, -1)
         assert kdb.kdb_get_tuning() == (len(part) - 1, len(rad) - 1)
+    finally:
+        kdb.kdb_set_tuning(0, 0)
+
+
+def test_tuning_file_round_trip_and_refusals(lib, tmp_path):
+    part = kdb.kdb_tuning_shapes(kdb.TUNE_PARTITION)
+    rad = kdb.kdb_tuning_shapes(kdb.TUNE_RADIX)
+    f = tmp_path / "tuning.json"
+    try:
+        kdb.kdb_set_tuning(2, 1)
+        kdb.kdb_save_tuning(str(f))
+        j = json.loads(f.read_text())
+        assert j == {"partition": list(part[2]), "radix": list(rad[1])}
+        kdb.kdb_set_tuning(0, 0)
+        kdb.kdb_load_tuning(str(f))
+        assert kdb.kdb_get_tuning() == (2, 1)
+        # shapes are matched by value: a shape this library does not carry,
+        # a malformed file or a missing one is refused and changes nothing
+        bad = [{"partition": [96, 7, 5], "radix": list(rad[0])},
+               {"partition": list(part[0])},
+               {"partition": list(part[0]), "radix": [256, 13]}]
+        for b in bad:
+            f.write_text(json.dumps(b))
+            with pytest.raises(kdb.KdbError):
+                kdb.kdb_load_tuning(str(f))
+        f.write_text("not json")
+        with pytest.raises(kdb.KdbError):
+            kdb.kdb_load_tuning(str(f))
+        with pytest.raises(kdb.KdbError):
+            kdb.kdb_load_tuning(str(tmp_path / "missing.json"))
+        assert kdb.kdb_get_tuning() == (2, 1)
+        # whitespace and key order are free
+        f.write_text('{ "radix" : [ %d , %d , %d ] ,\n "partition":[%d,%d,%d] }' % (rad[0] + part[1]))
+        kdb.kdb_load_tuning(str(f))
+        assert kdb.kdb_get_tuning() == (1, 0)
     finally:
         kdb.kdb_set_tuning(0, 0)
