@@ -168,12 +168,19 @@ KDB_API kdb_status kdb_build_batched_async(void* d_points, const int64_t* h_offs
 KDB_API kdb_status kdb_error_word_status(uint32_t word);
 
 /*
- * kdb_build_host -- kdb_build for records in host memory: copies them to the
- * device, builds, and copies the tree back into h_points on `stream` (pinned
- * host memory gives asynchronous copies).  The copy to the device goes in
- * chunks (of at least 64 MiB, at most 8) on a stream of the call's own, and
- * the build's first pass over each chunk starts as soon as that chunk has
- * landed.  On a device error (NaN input, ...) h_points is left as it was.
+ * kdb_build_host -- kdb_build for records in host memory.  Two paths, same
+ * output:
+ *   - page-locked records that the current device can address (e.g. from
+ *     cudaHostAlloc or cudaHostRegister), without payload (stride_bytes = 4k,
+ *     k <= 3) and under the default placement: the kernels read the records
+ *     and write the tree straight into h_points over the host link; no device
+ *     copy of the records is made (every record the build writes is rebuilt
+ *     from the 16-byte entry that carries its coordinates);
+ *   - otherwise: the records are copied to a device buffer in chunks (of at
+ *     least 64 MiB, at most 8) on a stream of the call's own, the build's
+ *     first pass over each chunk starting as soon as it has landed, and the
+ *     tree is copied back into h_points on `stream`.
+ * On a device error (NaN input, ...) h_points is left as it was.
  * Synchronises `stream`.
  */
 KDB_API kdb_status kdb_build_host(void* h_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,

@@ -188,6 +188,7 @@ struct Plan {
   bool singletons = false;  // a set of one record (its node is its record)
   bool too_wide = false;    // (set, subtree, rank) needs more than 64 bits
   int part_shape = -1, rec_shape = -1;  // tile shapes; -1: the process-wide setting
+  int placement = -1;                    // -1: the process-wide setting
   std::vector<std::vector<ActiveEntry>> act;  // per level l = 0 .. Lmax-2
   std::vector<uint32_t> items;                // per level
   std::vector<int> passes;                    // per level
@@ -690,7 +691,8 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   // Records without payload are written straight to their nodes from the
   // entries (which hold every coordinate bit) as the nodes are pinned; the
   // caller's array is not read after the prepass, and no placement is left.
-  const bool direct = P.can_direct && g_placement.load() == KDB_PLACEMENT_AUTO;
+  const int placement = P.placement >= 0 ? P.placement : g_placement.load();
+  const bool direct = P.can_direct && placement == KDB_PLACEMENT_AUTO;
   uint4* lents = P.has_lents && (direct || tight) ? at<uint4>(ws, P.o_lents) : nullptr;
   int lat[3] = {0, 0, 0};
   auto level_ctx = [&](int l) {
@@ -992,7 +994,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     // every record is at its node already; put the input back if the build failed
     Prof pf(K_PLACEMENT, 0.0, 1, st);
     KDB_CK(launch_restore(pts, ents0, T, k, err, P.ints, st));
-  } else if (g_placement.load() == KDB_PLACEMENT_AUTO && (size_t)T * P.stride <= P.gather_bytes) {
+  } else if (placement == KDB_PLACEMENT_AUTO && (size_t)T * P.stride <= P.gather_bytes) {
     Prof pf(K_PLACEMENT, (double)T * (4.0 + 4.0 * P.stride), 2, st);
     KDB_CK(launch_place_gather(pm, at<unsigned char>(ws, P.o_gather), sms, st));
   } else {
@@ -1656,6 +1658,32 @@ kdb_status kdb_build_host(void* h_points, int64_t n, int k, int stride_bytes, kd
   P.ints = ints_of(mode);
   make_plan(P);
   if (P.too_wide) return KDB_ERR_INVALID_ARGUMENT;
+  // Records without payload in page-locked memory that this device can
+  // address: every record the build writes is rebuilt from its entry, so the
+  // kernels read the caller's records and write the tree straight into them
+  // (over the host link), with no device copy of the records at all.
+  P.placement = g_placement.load();
+  if (P.can_direct && P.placement == KDB_PLACEMENT_AUTO &&
+      (reinterpret_cast<uintptr_t>(h_points) & 3) == 0) {
+    cudaPointerAttributes pa;
+    void* mapped = nullptr;
+    if (cudaPointerGetAttributes(&pa, h_points) == cudaSuccess && pa.type == cudaMemoryTypeHost)
+      mapped = pa.devicePointer;
+    cudaGetLastError();
+    if (mapped) {
+      void* ws = nullptr;
+      s = pool_alloc(&ws, P.bytes, pool, st);
+      if (s == KDB_OK) s = enqueue_build(P, static_cast<unsigned char*>(mapped), ws, sms, nullptr, nullptr, st);
+      const kdb_status f = ws ? finish(P, ws, st) : KDB_OK;
+      if (s == KDB_OK) s = f;
+      if (ws) cudaFreeAsync(ws, st);
+      if (cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        if (s == KDB_OK) s = KDB_ERR_CUDA;
+      }
+      return s;
+    }
+  }
   const size_t bytes = (size_t)n * stride_bytes;
   void* d = nullptr;
   void* ws = nullptr;

@@ -544,21 +544,28 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
           s_bad = 1;
           continue;
         }
-        if (side == 2) {
-          const uint32_t o = s_orig[it];
-          const uint32_t node = ls.off + full_nodes(L) + (wk.s_rel << jj) + tl;
-          a.perm[node] = o;
-          if (ent_of) {  // the record goes straight to its node
-            const uint4 e = ent_of[it];
-            write_record_from_entry(a.pts_out + (uint64_t)node * a.stride, e, k, a.ints);
-            if (widest)
-              s_lplane[dbase + tl] =
-                  __uint_as_float(key_to_float_bits(d == 0 ? e.x : (d == 1 ? e.y : e.z)));
-          } else if (widest) {
-            s_lplane[dbase + tl] = coord_of(a.pts, o, a.stride, d);
-          }
-        }
         s_info[it] = (uint16_t)((side << 14) | off);
+      }
+      // the group's first thread pins the segment's pivot: with one thread
+      // per segment, the lanes of a warp write consecutive nodes together
+      if (t0 == 0 && st + pr < en) {
+        const uint32_t it = list[st + pr - r.p0 + sb];
+        if (it >= m) {
+          s_bad = 1;
+          continue;
+        }
+        const uint32_t o = s_orig[it];
+        const uint32_t node = ls.off + full_nodes(L) + (wk.s_rel << jj) + tl;
+        a.perm[node] = o;
+        if (ent_of) {  // the record goes straight to its node
+          const uint4 e = ent_of[it];
+          write_record_from_entry(a.pts_out + (uint64_t)node * a.stride, e, k, a.ints);
+          if (widest)
+            s_lplane[dbase + tl] =
+                __uint_as_float(key_to_float_bits(d == 0 ? e.x : (d == 1 ? e.y : e.z)));
+        } else if (widest) {
+          s_lplane[dbase + tl] = coord_of(a.pts, o, a.stride, d);
+        }
       }
     }
   };

@@ -136,24 +136,70 @@ def test_host_buffer_entry_point():
     assert np.array_equal(h.numpy(), want)
 
 
+@pytest.mark.parametrize("path", ["mapped", "copied_pageable", "copied_payload"])
 @pytest.mark.parametrize("mode", [RR, WIDEST])
-def test_host_buffer_copied_in_chunks(mode):
-    """12M float3 records (144 MB): the copy to the device goes in two chunks
-    overlapped with the first pass; the tree equals the device build's, and a
-    NaN leaves the host records as they were."""
+def test_host_buffer_paths(mode, path):
+    """12M records (144-192 MB) in host memory.  Pinned records without payload
+    are read and written in place by the kernels ("mapped"); pageable records,
+    or records with payload, are copied to the device in two chunks overlapped
+    with the first pass.  Every path gives the device build's tree, and a NaN
+    leaves the host records as they were."""
     pts = synth.mixed(12_000_000, 3, seed=13)
+    if path == "copied_payload":
+        pts = synth.with_stride(pts, 4)
     d = torch.from_numpy(pts).cuda()
     kdb.kdb_build(d, 3, mode)
-    h = torch.from_numpy(pts.copy()).pin_memory()
+
+    def host(a):
+        t = torch.from_numpy(a.copy())
+        return t if path == "copied_pageable" else t.pin_memory()
+
+    h = host(pts)
     kdb.kdb_build_host(h, 3, mode)
     assert torch.equal(h.view(torch.int32), d.cpu().view(torch.int32))
     bad = pts.copy()
     bad[11_999_000, 1] = np.nan  # in the last chunk
-    hb = torch.from_numpy(bad.copy()).pin_memory()
+    hb = host(bad)
     with pytest.raises(kdb.KdbError) as e:
         kdb.kdb_build_host(hb, 3, mode)
     assert e.value.code == kdb.ERR_NAN_INPUT
     assert np.array_equal(hb.numpy().view(np.uint32), bad.view(np.uint32))
+
+
+@pytest.mark.parametrize("n", [2, 3, 1000, 8191, 8192, 300001])
+def test_host_buffer_mapped_small_and_ragged(n):
+    pts = synth.uniform(n, 2, seed=n)
+    want, _ = oracle.build(pts, 2, RR)
+    h = torch.from_numpy(pts.copy()).pin_memory()
+    kdb.kdb_build_host(h, 2, RR)
+    assert np.array_equal(h.numpy().view(np.uint32), want.view(np.uint32))
+
+
+def test_host_buffer_mapped_int32_and_tight():
+    pts = synth.int32_uniform(400003, 1, seed=5)
+    want, _ = oracle.build(pts, 1, RR)
+    h = torch.from_numpy(pts.copy()).pin_memory()
+    kdb.kdb_build_host(h, 1, RR)
+    assert np.array_equal(h.numpy(), want)
+    pts = synth.mixed(400003, 3, seed=6)
+    want, _ = oracle.build(pts, 3, oracle.WIDEST_TIGHT)
+    h = torch.from_numpy(pts.copy()).pin_memory()
+    kdb.kdb_build_host(h, 3, kdb.WIDEST_TIGHT)
+    assert np.array_equal(h.numpy().view(np.uint32), want.view(np.uint32))
+
+
+def test_host_buffer_in_place_placement_copies():
+    """Under the in-place placement setting the records go through a device
+    copy (the mapped path needs the default placement); same tree."""
+    pts = synth.uniform(200003, 3, seed=8)
+    want, _ = oracle.build(pts, 3, RR)
+    prev = kdb.kdb_set_placement(kdb.PLACEMENT_IN_PLACE)
+    try:
+        h = torch.from_numpy(pts.copy()).pin_memory()
+        kdb.kdb_build_host(h, 3, RR)
+    finally:
+        kdb.kdb_set_placement(prev)
+    assert np.array_equal(h.numpy().view(np.uint32), want.view(np.uint32))
 
 
 def test_streams_run_independently():
