@@ -14,8 +14,11 @@ from tests.test_gpu_parity import gpu_build, tie_grid
 
 pytestmark = pytest.mark.gpu
 
-PAIRS = list(itertools.product(range(len(kdb.kdb_tuning_shapes(kdb.TUNE_PARTITION))),
-                               range(len(kdb.kdb_tuning_shapes(kdb.TUNE_RADIX)))))
+NPART = len(kdb.kdb_tuning_shapes(kdb.TUNE_PARTITION))
+NRAD = len(kdb.kdb_tuning_shapes(kdb.TUNE_RADIX))
+PAIRS = list(itertools.product(range(NPART), range(NRAD)))
+# every shape of each kernel at least once
+COVER = sorted({(p, p % NRAD) for p in range(NPART)} | {(r % NPART, r) for r in range(NRAD)})
 
 
 @pytest.fixture(autouse=True)
@@ -56,21 +59,27 @@ def check(name, k, mode):
 
 
 @pytest.mark.parametrize("pair", PAIRS)
+def test_every_shape_pair_matches_the_oracle(pair):
+    kdb.kdb_set_tuning(*pair)
+    check("uniform3", 3, oracle.ROUND_ROBIN)
+
+
+@pytest.mark.parametrize("pair", COVER)
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("name", ["uniform3", "mixed2", "ties3"])
-def test_every_shape_pair_matches_the_oracle(name, mode, pair):
+def test_every_shape_in_every_mode(name, mode, pair):
     k = case(name).shape[1]
     kdb.kdb_set_tuning(*pair)
     check(name, k, mode)
 
 
-@pytest.mark.parametrize("pair", PAIRS)
-def test_every_shape_pair_int32(pair):
+@pytest.mark.parametrize("pair", COVER)
+def test_every_shape_int32(pair):
     kdb.kdb_set_tuning(*pair)
     check("int1", 1, oracle.ROUND_ROBIN)
 
 
-@pytest.mark.parametrize("pair", PAIRS[1:])
+@pytest.mark.parametrize("pair", [p for p in COVER if p != (0, 0)])
 def test_batched_sets_under_other_shapes(pair):
     sizes = [9000, 1, 40000, 8191, 8192, 130001, 2, 17000]
     offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
