@@ -17,7 +17,8 @@
  *
  * Conventions shared by every call:
  *   - Records: N records of stride_bytes each, the k coordinates are float32
- *     (or int32, with KDB_COORDS_INT32 in the mode argument) at byte offsets
+ *     (or int32 / uint32, with KDB_COORDS_INT32 / KDB_COORDS_UINT32 in the
+ *     mode argument) at byte offsets
  *     0, 4, ..., 4(k-1); bytes after 4k are payload that is
  *     moved with the record and never read as a coordinate.  1 <= k <= 8,
  *     stride_bytes >= 4k and a multiple of 4, the base 4-byte aligned.
@@ -69,14 +70,19 @@ typedef enum {
 
 /*
  * Coordinate type, OR'ed into the mode argument of every call (build,
- * batched, plans, server, validate): the k coordinates are int32 instead of
- * float32, ordered as integers -- the paper's int1 / int2 data (Table 1,
- * Sec. 5).  Tight-box extents are exact 64-bit differences.  The clipped
- * domain rule (KDB_SPLIT_WIDEST_EXTENT) clips float boxes and is float32
- * only: with this flag it returns KDB_ERR_INVALID_ARGUMENT.  No NaN check
- * applies to int32 coordinates.
+ * batched, plans, server, validate); at most one of the two:
+ *   KDB_COORDS_INT32   the k coordinates are int32 instead of float32,
+ *                      ordered as signed integers -- the paper's int1 / int2
+ *                      data (Table 1, Sec. 5);
+ *   KDB_COORDS_UINT32  they are uint32, ordered as unsigned integers (another
+ *                      scalar type of the templated builder of Sec. 7.2).
+ * Tight-box extents of integer coordinates are exact 64-bit differences.
+ * The clipped domain rule (KDB_SPLIT_WIDEST_EXTENT) clips float boxes and is
+ * float32 only: with either flag it returns KDB_ERR_INVALID_ARGUMENT, as does
+ * a mode with both flags.  No NaN check applies to integer coordinates.
  */
 #define KDB_COORDS_INT32 0x100
+#define KDB_COORDS_UINT32 0x200
 
 typedef enum {
   KDB_OK = 0,

@@ -98,7 +98,7 @@ def _fkey(v: float):
 
 def _widest(lo, hi) -> int:
     if all(isinstance(v, int) for v in list(lo) + list(hi)):
-        ext = [h - lo_ for lo_, h in zip(lo, hi)]  # int32 coordinates: exact
+        ext = [h - lo_ for lo_, h in zip(lo, hi)]  # integer coordinates: exact
     else:
         ext = [np.float32(h) - np.float32(lo_) for lo_, h in zip(lo, hi)]
     best = 0
@@ -113,7 +113,8 @@ def emulate(points: np.ndarray, k: int, mode: int = ROUND_ROBIN, trace=None):
     float32 coordinates).  Returns the original index of the point at each
     node.  ``trace(step, l, tags, order)`` is called after every sort and
     every update (step in {"sort", "update", "final"})."""
-    ints = np.asarray(points).dtype == np.int32  # int32 coordinates (Sec. 5 uses int2)
+    # integer coordinates: int32 (Sec. 5 uses int2) or uint32
+    ints = np.asarray(points).dtype in (np.int32, np.uint32)
     P = np.asarray(points) if ints else np.asarray(points, dtype=np.float32)
     n = P.shape[0]
     if n == 0:

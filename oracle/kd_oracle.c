@@ -34,10 +34,12 @@
  *     and is silent on equal keys);
  *   - NaN coordinates are rejected (KDO_NAN);
  *   - coordinates are float32 unless the mode argument carries KDO_INT32
- *     (the paper's int1 / int2 data, Table 1 and Sec. 5): then they are int32,
- *     ordered as integers, and box extents are exact 64-bit differences.  The
- *     clipped-domain rule is float-only here (its planes clip a float box);
- *     int32 with it is refused as an invalid argument;
+ *     (the paper's int1 / int2 data, Table 1 and Sec. 5) or KDO_UINT32
+ *     (another scalar type of the templated builder, Sec. 7.2): then they
+ *     are int32 or uint32, ordered as signed or unsigned integers, and box
+ *     extents are exact 64-bit differences.  The clipped-domain rule is
+ *     float-only here (its planes clip a float box); an integer type with it,
+ *     or both flags at once, is refused as an invalid argument;
  *   - the widest dimension is argmax over d of (hi[d] - lo[d]) computed in
  *     float32, scanned from d = 0 with a strict '>', so the lowest dimension
  *     wins ties; box corners are the smallest and largest coordinate under
@@ -59,14 +61,15 @@
 
 enum { KDO_OK = 0, KDO_INVALID = 1, KDO_NOMEM = 2, KDO_NAN = 4, KDO_NOT_KD = 6 };
 enum { KDO_ROUND_ROBIN = 0, KDO_WIDEST = 1, KDO_WIDEST_TIGHT = 2 };
-enum { KDO_INT32 = 0x100 }; /* flag in the mode argument: int32 coordinates */
+/* flags in the mode argument: int32 or uint32 coordinates */
+enum { KDO_INT32 = 0x100, KDO_UINT32 = 0x200 };
 #define KDO_MAXK 8
 
 typedef struct {
   const unsigned char* base; /* first record */
   int64_t stride;            /* bytes between records */
   int k;                     /* coordinates per record (4-byte items at offsets 0,4,..) */
-  int ints;                  /* 1: int32 coordinates, 0: float32 */
+  int ints;                  /* 0: float32, 1: int32, 2: uint32 coordinates */
 } pointset;
 
 static float coord(const pointset* P, int64_t i, int d) {
@@ -75,10 +78,20 @@ static float coord(const pointset* P, int64_t i, int d) {
   return v;
 }
 
-static int32_t icoord(const pointset* P, int64_t i, int d) {
+/* An integer coordinate as a 64-bit value: int32 or uint32 by the type. */
+static int64_t icoord(const pointset* P, int64_t i, int d) {
+  if (P->ints == 2) {
+    uint32_t u;
+    memcpy(&u, P->base + i * P->stride + 4 * (int64_t)d, sizeof u);
+    return (int64_t)u;
+  }
   int32_t v;
   memcpy(&v, P->base + i * P->stride + 4 * (int64_t)d, sizeof v);
-  return v;
+  return (int64_t)v;
+}
+
+static int coord_type(int mode) {
+  return (mode & KDO_INT32) ? 1 : ((mode & KDO_UINT32) ? 2 : 0);
 }
 
 /* Strict total order on (value, original index); -0.0 < +0.0.  Returns <0,
@@ -95,10 +108,10 @@ static int cmp_key(float a, int64_t ia, float b, int64_t ib) {
 }
 
 /* Strict total order of records a and b in dimension d: by coordinate (as
- * float32 with -0 < +0, or as int32), then by original index. */
+ * float32 with -0 < +0, or as int32 / uint32), then by original index. */
 static int cmp_rec(const pointset* P, int64_t a, int64_t b, int d) {
   if (P->ints) {
-    int32_t x = icoord(P, a, d), y = icoord(P, b, d);
+    int64_t x = icoord(P, a, d), y = icoord(P, b, d);
     if (x != y) return x < y ? -1 : 1;
     return a < b ? -1 : (a > b ? 1 : 0);
   }
@@ -178,7 +191,7 @@ static void tight_box(const pointset* P, const int64_t* S, int64_t n, float* lo,
 }
 
 /* Widest side of the tight box of S[0..n): float32 extents as widest_dim,
- * or for int32 coordinates the exact 64-bit extents max - min, scanned the
+ * or for integer coordinates the exact 64-bit extents max - min, scanned the
  * same way (strict '>' from d = 0). */
 static int tight_widest(const pointset* P, const int64_t* S, int64_t n) {
   if (!P->ints) {
@@ -189,13 +202,13 @@ static int tight_widest(const pointset* P, const int64_t* S, int64_t n) {
   int best = 0;
   int64_t bestExt = 0;
   for (int d = 0; d < P->k; ++d) {
-    int32_t l = icoord(P, S[0], d), h = l;
+    int64_t l = icoord(P, S[0], d), h = l;
     for (int64_t i = 1; i < n; ++i) {
-      int32_t v = icoord(P, S[i], d);
+      int64_t v = icoord(P, S[i], d);
       if (v < l) l = v;
       if (v > h) h = v;
     }
-    int64_t e = (int64_t)h - (int64_t)l;
+    int64_t e = h - l;
     if (d == 0 || e > bestExt) { bestExt = e; best = d; }
   }
   return best;
@@ -239,10 +252,11 @@ static int check_args(const void* points, int64_t N, int k, int stride, int mode
   if (N < 0 || N > 2147483647LL) return KDO_INVALID;
   if (k < 1 || k > KDO_MAXK) return KDO_INVALID;
   if (stride < 4 * k || (stride % 4) != 0) return KDO_INVALID;
-  if (mode & ~(0xFF | KDO_INT32)) return KDO_INVALID;
+  if (mode & ~(0xFF | KDO_INT32 | KDO_UINT32)) return KDO_INVALID;
+  if ((mode & KDO_INT32) && (mode & KDO_UINT32)) return KDO_INVALID;
   int split = mode & 0xFF;
   if (split != KDO_ROUND_ROBIN && split != KDO_WIDEST && split != KDO_WIDEST_TIGHT) return KDO_INVALID;
-  if ((mode & KDO_INT32) && split == KDO_WIDEST) return KDO_INVALID;
+  if ((mode & (KDO_INT32 | KDO_UINT32)) && split == KDO_WIDEST) return KDO_INVALID;
   if (N > 0 && points == NULL) return KDO_INVALID;
   return KDO_OK;
 }
@@ -263,7 +277,7 @@ int kdo_build(const void* points, int64_t N, int k, int stride, int mode,
   int rc = check_args(points, N, k, stride, mode);
   if (rc) return rc;
   if (N == 0) return KDO_OK;
-  pointset P = {(const unsigned char*)points, stride, k, (mode & KDO_INT32) != 0};
+  pointset P = {(const unsigned char*)points, stride, k, coord_type(mode)};
   mode &= 0xFF;
   if (has_nan(&P, N)) return KDO_NAN;
   int64_t* S = (int64_t*)malloc((size_t)N * sizeof *S);
@@ -307,8 +321,8 @@ int kdo_check(const void* in_points, const void* out_points, const int32_t* orig
   if (first_bad) *first_bad = -1;
   if (rc) return rc;
   if (N == 0) return KDO_OK;
-  pointset In = {(const unsigned char*)in_points, stride, k, (mode & KDO_INT32) != 0};
-  pointset Out = {(const unsigned char*)out_points, stride, k, (mode & KDO_INT32) != 0};
+  pointset In = {(const unsigned char*)in_points, stride, k, coord_type(mode)};
+  pointset Out = {(const unsigned char*)out_points, stride, k, coord_type(mode)};
   mode &= 0xFF;
   unsigned char* seen = (unsigned char*)calloc((size_t)N, 1);
   unsigned char* dim = (unsigned char*)malloc((size_t)N);
@@ -368,7 +382,7 @@ int kdo_check(const void* in_points, const void* out_points, const int32_t* orig
         /* the strict order on (coordinate, original index) of the two nodes */
         int c;
         if (Out.ints) {
-          int32_t xi = icoord(&Out, i, d), xp = icoord(&Out, p, d);
+          int64_t xi = icoord(&Out, i, d), xp = icoord(&Out, p, d);
           c = xi != xp ? (xi < xp ? -1 : 1) : (orig[i] < orig[p] ? -1 : (orig[i] > orig[p] ? 1 : 0));
         } else {
           c = cmp_key(coord(&Out, i, d), orig[i], coord(&Out, p, d), orig[p]);
@@ -427,7 +441,7 @@ int kdo_node(const void* points, int64_t N, int k, int stride, int mode, int64_t
   int rc = check_args(points, N, k, stride, mode);
   if (rc) return rc;
   if (node < 0 || node >= N || !out_orig) return KDO_INVALID;
-  pointset P = {(const unsigned char*)points, stride, k, (mode & KDO_INT32) != 0};
+  pointset P = {(const unsigned char*)points, stride, k, coord_type(mode)};
   mode &= 0xFF;
   if (has_nan(&P, N)) return KDO_NAN;
   int64_t* S = (int64_t*)malloc((size_t)N * sizeof *S);

@@ -9,8 +9,9 @@ called from the build step) and exposes numpy-level functions.
 Records are passed as 2-D C-contiguous numpy arrays with 4-byte items (one row
 per record, row bytes = stride); the first ``k`` columns are the coordinates
 and any further columns are payload that is moved, never compared.  An int32
-array has int32 coordinates (the oracle's INT32 mode flag is set from the
-dtype); any other 4-byte dtype is read as float32.
+or uint32 array has int32 or uint32 coordinates (the oracle's INT32 / UINT32
+mode flag is set from the dtype unless the mode already carries one); any
+other 4-byte dtype is read as float32.
 """
 from __future__ import annotations
 
@@ -25,6 +26,7 @@ ROUND_ROBIN = 0
 WIDEST = 1
 WIDEST_TIGHT = 2  # widest side of the subtree's own (tight) bounding box
 INT32 = 0x100     # mode flag: int32 coordinates
+UINT32 = 0x200    # mode flag: uint32 coordinates
 
 OK = 0
 INVALID = 1
@@ -77,7 +79,9 @@ def _records(points: np.ndarray) -> np.ndarray:
 
 
 def _mode(points: np.ndarray, mode: int) -> int:
-    return mode | (INT32 if points.dtype == np.int32 else 0)
+    if mode & (INT32 | UINT32):
+        return mode
+    return mode | {np.dtype(np.int32): INT32, np.dtype(np.uint32): UINT32}.get(points.dtype, 0)
 
 
 class OracleError(RuntimeError):

@@ -180,7 +180,7 @@ struct Plan {
   std::vector<SetInfo> sets;
   uint32_t total = 0;
   int k = 0, stride = 0, mode = 0;  // mode: the split rule (low byte of the mode argument)
-  bool ints = false;                // int32 coordinates (KDB_COORDS_INT32)
+  int ctype = kCoordF32;            // coordinate type (KDB_COORDS_INT32 / UINT32)
   int Lmax = 0;        // most levels of any set
   int rb = 0;          // bits of a rank
   int set_bits = 0;    // bits of a set id in the rank-sort keys (0 for one set)
@@ -416,17 +416,19 @@ kdb_status check_common(int64_t n, int k, int stride) {
   return KDB_OK;
 }
 
-// The mode argument: a split rule in the low byte, optionally OR'ed with
-// KDB_COORDS_INT32.
+// The mode argument: a split rule in the low byte, optionally OR'ed with one
+// of KDB_COORDS_INT32 / KDB_COORDS_UINT32.
 kdb_status check_mode(kdb_split_mode mode) {
   const int m = (int)mode;
-  if (m & ~(0xFF | KDB_COORDS_INT32)) return KDB_ERR_INVALID_ARGUMENT;
+  if (m & ~(0xFF | KDB_COORDS_INT32 | KDB_COORDS_UINT32)) return KDB_ERR_INVALID_ARGUMENT;
+  if ((m & KDB_COORDS_INT32) && (m & KDB_COORDS_UINT32)) return KDB_ERR_INVALID_ARGUMENT;
   const int split = m & 0xFF;
   if (split != KDB_SPLIT_ROUND_ROBIN && split != KDB_SPLIT_WIDEST_EXTENT &&
       split != KDB_SPLIT_WIDEST_TIGHT)
     return KDB_ERR_INVALID_ARGUMENT;
   // the clipped-domain rule clips float boxes: float32 coordinates only
-  if ((m & KDB_COORDS_INT32) && split == KDB_SPLIT_WIDEST_EXTENT) return KDB_ERR_INVALID_ARGUMENT;
+  if ((m & (KDB_COORDS_INT32 | KDB_COORDS_UINT32)) && split == KDB_SPLIT_WIDEST_EXTENT)
+    return KDB_ERR_INVALID_ARGUMENT;
   return KDB_OK;
 }
 // The tight-box rule runs on the presorted lists only (k <= 3).
@@ -435,7 +437,9 @@ kdb_status check_mode_k(kdb_split_mode mode, int k) {
   return ((int)mode & 0xFF) == KDB_SPLIT_WIDEST_TIGHT && k > 3 ? KDB_ERR_INVALID_ARGUMENT : KDB_OK;
 }
 inline int split_of(int mode) { return mode & 0xFF; }
-inline bool ints_of(int mode) { return (mode & KDB_COORDS_INT32) != 0; }
+inline int ctype_of(int mode) {
+  return (mode & KDB_COORDS_INT32) ? kCoordI32 : ((mode & KDB_COORDS_UINT32) ? kCoordU32 : kCoordF32);
+}
 
 #define KDB_CK(call)                      \
   do {                                    \
@@ -577,7 +581,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   }
   pa.bbox = bydim ? bbox : nullptr;  // the root's domain and its tight box alike
   pa.err = err;
-  pa.ints = P.ints;
+  pa.ctype = P.ctype;
   {
     Prof pf(K_PREPASS, P.use_lists ? (double)T * (4.0 * k + 16.0) : (double)T * k * (4.0 + (multi ? 8 : 4)),
             feed ? feed->chunks : 1, st);
@@ -674,7 +678,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   {
     Prof pf(K_WIDEST, 0.0, 1, st);
     KDB_CK(launch_widest_root(d_sets, d_act + P.act_off[0], (uint32_t)P.act[0].size(), bbox, k,
-                              widest ? boxA : nullptr, dims, P.ints, st));
+                              widest ? boxA : nullptr, dims, P.ctype, st));
   }
   const uint32_t* vals_cur = nullptr;  // level 0: original order
   uint4* lcur[3] = {nullptr, nullptr, nullptr};
@@ -824,7 +828,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       pv.mode = P.mode;
       pv.pts_out = direct ? pts : nullptr;
       pv.stride = P.stride;
-      pv.ints = P.ints;
+      pv.ctype = P.ctype;
       {
         Prof pf(K_PIVOT, (double)(x.nact << l) * 20, 1, st);
         KDB_CK(launch_pivots(pv, st));
@@ -841,7 +845,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
         ta.items_next = P.items[l + 1];
         ta.dims = dims;
         ta.k = k;
-        ta.ints = P.ints;
+        ta.ctype = P.ctype;
         Prof pf(K_WIDEST, (double)(x.nact << (l + 1)) * (2.0 * 16 * k + 1), 1, st);
         KDB_CK(launch_tight_children(ta, st));
       }
@@ -973,7 +977,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     la.err = err;
     la.lents = lents;
     la.pts_out = direct ? pts : nullptr;
-    la.ints = P.ints;
+    la.ctype = P.ctype;
     Prof pf(K_LOCAL, (double)T * (4.0 + 4.0 * k + 4.0), 1, st);
     KDB_CK(launch_local_finish(la, st));
   }
@@ -993,7 +997,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   if (direct) {
     // every record is at its node already; put the input back if the build failed
     Prof pf(K_PLACEMENT, 0.0, 1, st);
-    KDB_CK(launch_restore(pts, ents0, T, k, err, P.ints, st));
+    KDB_CK(launch_restore(pts, ents0, T, k, err, P.ctype, st));
   } else if (placement == KDB_PLACEMENT_AUTO && (size_t)T * P.stride <= P.gather_bytes) {
     Prof pf(K_PLACEMENT, (double)T * (4.0 + 4.0 * P.stride), 2, st);
     KDB_CK(launch_place_gather(pm, at<unsigned char>(ws, P.o_gather), sms, st));
@@ -1275,7 +1279,7 @@ kdb_status kdb_autotune(const void* d_points, int64_t n, int k, int stride_bytes
   P.k = k;
   P.stride = stride_bytes;
   P.mode = split_of(mode);
-  P.ints = ints_of(mode);
+  P.ctype = ctype_of(mode);
   make_plan(P);
   if (P.too_wide) return KDB_ERR_INVALID_ARGUMENT;
   int dev, sms;
@@ -1353,7 +1357,7 @@ size_t kdb_workspace_size(int64_t n, int k, int stride_bytes, kdb_split_mode mod
   P.k = k;
   P.stride = stride_bytes;
   P.mode = split_of(mode);
-  P.ints = ints_of(mode);
+  P.ctype = ctype_of(mode);
   make_plan(P);
   return P.bytes;
 }
@@ -1382,7 +1386,7 @@ kdb_status kdb_build_ex(void* d_points, int64_t n, int k, int stride_bytes, kdb_
   P.k = k;
   P.stride = stride_bytes;
   P.mode = split_of(mode);
-  P.ints = ints_of(mode);
+  P.ctype = ctype_of(mode);
   return run(P, static_cast<unsigned char*>(d_points), d_workspace, workspace_bytes,
              d_out_orig_index, d_out_split_dim, st);
 }
@@ -1406,7 +1410,7 @@ kdb_status kdb_build_noalloc(void* d_points, int64_t n, int k, int stride_bytes,
   P.k = k;
   P.stride = stride_bytes;
   P.mode = split_of(mode);
-  P.ints = ints_of(mode);
+  P.ctype = ctype_of(mode);
   make_plan(P);
   if (P.too_wide || P.bytes > KDB_NOALLOC_SCRATCH_BYTES) return KDB_ERR_INVALID_ARGUMENT;
   int dev = 0;
@@ -1450,7 +1454,7 @@ kdb_status kdb_build_batched(void* d_points, const int64_t* h_offsets, int num_s
   P.k = k;
   P.stride = stride_bytes;
   P.mode = split_of(mode);
-  P.ints = ints_of(mode);
+  P.ctype = ctype_of(mode);
   return run(P, static_cast<unsigned char*>(d_points), nullptr, 0, nullptr, nullptr,
              reinterpret_cast<cudaStream_t>(stream));
 }
@@ -1475,7 +1479,7 @@ kdb_status batched_sets(Plan& P, const int64_t* h_offsets, int num_sets, int k, 
   P.k = k;
   P.stride = stride_bytes;
   P.mode = split_of(mode);
-  P.ints = ints_of(mode);
+  P.ctype = ctype_of(mode);
   return KDB_OK;
 }
 }  // namespace
@@ -1551,7 +1555,7 @@ kdb_status kdb_plan_create(const int64_t* h_offsets, int num_sets, int k, int st
   P.k = k;
   P.stride = stride_bytes;
   P.mode = split_of(mode);
-  P.ints = ints_of(mode);
+  P.ctype = ctype_of(mode);
   po->trivial = total <= 1;
   if (po->trivial) {
     *out_plan = reinterpret_cast<kdb_plan>(po);
@@ -1655,7 +1659,7 @@ kdb_status kdb_build_host(void* h_points, int64_t n, int k, int stride_bytes, kd
   P.k = k;
   P.stride = stride_bytes;
   P.mode = split_of(mode);
-  P.ints = ints_of(mode);
+  P.ctype = ctype_of(mode);
   make_plan(P);
   if (P.too_wide) return KDB_ERR_INVALID_ARGUMENT;
   // Records without payload in page-locked memory that this device can
@@ -1742,7 +1746,7 @@ kdb_status kdb_validate(const void* d_points, int64_t n, int k, int stride_bytes
   const uint32_t N = (uint32_t)n;
   const bool widest = split_of(mode) == KDB_SPLIT_WIDEST_EXTENT;
   const bool tight = split_of(mode) == KDB_SPLIT_WIDEST_TIGHT;
-  const bool ints = ints_of(mode);
+  const int ctype = ctype_of(mode);
   const int L = num_levels(N);
   // single-set tables for the dimension pass (widest mode)
   std::vector<ActiveEntry> act(std::max(1, L - 1));
@@ -1825,7 +1829,7 @@ kdb_status kdb_validate(const void* d_points, int64_t n, int k, int stride_bytes
     if (tight) {
       dims = at<uint8_t>(ws, o_dims);
       if (launch_tight_validate_dims(static_cast<const unsigned char*>(d_points), N, k, stride_bytes,
-                                     at<uint32_t>(ws, o_tbox), dims, ints, st) != cudaSuccess) {
+                                     at<uint32_t>(ws, o_tbox), dims, ctype, st) != cudaSuccess) {
         result = KDB_ERR_CUDA;
         break;
       }

@@ -142,33 +142,37 @@ __host__ __device__ inline uint32_t float_key(uint32_t bits) {
 __host__ __device__ inline uint32_t key_to_float_bits(uint32_t key) {
   return key ^ ((key & 0x80000000u) ? 0x80000000u : 0xFFFFFFFFu);
 }
-// int32 coordinates: two's complement order is the unsigned order of the
-// bits with the sign bit flipped.
-__host__ __device__ inline uint32_t coord_key(uint32_t bits, bool ints) {
-  return ints ? bits ^ 0x80000000u : float_key(bits);
+// Coordinate types (the mode argument's KDB_COORDS_* flag): float32, int32,
+// uint32.  int32: two's complement order is the unsigned order of the bits
+// with the sign bit flipped; uint32: the bits are the key.
+enum : int { kCoordF32 = 0, kCoordI32 = 1, kCoordU32 = 2 };
+__host__ __device__ inline uint32_t coord_key(uint32_t bits, int ctype) {
+  return ctype == kCoordF32 ? float_key(bits) : (ctype == kCoordI32 ? bits ^ 0x80000000u : bits);
 }
-__host__ __device__ inline uint32_t key_to_coord_bits(uint32_t key, bool ints) {
-  return ints ? key ^ 0x80000000u : key_to_float_bits(key);
+__host__ __device__ inline uint32_t key_to_coord_bits(uint32_t key, int ctype) {
+  return ctype == kCoordF32 ? key_to_float_bits(key) : (ctype == kCoordI32 ? key ^ 0x80000000u : key);
 }
 #ifdef __CUDACC__
 // The record of a point from its entry (k <= 3 coordinate keys, no payload):
 // the key map is a bijection, so the bits are the input's.
-__device__ inline void write_record_from_entry(unsigned char* rec, const uint4& e, int k, bool ints) {
+__device__ inline void write_record_from_entry(unsigned char* rec, const uint4& e, int k, int ctype) {
   uint32_t* r = reinterpret_cast<uint32_t*>(rec);
-  r[0] = key_to_coord_bits(e.x, ints);
-  if (k > 1) r[1] = key_to_coord_bits(e.y, ints);
-  if (k > 2) r[2] = key_to_coord_bits(e.z, ints);
+  r[0] = key_to_coord_bits(e.x, ctype);
+  if (k > 1) r[1] = key_to_coord_bits(e.y, ctype);
+  if (k > 2) r[2] = key_to_coord_bits(e.z, ctype);
 }
 // Widest side of a box whose corners are coordinate keys: float32 extents
-// hi - lo (round to nearest, no contraction) or, for int32 coordinates, exact
-// 64-bit differences; scanned from d = 0 with a strict '>', so the lowest
+// hi - lo (round to nearest, no contraction) or, for integer coordinates,
+// exact 64-bit differences (of the keys, which differ by what the values
+// differ by: both integer key maps add a constant modulo 2^32 and keep the
+// order); scanned from d = 0 with a strict '>', so the lowest
 // dimension wins ties (an extent that is NaN, inf - inf, never wins).
-__device__ inline int widest_of_keys(const uint32_t* lo, const uint32_t* hi, int k, bool ints) {
+__device__ inline int widest_of_keys(const uint32_t* lo, const uint32_t* hi, int k, int ctype) {
   int best = 0;
-  if (ints) {
+  if (ctype != kCoordF32) {
     int64_t be = 0;
     for (int d = 0; d < k; ++d) {
-      const int64_t e = (int64_t)(int32_t)(hi[d] ^ 0x80000000u) - (int64_t)(int32_t)(lo[d] ^ 0x80000000u);
+      const int64_t e = (int64_t)hi[d] - (int64_t)lo[d];
       if (d == 0 || e > be) {
         be = e;
         best = d;

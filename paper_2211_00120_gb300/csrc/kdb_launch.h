@@ -77,7 +77,7 @@ struct PivotArgs {
   int k, mode;
   unsigned char* pts_out;   // records written directly at their nodes (stride = 4k), or nullptr
   int stride;
-  bool ints;                // int32 coordinates
+  int ctype;                // coordinate type (kCoordF32 / I32 / U32)
 };
 // Tight-box split rule: split dimension of every subtree of level l + 1 of
 // the sets that stay on the global levels, from their first and last entries
@@ -88,7 +88,7 @@ struct TightArgs {
   uint32_t items_next;      // items of level l + 1
   uint8_t* dims;
   int k;
-  bool ints;                // int32 coordinates: exact extents
+  int ctype;                // coordinate type: integers have exact extents
 };
 cudaError_t launch_tight_children(const TightArgs& a, cudaStream_t st);
 // One partition pass advances a list by 1..kLiftMax levels at once.
@@ -165,7 +165,7 @@ struct LocalArgs {
   uint32_t* perm;
   uint32_t* err;
   unsigned char* pts_out;    // records written directly at their nodes (stride = 4k), or nullptr
-  bool ints;                 // int32 coordinates
+  int ctype;                 // coordinate type (kCoordF32 / I32 / U32)
 };
 size_t local_smem_bytes(int k);
 cudaError_t launch_local_finish(const LocalArgs& a, cudaStream_t st);
@@ -221,7 +221,7 @@ struct PrepassArgs {
   int passes;
   uint32_t* bbox;       // nsets * 2k (min keys, then max keys) or nullptr
   uint32_t* err;
-  bool ints;            // int32 coordinates (else float32)
+  int ctype;            // coordinate type (kCoordF32 / I32 / U32)
   uint32_t beg, end;    // records [beg, end) of this launch (end = 0: all of them)
 };
 cudaError_t launch_prepass(const PrepassArgs& a, int num_sms, cudaStream_t st);
@@ -273,12 +273,12 @@ struct WidestArgs {
   const LocalSet* lsets;   // their slots (nullptr: no local finish)
 };
 cudaError_t launch_widest_root(const SetInfo* sets, const ActiveEntry* act0, uint32_t nact,
-                               const uint32_t* bbox, int k, float* boxes0, uint8_t* dims, bool ints,
+                               const uint32_t* bbox, int k, float* boxes0, uint8_t* dims, int ctype,
                                cudaStream_t st);
 cudaError_t launch_widest_children(const WidestArgs& a, cudaStream_t st);
 // validator, tight-box rule: per-node subtree boxes (n x 2k keys) and dims
 cudaError_t launch_tight_validate_dims(const unsigned char* pts, uint32_t n, int k, int stride,
-                                       uint32_t* box, uint8_t* dims, bool ints, cudaStream_t st);
+                                       uint32_t* box, uint8_t* dims, int ctype, cudaStream_t st);
 cudaError_t launch_rr_dims(uint8_t* dims, const SetInfo* sets, uint32_t nsets, uint32_t total,
                            int k, cudaStream_t st);
 
@@ -298,7 +298,7 @@ cudaError_t launch_place_gather(const PermuteArgs& a, unsigned char* tmp, int nu
 // Records of stride 4k rebuilt from their entries (input order) if the build
 // failed after writing records directly at their nodes.
 cudaError_t launch_restore(unsigned char* pts, const uint4* ents, uint32_t total, int k, const uint32_t* err,
-                           bool ints, cudaStream_t st);
+                           int ctype, cudaStream_t st);
 cudaError_t launch_init_bbox(uint32_t* bbox, uint32_t nsets, int k, cudaStream_t st);
 cudaError_t launch_unmark(const uint32_t* perm, int32_t* out, uint32_t total, cudaStream_t st);
 

@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
       lo[d] = d == 0 ? e0.x : (d == 1 ? e0.y : e0.z);
       hi[d] = d == 0 ? e1.x : (d == 1 ? e1.y : e1.z);
     }
-    return widest_of_keys(lo, hi, k, a.ints);
+    return widest_of_keys(lo, hi, k, a.ctype);
   };
   // per depth jj below the block's root (level l0 + jj): the block's layout,
   // the round-robin split dimension and the lists read on deeper levels,
@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
         a.perm[node] = o;
         if (ent_of) {  // the record goes straight to its node
           const uint4 e = ent_of[it];
-          write_record_from_entry(a.pts_out + (uint64_t)node * a.stride, e, k, a.ints);
+          write_record_from_entry(a.pts_out + (uint64_t)node * a.stride, e, k, a.ctype);
           if (widest)
             s_lplane[dbase + tl] =
                 __uint_as_float(key_to_float_bits(d == 0 ? e.x : (d == 1 ? e.y : e.z)));

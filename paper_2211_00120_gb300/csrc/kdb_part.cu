@@ -56,7 +56,7 @@ __global__ void pivot_kernel(PivotArgs a) {
   const uint4 ent = a.lists[d][pos];
   a.piv[gid] = make_uint2(comp(ent, d), ent.w);
   a.perm[si.off + node] = ent.w;
-  if (a.pts_out) write_record_from_entry(a.pts_out + (uint64_t)(si.off + node) * a.stride, ent, a.k, a.ints);
+  if (a.pts_out) write_record_from_entry(a.pts_out + (uint64_t)(si.off + node) * a.stride, ent, a.k, a.ctype);
 }
 
 // ---------------------------------------------------------------------------
@@ -65,7 +65,7 @@ __global__ void pivot_kernel(PivotArgs a) {
 // (subtree, key_d, index), so the subtree's smallest and largest key_d are
 // its first and last entries: the per-subtree min/max reduction costs two
 // reads per dimension.  Extent arithmetic as for the clipped domain: float32
-// hi - lo (exact differences for int32 coordinates), strict '>' from d = 0.
+// hi - lo (exact differences for integer coordinates), strict '>' from d = 0.
 __global__ void tight_children_kernel(TightArgs a) {
   const LevelCtx& x = a.x;
   const int lc = x.l + 1;
@@ -91,7 +91,7 @@ __global__ void tight_children_kernel(TightArgs a) {
     lo[d] = comp(a.lists[d][first], d);
     hi[d] = comp(a.lists[d][end - 1], d);
   }
-  a.dims[si.off + node] = (uint8_t)widest_of_keys(lo, hi, a.k, a.ints);
+  a.dims[si.off + node] = (uint8_t)widest_of_keys(lo, hi, a.k, a.ctype);
 }
 
 // ---------------------------------------------------------------------------

@@ -411,7 +411,8 @@ kdb_status kdb_server_submit(kdb_server srv, const void* h_points, void* h_out, 
   if (!srv || !out_id) return KDB_ERR_INVALID_ARGUMENT;
   Server& S = srv->s;
   if (n < 0 || n > 2147483647LL || k < 1 || k > 8 || stride_bytes < 4 * k || stride_bytes % 4 ||
-      ((int)mode & ~(0xFF | KDB_COORDS_INT32)) != 0 || (n > 0 && !h_points))
+      ((int)mode & ~(0xFF | KDB_COORDS_INT32 | KDB_COORDS_UINT32)) != 0 ||
+      (((int)mode & KDB_COORDS_INT32) && ((int)mode & KDB_COORDS_UINT32)) || (n > 0 && !h_points))
     return KDB_ERR_INVALID_ARGUMENT;
   Req r;
   r.h_in = static_cast<const unsigned char*>(h_points);

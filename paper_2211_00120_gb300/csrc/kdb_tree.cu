@@ -106,8 +106,8 @@ __global__ void __launch_bounds__(kThreads) prepass_kernel(PrepassArgs a) {
       uint32_t key = 0;
       if (ok) {
         const uint32_t bits = *reinterpret_cast<const uint32_t*>(rec + 4 * d);
-        if (!a.ints && (bits & 0x7FFFFFFFu) > 0x7F800000u) nan = true;
-        key = coord_key(bits, a.ints);
+        if (!a.ctype && (bits & 0x7FFFFFFFu) > 0x7F800000u) nan = true;
+        key = coord_key(bits, a.ctype);
         if (d < 3) ek[d] = key;
         lo[d] = min(lo[d], key);
         hi[d] = max(hi[d], key);
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kThreads) seg_level_keys_kernel(SegKeyArgs a) 
 // its node's domain).  Split dimension = widest side (hi - lo in float32,
 // first dimension wins ties).
 __global__ void widest_root_kernel(const SetInfo* sets, const ActiveEntry* act, uint32_t nact,
-                                   const uint32_t* bbox, int k, float* boxes, uint8_t* dims, bool ints) {
+                                   const uint32_t* bbox, int k, float* boxes, uint8_t* dims, int ctype) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nact) return;
   const ActiveEntry e = act[i];
@@ -286,7 +286,7 @@ __global__ void widest_root_kernel(const SetInfo* sets, const ActiveEntry* act, 
       boxes[(uint64_t)e.box0 * 2 * k + d] = __uint_as_float(key_to_float_bits(lo[d]));
       boxes[(uint64_t)e.box0 * 2 * k + k + d] = __uint_as_float(key_to_float_bits(hi[d]));
     }
-  dims[sets[e.set].off] = (uint8_t)widest_of_keys(lo, hi, k, ints);
+  dims[sets[e.set].off] = (uint8_t)widest_of_keys(lo, hi, k, ctype);
 }
 
 __global__ void widest_children_kernel(WidestArgs a) {
@@ -521,10 +521,10 @@ __global__ void place_copy_back_kernel(PermuteArgs a, const unsigned char* tmp, 
 // After a failed build that wrote records at their nodes: put every record
 // back from its entry, so the caller's array is as it was.
 __global__ void restore_kernel(unsigned char* pts, const uint4* ents, uint32_t total, int k,
-                               const uint32_t* err, bool ints) {
+                               const uint32_t* err, int ctype) {
   if (*reinterpret_cast<const volatile uint32_t*>(err) == 0) return;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
-    write_record_from_entry(pts + (uint64_t)i * (4 * k), ents[i], k, ints);
+    write_record_from_entry(pts + (uint64_t)i * (4 * k), ents[i], k, ctype);
 }
 
 // Scene-box accumulators of every set: lower keys at the top, upper at zero.
@@ -547,12 +547,12 @@ __global__ void unmark_kernel(const uint32_t* perm, int32_t* out, uint32_t total
 // (keys, so that min / max follow the strict order); the node's dimension is
 // the widest side of that box.
 __global__ void tight_box_level_kernel(const unsigned char* pts, uint32_t n, int k, int stride, int l,
-                                       uint32_t* box, uint8_t* dims, bool ints) {
+                                       uint32_t* box, uint8_t* dims, int ctype) {
   const uint64_t i = (uint64_t)full_nodes(l) + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i >= n || i >= (uint64_t)full_nodes(l + 1)) return;
   uint32_t lo[kMaxK], hi[kMaxK];
   for (int d = 0; d < k; ++d)
-    lo[d] = hi[d] = coord_key(__float_as_uint(coord_of(pts, (uint32_t)i, stride, d)), ints);
+    lo[d] = hi[d] = coord_key(__float_as_uint(coord_of(pts, (uint32_t)i, stride, d)), ctype);
   for (uint64_t c = 2 * i + 1; c <= 2 * i + 2 && c < n; ++c)
     for (int d = 0; d < k; ++d) {
       lo[d] = min(lo[d], box[c * 2 * k + d]);
@@ -562,7 +562,7 @@ __global__ void tight_box_level_kernel(const unsigned char* pts, uint32_t n, int
     box[i * 2 * k + d] = lo[d];
     box[i * 2 * k + k + d] = hi[d];
   }
-  dims[i] = (uint8_t)widest_of_keys(lo, hi, k, ints);
+  dims[i] = (uint8_t)widest_of_keys(lo, hi, k, ctype);
 }
 
 __global__ void validate_kernel(const unsigned char* pts, uint32_t n, int k, int stride, int mode,
@@ -571,11 +571,11 @@ __global__ void validate_kernel(const unsigned char* pts, uint32_t n, int k, int
   if (i == 0 || i >= n) return;
   uint32_t child = i;
   uint32_t p = (i - 1) / 2;
-  const bool ints = (mode & 0x100) != 0;  // int32 coordinates
+  const int ctype = (mode & 0x100) ? kCoordI32 : ((mode & 0x200) ? kCoordU32 : kCoordF32);
   for (;;) {
     const int d = (mode & 0xFF) == 0 ? level_of(p) % k : dims[p];
-    const uint32_t ki = coord_key(__float_as_uint(coord_of(pts, i, stride, d)), ints);
-    const uint32_t kp = coord_key(__float_as_uint(coord_of(pts, p, stride, d)), ints);
+    const uint32_t ki = coord_key(__float_as_uint(coord_of(pts, i, stride, d)), ctype);
+    const uint32_t kp = coord_key(__float_as_uint(coord_of(pts, p, stride, d)), ctype);
     const bool left = child == 2 * p + 1;
     if ((left && ki > kp) || (!left && ki < kp)) {
       atomicMin(first_bad, i);
@@ -619,20 +619,20 @@ cudaError_t launch_seg_level_keys(const SegKeyArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_widest_root(const SetInfo* sets, const ActiveEntry* act0, uint32_t nact,
-                               const uint32_t* bbox, int k, float* boxes0, uint8_t* dims, bool ints,
+                               const uint32_t* bbox, int k, float* boxes0, uint8_t* dims, int ctype,
                                cudaStream_t st) {
   if (nact == 0) return cudaSuccess;
-  widest_root_kernel<<<(nact + 127) / 128, 128, 0, st>>>(sets, act0, nact, bbox, k, boxes0, dims, ints);
+  widest_root_kernel<<<(nact + 127) / 128, 128, 0, st>>>(sets, act0, nact, bbox, k, boxes0, dims, ctype);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tight_validate_dims(const unsigned char* pts, uint32_t n, int k, int stride,
-                                       uint32_t* box, uint8_t* dims, bool ints, cudaStream_t st) {
+                                       uint32_t* box, uint8_t* dims, int ctype, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   for (int l = num_levels(n) - 1; l >= 0; --l) {
     const uint32_t cnt = std::min<uint64_t>((uint64_t)n, (uint64_t)full_nodes(l + 1)) - full_nodes(l);
     tight_box_level_kernel<<<(cnt + kThreads - 1) / kThreads, kThreads, 0, st>>>(pts, n, k, stride, l,
-                                                                                   box, dims, ints);
+                                                                                   box, dims, ctype);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -679,11 +679,11 @@ cudaError_t launch_place_gather(const PermuteArgs& a, unsigned char* tmp, int nu
 }
 
 cudaError_t launch_restore(unsigned char* pts, const uint4* ents, uint32_t total, int k, const uint32_t* err,
-                           bool ints, cudaStream_t st) {
+                           int ctype, cudaStream_t st) {
   if (total == 0) return cudaSuccess;
   // a small grid: the kernel usually finds no error and returns at once
   const uint32_t grid = std::min<uint32_t>((total + kThreads - 1) / kThreads, 1024);
-  restore_kernel<<<grid, kThreads, 0, st>>>(pts, ents, total, k, err, ints);
+  restore_kernel<<<grid, kThreads, 0, st>>>(pts, ents, total, k, err, ctype);
   return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@ ROUND_ROBIN = 0
 WIDEST_EXTENT = 1
 WIDEST_TIGHT = 2  # widest side of the subtree's own bounding box (k <= 3)
 COORDS_INT32 = 0x100  # mode flag: int32 coordinates (set from an int32 tensor's dtype)
+COORDS_UINT32 = 0x200  # mode flag: uint32 coordinates (set from a uint32 tensor's dtype)
 
 OK = 0
 ERR_INVALID_ARGUMENT = 1
@@ -167,10 +168,18 @@ def _records(points):
 
 
 def _mode(points, mode: int) -> int:
-    """The mode argument: the split rule, plus COORDS_INT32 for int32 records."""
+    """The mode argument: the split rule, plus COORDS_INT32 / COORDS_UINT32 for
+    int32 / uint32 records unless the mode already names a coordinate type
+    (so that uint32 data can also be passed as an int32 view)."""
     import torch
 
-    return mode | (COORDS_INT32 if points.dtype == torch.int32 else 0)
+    if mode & (COORDS_INT32 | COORDS_UINT32):
+        return mode
+    if points.dtype == torch.int32:
+        return mode | COORDS_INT32
+    if points.dtype == getattr(torch, "uint32", None):
+        return mode | COORDS_UINT32
+    return mode
 
 
 def _check(rc: int, call: str):

@@ -140,3 +140,13 @@ def test_tuning_file_round_trip_and_refusals(lib, tmp_path):
         assert kdb.kdb_get_tuning() == (1, 0)
     finally:
         kdb.kdb_set_tuning(0, 0)
+
+
+def test_uint32_flag_and_its_refusals(lib):
+    assert kdb.COORDS_UINT32 == 0x200
+    # a valid combination sizes a workspace; both flags, or uint32 with the
+    # clipped-domain rule, are invalid (size 0)
+    assert lib.kdb_workspace_size(100000, 3, 12, kdb.ROUND_ROBIN | kdb.COORDS_UINT32) > 0
+    assert lib.kdb_workspace_size(100000, 3, 12, kdb.WIDEST_TIGHT | kdb.COORDS_UINT32) > 0
+    assert lib.kdb_workspace_size(100000, 3, 12, kdb.WIDEST_EXTENT | kdb.COORDS_UINT32) == 0
+    assert lib.kdb_workspace_size(100000, 3, 12, kdb.COORDS_UINT32 | kdb.COORDS_INT32) == 0

@@ -448,3 +448,89 @@ def test_int32_with_the_clipped_domain_rule_is_refused():
     with pytest.raises(oracle.OracleError) as e:
         oracle.build(synth_ints(10, 3, seed=1), 3, WIDEST)
     assert e.value.code == oracle.INVALID
+
+
+# ------------------------------------------------------ uint32 coordinates --
+UINT_EDGE = [0, 1, 2**24, 2**24 + 1, 2**31 - 1, 2**31, 2**31 + 1, 2**32 - 2, 2**32 - 1]
+
+
+def uint_points(rng, n, k):
+    """uint32 coordinates on both sides of 2^31, where reading the bits as
+    int32 would reverse the order."""
+    return np.array([[rng.choice(UINT_EDGE) for _ in range(k)] for _ in range(n)], dtype=np.uint32)
+
+
+@pytest.mark.parametrize("mode", [RR, TIGHT])
+def test_uint32_bruteforce_unique_valid_arrangement(mode):
+    rng = random.Random(8765 + mode)
+    for n in range(1, 8):
+        for _ in range(4 if n == 7 else 8):
+            k = rng.randint(1, 3)
+            pts = uint_points(rng, n, k)
+            valid = [p for p in itertools.permutations(range(n)) if is_valid(pts, p, k, mode)]
+            assert len(valid) == 1, (n, k, pts)
+            _, orig = oracle.build(pts, k, mode)
+            assert tuple(int(o) for o in orig) == valid[0]
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 100, 1000])
+def test_uint32_k1_is_sorted_array_in_level_order(n):
+    rng = random.Random(100 + n)
+    pts = uint_points(rng, n, 1)
+    ranked = sorted(range(n), key=lambda i: (int(pts[i, 0]), i))  # int() of a uint32 is unsigned
+    for mode in (RR, TIGHT):
+        assert list(oracle.build(pts, 1, mode)[1]) == eytzinger(ranked)
+
+
+@pytest.mark.parametrize("mode", [RR, TIGHT])
+def test_uint32_equals_int32_with_the_top_bit_flipped(mode):
+    """v -> v xor 2^31 maps the unsigned order of uint32 values onto the signed
+    order of the int32 results and keeps every difference, so both trees (and
+    both tight-box extents) agree."""
+    rng = np.random.default_rng(12)
+    u = rng.integers(0, 2**32, size=(3000, 3), dtype=np.uint64).astype(np.uint32)
+    u[::7, 1] = np.uint32(2**31)  # ties on the boundary
+    s = (u ^ np.uint32(0x80000000)).view(np.int32)
+    assert list(oracle.build(u, 3, mode)[1]) == list(oracle.build(s, 3, mode)[1])
+
+
+def test_uint32_tight_box_uses_unsigned_extents():
+    """Three 2-D points A = (0, 0), B = (2^31 + 5, 1), C = (1, 2^31).  Unsigned
+    extents: x spans 2^31 + 5, y spans 2^31, so the root splits in x, and the
+    root is the x-rank-1 point (the left subtree of N = 3 holds one point):
+    A < C < B in x, so C.  Read as int32, B's x and C's y are negative, y
+    would span more (2^31 + 1 against 2^31 - 4) and the root would be A."""
+    pts = np.array([[0, 0], [2**31 + 5, 1], [1, 2**31]], dtype=np.uint32)
+    _, orig = oracle.build(pts, 2, TIGHT)
+    assert list(orig) == [2, 0, 1]
+    _, orig_signed = oracle.build(pts.view(np.int32), 2, TIGHT)
+    assert orig_signed[0] == 0
+
+
+@pytest.mark.parametrize("mode", [RR, TIGHT])
+def test_uint32_emulator_matches_oracle_and_checker(mode):
+    rng = random.Random(77 + mode)
+    for _ in range(150):
+        n = rng.randint(1, 60)
+        k = rng.randint(1, 3)
+        pts = uint_points(rng, n, k) if rng.random() < 0.5 else \
+            np.array([[rng.randint(0, 60) for _ in range(k)] for _ in range(n)], np.uint32)
+        out, orig = oracle.build(pts, k, mode)
+        assert list(emulator.emulate(pts, k, mode)) == list(orig)
+        assert oracle.check(pts, out, orig, k, mode) == -1
+    # planted: the top bit of one coordinate flipped
+    pts = np.random.default_rng(3).integers(0, 2**32, size=(5000, 3), dtype=np.uint64).astype(np.uint32)
+    out, orig = oracle.build(pts, 3, mode)
+    o2 = out.copy()
+    o2[91, 0] ^= np.uint32(0x80000000)
+    assert oracle.check(pts, o2, orig, 3, mode) >= 0
+
+
+def test_uint32_refusals():
+    pts = np.arange(30, dtype=np.uint32).reshape(10, 3)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.build(pts, 3, WIDEST)  # the clipped domain is float-only
+    assert e.value.code == oracle.INVALID
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.build(pts, 3, RR | oracle.INT32 | oracle.UINT32)
+    assert e.value.code == oracle.INVALID
