@@ -32,7 +32,7 @@
  * and sorts each run by (coordinate, index).  The moves are one parallel
  * pass; the runs are sorted in parallel, and a run larger than one thread's
  * share by a parallel merge sort.  Coordinates are compared as
- * order-preserving 32-bit keys (float32 with -0 < +0, or int32).
+ * order-preserving 32-bit keys (float32 with -0 < +0, int32 or uint32).
  */
 #define _POSIX_C_SOURCE 200809L
 #include <pthread.h>
@@ -42,7 +42,7 @@
 #include <unistd.h>
 
 enum { PC_OK = 0, PC_INVALID = 1, PC_NOMEM = 2, PC_NAN = 4 };
-enum { PC_RR = 0, PC_WIDEST = 1, PC_TIGHT = 2, PC_INT32 = 0x100 };
+enum { PC_RR = 0, PC_WIDEST = 1, PC_TIGHT = 2, PC_INT32 = 0x100, PC_UINT32 = 0x200 };
 #define PC_MAXK 8
 #define PC_MAXT 256
 
@@ -59,7 +59,9 @@ typedef struct {
   int level;
 } ctx_t;
 
+/* ints: 0 float32, 1 int32 (sign bit flipped), 2 uint32 (the bits) */
 static uint32_t key_of_bits(uint32_t b, int ints) {
+  if (ints == 2) return b;
   if (ints) return b ^ 0x80000000u;
   return b ^ ((b & 0x80000000u) ? 0xFFFFFFFFu : 0x80000000u);
 }
@@ -293,9 +295,10 @@ static void run_threads(void* (*fn)(void*), void* args, size_t sz, int T) {
 static int widest_keys(const uint32_t* lo, const uint32_t* hi, int k, int ints) {
   int best = 0;
   if (ints) {
+    /* both integer key maps keep differences: the extent is the key range */
     int64_t be = 0;
     for (int d = 0; d < k; ++d) {
-      int64_t e = (int64_t)(int32_t)(hi[d] ^ 0x80000000u) - (int64_t)(int32_t)(lo[d] ^ 0x80000000u);
+      int64_t e = (int64_t)hi[d] - (int64_t)lo[d];
       if (d == 0 || e > be) { be = e; best = d; }
     }
     return best;
@@ -311,7 +314,8 @@ static int widest_keys(const uint32_t* lo, const uint32_t* hi, int k, int ints) 
 int pc_build(const void* points, int64_t N, int k, int stride, int mode, int threads,
              int32_t* out_orig) {
   if (N < 0 || N > 2147483647LL || k < 1 || k > PC_MAXK || stride < 4 * k || stride % 4) return PC_INVALID;
-  const int ints = (mode & PC_INT32) != 0;
+  if ((mode & PC_INT32) && (mode & PC_UINT32)) return PC_INVALID;
+  const int ints = (mode & PC_INT32) ? 1 : ((mode & PC_UINT32) ? 2 : 0);
   mode &= 0xFF;
   if (mode != PC_RR && mode != PC_WIDEST && mode != PC_TIGHT) return PC_INVALID;
   if (ints && mode == PC_WIDEST) return PC_INVALID;

@@ -18,6 +18,7 @@ _lock = threading.Lock()
 _lib = None
 
 INT32 = 0x100
+UINT32 = 0x200
 
 
 def compile_lib(force: bool = False) -> str:
@@ -50,7 +51,7 @@ def build(points: np.ndarray, k: int, mode: int = 0, threads: int = 0) -> np.nda
         raise ValueError("records must be a 2-D array of 4-byte items")
     n, w = pts.shape
     orig = np.empty(n, dtype=np.int32)
-    m = mode | (INT32 if pts.dtype == np.int32 else 0)
+    m = mode | {np.dtype(np.int32): INT32, np.dtype(np.uint32): UINT32}.get(pts.dtype, 0)
     rc = _load().pc_build(pts.ctypes.data, n, k, 4 * w, m, threads, orig.ctypes.data)
     if rc != 0:
         raise RuntimeError(f"pc_build returned {rc}")

@@ -28,6 +28,14 @@ def test_int32_and_ties_equal_oracle(mode):
         assert list(paper_cpu.build(full, k, mode, 4)) == list(oracle.build(full, k, mode)[1])
 
 
+@pytest.mark.parametrize("mode", [RR, TIGHT])
+def test_uint32_equals_oracle(mode):
+    rng = np.random.default_rng(6)
+    for k in (1, 3):
+        full = rng.integers(0, 2**32, size=(20000, k), dtype=np.uint64).astype(np.uint32)
+        assert list(paper_cpu.build(full, k, mode, 4)) == list(oracle.build(full, k, mode)[1])
+
+
 def test_aniso_widest_and_payload():
     pts = synth.aniso_float4(50000, seed=2)
     for mode in (WIDEST, TIGHT):
