@@ -587,7 +587,9 @@ def main():
     prof = kdb.kdb_profile_stop()
     launches = kdb.kdb_launch_count() - launches0
     clocks = sampler.stop()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    step_ms = sorted(a.elapsed_time(b) for a, b in ev)
+    ms = sum(step_ms) / args.steps
+    ms_median = step_ms[len(step_ms) // 2]
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -667,6 +669,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "ms_per_step_median": ms_median,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": desc, "n_points": n, "k": k, "stride_bytes": stride,
