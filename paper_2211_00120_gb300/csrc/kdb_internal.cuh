@@ -145,12 +145,17 @@ __host__ __device__ inline uint32_t key_to_float_bits(uint32_t key) {
 // Coordinate types (the mode argument's KDB_COORDS_* flag): float32, int32,
 // uint32.  int32: two's complement order is the unsigned order of the bits
 // with the sign bit flipped; uint32: the bits are the key.
+// Both integer maps are one XOR with a per-type constant, so that each map is
+// a single choice between the float map and that XOR (the record writes of
+// the local finish go out over the host link for mapped host buffers, where
+// they are measurably sensitive to how their stores are scheduled).
 enum : int { kCoordF32 = 0, kCoordI32 = 1, kCoordU32 = 2 };
+__host__ __device__ inline uint32_t int_key_xor(int ctype) { return ctype == kCoordI32 ? 0x80000000u : 0u; }
 __host__ __device__ inline uint32_t coord_key(uint32_t bits, int ctype) {
-  return ctype == kCoordF32 ? float_key(bits) : (ctype == kCoordI32 ? bits ^ 0x80000000u : bits);
+  return ctype != kCoordF32 ? bits ^ int_key_xor(ctype) : float_key(bits);
 }
 __host__ __device__ inline uint32_t key_to_coord_bits(uint32_t key, int ctype) {
-  return ctype == kCoordF32 ? key_to_float_bits(key) : (ctype == kCoordI32 ? key ^ 0x80000000u : key);
+  return ctype != kCoordF32 ? key ^ int_key_xor(ctype) : key_to_float_bits(key);
 }
 #ifdef __CUDACC__
 // The record of a point from its entry (k <= 3 coordinate keys, no payload):
