@@ -1,7 +1,8 @@
 """ctypes wrapper around ``paper_cpu.c``: the paper's level loop on host
 threads, a parallel CPU baseline (test and benchmark infrastructure only; not
 the oracle, which is ``kd_oracle.c``).  Records as for ``oracle.py``: a 2-D
-array of 4-byte items, int32 arrays have int32 coordinates."""
+array of 4-byte items, int32 and uint32 arrays have int32 and uint32
+coordinates."""
 from __future__ import annotations
 
 import ctypes

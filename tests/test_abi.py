@@ -150,3 +150,17 @@ def test_uint32_flag_and_its_refusals(lib):
     assert lib.kdb_workspace_size(100000, 3, 12, kdb.WIDEST_TIGHT | kdb.COORDS_UINT32) > 0
     assert lib.kdb_workspace_size(100000, 3, 12, kdb.WIDEST_EXTENT | kdb.COORDS_UINT32) == 0
     assert lib.kdb_workspace_size(100000, 3, 12, kdb.COORDS_UINT32 | kdb.COORDS_INT32) == 0
+
+
+def test_binding_sets_the_coordinate_type_from_the_dtype():
+    import torch
+
+    f = torch.zeros(4, 3, dtype=torch.float32)
+    i = torch.zeros(4, 3, dtype=torch.int32)
+    assert kdb._mode(f, kdb.ROUND_ROBIN) == kdb.ROUND_ROBIN
+    assert kdb._mode(i, kdb.WIDEST_TIGHT) == kdb.WIDEST_TIGHT | kdb.COORDS_INT32
+    # an explicit type wins over the dtype (uint32 data passed as an int32 view)
+    assert kdb._mode(i, kdb.ROUND_ROBIN | kdb.COORDS_UINT32) == kdb.ROUND_ROBIN | kdb.COORDS_UINT32
+    if getattr(torch, "uint32", None) is not None:
+        u = i.view(torch.uint32)
+        assert kdb._mode(u, kdb.ROUND_ROBIN) == kdb.ROUND_ROBIN | kdb.COORDS_UINT32
