@@ -186,8 +186,9 @@ KDB_API kdb_status kdb_error_word_status(uint32_t word);
  *     least 64 MiB, at most 8) on a stream of the call's own, the build's
  *     first pass over each chunk starting as soon as it has landed, and the
  *     tree is copied back into h_points on `stream`.
- * On a device error (NaN input, ...) h_points is left as it was.
- * Synchronises `stream`.
+ * h_points is written by the device on both paths: page-locked records must
+ * not be registered read-only (cudaHostRegisterReadOnly).  On a device error
+ * (NaN input, ...) h_points is left as it was.  Synchronises `stream`.
  */
 KDB_API kdb_status kdb_build_host(void* h_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
                           kdb_stream_t stream);
