@@ -645,10 +645,18 @@ def main():
             if s > 0:
                 times.append(time.perf_counter() - t0)
         e_ms = 1000.0 * sum(times) / len(times)
+        # one more call, not timed, with the library's per-kernel events: which
+        # kernels the host link slows down (those that touch host records)
+        h.copy_(h_src)
+        torch.cuda.synchronize()
+        kdb.kdb_profile_start()
+        kdb.kdb_build_host(h, k, mode)
+        e_kernel_ms = {p["name"]: round(p["ms"], 3) for p in kdb.kdb_profile_stop()}
         mapped = stride == 4 * k and k <= 3
         e2e = {"value": world * n / (e_ms / 1000.0) / 1e6, "unit": "Mpts/s",
                "h2d_bytes_per_step": n * stride, "d2h_bytes_per_step": n * stride,
                "ms_per_step": e_ms, "steps": len(times), "warmup": 1,
+               "kernel_ms_one_call": e_kernel_ms,
                "api": "kdb_build_host on a pinned host tensor",
                "transfer": ("the kernels read the host records and write the tree into them "
                             "over the host link, no device copy of the records")
