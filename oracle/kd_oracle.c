@@ -52,7 +52,11 @@
  * final array of the 10-point walkthrough of Sec. 5, brute force over all N!
  * arrangements for N <= 7, the k = 1 case against the textbook level-order
  * (Eytzinger) layout of a sorted array, k-d and permutation invariants, and
- * agreement with a separate step-by-step emulator of the paper's level loop.
+ * agreement with a separate step-by-step emulator of the paper's level loop;
+ * for integer coordinates also the walkthrough as int2 points, values on both
+ * sides of 2^31 (a signed/unsigned mix-up fails the k = 1 pin), and the
+ * uint32 tree of any values equal to the int32 tree of the same values with
+ * the top bit flipped.
  */
 #include <math.h>
 #include <stdint.h>
