@@ -164,3 +164,36 @@ def test_binding_sets_the_coordinate_type_from_the_dtype():
     if getattr(torch, "uint32", None) is not None:
         u = i.view(torch.uint32)
         assert kdb._mode(u, kdb.ROUND_ROBIN) == kdb.ROUND_ROBIN | kdb.COORDS_UINT32
+
+
+def test_tuning_file_parser_survives_mutated_input(lib, tmp_path):
+    import random
+
+    rng = random.Random(7)
+    part = kdb.kdb_tuning_shapes(kdb.TUNE_PARTITION)
+    rad = kdb.kdb_tuning_shapes(kdb.TUNE_RADIX)
+    good = json.dumps({"partition": list(part[1]), "radix": list(rad[1])}).encode()
+    f = tmp_path / "t.json"
+    try:
+        for i in range(400):
+            b = bytearray(good)
+            for _ in range(rng.randint(1, 6)):
+                op = rng.randrange(4)
+                p = rng.randrange(len(b) + 1)
+                if op == 0 and b:
+                    del b[min(p, len(b) - 1)]
+                elif op == 1:
+                    b[p:p] = bytes([rng.randrange(256)])
+                elif op == 2 and b:
+                    b[min(p, len(b) - 1)] = rng.choice(b"0123456789,[]{}\": -+e\n\x00")
+                else:
+                    b = b[:p]
+            if i % 50 == 0:
+                b = bytes(rng.randrange(256) for _ in range(rng.randrange(2000)))
+            f.write_bytes(bytes(b))
+            rc = lib.kdb_load_tuning(str(f).encode())
+            assert rc in (kdb.OK, kdb.ERR_INVALID_ARGUMENT)
+            p_idx, r_idx = kdb.kdb_get_tuning()
+            assert 0 <= p_idx < len(part) and 0 <= r_idx < len(rad)
+    finally:
+        kdb.kdb_set_tuning(0, 0)
