@@ -83,6 +83,50 @@ int main(int argc, char** argv) {
       return 1;
     }
   }
+  // the coordinate key maps of the three coordinate types: each inverts
+  // exactly (every third bit pattern, a stride coprime to 2^32) and orders
+  // keys as the type orders values (random pairs): float32 by value with
+  // -0 < +0 (NaN excluded), int32 signed, uint32 unsigned
+  for (int ctype = 0; ctype < 3; ++ctype) {
+    for (uint64_t u = 0; u < (1ull << 32); u += 3) {
+      const uint32_t b = (uint32_t)u;
+      if (ctype == kdb::kCoordF32 && (b & 0x7FFFFFFFu) > 0x7F800000u) continue;
+      if (kdb::key_to_coord_bits(kdb::coord_key(b, ctype), ctype) != b) {
+        printf("FAIL key inverse type %d bits %u\n", ctype, b);
+        return 1;
+      }
+    }
+    uint64_t st = 0x1234567ull + (uint64_t)ctype;
+    auto rnd = [&st]() {  // SplitMix64 (Steele, Lea and Flood 2014)
+      uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      return z ^ (z >> 31);
+    };
+    for (int t = 0; t < 20000000; ++t) {
+      const uint64_t r = rnd();
+      uint32_t a = (uint32_t)r, b = (uint32_t)(r >> 32);
+      if (t % 4 == 0) b = a ^ (1u << (rnd() % 32));  // near pairs
+      if (ctype == kdb::kCoordF32 && (((a & 0x7FFFFFFFu) > 0x7F800000u) || ((b & 0x7FFFFFFFu) > 0x7F800000u)))
+        continue;
+      bool less;
+      if (ctype == kdb::kCoordF32) {
+        float fa, fb;
+        memcpy(&fa, &a, 4);
+        memcpy(&fb, &b, 4);
+        less = fa < fb || (fa == fb && std::signbit(fa) && !std::signbit(fb));
+      } else if (ctype == kdb::kCoordI32) {
+        less = (int32_t)a < (int32_t)b;
+      } else {
+        less = a < b;
+      }
+      if (less != (kdb::coord_key(a, ctype) < kdb::coord_key(b, ctype))) {
+        printf("FAIL key order type %d %u %u\n", ctype, a, b);
+        return 1;
+      }
+      ++cases;
+    }
+  }
   printf("OK %lld\n", cases);
   return 0;
 }
