@@ -61,10 +61,36 @@ KIND_SOURCE = {"partition_pass": "kdb_part.cu", "radix_pass": "kdb_lists.cu",
                "prepass": "kdb_tree.cu"}
 
 
+def code_only(text: str) -> str:
+    """C/C++/CUDA source without its comments and with every run of white
+    space collapsed to one blank: what the compiler sees of the code."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":  # a string or character literal, escapes included
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_hash(kind: str) -> str:
-    """Hash of the source file defining kernel kind `kind` and every header it
-    includes: a stored ncu traffic figure is only reused while that kernel is
-    exactly the one it was measured on."""
+    """Hash of the code (comments and layout left out) of the source file
+    defining kernel kind `kind` and of every header it includes: a stored ncu
+    figure is only reused while that kernel's code is exactly the code it was
+    measured on."""
     d = os.path.join(ROOT, "paper_2211_00120_gb300", "csrc")
     h = hashlib.sha256()
     todo, seen = [KIND_SOURCE.get(kind, "")], set()
@@ -74,9 +100,9 @@ def kernel_hash(kind: str) -> str:
             continue
         seen.add(f)
         with open(os.path.join(d, f), "rb") as fh:
-            text = fh.read()
-        h.update(f.encode() + text)
-        todo += re.findall(r'#include "([^"/]+)"', text.decode())
+            text = fh.read().decode()
+        h.update(f.encode() + code_only(text).encode())
+        todo += re.findall(r'#include "([^"/]+)"', text)
     return h.hexdigest()[:16] if seen else ""
 
 

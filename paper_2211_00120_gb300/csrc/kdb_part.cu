@@ -12,15 +12,18 @@
 //   pivot      for every subtree s the entry at rank ss(lChild(s)) of s's
 //              segment in the list of s's split dimension is node s
 //              (Observation 1): pinned;
-//   partition  every list is re-sorted by (new tag, key, index).  The new tag
-//              is 2s+1 / 2s+2 by comparing the entry with the pivot (the tag
-//              update of Sec. 3.2); since the list is already sorted by
-//              (s, key, index), this is one stable radix pass on the child
-//              bit within every segment.  The pass stages a tile in shared
-//              memory by bulk copy, ranks left/right items with warp ballots,
-//              finds the counts of earlier tiles of the same segment by
-//              decoupled look-back (a warp reads 32 predecessors per round
-//              trip), and writes both children's runs in order.
+//   partition  a list is advanced b = 1 .. 3 levels at once: re-sorted by
+//              (tag b levels down, key, index).  Each step of the tag update
+//              (Sec. 3.2) sends an entry to 2s+1 / 2s+2 by comparing it with
+//              the pivot of s; since the list is already sorted by
+//              (s, key, index), the b steps together are one stable split of
+//              every segment into its 2^b descendants' runs.  The pass stages
+//              a tile in shared memory by bulk copy (its shape a template
+//              argument), ranks the entries per (segment, descendant) with
+//              warp match_any, finds the counts of earlier tiles of the same
+//              segment by decoupled look-back (lane groups read several
+//              predecessors per round trip), and writes every descendant's
+//              run in order.
 #include "kdb_launch.h"
 #include "kdb_segsort.cuh"
 

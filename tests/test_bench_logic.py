@@ -45,9 +45,15 @@ def test_stored_traffic_only_for_its_tile_shape():
     assert bench.traffic_per_launch("partition_pass", 1e6, {"partition": (999, 1, 1)}) is None
 
 
+def test_code_only_drops_comments_and_layout():
+    src = 'int a = 1; // one\n/* two\n lines */  char* s = "a // b /* c */";\n  char q = \'"\';'
+    assert bench.code_only(src) == 'int a = 1; char* s = "a // b /* c */"; char q = \'"\';'
+    assert bench.code_only("x\n\n\t y") == "x y"
+
+
 def test_kernel_hash_follows_included_headers(tmp_path, monkeypatch):
-    """A change to a header that a kernel's file includes changes its hash; a
-    change to a file it does not include does not."""
+    """A code change in a header that a kernel's file includes changes its
+    hash; a comment, or a change to a file it does not include, does not."""
     import shutil
 
     src = os.path.join(bench.ROOT, "paper_2211_00120_gb300", "csrc")
@@ -57,9 +63,12 @@ def test_kernel_hash_follows_included_headers(tmp_path, monkeypatch):
     h0 = bench.kernel_hash("radix_pass")
     assert len(h0) == 16 and h0 == bench.kernel_hash("radix_pass")
     with open(dst / "kdb_serve.cu", "a") as f:  # not included by kdb_lists.cu
-        f.write("\n// unrelated\n")
+        f.write("\nstatic int unrelated_code = 0;\n")
     assert bench.kernel_hash("radix_pass") == h0
-    with open(dst / "kdb_segsort.cuh", "a") as f:  # included by kdb_lists.cu
-        f.write("\n// changed\n")
+    with open(dst / "kdb_segsort.cuh", "a") as f:  # included: a comment only
+        f.write("\n// a comment\n/* and another */\n")
+    assert bench.kernel_hash("radix_pass") == h0
+    with open(dst / "kdb_segsort.cuh", "a") as f:  # included: code
+        f.write("\nstatic int changed_code = 1;\n")
     assert bench.kernel_hash("radix_pass") != h0
     assert bench.kernel_hash("no_such_kind") == ""
