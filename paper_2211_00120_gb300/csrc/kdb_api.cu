@@ -1,19 +1,25 @@
 // kdb_api.cu -- host driver of the build and the C ABI declared in kdb.h.
 //
-// The level loop (Sec. 3.2, parallelKDTreeBuild):
-//   prepass      one read of the records: coordinate keys, NaN check, digit
-//                histograms, scene boxes (widest mode, Sec. 6);
-//   rank sorts   per dimension, a stable LSD radix sort of the coordinate keys
-//                from input order, so equal coordinates keep index order; its
-//                last pass writes each point's rank in that dimension.  The
-//                rank is then a strict stand-in for (coordinate, index) in
-//                every later key;
-//   level l      key = (set, subtree, rank in the split dimension), radix sort
-//                of the level's live items (Sec. 3.1), the tag update of
-//                Sec. 3.2 fused into the last pass; widest mode then derives
-//                the next level's split dimensions;
-//   placement    the records are permuted in place by the node -> original
-//                index array (one int32 per point).
+// The level loop (Sec. 3.2, parallelKDTreeBuild), k <= 3:
+//   prepass       one read of the records: a 16-byte entry per point (the
+//                 order-preserving keys of its coordinates and its index), NaN
+//                 check, scene boxes (widest mode, Sec. 6);
+//   level-0 lists per dimension, a stable LSD radix sort of the entries from
+//                 input order (kdb_lists.cu): list d is the order of the
+//                 level-0 sort (Sec. 3.1) when d is the split dimension;
+//   level l       the pivots of level l at rank ss(lChild) of each segment of
+//                 the split dimension's list (Observation 1), then a list
+//                 advanced by one to three levels of the tag update
+//                 (kdb_part.cu); lists are advanced lazily under round robin;
+//   local finish  once every subtree holds at most 2^13 - 1 points, one block
+//                 per subtree runs its remaining levels on chip (kdb_local.cu);
+//   records       without payload, each record is written at its node from its
+//                 entry when the node is pinned; with payload, the records are
+//                 gathered by the node -> original index array (one int32 per
+//                 point), or permuted in place by it (kdb_set_placement).
+// k > 3: coordinate ranks by per-dimension radix sorts, then each level sorts
+// (set, subtree, rank in the split dimension) keys with the tag update fused
+// into the last pass (kdb_sort.cu); the same local finish and placement.
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
