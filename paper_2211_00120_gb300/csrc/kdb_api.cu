@@ -19,7 +19,9 @@
 //                 point), or permuted in place by it (kdb_set_placement).
 // k > 3: coordinate ranks by per-dimension radix sorts, then each level sorts
 // (set, subtree, rank in the split dimension) keys with the tag update fused
-// into the last pass (kdb_sort.cu); the same local finish and placement.
+// into the last pass (kdb_sort.cu); the local finish for k = 4 (its k + 1
+// lists fill the shared memory), every level globally for k = 5 .. 8; then the
+// placement.
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
