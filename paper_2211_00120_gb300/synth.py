@@ -21,6 +21,11 @@ Sec. 7.1, Table 1) and the configurations the library is measured on:
 * ``aniso_float4``: x in U[0,100), y in U[0,1), z in U[0,10), and a fourth
   float that carries the uint32 bit pattern of the row index (payload).
 * ``lognormal_sizes``: set sizes floor(exp(U[ln lo, ln hi])).
+* ``int32_uniform``: int32 coordinates uniform over the whole range (the
+  paper's int1 data, Table 1).
+* ``poisson_requests``: a Poisson stream of build requests for the serving
+  measurement: exponential gaps, log-uniform sizes, float3/float4 and
+  uniform/clustered by fair coins.
 """
 from __future__ import annotations
 
