@@ -247,6 +247,167 @@ def floor_bytes(n: int, stride_bytes: int) -> float:
     return tot
 
 
+def model_bytes(prof: list, steps: int) -> float:
+    """Algorithmic bytes of every launch of one build (the library's profiling
+    rows: each kernel's pass model, summed over its launches)."""
+    return sum(p["bytes"] for p in prof) / max(steps, 1)
+
+
+def build_rooflines(prof: list, steps: int, n: int, stride: int, build_ms: float, peak: float,
+                    peak_src: str, shapes: dict) -> dict:
+    """Roofline entry of the dominant kernel (largest share of the step), each
+    big kernel against its own bound, and two whole-build fractions: the
+    pass-model bytes of every launch, and the floor bytes (each live record
+    and its int32 read and written once per level), each over the peak and
+    the build time."""
+    dom = max(prof, key=lambda p: p["ms"])
+    roof = kernel_roofline(dom, steps, n, peak, peak_src, shapes) or {}
+    roof["kernel_share_of_step"] = dom["ms"] / steps / build_ms
+    mb = model_bytes(prof, steps)
+    roof["build_model_bytes"] = mb
+    roof["build_model_frac"] = mb / (peak * 1e9) / (build_ms / 1000.0)
+    roof["build_floor_bytes"] = floor_bytes(n, stride)
+    roof["build_floor_frac"] = floor_bytes(n, stride) / (peak * 1e9) / (build_ms / 1000.0)
+    roof["kernels"] = [r for r in (kernel_roofline(p, steps, n, peak, peak_src, shapes)
+                                   for p in prof
+                                   if p["name"] in ("partition_pass", "radix_pass", "local_finish"))
+                       if r]
+    return roof
+
+
+def timed_builds(kdb, work, src, k: int, mode: int, steps: int, stream):
+    """`steps` builds of `work`, each after restoring the input by a device
+    copy (which also evicts L2 for inputs above its size), timed with CUDA
+    events on the launching stream; returns (ms per build, profiling rows,
+    library launches)."""
+    import torch
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize()
+    launches0 = kdb.kdb_launch_count()
+    kdb.kdb_profile_start()
+    for s in range(steps):
+        work.copy_(src)
+        ev[s][0].record(stream)
+        kdb.kdb_build(work, k, mode)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    prof = kdb.kdb_profile_stop()
+    launches = kdb.kdb_launch_count() - launches0
+    return [a.elapsed_time(b) for a, b in ev], prof, launches
+
+
+def workload_leg(kdb, name: str, steps: int, warmup: int, peak: float, peak_src: str,
+                 shapes: dict) -> dict:
+    """One more workload of the build, timed like the headline: device-resident
+    input restored before each step, CUDA events, per-kernel rooflines."""
+    import torch
+
+    desc, n, k, sf, mode, gen = WORKLOADS[name]
+    host = gen(n)
+    src = torch.from_numpy(host).cuda()
+    work = torch.empty_like(src)
+    del host
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        work.copy_(src)
+        kdb.kdb_build(work, k, mode)
+    torch.cuda.synchronize()
+    bad = kdb.kdb_validate(work, k, mode)
+    if bad != -1:
+        raise SystemExit(f"bench: {name}: built array is not a k-d tree (node {bad})")
+    times, prof, launches = timed_builds(kdb, work, src, k, mode, steps, stream)
+    ms = sum(times) / len(times)
+    stride = 4 * sf
+    out = {"workload": desc, "n_points": n, "k": k, "stride_bytes": stride,
+           "split": ["round_robin", "widest_extent", "widest_tight_box"][mode],
+           "steps": steps, "warmup": warmup, "ms_per_step": ms,
+           "ms_per_step_median": sorted(times)[len(times) // 2],
+           "value": n / (ms / 1000.0) / 1e6, "unit": "Mpts/s", "gpu_launches": launches,
+           "kernel_ms_per_step": {p["name"]: round(p["ms"] / steps, 3) for p in prof},
+           "roofline": build_rooflines(prof, steps, n, stride, ms, peak, peak_src, shapes)}
+    del src, work
+    torch.cuda.empty_cache()
+    return out
+
+
+def host_info() -> dict:
+    """CPU model and core counts of the host the CPU baselines run on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model Name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return {"cpu_model": model, "nproc": len(os.sched_getaffinity(0)),
+            "machine": os.uname().machine}
+
+
+def host_link(t, device: int) -> dict:
+    """Where the pinned host records live: the NUMA node of a sample of the
+    buffer's pages (move_pages in query mode), the NUMA node the GPU's PCI
+    function reports, and the nodes that have CPUs."""
+    import ctypes
+
+    info = {"gpu_numa_node": None, "pages_numa_nodes": None, "cpu_numa_nodes": None}
+    try:
+        import torch
+
+        pr = torch.cuda.get_device_properties(device)
+        bus = (f"{getattr(pr, 'pci_domain_id', 0):04x}:{pr.pci_bus_id:02x}:"
+               f"{pr.pci_device_id:02x}.0")
+        with open(f"/sys/bus/pci/devices/{bus}/numa_node") as f:
+            info["gpu_numa_node"] = int(f.read().strip())
+        info["gpu_pci"] = bus
+    except Exception:
+        pass
+    try:
+        nodes = {}
+        base = "/sys/devices/system/node"
+        for d in sorted(os.listdir(base)):
+            if d.startswith("node") and d[4:].isdigit():
+                with open(os.path.join(base, d, "cpulist")) as f:
+                    cl = f.read().strip()
+                if cl:
+                    nodes[int(d[4:])] = cl
+        info["cpu_numa_nodes"] = nodes
+    except Exception:
+        pass
+    try:
+        nr = {"x86_64": 279, "aarch64": 239}[os.uname().machine]
+        libc = ctypes.CDLL(None, use_errno=True)
+        page = os.sysconf("SC_PAGE_SIZE")
+        nbytes = t.numel() * t.element_size()
+        m = 64
+        addrs = [(t.data_ptr() + i * (nbytes // m)) & ~(page - 1) for i in range(m)]
+        pages = (ctypes.c_void_p * m)(*addrs)
+        status = (ctypes.c_int * m)()
+        libc.syscall.restype = ctypes.c_long
+        rc = libc.syscall(ctypes.c_long(nr), ctypes.c_int(0), ctypes.c_ulong(m), pages, None,
+                          status, ctypes.c_int(0))
+        if rc == 0:
+            hist = {}
+            for v in status:
+                hist[str(v)] = hist.get(str(v), 0) + 1
+            info["pages_numa_nodes"] = hist
+    except Exception:
+        pass
+    return info
+
+
 def cpu_baseline(workload: str, target_s: float = 15.0):
     """The oracle as it stands, single-threaded, on a bounded sample of the
     workload: the first n points of the same generator, n grown until one
@@ -272,7 +433,7 @@ def cpu_baseline(workload: str, target_s: float = 15.0):
         reps += 1
     return {"value": reps * n / total / 1e6, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
             "sample": f"{reps} builds of the first {n} points of the same generator "
-                      f"({desc}); oracle single-threaded, {total:.1f} s"}
+                      f"({desc}); oracle single-threaded, {total:.1f} s", **host_info()}
 
 
 def cpu_parallel_baseline(workload: str, log2_points: int = 24):
@@ -291,7 +452,7 @@ def cpu_parallel_baseline(workload: str, log2_points: int = 24):
     return {"value": n / dt / 1e6, "unit": "Mpts/s", "cores": paper_cpu.cores(),
             "kind": "paper level loop on host threads (parallel sort per level + tag update)",
             "sample": f"one build of the first {n} points of the same generator ({desc}), "
-                      f"{dt:.1f} s"}
+                      f"{dt:.1f} s", **host_info()}
 
 
 def batched_vs_serial(sets: int = 4096, lo: int = 100, hi: int = 1_000_000, seed: int = 3,
@@ -501,7 +662,8 @@ def run_reference(args):
             "data": "synthetic", "config": {"workload": desc, "sample_points": n, "k": k,
                                             "stride_bytes": 4 * sf},
             "cpu_baseline": {"value": val, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {n} points of the workload per step"},
+                             "sample": f"first {n} points of the workload per step",
+                             **host_info()},
             "e2e": {"value": val, "unit": "Mpts/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -521,6 +683,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched vs serial measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the 1e7 mixed and 1e8 float4 widest-extent workloads")
     ap.add_argument("--serving-only", action="store_true",
                     help="only the serving measurement (prints its JSON object)")
     ap.add_argument("--points", type=int, default=0,
@@ -595,25 +759,13 @@ def main():
 
     sampler = ClockSampler(local)
     time.sleep(0.3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
     if dist:
         dist.barrier()
-    torch.cuda.synchronize()
-    launches0 = kdb.kdb_launch_count()
-    kdb.kdb_profile_start()
-    for s in range(args.steps):
-        work.copy_(src)  # restore the input (1.2 GB write: also evicts L2)
-        ev[s][0].record(stream)
-        kdb.kdb_build(work, k, mode)
-        ev[s][1].record(stream)
-    torch.cuda.synchronize()
+    step_ms, prof, launches = timed_builds(kdb, work, src, k, mode, args.steps, stream)
     if dist:
         dist.barrier()
-    prof = kdb.kdb_profile_stop()
-    launches = kdb.kdb_launch_count() - launches0
     clocks = sampler.stop()
-    step_ms = sorted(a.elapsed_time(b) for a, b in ev)
+    step_ms = sorted(step_ms)
     ms = sum(step_ms) / args.steps
     ms_median = step_ms[len(step_ms) // 2]
     if dist:
@@ -627,17 +779,8 @@ def main():
     # (algorithmic bytes over their CUDA-event time in the timed steps), the
     # issue-bound local finish against the warp-instruction issue peak
     peak, peak_src = measured_peak()
-    build_ms_total = ms
     kernel_ms = {p["name"]: round(p["ms"] / args.steps, 3) for p in prof}
-    fb = floor_bytes(n, stride)
-    per_kernel = [r for r in (kernel_roofline(p, args.steps, n, peak, peak_src, shapes)
-                              for p in prof
-                              if p["name"] in ("partition_pass", "radix_pass", "local_finish")) if r]
-    dom = max(prof, key=lambda p: p["ms"])
-    roofline = kernel_roofline(dom, args.steps, n, peak, peak_src, shapes) or {}
-    roofline["kernel_share_of_step"] = dom["ms"] / args.steps / build_ms_total
-    roofline["build_floor_frac"] = fb / (peak * 1e9) / (build_ms_total / 1000.0)
-    roofline["kernels"] = per_kernel
+    roofline = build_rooflines(prof, args.steps, n, stride, ms, peak, peak_src, shapes)
 
     # the paper's almost-in-place placement (one int32 per point) on the same
     # builds, for comparison with the default gather through spare workspace
@@ -679,7 +822,14 @@ def main():
         kdb.kdb_build_host(h, k, mode)
         e_kernel_ms = {p["name"]: round(p["ms"], 3) for p in kdb.kdb_profile_stop()}
         mapped = stride == 4 * k and k <= 3
+        link = host_link(h, local)
+        pre = e_kernel_ms.get("prepass")
+        if mapped and pre:
+            # the prepass reads every host record once over the host link
+            link["prepass_ms"] = pre
+            link["prepass_read_gbs"] = n * stride / (pre / 1000.0) / 1e9
         e2e = {"value": world * n / (e_ms / 1000.0) / 1e6, "unit": "Mpts/s",
+               "host_link": link,
                "h2d_bytes_per_step": n * stride, "d2h_bytes_per_step": n * stride,
                "ms_per_step": e_ms, "steps": len(times), "warmup": 1,
                "kernel_ms_one_call": e_kernel_ms,
@@ -688,6 +838,16 @@ def main():
                             "over the host link, no device copy of the records")
                if mapped else "chunked copies to the device overlapped with the first pass, "
                               "one copy back"}
+
+    legs = {}
+    if not args.no_legs and not args.points:
+        del src, work
+        torch.cuda.empty_cache()
+        src = work = None
+        for name in ("mixed_1e7_f3_rr", "aniso_1e8_f4_widest"):
+            if name != args.workload:
+                legs[name] = workload_leg(kdb, name, min(args.steps, 20), args.warmup, peak,
+                                          peak_src, shapes)
 
     batched = None
     if not args.no_batched:
@@ -717,7 +877,8 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_parallel": cpu_par,
                 "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "kernel_ms_per_step": kernel_ms,
-                "placement_in_place": in_place, "tuning": tuned, "batched": batched,
+                "placement_in_place": in_place, "tuning": tuned, "workloads": legs,
+                "batched": batched,
                 "serving": served}
         print(json.dumps(line), flush=True)
     if dist:

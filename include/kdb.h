@@ -209,6 +209,9 @@ KDB_API kdb_status kdb_build_host(void* h_points, int64_t n, int k, int stride_b
  * KDB_ERR_INVALID_ARGUMENT before any work is enqueued.
  * The first call on each device looks up the array's device address (with
  * that device current); make that first call before any stream capture.
+ * The address is kept for the life of the process, so the library must not
+ * be used across a cudaDeviceReset of that device (the reset unloads the
+ * array, and the kept address would no longer name it).
  * Every call uses the same array, which keeps the previous call's contents
  * (the build clears what must start at zero): calls that overlap on the GPU,
  * from several streams or host threads, race with each other and must be

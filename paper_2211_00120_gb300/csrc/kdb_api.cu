@@ -749,7 +749,11 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     pa.wait_epoch = c.wait_epoch;
     pa.wait_ns = c.wait_ns;
     pa.status_words = c.status_words;
-    Prof pf(K_PARTITION, (double)P.items[p] * 32, 1, st);
+    // algorithmic bytes: every item of level p read once; the survivors
+    // written as entries, or (hand-over) as original indices, list 0 as
+    // entries when it is handed over whole
+    const double wbytes = !handoff ? 16.0 : (lents && d == 0 ? 16.0 : 4.0);
+    Prof pf(K_PARTITION, (double)P.items[p] * (16.0 + wbytes), 1, st);
     pa.shape = part_shape;
     cudaError_t e = launch_partition(pa, st);
     std::swap(lcur[d], lnext[d]);
@@ -986,7 +990,11 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     la.lents = lents;
     la.pts_out = direct ? pts : nullptr;
     la.ctype = P.ctype;
-    Prof pf(K_LOCAL, (double)T * (4.0 + 4.0 * k + 4.0), 1, st);
+    // algorithmic bytes per point: the handed-over lists in (list 0 as
+    // entries when handed over whole), perm out, and the record written at
+    // its node when it is written from its entry
+    const double lin = P.use_lists ? (lents ? 16.0 + 4.0 * (k - 1) : 4.0 * k) : 4.0 + 4.0 * k;
+    Prof pf(K_LOCAL, (double)T * (lin + 4.0 + (direct ? (double)P.stride : 0.0)), 1, st);
     KDB_CK(launch_local_finish(la, st));
   }
 

@@ -235,6 +235,7 @@ def kdb_build_host(points, k: int, mode: int = ROUND_ROBIN, stream=None) -> None
 
 
 NOALLOC_MAX_POINTS = 262144
+NOALLOC_SCRATCH_BYTES = 64 << 20  # the static workspace array (KDB_NOALLOC_SCRATCH_BYTES)
 
 
 def kdb_build_noalloc(points, k: int, mode: int = ROUND_ROBIN, stream=None) -> None:

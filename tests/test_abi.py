@@ -197,3 +197,15 @@ def test_tuning_file_parser_survives_mutated_input(lib, tmp_path):
             assert 0 <= p_idx < len(part) and 0 <= r_idx < len(rad)
     finally:
         kdb.kdb_set_tuning(0, 0)
+
+
+def test_binding_constants_match_the_header():
+    """The binding's copies of the header's limits (the no-alloc build's point
+    count and static workspace size) are the header's values."""
+    import re
+
+    text = open(kdb.HEADER).read()
+    pts = int(re.search(r"#define KDB_NOALLOC_MAX_POINTS (\d+)", text).group(1))
+    m = re.search(r"#define KDB_NOALLOC_SCRATCH_BYTES \((\d+)u << (\d+)\)", text)
+    assert pts == kdb.NOALLOC_MAX_POINTS
+    assert int(m.group(1)) << int(m.group(2)) == kdb.NOALLOC_SCRATCH_BYTES
