@@ -5,18 +5,25 @@
 // memory, writing only the final node -> point entries.
 //
 // Inside the block, each level still performs the paper's step: order every
-// sub-segment by (tag, coordinate) (Sec. 3.1) and apply the tag update
-// (Sec. 3.2).  The order is kept as k lists of local ids, one per dimension,
-// each sorted by (sub-segment, key_d, original index).  For a level with split
-// dimension d, the list of d *is* the sorted order the tag update needs: in
-// sub-segment t the point at rank ss(lChild) is pinned (Observation 1), lower
-// ranks go left, higher ranks right.  One pass over that list writes, per
-// point, its side and the closed-form start of its run on the next level (the
-// sub-segment sizes of Sec. 4); every list is then partitioned stably by side
-// with warp ballots, which leaves each child's points sorted by (child, key,
-// index) -- the next level's sort order -- without sorting again.  Once a
-// depth has at least 32 sub-segments, each warp finishes its own subtrees
-// without block barriers.
+// node's points by (tag, coordinate) (Sec. 3.1) and apply the tag update
+// (Sec. 3.2).  The block keeps k lists of local ids, one per dimension, each
+// sorted by (key_d, original index), and one tag per point: its node on the
+// current level.  The points of a node are a subset of every list, in the
+// list's order, so a point's rank among its node's points in the order of
+// dimension d is the number of earlier entries of list d with the same tag.
+// A level with split dimension d is therefore one pass over list d: each
+// point gets that rank by counting (warp match_any, per-node counters), the
+// point at rank ss(lChild) is pinned as the node (Observation 1), lower ranks
+// go to the left child and higher ranks to the right one -- only the tags
+// change, the lists are not re-sorted.
+//
+// The first levels run block-wide (per-warp counts, then an exclusive prefix
+// over the warps for each node).  At the depth with 32 nodes every list is
+// split once, stably, into the 32 nodes' runs; from then on each warp owns
+// one node's points and finishes its subtree alone, with counters of its
+// own and no block barrier.  The pinned points are recorded per node and
+// written at the end, node by node, so that consecutive threads write
+// consecutive nodes.
 //
 // The lists arrive from the global passes already in order (as original
 // indices); a set small enough to start here builds them from its entries by
@@ -30,11 +37,17 @@ constexpr int T = kLocalThreads;
 constexpr int W = T / 32;
 static_assert(W == 32, "the warp phase starts at the first depth with >= 32 subtrees");
 // scratch area (12 bytes per item): the setup's sort buffers (4 + 4 + 2 + 2)
-// or hash table (2 slots per item of 4 + 2 bytes); the levels' info words,
-// split dimensions and planes (2 + 1 + 4)
+// or hash table (2 slots per item of 4 + 2 bytes); on the levels, per item a
+// tag (2), per block node the pinned item, split dimension and plane (or
+// tight-box corners) (2 + 1 + 4), and the counters (3)
 static_assert(2 * kLocalCap * 4 + 2 * kLocalCap * 2 <= 12 * kLocalCap, "hash table fits");
-static_assert(kLocalCap * (2 + 1 + 4) <= 12 * kLocalCap, "level scratch fits");
-static_assert(kLocalCap <= (1 << 14), "info words hold 14-bit offsets");
+constexpr int kJW = 5;                       // first depth of the warp phase: 2^5 = W nodes
+constexpr int kWT = kLocalCap >> (kJW + 1);  // most nodes of one warp on a depth that splits
+constexpr uint32_t kPin = 0xFFFFu;           // tag of a pinned item
+constexpr uint32_t kMoved = 0x8000u;         // tag flag: already split on this depth
+static_assert((1 << kJW) == W, "one warp per node of the first warp depth");
+static_assert(2 * W * 32 * 4 <= 3 * kLocalCap && W * kWT * 4 <= 3 * kLocalCap, "counters fit");
+static_assert(kLocalCap <= (1 << 13) && kLocalMax < (1 << 13), "ids and in-warp ranks pack in 13 bits");
 
 __device__ inline int widest_dim(const float* lo, const float* hi, int k) {
   int best = 0;
@@ -203,34 +216,30 @@ __device__ inline uint32_t l_left(const Local& y, uint32_t u) {  // h >= 1
   const uint32_t low = lowest >= y.mb ? 0u : min(y.mb - lowest, y.w);
   return (y.w - 1u) + low;
 }
-__device__ inline uint32_t l_left_before(const Local& y, uint32_t u) {  // h >= 1
-  const uint32_t fb = y.mb >> y.h;
-  uint32_t low = min(u, fb) * y.w;
-  if (u > fb) low += min(y.mb - fb * (2u * y.w), y.w);
-  return u * (y.w - 1u) + low;
+
+__device__ inline uint32_t comp3(const uint4& e, int d) {
+  return d == 0 ? e.x : (d == 1 ? e.y : e.z);
 }
 
-// Segments [uf, uf + cnt) of one level handled by one thread group.
-struct Range {
-  Local y;
-  uint32_t uf;       // first segment
-  uint32_t p0, p1;   // positions of the range's items
-  uint32_t lb0;      // lefts before uf
-  uint32_t nb;       // position of the range's first item on the next level
-};
-
-__device__ inline Range make_range(const Local& y, uint32_t uf, uint32_t cnt) {
-  Range r;
-  r.y = y;
-  r.uf = uf;
-  r.p0 = l_start(y, uf);
-  r.p1 = l_start(y, uf + cnt);
-  r.lb0 = y.h >= 1 ? l_left_before(y, uf) : 0u;
-  // the next level holds every item of this level but the pinned ones, in
-  // segment order: items before the range's first child = items before uf
-  // minus the uf pivots above them
-  r.nb = r.p0 - uf;
-  return r;
+// Tight-box rule, one dimension at a time: extent hi - lo of dimension d
+// (float32, round to nearest; integers: the exact difference of the keys,
+// which are ordered like the values) against the widest so far, scanned from
+// d = 0 with a strict '>' (the lowest dimension wins ties), as for a whole box.
+__device__ inline void tight_step(uint32_t lo, uint32_t hi, int d, int ctype, uint32_t* best,
+                                  uint8_t* dim) {
+  if (ctype != kCoordF32) {
+    const uint32_t e = hi - lo;
+    if (d == 0 || e > *best) {
+      *best = e;
+      *dim = (uint8_t)d;
+    }
+    return;
+  }
+  const float e = __fsub_rn(__uint_as_float(key_to_float_bits(hi)), __uint_as_float(key_to_float_bits(lo)));
+  if (d == 0 || e > __uint_as_float(*best)) {
+    *best = __float_as_uint(e);
+    *dim = (uint8_t)d;
+  }
 }
 
 // kMode: the split rule (0 round robin, 1 clipped domain, 2 tight box), a
@@ -256,9 +265,17 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
   uint32_t* s_hkey = reinterpret_cast<uint32_t*>(s_area);                  // 2 * cap
   uint16_t* s_hval = reinterpret_cast<uint16_t*>(s_hkey + 2 * kLocalCap);  // 2 * cap
   // level view of the scratch area
-  uint16_t* s_info = reinterpret_cast<uint16_t*>(s_area);                  // cap
-  uint8_t* s_ldim = reinterpret_cast<uint8_t*>(s_info + kLocalCap);        // cap
-  float* s_lplane = reinterpret_cast<float*>(s_ldim + kLocalCap);          // cap
+  uint16_t* s_tag = reinterpret_cast<uint16_t*>(s_area);                   // per item: its node
+  uint16_t* s_pin = s_tag + kLocalCap;                                      // per block node: its item
+  uint8_t* s_ldim = reinterpret_cast<uint8_t*>(s_pin + kLocalCap);         // per block node
+  float* s_lplane = reinterpret_cast<float*>(s_ldim + kLocalCap);          // per block node
+  uint32_t* s_ctr = reinterpret_cast<uint32_t*>(s_lplane + kLocalCap);     // counters
+  // tight-box rule, in place of the planes: per node of the current depth
+  // the items holding its smallest and largest key of one dimension, and its
+  // widest extent so far (a splitting depth has at most cap / 2 nodes)
+  uint16_t* s_tlo = reinterpret_cast<uint16_t*>(s_lplane);
+  uint16_t* s_thi = s_tlo + kLocalCap / 2;
+  uint32_t* s_tbest = reinterpret_cast<uint32_t*>(s_thi + kLocalCap / 2);
 
   const LocalWork wk = a.work[blockIdx.x];
   const LocalSet ls = a.lsets[wk.set];
@@ -287,10 +304,28 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     const uint32_t* lo0 = a.lorig + ls.off + start0;
     const uint4* le0 = a.lents ? a.lents + ls.off + start0 : nullptr;  // list 0 as entries
     constexpr uint32_t HM = 2 * kLocalCap - 1;
+    constexpr int PER = kLocalCap / T;  // items per thread (8)
+    if (k > 3) s_bad = 1;  // lists are handed over for k <= 3 only
+    // every thread's items of every list are loaded at once, so that their
+    // global loads are in flight together
+    uint32_t ov[3][PER];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const uint32_t i = threadIdx.x + (uint32_t)r * T;
+      ov[0][r] = ov[1][r] = ov[2][r] = 0;
+      if (i < m) {
+        ov[0][r] = le0 ? reinterpret_cast<const uint32_t*>(le0 + i)[3] : lo0[i];
+        if (k > 1) ov[1][r] = a.lorig[(size_t)a.total + ls.off + start0 + i];
+        if (k > 2) ov[2][r] = a.lorig[(size_t)2 * a.total + ls.off + start0 + i];
+      }
+    }
     for (uint32_t i = threadIdx.x; i < 2 * kLocalCap; i += T) s_hkey[i] = 0xFFFFFFFFu;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < m; i += T) {
-      uint32_t o = le0 ? le0[i].w : lo0[i];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const uint32_t i = threadIdx.x + (uint32_t)r * T;
+      if (i >= m) continue;
+      uint32_t o = ov[0][r];
       if (o >= a.total) {
         s_bad = 1;
         o = 0;
@@ -312,11 +347,15 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
       if (!done) s_bad = 1;
     }
     __syncthreads();
-    for (int d = 1; d < k; ++d) {
-      const uint32_t* lod = a.lorig + (size_t)d * a.total + ls.off + start0;
+#pragma unroll
+    for (int d = 1; d < 3; ++d) {
+      if (d >= k) break;
       uint16_t* list = s_lists + (size_t)d * kLocalCap;
-      for (uint32_t i = threadIdx.x; i < m; i += T) {
-        const uint32_t o = lod[i];
+#pragma unroll
+      for (int r = 0; r < PER; ++r) {
+        const uint32_t i = threadIdx.x + (uint32_t)r * T;
+        if (i >= m) continue;
+        const uint32_t o = ov[d][r];
         uint32_t h = (o * 0x9E3779B1u) >> (32 - (kLocalLog + 1));
         uint32_t id = 0xFFFFFFFFu;
         for (uint32_t probe = 0; probe <= HM; ++probe) {
@@ -417,9 +456,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
         s_box[d] = __uint_as_float(key_to_float_bits(a.bbox[wk.set * 2 * k + d]));
         s_box[kMaxK + d] = __uint_as_float(key_to_float_bits(a.bbox[wk.set * 2 * k + k + d]));
       }
-      const int d0 = widest_dim(s_box, s_box + kMaxK, k);
-      a.dims[ls.off + s0] = (uint8_t)d0;
-      s_ldim[0] = (uint8_t)d0;
+      s_ldim[0] = (uint8_t)widest_dim(s_box, s_box + kMaxK, k);
     } else {
       const float* b = a.boxes_local + ((size_t)ls.lbox0 + wk.s_rel) * 2 * k;
       for (int d = 0; d < k; ++d) {
@@ -429,7 +466,6 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
       s_ldim[0] = a.dims[ls.off + s0];
     }
   }
-  __syncthreads();
 
   constexpr bool widest = kMode == 1;  // widest side of the clipped domain (Sec. 6)
   constexpr bool tight = kMode == 2;   // widest side of the subtree's own box
@@ -444,9 +480,9 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     if (threadIdx.x == 0) atomicOr(a.err, ERR_INTERNAL);
     return;
   }
-  // split dimension of node tl (index among the block's nodes at depth jj):
-  // widest side of its domain, the root's domain clipped by the planes of
-  // its ancestors inside the block (Sec. 6)
+  // split dimension of block node tl at depth jj: widest side of its domain,
+  // the root's domain clipped by the planes of its ancestors inside the block
+  // (Sec. 6)
   auto node_dim = [&](uint32_t jj, uint32_t tl) -> int {
     float lo[kMaxK], hi[kMaxK];
     for (int d = 0; d < k; ++d) {
@@ -461,250 +497,339 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     }
     return widest_dim(lo, hi, k);
   };
-  // split dimension under the tight-box rule of the node whose items sit at
-  // list positions [q0, q1): each list is sorted by key within the node, so
-  // its first and last items hold the node's smallest and largest key
-  auto tight_dim = [&](uint32_t sl, uint32_t q0, uint32_t q1) -> int {
-    uint32_t lo[3], hi[3];
-    for (int d = 0; d < k; ++d) {
-      const uint16_t* list = s_lists + (size_t)slot_of(sl, d) * kLocalCap;
-      const uint4 e0 = key_of[list[q0]], e1 = key_of[list[q1 - 1]];
-      lo[d] = d == 0 ? e0.x : (d == 1 ? e0.y : e0.z);
-      hi[d] = d == 0 ? e1.x : (d == 1 ? e1.y : e1.z);
-    }
-    return widest_of_keys(lo, hi, k, a.ctype);
-  };
-  // per depth jj below the block's root (level l0 + jj): the block's layout,
-  // the round-robin split dimension and the lists read on deeper levels,
-  // computed once
+  // per depth jj below the block's root (level l0 + jj): the block's layout
+  // and the round-robin split dimension, computed once
   __shared__ Local s_lay[kLocalLog + 1];
-  __shared__ uint8_t s_drr[kLocalLog + 1], s_need[kLocalLog + 1];
+  __shared__ uint8_t s_drr[kLocalLog + 1];
+  __shared__ uint32_t s_prb[W];  // block phase: pivot rank (and size) of each node
+  __shared__ uint32_t s_szb[W];
   const int depths = tree.L - l0;  // levels l0 .. tree.L - 1
-  if (depths > kLocalLog + 1) {
+  if (depths > kLocalLog + 1 || depths < 1) {
     if (threadIdx.x == 0) atomicOr(a.err, ERR_INTERNAL);
     return;
   }
   if (threadIdx.x < (unsigned)depths) {
     const int jj = threadIdx.x, L = l0 + jj;
     s_lay[jj] = make_local(tree, L, wk.s_rel << jj, 1u << jj);
-    const int dr = L % k;
-    s_drr[jj] = (uint8_t)dr;
-    uint32_t need = bydim ? (1u << k) - 1u : 0u;
-    int md = dr + 1 == k ? 0 : dr + 1;
-    for (int q = L + 1, c = 0; q <= tree.L - 1 && c < k; ++q, ++c) {
-      need |= 1u << md;
-      md = md + 1 == k ? 0 : md + 1;
-    }
-    s_need[jj] = (uint8_t)need;
+    s_drr[jj] = (uint8_t)(L % k);
   }
+  for (uint32_t i = threadIdx.x; i < kLocalCap; i += T) {
+    if (i < m) s_tag[i] = 0;  // every item starts in the root
+    s_pin[i] = (uint16_t)kPin;
+  }
+  s_ctr[threadIdx.x] = 0;  // block counters [W][32]
   __syncthreads();
-  // Tag update of depth jj (Sec. 3.2 with Observation 1) for the segments
-  // [r.uf, r.uf + cnt) of range r: in its segment the item at rank pr (the
-  // left subtree's size) is pinned as the node, lower ranks go left, higher
-  // ranks right.  Each item gets an info word (side << 14 | offset); the
-  // offset is its position on the next level minus its rank among the
-  // range's items of the same side in list order: left items of a segment go
-  // after the right items of the range's earlier segments, right items after
-  // the left items of the earlier segments and of the segment itself.  The
-  // pivots are pinned and (clipped-domain rule) their planes recorded.  The
-  // range's items are stored from list position sb on.
-  //
-  // The `gs` threads of a group (g0 = index in the group) take whole
-  // segments: with at least as many threads as segments, 2^x threads share
-  // one segment; with fewer, each thread takes every gs-th segment.  Either
-  // way a segment's constants (start, pivot rank, next-level offsets of its
-  // two sides, from the closed forms of Sec. 4) are computed once per thread
-  // and segment, not once per item.
-  auto info_pass = [&](const Range& r, uint32_t cnt, uint32_t jj, int L, uint32_t slots, uint32_t sb,
-                       uint32_t g0, uint32_t gs) {
-    const int drr = s_drr[jj];
-    const uint32_t dbase = (1u << jj) - 1;  // local index of the first node at depth jj
-    const Local& y = r.y;
-    const uint32_t tps = gs >= cnt ? gs / cnt : 1u;  // threads per segment
-    const uint32_t u0 = gs >= cnt ? g0 / tps : g0, ustep = gs >= cnt ? cnt : gs;
-    const uint32_t t0 = gs >= cnt ? g0 % tps : 0u;
-    for (uint32_t uu = u0; uu < cnt; uu += ustep) {
-      const uint32_t tl = r.uf + uu;
-      const uint32_t st = l_start(y, tl), en = l_start(y, tl + 1);
-      uint32_t pr = 0, sl = 0;
-      if (y.h >= 1) {
-        pr = l_left(y, tl);
-        sl = l_left_before(y, tl) - r.lb0;
+
+  // The pivot of node t at depth jj: its item is recorded, its plane kept for
+  // the children's domains (clipped-domain rule).
+  auto pin = [&](uint32_t id, uint32_t jj, uint32_t t, int d) {
+    const uint32_t hn = (1u << jj) - 1 + t;
+    s_pin[hn] = (uint16_t)id;
+    if (widest)
+      s_lplane[hn] = ent_of ? __uint_as_float(key_to_float_bits(comp3(ent_of[id], d)))
+                            : coord_of(a.pts, s_orig[id], a.stride, d);
+  };
+  uint32_t slots = 0;
+  for (int q = 0; q <= k; ++q) slots |= (uint32_t)q << (4 * q);
+  auto list_of = [&](uint32_t sl, int d) -> uint16_t* {
+    return s_lists + (size_t)slot_of(sl, d) * kLocalCap;
+  };
+
+  // Block-wide pass over list `list` at depth j (at most W nodes): every item
+  // whose node splits in dimension d (every live item if d < 0) gets its
+  // rank among its node's items in the list's order -- per-warp counts of
+  // each node over contiguous chunks of the list, then for each node an
+  // exclusive prefix over the warps -- and use(id, t, rank) is called.
+  constexpr int PER = kLocalCap / T;  // positions per thread (8)
+  auto block_ranks = [&](const uint16_t* list, uint32_t j, int d, auto&& use) {
+    uint32_t* s_bc = s_ctr;           // [W][32] items per warp and node
+    uint32_t* s_bb = s_ctr + W * 32;  // [W][32] items of the node in earlier warps
+    const uint32_t nodes = 1u << j;
+    const uint32_t nb = nodes - 1;
+    const uint32_t chunk = ((m + W * 32 - 1) / (W * 32)) * 32;
+    const int rounds = (int)(chunk / 32);  // block-uniform
+    const uint32_t c0 = (uint32_t)warp * chunk;
+    uint32_t pk[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      pk[q] = 0xFFFFFFFFu;
+      if (q >= rounds) continue;
+      const uint32_t p = c0 + (uint32_t)q * 32 + lane;
+      uint32_t t = kPin, id = 0;
+      if (p < m) {
+        id = list[p];
+        t = s_tag[id];
+        if (t >= kMoved || (d >= 0 && s_ldim[nb + t] != d)) t = kPin;
       }
-      const uint32_t sr = (st - r.p0) - uu - sl;
-      const uint32_t offl = r.nb + sr, offr = r.nb + sl + pr;
-      const int d = bydim ? s_ldim[dbase + tl] : drr;
-      const uint16_t* list = s_lists + (size_t)slot_of(slots, d) * kLocalCap;
-      for (uint32_t p = st + t0; p < en; p += tps) {
-        const uint32_t q = p - st;
-        const uint32_t side = q < pr ? 0u : (q == pr ? 2u : 1u);
-        const uint32_t off = side == 0 ? offl : (side == 1 ? offr : 0u);
-        const uint32_t it = list[p - r.p0 + sb];
-        if (it >= m || off >= kLocalCap) {
-          s_bad = 1;
-          continue;
-        }
-        s_info[it] = (uint16_t)((side << 14) | off);
+      const uint32_t peers = __match_any_sync(0xffffffffu, t);
+      uint32_t before = 0;
+      if (t != kPin) before = s_bc[warp * 32 + t];
+      __syncwarp();
+      if (t != kPin) {
+        if ((peers & lt) == 0) s_bc[warp * 32 + t] = before + __popc(peers);
+        pk[q] = ((before + __popc(peers & lt)) << 18) | (t << 13) | id;
       }
-      // the group's first thread pins the segment's pivot: with one thread
-      // per segment, the lanes of a warp write consecutive nodes together
-      if (t0 == 0 && st + pr < en) {
-        const uint32_t it = list[st + pr - r.p0 + sb];
-        if (it >= m) {
-          s_bad = 1;
-          continue;
-        }
-        const uint32_t o = s_orig[it];
-        const uint32_t node = ls.off + full_nodes(L) + (wk.s_rel << jj) + tl;
-        a.perm[node] = o;
-        if (ent_of) {  // the record goes straight to its node
-          const uint4 e = ent_of[it];
-          write_record_from_entry(a.pts_out + (uint64_t)node * a.stride, e, k, a.ctype);
-          if (widest)
-            s_lplane[dbase + tl] =
-                __uint_as_float(key_to_float_bits(d == 0 ? e.x : (d == 1 ? e.y : e.z)));
-        } else if (widest) {
-          s_lplane[dbase + tl] = coord_of(a.pts, o, a.stride, d);
-        }
+      __syncwarp();
+    }
+    __syncthreads();
+    if ((uint32_t)warp < nodes) {  // warp t: node t's counts over the warps
+      const uint32_t v = s_bc[lane * 32 + warp];
+      uint32_t x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
       }
+      s_bb[lane * 32 + warp] = x - v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      if (pk[q] == 0xFFFFFFFFu) continue;
+      const uint32_t id = pk[q] & 0x1FFFu, t = (pk[q] >> 13) & 31u;
+      use(id, t, s_bb[warp * 32 + t] + (pk[q] >> 18));
+    }
+    s_bc[threadIdx.x] = 0;  // for the next pass
+    __syncthreads();
+  };
+  // tag update of one item at depth jj from its rank r in its node t
+  // (Sec. 3.2 with Observation 1): the children of block node t are 2t, 2t+1.
+  // With a split dimension per node, a depth takes one pass per dimension:
+  // the new tag is flagged so that the later passes of the depth skip it.
+  constexpr uint32_t kFlag = bydim ? kMoved : 0u;
+  auto split_item = [&](uint32_t id, uint32_t jj, uint32_t t, uint32_t r, uint32_t pr, int d) {
+    if (r < pr) s_tag[id] = (uint16_t)((2 * t) | kFlag);
+    else if (r > pr) s_tag[id] = (uint16_t)((2 * t + 1) | kFlag);
+    else {
+      s_tag[id] = (uint16_t)kPin;
+      pin(id, jj, t, d);
     }
   };
 
-  uint32_t slots = 0;
-  for (int q = 0; q <= k; ++q) slots |= (uint32_t)q << (4 * q);
-  constexpr int PER = kLocalCap / T;  // positions per thread in a block-wide partition
-
-  for (uint32_t j = 0;; ++j) {
-    const int L = l0 + (int)j;
-    if (L > tree.L - 1) break;
-    const uint32_t nodes = 1u << j;
-    const uint32_t first = wk.s_rel << j;
-    const Local& yj = s_lay[j];
-    if (nodes >= (uint32_t)W) {
-      // From here every subtree of depth j is finished by one warp.  On every
-      // later level the warp keeps its subtree's items from the subtree's
-      // start at depth j on (the set of items only shrinks), so no other
-      // warp touches them and warps need no block barrier.
-      for (uint32_t tw = warp; tw < nodes; tw += W) {
-        uint32_t wslots = slots;
-        const uint32_t sb = l_start(yj, tw);
-        for (uint32_t i = 0;; ++i) {
-          const int Li = L + (int)i;
-          if (Li > tree.L - 1) break;
-          const uint32_t jj = j + i;
-          const uint32_t firsti = wk.s_rel << jj;
-          const uint32_t cnt = 1u << i;
-          const Range r = make_range(s_lay[jj], tw << i, cnt);
-          if (r.p0 >= r.p1) break;
-          if (bydim) {
-            for (uint32_t u = lane; u < cnt; u += 32) {
-              const uint32_t tl = (tw << i) + u;
-              const uint32_t node = full_nodes(Li) + firsti + tl;
-              if (node >= tree.n) continue;
-              const int d = widest ? node_dim(jj, tl)
-                                   : tight_dim(wslots, l_start(s_lay[jj], tl) - r.p0 + sb,
-                                               l_start(s_lay[jj], tl + 1) - r.p0 + sb);
-              s_ldim[(1u << jj) - 1 + tl] = (uint8_t)d;
-              a.dims[ls.off + node] = (uint8_t)d;
-            }
-            __syncwarp();
-          }
-          info_pass(r, cnt, jj, Li, wslots, sb, lane, 32);
-          __syncwarp();
-          if (Li == tree.L - 1) break;
-          const uint32_t lim = r.nb + (r.p1 - r.p0) - cnt;  // end of the range's next-level items
-          for (int d = 0; d < k; ++d) {
-            if (!((s_need[jj] >> d) & 1u)) continue;
-            const uint16_t* src = s_lists + (size_t)slot_of(wslots, d) * kLocalCap;
-            uint16_t* dst = s_lists + (size_t)slot_of(wslots, k) * kLocalCap;
-            uint32_t cl = 0, cr = 0;
-            for (uint32_t b = r.p0; b < r.p1; b += 32) {
-              const uint32_t p = b + lane;
-              uint32_t it = 0, v = 3u << 14;
-              if (p < r.p1) {
-                it = src[p - r.p0 + sb];
-                v = s_info[it];
-              }
-              const uint32_t side = v >> 14;
-              const uint32_t bl = __ballot_sync(0xffffffffu, side == 0);
-              const uint32_t br = __ballot_sync(0xffffffffu, side == 1);
-              if (side < 2) {
-                const uint32_t np =
-                    (v & 0x3FFFu) + (side == 0 ? cl + __popc(bl & lt) : cr + __popc(br & lt));
-                if (np >= r.nb && np < lim) dst[np - r.nb + sb] = (uint16_t)it;
-                else s_bad = 1;
-              }
-              cl += __popc(bl);
-              cr += __popc(br);
-            }
-            __syncwarp();
-            wslots = swap_slots(wslots, d, k);
-          }
+  const int D = depths;
+  const int jb = D - 1 < kJW ? D - 1 : kJW;  // block phase: depths 0 .. jb-1 (the last one is leaves)
+  int jfirst = 0;
+  if (jb > 0) {
+    // depth 0: one node holds every item, so an item's rank in it is its
+    // position in the list
+    if (tight) {
+      if (threadIdx.x == 0)
+        for (int d = 0; d < k; ++d) {
+          const uint16_t* ld = list_of(slots, d);
+          tight_step(comp3(key_of[ld[0]], d), comp3(key_of[ld[m - 1]], d), d, a.ctype, &s_tbest[0],
+                     &s_ldim[0]);
         }
-      }
-      break;
-    }
-    const Range r = make_range(yj, 0, nodes);
-    const uint32_t mj = r.p1;
-    if ((widest && j > 0) || tight) {
-      for (uint32_t tl = threadIdx.x; tl < nodes; tl += T) {
-        const uint32_t node = full_nodes(L) + first + tl;
-        if (node >= tree.n) continue;
-        const int d = widest ? node_dim(j, tl) : tight_dim(slots, l_start(yj, tl), l_start(yj, tl + 1));
-        s_ldim[(1u << j) - 1 + tl] = (uint8_t)d;
-        a.dims[ls.off + node] = (uint8_t)d;
-      }
       __syncthreads();
     }
-    info_pass(r, nodes, j, L, slots, 0, threadIdx.x, T);
+    const int d0 = bydim ? (int)s_ldim[0] : (int)s_drr[0];
+    const uint32_t pr0 = l_left(s_lay[0], 0);
+    const uint16_t* ld = list_of(slots, d0);
+    for (uint32_t p = threadIdx.x; p < m; p += T) {
+      const uint32_t id = ld[p];
+      if (p < pr0) s_tag[id] = 0;
+      else if (p > pr0) s_tag[id] = 1;
+      else {
+        s_tag[id] = (uint16_t)kPin;
+        pin(id, 0, 0, d0);
+      }
+    }
     __syncthreads();
-    if (L == tree.L - 1) break;  // lowest level: every item was pinned
-    const uint32_t mn = mj - nodes;
-    // stable partition of every list still needed into the next level's
-    // order: each warp ranks a contiguous chunk with ballots, one block
-    // exchange of the warps' counts, then every item is written
-    const uint32_t chunk = ((mj + W * 32 - 1) / (W * 32)) * 32;
+    jfirst = 1;
+  }
+  for (int j = jfirst; j < jb; ++j) {
+    const Local& y = s_lay[j];
+    const uint32_t nodes = 1u << j, nb = nodes - 1;
+    if (threadIdx.x < nodes) {
+      s_prb[threadIdx.x] = l_left(y, threadIdx.x);
+      s_szb[threadIdx.x] = l_start(y, threadIdx.x + 1) - l_start(y, threadIdx.x);
+      if (widest && j > 0) s_ldim[nb + threadIdx.x] = (uint8_t)node_dim(j, threadIdx.x);
+    }
+    __syncthreads();
+    if (tight) {
+      // the box of every node: in list d its first and last items hold its
+      // smallest and largest key_d
+      for (int d = 0; d < k; ++d) {
+        block_ranks(list_of(slots, d), j, -1, [&](uint32_t id, uint32_t t, uint32_t r) {
+          if (r == 0) s_tlo[t] = (uint16_t)id;
+          if (r + 1 == s_szb[t]) s_thi[t] = (uint16_t)id;
+        });
+        if (threadIdx.x < nodes)
+          tight_step(comp3(key_of[s_tlo[threadIdx.x]], d), comp3(key_of[s_thi[threadIdx.x]], d), d,
+                     a.ctype, &s_tbest[threadIdx.x], &s_ldim[nb + threadIdx.x]);
+        __syncthreads();
+      }
+    }
     for (int d = 0; d < k; ++d) {
-      if (!((s_need[j] >> d) & 1u)) continue;
-      const uint16_t* src = s_lists + (size_t)slot_of(slots, d) * kLocalCap;
-      uint16_t* dst = s_lists + (size_t)slot_of(slots, k) * kLocalCap;
-      uint32_t its[PER], vs[PER];
-      uint32_t cl = 0, cr = 0;
-      const uint32_t c0 = (uint32_t)warp * chunk;
-      const int rounds = (int)(chunk / 32);  // block-uniform
-#pragma unroll
-      for (int q = 0; q < PER; ++q) {
-        if (q >= rounds) break;
-        const uint32_t p = c0 + (uint32_t)q * 32 + lane;
-        uint32_t it = 0, v = 3u << 14;
-        if (p < mj) {
-          it = src[p];
-          v = s_info[it];
-        }
-        const uint32_t side = v >> 14;
-        const uint32_t bl = __ballot_sync(0xffffffffu, side == 0);
-        const uint32_t br = __ballot_sync(0xffffffffu, side == 1);
-        const uint32_t rank = side == 0 ? cl + __popc(bl & lt) : cr + __popc(br & lt);
-        its[q] = it | (rank << 16);
-        vs[q] = v;
-        cl += __popc(bl);
-        cr += __popc(br);
+      if (!bydim && d != s_drr[j]) continue;
+      block_ranks(list_of(slots, d), j, bydim ? d : -1, [&](uint32_t id, uint32_t t, uint32_t r) {
+        split_item(id, j, t, r, s_prb[t], d);
+      });
+    }
+    if (bydim) {  // clear the flags of the depth
+      for (uint32_t id = threadIdx.x; id < m; id += T) {
+        const uint32_t t = s_tag[id];
+        if (t != kPin) s_tag[id] = (uint16_t)(t & ~kMoved);
       }
-      if (lane == 0) s_w[warp] = cl | (cr << 16);
       __syncthreads();
-      const uint32_t before = __reduce_add_sync(0xffffffffu, lane < warp ? s_w[lane] : 0u);
-      const uint32_t wl = before & 0xFFFFu, wr = before >> 16;
-#pragma unroll
-      for (int q = 0; q < PER; ++q) {
-        if (q >= rounds) break;
-        const uint32_t side = vs[q] >> 14;
-        if (side > 1) continue;
-        const uint32_t np = (vs[q] & 0x3FFFu) + (side == 0 ? wl : wr) + (its[q] >> 16);
-        if (np < mn) dst[np] = (uint16_t)(its[q] & 0xFFFFu);
+    }
+  }
+
+  if (D - 1 > kJW) {
+    // every list read on a warp depth is split into the runs of the 32 nodes
+    // of depth kJW, in the layout of that depth (pinned items dropped)
+    uint32_t need = bydim ? (1u << k) - 1u : 0u;
+    if (!bydim)
+      for (int jj = kJW; jj < D - 1; ++jj) need |= 1u << s_drr[jj];
+    const Local& y5 = s_lay[kJW];
+    for (int d = 0; d < k; ++d) {
+      if (!((need >> d) & 1u)) continue;
+      uint16_t* dst = list_of(slots, k);
+      block_ranks(list_of(slots, d), kJW, -1, [&](uint32_t id, uint32_t t, uint32_t r) {
+        const uint32_t pos = l_start(y5, t) + r;
+        if (pos < kLocalCap) dst[pos] = (uint16_t)id;
         else s_bad = 1;
-      }
-      __syncthreads();
+      });
       slots = swap_slots(slots, d, k);
+    }
+    // warp phase: warp w finishes node w of depth kJW
+    const uint32_t wb = l_start(y5, warp), we = l_start(y5, warp + 1);
+    // per node of the warp: pivot rank << 16 | items counted so far
+    uint32_t* wc = s_ctr + warp * kWT;
+    // One warp's pass over its run of list `list` at depth jj: every item
+    // whose node splits in dimension d (all if d < 0) gets its rank among its
+    // node's items in list order (the warp holds all of them, so a running
+    // count per node is the rank).
+    // (each item is in the run once, so reading the next round's item and
+    // tag ahead of this round's tag updates reads nothing they write)
+    auto warp_ranks = [&](const uint16_t* list, uint32_t jj, uint32_t tb, int d, auto&& use) {
+      const uint32_t nb = (1u << jj) - 1, nloc = 1u << (jj - kJW);
+      uint32_t nid = 0, ntag = kPin;
+      if (wb + lane < we) {
+        nid = list[wb + lane];
+        ntag = s_tag[nid];
+      }
+      for (uint32_t b = wb; b < we; b += 32) {
+        const uint32_t id = nid, t = ntag;
+        ntag = kPin;
+        if (b + 32 + lane < we) {
+          nid = list[b + 32 + lane];
+          ntag = s_tag[nid];
+        }
+        uint32_t u = kPin;
+        if (t < kMoved && (d < 0 || s_ldim[nb + t] == d)) u = t - tb;
+        if (u != kPin && u >= nloc) {  // not this warp's: inconsistent lists
+          s_bad = 1;
+          u = kPin;
+        }
+        const uint32_t peers = __match_any_sync(0xffffffffu, u);
+        uint32_t w = 0;
+        if (u != kPin) w = wc[u];
+        __syncwarp();
+        if (u != kPin) {
+          if ((peers & lt) == 0) wc[u] = w + __popc(peers);
+          use(id, u, (w & 0xFFFFu) + __popc(peers & lt), w >> 16);
+        }
+        __syncwarp();
+      }
+    };
+    for (int jj = kJW; jj < D - 1; ++jj) {
+      const Local& y = s_lay[jj];
+      const uint32_t i = (uint32_t)(jj - kJW), nloc = 1u << i, tb = (uint32_t)warp << i;
+      const uint32_t nb = (1u << jj) - 1;
+      if (nloc > (uint32_t)kWT) {
+        s_bad = 1;
+        break;
+      }
+      for (uint32_t u = lane; u < nloc; u += 32) {
+        wc[u] = l_left(y, tb + u) << 16;
+        if (widest) s_ldim[nb + tb + u] = (uint8_t)node_dim(jj, tb + u);
+      }
+      __syncwarp();
+      if (tight) {
+        for (int d = 0; d < k; ++d) {
+          warp_ranks(list_of(slots, d), jj, tb, -1, [&](uint32_t id, uint32_t u, uint32_t r, uint32_t) {
+            const uint32_t t = tb + u;
+            if (r == 0) s_tlo[t] = (uint16_t)id;
+            if (r + 1 == l_start(y, t + 1) - l_start(y, t)) s_thi[t] = (uint16_t)id;
+          });
+          for (uint32_t u = lane; u < nloc; u += 32) {
+            const uint32_t t = tb + u;
+            tight_step(comp3(key_of[s_tlo[t]], d), comp3(key_of[s_thi[t]], d), d, a.ctype, &s_tbest[t],
+                       &s_ldim[nb + t]);
+            wc[u] &= 0xFFFF0000u;
+          }
+          __syncwarp();
+        }
+      }
+      for (int d = 0; d < k; ++d) {
+        if (!bydim && d != s_drr[jj]) continue;
+        warp_ranks(list_of(slots, d), jj, tb, bydim ? d : -1,
+                   [&](uint32_t id, uint32_t u, uint32_t r, uint32_t pr) { split_item(id, jj, tb + u, r, pr, d); });
+      }
+      if (bydim) {  // clear the flags of the warp's items
+        const uint16_t* l0s = list_of(slots, 0);
+        for (uint32_t p = wb + lane; p < we; p += 32) {
+          const uint32_t id = l0s[p], t = s_tag[id];
+          if (t != kPin) s_tag[id] = (uint16_t)(t & ~kMoved);
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+  // the lowest depth: every item left is a leaf, its node is its tag
+  {
+    const uint32_t nb = (1u << (D - 1)) - 1, nodes = 1u << (D - 1);
+    for (uint32_t id = threadIdx.x; id < m; id += T) {
+      const uint32_t t = s_tag[id];
+      if (t == kPin) continue;
+      if (t < nodes) s_pin[nb + t] = (uint16_t)id;
+      else s_bad = 1;
+    }
+  }
+  __syncthreads();
+  // every node of the block's subtree, in heap order (block node q is depth
+  // jj = level(q), index q + 1 - 2^jj there): consecutive threads write
+  // consecutive nodes (perm, the record, the split dimension); each thread
+  // reads what four nodes need before it writes, so that the reads are in
+  // flight together
+  {
+    const uint32_t hnodes = (1u << D) - 1;
+    for (uint32_t q0 = threadIdx.x; q0 < hnodes; q0 += 4 * T) {
+      uint32_t node[4], o[4], dd[4];
+      uint4 e[4];
+      bool ok[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint32_t q = q0 + (uint32_t)r * T;
+        ok[r] = false;
+        if (q >= hnodes) continue;
+        const int jj = level_of(q);
+        const uint32_t t = q + 1 - (1u << jj);
+        const uint32_t first = full_nodes(l0 + jj) + (wk.s_rel << jj);  // the depth's first node
+        if (first + t >= tree.n) continue;
+        const uint32_t id = s_pin[q];
+        if (id >= m) {
+          s_bad = 1;
+          continue;
+        }
+        ok[r] = true;
+        node[r] = ls.off + first + t;
+        o[r] = s_orig[id];
+        if (ent_of) e[r] = ent_of[id];
+        if (bydim) {
+          if (jj + 1 < D) dd[r] = s_ldim[q];
+          else if (widest) dd[r] = jj == 0 ? s_ldim[0] : (uint32_t)node_dim(jj, t);
+          else dd[r] = 0;  // tight box of a leaf: one point, every extent 0
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (!ok[r]) continue;
+        a.perm[node[r]] = o[r];
+        if (ent_of) write_record_from_entry(a.pts_out + (uint64_t)node[r] * a.stride, e[r], k, a.ctype);
+        if (bydim) a.dims[node[r]] = (uint8_t)dd[r];
+      }
     }
   }
   __syncthreads();
