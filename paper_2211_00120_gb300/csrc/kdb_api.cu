@@ -749,6 +749,12 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     pa.wait_epoch = c.wait_epoch;
     pa.wait_ns = c.wait_ns;
     pa.status_words = c.status_words;
+    if (P.sets.size() == 1) {
+      pa.single = 1;
+      pa.set0 = P.sets[0];
+      pa.act0 = P.act[p][0];
+      pa.out_base0 = q < levels ? P.act[q][0].base : 0u;
+    }
     // algorithmic bytes: every item of level p read once; the survivors
     // written as entries, or (hand-over) as original indices, list 0 as
     // entries when it is handed over whole

@@ -116,6 +116,11 @@ struct PartArgs {
   uint32_t epoch, wait_epoch;
   uint64_t wait_ns;
   uint64_t status_words;    // capacity of status
+  // one set (single = 1): its tables, so that a tile's setup reads no memory
+  int single;
+  SetInfo set0;
+  ActiveEntry act0;         // the set's entry on level p
+  uint32_t out_base0;       // the set's first position in the list on level p + b
 };
 size_t partition_smem(int shape);
 size_t rec_sort_smem(int shape);

@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(RT, RB)
     const bool ok = p < tn;
     uint32_t bin = BINS;
     if (ok) bin = ((p >= bpos) ? (uint32_t)kRadix : 0u) | ((comp(s_rec[p], d) >> c.shift) & 255u);
-    const uint32_t peers = __match_any_sync(0xffffffffu, bin);
+    const uint32_t peers = warp_peers(bin, ok, 9);  // (segment, digit): 9 bits
     uint32_t before = 0;
     if (ok) before = s_whist[warp * BINS + bin];
     __syncwarp();

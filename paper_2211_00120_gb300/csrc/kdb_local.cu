@@ -130,7 +130,7 @@ __device__ uint16_t* smem_radix_sort(uint32_t* ka, uint16_t* ia, uint32_t* kb, u
       const bool ok = i < m;
       key[r] = ok ? ka[i] : 0u;
       const uint32_t d = ok ? (key[r] >> shift) & 255u : 256u;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t peers = warp_peers(d, ok, 8);
       uint32_t before = 0;
       if (ok) before = s_wh[d * W + w];
       __syncwarp();

@@ -111,22 +111,48 @@ struct LiftSeg {
   int mode;                    // 0: next level's list, 1: original indices for the local finish
 };
 
+// The segment holding position j of level p, with its bounds (the set's
+// tables from the arguments for a single set, else from the active list).
+__device__ inline void part_segment_at(const PartArgs& a, uint32_t j, uint32_t* ai, uint32_t* srel,
+                                       uint32_t* start, uint32_t* end) {
+  if (!a.single) {
+    segment_at(a.x, j, ai, srel, start, end);
+    return;
+  }
+  const LevelLayout y = LevelLayout::make(make_tree(a.set0.n), a.x.l);
+  const uint32_t s = y.seg_of(j - a.act0.base);
+  *ai = 0;
+  *srel = s;
+  *start = a.act0.base + y.seg_start(s);
+  *end = a.act0.base + y.seg_start(s + 1);
+}
+
+// One segment's setup, by the 16 lanes hl = 0..15 of a half warp: lanes
+// 0..7 the first output position of each descendant's run, lanes 8..14 the
+// pivots (and split dimensions) of the segment's first b levels, lane 0 the
+// rest; the pivot loads are issued side by side.
 __device__ inline void lift_seg_info(const PartArgs& a, uint32_t ai, uint32_t srel, uint32_t start,
-                                     LiftSeg* ps) {
+                                     LiftSeg* ps, uint32_t hl) {
   const LevelCtx& x = a.x;
-  const ActiveEntry e = x.act[ai];
-  const SetInfo si = x.sets[e.set];
+  const ActiveEntry e = a.single ? a.act0 : x.act[ai];
+  const SetInfo si = a.single ? a.set0 : x.sets[e.set];
   const Tree tree = make_tree(si.n);
-  ps->start = start;
-  ps->mode = (a.handoff || e.next < 0) ? 1 : 0;
-  uint32_t base_out;
-  if (ps->mode == 1) base_out = si.off;
-  else base_out = a.act_out[a.b == 1 ? (uint32_t)e.next : 0u].base;
-  ps->left0 = LevelLayout::make(tree, x.l).left_size(srel);
-  const LevelLayout yo = LevelLayout::make(tree, x.l + a.b);
+  const int mode = (a.handoff || e.next < 0) ? 1 : 0;
   const uint32_t nb = 1u << a.b;
-  for (uint32_t c = 0; c < nb; ++c) ps->cs[c] = base_out + yo.seg_start((srel << a.b) + c);
-  for (uint32_t h = 0; h + 1 < nb; ++h) {
+  if (hl == 0) {
+    ps->start = start;
+    ps->mode = mode;
+    ps->left0 = LevelLayout::make(tree, x.l).left_size(srel);
+  }
+  if (hl < nb) {
+    uint32_t base_out;
+    if (mode == 1) base_out = si.off;
+    else base_out = a.single ? a.out_base0 : a.act_out[a.b == 1 ? (uint32_t)e.next : 0u].base;
+    const LevelLayout yo = LevelLayout::make(tree, x.l + a.b);
+    ps->cs[hl] = base_out + yo.seg_start((srel << a.b) + hl);
+  }
+  if (hl >= kLiftBins && hl - kLiftBins + 1 < nb) {
+    const uint32_t h = hl - kLiftBins;
     const int e2 = 31 - __clz(h + 1);  // depth of heap node h below the segment
     const uint32_t rel = (srel << e2) + (h + 1 - (1u << e2));
     const int lq = x.l + e2;
@@ -210,40 +236,52 @@ __global__ void __launch_bounds__(PT, PB) partition_kernel(PartArgs a) {
   __shared__ uint32_t s_wcnt[PW][NB];  // per warp and bin: items, then exclusive offsets
   __shared__ uint32_t s_tcnt[NB];      // tile totals per bin
   __shared__ uint32_t s_prefA[kLiftBins];
+  __shared__ uint32_t s_wbase[PW][NB];  // per warp and bin: first output position
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const LevelCtx& x = a.x;
   const int nbin = 1 << a.b;
-  if (tid == 0) {
-    s_abort = *reinterpret_cast<volatile uint32_t*>(x.err) != 0u;
-    if (!s_abort) {
-      s_tile = atomicAdd(a.ticket, 1u);
-      if ((uint64_t)(s_tile + 1) * kLiftBins > a.status_words) {  // the last tiles: no tile waits on them
-        atomicOr(x.err, ERR_INTERNAL);
-        s_abort = 1;
+  // tile setup by warp 0: lane 0 takes the ticket and issues the bulk copy,
+  // then the two half warps fill in segments A and B side by side (B = A
+  // when the tile lies in one segment)
+  if (warp == 0) {
+    uint32_t tile = 0, ab = 0;
+    if (lane == 0) {
+      ab = *reinterpret_cast<volatile uint32_t*>(x.err) != 0u;
+      if (!ab) {
+        tile = atomicAdd(a.ticket, 1u);
+        if ((uint64_t)(tile + 1) * kLiftBins > a.status_words) {  // the last tiles: no tile waits on them
+          atomicOr(x.err, ERR_INTERNAL);
+          ab = 1;
+        }
       }
     }
-    if (!s_abort) {
-      const uint32_t tile = s_tile;
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    ab = __shfl_sync(0xffffffffu, ab, 0);
+    if (!ab) {
       const uint32_t tb = tile * (uint32_t)PTILE;
       const uint32_t tn = a.n - tb < (uint32_t)PTILE ? a.n - tb : (uint32_t)PTILE;
-      mbar_init(&s_bar, 1);
-      mbar_expect_tx(&s_bar, tn * 16u);
-      bulk_g2s(s_in, a.in + tb, tn * 16u, &s_bar);
-      uint32_t ai, sr, st, en;
-      segment_at(x, tb, &ai, &sr, &st, &en);
-      lift_seg_info(a, ai, sr, st, &s_seg[0]);
-      s_acont = st < tb;
-      s_bpos = tn;
-      if (en < tb + tn) {
-        uint32_t a2, s2, st2, en2;
-        segment_at(x, en, &a2, &s2, &st2, &en2);
-        lift_seg_info(a, a2, s2, st2, &s_seg[1]);
-        s_bpos = en - tb;
-        if (en2 < tb + tn) s_abort = 2;  // a segment shorter than a tile: not allowed
-      } else {
-        s_seg[1] = s_seg[0];
+      if (lane == 0) {
+        mbar_init(&s_bar, 1);
+        mbar_expect_tx(&s_bar, tn * 16u);
+        bulk_g2s(s_in, a.in + tb, tn * 16u, &s_bar);
       }
+      uint32_t ai, sr, st, en;
+      part_segment_at(a, tb, &ai, &sr, &st, &en);
+      const bool hasB = en < tb + tn;
+      uint32_t a2 = ai, s2 = sr, st2 = st, en2 = en;
+      if (hasB) part_segment_at(a, en, &a2, &s2, &st2, &en2);
+      const uint32_t half = (uint32_t)lane >> 4;
+      lift_seg_info(a, half ? a2 : ai, half ? s2 : sr, half ? st2 : st, &s_seg[half], (uint32_t)lane & 15u);
+      if (lane == 0) {
+        s_acont = st < tb;
+        s_bpos = hasB ? en - tb : tn;
+        if (hasB && en2 < tb + tn) ab = 2;  // a segment shorter than a tile: not allowed
+      }
+    }
+    if (lane == 0) {
+      s_tile = tile;
+      s_abort = ab;
     }
   }
   for (int i = tid; i < PW * NB; i += PT) (&s_wcnt[0][0])[i] = 0;
@@ -359,22 +397,29 @@ __global__ void __launch_bounds__(PT, PB) partition_kernel(PartArgs a) {
   }
   __syncthreads();
   if (s_abort) return;
+  // where each warp's items of each bin start in the output: the child's
+  // run, the earlier tiles' items of the child (segment A), the earlier warps'
+  for (int i = tid; i < PW * NB; i += PT) {
+    const int w = i / NB, bin = i % NB, sg = bin / kLiftBins, c = bin % kLiftBins;
+    s_wbase[w][bin] = s_seg[sg].cs[c] + (sg ? 0u : s_prefA[c]) + s_wcnt[w][bin];
+  }
+  const int modeA = s_seg[0].mode, modeB = s_seg[1].mode;
+  __syncthreads();
 
   // write every child's run in order
 #pragma unroll
   for (int i = 0; i < PI; ++i) {
     const uint32_t bin = bins[i];
     if (bin >= NB) continue;
-    const uint32_t sg = bin / kLiftBins, c = bin % kLiftBins;
-    const LiftSeg& S = s_seg[sg];
-    const uint32_t pos = S.cs[c] + (sg ? 0u : s_prefA[c]) + s_wcnt[warp][bin] + rnk[i];
-    const uint32_t lim = S.mode == 0 ? a.next_items : a.total;
+    const int mode = bin >= (uint32_t)kLiftBins ? modeB : modeA;
+    const uint32_t pos = s_wbase[warp][bin] + rnk[i];
+    const uint32_t lim = mode == 0 ? a.next_items : a.total;
     if (pos >= lim) {
       atomicOr(x.err, ERR_INTERNAL);
       continue;
     }
     const uint4 en = s_in[wbase + i * 32 + lane];
-    if (S.mode == 0) a.out_next[pos] = en;
+    if (mode == 0) a.out_next[pos] = en;
     else if (a.out_lents && a.dlist == 0) a.out_lents[pos] = en;
     else a.out_lorig[(size_t)a.dlist * a.total + pos] = en.w;
   }
