@@ -36,21 +36,24 @@ cudaError_t ensure_smem(const void* func, size_t bytes);
 // number of resident blocks per SM.  Each kernel is compiled for a few
 // measured shapes; the autotuner (kdb_autotune) times them on a problem and
 // keeps the fastest, shape 0 being the default.  Measured at 1e8 float3
-// round robin: partition 256 x 13 at four blocks per SM 11.1 ms, 512 x 13 at
-// two 11.1 ms, 128 x 13 at eight 12.2 ms; record sort 256 x 13 at three
-// 11.7 ms, 256 x 9 at four 11.9 ms.
+// round robin (record sort ranking by ballots, partition tiles set up by
+// warp 0): partition 256 x 13 at four blocks per SM 10.47 ms, 512 x 13 at two
+// 10.74 ms; record sort 256 x 13 at three 10.30 ms, 512 x 8 at two 10.42 ms,
+// 384 x 11 at two 10.52 ms, 256 x 16 at two 11.65 ms, 256 x 9 at four
+// 12.87 ms.
 struct TileShape {
   int threads, items, blocks;
 };
 constexpr int kPartShapes = 3;
 constexpr TileShape kPartShape[kPartShapes] = {{256, 13, 4}, {512, 13, 2}, {128, 13, 8}};
 constexpr int kRecShapes = 2;
-constexpr TileShape kRecShape[kRecShapes] = {{256, 13, 3}, {256, 9, 4}};
+constexpr TileShape kRecShape[kRecShapes] = {{256, 13, 3}, {512, 8, 2}};
 // smallest tile of each kernel: the look-back buffers are sized for it.  A
 // partition tile stays below 2^13 - 1 entries, so it holds at most two
 // segments of a global level.
 constexpr int kPartTile = 128 * 13;
-constexpr int kRecTileMin = 256 * 9;
+constexpr int kRecTileMin = 256 * 13;
+static_assert(kRecTileMin <= 512 * 8, "the smallest record-sort tile");
 static_assert(512 * 13 < (1 << 13) - 1, "partition tiles hold at most two segments");
 struct ListBuildArgs {      // level-0 array of several sets
   LevelCtx x;               // level 0

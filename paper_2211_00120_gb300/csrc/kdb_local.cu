@@ -321,32 +321,62 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     }
     for (uint32_t i = threadIdx.x; i < 2 * kLocalCap; i += T) s_hkey[i] = 0xFFFFFFFFu;
     __syncthreads();
+    // Inserts in rounds, without atomics: every pending item writes its key
+    // into the first empty slot it sees from its probe position on; after a
+    // barrier the item whose key is in the slot owns it, the others move on
+    // to the next slot.  A slot owned in an earlier round is never empty
+    // again, so no owner is displaced.
+    uint32_t hh[PER];
+    uint32_t pend = 0;
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
       const uint32_t i = threadIdx.x + (uint32_t)r * T;
+      hh[r] = 0;
       if (i >= m) continue;
-      uint32_t o = ov[0][r];
-      if (o >= a.total) {
+      if (ov[0][r] >= a.total) {
         s_bad = 1;
-        o = 0;
+        ov[0][r] = 0;
       }
-      s_orig[i] = o;
+      s_orig[i] = ov[0][r];
       s_lists[i] = (uint16_t)i;
-      uint32_t h = (o * 0x9E3779B1u) >> (32 - (kLocalLog + 1));
-      bool done = false;
-      for (uint32_t probe = 0; probe <= HM && !done; ++probe) {
-        const uint32_t prev = atomicCAS(&s_hkey[h], 0xFFFFFFFFu, o);
-        if (prev == 0xFFFFFFFFu) {
-          s_hval[h] = (uint16_t)i;
-          done = true;
-        } else if (prev == o) {
-          break;  // an original index twice: corrupt input lists
-        }
-        h = (h + 1) & HM;
-      }
-      if (!done) s_bad = 1;
+      hh[r] = (ov[0][r] * 0x9E3779B1u) >> (32 - (kLocalLog + 1));
+      pend |= 1u << r;
     }
+    for (int round = 0; round < 64; ++round) {
+#pragma unroll
+      for (int r = 0; r < PER; ++r) {
+        if (!((pend >> r) & 1u)) continue;
+        uint32_t h = hh[r];
+        for (uint32_t probe = 0; probe <= HM; ++probe) {
+          const uint32_t key = s_hkey[h];
+          if (key == 0xFFFFFFFFu) break;
+          if (key == ov[0][r]) s_bad = 1;  // the key is owned already: an original index twice
+          h = (h + 1) & HM;
+        }
+        hh[r] = h;
+        s_hkey[h] = ov[0][r];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < PER; ++r) {
+        if (!((pend >> r) & 1u)) continue;
+        if (s_hkey[hh[r]] == ov[0][r]) {
+          s_hval[hh[r]] = (uint16_t)(threadIdx.x + (uint32_t)r * T);
+          pend &= ~(1u << r);
+        } else {
+          hh[r] = (hh[r] + 1) & HM;
+        }
+      }
+      if (!__syncthreads_or(pend != 0u)) break;
+    }
+    if (pend) s_bad = 1;
     __syncthreads();
+    // an original index twice (corrupt input lists): two items own one slot
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const uint32_t i = threadIdx.x + (uint32_t)r * T;
+      if (i < m && s_hval[hh[r]] != (uint16_t)i) s_bad = 1;
+    }
 #pragma unroll
     for (int d = 1; d < 3; ++d) {
       if (d >= k) break;
