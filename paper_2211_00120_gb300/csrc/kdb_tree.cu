@@ -159,6 +159,83 @@ __global__ void __launch_bounds__(kThreads) prepass_kernel(PrepassArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// The same prepass for the presorted-list path of one set with records of at
+// most 16 bytes (k <= 3, payload allowed): each thread takes groups of four consecutive
+// records, read as SW 16-byte words (SW = stride / 4, the group starts on a
+// 16-byte boundary), two groups in flight, and writes their four entries.
+// Records outside whole groups (the range's ragged ends) are done one by one.
+template <int SW>
+__device__ inline void prepass_record(const PrepassArgs& a, uint32_t i, const uint32_t* w, uint32_t* lo,
+                                      uint32_t* hi, bool* nan) {
+  uint32_t ek[3] = {0u, 0u, 0u};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (d >= a.k) break;
+    const uint32_t bits = w[d];
+    if (!a.ctype && (bits & 0x7FFFFFFFu) > 0x7F800000u) *nan = true;
+    const uint32_t key = coord_key(bits, a.ctype);
+    ek[d] = key;
+    lo[d] = min(lo[d], key);
+    hi[d] = max(hi[d], key);
+  }
+  a.ents[i] = make_uint4(ek[0], ek[1], ek[2], i);
+}
+
+template <int SW>
+__global__ void __launch_bounds__(kThreads) prepass_vec_kernel(PrepassArgs a) {
+  const uint32_t r0 = a.end ? a.beg : 0u, r1 = a.end ? a.end : a.total;
+  const uint32_t g0 = (r0 + 3u) / 4u, g1 = r1 / 4u;  // whole groups inside [r0, r1)
+  uint32_t lo[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, hi[3] = {0u, 0u, 0u};
+  bool nan = false;
+  const uint32_t nthreads = gridDim.x * blockDim.x;
+  const uint4* src = reinterpret_cast<const uint4*>(a.pts);
+  for (uint32_t g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g < g1; g += 2u * nthreads) {
+    const uint32_t g2 = g + nthreads;
+    uint4 va[SW], vb[SW];
+#pragma unroll
+    for (int q = 0; q < SW; ++q) va[q] = src[(uint64_t)g * SW + q];
+    if (g2 < g1) {
+#pragma unroll
+      for (int q = 0; q < SW; ++q) vb[q] = src[(uint64_t)g2 * SW + q];
+    }
+    const uint32_t* wa = reinterpret_cast<const uint32_t*>(va);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) prepass_record<SW>(a, 4u * g + j, wa + j * SW, lo, hi, &nan);
+    if (g2 < g1) {
+      const uint32_t* wb = reinterpret_cast<const uint32_t*>(vb);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) prepass_record<SW>(a, 4u * g2 + j, wb + j * SW, lo, hi, &nan);
+    }
+  }
+  // the ragged ends, by the first block
+  if (blockIdx.x == 0) {
+    const uint32_t h1 = min(4u * g0, r1), t0 = max(4u * g1, h1);
+    for (uint32_t i = r0 + threadIdx.x; i < h1; i += blockDim.x) {
+      uint32_t w[4];
+      for (int d = 0; d < a.k; ++d) w[d] = reinterpret_cast<const uint32_t*>(a.pts)[(uint64_t)i * SW + d];
+      prepass_record<SW>(a, i, w, lo, hi, &nan);
+    }
+    for (uint32_t i = t0 + threadIdx.x; i < r1; i += blockDim.x) {
+      uint32_t w[4];
+      for (int d = 0; d < a.k; ++d) w[d] = reinterpret_cast<const uint32_t*>(a.pts)[(uint64_t)i * SW + d];
+      prepass_record<SW>(a, i, w, lo, hi, &nan);
+    }
+  }
+  if (a.bbox) {
+    const int lane = threadIdx.x & 31;
+    for (int d = 0; d < a.k; ++d) {
+      const uint32_t l = __reduce_min_sync(0xffffffffu, lo[d]);
+      const uint32_t h = __reduce_max_sync(0xffffffffu, hi[d]);
+      if (lane == 0 && l <= h) {
+        atomicMin(a.bbox + d, l);
+        atomicMax(a.bbox + a.k + d, h);
+      }
+    }
+  }
+  if (nan) atomicOr(a.err, ERR_NAN);
+}
+
+// ---------------------------------------------------------------------------
 // Key of every item of level l: (active set, subtree, rank of the item in the
 // subtree's split dimension).  The subtree of an item is implied by its
 // position in the compacted array (Observation 3 / Sec. 4.2 inverted), so no
@@ -593,6 +670,21 @@ __global__ void validate_kernel(const unsigned char* pts, uint32_t n, int k, int
 cudaError_t launch_prepass(const PrepassArgs& a, int num_sms, cudaStream_t st) {
   const uint32_t count = a.end ? a.end - a.beg : a.total;
   if (count == 0) return cudaSuccess;
+  // one set, entries only, records of 4k <= 16 bytes on a 16-byte boundary:
+  // the vectorised prepass
+  if (a.ents && !a.hist && !a.keys32 && !a.keys64 && a.nsets == 1 && a.k <= 3 && a.stride <= 16 &&
+      a.stride % 4 == 0 && 4 * a.k <= a.stride && (reinterpret_cast<uintptr_t>(a.pts) & 15u) == 0) {
+    uint32_t grid = (uint32_t)num_sms * 8;
+    const uint32_t need = (count / 4 + 2 * kThreads - 1) / (2 * kThreads);
+    if (grid > need) grid = need > 0 ? need : 1;
+    switch (a.stride / 4) {
+      case 1: prepass_vec_kernel<1><<<grid, kThreads, 0, st>>>(a); break;
+      case 2: prepass_vec_kernel<2><<<grid, kThreads, 0, st>>>(a); break;
+      case 3: prepass_vec_kernel<3><<<grid, kThreads, 0, st>>>(a); break;
+      default: prepass_vec_kernel<4><<<grid, kThreads, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+  }
   const size_t smem = a.hist ? (size_t)a.k * a.passes * kRadixBins * sizeof(uint32_t) : 0;
   cudaError_t e = ensure_smem((const void*)prepass_kernel, smem);
   if (e != cudaSuccess) return e;
