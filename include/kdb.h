@@ -114,6 +114,32 @@ KDB_API kdb_status kdb_build(void* d_points, int64_t n, int k, int stride_bytes,
                      kdb_stream_t stream);
 
 /*
+ * kdb_build_subtree -- build the subtree below one node of a larger tree, in
+ * place, in the subtree's own level order (its root at record 0, children of
+ * record i at 2i+1 and 2i+2).  A subtree of a left-balanced complete tree is
+ * itself one (Sec. 2, Observation 3), so this is kdb_build with the split
+ * rule continued from the node: used by the sharded single-tree build, where
+ * the top levels are split across GPUs and each GPU builds one subtree.
+ *   d_points, n, k, stride_bytes, mode: as for kdb_build.  Ties are broken
+ *                 by the records' order in d_points, so the caller passes them
+ *                 in ascending original index.
+ *   first_dim     round robin: the subtree's root splits in dimension
+ *                 first_dim and level l below it in (first_dim + l) mod k
+ *                 (the root's depth in the larger tree, mod k); 0 <= first_dim
+ *                 < k; ignored by the other rules.
+ *   h_root_domain host, 2k floats (lower corner, then upper corner): the
+ *                 root's domain, the scene box clipped by the planes of its
+ *                 ancestors (Sec. 6); required by KDB_SPLIT_WIDEST_EXTENT,
+ *                 ignored by the other rules (the tight box needs no input).
+ *   d_out_orig_index device int32[N] or NULL: position in d_points (on entry)
+ *                 of the record that ends up at each node.
+ * Synchronises `stream`; errors as for kdb_build.
+ */
+KDB_API kdb_status kdb_build_subtree(void* d_points, int64_t n, int k, int stride_bytes,
+                                     kdb_split_mode mode, int first_dim, const float* h_root_domain,
+                                     int32_t* d_out_orig_index, kdb_stream_t stream);
+
+/*
  * kdb_workspace_size -- bytes of device workspace kdb_build_ex needs for
  * this problem (0 for N <= 1).  Returns 0 for invalid arguments too.
  */
@@ -221,6 +247,68 @@ KDB_API kdb_status kdb_build_host(void* h_points, int64_t n, int k, int stride_b
 #define KDB_NOALLOC_SCRATCH_BYTES (64u << 20)
 KDB_API kdb_status kdb_build_noalloc(void* d_points, int64_t n, int k, int stride_bytes,
                                      kdb_split_mode mode, kdb_stream_t stream);
+
+/*
+ * Steps of the sharded single-tree build.  The paper builds one tree on one
+ * GPU; these entry points let several GPUs (one process each) share one tree:
+ * the top levels are split across the shards, then each GPU receives the
+ * points of one subtree and builds it with kdb_build_subtree.  A shard is
+ * d_points[0, n) of the global array, whose original indices are
+ * index_base .. index_base + n - 1; the tags (device int32[n], the paper's
+ * one int per point, Sec. 3) hold each point's node on the current top
+ * level (heap index; the root is 0) or -1 once the point is pinned.  Levels
+ * 0 .. 6 (at most 64 nodes).  Each call synchronises `stream` and returns
+ * KDB_ERR_INVALID_ARGUMENT for bad arguments, KDB_ERR_INTERNAL if a device
+ * check failed (a split dimension >= k, an output position out of range).
+ * Keys: a point's key in dimension d is (order-preserving coordinate key <<
+ * 32) | original index, so keys are unique and their order is the strict
+ * order of Sec. 3.1 with the tie rule.
+ *
+ * kdb_dist_histogram -- radix-select step of the pivots of level `level`
+ * (Observation 1): for every node u of the level (u = tag - (2^level - 1)),
+ * count the node's points whose key in dimension d_node_dim[u] agrees with
+ * d_node_prefix[u] in its top prefix_bits bits (0, 8, .., 56), by the next 8
+ * bits.  d_hist: device uint32[2^level][256], overwritten.
+ */
+KDB_API kdb_status kdb_dist_histogram(const void* d_points, int64_t n, int k, int stride_bytes,
+                                      kdb_split_mode mode, const int32_t* d_tags, int level,
+                                      const uint8_t* d_node_dim, const uint64_t* d_node_prefix,
+                                      int prefix_bits, uint32_t index_base, uint32_t* d_hist,
+                                      kdb_stream_t stream);
+
+/*
+ * kdb_dist_box -- smallest and largest coordinate key of every node's points
+ * of level `level` in every dimension (the scene box of Sec. 6 at level 0;
+ * the tight boxes of the tight-box rule).  d_box: device uint32[2^level][2k]
+ * (k minima, then k maxima), overwritten; a node without points on this
+ * shard gets 0xFFFFFFFF minima and 0 maxima.
+ */
+KDB_API kdb_status kdb_dist_box(const void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
+                                const int32_t* d_tags, int level, uint32_t* d_box, kdb_stream_t stream);
+
+/*
+ * kdb_dist_assign -- tag update of level `level` (Sec. 3.2): a point of node
+ * t whose key in dimension d_node_dim[u] is below the node's pivot key
+ * d_pivot[u] moves to 2t+1, above it to 2t+2; the point equal to it is
+ * pinned (tag -1) and its shard position written to d_pinned[u] (device
+ * int64[2^level]; entries of nodes whose pivot is elsewhere are untouched).
+ */
+KDB_API kdb_status kdb_dist_assign(const void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
+                                   int32_t* d_tags, int level, const uint8_t* d_node_dim,
+                                   const uint64_t* d_pivot, uint32_t index_base, int64_t* d_pinned,
+                                   kdb_stream_t stream);
+
+/*
+ * kdb_dist_partition -- the points whose tag is in [first_node, first_node +
+ * num_dest) (num_dest <= 64), grouped by destination j = tag - first_node in
+ * their shard order (a stable partition), for the exchange: records to
+ * d_out_points (device, at least the selected records), their original
+ * indices to d_out_index (device uint32).  h_counts: host int64[num_dest],
+ * the records of each destination.  Other points (pinned) are left out.
+ */
+KDB_API kdb_status kdb_dist_partition(const void* d_points, int64_t n, int stride_bytes, const int32_t* d_tags,
+                                      int32_t first_node, int num_dest, uint32_t index_base, void* d_out_points,
+                                      uint32_t* d_out_index, int64_t* h_counts, kdb_stream_t stream);
 
 /*
  * Plans: a build prepared once and enqueued many times, for repeated builds

@@ -56,7 +56,10 @@
  * for integer coordinates also the walkthrough as int2 points, values on both
  * sides of 2^31 (a signed/unsigned mix-up fails the k = 1 pin), and the
  * uint32 tree of any values equal to the int32 tree of the same values with
- * the top bit flipped.
+ * the top bit flipped.  The subtree entry (kdo_build_sub) is pinned by the
+ * whole build: rebuilt on their own, the subtrees of a whole build are the
+ * same subtrees, and round robin started at dimension f is the build of the
+ * coordinates rotated by f.
  */
 #include <math.h>
 #include <stdint.h>
@@ -293,6 +296,48 @@ int kdo_build(const void* points, int64_t N, int k, int stride, int mode,
   if (!P.ints) scene_box(&P, N, lo, hi);
   build_ctx C = {&P, N, mode, tmp, orig};
   build_rec(&C, S, N, 0, 0, lo, hi);
+  if (out_points) {
+    unsigned char* o = (unsigned char*)out_points;
+    for (int64_t s = 0; s < N; ++s)
+      memcpy(o + s * stride, P.base + (int64_t)orig[s] * stride, (size_t)stride);
+  }
+  if (out_orig) memcpy(out_orig, orig, (size_t)N * sizeof *orig);
+  free(S); free(tmp); free(orig);
+  return KDO_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * The subtree below one node of a larger tree, built on its own: the same
+ * recursion started at the node's depth (round robin continues with
+ * dimension (first_dim + depth) mod k) and, for the clipped-domain rule, from
+ * the node's domain (root_domain: k lower bounds, then k upper bounds).  A
+ * subtree of a left-balanced complete tree is itself one of its size, so the
+ * subtree's nodes in their own level order follow from Observation 1 exactly
+ * as for a whole tree; ties still go by position in `points`.
+ * ---------------------------------------------------------------------- */
+int kdo_build_sub(const void* points, int64_t N, int k, int stride, int mode, int first_dim,
+                  const float* root_domain, void* out_points, int32_t* out_orig) {
+  int rc = check_args(points, N, k, stride, mode);
+  if (rc) return rc;
+  if (first_dim < 0 || first_dim >= k) return KDO_INVALID;
+  if ((mode & 0xFF) == KDO_WIDEST && !root_domain) return KDO_INVALID;
+  if (N == 0) return KDO_OK;
+  pointset P = {(const unsigned char*)points, stride, k, coord_type(mode)};
+  mode &= 0xFF;
+  if (has_nan(&P, N)) return KDO_NAN;
+  int64_t* S = (int64_t*)malloc((size_t)N * sizeof *S);
+  int64_t* tmp = (int64_t*)malloc((size_t)N * sizeof *tmp);
+  int32_t* orig = (int32_t*)malloc((size_t)N * sizeof *orig);
+  if (!S || !tmp || !orig) { free(S); free(tmp); free(orig); return KDO_NOMEM; }
+  for (int64_t i = 0; i < N; ++i) S[i] = i;
+  float lo[KDO_MAXK] = {0}, hi[KDO_MAXK] = {0};
+  if (mode == KDO_WIDEST)
+    for (int d = 0; d < k; ++d) {
+      lo[d] = root_domain[d];
+      hi[d] = root_domain[k + d];
+    }
+  build_ctx C = {&P, N, mode, tmp, orig};
+  build_rec(&C, S, N, 0, mode == KDO_ROUND_ROBIN ? first_dim : 0, lo, hi);
   if (out_points) {
     unsigned char* o = (unsigned char*)out_points;
     for (int64_t s = 0; s < N; ++s)

@@ -66,6 +66,8 @@ def _load():
             lib.kdo_check.restype = i32
             lib.kdo_node.argtypes = [vp, i64, i32, i32, i32, i64, ctypes.POINTER(ctypes.c_int32)]
             lib.kdo_node.restype = i32
+            lib.kdo_build_sub.argtypes = [vp, i64, i32, i32, i32, i32, vp, vp, vp]
+            lib.kdo_build_sub.restype = i32
             lib.kdo_subtree_size.argtypes = [i64, i64]
             lib.kdo_subtree_size.restype = i64
             _lib = lib
@@ -100,6 +102,23 @@ def build(points: np.ndarray, k: int, mode: int = ROUND_ROBIN):
                            orig.ctypes.data)
     if rc != OK:
         raise OracleError(rc, "kdo_build")
+    return out, orig
+
+
+def build_sub(points: np.ndarray, k: int, mode: int = ROUND_ROBIN, first_dim: int = 0, root_domain=None):
+    """The subtree below a node of a larger tree, built on its own: round
+    robin starts at dimension ``first_dim``; the clipped-domain rule starts
+    from ``root_domain`` (k lower bounds, then k upper bounds).  Returns
+    (records in the subtree's level order, position of each node's record)."""
+    pts = _records(points)
+    n, w = pts.shape
+    out = np.empty_like(pts)
+    orig = np.empty(n, dtype=np.int32)
+    dom = None if root_domain is None else np.ascontiguousarray(root_domain, dtype=np.float32)
+    rc = _load().kdo_build_sub(pts.ctypes.data, n, k, 4 * w, _mode(pts, mode), first_dim,
+                               None if dom is None else dom.ctypes.data, out.ctypes.data, orig.ctypes.data)
+    if rc != OK:
+        raise OracleError(rc, "kdo_build_sub")
     return out, orig
 
 

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libkdb.so")
 SOURCES = ["kdb_sort.cu", "kdb_tree.cu", "kdb_local.cu", "kdb_lists.cu", "kdb_part.cu", "kdb_api.cu",
-           "kdb_serve.cu"]
+           "kdb_serve.cu", "kdb_dist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

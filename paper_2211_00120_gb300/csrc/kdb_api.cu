@@ -196,6 +196,9 @@ struct Plan {
   bool singletons = false;  // a set of one record (its node is its record)
   bool too_wide = false;    // (set, subtree, rank) needs more than 64 bits
   int part_shape = -1, rec_shape = -1;  // tile shapes; -1: the process-wide setting
+  int dim0 = 0;              // round robin: level l splits in dimension (l + dim0) mod k
+  bool has_domain = false;   // widest extent: the root's domain is given, not the scene box
+  float domain[2 * kMaxK] = {};  // its lower corner, then its upper corner
   int placement = -1;                    // -1: the process-wide setting
   std::vector<std::vector<ActiveEntry>> act;  // per level l = 0 .. Lmax-2
   std::vector<uint32_t> items;                // per level
@@ -614,6 +617,17 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       pa.beg = pa.end = 0;
     }
   }
+  if (P.has_domain && bydim) {
+    // the root's domain is given (a subtree of a larger tree): it replaces
+    // the scene box as the root's domain, stored as coordinate keys
+    uint32_t keys[2 * kMaxK];
+    for (int d = 0; d < 2 * k; ++d) {
+      uint32_t bits;
+      std::memcpy(&bits, &P.domain[d < k ? d : kMaxK + d - k], 4);
+      keys[d] = float_key(bits);
+    }
+    KDB_CK(cudaMemcpyAsync(bbox, keys, 2 * k * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+  }
   uint32_t* hcur = hist + (size_t)k * P.rank_passes * kRadixBins;
 
   // ---- per-dimension ranks (packed-key levels, k >= 4)
@@ -632,6 +646,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       wx.act = d_whole;
       wx.nact = 1;
       wx.l = 0;
+      wx.dim0 = P.dim0;
       wx.err = err;
       const uint32_t* kin = at<uint32_t>(ws, P.o_ckeys) + (size_t)d * P.kstride;
       const uint32_t* vin = nullptr;
@@ -714,6 +729,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     x.act_next = l + 1 < levels ? d_act + P.act_off[l + 1] : nullptr;
     x.nact = (uint32_t)P.act[l].size();
     x.l = l;
+    x.dim0 = P.dim0;
     x.rb = P.rb;
     x.err = err;
     x.local_next = P.use_local ? 1 : 0;
@@ -739,7 +755,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     pa.k = k;
     pa.mode = P.mode;
     pa.dlist = d;
-    pa.pos_first = P.mode == KDB_SPLIT_ROUND_ROBIN && p % k == d ? 1 : 0;
+    pa.pos_first = P.mode == KDB_SPLIT_ROUND_ROBIN && (p + P.dim0) % k == d ? 1 : 0;
     pa.n = P.items[p];
     pa.next_items = q < levels ? P.items[q] : 0;
     pa.total = T;
@@ -779,6 +795,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       x0.act = d_act + P.act_off[0];
       x0.nact = (uint32_t)P.act[0].size();
       x0.l = 0;
+      x0.dim0 = P.dim0;
       x0.err = err;
       const uint32_t n0 = P.items[0];
       const uint4* l0 = ents0;
@@ -825,6 +842,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     x.act_next = l + 1 < levels ? d_act + P.act_off[l + 1] : nullptr;
     x.nact = (uint32_t)P.act[l].size();
     x.l = l;
+    x.dim0 = P.dim0;
     x.rb = P.rb;
     x.err = err;
     x.local_next = P.use_local ? 1 : 0;
@@ -834,7 +852,8 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     uint32_t* vfree = vals_cur == valsA ? valsB : valsA;
     hcur = hist + P.hist_off[l];
     if (P.use_lists) {
-      if (lazy && lat[l % k] < l) KDB_CK(lift(l % k, lat[l % k], l, false));
+      const int dl = (l + P.dim0) % k;  // the level's round-robin split dimension
+      if (lazy && lat[dl] < l) KDB_CK(lift(dl, lat[dl], l, false));
       PivotArgs pv{};
       pv.x = x;
       for (int d = 0; d < k; ++d) pv.lists[d] = lcur[d];
@@ -996,6 +1015,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     la.lents = lents;
     la.pts_out = direct ? pts : nullptr;
     la.ctype = P.ctype;
+    la.dim0 = P.dim0;
     // algorithmic bytes per point: the handed-over lists in (list 0 as
     // entries when handed over whole), perm out, and the record written at
     // its node when it is written from its entry
@@ -1007,7 +1027,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   // ---- placement
   if (out_dim && !bydim) {
     Prof pf(K_WIDEST, (double)T, 1, st);
-    KDB_CK(launch_rr_dims(dims, d_sets, (uint32_t)P.sets.size(), T, k, st));
+    KDB_CK(launch_rr_dims(dims, d_sets, (uint32_t)P.sets.size(), T, k, P.dim0, st));
   }
   PermuteArgs pm{};
   pm.pts = pts;
@@ -1413,6 +1433,43 @@ kdb_status kdb_build_ex(void* d_points, int64_t n, int k, int stride_bytes, kdb_
              d_out_orig_index, d_out_split_dim, st);
 }
 
+kdb_status kdb_build_subtree(void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
+                             int first_dim, const float* h_root_domain, int32_t* d_out_orig_index,
+                             kdb_stream_t stream) {
+  kdb_status s = check_common(n, k, stride_bytes);
+  if (s == KDB_OK) s = check_mode_k(mode, k);
+  if (s != KDB_OK) return s;
+  const int split = split_of(mode);
+  if (first_dim < 0 || first_dim >= k) return KDB_ERR_INVALID_ARGUMENT;
+  if (split == KDB_SPLIT_WIDEST_EXTENT && !h_root_domain) return KDB_ERR_INVALID_ARGUMENT;
+  if (n > 0 && (!d_points || (reinterpret_cast<uintptr_t>(d_points) & 3))) return KDB_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (n <= 1) {
+    if (n == 1 && d_out_orig_index) {
+      int32_t zero = 0;
+      KDB_CK(cudaMemcpyAsync(d_out_orig_index, &zero, 4, cudaMemcpyHostToDevice, st));
+      KDB_CK(cudaStreamSynchronize(st));
+    }
+    return KDB_OK;
+  }
+  Plan P;
+  P.sets.push_back(SetInfo{0u, (uint32_t)n});
+  P.total = (uint32_t)n;
+  P.k = k;
+  P.stride = stride_bytes;
+  P.mode = split;
+  P.ctype = ctype_of(mode);
+  P.dim0 = split == KDB_SPLIT_ROUND_ROBIN ? first_dim : 0;
+  if (split == KDB_SPLIT_WIDEST_EXTENT) {
+    P.has_domain = true;
+    for (int d = 0; d < k; ++d) {
+      P.domain[d] = h_root_domain[d];
+      P.domain[kMaxK + d] = h_root_domain[k + d];
+    }
+  }
+  return run(P, static_cast<unsigned char*>(d_points), nullptr, 0, d_out_orig_index, nullptr, st);
+}
+
 kdb_status kdb_build(void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
                      kdb_stream_t stream) {
   return kdb_build_ex(d_points, n, k, stride_bytes, mode, nullptr, 0, nullptr, nullptr, stream);
@@ -1453,6 +1510,179 @@ kdb_status kdb_build_noalloc(void* d_points, int64_t n, int k, int stride_bytes,
                     nullptr, st);
   kdb_status f = finish(P, ws, st);
   return s != KDB_OK ? s : f;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------- sharded single tree --
+namespace kdb {
+namespace {
+// Common checks of the sharded-build steps and one synchronous run of
+// `launch` with a device status word from the pool.
+template <class F>
+kdb_status dist_run(int64_t n, int k, int stride_bytes, kdb_split_mode mode, int level, uint32_t index_base,
+                    kdb_stream_t stream, F launch) {
+  kdb_status s = check_common(n, k, stride_bytes);
+  if (s == KDB_OK) s = check_mode(mode);
+  if (s != KDB_OK) return s;
+  if (level < 0 || (1 << level) > kDistMaxDest) return KDB_ERR_INVALID_ARGUMENT;
+  if ((uint64_t)index_base + (uint64_t)n > 2147483647ull) return KDB_ERR_INVALID_ARGUMENT;
+  int dev, sms;
+  cudaMemPool_t pool;
+  s = device_setup(&dev, &pool, &sms);
+  if (s != KDB_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  void* err = nullptr;
+  s = pool_alloc(&err, 4, pool, st);
+  if (s != KDB_OK) return s;
+  kdb_status r = KDB_OK;
+  if (cudaMemsetAsync(err, 0, 4, st) != cudaSuccess || launch(static_cast<uint32_t*>(err), sms, st) != cudaSuccess)
+    r = KDB_ERR_CUDA;
+  uint32_t h_err = 0;
+  if (r == KDB_OK && cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) r = KDB_ERR_CUDA;
+  cudaFreeAsync(err, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) r = KDB_ERR_CUDA;
+  if (r != KDB_OK) {
+    cudaGetLastError();
+    return r;
+  }
+  return (h_err & ERR_INTERNAL) ? KDB_ERR_INTERNAL : KDB_OK;
+}
+
+DistArgs dist_args(const void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode, const int32_t* d_tags,
+                   int level, uint32_t index_base) {
+  DistArgs a{};
+  a.pts = static_cast<const unsigned char*>(d_points);
+  a.n = (uint32_t)n;
+  a.k = k;
+  a.stride = stride_bytes;
+  a.ctype = ctype_of((int)mode);
+  a.tags = const_cast<int32_t*>(d_tags);
+  a.first = full_nodes(level);
+  a.nodes = 1u << level;
+  a.index_base = index_base;
+  return a;
+}
+}  // namespace
+}  // namespace kdb
+
+extern "C" {
+
+kdb_status kdb_dist_histogram(const void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
+                              const int32_t* d_tags, int level, const uint8_t* d_node_dim,
+                              const uint64_t* d_node_prefix, int prefix_bits, uint32_t index_base,
+                              uint32_t* d_hist, kdb_stream_t stream) {
+  if (prefix_bits < 0 || prefix_bits > 56 || prefix_bits % 8 || !d_hist || !d_node_dim || !d_node_prefix ||
+      (n > 0 && (!d_points || !d_tags)))
+    return KDB_ERR_INVALID_ARGUMENT;
+  return dist_run(n, k, stride_bytes, mode, level, index_base, stream,
+                  [&](uint32_t* err, int sms, cudaStream_t st) -> cudaError_t {
+                    DistArgs a = dist_args(d_points, n, k, stride_bytes, mode, d_tags, level, index_base);
+                    a.node_dim = d_node_dim;
+                    a.prefix = d_node_prefix;
+                    a.prefix_bits = prefix_bits;
+                    a.hist = d_hist;
+                    a.err = err;
+                    cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)a.nodes * 256 * 4, st);
+                    return e != cudaSuccess ? e : launch_dist_hist(a, sms, st);
+                  });
+}
+
+kdb_status kdb_dist_box(const void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
+                        const int32_t* d_tags, int level, uint32_t* d_box, kdb_stream_t stream) {
+  if (!d_box || (n > 0 && (!d_points || !d_tags))) return KDB_ERR_INVALID_ARGUMENT;
+  return dist_run(n, k, stride_bytes, mode, level, 0, stream,
+                  [&](uint32_t* err, int sms, cudaStream_t st) -> cudaError_t {
+                    DistArgs a = dist_args(d_points, n, k, stride_bytes, mode, d_tags, level, 0);
+                    a.box = d_box;
+                    a.err = err;
+                    std::vector<uint32_t> init((size_t)a.nodes * 2 * k);
+                    for (size_t i = 0; i < init.size(); ++i) init[i] = (i / k) % 2 == 0 ? 0xFFFFFFFFu : 0u;
+                    cudaError_t e = cudaMemcpyAsync(d_box, init.data(), init.size() * 4, cudaMemcpyHostToDevice, st);
+                    return e != cudaSuccess ? e : launch_dist_box(a, sms, st);
+                  });
+}
+
+kdb_status kdb_dist_assign(const void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
+                           int32_t* d_tags, int level, const uint8_t* d_node_dim, const uint64_t* d_pivot,
+                           uint32_t index_base, int64_t* d_pinned, kdb_stream_t stream) {
+  if (!d_node_dim || !d_pivot || !d_pinned || (n > 0 && (!d_points || !d_tags))) return KDB_ERR_INVALID_ARGUMENT;
+  return dist_run(n, k, stride_bytes, mode, level, index_base, stream,
+                  [&](uint32_t* err, int sms, cudaStream_t st) -> cudaError_t {
+                    DistArgs a = dist_args(d_points, n, k, stride_bytes, mode, d_tags, level, index_base);
+                    a.node_dim = d_node_dim;
+                    a.pivot = d_pivot;
+                    a.pinned = d_pinned;
+                    a.err = err;
+                    return launch_dist_assign(a, sms, st);
+                  });
+}
+
+kdb_status kdb_dist_partition(const void* d_points, int64_t n, int stride_bytes, const int32_t* d_tags,
+                              int32_t first_node, int num_dest, uint32_t index_base, void* d_out_points,
+                              uint32_t* d_out_index, int64_t* h_counts, kdb_stream_t stream) {
+  if (num_dest < 1 || num_dest > kDistMaxDest || first_node < 0 || !h_counts) return KDB_ERR_INVALID_ARGUMENT;
+  if (n > 0 && (!d_points || !d_tags || !d_out_points || !d_out_index)) return KDB_ERR_INVALID_ARGUMENT;
+  if (n < 0 || n > 2147483647LL || stride_bytes < 4 || stride_bytes % 4 ||
+      (uint64_t)index_base + (uint64_t)n > 2147483647ull)
+    return KDB_ERR_INVALID_ARGUMENT;
+  for (int j = 0; j < num_dest; ++j) h_counts[j] = 0;
+  if (n == 0) return KDB_OK;
+  int dev, sms;
+  cudaMemPool_t pool;
+  kdb_status s = device_setup(&dev, &pool, &sms);
+  if (s != KDB_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  DistArgs a{};
+  a.pts = static_cast<const unsigned char*>(d_points);
+  a.n = (uint32_t)n;
+  a.stride = stride_bytes;
+  a.tags = const_cast<int32_t*>(d_tags);
+  a.first = (uint32_t)first_node;
+  a.nodes = (uint32_t)num_dest;
+  a.index_base = index_base;
+  a.out_pts = static_cast<unsigned char*>(d_out_points);
+  a.out_index = d_out_index;
+  const uint32_t blocks = dist_blocks(a.n, sms);
+  const size_t cnt = (size_t)blocks * num_dest;
+  void* ws = nullptr;
+  s = pool_alloc(&ws, cnt * 8 + 4, pool, st);
+  if (s != KDB_OK) return s;
+  a.block_counts = static_cast<uint32_t*>(ws);
+  a.err = a.block_counts + 2 * cnt;
+  std::vector<uint32_t> h(cnt);
+  kdb_status r = KDB_OK;
+  if (cudaMemsetAsync(a.err, 0, 4, st) != cudaSuccess || launch_dist_count(a, blocks, st) != cudaSuccess ||
+      cudaMemcpyAsync(h.data(), a.block_counts, cnt * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    r = KDB_ERR_CUDA;
+  } else {
+    // exclusive offsets: destination-major, then block order (a stable partition)
+    std::vector<uint32_t> off(cnt);
+    uint64_t run = 0;
+    for (int j = 0; j < num_dest; ++j) {
+      const uint64_t first = run;
+      for (uint32_t b = 0; b < blocks; ++b) {
+        off[(size_t)b * num_dest + j] = (uint32_t)run;
+        run += h[(size_t)b * num_dest + j];
+      }
+      h_counts[j] = (int64_t)(run - first);
+    }
+    a.block_offsets = a.block_counts + cnt;
+    uint32_t h_err = 0;
+    if (cudaMemcpyAsync(const_cast<uint32_t*>(a.block_offsets), off.data(), cnt * 4, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        launch_dist_scatter(a, blocks, st) != cudaSuccess ||
+        cudaMemcpyAsync(&h_err, a.err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      r = KDB_ERR_CUDA;
+    else if (h_err & ERR_INTERNAL)
+      r = KDB_ERR_INTERNAL;
+  }
+  cudaFreeAsync(ws, st);
+  cudaStreamSynchronize(st);
+  if (r == KDB_ERR_CUDA) cudaGetLastError();
+  return r;
 }
 
 kdb_status kdb_build_batched(void* d_points, const int64_t* h_offsets, int num_sets, int k,

@@ -16,6 +16,7 @@ struct LevelCtx {
   const ActiveEntry* act_next;  // active sets of level l+1 (device), may be empty
   uint32_t nact;
   int l;
+  int dim0;        // round robin: level l splits in dimension (l + dim0) mod k
   int rb;          // bits of a rank
   uint32_t* err;   // device status word: kernels do nothing once it is set
   int local_next;  // 1: a set that leaves the active list goes to the local finish
@@ -174,6 +175,7 @@ struct LocalArgs {
   uint32_t* err;
   unsigned char* pts_out;    // records written directly at their nodes (stride = 4k), or nullptr
   int ctype;                 // coordinate type (kCoordF32 / I32 / U32)
+  int dim0;                  // round robin: level l splits in dimension (l + dim0) mod k
 };
 size_t local_smem_bytes(int k);
 cudaError_t launch_local_finish(const LocalArgs& a, cudaStream_t st);
@@ -213,6 +215,36 @@ cudaError_t seg_pass_update(const uint32_t* kin, const uint32_t* vin, const Leve
 cudaError_t seg_pass_rank(const uint32_t* kin, const uint32_t* vin, const LevelCtx& x,
                           const uint32_t* seg_hist, const RankOut& out, const PassCtl& c,
                           cudaStream_t st);
+
+// Sharded single-tree build (kdb_dist.cu): the steps of the top levels on
+// one shard of the points.
+constexpr int kDistMaxDest = 64;  // nodes of a top level, destinations of the exchange
+struct DistArgs {
+  const unsigned char* pts;
+  uint32_t n;               // points of the shard
+  int k, stride, ctype;
+  int32_t* tags;            // per point: node (heap index) on the current level, -1 once pinned
+  uint32_t first, nodes;    // the level's first node and its node count (or first destination node, count)
+  const uint8_t* node_dim;  // split dimension per node of the level
+  const uint64_t* prefix;   // radix select: per node the key bits fixed so far
+  int prefix_bits;
+  uint32_t index_base;      // original index of the shard's first point
+  uint32_t* hist;           // [nodes][256]
+  uint32_t* box;            // [nodes][2k] coordinate keys: min, then max
+  const uint64_t* pivot;    // per node its pivot's key (coordinate key << 32 | original index)
+  int64_t* pinned;          // per node the shard position of its pivot (if on this shard)
+  uint32_t* block_counts;   // [blocks][nodes]
+  const uint32_t* block_offsets;  // [blocks][nodes]: first output position
+  unsigned char* out_pts;
+  uint32_t* out_index;
+  uint32_t* err;
+};
+uint32_t dist_blocks(uint32_t n, int sms);
+cudaError_t launch_dist_hist(const DistArgs& a, int sms, cudaStream_t st);
+cudaError_t launch_dist_box(const DistArgs& a, int sms, cudaStream_t st);
+cudaError_t launch_dist_assign(const DistArgs& a, int sms, cudaStream_t st);
+cudaError_t launch_dist_count(const DistArgs& a, uint32_t blocks, cudaStream_t st);
+cudaError_t launch_dist_scatter(const DistArgs& a, uint32_t blocks, cudaStream_t st);
 
 // tree kernels (kdb_tree.cu)
 struct PrepassArgs {
@@ -288,7 +320,7 @@ cudaError_t launch_widest_children(const WidestArgs& a, cudaStream_t st);
 cudaError_t launch_tight_validate_dims(const unsigned char* pts, uint32_t n, int k, int stride,
                                        uint32_t* box, uint8_t* dims, int ctype, cudaStream_t st);
 cudaError_t launch_rr_dims(uint8_t* dims, const SetInfo* sets, uint32_t nsets, uint32_t total,
-                           int k, cudaStream_t st);
+                           int k, int dim0, cudaStream_t st);
 
 // Placement: one cycle leader (and one staged record) per kPermGroup nodes.
 constexpr uint32_t kPermGroup = 16;

@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
 
   // ---- the k lists: local ids 0..m-1 ordered by (key_d, original index)
   int dpar = -1;  // dimension the items arrive sorted by (the parent's split)
-  if (l0 > 0) dpar = kMode == 0 ? (l0 - 1) % k : a.dims[ls.off + (s0 - 1) / 2];
+  if (l0 > 0) dpar = kMode == 0 ? (l0 - 1 + a.dim0) % k : a.dims[ls.off + (s0 - 1) / 2];
   uint16_t* s_wh = s_lists + (size_t)k * kLocalCap;  // radix counters (spare list slot)
   if (a.lorig && l0 > 0) {
     // The global passes hand over every list of the subtree as original
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
   if (threadIdx.x < (unsigned)depths) {
     const int jj = threadIdx.x, L = l0 + jj;
     s_lay[jj] = make_local(tree, L, wk.s_rel << jj, 1u << jj);
-    s_drr[jj] = (uint8_t)(L % k);
+    s_drr[jj] = (uint8_t)((L + a.dim0) % k);
   }
   for (uint32_t i = threadIdx.x; i < kLocalCap; i += T) {
     if (i < m) s_tag[i] = 0;  // every item starts in the root

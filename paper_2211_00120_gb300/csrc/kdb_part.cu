@@ -50,7 +50,7 @@ __global__ void pivot_kernel(PivotArgs a) {
   const SetInfo si = x.sets[e.set];
   const LevelLayout y = LevelLayout::make(make_tree(si.n), x.l);
   const uint32_t node = full_nodes(x.l) + s_rel;
-  const int d = a.mode == 0 ? x.l % a.k : a.dims[si.off + node];
+  const int d = a.mode == 0 ? (x.l + x.dim0) % a.k : a.dims[si.off + node];
   const uint32_t pos = e.base + y.seg_start(s_rel) + y.left_size(s_rel);
   if (d >= a.k || pos >= a.items) {
     atomicOr(x.err, ERR_INTERNAL);
@@ -159,7 +159,7 @@ __device__ inline void lift_seg_info(const PartArgs& a, uint32_t ai, uint32_t sr
     const uint2 pv = a.piv[e2][(ai << lq) | rel];
     ps->pk[h] = pv.x;
     ps->po[h] = pv.y;
-    ps->dim[h] = (uint8_t)(a.mode == 0 ? lq % a.k : a.dims[si.off + full_nodes(lq) + rel]);
+    ps->dim[h] = (uint8_t)(a.mode == 0 ? (lq + x.dim0) % a.k : a.dims[si.off + full_nodes(lq) + rel]);
   }
 }
 

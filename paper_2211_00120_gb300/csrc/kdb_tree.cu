@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kThreads) level_keys_kernel(LevelKeyArgs a) {
       const uint32_t s_rel = y.seg_of(jj);
       const uint32_t orig = a.vals ? a.vals[j] : soff + jj;
       if (!a.vals) a.vals_out[j] = orig;
-      const int d = a.mode == 0 ? x.l % a.k : a.dims[soff + Fl + s_rel];
+      const int d = a.mode == 0 ? (x.l + x.dim0) % a.k : a.dims[soff + Fl + s_rel];
       uint32_t r = 0;
       if (orig < a.total && d < a.k) {
         r = a.ranks[(uint64_t)d * a.total + orig];
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(kThreads) seg_level_keys_kernel(SegKeyArgs a) 
   const int H = a.passes * kRadixBins;
   for (int i = threadIdx.x; i < H; i += blockDim.x) s_hist[i] = 0;
   __syncthreads();
-  const int d = a.mode == 0 ? x.l % a.k : a.dims[si.off + full_nodes(x.l) + s_rel];
+  const int d = a.mode == 0 ? (x.l + x.dim0) % a.k : a.dims[si.off + full_nodes(x.l) + s_rel];
   const uint32_t* rank_d = a.ranks + (uint64_t)(d < a.k ? d : 0) * a.total;
   for (uint32_t j = beg + threadIdx.x; j < end; j += blockDim.x) {
     const uint32_t orig = a.vals ? a.vals[j] : si.off + (j - e.base);
@@ -413,11 +413,11 @@ __global__ void widest_children_kernel(WidestArgs a) {
 }
 
 __global__ void rr_dims_kernel(uint8_t* dims, const SetInfo* sets, uint32_t nsets, uint32_t total,
-                               int k) {
+                               int k, int dim0) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   const uint32_t s = nsets > 1 ? find_set(sets, nsets, i) : 0;
-  dims[i] = (uint8_t)(level_of(i - sets[s].off) % k);
+  dims[i] = (uint8_t)((level_of(i - sets[s].off) + dim0) % k);
 }
 
 // ---------------------------------------------------------------------------
@@ -738,9 +738,10 @@ cudaError_t launch_widest_children(const WidestArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_rr_dims(uint8_t* dims, const SetInfo* sets, uint32_t nsets, uint32_t total,
-                           int k, cudaStream_t st) {
+                           int k, int dim0, cudaStream_t st) {
   if (total == 0) return cudaSuccess;
-  rr_dims_kernel<<<(total + kThreads - 1) / kThreads, kThreads, 0, st>>>(dims, sets, nsets, total, k);
+  rr_dims_kernel<<<(total + kThreads - 1) / kThreads, kThreads, 0, st>>>(dims, sets, nsets, total, k,
+                                                                          dim0);
   return cudaGetLastError();
 }
 

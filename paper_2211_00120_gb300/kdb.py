@@ -136,6 +136,12 @@ def load():
             "kdb_server_poll": ([vp, ctypes.POINTER(RequestResult), i32, i32], i32),
             "kdb_server_get_stats": ([vp, ctypes.POINTER(ServerStats)], i32),
             "kdb_server_destroy": ([vp], i32),
+            "kdb_build_subtree": ([vp, i64, i32, i32, i32, i32, vp, vp, vp], i32),
+            "kdb_dist_histogram": ([vp, i64, i32, i32, i32, vp, i32, vp, vp, i32, ctypes.c_uint32, vp, vp], i32),
+            "kdb_dist_box": ([vp, i64, i32, i32, i32, vp, i32, vp, vp], i32),
+            "kdb_dist_assign": ([vp, i64, i32, i32, i32, vp, i32, vp, vp, ctypes.c_uint32, vp, vp], i32),
+            "kdb_dist_partition": ([vp, i64, i32, vp, i32, i32, ctypes.c_uint32, vp, vp,
+                                    ctypes.POINTER(i64), vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -232,6 +238,62 @@ def kdb_build_host(points, k: int, mode: int = ROUND_ROBIN, stream=None) -> None
     ptr, n, stride = _records(points)
     _check(load().kdb_build_host(ptr, n, k, stride, _mode(points, mode), _stream(stream)),
            "kdb_build_host")
+
+
+def kdb_build_subtree(points, k: int, mode: int = ROUND_ROBIN, first_dim: int = 0, root_domain=None,
+                      out_orig_index=None, stream=None) -> None:
+    """kdb_build of the subtree below one node of a larger tree: round robin
+    continues from ``first_dim``; the clipped-domain rule starts from
+    ``root_domain`` (2k floats: lower corner, then upper corner)."""
+    ptr, n, stride = _records(points)
+    dom = None
+    if root_domain is not None:
+        vals = [float(v) for v in root_domain]
+        dom = (ctypes.c_float * len(vals))(*vals)
+    oi = out_orig_index.data_ptr() if out_orig_index is not None else None
+    _check(load().kdb_build_subtree(ptr, n, k, stride, _mode(points, mode), first_dim, dom, oi,
+                                    _stream(stream)), "kdb_build_subtree")
+
+
+def kdb_dist_histogram(points, k: int, mode: int, tags, level: int, node_dim, node_prefix, prefix_bits: int,
+                       index_base: int, hist, stream=None) -> None:
+    """Radix-select digit histograms of one top level of a sharded build
+    (device tensors: tags int32[n], node_dim uint8[2^level], node_prefix
+    int64[2^level], hist int32[2^level, 256])."""
+    ptr, n, stride = _records(points)
+    _check(load().kdb_dist_histogram(ptr, n, k, stride, _mode(points, mode), tags.data_ptr(), level,
+                                     node_dim.data_ptr(), node_prefix.data_ptr(), prefix_bits, index_base,
+                                     hist.data_ptr(), _stream(stream)), "kdb_dist_histogram")
+
+
+def kdb_dist_box(points, k: int, mode: int, tags, level: int, box, stream=None) -> None:
+    """Per node of one top level: min and max coordinate keys (box int32[2^level, 2k])."""
+    ptr, n, stride = _records(points)
+    _check(load().kdb_dist_box(ptr, n, k, stride, _mode(points, mode), tags.data_ptr(), level, box.data_ptr(),
+                               _stream(stream)), "kdb_dist_box")
+
+
+def kdb_dist_assign(points, k: int, mode: int, tags, level: int, node_dim, pivot, index_base: int, pinned,
+                    stream=None) -> None:
+    """Tag update of one top level against the nodes' pivot keys (pivot
+    int64[2^level]); pinned int64[2^level] receives the local position of
+    each pivot held here."""
+    ptr, n, stride = _records(points)
+    _check(load().kdb_dist_assign(ptr, n, k, stride, _mode(points, mode), tags.data_ptr(), level,
+                                  node_dim.data_ptr(), pivot.data_ptr(), index_base, pinned.data_ptr(),
+                                  _stream(stream)), "kdb_dist_assign")
+
+
+def kdb_dist_partition(points, tags, first_node: int, num_dest: int, index_base: int, out_points, out_index,
+                       stream=None) -> list:
+    """Stable partition of the points by destination tag - first_node; returns
+    the record count of each destination."""
+    ptr, n, stride = _records(points)
+    counts = (ctypes.c_int64 * num_dest)()
+    _check(load().kdb_dist_partition(ptr, n, stride, tags.data_ptr(), first_node, num_dest, index_base,
+                                     out_points.data_ptr(), out_index.data_ptr(), counts, _stream(stream)),
+           "kdb_dist_partition")
+    return [int(c) for c in counts]
 
 
 NOALLOC_MAX_POINTS = 262144

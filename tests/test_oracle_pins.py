@@ -534,3 +534,89 @@ def test_uint32_refusals():
     with pytest.raises(oracle.OracleError) as e:
         oracle.build(pts, 3, RR | oracle.INT32 | oracle.UINT32)
     assert e.value.code == oracle.INVALID
+
+
+# ---- a subtree built on its own (the sharded single-tree build's local step)
+
+def subtree_nodes(root, n):
+    """Nodes of the subtree at `root` in its own level order."""
+    out, first, width = [], root, 1
+    while first < n:
+        out += [t for t in range(first, min(first + width, n))]
+        first, width = 2 * first + 1, 2 * width
+    return out
+
+
+def clipped_domain(out, k, node, scene_lo, scene_hi):
+    """The domain of `node` in a clipped-domain tree `out` (records in level
+    order): the scene box clipped by every ancestor's plane, the ancestors'
+    dimensions recomputed top-down (float32 extents, lowest dimension wins
+    ties) -- restated here from Sec. 6, independently of the oracle."""
+    lo, hi = np.array(scene_lo, np.float32), np.array(scene_hi, np.float32)
+    path = []
+    v = node
+    while v > 0:
+        path.append(v)
+        v = (v - 1) // 2
+    p = 0
+    for child in reversed(path):
+        ext = [np.float32(hi[d]) - np.float32(lo[d]) for d in range(k)]
+        d = 0
+        for e in range(1, k):
+            if ext[e] > ext[d]:
+                d = e
+        plane = out[p, d]
+        if child == 2 * p + 1:
+            hi[d] = plane
+        else:
+            lo[d] = plane
+        p = child
+    return np.concatenate([lo, hi])
+
+
+def test_build_sub_at_the_root_is_the_whole_build():
+    pts = synth.mixed(3000, 3, seed=12)
+    for mode in (RR, WIDEST, TIGHT):
+        dom = np.concatenate([pts.min(axis=0), pts.max(axis=0)]) if mode == WIDEST else None
+        a, ao = oracle.build(pts, 3, mode)
+        b, bo = oracle.build_sub(pts, 3, mode, 0, dom)
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32)) and np.array_equal(ao, bo)
+
+
+@pytest.mark.parametrize("mode", [RR, WIDEST, TIGHT])
+def test_build_sub_equals_the_subtrees_of_the_whole_build(mode):
+    """Every subtree at depths 1..3 of a whole build, rebuilt on its own from
+    its points in original-index order, is the same subtree: round robin from
+    dimension depth mod k, the clipped-domain rule from the node's domain."""
+    rng = np.random.default_rng(4 + mode)
+    for n, k in ((2047, 3), (3001, 2), (777, 3), (100, 1)):
+        pts = tie_heavy(random.Random(n), n, k, values=tuple(float(v) for v in range(9))) \
+            if n == 777 else rng.random((n, k), dtype=np.float32)
+        if mode == WIDEST:
+            pts = pts * np.array([100.0, 1.0, 10.0][:k], np.float32)
+        out, orig = oracle.build(pts, k, mode)
+        for depth in (1, 2, 3):
+            for node in range((1 << depth) - 1, (1 << (depth + 1)) - 1):
+                if node >= n:
+                    continue
+                nodes = subtree_nodes(node, n)
+                ids = np.sort(orig[nodes])
+                dom = clipped_domain(out, k, node, pts.min(axis=0), pts.max(axis=0)) if mode == WIDEST else None
+                sub, sorig = oracle.build_sub(pts[ids], k, mode, depth % k, dom)
+                assert np.array_equal(ids[sorig], orig[nodes]), (n, k, node)
+                assert np.array_equal(sub.view(np.uint32), out[nodes].view(np.uint32))
+
+
+def test_build_sub_round_robin_is_the_build_of_rotated_coordinates():
+    """Starting round robin at dimension f is the ordinary build of the
+    coordinates rotated by f (column c holds dimension (c + f) mod k)."""
+    pts = synth.uniform(1500, 3, seed=21)
+    for f in range(3):
+        rot = np.ascontiguousarray(np.roll(pts, -f, axis=1))
+        _, want = oracle.build(rot, 3, RR)
+        _, got = oracle.build_sub(pts, 3, RR, f)
+        assert np.array_equal(want, got)
+    with pytest.raises(oracle.OracleError):
+        oracle.build_sub(pts, 3, RR, 3)
+    with pytest.raises(oracle.OracleError):
+        oracle.build_sub(pts, 3, WIDEST, 0, None)
