@@ -711,10 +711,12 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   uint2* piv_ring[kLiftMax];
   for (int i = 0; i < kLiftMax; ++i)
     piv_ring[i] = at<uint2>(ws, P.o_piv) + (size_t)i * std::max<uint32_t>(P.max_nseg, 1);
-  // Round robin over one set: a list is read only on the levels that split
-  // in its dimension, so it is advanced lazily, several levels in one pass,
-  // just before those levels (lat[d]: the level list d is sorted for).
-  const bool lazy = P.use_lists && P.mode == KDB_SPLIT_ROUND_ROBIN && P.sets.size() == 1;
+  // Round robin: a list is read only on the levels that split in its
+  // dimension (the same levels in every set), so it is advanced lazily,
+  // several levels in one pass, just before those levels (lat[d]: the level
+  // list d is sorted for); a set that leaves the active list within such a
+  // pass is handed to the local finish at the level where it leaves.
+  const bool lazy = P.use_lists && P.mode == KDB_SPLIT_ROUND_ROBIN;
   // Records without payload are written straight to their nodes from the
   // entries (which hold every coordinate bit) as the nodes are pinned; the
   // caller's array is not read after the prepass, and no placement is left.
@@ -744,6 +746,8 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     PartArgs pa{};
     pa.x = level_ctx(p);
     pa.act_out = q < levels ? d_act + P.act_off[q] : nullptr;
+    for (int j = 0; j < kLiftMax - 1; ++j)
+      pa.act_mid[j] = p + 1 + j < levels ? d_act + P.act_off[p + 1 + j] : nullptr;
     pa.b = q - p;
     pa.handoff = handoff ? 1 : 0;
     pa.in = lcur[d];

@@ -101,11 +101,14 @@ constexpr int kLiftBins = 1 << kLiftMax;  // descendants of a segment kLiftMax l
 struct PartArgs {
   LevelCtx x;               // level p, the input list's level
   const ActiveEntry* act_out;  // active sets of level p + b
-  int b;                    // levels to advance, 1..kLiftMax (b > 1: one active set)
+  const ActiveEntry* act_mid[kLiftMax - 1];  // active sets of levels p + 1, p + 2 (or nullptr)
+  int b;                    // levels to advance, 1..kLiftMax; a set that leaves the
+                            // active list before p + b stops there (its local finish)
   int pos_first;            // 1: the list is in level p's split order (its dimension is
                             // level p's), so the first level goes by position
   int shape;                // tile shape: index into kPartShape
-  int handoff;              // 1: every set goes to the local finish at level p + b
+  int handoff;              // 1: every set goes to the local finish (at level p + b,
+                            // or earlier where it leaves the active list)
   const uint4* in;          // list sorted by (tag on level p, key_dlist, index)
   uint4* out_next;          // the list on level p + b
   uint32_t* out_lorig;      // original indices for the local finish (sets leaving),

@@ -105,9 +105,11 @@ struct LiftSeg {
   uint32_t start;              // first position of the segment in the level-p array
   uint32_t left0;              // ss(lChild) of the segment's root: its pivot's rank
   uint32_t cs[kLiftBins];      // first output position of each child's run
-  uint32_t pk[kLiftBins - 1];  // pivots of the segment's first b levels, heap order
+  uint32_t pk[kLiftBins - 1];  // pivots of the segment's first bs levels, heap order
   uint32_t po[kLiftBins - 1];
   uint8_t dim[kLiftBins - 1];  // their split dimensions
+  int bs;                      // levels the segment descends: b, or fewer where its set
+                               // leaves the active list on the way
   int mode;                    // 0: next level's list, 1: original indices for the local finish
 };
 
@@ -129,34 +131,47 @@ __device__ inline void part_segment_at(const PartArgs& a, uint32_t j, uint32_t* 
 
 // One segment's setup, by the 16 lanes hl = 0..15 of a half warp: lanes
 // 0..7 the first output position of each descendant's run, lanes 8..14 the
-// pivots (and split dimensions) of the segment's first b levels, lane 0 the
-// rest; the pivot loads are issued side by side.
+// pivots (and split dimensions) of the segment's first bs levels, lane 0 the
+// rest; the pivot loads are issued side by side.  Every lane first follows
+// the set through the active lists of levels p + 1 .. p + b - 1: the set
+// descends while it is active (bs levels), and its pivots of level p + e sit
+// at its index in that level's active list.
 __device__ inline void lift_seg_info(const PartArgs& a, uint32_t ai, uint32_t srel, uint32_t start,
                                      LiftSeg* ps, uint32_t hl) {
   const LevelCtx& x = a.x;
   const ActiveEntry e = a.single ? a.act0 : x.act[ai];
   const SetInfo si = a.single ? a.set0 : x.sets[e.set];
   const Tree tree = make_tree(si.n);
-  const int mode = (a.handoff || e.next < 0) ? 1 : 0;
-  const uint32_t nb = 1u << a.b;
+  uint32_t idx[kLiftMax];
+  idx[0] = ai;
+  int bs = 1;
+  int32_t nxt = e.next;  // the set's index on level p + bs, -1 if it is not active there
+  while (bs < a.b && nxt >= 0) {
+    idx[bs] = (uint32_t)nxt;
+    nxt = a.act_mid[bs - 1][nxt].next;
+    ++bs;
+  }
+  const int mode = (a.handoff || nxt < 0) ? 1 : 0;  // mode 0: bs = b, nxt its index on p + b
+  const uint32_t nb = 1u << bs;
   if (hl == 0) {
     ps->start = start;
     ps->mode = mode;
+    ps->bs = bs;
     ps->left0 = LevelLayout::make(tree, x.l).left_size(srel);
   }
   if (hl < nb) {
     uint32_t base_out;
     if (mode == 1) base_out = si.off;
-    else base_out = a.single ? a.out_base0 : a.act_out[a.b == 1 ? (uint32_t)e.next : 0u].base;
-    const LevelLayout yo = LevelLayout::make(tree, x.l + a.b);
-    ps->cs[hl] = base_out + yo.seg_start((srel << a.b) + hl);
+    else base_out = a.single ? a.out_base0 : a.act_out[nxt].base;
+    const LevelLayout yo = LevelLayout::make(tree, x.l + bs);
+    ps->cs[hl] = base_out + yo.seg_start((srel << bs) + hl);
   }
   if (hl >= kLiftBins && hl - kLiftBins + 1 < nb) {
     const uint32_t h = hl - kLiftBins;
     const int e2 = 31 - __clz(h + 1);  // depth of heap node h below the segment
     const uint32_t rel = (srel << e2) + (h + 1 - (1u << e2));
     const int lq = x.l + e2;
-    const uint2 pv = a.piv[e2][(ai << lq) | rel];
+    const uint2 pv = a.piv[e2][(idx[e2] << lq) | rel];
     ps->pk[h] = pv.x;
     ps->po[h] = pv.y;
     ps->dim[h] = (uint8_t)(a.mode == 0 ? (lq + x.dim0) % a.k : a.dims[si.off + full_nodes(lq) + rel]);
@@ -340,7 +355,7 @@ __global__ void __launch_bounds__(PT, PB) partition_kernel(PartArgs a) {
         h = q < S.left0 ? 1u : 2u;
         e2 = 1;
       }
-      for (; e2 < a.b && !pinned; ++e2) {
+      for (; e2 < S.bs && !pinned; ++e2) {
         const uint32_t key = comp(en, S.dim[h]);
         const uint32_t pk = S.pk[h], po = S.po[h];
         if (key == pk && en.w == po) {
@@ -349,7 +364,7 @@ __global__ void __launch_bounds__(PT, PB) partition_kernel(PartArgs a) {
         }
         h = 2 * h + (before(key, en.w, pk, po) ? 1u : 2u);
       }
-      if (!pinned) bin = sg * kLiftBins + (h - (uint32_t)(nbin - 1));
+      if (!pinned) bin = sg * kLiftBins + (h - ((1u << S.bs) - 1u));
     }
     const uint32_t peers = __match_any_sync(0xffffffffu, bin);
     uint32_t prev = 0;
