@@ -191,6 +191,8 @@ def traffic_per_launch(kind: str, n_items_per_launch: float, shapes: dict):
         return None
     if not j.get("kernel_hash") or j["kernel_hash"] != kernel_hash(kind):
         return None
+    if kind == "radix_pass" and j.get("digit_bits", 8) != shapes.get("digit_bits", 8):
+        return None  # counted with another digit width
     shape = shapes.get({"partition_pass": "partition", "radix_pass": "radix"}.get(kind, ""))
     if shape is None:
         return j["dram_bytes_per_item"] * n_items_per_launch
@@ -298,8 +300,20 @@ def timed_builds(kdb, work, src, k: int, mode: int, steps: int, stream):
     return [a.elapsed_time(b) for a, b in ev], prof, launches
 
 
-def workload_leg(kdb, name: str, steps: int, warmup: int, peak: float, peak_src: str,
-                 shapes: dict) -> dict:
+def tuning_record(kdb, n: int, k: int, stride: int, mode_arg: int):
+    """The setting a build of this kind takes (its tuning-table entry, else
+    the process-wide setting): a record for the JSON line, and the shapes and
+    digit width that select stored counters."""
+    (p, r, bits), from_table = kdb.kdb_lookup_tuning(n, k, stride, mode_arg)
+    shapes = {"partition": kdb.kdb_tuning_shapes(kdb.TUNE_PARTITION)[p],
+              "radix": kdb.kdb_tuning_shapes(kdb.TUNE_RADIX)[r], "digit_bits": bits}
+    rec = {"indices": [p, r], "digit_bits": bits, "from_table": from_table,
+           "partition_shape": list(shapes["partition"]), "radix_shape": list(shapes["radix"]),
+           "shape_fields": ["threads", "items_per_thread", "blocks_per_sm"]}
+    return rec, shapes
+
+
+def workload_leg(kdb, name: str, steps: int, warmup: int, peak: float, peak_src: str) -> dict:
     """One more workload of the build, timed like the headline: device-resident
     input restored before each step, CUDA events, per-kernel rooflines."""
     import torch
@@ -310,6 +324,7 @@ def workload_leg(kdb, name: str, steps: int, warmup: int, peak: float, peak_src:
     work = torch.empty_like(src)
     del host
     stream = torch.cuda.current_stream()
+    tuned, shapes = tuning_record(kdb, n, k, 4 * sf, kdb._mode(src, mode))
     for _ in range(warmup):
         work.copy_(src)
         kdb.kdb_build(work, k, mode)
@@ -326,6 +341,7 @@ def workload_leg(kdb, name: str, steps: int, warmup: int, peak: float, peak_src:
            "ms_per_step_median": sorted(times)[len(times) // 2],
            "value": n / (ms / 1000.0) / 1e6, "unit": "Mpts/s", "gpu_launches": launches,
            "kernel_ms_per_step": {p["name"]: round(p["ms"] / steps, 3) for p in prof},
+           "tuning": tuned,
            "roofline": build_rooflines(prof, steps, n, stride, ms, peak, peak_src, shapes)}
     del src, work
     torch.cuda.empty_cache()
@@ -692,7 +708,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tile shapes instead of timing the compiled ones first")
     ap.add_argument("--tuning", default="",
-                    help="partition,radix tile-shape indices to use (skips the autotuner)")
+                    help="partition,radix tile-shape indices[,digit bits] to use (skips the autotuner)")
     ap.add_argument("--profile-only", action="store_true",
                     help="warm-up and one build, nothing timed (for ncu launch lists)")
     args = ap.parse_args()
@@ -735,14 +751,10 @@ def main():
     elif not args.no_autotune and not args.profile_only:
         r = kdb.kdb_autotune(src, k, mode, reps=3)
         autotune = {"best": list(r["best"]), "best_ms": r["best_ms"],
-                    "ms": {f"{p},{q}": round(v, 3) for (p, q), v in sorted(r["ms"].items())}}
-    tuning = kdb.kdb_get_tuning()
-    shapes = {"partition": kdb.kdb_tuning_shapes(kdb.TUNE_PARTITION)[tuning[0]],
-              "radix": kdb.kdb_tuning_shapes(kdb.TUNE_RADIX)[tuning[1]]}
-    tuned = {"indices": list(tuning),
-             "partition_shape": list(shapes["partition"]), "radix_shape": list(shapes["radix"]),
-             "shape_fields": ["threads", "items_per_thread", "blocks_per_sm"],
-             "autotune": autotune}
+                    "ms": {f"{p},{q},{b}": round(v, 3) for (p, q, b), v in sorted(r["ms"].items())},
+                    "key_fields": ["partition_shape", "radix_shape", "digit_bits"]}
+    tuned, shapes = tuning_record(kdb, n, k, stride, kdb._mode(src, mode))
+    tuned["autotune"] = autotune
 
     for _ in range(args.warmup):
         work.copy_(src)
@@ -846,8 +858,7 @@ def main():
         src = work = None
         for name in ("mixed_1e7_f3_rr", "aniso_1e8_f4_widest"):
             if name != args.workload:
-                legs[name] = workload_leg(kdb, name, min(args.steps, 20), args.warmup, peak,
-                                          peak_src, shapes)
+                legs[name] = workload_leg(kdb, name, min(args.steps, 20), args.warmup, peak, peak_src)
 
     batched = None
     if not args.no_batched:

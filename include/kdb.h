@@ -433,59 +433,89 @@ typedef enum { KDB_PLACEMENT_AUTO = 0, KDB_PLACEMENT_IN_PLACE = 1 } kdb_placemen
 KDB_API kdb_placement kdb_set_placement(kdb_placement placement);
 
 /*
- * Tile shapes of the two sort kernels of the per-dimension-list path (k <= 3):
- *   KDB_TUNE_PARTITION  the per-level stable split (the sorts of Sec. 3.1
- *                       that follow level 0, Observation 1 fused in);
- *   KDB_TUNE_RADIX      the passes of the level-0 sort.
- * The library carries a few compiled shapes of each.  A shape is threads per
- * block, entries per thread and resident blocks per SM.  The setting only
- * changes speed: every shape gives bit-identical output.
+ * Tuning of the per-dimension-list path (k <= 3).  Three choices, none of
+ * which changes the output (every choice gives bit-identical trees):
+ *   KDB_TUNE_PARTITION  tile shape of the per-level stable split (the sorts
+ *                       of Sec. 3.1 that follow level 0, Observation 1 fused
+ *                       in);
+ *   KDB_TUNE_RADIX      tile shape of the passes of the level-0 sort;
+ *   KDB_TUNE_DIGITS     digit width of the level-0 sort (the radix-key sort
+ *                       of Sec. 7.1): a 32-bit key takes 32 / width passes,
+ *                       rounded up.
+ * The library carries a few compiled shapes and widths.  A shape is threads
+ * per block, entries per thread and resident blocks per SM.
  *
- * kdb_tuning_shape_count -- number of shapes of `kernel`, or -1 for an
- *   unknown kernel.
+ * kdb_tuning_shape_count -- number of shapes (widths for KDB_TUNE_DIGITS) of
+ *   `kernel`, or -1 for an unknown kernel.
  * kdb_tuning_shape       -- shape `index` of `kernel` (host out-pointers, each
- *   may be NULL).  KDB_ERR_INVALID_ARGUMENT for an unknown kernel or index.
- * kdb_get_tuning / kdb_set_tuning -- the process-wide setting, read when a
- *   build is enqueued (a captured graph keeps the shapes it was captured
- *   with).  Default {0, 0}.  kdb_set_tuning returns KDB_ERR_INVALID_ARGUMENT
- *   and changes nothing if an index is out of range.
- * kdb_autotune -- times every pair of shapes on the caller's points and keeps
- *   the fastest pair as the process-wide setting.
+ *   may be NULL); for KDB_TUNE_DIGITS `threads` receives the width in bits,
+ *   `items_per_thread` the passes per key and `blocks_per_sm` 1.
+ *   KDB_ERR_INVALID_ARGUMENT for an unknown kernel or index.
+ * kdb_get_tuning / kdb_set_tuning -- the process-wide setting.  Default
+ *   {0, 0, 8}.  kdb_set_tuning returns KDB_ERR_INVALID_ARGUMENT and changes
+ *   nothing if a shape index is out of range or the width is not compiled.
+ *
+ * The tuning table keeps one setting per kind of build: (bit length of the
+ * total point count, k, stride_bytes, mode argument as given).  Every build
+ * takes its kind's entry when the table has one, else the process-wide
+ * setting, at the time it is planned (kdb_build and friends: at the call;
+ * kdb_plan_create: at creation, and a captured graph keeps what it was
+ * captured with).  The table holds at most 256 kinds; a new kind beyond
+ * that drops the oldest.  Thread safe.
+ * kdb_lookup_tuning -- the setting a build of this kind would take; host
+ *   out-pointers; *from_table (may be NULL) = 1 if it comes from the table.
+ *   KDB_ERR_INVALID_ARGUMENT if `out` is NULL or n < 0.
+ * kdb_clear_tuning_table -- forget every kept kind.
+ * kdb_autotune -- times every (partition shape, radix shape, width) on the
+ *   caller's points, keeps the fastest as the process-wide setting and as
+ *   the table entry of this kind of build.
  *     d_points    device, in: n points as for kdb_build; read only (each
  *                 trial builds a copy).
- *     reps        timed builds per pair, 1..64; a pair's time is the median.
- *     out_best    host, out (may be NULL): the chosen pair.
+ *     reps        timed builds per choice, 1..64; a choice's time is the
+ *                 median.
+ *     out_best    host, out (may be NULL): the chosen setting.
  *     out_best_ms host, out (may be NULL): its median build time.
- *     h_ms        host, out (may be NULL): kdb_tuning_shape_count(PARTITION)
- *                 x kdb_tuning_shape_count(RADIX) medians, partition shape
- *                 major; -1 for pairs not timed.  Where the build does not
- *                 use the tuned kernels (k > 3, or n too small for a global
- *                 level) only the current setting is timed and kept.
+ *     h_ms        host, out (may be NULL): count(PARTITION) x count(RADIX) x
+ *                 count(DIGITS) medians, partition shape major, width minor;
+ *                 -1 where not timed.  Where the build does not use the
+ *                 tuned kernels (k > 3, or n too small for a global level)
+ *                 only the current setting is timed and kept, and the table
+ *                 is left alone.
  *   Allocates a copy of the points and a workspace from the device's memory
  *   pool and frees them before returning.  Synchronous.  Returns the first
  *   build error, KDB_ERR_OUT_OF_MEMORY, or KDB_ERR_INVALID_ARGUMENT for bad
  *   arguments (as kdb_build, plus n < 2 or reps out of range).
+ * The workspace size of a build does not depend on the setting.
  */
-enum { KDB_TUNE_PARTITION = 0, KDB_TUNE_RADIX = 1 };
+enum { KDB_TUNE_PARTITION = 0, KDB_TUNE_RADIX = 1, KDB_TUNE_DIGITS = 2 };
 typedef struct {
-  int32_t partition_shape;
-  int32_t radix_shape;
+  int32_t partition_shape;  /* index into the partition shapes */
+  int32_t radix_shape;      /* index into the radix shapes */
+  int32_t digit_bits;       /* level-0 digit width in bits (a compiled width) */
 } kdb_tuning;
 KDB_API int kdb_tuning_shape_count(int kernel);
 KDB_API kdb_status kdb_tuning_shape(int kernel, int index, int* threads, int* items_per_thread,
                                     int* blocks_per_sm);
 KDB_API kdb_status kdb_get_tuning(kdb_tuning* out);
 KDB_API kdb_status kdb_set_tuning(const kdb_tuning* tuning);
+KDB_API kdb_status kdb_lookup_tuning(int64_t n, int k, int stride_bytes, kdb_split_mode mode,
+                                     kdb_tuning* out, int* from_table);
+KDB_API void kdb_clear_tuning_table(void);
 KDB_API kdb_status kdb_autotune(const void* d_points, int64_t n, int k, int stride_bytes,
                                 kdb_split_mode mode, int reps, kdb_tuning* out_best,
                                 float* out_best_ms, float* h_ms, kdb_stream_t stream);
 /*
- * kdb_save_tuning / kdb_load_tuning -- the process-wide setting as a small
- * JSON file: {"partition": [threads, items, blocks], "radix": [threads, items,
- * blocks]}.  Shapes are stored by value, so a file from a library with other
- * compiled shapes is refused on load (KDB_ERR_INVALID_ARGUMENT, setting
- * unchanged), as are unreadable or malformed files.  Saving returns
- * KDB_ERR_INVALID_ARGUMENT if the file cannot be written.  Host only.
+ * kdb_save_tuning / kdb_load_tuning -- the process-wide setting and the table
+ * as a small JSON file:
+ *   {"partition": [threads, items, blocks], "radix": [threads, items, blocks],
+ *    "digit_bits": w, "table": [{"log2n": b, "k": k, "stride": s, "mode": m,
+ *    "partition": [...], "radix": [...], "digit_bits": w}, ...]}
+ * Shapes are stored by value, so a file from a library with other compiled
+ * shapes or widths is refused on load (KDB_ERR_INVALID_ARGUMENT, setting and
+ * table unchanged), as are unreadable or malformed files and tables of more
+ * than 256 entries.  A missing "digit_bits" reads as 8 and a missing "table"
+ * as an empty one; loading replaces the setting and the whole table.  Saving
+ * returns KDB_ERR_INVALID_ARGUMENT if the file cannot be written.  Host only.
  */
 KDB_API kdb_status kdb_save_tuning(const char* path);
 KDB_API kdb_status kdb_load_tuning(const char* path);

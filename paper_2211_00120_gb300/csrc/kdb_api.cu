@@ -76,7 +76,54 @@ std::vector<ProfRec> g_prof;
 std::vector<cudaEvent_t> g_event_pool;
 std::atomic<int64_t> g_launches{0};
 std::atomic<int> g_placement{KDB_PLACEMENT_AUTO};
-std::atomic<int> g_part_shape{0}, g_rec_shape{0};  // tile shapes of the two sort kernels
+// Tuning: the process-wide setting (tile shapes of the two sort kernels and
+// the level-0 digit width), and a table of settings kept per kind of build,
+// keyed by (bit length of N, k, record stride, mode argument).  A build takes
+// its kind's entry, else the process-wide setting.
+std::atomic<int> g_part_shape{0}, g_rec_shape{0}, g_rec_bits{8};
+struct TuneEntry {
+  int log2n, k, stride, mode;  // the kind
+  int part, rec, bits;         // its setting
+};
+constexpr int kTuneTableMax = 256;
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune_table;
+
+int tune_bucket(uint64_t n) {  // bit length of n
+  int b = 0;
+  while (n) {
+    ++b;
+    n >>= 1;
+  }
+  return b;
+}
+
+// The setting a build of this kind takes; *found: whether it came from the table.
+TuneEntry tuning_for(uint64_t n, int k, int stride, int mode, bool* found) {
+  const int b = tune_bucket(n);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const TuneEntry& e : g_tune_table)
+      if (e.log2n == b && e.k == k && e.stride == stride && e.mode == mode) {
+        if (found) *found = true;
+        return e;
+      }
+  }
+  if (found) *found = false;
+  return TuneEntry{b, k, stride, mode, g_part_shape.load(), g_rec_shape.load(), g_rec_bits.load()};
+}
+
+// Keep (or replace) the entry of a kind; a full table drops its oldest entry.
+void put_tuning_entry(const TuneEntry& t) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (TuneEntry& e : g_tune_table)
+    if (e.log2n == t.log2n && e.k == t.k && e.stride == t.stride && e.mode == t.mode) {
+      e = t;
+      return;
+    }
+  if ((int)g_tune_table.size() >= kTuneTableMax) g_tune_table.erase(g_tune_table.begin());  // oldest out
+  g_tune_table.push_back(t);
+}
 
 struct SmemAttr {
   int dev;
@@ -195,7 +242,9 @@ struct Plan {
   int rank_passes = 0;
   bool singletons = false;  // a set of one record (its node is its record)
   bool too_wide = false;    // (set, subtree, rank) needs more than 64 bits
-  int part_shape = -1, rec_shape = -1;  // tile shapes; -1: the process-wide setting
+  int mode_arg = 0;     // the mode argument as given (the tuning table's key)
+  int part_shape = -1, rec_shape = -1;  // tile shapes; -1: from the tuning (make_plan)
+  int rec_bits = -1;                    // level-0 digit width; -1: from the tuning
   int dim0 = 0;              // round robin: level l splits in dimension (l + dim0) mod k
   bool has_domain = false;   // widest extent: the root's domain is given, not the scene box
   float domain[2 * kMaxK] = {};  // its lower corner, then its upper corner
@@ -241,6 +290,12 @@ inline int global_levels(const Plan& P, uint32_t n) {
 }
 
 void make_plan(Plan& P) {
+  if (P.part_shape < 0 || P.rec_shape < 0 || P.rec_bits < 0) {
+    const TuneEntry t = tuning_for(P.total, P.k, P.stride, P.mode_arg, nullptr);
+    if (P.part_shape < 0) P.part_shape = t.part;
+    if (P.rec_shape < 0) P.rec_shape = t.rec;
+    if (P.rec_bits < 0) P.rec_bits = t.bits;
+  }
   uint32_t nmax = 0;
   for (const SetInfo& s : P.sets) {
     nmax = std::max(nmax, s.n);
@@ -317,8 +372,8 @@ void make_plan(Plan& P) {
           chunk += e.cps;
         }
         P.chunks[0] = chunk;
-        P.rec_hist_off = hist_words;
-        hist_words += (size_t)P.k * 4 * na * kRadixBins;
+        P.rec_hist_off = hist_words;  // room for the most passes of any width
+        hist_words += (size_t)P.k * kRecMaxPasses * na * kRadixBins;
       }
     } else if (P.seg[l]) {
       P.passes[l] = std::max(1, ceil_div_i(P.rb, 8));
@@ -351,7 +406,7 @@ void make_plan(Plan& P) {
       if (j < P.act[l + 1].size() && P.act[l + 1][j].set == e.set) e.next = (int32_t)j;
     }
   }
-  P.total_passes += P.k * (P.use_lists ? 4 : P.rank_passes);
+  P.total_passes += P.k * (P.use_lists ? kRecMaxPasses : P.rank_passes);
 
   const uint64_t T = P.total;
   const size_t ksz = P.sets.size() > 1 ? 8 : 4;
@@ -510,8 +565,10 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
                          bool tables_ready = false, const HostFeed* feed = nullptr) {
   const uint32_t T = P.total;
   const int k = P.k;
-  const int part_shape = P.part_shape >= 0 ? P.part_shape : g_part_shape.load();
-  const int rec_shape = P.rec_shape >= 0 ? P.rec_shape : g_rec_shape.load();
+  const int part_shape = P.part_shape;
+  const int rec_shape = P.rec_shape;
+  const int rec_bits = P.rec_bits;
+  const int rec_np = rec_passes(rec_bits);
   uint64_t* keysA = at<uint64_t>(ws, P.o_keysA);
   uint64_t* keysB = at<uint64_t>(ws, P.o_keysB);
   uint32_t* valsA = at<uint32_t>(ws, P.o_valsA);
@@ -821,19 +878,20 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       rh.hist = hist + P.rec_hist_off;
       rh.nseg = x0.nact;
       rh.k = k;
+      rh.bits = rec_bits;
       {
         Prof pf(K_LISTS, (double)n0 * 16, 1, st);
         KDB_CK(launch_rec_hist(rh, st));
       }
       for (int d = 0; d < k; ++d) {
         const uint4* in = l0;
-        for (int p = 0; p < 4; ++p) {
+        for (int p = 0; p < rec_np; ++p) {
           // ping-pong between the dimension's two list buffers, ending in lcur
-          uint4* out = (p & 1) ? lcur[d] : lnext[d];
-          PassCtl c = ctl(n0, 8 * p, nullptr);
-          const uint32_t* sh = rh.hist + ((size_t)(d * 4 + p) * x0.nact) * kRadixBins;
+          uint4* out = ((rec_np - 1 - p) & 1) ? lnext[d] : lcur[d];
+          PassCtl c = ctl(n0, rec_bits * p, nullptr);
+          const uint32_t* sh = rh.hist + ((size_t)(d * rec_np + p) * x0.nact) * kRadixBins;
           Prof pf(K_RADIX, (double)n0 * 32, 1, st);
-          KDB_CK(launch_rec_sort_pass(in, out, c, x0, sh, d, rec_shape, st));
+          KDB_CK(launch_rec_sort_pass(in, out, c, x0, sh, d, rec_shape, rec_bits, st));
           in = out;
         }
       }
@@ -1220,6 +1278,7 @@ kdb_placement kdb_set_placement(kdb_placement placement) {
 int kdb_tuning_shape_count(int kernel) {
   if (kernel == KDB_TUNE_PARTITION) return kPartShapes;
   if (kernel == KDB_TUNE_RADIX) return kRecShapes;
+  if (kernel == KDB_TUNE_DIGITS) return kRecDigitWidths;
   return -1;
 }
 
@@ -1227,6 +1286,12 @@ kdb_status kdb_tuning_shape(int kernel, int index, int* threads, int* items_per_
                             int* blocks_per_sm) {
   const int count = kdb_tuning_shape_count(kernel);
   if (count < 0 || index < 0 || index >= count) return KDB_ERR_INVALID_ARGUMENT;
+  if (kernel == KDB_TUNE_DIGITS) {  // width in bits, passes per 32-bit key
+    if (threads) *threads = kRecDigitBits[index];
+    if (items_per_thread) *items_per_thread = rec_passes(kRecDigitBits[index]);
+    if (blocks_per_sm) *blocks_per_sm = 1;
+    return KDB_OK;
+  }
   const TileShape& sh = kernel == KDB_TUNE_PARTITION ? kPartShape[index] : kRecShape[index];
   if (threads) *threads = sh.threads;
   if (items_per_thread) *items_per_thread = sh.items;
@@ -1234,64 +1299,197 @@ kdb_status kdb_tuning_shape(int kernel, int index, int* threads, int* items_per_
   return KDB_OK;
 }
 
+namespace {
+int width_index(int bits) {
+  for (int i = 0; i < kRecDigitWidths; ++i)
+    if (kRecDigitBits[i] == bits) return i;
+  return -1;
+}
+bool tuning_valid(const kdb_tuning& t) {
+  return t.partition_shape >= 0 && t.partition_shape < kPartShapes && t.radix_shape >= 0 &&
+         t.radix_shape < kRecShapes && width_index(t.digit_bits) >= 0;
+}
+}  // namespace
+
 kdb_status kdb_get_tuning(kdb_tuning* out) {
   if (!out) return KDB_ERR_INVALID_ARGUMENT;
   out->partition_shape = g_part_shape.load();
   out->radix_shape = g_rec_shape.load();
+  out->digit_bits = g_rec_bits.load();
   return KDB_OK;
 }
 
 kdb_status kdb_set_tuning(const kdb_tuning* t) {
-  if (!t || t->partition_shape < 0 || t->partition_shape >= kPartShapes || t->radix_shape < 0 ||
-      t->radix_shape >= kRecShapes)
-    return KDB_ERR_INVALID_ARGUMENT;
+  if (!t || !tuning_valid(*t)) return KDB_ERR_INVALID_ARGUMENT;
   g_part_shape.store(t->partition_shape);
   g_rec_shape.store(t->radix_shape);
+  g_rec_bits.store(t->digit_bits);
   return KDB_OK;
+}
+
+kdb_status kdb_lookup_tuning(int64_t n, int k, int stride_bytes, kdb_split_mode mode, kdb_tuning* out,
+                             int* from_table) {
+  if (!out || n < 0) return KDB_ERR_INVALID_ARGUMENT;
+  bool found = false;
+  const TuneEntry e = tuning_for((uint64_t)n, k, stride_bytes, (int)mode, &found);
+  *out = kdb_tuning{e.part, e.rec, e.bits};
+  if (from_table) *from_table = found ? 1 : 0;
+  return KDB_OK;
+}
+
+void kdb_clear_tuning_table(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_table.clear();
 }
 
 kdb_status kdb_save_tuning(const char* path) {
   if (!path) return KDB_ERR_INVALID_ARGUMENT;
-  const TileShape& p = kPartShape[g_part_shape.load()];
-  const TileShape& r = kRecShape[g_rec_shape.load()];
+  std::vector<TuneEntry> table;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    table = g_tune_table;
+  }
   FILE* f = fopen(path, "w");
   if (!f) return KDB_ERR_INVALID_ARGUMENT;
-  const int w = fprintf(f, "{\"partition\": [%d, %d, %d], \"radix\": [%d, %d, %d]}\n", p.threads,
-                        p.items, p.blocks, r.threads, r.items, r.blocks);
-  return (fclose(f) == 0 && w > 0) ? KDB_OK : KDB_ERR_INVALID_ARGUMENT;
+  auto shape = [](const TileShape& sh) {
+    char b[64];
+    snprintf(b, sizeof b, "[%d, %d, %d]", sh.threads, sh.items, sh.blocks);
+    return std::string(b);
+  };
+  std::string text = "{\"partition\": " + shape(kPartShape[g_part_shape.load()]) +
+                     ", \"radix\": " + shape(kRecShape[g_rec_shape.load()]) +
+                     ", \"digit_bits\": " + std::to_string(g_rec_bits.load()) + ", \"table\": [";
+  for (size_t i = 0; i < table.size(); ++i) {
+    const TuneEntry& e = table[i];
+    text += (i ? ",\n  " : "\n  ");
+    text += "{\"log2n\": " + std::to_string(e.log2n) + ", \"k\": " + std::to_string(e.k) +
+            ", \"stride\": " + std::to_string(e.stride) + ", \"mode\": " + std::to_string(e.mode) +
+            ", \"partition\": " + shape(kPartShape[e.part]) + ", \"radix\": " + shape(kRecShape[e.rec]) +
+            ", \"digit_bits\": " + std::to_string(e.bits) + "}";
+  }
+  text += "]}\n";
+  const size_t w = fwrite(text.data(), 1, text.size(), f);
+  return (fclose(f) == 0 && w == text.size()) ? KDB_OK : KDB_ERR_INVALID_ARGUMENT;
 }
 
 namespace {
-// The three integers of the array that follows "key": in a JSON text; false
-// if the key is missing or the value is not an array of three integers.
-bool json_shape(const std::string& text, const char* key, TileShape* out) {
-  const std::string k = std::string("\"") + key + "\"";
-  size_t at = text.find(k);
-  if (at == std::string::npos) return false;
-  at = text.find_first_not_of(" \t\r\n", at + k.size());
-  if (at == std::string::npos || text[at] != ':') return false;
-  at = text.find_first_not_of(" \t\r\n", at + 1);
-  if (at == std::string::npos || text[at] != '[') return false;
-  const char* c = text.c_str() + at + 1;
-  int v[3];
-  for (int i = 0; i < 3; ++i) {
-    char* end = nullptr;
-    const long x = strtol(c, &end, 10);
-    if (end == c || x < 1 || x > 4096) return false;
-    v[i] = (int)x;
-    while (*end == ' ' || *end == '\t' || *end == '\r' || *end == '\n') ++end;
-    if (*end != (i < 2 ? ',' : ']')) return false;
-    c = end + 1;
+// A small JSON reader for the tuning file: objects, arrays, integers and
+// plain strings (no escapes), nested at most four deep.
+struct JVal {
+  enum Kind { NONE, INT, STR, ARR, OBJ } kind = NONE;
+  long long num = 0;
+  std::string str;
+  std::vector<std::string> keys;  // OBJ: parallel to items
+  std::vector<JVal> items;        // ARR elements or OBJ values
+  const JVal* get(const char* key) const {
+    if (kind != OBJ) return nullptr;
+    for (size_t i = 0; i < keys.size(); ++i)
+      if (keys[i] == key) return &items[i];
+    return nullptr;
   }
-  *out = TileShape{v[0], v[1], v[2]};
+};
+
+struct JReader {
+  const char* p;
+  const char* end;
+  void ws() {
+    while (p < end && (*p == ' ' || *p == '\t' || *p == '\r' || *p == '\n')) ++p;
+  }
+  bool text(std::string& s) {
+    if (p >= end || *p != '"') return false;
+    const char* b = ++p;
+    while (p < end && *p != '"') {
+      if (*p == '\\' || (unsigned char)*p < 0x20) return false;
+      ++p;
+    }
+    if (p >= end || p - b > 64) return false;
+    s.assign(b, p);
+    ++p;
+    return true;
+  }
+  bool value(JVal& v, int depth) {
+    if (depth > 4) return false;
+    ws();
+    if (p >= end) return false;
+    if (*p == '{' || *p == '[') {
+      const bool obj = *p == '{';
+      const char close = obj ? '}' : ']';
+      v.kind = obj ? JVal::OBJ : JVal::ARR;
+      ++p;
+      ws();
+      if (p < end && *p == close) {
+        ++p;
+        return true;
+      }
+      for (;;) {
+        if (v.items.size() >= 4096) return false;
+        if (obj) {
+          ws();
+          std::string key;
+          if (!text(key)) return false;
+          ws();
+          if (p >= end || *p != ':') return false;
+          ++p;
+          v.keys.push_back(key);
+        }
+        v.items.emplace_back();
+        if (!value(v.items.back(), depth + 1)) return false;
+        ws();
+        if (p >= end) return false;
+        if (*p == ',') {
+          ++p;
+          continue;
+        }
+        if (*p != close) return false;
+        ++p;
+        return true;
+      }
+    }
+    if (*p == '"') {
+      v.kind = JVal::STR;
+      return text(v.str);
+    }
+    const bool neg = *p == '-';
+    if (neg) ++p;
+    long long x = 0;
+    int digits = 0;
+    while (p < end && *p >= '0' && *p <= '9') {
+      if (++digits > 12) return false;
+      x = 10 * x + (*p - '0');
+      ++p;
+    }
+    if (digits == 0) return false;
+    v.kind = JVal::INT;
+    v.num = neg ? -x : x;
+    return true;
+  }
+};
+
+bool json_int(const JVal* v, long long lo, long long hi, int* out) {
+  if (!v || v->kind != JVal::INT || v->num < lo || v->num > hi) return false;
+  *out = (int)v->num;
   return true;
 }
 
-int shape_index(const TileShape* table, int count, const TileShape& s) {
+// index of the compiled shape stored by value as [threads, items, blocks]
+int json_shape(const JVal* v, const TileShape* table, int count) {
+  if (!v || v->kind != JVal::ARR || v->items.size() != 3) return -1;
+  int x[3];
+  for (int i = 0; i < 3; ++i)
+    if (!json_int(&v->items[i], 1, 4096, &x[i])) return -1;
   for (int i = 0; i < count; ++i)
-    if (table[i].threads == s.threads && table[i].items == s.items && table[i].blocks == s.blocks)
-      return i;
+    if (table[i].threads == x[0] && table[i].items == x[1] && table[i].blocks == x[2]) return i;
   return -1;
+}
+
+// a setting: "partition", "radix" and (default 8) "digit_bits"
+bool json_tuning(const JVal& o, kdb_tuning* t) {
+  t->partition_shape = json_shape(o.get("partition"), kPartShape, kPartShapes);
+  t->radix_shape = json_shape(o.get("radix"), kRecShape, kRecShapes);
+  t->digit_bits = 8;
+  const JVal* b = o.get("digit_bits");
+  if (b && !json_int(b, 1, 32, &t->digit_bits)) return false;
+  return tuning_valid(*t);
 }
 }  // namespace
 
@@ -1300,14 +1498,45 @@ kdb_status kdb_load_tuning(const char* path) {
   FILE* f = fopen(path, "r");
   if (!f) return KDB_ERR_INVALID_ARGUMENT;
   std::string text;
-  char buf[512];
+  char buf[4096];
   size_t got;
-  while ((got = fread(buf, 1, sizeof buf, f)) > 0 && text.size() < 65536) text.append(buf, got);
+  while ((got = fread(buf, 1, sizeof buf, f)) > 0 && text.size() <= (1u << 18)) text.append(buf, got);
   fclose(f);
-  TileShape p, r;
-  if (!json_shape(text, "partition", &p) || !json_shape(text, "radix", &r)) return KDB_ERR_INVALID_ARGUMENT;
-  const kdb_tuning t{shape_index(kPartShape, kPartShapes, p), shape_index(kRecShape, kRecShapes, r)};
-  return kdb_set_tuning(&t);  // refuses a shape this library does not carry
+  if (text.size() > (1u << 18)) return KDB_ERR_INVALID_ARGUMENT;
+  JVal root;
+  JReader r{text.data(), text.data() + text.size()};
+  if (!r.value(root, 0) || root.kind != JVal::OBJ) return KDB_ERR_INVALID_ARGUMENT;
+  r.ws();
+  if (r.p != r.end) return KDB_ERR_INVALID_ARGUMENT;
+  kdb_tuning g{};
+  if (!json_tuning(root, &g)) return KDB_ERR_INVALID_ARGUMENT;
+  std::vector<TuneEntry> table;
+  if (const JVal* tv = root.get("table")) {  // absent: an empty table
+    if (tv->kind != JVal::ARR || tv->items.size() > (size_t)kTuneTableMax) return KDB_ERR_INVALID_ARGUMENT;
+    for (const JVal& o : tv->items) {
+      if (o.kind != JVal::OBJ) return KDB_ERR_INVALID_ARGUMENT;
+      TuneEntry e{};
+      kdb_tuning t{};
+      if (!json_int(o.get("log2n"), 0, 64, &e.log2n) || !json_int(o.get("k"), 1, kMaxK, &e.k) ||
+          !json_int(o.get("stride"), 1, 1 << 24, &e.stride) || !json_int(o.get("mode"), 0, 1 << 16, &e.mode) ||
+          !json_tuning(o, &t))
+        return KDB_ERR_INVALID_ARGUMENT;
+      e.part = t.partition_shape;
+      e.rec = t.radix_shape;
+      e.bits = t.digit_bits;
+      bool dup = false;  // a repeated kind: the later entry wins
+      for (TuneEntry& x : table)
+        if (x.log2n == e.log2n && x.k == e.k && x.stride == e.stride && x.mode == e.mode) {
+          x = e;
+          dup = true;
+        }
+      if (!dup) table.push_back(e);
+    }
+  }
+  kdb_set_tuning(&g);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_table = table;
+  return KDB_OK;
 }
 
 kdb_status kdb_autotune(const void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
@@ -1319,6 +1548,7 @@ kdb_status kdb_autotune(const void* d_points, int64_t n, int k, int stride_bytes
   if (n < 2 || reps < 1 || reps > 64 || !d_points || (reinterpret_cast<uintptr_t>(d_points) & 3))
     return KDB_ERR_INVALID_ARGUMENT;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const kdb_tuning cur{g_part_shape.load(), g_rec_shape.load(), g_rec_bits.load()};
   Plan P;
   P.sets.push_back(SetInfo{0u, (uint32_t)n});
   P.total = (uint32_t)n;
@@ -1326,6 +1556,10 @@ kdb_status kdb_autotune(const void* d_points, int64_t n, int k, int stride_bytes
   P.stride = stride_bytes;
   P.mode = split_of(mode);
   P.ctype = ctype_of(mode);
+  P.mode_arg = (int)mode;
+  P.part_shape = cur.partition_shape;  // the workspace does not depend on the setting
+  P.rec_shape = cur.radix_shape;
+  P.rec_bits = cur.digit_bits;
   make_plan(P);
   if (P.too_wide) return KDB_ERR_INVALID_ARGUMENT;
   int dev, sms;
@@ -1341,15 +1575,16 @@ kdb_status kdb_autotune(const void* d_points, int64_t n, int k, int stride_bytes
     s = KDB_ERR_CUDA;
   // the tuned kernels run only on the list path with at least one global level
   const bool tuned = P.use_lists && !P.act.empty();
-  const kdb_tuning cur{g_part_shape.load(), g_rec_shape.load()};
-  const int np = kPartShapes, nr = kRecShapes;
-  std::vector<float> med(np * nr, -1.0f);
+  const int np = kPartShapes, nr = kRecShapes, nw = kRecDigitWidths;
+  const int combos = np * nr * nw;
+  std::vector<float> med(combos, -1.0f);
   std::vector<float> t(reps);
-  for (int c = 0; c < np * nr && s == KDB_OK; ++c) {
-    const int ps = c / nr, rs = c % nr;
-    if (!tuned && (ps != cur.partition_shape || rs != cur.radix_shape)) continue;
+  for (int c = 0; c < combos && s == KDB_OK; ++c) {
+    const int ps = c / (nr * nw), rs = (c / nw) % nr, bits = kRecDigitBits[c % nw];
+    if (!tuned && (ps != cur.partition_shape || rs != cur.radix_shape || bits != cur.digit_bits)) continue;
     P.part_shape = ps;
     P.rec_shape = rs;
+    P.rec_bits = bits;
     for (int r = -1; r < reps && s == KDB_OK; ++r) {  // r = -1: untimed first build
       if (cudaMemcpyAsync(copy, d_points, pts_bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
           cudaEventRecord(ev[0], st) != cudaSuccess) {
@@ -1370,11 +1605,14 @@ kdb_status kdb_autotune(const void* d_points, int64_t n, int k, int stride_bytes
     }
   }
   int best = -1;
-  for (int c = 0; c < np * nr; ++c)
+  for (int c = 0; c < combos; ++c)
     if (med[c] >= 0.0f && (best < 0 || med[c] < med[best])) best = c;
   if (s == KDB_OK && best >= 0) {
-    const kdb_tuning b{best / nr, best % nr};
+    const kdb_tuning b{best / (nr * nw), (best / nw) % nr, kRecDigitBits[best % nw]};
     kdb_set_tuning(&b);
+    if (tuned)  // kept for later builds of this kind
+      put_tuning_entry(TuneEntry{tune_bucket((uint64_t)n), k, stride_bytes, (int)mode, b.partition_shape,
+                                 b.radix_shape, b.digit_bits});
     if (out_best) *out_best = b;
     if (out_best_ms) *out_best_ms = med[best];
     if (h_ms) std::copy(med.begin(), med.end(), h_ms);
@@ -1404,6 +1642,7 @@ size_t kdb_workspace_size(int64_t n, int k, int stride_bytes, kdb_split_mode mod
   P.stride = stride_bytes;
   P.mode = split_of(mode);
   P.ctype = ctype_of(mode);
+  P.mode_arg = (int)mode;
   make_plan(P);
   return P.bytes;
 }
@@ -1433,6 +1672,7 @@ kdb_status kdb_build_ex(void* d_points, int64_t n, int k, int stride_bytes, kdb_
   P.stride = stride_bytes;
   P.mode = split_of(mode);
   P.ctype = ctype_of(mode);
+  P.mode_arg = (int)mode;
   return run(P, static_cast<unsigned char*>(d_points), d_workspace, workspace_bytes,
              d_out_orig_index, d_out_split_dim, st);
 }
@@ -1463,6 +1703,7 @@ kdb_status kdb_build_subtree(void* d_points, int64_t n, int k, int stride_bytes,
   P.stride = stride_bytes;
   P.mode = split;
   P.ctype = ctype_of(mode);
+  P.mode_arg = (int)mode;
   P.dim0 = split == KDB_SPLIT_ROUND_ROBIN ? first_dim : 0;
   if (split == KDB_SPLIT_WIDEST_EXTENT) {
     P.has_domain = true;
@@ -1494,6 +1735,7 @@ kdb_status kdb_build_noalloc(void* d_points, int64_t n, int k, int stride_bytes,
   P.stride = stride_bytes;
   P.mode = split_of(mode);
   P.ctype = ctype_of(mode);
+  P.mode_arg = (int)mode;
   make_plan(P);
   if (P.too_wide || P.bytes > KDB_NOALLOC_SCRATCH_BYTES) return KDB_ERR_INVALID_ARGUMENT;
   int dev = 0;
@@ -1711,6 +1953,7 @@ kdb_status kdb_build_batched(void* d_points, const int64_t* h_offsets, int num_s
   P.stride = stride_bytes;
   P.mode = split_of(mode);
   P.ctype = ctype_of(mode);
+  P.mode_arg = (int)mode;
   return run(P, static_cast<unsigned char*>(d_points), nullptr, 0, nullptr, nullptr,
              reinterpret_cast<cudaStream_t>(stream));
 }
@@ -1736,6 +1979,7 @@ kdb_status batched_sets(Plan& P, const int64_t* h_offsets, int num_sets, int k, 
   P.stride = stride_bytes;
   P.mode = split_of(mode);
   P.ctype = ctype_of(mode);
+  P.mode_arg = (int)mode;
   return KDB_OK;
 }
 }  // namespace
@@ -1812,6 +2056,7 @@ kdb_status kdb_plan_create(const int64_t* h_offsets, int num_sets, int k, int st
   P.stride = stride_bytes;
   P.mode = split_of(mode);
   P.ctype = ctype_of(mode);
+  P.mode_arg = (int)mode;
   po->trivial = total <= 1;
   if (po->trivial) {
     *out_plan = reinterpret_cast<kdb_plan>(po);
@@ -1916,6 +2161,7 @@ kdb_status kdb_build_host(void* h_points, int64_t n, int k, int stride_bytes, kd
   P.stride = stride_bytes;
   P.mode = split_of(mode);
   P.ctype = ctype_of(mode);
+  P.mode_arg = (int)mode;
   make_plan(P);
   if (P.too_wide) return KDB_ERR_INVALID_ARGUMENT;
   // Records without payload in page-locked memory that this device can

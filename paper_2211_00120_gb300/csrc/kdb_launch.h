@@ -56,6 +56,14 @@ constexpr int kPartTile = 128 * 13;
 constexpr int kRecTileMin = 256 * 13;
 static_assert(kRecTileMin <= 512 * 8, "the smallest record-sort tile");
 static_assert(512 * 13 < (1 << 13) - 1, "partition tiles hold at most two segments");
+// Digit widths of the level-0 sort: a 32-bit key takes rec_passes(bits)
+// passes.  Histograms and look-back words keep a stride of kRadixBins per
+// (pass, segment) and per tile whatever the width.
+constexpr int kRecDigitWidths = 2;
+constexpr int kRecDigitBits[kRecDigitWidths] = {8, 6};
+constexpr int kRecMaxPasses = 6;
+constexpr int rec_passes(int bits) { return (32 + bits - 1) / bits; }
+static_assert(rec_passes(8) <= kRecMaxPasses && rec_passes(6) <= kRecMaxPasses, "passes");
 struct ListBuildArgs {      // level-0 array of several sets
   LevelCtx x;               // level 0
   uint32_t items;
@@ -67,9 +75,10 @@ struct RecHistArgs {        // digit histograms per (dimension, pass, set)
   LevelCtx x;               // level 0 (chunk0 / cps filled in)
   uint32_t chunks;
   const uint4* ents;        // level-0 array
-  uint32_t* hist;           // [k*4][nseg][256]
+  uint32_t* hist;           // [k * passes][nseg][256]
   uint32_t nseg;
   int k;
+  int bits;                 // digit width: one of kRecDigitBits
 };
 struct PivotArgs {
   LevelCtx x;
@@ -135,7 +144,7 @@ uint32_t rec_sort_tile();  // entries of the smallest record-sort tile (one look
 cudaError_t launch_gather_level0(const ListBuildArgs& a, cudaStream_t st);
 cudaError_t launch_rec_hist(const RecHistArgs& a, cudaStream_t st);
 cudaError_t launch_rec_sort_pass(const uint4* in, uint4* out, const PassCtl& c, const LevelCtx& x,
-                                 const uint32_t* seg_hist, int d, int shape, cudaStream_t st);
+                                 const uint32_t* seg_hist, int d, int shape, int bits, cudaStream_t st);
 cudaError_t launch_pivots(const PivotArgs& a, cudaStream_t st);
 cudaError_t launch_partition(const PartArgs& a, cudaStream_t st);
 

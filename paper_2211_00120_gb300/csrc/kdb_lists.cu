@@ -6,10 +6,10 @@
 // with the tie rule.
 //
 // For every dimension d, list d is a stable LSD radix sort of the entries by
-// key_d (4 passes of 8-bit digits, each a segmented onesweep pass over 16-byte
-// records, one segment per set) starting from input order, which leaves list d
-// sorted by (key_d, original index): the order the level-0 sort produces when
-// d is the root's split dimension.
+// key_d (4 passes of 8-bit digits, or 6 passes of 6-bit digits, each a
+// segmented onesweep pass over 16-byte records, one segment per set) starting
+// from input order, which leaves list d sorted by (key_d, original index): the
+// order the level-0 sort produces when d is the root's split dimension.
 #include "kdb_launch.h"
 #include "kdb_segsort.cuh"
 
@@ -37,9 +37,12 @@ __global__ void gather_level0_kernel(ListBuildArgs a) {
 }
 
 // Digit histograms of every (dimension, pass, segment) of the level-0 array;
-// one block per chunk of one segment (a set).
+// one block per chunk of one segment (a set).  BITS: the digit width.
+template <int BITS>
 __global__ void __launch_bounds__(256) rec_hist_kernel(RecHistArgs a) {
-  __shared__ uint32_t s_hist[3 * 4 * kRadixBins];
+  constexpr int P = rec_passes(BITS);
+  constexpr uint32_t R = 1u << BITS;
+  __shared__ uint32_t s_hist[3 * P * R];
   if (*reinterpret_cast<volatile uint32_t*>(a.x.err)) return;
   const LevelCtx& x = a.x;
   const uint32_t g = blockIdx.x;
@@ -57,38 +60,41 @@ __global__ void __launch_bounds__(256) rec_hist_kernel(RecHistArgs a) {
   const uint32_t beg = e.base + (g - e.chunk0) * kSegChunk;
   const uint32_t end = min(e.base + n, beg + kSegChunk);
   if (beg >= end) return;
-  const int H = a.k * 4 * kRadixBins;
+  const int H = a.k * P * (int)R;
   for (int i = threadIdx.x; i < H; i += blockDim.x) s_hist[i] = 0;
   __syncthreads();
   for (uint32_t j = beg + threadIdx.x; j < end; j += blockDim.x) {
     const uint4 en = a.ents[j];
     for (int d = 0; d < a.k; ++d) {
       const uint32_t key = comp(en, d);
-      for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[(d * 4 + p) * kRadixBins + ((key >> (8 * p)) & 255u)], 1u);
+#pragma unroll
+      for (int p = 0; p < P; ++p) atomicAdd(&s_hist[(d * P + p) * R + ((key >> (BITS * p)) & (R - 1u))], 1u);
     }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < H; i += blockDim.x) {
     const uint32_t v = s_hist[i];
     if (v) {
-      const int dp = i / kRadixBins, dg = i % kRadixBins;  // dp = d * 4 + p
+      const int dp = i / R, dg = i % R;  // dp = d * P + p
       atomicAdd(a.hist + ((uint64_t)dp * a.nseg + ai) * kRadixBins + dg, v);
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// One stable LSD pass over 16-byte entries by digit (key_d >> shift) & 255,
-// every set its own segment.  The tile's records are staged by bulk copy; only
+// One stable LSD pass over 16-byte entries by digit (key_d >> shift) of BITS
+// bits, every set its own segment.  The tile's records are staged by bulk copy; only
 // their slot order is staged for the write-out, which reads the records from
 // shared memory in digit order and writes each digit's run contiguously.
 // The tile shape (threads RT, entries per thread RI, resident blocks RB) is a
 // template parameter; the shapes built are listed in kRecShape.
-template <int RT, int RI, int RB>
+template <int RT, int RI, int RB, int BITS>
 __global__ void __launch_bounds__(RT, RB)
     rec_sort_pass(const uint4* __restrict__ in, uint4* __restrict__ out, PassCtl c, LevelCtx x,
                   const uint32_t* __restrict__ seg_hist, int d) {
-  constexpr int BINS = 2 * kRadix;
+  constexpr int RADIX = 1 << BITS;
+  constexpr uint32_t DMASK = RADIX - 1;
+  constexpr int BINS = 2 * RADIX;  // (segment A or B) x digit
   constexpr int RTILE = RT * RI;
   constexpr int RW = RT / 32;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -181,8 +187,8 @@ __global__ void __launch_bounds__(RT, RB)
     const uint32_t p = wbase + i * 32 + lane;
     const bool ok = p < tn;
     uint32_t bin = BINS;
-    if (ok) bin = ((p >= bpos) ? (uint32_t)kRadix : 0u) | ((comp(s_rec[p], d) >> c.shift) & 255u);
-    const uint32_t peers = warp_peers(bin, ok, 9);  // (segment, digit): 9 bits
+    if (ok) bin = ((p >= bpos) ? (uint32_t)RADIX : 0u) | ((comp(s_rec[p], d) >> c.shift) & DMASK);
+    const uint32_t peers = warp_peers(bin, ok, BITS + 1);  // (segment, digit)
     uint32_t before = 0;
     if (ok) before = s_whist[warp * BINS + bin];
     __syncwarp();
@@ -193,12 +199,12 @@ __global__ void __launch_bounds__(RT, RB)
   }
   __syncthreads();
   uint32_t cA = 0, cB = 0;
-  if (tid < kRadix) {
+  if (tid < RADIX) {
 #pragma unroll
     for (int w = 0; w < RW; ++w) {
-      const uint32_t ta = s_whist[w * BINS + tid], tb2 = s_whist[w * BINS + kRadix + tid];
+      const uint32_t ta = s_whist[w * BINS + tid], tb2 = s_whist[w * BINS + RADIX + tid];
       s_whist[w * BINS + tid] = (uint16_t)cA;
-      s_whist[w * BINS + kRadix + tid] = (uint16_t)cB;
+      s_whist[w * BINS + RADIX + tid] = (uint16_t)cB;
       cA += ta;
       cB += tb2;
     }
@@ -207,20 +213,20 @@ __global__ void __launch_bounds__(RT, RB)
     else st_relaxed_u64(mine, lb_pack(kFlagAgg, c.epoch, cA));
   }
   uint32_t hA = 0, hB = 0;
-  if (tid < kRadix) {
+  if (tid < RADIX) {
     hA = seg_hist[(uint64_t)s_ts.gid[0] * kRadix + tid];
     hB = hasB ? seg_hist[(uint64_t)s_ts.gid[1] * kRadix + tid] : 0u;
   }
   const uint64_t tsc = block_excl_scan64<RT>((uint64_t)cA | ((uint64_t)cB << 32), s_scan64);
   const uint64_t hsc = block_excl_scan64<RT>((uint64_t)hA | ((uint64_t)hB << 32), s_scan64);
-  if (tid == kRadix - 1) s_totA = (uint32_t)tsc + cA;
+  if (tid == RADIX - 1) s_totA = (uint32_t)tsc + cA;
   __syncthreads();
   uint32_t toffA = 0, toffB = 0;
-  if (tid < kRadix) {
+  if (tid < RADIX) {
     toffA = (uint32_t)tsc;
     toffB = (uint32_t)(tsc >> 32) + s_totA;
     s_toff[tid] = toffA;
-    s_toff[kRadix + tid] = toffB;
+    s_toff[RADIX + tid] = toffB;
   }
   __syncthreads();
 #pragma unroll
@@ -231,7 +237,7 @@ __global__ void __launch_bounds__(RT, RB)
       s_slot[s_toff[bin] + s_whist[warp * BINS + bin] + rnk[i]] = (uint16_t)p;
     }
   }
-  if (tid < kRadix) {
+  if (tid < RADIX) {
     uint32_t prefA = 0;
     if (a_cont && s_abort == 0) {
       if (!look_back<16>(c, tile, tid, &prefA)) {
@@ -242,14 +248,14 @@ __global__ void __launch_bounds__(RT, RB)
                                 lb_pack(kFlagPre, c.epoch, prefA + cA));
     }
     s_gbase[tid] = s_ts.start[0] + (uint32_t)hsc + prefA - toffA;
-    s_gbase[kRadix + tid] = s_ts.start[1] + (uint32_t)(hsc >> 32) - toffB;
+    s_gbase[RADIX + tid] = s_ts.start[1] + (uint32_t)(hsc >> 32) - toffB;
   }
   __syncthreads();
   if (s_abort) return;
   const uint32_t totA = s_totA;
   for (uint32_t sl = tid; sl < tn; sl += RT) {
     const uint4 rec = s_rec[s_slot[sl]];
-    const uint32_t bin = (sl >= totA ? (uint32_t)kRadix : 0u) | ((comp(rec, d) >> c.shift) & 255u);
+    const uint32_t bin = (sl >= totA ? (uint32_t)RADIX : 0u) | ((comp(rec, d) >> c.shift) & DMASK);
     const uint32_t dest = s_gbase[bin] + sl;
     if (dest >= c.n) {
       atomicOr(c.err, ERR_INTERNAL);
@@ -275,30 +281,37 @@ cudaError_t launch_gather_level0(const ListBuildArgs& a, cudaStream_t st) {
 
 cudaError_t launch_rec_hist(const RecHistArgs& a, cudaStream_t st) {
   if (a.chunks == 0) return cudaSuccess;
-  rec_hist_kernel<<<a.chunks, 256, 0, st>>>(a);
+  static_assert(kRecDigitWidths == 2, "one launcher per width");
+  if (a.bits == 6) rec_hist_kernel<6><<<a.chunks, 256, 0, st>>>(a);
+  else rec_hist_kernel<8><<<a.chunks, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-template <int S>
+template <int S, int BITS>
 cudaError_t launch_rec_sort_shape(const uint4* in, uint4* out, const PassCtl& c, const LevelCtx& x,
                                   const uint32_t* seg_hist, int d, cudaStream_t st) {
   constexpr TileShape sh = kRecShape[S];
   const size_t smem = rec_sort_smem(S);
-  cudaError_t e = ensure_smem((const void*)rec_sort_pass<sh.threads, sh.items, sh.blocks>, smem);
+  const void* fn = (const void*)rec_sort_pass<sh.threads, sh.items, sh.blocks, BITS>;
+  cudaError_t e = ensure_smem(fn, smem);
   if (e != cudaSuccess) return e;
   const uint32_t tile = (uint32_t)(sh.threads * sh.items);
   const uint32_t tiles = (c.n + tile - 1) / tile;
-  rec_sort_pass<sh.threads, sh.items, sh.blocks><<<tiles, sh.threads, smem, st>>>(in, out, c, x,
-                                                                                   seg_hist, d);
+  rec_sort_pass<sh.threads, sh.items, sh.blocks, BITS><<<tiles, sh.threads, smem, st>>>(in, out, c, x,
+                                                                                         seg_hist, d);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rec_sort_pass(const uint4* in, uint4* out, const PassCtl& c, const LevelCtx& x,
-                                 const uint32_t* seg_hist, int d, int shape, cudaStream_t st) {
+                                 const uint32_t* seg_hist, int d, int shape, int bits, cudaStream_t st) {
   if (c.n == 0) return cudaSuccess;
-  static_assert(kRecShapes == 2, "one launcher per shape");
-  if (shape == 1) return launch_rec_sort_shape<1>(in, out, c, x, seg_hist, d, st);
-  return launch_rec_sort_shape<0>(in, out, c, x, seg_hist, d, st);
+  static_assert(kRecShapes == 2 && kRecDigitWidths == 2, "one launcher per shape and width");
+  if (bits == 6) {
+    if (shape == 1) return launch_rec_sort_shape<1, 6>(in, out, c, x, seg_hist, d, st);
+    return launch_rec_sort_shape<0, 6>(in, out, c, x, seg_hist, d, st);
+  }
+  if (shape == 1) return launch_rec_sort_shape<1, 8>(in, out, c, x, seg_hist, d, st);
+  return launch_rec_sort_shape<0, 8>(in, out, c, x, seg_hist, d, st);
 }
 
 }  // namespace kdb

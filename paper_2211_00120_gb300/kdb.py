@@ -33,6 +33,7 @@ PLACEMENT_IN_PLACE = 1
 
 TUNE_PARTITION = 0
 TUNE_RADIX = 1
+TUNE_DIGITS = 2
 
 FAULT_NONE = 0
 FAULT_ALLOC = 1
@@ -71,7 +72,8 @@ class ServerStats(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("partition_shape", ctypes.c_int32), ("radix_shape", ctypes.c_int32)]
+    _fields_ = [("partition_shape", ctypes.c_int32), ("radix_shape", ctypes.c_int32),
+                ("digit_bits", ctypes.c_int32)]
 
 
 class KdbError(RuntimeError):
@@ -116,6 +118,8 @@ def load():
                                   ctypes.POINTER(i32)], i32),
             "kdb_get_tuning": ([ctypes.POINTER(Tuning)], i32),
             "kdb_set_tuning": ([ctypes.POINTER(Tuning)], i32),
+            "kdb_lookup_tuning": ([i64, i32, i32, i32, ctypes.POINTER(Tuning), ctypes.POINTER(i32)], i32),
+            "kdb_clear_tuning_table": ([], None),
             "kdb_save_tuning": ([ctypes.c_char_p], i32),
             "kdb_load_tuning": ([ctypes.c_char_p], i32),
             "kdb_autotune": ([vp, i64, i32, i32, i32, i32, ctypes.POINTER(Tuning),
@@ -455,7 +459,8 @@ def kdb_set_placement(placement: int) -> int:
 
 def kdb_tuning_shapes(kernel: int) -> list[tuple[int, int, int]]:
     """(threads, items per thread, blocks per SM) of each compiled shape of
-    ``kernel`` (TUNE_PARTITION or TUNE_RADIX)."""
+    ``kernel`` (TUNE_PARTITION or TUNE_RADIX); for TUNE_DIGITS (bits, passes
+    per key, 1) of each compiled digit width."""
     lib = load()
     count = lib.kdb_tuning_shape_count(kernel)
     if count < 0:
@@ -469,43 +474,71 @@ def kdb_tuning_shapes(kernel: int) -> list[tuple[int, int, int]]:
     return out
 
 
-def kdb_get_tuning() -> tuple[int, int]:
-    """Process-wide (partition shape, radix shape)."""
+def kdb_digit_widths() -> list[int]:
+    """The compiled digit widths of the level-0 sort, in bits."""
+    return [w for w, _, _ in kdb_tuning_shapes(TUNE_DIGITS)]
+
+
+def kdb_get_tuning() -> tuple[int, int, int]:
+    """Process-wide (partition shape, radix shape, digit bits)."""
     t = Tuning()
     _check(load().kdb_get_tuning(ctypes.byref(t)), "kdb_get_tuning")
-    return t.partition_shape, t.radix_shape
+    return t.partition_shape, t.radix_shape, t.digit_bits
 
 
-def kdb_set_tuning(partition_shape: int, radix_shape: int) -> None:
-    t = Tuning(partition_shape, radix_shape)
+def kdb_set_tuning(partition_shape: int, radix_shape: int, digit_bits: int = 8) -> None:
+    t = Tuning(partition_shape, radix_shape, digit_bits)
     _check(load().kdb_set_tuning(ctypes.byref(t)), "kdb_set_tuning")
 
 
+def kdb_lookup_tuning(n: int, k: int, stride_bytes: int, mode: int = ROUND_ROBIN):
+    """The setting a build of this kind takes: ((partition shape, radix
+    shape, digit bits), whether it comes from the tuning table).  ``mode`` is
+    the mode argument as the build passes it (coordinate-type flags
+    included)."""
+    t = Tuning()
+    hit = ctypes.c_int32()
+    _check(load().kdb_lookup_tuning(n, k, stride_bytes, mode, ctypes.byref(t), ctypes.byref(hit)),
+           "kdb_lookup_tuning")
+    return (t.partition_shape, t.radix_shape, t.digit_bits), bool(hit.value)
+
+
+def kdb_clear_tuning_table() -> None:
+    load().kdb_clear_tuning_table()
+
+
 def kdb_save_tuning(path: str) -> None:
-    """Writes the process-wide tile shapes to a JSON file."""
+    """Writes the process-wide setting and the tuning table to a JSON file."""
     _check(load().kdb_save_tuning(os.fsencode(path)), "kdb_save_tuning")
 
 
 def kdb_load_tuning(path: str) -> None:
-    """Sets the process-wide tile shapes from a file written by kdb_save_tuning."""
+    """Replaces the process-wide setting and the tuning table with a file
+    written by kdb_save_tuning."""
     _check(load().kdb_load_tuning(os.fsencode(path)), "kdb_load_tuning")
 
 
 def kdb_autotune(points, k: int, mode: int = ROUND_ROBIN, reps: int = 3, stream=None) -> dict:
-    """Times every pair of tile shapes on a copy of ``points`` and keeps the
-    fastest as the process-wide setting.  Returns {"best": (p, r), "best_ms":
-    median ms, "ms": {(p, r): median ms}} (pairs not timed are left out)."""
+    """Times every (partition shape, radix shape, digit width) on a copy of
+    ``points`` and keeps the fastest as the process-wide setting and as the
+    table entry of this kind of build.  Returns {"best": (p, r, bits),
+    "best_ms": median ms, "ms": {(p, r, bits): median ms}} (choices not timed
+    are left out)."""
     ptr, n, stride = _records(points)
     lib = load()
     npart = lib.kdb_tuning_shape_count(TUNE_PARTITION)
     nrad = lib.kdb_tuning_shape_count(TUNE_RADIX)
+    widths = kdb_digit_widths()
+    nw = len(widths)
     best = Tuning()
     best_ms = ctypes.c_float()
-    ms = (ctypes.c_float * (npart * nrad))()
+    ms = (ctypes.c_float * (npart * nrad * nw))()
     _check(lib.kdb_autotune(ptr, n, k, stride, _mode(points, mode), reps, ctypes.byref(best),
                             ctypes.byref(best_ms), ms, _stream(stream)), "kdb_autotune")
-    table = {(c // nrad, c % nrad): ms[c] for c in range(npart * nrad) if ms[c] >= 0}
-    return {"best": (best.partition_shape, best.radix_shape), "best_ms": best_ms.value, "ms": table}
+    table = {(c // (nrad * nw), (c // nw) % nrad, widths[c % nw]): ms[c]
+             for c in range(npart * nrad * nw) if ms[c] >= 0}
+    return {"best": (best.partition_shape, best.radix_shape, best.digit_bits), "best_ms": best_ms.value,
+            "ms": table}
 
 
 def kdb_debug_inject_fault(fault: int, arg: int = 0) -> int:

@@ -74,11 +74,11 @@ int main(int argc, char** argv) {
   if (kdb_batched_workspace_size(nullptr, 3, 3, 12, KDB_SPLIT_ROUND_ROBIN) != 0)
     return fail("NULL set table sized", 0, 0);
 
-  // tile shapes and the process-wide setting
-  for (int kernel = -1; kernel <= 2; ++kernel) {
+  // tile shapes, digit widths and the process-wide setting
+  for (int kernel = -1; kernel <= 3; ++kernel) {
     const int count = kdb_tuning_shape_count(kernel);
-    if ((kernel == KDB_TUNE_PARTITION || kernel == KDB_TUNE_RADIX) != (count > 0))
-      return fail("shape count", kernel, count);
+    const bool known = kernel == KDB_TUNE_PARTITION || kernel == KDB_TUNE_RADIX || kernel == KDB_TUNE_DIGITS;
+    if (known != (count > 0)) return fail("shape count", kernel, count);
     for (int i = -1; i <= count + 1; ++i) {
       int th = 0, it = 0, bl = 0;
       const kdb_status s = kdb_tuning_shape(kernel, i, &th, &it, &bl);
@@ -87,25 +87,64 @@ int main(int argc, char** argv) {
     }
   }
   for (int p = -1; p <= 4; ++p)
-    for (int r = -1; r <= 3; ++r) {
-      const kdb_tuning t{p, r};
-      const kdb_status s = kdb_set_tuning(&t);
-      kdb_tuning g{};
-      kdb_get_tuning(&g);
-      if (s == KDB_OK && (g.partition_shape != p || g.radix_shape != r)) return fail("set/get", p, r);
-      if (s == KDB_OK) {
-        if (kdb_save_tuning(tmp.c_str()) != KDB_OK) return fail("save", p, r);
-        const kdb_tuning z{0, 0};
-        kdb_set_tuning(&z);
-        if (kdb_load_tuning(tmp.c_str()) != KDB_OK) return fail("load", p, r);
+    for (int r = -1; r <= 3; ++r)
+      for (int bits = 5; bits <= 9; ++bits) {
+        const kdb_tuning t{p, r, bits};
+        const kdb_status s = kdb_set_tuning(&t);
+        kdb_tuning g{};
         kdb_get_tuning(&g);
-        if (g.partition_shape != p || g.radix_shape != r) return fail("round trip", p, r);
+        if (s == KDB_OK && (g.partition_shape != p || g.radix_shape != r || g.digit_bits != bits))
+          return fail("set/get", p, r);
+        if (s == KDB_OK) {
+          if (kdb_save_tuning(tmp.c_str()) != KDB_OK) return fail("save", p, r);
+          const kdb_tuning z{0, 0, 8};
+          kdb_set_tuning(&z);
+          if (kdb_load_tuning(tmp.c_str()) != KDB_OK) return fail("load", p, r);
+          kdb_get_tuning(&g);
+          if (g.partition_shape != p || g.radix_shape != r || g.digit_bits != bits) return fail("round trip", p, r);
+        }
+        ++cases;
       }
-      ++cases;
-    }
+  {
+    const kdb_tuning z{0, 0, 8};
+    kdb_set_tuning(&z);
+  }
+  // the table: lookups by kind, and a file holding it
+  kdb_clear_tuning_table();
+  for (int64_t n : {(int64_t)0, (int64_t)1, (int64_t)1000, (int64_t)1 << 40}) {
+    kdb_tuning g{};
+    int hit = 7;
+    if (kdb_lookup_tuning(n, 3, 12, KDB_SPLIT_ROUND_ROBIN, &g, &hit) != KDB_OK || hit != 0 || g.digit_bits != 8)
+      return fail("lookup of an empty table", (int)n, hit);
+    ++cases;
+  }
+  if (kdb_lookup_tuning(10, 3, 12, KDB_SPLIT_ROUND_ROBIN, nullptr, nullptr) != KDB_ERR_INVALID_ARGUMENT)
+    return fail("lookup into NULL", 0, 0);
+  {
+    FILE* f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return fail("temp file", 0, 0);
+    std::fputs("{\"partition\": [256, 13, 4], \"radix\": [256, 13, 3], \"digit_bits\": 8, \"table\": ["
+               "{\"log2n\": 27, \"k\": 3, \"stride\": 12, \"mode\": 0, \"partition\": [256, 13, 4], "
+               "\"radix\": [256, 13, 3], \"digit_bits\": 6}]}", f);
+    std::fclose(f);
+    if (kdb_load_tuning(tmp.c_str()) != KDB_OK) return fail("table load", 0, 0);
+    kdb_tuning g{};
+    int hit = 0;
+    kdb_lookup_tuning(100000000, 3, 12, KDB_SPLIT_ROUND_ROBIN, &g, &hit);
+    if (!hit || g.digit_bits != 6) return fail("table entry", hit, g.digit_bits);
+    kdb_lookup_tuning(100000000, 3, 16, KDB_SPLIT_ROUND_ROBIN, &g, &hit);
+    if (hit || g.digit_bits != 8) return fail("other stride", hit, g.digit_bits);
+    kdb_clear_tuning_table();
+    kdb_lookup_tuning(100000000, 3, 12, KDB_SPLIT_ROUND_ROBIN, &g, &hit);
+    if (hit) return fail("cleared table", hit, 0);
+    cases += 3;
+  }
 
   // the tuning-file parser on random bytes and on mutated valid files
-  const std::string good = "{\"partition\": [256, 13, 4], \"radix\": [256, 13, 3]}";
+  const std::string good =
+      "{\"partition\": [256, 13, 4], \"radix\": [256, 13, 3], \"digit_bits\": 6, \"table\": [{\"log2n\": 20, "
+      "\"k\": 2, \"stride\": 8, \"mode\": 1, \"partition\": [512, 13, 2], \"radix\": [512, 8, 2], "
+      "\"digit_bits\": 8}]}";
   for (int trial = 0; trial < 3000; ++trial) {
     std::string s;
     if (trial % 3 == 0) {
@@ -132,8 +171,14 @@ int main(int argc, char** argv) {
     kdb_tuning g{};
     kdb_get_tuning(&g);
     if (g.partition_shape < 0 || g.partition_shape >= kdb_tuning_shape_count(KDB_TUNE_PARTITION) ||
-        g.radix_shape < 0 || g.radix_shape >= kdb_tuning_shape_count(KDB_TUNE_RADIX))
+        g.radix_shape < 0 || g.radix_shape >= kdb_tuning_shape_count(KDB_TUNE_RADIX) ||
+        (g.digit_bits != 8 && g.digit_bits != 6))
       return fail("setting out of range", g.partition_shape, g.radix_shape);
+    int hit = 0;
+    if (kdb_lookup_tuning(1 << 19, 2, 8, (kdb_split_mode)1, &g, &hit) != KDB_OK ||
+        (hit && (g.partition_shape < 0 || g.partition_shape >= kdb_tuning_shape_count(KDB_TUNE_PARTITION) ||
+                 g.radix_shape < 0 || g.radix_shape >= kdb_tuning_shape_count(KDB_TUNE_RADIX))))
+      return fail("table entry out of range", trial, hit);
     ++cases;
   }
   std::remove(tmp.c_str());

@@ -92,18 +92,74 @@ def test_tuning_shapes_and_setting_round_trip(lib):
         # level (subtrees there hold at least 2^13 - 1 points)
         assert threads * items < (1 << 13) - 1
     assert part[0] == (256, 13, 4) and rad[0] == (256, 13, 3)  # the defaults
+    # digit widths: (bits, passes per 32-bit key, 1), 8 bits first
+    assert kdb.kdb_tuning_shapes(kdb.TUNE_DIGITS) == [(8, 4, 1), (6, 6, 1)]
+    assert kdb.kdb_digit_widths() == [8, 6]
     assert lib.kdb_tuning_shape_count(9) == -1
     assert lib.kdb_tuning_shape(kdb.TUNE_RADIX, len(rad), None, None, None) == kdb.ERR_INVALID_ARGUMENT
-    assert kdb.kdb_get_tuning() == (0, 0)
+    assert lib.kdb_tuning_shape(kdb.TUNE_DIGITS, 2, None, None, None) == kdb.ERR_INVALID_ARGUMENT
+    assert kdb.kdb_get_tuning() == (0, 0, 8)
     try:
-        kdb.kdb_set_tuning(len(part) - 1, len(rad) - 1)
-        assert kdb.kdb_get_tuning() == (len(part) - 1, len(rad) - 1)
-        with pytest.raises(kdb.KdbError):
-            kdb.kdb_set_tuning(len(part), 0)  # out of range: unchanged
-        with pytest.raises(kdb.KdbError):
-            kdb.kdb_set_tuning(0, -1)
-        assert kdb.kdb_get_tuning() == (len(part) - 1, len(rad) - 1)
+        kdb.kdb_set_tuning(len(part) - 1, len(rad) - 1, 6)
+        assert kdb.kdb_get_tuning() == (len(part) - 1, len(rad) - 1, 6)
+        for bad in [(len(part), 0, 8), (0, -1, 8), (0, 0, 7), (0, 0, 11)]:
+            with pytest.raises(kdb.KdbError):
+                kdb.kdb_set_tuning(*bad)  # out of range or not compiled: unchanged
+        assert kdb.kdb_get_tuning() == (len(part) - 1, len(rad) - 1, 6)
     finally:
+        kdb.kdb_set_tuning(0, 0)
+
+
+def test_tuning_table_lookup_by_kind(lib, tmp_path):
+    """A table entry applies to its kind only: the same bit length of N, k,
+    stride and mode argument; everything else takes the process-wide
+    setting."""
+    part = kdb.kdb_tuning_shapes(kdb.TUNE_PARTITION)
+    rad = kdb.kdb_tuning_shapes(kdb.TUNE_RADIX)
+    f = tmp_path / "table.json"
+    entry = {"log2n": 27, "k": 3, "stride": 12, "mode": 0, "partition": list(part[1]),
+             "radix": list(rad[1]), "digit_bits": 6}
+    try:
+        kdb.kdb_clear_tuning_table()
+        assert kdb.kdb_lookup_tuning(10**8, 3, 12) == ((0, 0, 8), False)
+        f.write_text(json.dumps({"partition": list(part[0]), "radix": list(rad[0]), "table": [entry]}))
+        kdb.kdb_load_tuning(str(f))
+        assert kdb.kdb_lookup_tuning(10**8, 3, 12) == ((1, 1, 6), True)  # 1e8 has 27 bits
+        assert kdb.kdb_lookup_tuning(2**26, 3, 12) == ((1, 1, 6), True)
+        for other in [(2**27, 3, 12, 0), (2**26 - 1, 3, 12, 0), (10**8, 2, 12, 0), (10**8, 3, 16, 0),
+                      (10**8, 3, 12, kdb.WIDEST_EXTENT), (10**8, 3, 12, kdb.COORDS_INT32)]:
+            assert kdb.kdb_lookup_tuning(*other) == ((0, 0, 8), False), other
+        kdb.kdb_set_tuning(2, 1, 6)  # the process-wide setting moves the rest only
+        assert kdb.kdb_lookup_tuning(10**8, 3, 16) == ((2, 1, 6), False)
+        assert kdb.kdb_lookup_tuning(10**8, 3, 12) == ((1, 1, 6), True)
+        # saved with the setting, replaced whole on load
+        kdb.kdb_save_tuning(str(f))
+        j = json.loads(f.read_text())
+        assert j["digit_bits"] == 6 and j["table"] == [entry]
+        kdb.kdb_clear_tuning_table()
+        kdb.kdb_set_tuning(0, 0)
+        kdb.kdb_load_tuning(str(f))
+        assert kdb.kdb_get_tuning() == (2, 1, 6)
+        assert kdb.kdb_lookup_tuning(10**8, 3, 12) == ((1, 1, 6), True)
+        # a repeated kind: the later entry wins
+        later = dict(entry, digit_bits=8)
+        f.write_text(json.dumps({"partition": list(part[0]), "radix": list(rad[0]), "table": [entry, later]}))
+        kdb.kdb_load_tuning(str(f))
+        assert kdb.kdb_lookup_tuning(10**8, 3, 12) == ((1, 1, 8), True)
+        # a bad entry refuses the whole file
+        for bad in [dict(entry, digit_bits=7), dict(entry, k=9), dict(entry, log2n=-1),
+                    dict(entry, radix=[96, 7, 5]), {"k": 3}]:
+            f.write_text(json.dumps({"partition": list(part[0]), "radix": list(rad[0]), "table": [bad]}))
+            with pytest.raises(kdb.KdbError):
+                kdb.kdb_load_tuning(str(f))
+        f.write_text(json.dumps({"partition": list(part[0]), "radix": list(rad[0]), "table": [entry] * 257}))
+        with pytest.raises(kdb.KdbError):
+            kdb.kdb_load_tuning(str(f))
+        assert kdb.kdb_lookup_tuning(10**8, 3, 12) == ((1, 1, 8), True)
+        with pytest.raises(kdb.KdbError):
+            kdb.kdb_lookup_tuning(-1, 3, 12)
+    finally:
+        kdb.kdb_clear_tuning_table()
         kdb.kdb_set_tuning(0, 0)
 
 
@@ -112,32 +168,37 @@ def test_tuning_file_round_trip_and_refusals(lib, tmp_path):
     rad = kdb.kdb_tuning_shapes(kdb.TUNE_RADIX)
     f = tmp_path / "tuning.json"
     try:
+        kdb.kdb_clear_tuning_table()
         kdb.kdb_set_tuning(2, 1)
         kdb.kdb_save_tuning(str(f))
         j = json.loads(f.read_text())
-        assert j == {"partition": list(part[2]), "radix": list(rad[1])}
-        kdb.kdb_set_tuning(0, 0)
+        assert j == {"partition": list(part[2]), "radix": list(rad[1]), "digit_bits": 8, "table": []}
+        kdb.kdb_set_tuning(0, 0, 6)
         kdb.kdb_load_tuning(str(f))
-        assert kdb.kdb_get_tuning() == (2, 1)
+        assert kdb.kdb_get_tuning() == (2, 1, 8)
         # shapes are matched by value: a shape this library does not carry,
         # a malformed file or a missing one is refused and changes nothing
         bad = [{"partition": [96, 7, 5], "radix": list(rad[0])},
                {"partition": list(part[0])},
-               {"partition": list(part[0]), "radix": [256, 13]}]
+               {"partition": list(part[0]), "radix": [256, 13]},
+               {"partition": list(part[0]), "radix": list(rad[0]), "digit_bits": 11},
+               {"partition": list(part[0]), "radix": list(rad[0]), "table": {}}]
         for b in bad:
             f.write_text(json.dumps(b))
             with pytest.raises(kdb.KdbError):
                 kdb.kdb_load_tuning(str(f))
-        f.write_text("not json")
-        with pytest.raises(kdb.KdbError):
-            kdb.kdb_load_tuning(str(f))
+        for text in ["not json", json.dumps({"partition": list(part[0]), "radix": list(rad[0])}) + " x"]:
+            f.write_text(text)
+            with pytest.raises(kdb.KdbError):
+                kdb.kdb_load_tuning(str(f))
         with pytest.raises(kdb.KdbError):
             kdb.kdb_load_tuning(str(tmp_path / "missing.json"))
-        assert kdb.kdb_get_tuning() == (2, 1)
-        # whitespace and key order are free
+        assert kdb.kdb_get_tuning() == (2, 1, 8)
+        # whitespace and key order are free; the width defaults to 8 bits
         f.write_text('{ "radix" : [ %d , %d , %d ] ,\n "partition":[%d,%d,%d] }' % (rad[0] + part[1]))
+        kdb.kdb_set_tuning(0, 0, 6)
         kdb.kdb_load_tuning(str(f))
-        assert kdb.kdb_get_tuning() == (1, 0)
+        assert kdb.kdb_get_tuning() == (1, 0, 8)
     finally:
         kdb.kdb_set_tuning(0, 0)
 
@@ -172,7 +233,9 @@ def test_tuning_file_parser_survives_mutated_input(lib, tmp_path):
     rng = random.Random(7)
     part = kdb.kdb_tuning_shapes(kdb.TUNE_PARTITION)
     rad = kdb.kdb_tuning_shapes(kdb.TUNE_RADIX)
-    good = json.dumps({"partition": list(part[1]), "radix": list(rad[1])}).encode()
+    good = json.dumps({"partition": list(part[1]), "radix": list(rad[1]), "digit_bits": 6,
+                       "table": [{"log2n": 20, "k": 3, "stride": 12, "mode": 0, "partition": list(part[0]),
+                                  "radix": list(rad[1]), "digit_bits": 8}]}).encode()
     f = tmp_path / "t.json"
     try:
         for i in range(400):
@@ -193,9 +256,12 @@ def test_tuning_file_parser_survives_mutated_input(lib, tmp_path):
             f.write_bytes(bytes(b))
             rc = lib.kdb_load_tuning(str(f).encode())
             assert rc in (kdb.OK, kdb.ERR_INVALID_ARGUMENT)
-            p_idx, r_idx = kdb.kdb_get_tuning()
-            assert 0 <= p_idx < len(part) and 0 <= r_idx < len(rad)
+            p_idx, r_idx, bits = kdb.kdb_get_tuning()
+            assert 0 <= p_idx < len(part) and 0 <= r_idx < len(rad) and bits in (6, 8)
+            (p_idx, r_idx, bits), _ = kdb.kdb_lookup_tuning(2**19, 3, 12)
+            assert 0 <= p_idx < len(part) and 0 <= r_idx < len(rad) and bits in (6, 8)
     finally:
+        kdb.kdb_clear_tuning_table()
         kdb.kdb_set_tuning(0, 0)
 
 
