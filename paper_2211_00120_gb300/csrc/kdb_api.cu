@@ -650,6 +650,14 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   pa.bbox = bydim ? bbox : nullptr;  // the root's domain and its tight box alike
   pa.err = err;
   pa.ctype = P.ctype;
+  // one set on the list path: the vectorised prepass also counts the level-0
+  // sort's digit histograms, so that the entries are not read again for them
+  const bool hist_in_prepass = P.use_lists && !multi && !P.act.empty() && !P.act[0].empty() &&
+                               prepass_fuses_rec_hist(pa);
+  if (hist_in_prepass) {
+    pa.rec_hist = hist + P.rec_hist_off;
+    pa.rec_bits = rec_bits;
+  }
   {
     Prof pf(K_PREPASS, P.use_lists ? (double)T * (4.0 * k + 16.0) : (double)T * k * (4.0 + (multi ? 8 : 4)),
             feed ? feed->chunks : 1, st);
@@ -879,7 +887,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       rh.nseg = x0.nact;
       rh.k = k;
       rh.bits = rec_bits;
-      {
+      if (!hist_in_prepass) {
         Prof pf(K_LISTS, (double)n0 * 16, 1, st);
         KDB_CK(launch_rec_hist(rh, st));
       }

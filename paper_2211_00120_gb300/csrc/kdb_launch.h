@@ -275,8 +275,15 @@ struct PrepassArgs {
   uint32_t* err;
   int ctype;            // coordinate type (kCoordF32 / I32 / U32)
   uint32_t beg, end;    // records [beg, end) of this launch (end = 0: all of them)
+  // one set of entries (prepass_fuses_rec_hist): the digit histograms of the
+  // level-0 list sort ([k * passes][256], added to), or nullptr
+  uint32_t* rec_hist;
+  int rec_bits;         // their digit width
 };
 cudaError_t launch_prepass(const PrepassArgs& a, int num_sms, cudaStream_t st);
+// Whether launch_prepass takes the vectorised kernel for these arguments,
+// which also counts the level-0 digit histograms when rec_hist is given.
+bool prepass_fuses_rec_hist(const PrepassArgs& a);
 
 struct LevelKeyArgs {
   LevelCtx x;

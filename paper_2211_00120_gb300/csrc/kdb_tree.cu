@@ -164,9 +164,11 @@ __global__ void __launch_bounds__(kThreads) prepass_kernel(PrepassArgs a) {
 // records, read as SW 16-byte words (SW = stride / 4, the group starts on a
 // 16-byte boundary), two groups in flight, and writes their four entries.
 // Records outside whole groups (the range's ragged ends) are done one by one.
-template <int SW>
+// BITS > 0: also counts every digit of BITS bits of every key into s_hist
+// ([dimension * passes + pass][2^BITS]).
+template <int SW, int BITS>
 __device__ inline void prepass_record(const PrepassArgs& a, uint32_t i, const uint32_t* w, uint32_t* lo,
-                                      uint32_t* hi, bool* nan) {
+                                      uint32_t* hi, bool* nan, uint32_t* s_hist) {
   uint32_t ek[3] = {0u, 0u, 0u};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -177,12 +179,24 @@ __device__ inline void prepass_record(const PrepassArgs& a, uint32_t i, const ui
     ek[d] = key;
     lo[d] = min(lo[d], key);
     hi[d] = max(hi[d], key);
+    if constexpr (BITS > 0) {
+      constexpr int P = rec_passes(BITS);
+      constexpr uint32_t R = 1u << BITS;
+#pragma unroll
+      for (int p = 0; p < P; ++p) atomicAdd(&s_hist[(d * P + p) * R + ((key >> (BITS * p)) & (R - 1u))], 1u);
+    }
   }
   a.ents[i] = make_uint4(ek[0], ek[1], ek[2], i);
 }
 
-template <int SW>
+template <int SW, int BITS>
 __global__ void __launch_bounds__(kThreads) prepass_vec_kernel(PrepassArgs a) {
+  constexpr int HP = BITS > 0 ? 3 * rec_passes(BITS) << BITS : 1;
+  __shared__ uint32_t s_hist[HP];
+  if constexpr (BITS > 0) {
+    for (int i = threadIdx.x; i < HP; i += blockDim.x) s_hist[i] = 0;
+    __syncthreads();
+  }
   const uint32_t r0 = a.end ? a.beg : 0u, r1 = a.end ? a.end : a.total;
   const uint32_t g0 = (r0 + 3u) / 4u, g1 = r1 / 4u;  // whole groups inside [r0, r1)
   uint32_t lo[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, hi[3] = {0u, 0u, 0u};
@@ -200,11 +214,11 @@ __global__ void __launch_bounds__(kThreads) prepass_vec_kernel(PrepassArgs a) {
     }
     const uint32_t* wa = reinterpret_cast<const uint32_t*>(va);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) prepass_record<SW>(a, 4u * g + j, wa + j * SW, lo, hi, &nan);
+    for (int j = 0; j < 4; ++j) prepass_record<SW, BITS>(a, 4u * g + j, wa + j * SW, lo, hi, &nan, s_hist);
     if (g2 < g1) {
       const uint32_t* wb = reinterpret_cast<const uint32_t*>(vb);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) prepass_record<SW>(a, 4u * g2 + j, wb + j * SW, lo, hi, &nan);
+      for (int j = 0; j < 4; ++j) prepass_record<SW, BITS>(a, 4u * g2 + j, wb + j * SW, lo, hi, &nan, s_hist);
     }
   }
   // the ragged ends, by the first block
@@ -213,12 +227,12 @@ __global__ void __launch_bounds__(kThreads) prepass_vec_kernel(PrepassArgs a) {
     for (uint32_t i = r0 + threadIdx.x; i < h1; i += blockDim.x) {
       uint32_t w[4];
       for (int d = 0; d < a.k; ++d) w[d] = reinterpret_cast<const uint32_t*>(a.pts)[(uint64_t)i * SW + d];
-      prepass_record<SW>(a, i, w, lo, hi, &nan);
+      prepass_record<SW, BITS>(a, i, w, lo, hi, &nan, s_hist);
     }
     for (uint32_t i = t0 + threadIdx.x; i < r1; i += blockDim.x) {
       uint32_t w[4];
       for (int d = 0; d < a.k; ++d) w[d] = reinterpret_cast<const uint32_t*>(a.pts)[(uint64_t)i * SW + d];
-      prepass_record<SW>(a, i, w, lo, hi, &nan);
+      prepass_record<SW, BITS>(a, i, w, lo, hi, &nan, s_hist);
     }
   }
   if (a.bbox) {
@@ -233,6 +247,15 @@ __global__ void __launch_bounds__(kThreads) prepass_vec_kernel(PrepassArgs a) {
     }
   }
   if (nan) atomicOr(a.err, ERR_NAN);
+  if constexpr (BITS > 0) {
+    __syncthreads();
+    constexpr uint32_t R = 1u << BITS;
+    const int H = a.k * rec_passes(BITS) * (int)R;
+    for (int i = threadIdx.x; i < H; i += blockDim.x) {
+      const uint32_t v = s_hist[i];
+      if (v) atomicAdd(a.rec_hist + (uint32_t)i / R * kRadixBins + (uint32_t)i % R, v);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -667,22 +690,34 @@ __global__ void validate_kernel(const unsigned char* pts, uint32_t n, int k, int
 }  // namespace
 
 // ------------------------------------------------------------- launchers --
+// one set, entries only, records of 4k <= 16 bytes on a 16-byte boundary:
+// the vectorised prepass
+bool prepass_fuses_rec_hist(const PrepassArgs& a) {
+  return a.ents && !a.hist && !a.keys32 && !a.keys64 && a.nsets == 1 && a.k <= 3 && a.stride <= 16 &&
+         a.stride % 4 == 0 && 4 * a.k <= a.stride && (reinterpret_cast<uintptr_t>(a.pts) & 15u) == 0;
+}
+
+template <int BITS>
+void launch_prepass_vec(const PrepassArgs& a, uint32_t grid, cudaStream_t st) {
+  switch (a.stride / 4) {
+    case 1: prepass_vec_kernel<1, BITS><<<grid, kThreads, 0, st>>>(a); break;
+    case 2: prepass_vec_kernel<2, BITS><<<grid, kThreads, 0, st>>>(a); break;
+    case 3: prepass_vec_kernel<3, BITS><<<grid, kThreads, 0, st>>>(a); break;
+    default: prepass_vec_kernel<4, BITS><<<grid, kThreads, 0, st>>>(a); break;
+  }
+}
+
 cudaError_t launch_prepass(const PrepassArgs& a, int num_sms, cudaStream_t st) {
   const uint32_t count = a.end ? a.end - a.beg : a.total;
   if (count == 0) return cudaSuccess;
-  // one set, entries only, records of 4k <= 16 bytes on a 16-byte boundary:
-  // the vectorised prepass
-  if (a.ents && !a.hist && !a.keys32 && !a.keys64 && a.nsets == 1 && a.k <= 3 && a.stride <= 16 &&
-      a.stride % 4 == 0 && 4 * a.k <= a.stride && (reinterpret_cast<uintptr_t>(a.pts) & 15u) == 0) {
+  if (prepass_fuses_rec_hist(a)) {
     uint32_t grid = (uint32_t)num_sms * 8;
     const uint32_t need = (count / 4 + 2 * kThreads - 1) / (2 * kThreads);
     if (grid > need) grid = need > 0 ? need : 1;
-    switch (a.stride / 4) {
-      case 1: prepass_vec_kernel<1><<<grid, kThreads, 0, st>>>(a); break;
-      case 2: prepass_vec_kernel<2><<<grid, kThreads, 0, st>>>(a); break;
-      case 3: prepass_vec_kernel<3><<<grid, kThreads, 0, st>>>(a); break;
-      default: prepass_vec_kernel<4><<<grid, kThreads, 0, st>>>(a); break;
-    }
+    static_assert(kRecDigitWidths == 2, "one launcher per width");
+    if (!a.rec_hist) launch_prepass_vec<0>(a, grid, st);
+    else if (a.rec_bits == 6) launch_prepass_vec<6>(a, grid, st);
+    else launch_prepass_vec<8>(a, grid, st);
     return cudaGetLastError();
   }
   const size_t smem = a.hist ? (size_t)a.k * a.passes * kRadixBins * sizeof(uint32_t) : 0;
