@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(RT, RB)
   if (tid < RADIX) {
     uint32_t prefA = 0;
     if (a_cont && s_abort == 0) {
-      if (!look_back<16>(c, tile, tid, &prefA)) {
+      if (!look_back<8>(c, tile, tid, &prefA)) {
         atomicOr(c.err, ERR_TIMEOUT);
         s_abort = 1;
       }

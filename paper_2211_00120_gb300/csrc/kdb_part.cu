@@ -178,10 +178,12 @@ __device__ inline void lift_seg_info(const PartArgs& a, uint32_t ai, uint32_t sr
   }
 }
 
-// Warp-parallel decoupled look-back over nb bins: lane group g (32 / nb
-// lanes) reads bin g of the words of as many preceding tiles at a time and
-// adds published values up to the nearest inclusive prefix.  Writes the
-// exclusive prefix of every bin to s_pref; false if a wait ran past wait_ns.
+// Warp-parallel decoupled look-back over nbin bins: lane group g (32 / nbin
+// lanes) takes bin g, each lane reading R consecutive predecessor words, so
+// a group covers R * 32 / nbin predecessors per round trip; it adds published
+// values up to the nearest inclusive prefix.  Writes the exclusive prefix of
+// every bin to s_pref; false if a wait ran past wait_ns.
+template <int R>
 __device__ inline bool warp_look_back_bins(const PartArgs& a, uint32_t tile, int nbin,
                                            uint32_t* s_pref) {
   const int lane = threadIdx.x & 31;
@@ -193,29 +195,52 @@ __device__ inline bool warp_look_back_bins(const PartArgs& a, uint32_t tile, int
   bool done = false, ok = true, waiting = false;
   uint64_t t0 = 0;
   for (;;) {
-    const int64_t mine = t - j;
-    uint64_t w = lb_pack(kFlagPre, a.wait_epoch, 0);
-    if (!done && mine >= 0) w = ld_relaxed_u64(a.status + (uint64_t)mine * kLiftBins + g);
-    const uint32_t ep = (uint32_t)(w >> 32) & 0x3FFFFFFFu;
-    const bool ready = done || (ep == a.wait_epoch && (w >> 62) != 0);
-    const bool pre = !done && ready && (w >> 62) == 2;
-    const uint32_t nr = __ballot_sync(0xffffffffu, !ready) & gmask;
-    const uint32_t pr = __ballot_sync(0xffffffffu, pre) & gmask;
-    const int fnr = nr ? __ffs(nr) - 1 - g * lpb : lpb;
-    const int fpr = pr ? __ffs(pr) - 1 - g * lpb : lpb;
-    const uint32_t v = done ? 0u : (uint32_t)w;
-    uint32_t s1 = j <= fpr ? v : 0u, s2 = j < fnr ? v : 0u;
+    // this lane's words: positions j * R + r back from t
+    uint64_t w[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t mine = t - (int64_t)(j * R + r);
+      w[r] = lb_pack(kFlagPre, a.wait_epoch, 0);
+      if (!done && mine >= 0) w[r] = ld_relaxed_u64(a.status + (uint64_t)mine * kLiftBins + g);
+    }
+    int fnr = R, fpr = R;  // the lane's first word not ready, first inclusive prefix
+    uint32_t v[R];
+#pragma unroll
+    for (int r = R - 1; r >= 0; --r) {
+      const uint32_t ep = (uint32_t)(w[r] >> 32) & 0x3FFFFFFFu;
+      const bool ready = done || (ep == a.wait_epoch && (w[r] >> 62) != 0);
+      const bool pre = !done && ready && (w[r] >> 62) == 2;
+      v[r] = done ? 0u : (uint32_t)w[r];
+      if (!ready) fnr = r;
+      if (pre) fpr = r;
+    }
+    const uint32_t nr = __ballot_sync(0xffffffffu, fnr < R) & gmask;
+    const uint32_t pr = __ballot_sync(0xffffffffu, fpr < R) & gmask;
+    const int jn = nr ? __ffs(nr) - 1 - g * lpb : lpb;
+    const int jp = pr ? __ffs(pr) - 1 - g * lpb : lpb;
+    int FNR = jn * R, FPR = jp * R;  // the group's first word not ready, first prefix
+    if (R > 1) {
+      FNR += __shfl_sync(0xffffffffu, fnr, g * lpb + (jn < lpb ? jn : 0)) % R;
+      FPR += __shfl_sync(0xffffffffu, fpr, g * lpb + (jp < lpb ? jp : 0)) % R;
+    }
+    uint32_t s1 = 0, s2 = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int pos = j * R + r;
+      if (pos <= FPR) s1 += v[r];
+      if (pos < FNR) s2 += v[r];
+    }
     for (int o = 1; o < lpb; o <<= 1) {
       s1 += __shfl_xor_sync(0xffffffffu, s1, o);
       s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     }
     if (!done) {
-      if (fpr < fnr) {  // everything up to the prefix is published
+      if (FPR < FNR) {  // everything up to the prefix is published
         acc += s1;
         done = true;
-      } else if (fnr > 0) {  // consume the published aggregates and move on
+      } else if (FNR > 0) {  // consume the published aggregates and move on
         acc += s2;
-        t -= fnr;
+        t -= FNR;
         waiting = false;
       } else {
         const uint64_t now = global_timer_ns();
@@ -397,7 +422,10 @@ __global__ void __launch_bounds__(PT, PB) partition_kernel(PartArgs a) {
   }
   if (warp == 0) {
     bool ok = true;
-    if (a_cont) ok = warp_look_back_bins(a, tile, nbin, s_prefA);
+    // three-level lifts (four lanes per child): two words a lane, eight
+    // predecessors a round trip; otherwise one word a lane
+    if (a_cont) ok = nbin == kLiftBins ? warp_look_back_bins<2>(a, tile, nbin, s_prefA)
+                                       : warp_look_back_bins<1>(a, tile, nbin, s_prefA);
     else if (lane < kLiftBins) s_prefA[lane] = 0;
     __syncwarp();
     if (lane < nbin) {
