@@ -348,6 +348,44 @@ def workload_leg(kdb, name: str, steps: int, warmup: int, peak: float, peak_src:
     return out
 
 
+def lean_leg(kdb, name: str, steps: int, warmup: int) -> dict:
+    """The memory-lean build (kdb_set_memory_mode(MEMORY_LEAN)) of a workload,
+    timed like the headline, with its device memory per point beside the
+    default build's, and whether its tree equals the default build's."""
+    import torch
+
+    desc, n, k, sf, mode, gen = WORKLOADS[name]
+    src = torch.from_numpy(gen(n)).cuda()
+    work = torch.empty_like(src)
+    stream = torch.cuda.current_stream()
+    work.copy_(src)
+    kdb.kdb_build(work, k, mode)
+    want = work.clone()
+    prev = kdb.kdb_set_memory_mode(kdb.MEMORY_LEAN)
+    try:
+        for _ in range(warmup):
+            work.copy_(src)
+            kdb.kdb_build(work, k, mode)
+        torch.cuda.synchronize()
+        equal = bool(torch.equal(work.view(torch.int32), want.view(torch.int32)))
+        times, prof, launches = timed_builds(kdb, work, src, k, mode, steps, stream)
+    finally:
+        kdb.kdb_set_memory_mode(prev)
+    del src, work, want
+    torch.cuda.empty_cache()
+    ms = sum(times) / len(times)
+    stride = 4 * sf
+    return {"workload": desc, "memory_mode": "lean", "steps": steps, "warmup": warmup,
+            "ms_per_step": ms, "ms_per_step_median": sorted(times)[len(times) // 2],
+            "value": n / (ms / 1000.0) / 1e6, "unit": "Mpts/s", "gpu_launches": launches,
+            "workspace_bytes_per_point": kdb.kdb_lean_workspace_size(n, k, stride, mode) / n,
+            "default_workspace_bytes_per_point": kdb.load().kdb_workspace_size(n, k, stride, mode) / n,
+            "equal_to_default_build": equal,
+            "kernel_ms_per_step": {p["name"]: round(p["ms"] / steps, 3) for p in prof},
+            "timing": "CUDA events around each synchronous kdb_build call (host decisions between "
+                      "the top levels' passes included)"}
+
+
 def host_info() -> dict:
     """CPU model and core counts of the host the CPU baselines run on."""
     model = None
@@ -859,6 +897,7 @@ def main():
         for name in ("mixed_1e7_f3_rr", "aniso_1e8_f4_widest"):
             if name != args.workload:
                 legs[name] = workload_leg(kdb, name, min(args.steps, 20), args.warmup, peak, peak_src)
+        legs["lean_" + args.workload] = lean_leg(kdb, args.workload, min(args.steps, 5), args.warmup)
 
     batched = None
     if not args.no_batched:

@@ -433,6 +433,37 @@ typedef enum { KDB_PLACEMENT_AUTO = 0, KDB_PLACEMENT_IN_PLACE = 1 } kdb_placemen
 KDB_API kdb_placement kdb_set_placement(kdb_placement placement);
 
 /*
+ * kdb_set_memory_mode -- how kdb_build and kdb_build_ex (without caller
+ * workspace and without the original-index or split-dimension outputs) size
+ * their device memory.  The paper builds with one int per point beside the
+ * records (abstract, Sec. 1, Sec. 7.1); the default pipeline trades that for
+ * bandwidth (per-dimension lists, kdb_workspace_size).
+ *   KDB_MEMORY_AUTO  the default pipeline, unless its workspace does not fit
+ *                    the device memory free at the call (plus what the
+ *                    library's memory pool holds unused, less 256 MiB): then
+ *                    the lean build.
+ *   KDB_MEMORY_FAST  always the default pipeline.
+ *   KDB_MEMORY_LEAN  always the lean build (N >= 4; smaller N build as usual).
+ * The lean build follows the steps of the sharded build with every shard on
+ * this GPU: the top 4 levels by a radix select of every node's pivot
+ * (Observation 1) over the whole array, one stable move of every point to
+ * its level-4 subtree's slice, then each of the 16 subtrees built alone by
+ * the default pipeline in a workspace sized for one subtree.  Its device
+ * memory (kdb_lean_workspace_size) is one tag and one index per point, a
+ * copy of the records, and one subtree's workspace: about 29 B per point for
+ * float3 records without payload, against about 146 B for the default.  The
+ * output is the same tree.  The records are only read until every subtree is
+ * built, so a device error leaves them untouched, as for the default.
+ * Synchronous, like kdb_build.  Process-wide; returns the previous setting;
+ * any other value leaves it unchanged.
+ * kdb_lean_workspace_size -- device bytes the lean build allocates for these
+ *   arguments, 0 for invalid arguments or N < 4.
+ */
+typedef enum { KDB_MEMORY_AUTO = 0, KDB_MEMORY_FAST = 1, KDB_MEMORY_LEAN = 2 } kdb_memory_mode;
+KDB_API kdb_memory_mode kdb_set_memory_mode(kdb_memory_mode mode);
+KDB_API size_t kdb_lean_workspace_size(int64_t n, int k, int stride_bytes, kdb_split_mode mode);
+
+/*
  * Tuning of the per-dimension-list path (k <= 3).  Three choices, none of
  * which changes the output (every choice gives bit-identical trees):
  *   KDB_TUNE_PARTITION  tile shape of the per-level stable split (the sorts

@@ -58,12 +58,14 @@ enum Kind {
   K_PARTITION,
   K_PIVOT,
   K_LISTS,
+  K_LEAN,
   K_COUNT
 };
 const char* const kKindName[K_COUNT] = {"prepass",      "radix_pass",  "radix_pass_rank",
                                         "radix_pass_update", "level_keys", "widest_dims",
                                         "placement",    "validate",   "local_finish",
-                                        "partition_pass", "pivots",     "build_lists"};
+                                        "partition_pass", "pivots",     "build_lists",
+                                        "lean_top_levels"};
 struct ProfRec {
   int kind;
   double bytes;
@@ -1210,6 +1212,403 @@ cudaError_t ensure_smem(const void* func, size_t bytes) {
 }
 }  // namespace kdb
 
+// ------------------------------------------------------ memory-lean build --
+// A single build in a small workspace, on one GPU, by the steps of the
+// sharded build with every shard on this GPU: the top g levels are chosen
+// over the whole array (per node the point of rank ss(lChild) in the node's
+// order, Observation 1, by a radix select over (coordinate key << 32 |
+// index)), every point is moved once to its level-g subtree's slice (a
+// stable partition), and each of the 2^g subtrees is then built alone with
+// the ordinary pipeline in a workspace sized for one subtree.  The caller's
+// records are only read until every subtree is built; the tree is written
+// into them at the end.
+namespace kdb {
+namespace {
+std::atomic<int> g_memory_mode{KDB_MEMORY_AUTO};
+constexpr int kLeanLevels = 4;  // 16 subtrees: each build's workspace is about 1/16 of one over all points
+
+// Widest side of a box of coordinate keys, as the device's widest_of_keys:
+// float32 hi - lo (exact key differences for integer coordinates), strict
+// '>' from d = 0, so the lowest dimension wins ties.
+int host_widest(const uint32_t* lo, const uint32_t* hi, int k, int ctype) {
+  int best = 0;
+  if (ctype != kCoordF32) {
+    int64_t be = 0;
+    for (int d = 0; d < k; ++d) {
+      const int64_t e = (int64_t)hi[d] - (int64_t)lo[d];
+      if (d == 0 || e > be) {
+        be = e;
+        best = d;
+      }
+    }
+    return best;
+  }
+  float be = 0.0f;
+  for (int d = 0; d < k; ++d) {
+    const uint32_t hb = key_to_float_bits(hi[d]), lb = key_to_float_bits(lo[d]);
+    float hf, lf;
+    std::memcpy(&hf, &hb, 4);
+    std::memcpy(&lf, &lb, 4);
+    const float e = hf - lf;
+    if (d == 0 || e > be) {
+      be = e;
+      best = d;
+    }
+  }
+  return best;
+}
+
+struct LeanPlan {
+  int g = 0;                 // levels chosen over the whole array
+  uint32_t G = 0;            // subtrees
+  std::vector<uint32_t> m;   // points of each subtree
+  size_t sub_bytes = 0;      // workspace of the largest subtree build
+  uint32_t blocks = 0;       // partition blocks
+  size_t o_tags, o_out, o_idx, o_hist, o_box, o_dims, o_pre, o_pin, o_top, o_cnt, o_err, o_ws, bytes;
+};
+
+// Layout of the lean build's device memory; g = 0 if n is too small for it.
+LeanPlan lean_plan(int64_t n, int k, int stride, int mode_arg, int sms) {
+  LeanPlan L;
+  const uint32_t N = (uint32_t)n;
+  L.g = std::min(kLeanLevels, num_levels(N) - 2);  // levels 0..g full
+  if (L.g < 1) {
+    L.g = 0;
+    return L;
+  }
+  L.G = 1u << L.g;
+  const Tree t = make_tree(N);
+  for (uint32_t r = 0; r < L.G; ++r) {
+    L.m.push_back(subtree_size(t, full_nodes(L.g) + r));
+    Plan P;
+    P.sets.push_back(SetInfo{0u, L.m.back()});
+    P.total = L.m.back();
+    P.k = k;
+    P.stride = stride;
+    P.mode = mode_arg & 0xFF;
+    P.ctype = ctype_of(mode_arg);
+    P.mode_arg = mode_arg;
+    make_plan(P);
+    L.sub_bytes = std::max(L.sub_bytes, P.bytes);
+  }
+  L.blocks = dist_blocks(N, sms);
+  const uint32_t top_nodes = 1u << (L.g - 1);  // most nodes of a chosen level
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  L.o_tags = take((size_t)N * 4);
+  L.o_out = take((size_t)N * stride);
+  L.o_idx = take((size_t)N * 4);
+  L.o_hist = take((size_t)top_nodes * 256 * 4);
+  L.o_box = take((size_t)top_nodes * 2 * k * 4);
+  L.o_dims = take(top_nodes);
+  L.o_pre = take((size_t)top_nodes * 8);
+  L.o_pin = take((size_t)top_nodes * 8);
+  L.o_top = take((size_t)full_nodes(L.g) * stride);
+  L.o_cnt = take((size_t)L.blocks * L.G * 8);
+  L.o_err = take(4);
+  L.o_ws = take(L.sub_bytes);
+  L.bytes = off;
+  return L;
+}
+
+kdb_status lean_build(unsigned char* pts, int64_t n, int k, int stride, int mode_arg, cudaStream_t st) {
+  int dev, sms;
+  cudaMemPool_t pool;
+  kdb_status s = device_setup(&dev, &pool, &sms);
+  if (s != KDB_OK) return s;
+  const LeanPlan L = lean_plan(n, k, stride, mode_arg, sms);
+  if (L.g == 0) return KDB_ERR_INVALID_ARGUMENT;
+  const uint32_t N = (uint32_t)n;
+  const int split = mode_arg & 0xFF, ctype = ctype_of(mode_arg);
+  const Tree tree = make_tree(N);
+  void* ws = nullptr;
+  s = pool_alloc(&ws, L.bytes, pool, st);
+  if (s != KDB_OK) return s;
+  unsigned char* base = static_cast<unsigned char*>(ws);
+  int32_t* tags = reinterpret_cast<int32_t*>(base + L.o_tags);
+  unsigned char* out = base + L.o_out;
+  uint32_t* idx = reinterpret_cast<uint32_t*>(base + L.o_idx);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(base + L.o_hist);
+  uint32_t* box = reinterpret_cast<uint32_t*>(base + L.o_box);
+  uint8_t* d_dims = base + L.o_dims;
+  uint64_t* d_pre = reinterpret_cast<uint64_t*>(base + L.o_pre);
+  int64_t* d_pin = reinterpret_cast<int64_t*>(base + L.o_pin);
+  unsigned char* top = base + L.o_top;
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(base + L.o_cnt);
+  uint32_t* err = reinterpret_cast<uint32_t*>(base + L.o_err);
+  void* sub_ws = base + L.o_ws;
+  kdb_status result = KDB_OK;
+  // a device error word read back after each host decision
+  auto sync_err = [&](uint32_t* h) -> kdb_status {
+    uint32_t e = 0;
+    if (cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return KDB_ERR_CUDA;
+    if (h) *h = e;
+    if (e & ERR_NAN) return KDB_ERR_NAN_INPUT;
+    if (e & ERR_TIMEOUT) return KDB_ERR_TIMEOUT;
+    if (e & ERR_INTERNAL) return KDB_ERR_INTERNAL;
+    return KDB_OK;
+  };
+  DistArgs a{};
+  a.pts = pts;
+  a.n = N;
+  a.k = k;
+  a.stride = stride;
+  a.ctype = ctype;
+  a.tags = tags;
+  a.err = err;
+  do {
+    if (cudaMemsetAsync(err, 0, 4, st) != cudaSuccess || cudaMemsetAsync(tags, 0, (size_t)N * 4, st) != cudaSuccess) {
+      result = KDB_ERR_CUDA;
+      break;
+    }
+    if (ctype == kCoordF32) {  // NaN coordinates: refused before anything is built
+      Prof pf(K_LEAN, (double)N * 4 * k, 1, st);
+      if (launch_nan_check(pts, N, k, stride, err, sms, st) != cudaSuccess) {
+        result = KDB_ERR_CUDA;
+        break;
+      }
+    }
+    if ((result = sync_err(nullptr)) != KDB_OK) break;
+    // top levels: per level the split dimensions, a radix select of every
+    // node's pivot and the tag update
+    std::vector<uint32_t> dom_lo, dom_hi;  // widest extent: node domains as keys, heap order
+    auto read_boxes = [&](int l, std::vector<uint32_t>* h) -> kdb_status {
+      a.first = full_nodes(l);
+      a.nodes = 1u << l;
+      a.box = box;
+      std::vector<uint32_t> init((size_t)a.nodes * 2 * k);
+      for (size_t i = 0; i < init.size(); ++i) init[i] = (i / k) % 2 == 0 ? 0xFFFFFFFFu : 0u;
+      h->resize(init.size());
+      Prof pf(K_LEAN, (double)N * (4.0 * k + 4.0), 1, st);
+      if (cudaMemcpyAsync(box, init.data(), init.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          launch_dist_box(a, sms, st) != cudaSuccess ||
+          cudaMemcpyAsync(h->data(), box, init.size() * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return KDB_ERR_CUDA;
+      return sync_err(nullptr);
+    };
+    if (split == KDB_SPLIT_WIDEST_EXTENT) {
+      std::vector<uint32_t> b;
+      if ((result = read_boxes(0, &b)) != KDB_OK) break;
+      dom_lo.assign((size_t)full_nodes(L.g + 1) * k, 0);
+      dom_hi.assign((size_t)full_nodes(L.g + 1) * k, 0);
+      for (int d = 0; d < k; ++d) {
+        dom_lo[d] = b[d];
+        dom_hi[d] = b[k + d];
+      }
+    }
+    for (int l = 0; l < L.g && result == KDB_OK; ++l) {
+      const uint32_t nodes = 1u << l, first = full_nodes(l);
+      std::vector<uint8_t> dims(nodes);
+      if (split == KDB_SPLIT_ROUND_ROBIN) {
+        for (uint32_t u = 0; u < nodes; ++u) dims[u] = (uint8_t)(l % k);
+      } else if (split == KDB_SPLIT_WIDEST_EXTENT) {
+        for (uint32_t u = 0; u < nodes; ++u)
+          dims[u] = (uint8_t)host_widest(&dom_lo[(size_t)(first + u) * k], &dom_hi[(size_t)(first + u) * k], k, ctype);
+      } else {
+        std::vector<uint32_t> b;
+        if ((result = read_boxes(l, &b)) != KDB_OK) break;
+        for (uint32_t u = 0; u < nodes; ++u)
+          dims[u] = (uint8_t)host_widest(&b[(size_t)u * 2 * k], &b[(size_t)u * 2 * k + k], k, ctype);
+      }
+      std::vector<uint64_t> remaining(nodes), prefix(nodes, 0);
+      for (uint32_t u = 0; u < nodes; ++u) remaining[u] = subtree_size(tree, 2 * (first + u) + 1);
+      a.first = first;
+      a.nodes = nodes;
+      a.node_dim = d_dims;
+      a.prefix = d_pre;
+      a.hist = hist;
+      if (cudaMemcpyAsync(d_dims, dims.data(), nodes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        result = KDB_ERR_CUDA;
+        break;
+      }
+      std::vector<uint32_t> h((size_t)nodes * 256);
+      for (int rnd = 0; rnd < 8 && result == KDB_OK; ++rnd) {
+        a.prefix_bits = 8 * rnd;
+        Prof pf(K_LEAN, (double)N * 8.0, 1, st);
+        if (cudaMemcpyAsync(d_pre, prefix.data(), (size_t)nodes * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemsetAsync(hist, 0, h.size() * 4, st) != cudaSuccess || launch_dist_hist(a, sms, st) != cudaSuccess ||
+            cudaMemcpyAsync(h.data(), hist, h.size() * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+          result = KDB_ERR_CUDA;
+          break;
+        }
+        if ((result = sync_err(nullptr)) != KDB_OK) break;
+        for (uint32_t u = 0; u < nodes; ++u) {
+          // the digit of the pivot: the bucket holding rank remaining[u]
+          uint64_t cum = 0;
+          int dgt = 0;
+          while (dgt < 256 && cum + h[(size_t)u * 256 + dgt] <= remaining[u]) cum += h[(size_t)u * 256 + dgt++];
+          if (dgt == 256) {
+            result = KDB_ERR_INTERNAL;
+            break;
+          }
+          remaining[u] -= cum;
+          prefix[u] = (prefix[u] << 8) | (uint64_t)dgt;
+        }
+      }
+      if (result != KDB_OK) break;
+      std::vector<int64_t> pinned(nodes, -1);
+      a.pivot = d_pre;
+      a.pinned = d_pin;
+      {
+        Prof pf(K_LEAN, (double)N * 12.0, 1, st);
+        if (cudaMemcpyAsync(d_pre, prefix.data(), (size_t)nodes * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemsetAsync(d_pin, 0xFF, (size_t)nodes * 8, st) != cudaSuccess ||
+            launch_dist_assign(a, sms, st) != cudaSuccess ||
+            cudaMemcpyAsync(pinned.data(), d_pin, (size_t)nodes * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+          result = KDB_ERR_CUDA;
+          break;
+        }
+      }
+      if ((result = sync_err(nullptr)) != KDB_OK) break;
+      for (uint32_t u = 0; u < nodes && result == KDB_OK; ++u) {
+        if (pinned[u] < 0 || pinned[u] >= (int64_t)N || (uint64_t)pinned[u] != (prefix[u] & 0xFFFFFFFFu)) {
+          result = KDB_ERR_INTERNAL;
+          break;
+        }
+        // the pivot's record, kept for its node
+        if (cudaMemcpyAsync(top + (size_t)(first + u) * stride, pts + (size_t)pinned[u] * stride, stride,
+                            cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+          result = KDB_ERR_CUDA;
+        if (split == KDB_SPLIT_WIDEST_EXTENT) {  // the children's domains, clipped at the pivot's plane
+          const uint32_t plane = (uint32_t)(prefix[u] >> 32);
+          const size_t s0 = (size_t)(first + u) * k, lc = (size_t)(2 * (first + u) + 1) * k, rc = lc + k;
+          for (int d = 0; d < k; ++d) {
+            dom_lo[lc + d] = dom_lo[rc + d] = dom_lo[s0 + d];
+            dom_hi[lc + d] = dom_hi[rc + d] = dom_hi[s0 + d];
+          }
+          dom_hi[lc + dims[u]] = plane;
+          dom_lo[rc + dims[u]] = plane;
+        }
+      }
+    }
+    if (result != KDB_OK) break;
+    // every point to its level-g subtree's slice, in original-index order
+    a.first = full_nodes(L.g);
+    a.nodes = L.G;
+    a.out_pts = out;
+    a.out_index = idx;
+    a.block_counts = cnt;
+    const size_t cells = (size_t)L.blocks * L.G;
+    std::vector<uint32_t> bc(cells), off(cells);
+    {
+      Prof pf(K_LEAN, (double)N * 4.0, 1, st);
+      if (launch_dist_count(a, L.blocks, st) != cudaSuccess ||
+          cudaMemcpyAsync(bc.data(), cnt, cells * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) {
+        result = KDB_ERR_CUDA;
+        break;
+      }
+    }
+    std::vector<uint32_t> start(L.G + 1, 0);
+    uint64_t run = 0;
+    for (uint32_t r = 0; r < L.G; ++r) {
+      start[r] = (uint32_t)run;
+      for (uint32_t b = 0; b < L.blocks; ++b) {
+        off[(size_t)b * L.G + r] = (uint32_t)run;
+        run += bc[(size_t)b * L.G + r];
+      }
+      if (run - start[r] != L.m[r]) result = KDB_ERR_INTERNAL;  // the subtree's size is fixed by N
+    }
+    start[L.G] = (uint32_t)run;
+    if (result != KDB_OK) break;
+    a.block_offsets = cnt + cells;
+    {
+      Prof pf(K_LEAN, (double)N * (2.0 * stride + 8.0), 1, st);
+      if (cudaMemcpyAsync(cnt + cells, off.data(), cells * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          launch_dist_scatter(a, L.blocks, st) != cudaSuccess) {
+        result = KDB_ERR_CUDA;
+        break;
+      }
+    }
+    if ((result = sync_err(nullptr)) != KDB_OK) break;
+    // each subtree alone: round robin continued from its level, or its
+    // domain clipped by its ancestors' planes
+    for (uint32_t r = 0; r < L.G && result == KDB_OK; ++r) {
+      Plan P;
+      P.sets.push_back(SetInfo{0u, L.m[r]});
+      P.total = L.m[r];
+      P.k = k;
+      P.stride = stride;
+      P.mode = split;
+      P.ctype = ctype;
+      P.mode_arg = mode_arg;
+      P.dim0 = split == KDB_SPLIT_ROUND_ROBIN ? L.g % k : 0;
+      if (split == KDB_SPLIT_WIDEST_EXTENT) {
+        P.has_domain = true;
+        const size_t s0 = (size_t)(full_nodes(L.g) + r) * k;
+        for (int d = 0; d < k; ++d) {
+          const uint32_t lb = key_to_float_bits(dom_lo[s0 + d]), hb = key_to_float_bits(dom_hi[s0 + d]);
+          std::memcpy(&P.domain[d], &lb, 4);
+          std::memcpy(&P.domain[kMaxK + d], &hb, 4);
+        }
+      }
+      make_plan(P);
+      if (P.too_wide || P.bytes > L.sub_bytes) {
+        result = KDB_ERR_INTERNAL;
+        break;
+      }
+      if (L.m[r] <= 1) continue;
+      result = enqueue_build(P, out + (size_t)start[r] * stride, sub_ws, sms, nullptr, nullptr, st);
+      const kdb_status f = finish(P, sub_ws, st);
+      if (result == KDB_OK) result = f;
+    }
+    if (result != KDB_OK) break;
+    // every subtree and the top nodes into the caller's array
+    for (uint32_t r = 0; r < L.G && result == KDB_OK; ++r) {
+      LeanPlaceArgs pa{};
+      pa.src = out + (size_t)start[r] * stride;
+      pa.dst = pts;
+      pa.m = L.m[r];
+      pa.total = N;
+      pa.g = L.g;
+      pa.rank = r;
+      pa.stride = stride;
+      pa.err = err;
+      Prof pf(K_PLACEMENT, (double)L.m[r] * 2.0 * stride, 1, st);
+      if (launch_lean_place(pa, st) != cudaSuccess) result = KDB_ERR_CUDA;
+    }
+    if (result != KDB_OK) break;
+    if (cudaMemcpyAsync(pts, top, (size_t)full_nodes(L.g) * stride, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+      result = KDB_ERR_CUDA;
+      break;
+    }
+    result = sync_err(nullptr);
+  } while (0);
+  if (result == KDB_ERR_CUDA) cudaGetLastError();
+  cudaFreeAsync(ws, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && result == KDB_OK) result = KDB_ERR_CUDA;
+  return result;
+}
+
+// Whether an automatic build goes the lean way: its ordinary workspace does
+// not fit the device memory free now (free memory plus what the library's
+// pool holds unused), less a margin.
+bool lean_needed(size_t ws_bytes) {
+  int dev, sms;
+  cudaMemPool_t pool;
+  if (device_setup(&dev, &pool, &sms) != KDB_OK) return false;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  uint64_t reserved = 0, used = 0;
+  cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+  cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+  const size_t avail = free_b + (size_t)(reserved > used ? reserved - used : 0);
+  const size_t margin = (size_t)256 << 20;
+  return ws_bytes + margin > avail;
+}
+}  // namespace
+}  // namespace kdb
+
+
 using namespace kdb;
 
 extern "C" {
@@ -1681,6 +2080,20 @@ kdb_status kdb_build_ex(void* d_points, int64_t n, int k, int stride_bytes, kdb_
   P.mode = split_of(mode);
   P.ctype = ctype_of(mode);
   P.mode_arg = (int)mode;
+  // the memory-lean build, where asked for, or (automatic) where the
+  // ordinary workspace does not fit: only for builds without caller
+  // workspace or extra outputs
+  const int mm = g_memory_mode.load();
+  if (!d_workspace && !d_out_orig_index && !d_out_split_dim && mm != KDB_MEMORY_FAST &&
+      num_levels((uint32_t)n) >= 3) {
+    bool lean = mm == KDB_MEMORY_LEAN;
+    if (!lean) {
+      Plan Q = P;
+      make_plan(Q);
+      lean = !Q.too_wide && lean_needed(Q.bytes);
+    }
+    if (lean) return lean_build(static_cast<unsigned char*>(d_points), n, k, stride_bytes, (int)mode, st);
+  }
   return run(P, static_cast<unsigned char*>(d_points), d_workspace, workspace_bytes,
              d_out_orig_index, d_out_split_dim, st);
 }
@@ -2359,6 +2772,24 @@ kdb_status kdb_validate(const void* d_points, int64_t n, int k, int stride_bytes
   cudaFreeAsync(ws, st);
   cudaStreamSynchronize(st);
   return result;
+}
+
+}  // extern "C"
+extern "C" {
+
+kdb_memory_mode kdb_set_memory_mode(kdb_memory_mode m) {
+  if (m != KDB_MEMORY_AUTO && m != KDB_MEMORY_FAST && m != KDB_MEMORY_LEAN)
+    return (kdb_memory_mode)kdb::g_memory_mode.load();
+  return (kdb_memory_mode)kdb::g_memory_mode.exchange(m);
+}
+
+size_t kdb_lean_workspace_size(int64_t n, int k, int stride_bytes, kdb_split_mode mode) {
+  if (check_common(n, k, stride_bytes) != KDB_OK || check_mode_k(mode, k) != KDB_OK) return 0;
+  int dev, sms;
+  cudaMemPool_t pool;
+  if (device_setup(&dev, &pool, &sms) != KDB_OK) sms = 152;  // no GPU: the size for a GB300
+  const kdb::LeanPlan L = kdb::lean_plan(n, k, stride_bytes, (int)mode, sms);
+  return L.g ? L.bytes : 0;
 }
 
 }  // extern "C"

@@ -170,6 +170,37 @@ __global__ void __launch_bounds__(kDistThreads) dist_scatter_kernel(DistArgs a) 
   }
 }
 
+// Memory-lean build (one GPU): the subtree rooted at node F(g) + rank, built
+// in its own level order, goes to its nodes of the whole tree.  Local node q
+// on the subtree's level lam is node F(g + lam) + (rank << lam) + (q - F(lam))
+// of the whole tree (the level-order numbering of Sec. 2), so the nodes of
+// one local level are one contiguous run.
+__global__ void __launch_bounds__(kDistThreads) lean_place_kernel(LeanPlaceArgs a) {
+  const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.m) return;
+  const int lam = level_of(q);
+  const uint64_t node = (uint64_t)full_nodes(a.g + lam) + ((uint64_t)a.rank << lam) + (q - full_nodes(lam));
+  if (node >= a.total) {
+    atomicOr(a.err, ERR_INTERNAL);
+    return;
+  }
+  const uint32_t words = (uint32_t)a.stride / 4u;
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(a.src + (uint64_t)q * (uint32_t)a.stride);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(a.dst + node * (uint32_t)a.stride);
+  for (uint32_t w = 0; w < words; ++w) dst[w] = src[w];
+}
+
+__global__ void __launch_bounds__(kDistThreads) nan_check_kernel(const unsigned char* pts, uint32_t n, int k,
+                                                                 int stride, uint32_t* err) {
+  bool nan = false;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t* r = reinterpret_cast<const uint32_t*>(pts + (uint64_t)i * (uint32_t)stride);
+    for (int d = 0; d < k; ++d)
+      if ((r[d] & 0x7FFFFFFFu) > 0x7F800000u) nan = true;
+  }
+  if (__any_sync(0xffffffffu, nan) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_NAN);
+}
+
 uint32_t dist_grid(uint32_t n, int sms) {
   uint32_t g = (uint32_t)sms * 4u;
   const uint32_t need = (n + kDistThreads - 1) / kDistThreads;
@@ -212,6 +243,19 @@ cudaError_t launch_dist_count(const DistArgs& a, uint32_t blocks, cudaStream_t s
 cudaError_t launch_dist_scatter(const DistArgs& a, uint32_t blocks, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
   dist_scatter_kernel<<<blocks, kDistThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lean_place(const LeanPlaceArgs& a, cudaStream_t st) {
+  if (a.m == 0) return cudaSuccess;
+  lean_place_kernel<<<(a.m + kDistThreads - 1) / kDistThreads, kDistThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nan_check(const unsigned char* pts, uint32_t n, int k, int stride, uint32_t* err, int sms,
+                             cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  nan_check_kernel<<<dist_grid(n, sms), kDistThreads, 0, st>>>(pts, n, k, stride, err);
   return cudaGetLastError();
 }
 

@@ -257,6 +257,21 @@ cudaError_t launch_dist_box(const DistArgs& a, int sms, cudaStream_t st);
 cudaError_t launch_dist_assign(const DistArgs& a, int sms, cudaStream_t st);
 cudaError_t launch_dist_count(const DistArgs& a, uint32_t blocks, cudaStream_t st);
 cudaError_t launch_dist_scatter(const DistArgs& a, uint32_t blocks, cudaStream_t st);
+// Memory-lean build: a subtree built in its own level order (in a slice of
+// the partitioned records) written to its nodes of the whole tree.
+struct LeanPlaceArgs {
+  const unsigned char* src;  // the subtree's m records, its level order
+  unsigned char* dst;        // the whole tree's records
+  uint32_t m, total;         // subtree nodes, tree nodes
+  int g;                     // the subtree's root is node F(g) + rank
+  uint32_t rank;
+  int stride;
+  uint32_t* err;
+};
+cudaError_t launch_lean_place(const LeanPlaceArgs& a, cudaStream_t st);
+// ERR_NAN in *err if a float coordinate of the n records is NaN.
+cudaError_t launch_nan_check(const unsigned char* pts, uint32_t n, int k, int stride, uint32_t* err, int sms,
+                             cudaStream_t st);
 
 // tree kernels (kdb_tree.cu)
 struct PrepassArgs {

@@ -29,6 +29,7 @@ ERR_NOT_A_KD_TREE = 6
 ERR_INTERNAL = 7
 
 PLACEMENT_AUTO = 0
+MEMORY_AUTO, MEMORY_FAST, MEMORY_LEAN = 0, 1, 2
 PLACEMENT_IN_PLACE = 1
 
 TUNE_PARTITION = 0
@@ -113,6 +114,8 @@ def load():
             "kdb_validate": ([vp, i64, i32, i32, i32, ctypes.POINTER(i64), vp], i32),
             "kdb_debug_inject_fault": ([i32, i64], i32),
             "kdb_set_placement": ([i32], i32),
+            "kdb_set_memory_mode": ([i32], i32),
+            "kdb_lean_workspace_size": ([i64, i32, i32, i32], sz),
             "kdb_tuning_shape_count": ([i32], i32),
             "kdb_tuning_shape": ([i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                   ctypes.POINTER(i32)], i32),
@@ -449,6 +452,17 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def kdb_set_memory_mode(mode: int) -> int:
+    """Process-wide memory mode (MEMORY_AUTO / MEMORY_FAST / MEMORY_LEAN) of
+    kdb_build; returns the previous one."""
+    return load().kdb_set_memory_mode(mode)
+
+
+def kdb_lean_workspace_size(n: int, k: int, stride_bytes: int, mode: int = ROUND_ROBIN) -> int:
+    """Device bytes of the memory-lean build (0: invalid arguments or n < 4)."""
+    return int(load().kdb_lean_workspace_size(n, k, stride_bytes, mode))
 
 
 def kdb_set_placement(placement: int) -> int:

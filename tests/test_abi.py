@@ -275,3 +275,27 @@ def test_binding_constants_match_the_header():
     m = re.search(r"#define KDB_NOALLOC_SCRATCH_BYTES \((\d+)u << (\d+)\)", text)
     assert pts == kdb.NOALLOC_MAX_POINTS
     assert int(m.group(1)) << int(m.group(2)) == kdb.NOALLOC_SCRATCH_BYTES
+
+
+def test_memory_mode_setting_and_lean_sizes(lib):
+    """The memory-mode setting round trip, and the lean build's device memory:
+    at most 40 B per point for float3 at 1e8 (against about 146 for the
+    default), one tag and one index per point, a copy of the records and one
+    subtree's workspace."""
+    try:
+        assert kdb.kdb_set_memory_mode(kdb.MEMORY_LEAN) == kdb.MEMORY_AUTO
+        assert kdb.kdb_set_memory_mode(7) == kdb.MEMORY_LEAN  # refused: unchanged
+        assert kdb.kdb_set_memory_mode(kdb.MEMORY_FAST) == kdb.MEMORY_LEAN
+    finally:
+        kdb.kdb_set_memory_mode(kdb.MEMORY_AUTO)
+    n = 100_000_000
+    lean = kdb.kdb_lean_workspace_size(n, 3, 12)
+    fast = lib.kdb_workspace_size(n, 3, 12, kdb.ROUND_ROBIN)
+    assert 4 * n + 12 * n + 4 * n < lean <= 40 * n < fast
+    for k, stride, mode in [(3, 16, kdb.WIDEST_EXTENT), (3, 12, kdb.WIDEST_TIGHT), (1, 4, kdb.COORDS_INT32),
+                            (4, 16, kdb.ROUND_ROBIN)]:
+        b = kdb.kdb_lean_workspace_size(n, k, stride, mode)
+        assert (8 + stride) * n < b <= (8 + stride + 24) * n, (k, stride, mode)
+    assert kdb.kdb_lean_workspace_size(3, 3, 12) == 0  # too few points for a chosen level
+    assert kdb.kdb_lean_workspace_size(4, 3, 12) > 0
+    assert kdb.kdb_lean_workspace_size(n, 3, 12, kdb.WIDEST_EXTENT | kdb.COORDS_INT32) == 0
