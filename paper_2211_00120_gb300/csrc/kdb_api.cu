@@ -27,6 +27,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -547,6 +548,106 @@ kdb_status upload_tables(const Plan& P, void* ws, cudaStream_t st, bool sync) {
   w.next = -1;
   KDB_CK(copy(at<ActiveEntry>(ws, P.o_whole), &w, sizeof w));
   return KDB_OK;
+}
+
+// The plan's tables as one host image of the workspace span [*off, *off +
+// *bytes) that holds them (gaps zero); false where that span also holds
+// large work arrays (the packed-key path), which upload_tables copies
+// table by table instead.
+bool table_image_span(const Plan& P, size_t* off, size_t* bytes) {
+  const size_t b = P.o_sets, e = align256(P.o_whole + sizeof(ActiveEntry));
+  if (P.o_lbox - P.o_vloc > ((size_t)1 << 16) || P.o_lsets - P.o_lbox > ((size_t)1 << 20)) return false;
+  *off = b;
+  *bytes = e - b;
+  return true;
+}
+void fill_table_image(const Plan& P, unsigned char* img, size_t off) {
+  auto put = [&](size_t o, const void* src, size_t n) {
+    if (n) std::memcpy(img + (o - off), src, n);
+  };
+  put(P.o_sets, P.sets.data(), P.sets.size() * sizeof(SetInfo));
+  size_t at_act = P.o_act;
+  for (const auto& v : P.act) {
+    put(at_act, v.data(), v.size() * sizeof(ActiveEntry));
+    at_act += v.size() * sizeof(ActiveEntry);
+  }
+  if (P.use_local) {
+    put(P.o_lsets, P.lsets.data(), P.lsets.size() * sizeof(LocalSet));
+    put(P.o_work, P.work.data(), P.work.size() * sizeof(LocalWork));
+  }
+  ActiveEntry w{};
+  w.set = 0;
+  w.base = 0;
+  w.next = -1;
+  put(P.o_whole, &w, sizeof w);
+}
+
+// Plans of single builds, kept for builds of the same kind: the same N, k,
+// stride, mode argument and tuning setting give the same plan, so a repeated
+// build skips the planning and uploads its tables from pinned host memory in
+// one asynchronous copy.  A few recent kinds are kept; an entry stays alive
+// while a call that took it runs.
+struct CachedPlan {
+  Plan P;
+  unsigned char* h_img = nullptr;  // pinned, or nullptr: tables uploaded one by one
+  size_t img_off = 0, img_bytes = 0;
+  ~CachedPlan() {
+    if (h_img) cudaFreeHost(h_img);
+  }
+};
+struct PlanKey {
+  uint32_t n;
+  int k, stride, mode_arg, part, rec, bits;
+  bool operator==(const PlanKey& o) const {
+    return n == o.n && k == o.k && stride == o.stride && mode_arg == o.mode_arg && part == o.part &&
+           rec == o.rec && bits == o.bits;
+  }
+};
+constexpr size_t kPlanCacheMax = 8;
+std::mutex g_pcache_mu;
+// never destroyed: its pinned images may outlive the CUDA runtime at exit
+auto* g_pcache = new std::vector<std::pair<PlanKey, std::shared_ptr<CachedPlan>>>();
+
+std::shared_ptr<CachedPlan> cached_plan(int64_t n, int k, int stride, int mode_arg) {
+  const TuneEntry t = tuning_for((uint64_t)n, k, stride, mode_arg, nullptr);
+  const PlanKey key{(uint32_t)n, k, stride, mode_arg, t.part, t.rec, t.bits};
+  {
+    std::lock_guard<std::mutex> lk(g_pcache_mu);
+    for (size_t i = 0; i < g_pcache->size(); ++i)
+      if ((*g_pcache)[i].first == key) {
+        auto e = (*g_pcache)[i];
+        g_pcache->erase(g_pcache->begin() + i);
+        g_pcache->push_back(e);  // most recent last
+        return e.second;
+      }
+  }
+  auto cp = std::make_shared<CachedPlan>();
+  Plan& P = cp->P;
+  P.sets.push_back(SetInfo{0u, (uint32_t)n});
+  P.total = (uint32_t)n;
+  P.k = k;
+  P.stride = stride;
+  P.mode = mode_arg & 0xFF;
+  P.ctype = ctype_of(mode_arg);
+  P.mode_arg = mode_arg;
+  P.part_shape = t.part;
+  P.rec_shape = t.rec;
+  P.rec_bits = t.bits;
+  make_plan(P);
+  if (!P.too_wide && table_image_span(P, &cp->img_off, &cp->img_bytes)) {
+    void* h = nullptr;
+    if (cudaHostAlloc(&h, cp->img_bytes, cudaHostAllocDefault) == cudaSuccess) {
+      cp->h_img = static_cast<unsigned char*>(h);
+      std::memset(cp->h_img, 0, cp->img_bytes);
+      fill_table_image(P, cp->h_img, cp->img_off);
+    } else {
+      cudaGetLastError();
+    }
+  }
+  std::lock_guard<std::mutex> lk(g_pcache_mu);
+  if (g_pcache->size() >= kPlanCacheMax) g_pcache->erase(g_pcache->begin());
+  g_pcache->push_back({key, cp});
+  return cp;
 }
 
 // Enqueues the whole build on `st`.  Does not synchronise.  With
@@ -1138,8 +1239,8 @@ kdb_status finish(const Plan& P, void* ws, cudaStream_t st) {
 }
 
 kdb_status run(Plan& P, unsigned char* pts, void* user_ws, size_t user_bytes, int32_t* out_orig,
-               uint8_t* out_dim, cudaStream_t st) {
-  make_plan(P);
+               uint8_t* out_dim, cudaStream_t st, bool planned = false) {
+  if (!planned) make_plan(P);
   if (P.too_wide) return KDB_ERR_INVALID_ARGUMENT;
   int dev, sms;
   cudaMemPool_t pool;
@@ -1153,6 +1254,40 @@ kdb_status run(Plan& P, unsigned char* pts, void* user_ws, size_t user_bytes, in
     if (s != KDB_OK) return s;
   }
   s = enqueue_build(P, pts, ws, sms, out_orig, out_dim, st);
+  kdb_status f = finish(P, ws, st);
+  if (!user_ws) {
+    cudaFreeAsync(ws, st);
+    cudaStreamSynchronize(st);
+  }
+  return s != KDB_OK ? s : f;
+}
+
+// run() for a cached plan: the tables come from its pinned image.
+kdb_status run_cached(const CachedPlan& C, unsigned char* pts, void* user_ws, size_t user_bytes,
+                      int32_t* out_orig, uint8_t* out_dim, cudaStream_t st) {
+  const Plan& P = C.P;
+  if (P.too_wide) return KDB_ERR_INVALID_ARGUMENT;
+  int dev, sms;
+  cudaMemPool_t pool;
+  kdb_status s = device_setup(&dev, &pool, &sms);
+  if (s != KDB_OK) return s;
+  void* ws = user_ws;
+  if (ws) {
+    if (user_bytes < P.bytes || (reinterpret_cast<uintptr_t>(ws) & 255)) return KDB_ERR_INVALID_ARGUMENT;
+  } else {
+    s = pool_alloc(&ws, P.bytes, pool, st);
+    if (s != KDB_OK) return s;
+  }
+  bool ready = false;
+  if (C.h_img) {
+    if (cudaMemcpyAsync(static_cast<unsigned char*>(ws) + C.img_off, C.h_img, C.img_bytes,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      cudaGetLastError();
+      s = KDB_ERR_CUDA;
+    }
+    ready = true;
+  }
+  if (s == KDB_OK) s = enqueue_build(P, pts, ws, sms, out_orig, out_dim, st, ready);
   kdb_status f = finish(P, ws, st);
   if (!user_ws) {
     cudaFreeAsync(ws, st);
@@ -2072,30 +2207,18 @@ kdb_status kdb_build_ex(void* d_points, int64_t n, int k, int stride_bytes, kdb_
     }
     return KDB_OK;
   }
-  Plan P;
-  P.sets.push_back(SetInfo{0u, (uint32_t)n});
-  P.total = (uint32_t)n;
-  P.k = k;
-  P.stride = stride_bytes;
-  P.mode = split_of(mode);
-  P.ctype = ctype_of(mode);
-  P.mode_arg = (int)mode;
   // the memory-lean build, where asked for, or (automatic) where the
   // ordinary workspace does not fit: only for builds without caller
   // workspace or extra outputs
   const int mm = g_memory_mode.load();
-  if (!d_workspace && !d_out_orig_index && !d_out_split_dim && mm != KDB_MEMORY_FAST &&
-      num_levels((uint32_t)n) >= 3) {
-    bool lean = mm == KDB_MEMORY_LEAN;
-    if (!lean) {
-      Plan Q = P;
-      make_plan(Q);
-      lean = !Q.too_wide && lean_needed(Q.bytes);
-    }
-    if (lean) return lean_build(static_cast<unsigned char*>(d_points), n, k, stride_bytes, (int)mode, st);
-  }
-  return run(P, static_cast<unsigned char*>(d_points), d_workspace, workspace_bytes,
-             d_out_orig_index, d_out_split_dim, st);
+  const bool lean_ok = !d_workspace && !d_out_orig_index && !d_out_split_dim && num_levels((uint32_t)n) >= 3;
+  if (lean_ok && mm == KDB_MEMORY_LEAN)
+    return lean_build(static_cast<unsigned char*>(d_points), n, k, stride_bytes, (int)mode, st);
+  const std::shared_ptr<CachedPlan> cp = cached_plan(n, k, stride_bytes, (int)mode);
+  if (lean_ok && mm == KDB_MEMORY_AUTO && !cp->P.too_wide && lean_needed(cp->P.bytes))
+    return lean_build(static_cast<unsigned char*>(d_points), n, k, stride_bytes, (int)mode, st);
+  return run_cached(*cp, static_cast<unsigned char*>(d_points), d_workspace, workspace_bytes, d_out_orig_index,
+                    d_out_split_dim, st);
 }
 
 kdb_status kdb_build_subtree(void* d_points, int64_t n, int k, int stride_bytes, kdb_split_mode mode,
