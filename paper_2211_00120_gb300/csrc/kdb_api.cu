@@ -1361,6 +1361,7 @@ namespace kdb {
 namespace {
 std::atomic<int> g_memory_mode{KDB_MEMORY_AUTO};
 constexpr int kLeanLevels = 4;  // 16 subtrees: each build's workspace is about 1/16 of one over all points
+constexpr uint32_t kLeanCand = 4096;  // points of one coordinate key gathered per node, at most
 
 // Widest side of a box of coordinate keys, as the device's widest_of_keys:
 // float32 hi - lo (exact key differences for integer coordinates), strict
@@ -1399,7 +1400,7 @@ struct LeanPlan {
   std::vector<uint32_t> m;   // points of each subtree
   size_t sub_bytes = 0;      // workspace of the largest subtree build
   uint32_t blocks = 0;       // partition blocks
-  size_t o_tags, o_out, o_idx, o_hist, o_box, o_dims, o_pre, o_pin, o_top, o_cnt, o_err, o_ws, bytes;
+  size_t o_tags, o_out, o_idx, o_hist, o_box, o_dims, o_pre, o_pin, o_top, o_cnt, o_cand, o_err, o_ws, bytes;
 };
 
 // Layout of the lean build's device memory; g = 0 if n is too small for it.
@@ -1444,6 +1445,7 @@ LeanPlan lean_plan(int64_t n, int k, int stride, int mode_arg, int sms) {
   L.o_pin = take((size_t)top_nodes * 8);
   L.o_top = take((size_t)full_nodes(L.g) * stride);
   L.o_cnt = take((size_t)L.blocks * L.G * 8);
+  L.o_cand = take((size_t)top_nodes * (kLeanCand + 1) * 4);
   L.o_err = take(4);
   L.o_ws = take(L.sub_bytes);
   L.bytes = off;
@@ -1474,6 +1476,7 @@ kdb_status lean_build(unsigned char* pts, int64_t n, int k, int stride, int mode
   int64_t* d_pin = reinterpret_cast<int64_t*>(base + L.o_pin);
   unsigned char* top = base + L.o_top;
   uint32_t* cnt = reinterpret_cast<uint32_t*>(base + L.o_cnt);
+  uint32_t* cand = reinterpret_cast<uint32_t*>(base + L.o_cand);  // [nodes] counts, then [nodes][kLeanCand]
   uint32_t* err = reinterpret_cast<uint32_t*>(base + L.o_err);
   void* sub_ws = base + L.o_ws;
   kdb_status result = KDB_OK;
@@ -1564,6 +1567,32 @@ kdb_status lean_build(unsigned char* pts, int64_t n, int k, int stride, int mode
       }
       std::vector<uint32_t> h((size_t)nodes * 256);
       for (int rnd = 0; rnd < 8 && result == KDB_OK; ++rnd) {
+        if (rnd == 4) {
+          // the coordinate keys are fixed: gather every node's points with
+          // its key; the pivot is the one of rank remaining[u] among them by
+          // index (four histogram passes over all points otherwise)
+          std::vector<uint32_t> cc(nodes), cl((size_t)nodes * kLeanCand);
+          Prof pf(K_LEAN, (double)N * 8.0, 1, st);
+          if (cudaMemcpyAsync(d_pre, prefix.data(), (size_t)nodes * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+              cudaMemsetAsync(cand, 0, (size_t)nodes * 4, st) != cudaSuccess ||
+              launch_lean_collect(a, kLeanCand, cand, cand + nodes, sms, st) != cudaSuccess ||
+              cudaMemcpyAsync(cc.data(), cand, (size_t)nodes * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+              cudaMemcpyAsync(cl.data(), cand + nodes, cl.size() * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+            result = KDB_ERR_CUDA;
+            break;
+          }
+          if ((result = sync_err(nullptr)) != KDB_OK) break;
+          bool all = true;
+          for (uint32_t u = 0; u < nodes; ++u) all = all && cc[u] <= kLeanCand && remaining[u] < cc[u];
+          if (all) {
+            for (uint32_t u = 0; u < nodes; ++u) {
+              uint32_t* c0 = cl.data() + (size_t)u * kLeanCand;
+              std::nth_element(c0, c0 + remaining[u], c0 + cc[u]);
+              prefix[u] = (prefix[u] << 32) | c0[remaining[u]];
+            }
+            break;  // every pivot is known
+          }
+        }
         a.prefix_bits = 8 * rnd;
         Prof pf(K_LEAN, (double)N * 8.0, 1, st);
         if (cudaMemcpyAsync(d_pre, prefix.data(), (size_t)nodes * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||

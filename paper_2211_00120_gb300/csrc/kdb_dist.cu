@@ -190,6 +190,25 @@ __global__ void __launch_bounds__(kDistThreads) lean_place_kernel(LeanPlaceArgs 
   for (uint32_t w = 0; w < words; ++w) dst[w] = src[w];
 }
 
+// Memory-lean build: once a node's pivot has its coordinate key fixed, its
+// index is one of the few points of the node with that key; they are
+// gathered here instead of four more histogram passes over all points.
+__global__ void __launch_bounds__(kDistThreads) lean_collect_kernel(DistArgs a, uint32_t cap, uint32_t* counts,
+                                                                    uint32_t* out) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+    const int u = dist_node(a, i);
+    if (u < 0) continue;
+    const int d = a.node_dim[u];
+    if (d >= a.k) {
+      atomicOr(a.err, ERR_INTERNAL);
+      continue;
+    }
+    if ((uint32_t)(dist_key64(a, i, d) >> 32) != (uint32_t)a.prefix[u]) continue;
+    const uint32_t j = atomicAdd(&counts[u], 1u);
+    if (j < cap) out[(uint64_t)u * cap + j] = a.index_base + i;
+  }
+}
+
 __global__ void __launch_bounds__(kDistThreads) nan_check_kernel(const unsigned char* pts, uint32_t n, int k,
                                                                  int stride, uint32_t* err) {
   bool nan = false;
@@ -249,6 +268,13 @@ cudaError_t launch_dist_scatter(const DistArgs& a, uint32_t blocks, cudaStream_t
 cudaError_t launch_lean_place(const LeanPlaceArgs& a, cudaStream_t st) {
   if (a.m == 0) return cudaSuccess;
   lean_place_kernel<<<(a.m + kDistThreads - 1) / kDistThreads, kDistThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lean_collect(const DistArgs& a, uint32_t cap, uint32_t* counts, uint32_t* out, int sms,
+                                cudaStream_t st) {
+  if (a.n == 0) return cudaSuccess;
+  lean_collect_kernel<<<dist_grid(a.n, sms), kDistThreads, 0, st>>>(a, cap, counts, out);
   return cudaGetLastError();
 }
 

@@ -269,6 +269,11 @@ struct LeanPlaceArgs {
   uint32_t* err;
 };
 cudaError_t launch_lean_place(const LeanPlaceArgs& a, cudaStream_t st);
+// Memory-lean build: the original indices of every node's points whose
+// coordinate key equals the node's (a.prefix, 32 bits), up to `cap` per node
+// (out[node * cap + j]; counts[node] = all of them, zeroed by the caller).
+cudaError_t launch_lean_collect(const DistArgs& a, uint32_t cap, uint32_t* counts, uint32_t* out, int sms,
+                                cudaStream_t st);
 // ERR_NAN in *err if a float coordinate of the n records is NaN.
 cudaError_t launch_nan_check(const unsigned char* pts, uint32_t n, int k, int stride, uint32_t* err, int sms,
                              cudaStream_t st);
