@@ -594,9 +594,17 @@ KDB_API int64_t kdb_launch_count(void);
  *   KDB_FAULT_LOOKBACK_PARTITION  the same for the next build's per-level
  *                         partition passes only, which run after the first
  *                         pivots have been placed.
+ *   KDB_FAULT_LOW_MEMORY  the next automatic memory-mode decision
+ *                         (kdb_set_memory_mode) sees only `arg` bytes free.
  * Returns the previous fault setting.  Not thread-safe; tests only.
  */
-enum { KDB_FAULT_NONE = 0, KDB_FAULT_ALLOC = 1, KDB_FAULT_LOOKBACK = 2, KDB_FAULT_LOOKBACK_PARTITION = 3 };
+enum {
+  KDB_FAULT_NONE = 0,
+  KDB_FAULT_ALLOC = 1,
+  KDB_FAULT_LOOKBACK = 2,
+  KDB_FAULT_LOOKBACK_PARTITION = 3,
+  KDB_FAULT_LOW_MEMORY = 4
+};
 KDB_API int kdb_debug_inject_fault(int fault, int64_t arg);
 
 #ifdef __cplusplus

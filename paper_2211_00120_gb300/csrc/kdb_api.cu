@@ -280,6 +280,12 @@ struct Plan {
   bool can_direct = false;   // records (stride 4k) can be written from their entries
   size_t o_gather = 0, gather_bytes = 0;  // placement through spare workspace
   size_t rec_hist_off = 0;  // record-sort histograms (in u32, inside the histogram area)
+  // Round robin over one set, k >= 2, at least two global levels: list
+  // dim0 + 1 is sorted by (side of the root, key) in its last digit pass and
+  // starts on level 1 (8-bit digits; the workspace is sized for it whatever
+  // the width).  tag_hist_off: its (side, digit) counts (512 u32).
+  bool tag_fold_room = false;
+  size_t tag_hist_off = 0;
   uint32_t max_nseg = 0;
   uint64_t kstride = 0;  // elements between two dimensions' coordinate keys
 };
@@ -377,6 +383,8 @@ void make_plan(Plan& P) {
         P.chunks[0] = chunk;
         P.rec_hist_off = hist_words;  // room for the most passes of any width
         hist_words += (size_t)P.k * kRecMaxPasses * na * kRadixBins;
+        P.tag_hist_off = hist_words;
+        hist_words += 2 * kRadixBins;
       }
     } else if (P.seg[l]) {
       P.passes[l] = std::max(1, ceil_div_i(P.rb, 8));
@@ -440,7 +448,10 @@ void make_plan(Plan& P) {
       std::min<uint64_t>(std::min(kSortTile, kSegTile), (uint64_t)rec_sort_tile());
   const size_t tiles = (std::max<uint64_t>(T, P.max_items) + min_tile - 1) / min_tile;
   const size_t part_tiles = (std::max<uint64_t>(T, P.max_items) + kPartTile - 1) / kPartTile;
-  P.o_status = take(std::max(tiles * kRadixBins, part_tiles * kLiftBins) * 8);
+  P.tag_fold_room = P.use_lists && P.mode == KDB_SPLIT_ROUND_ROBIN && P.sets.size() == 1 && P.k >= 2 &&
+                    levels >= 2;
+  // the tagged pass takes a second set of look-back words (one per side)
+  P.o_status = take(std::max(tiles * kRadixBins * (P.tag_fold_room ? 2 : 1), part_tiles * kLiftBins) * 8);
   P.o_hist = take(hist_words * 4);
   P.o_tickets = take((size_t)P.total_passes * 4);
   P.o_err = take(4);
@@ -954,6 +965,26 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     lat[d] = q;
     return e;
   };
+  // pivots of level l (Observation 1), from the list of its split dimension
+  auto pivots_of = [&](int l) -> cudaError_t {
+    PivotArgs pv{};
+    pv.x = level_ctx(l);
+    for (int d = 0; d < k; ++d) pv.lists[d] = lcur[d];
+    pv.items = P.items[l];
+    pv.piv = piv_ring[l % kLiftMax];
+    pv.perm = perm;
+    pv.dims = dims;
+    pv.k = k;
+    pv.mode = P.mode;
+    pv.pts_out = direct ? pts : nullptr;
+    pv.stride = P.stride;
+    pv.ctype = P.ctype;
+    Prof pf(K_PIVOT, (double)(pv.x.nact << l) * 20, 1, st);
+    return launch_pivots(pv, st);
+  };
+  // list dim0 + 1 arrives on level 1 from its last digit pass (one set,
+  // round robin, 8-bit digits): no partition pass for level 1
+  const bool fold = P.tag_fold_room && lazy && rec_bits == 8;
   if (P.use_lists) {
     for (int d = 0; d < k; ++d) {
       lcur[d] = at<uint4>(ws, P.o_lists) + (size_t)(2 * d) * T;
@@ -994,7 +1025,11 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
         Prof pf(K_LISTS, (double)n0 * 16, 1, st);
         KDB_CK(launch_rec_hist(rh, st));
       }
-      for (int d = 0; d < k; ++d) {
+      const int d0 = P.dim0 % k, d1 = (P.dim0 + 1) % k;
+      uint32_t* thist = hist + P.tag_hist_off;
+      for (int di = 0; di < k; ++di) {
+        const int d = (P.dim0 + di) % k;
+        const bool tagged = fold && d == d1;
         const uint4* in = l0;
         for (int p = 0; p < rec_np; ++p) {
           // ping-pong between the dimension's two list buffers, ending in lcur
@@ -1002,9 +1037,23 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
           PassCtl c = ctl(n0, rec_bits * p, nullptr);
           const uint32_t* sh = rh.hist + ((size_t)(d * rec_np + p) * x0.nact) * kRadixBins;
           Prof pf(K_RADIX, (double)n0 * 32, 1, st);
-          KDB_CK(launch_rec_sort_pass(in, out, c, x0, sh, d, rec_shape, rec_bits, st));
+          if (tagged && p + 1 == rec_np) {
+            // the last digit with the side of the root: the list leaves on level 1
+            PassCtl c1 = c;
+            c.status_words /= 2;
+            c1.status_words = c.status_words;
+            c1.status = c.status + c.status_words;
+            KDB_CK(launch_rec_tag_pass(in, out, c, c1, piv_ring[0], d0, thist, d, rec_shape, st));
+          } else if (tagged && p == 0) {
+            const RecCount rc{piv_ring[0], d0, thist, rec_bits * (rec_np - 1)};
+            KDB_CK(launch_rec_sort_pass(in, out, c, x0, sh, d, rec_shape, rec_bits, st, &rc));
+          } else {
+            KDB_CK(launch_rec_sort_pass(in, out, c, x0, sh, d, rec_shape, rec_bits, st));
+          }
           in = out;
         }
+        if (fold && d == d0) KDB_CK(pivots_of(0));  // the root, before list d1's passes need its side
+        if (tagged) lat[d] = 1;
       }
     }
   }
@@ -1027,22 +1076,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     if (P.use_lists) {
       const int dl = (l + P.dim0) % k;  // the level's round-robin split dimension
       if (lazy && lat[dl] < l) KDB_CK(lift(dl, lat[dl], l, false));
-      PivotArgs pv{};
-      pv.x = x;
-      for (int d = 0; d < k; ++d) pv.lists[d] = lcur[d];
-      pv.items = n;
-      pv.piv = piv_ring[l % kLiftMax];
-      pv.perm = perm;
-      pv.dims = dims;
-      pv.k = k;
-      pv.mode = P.mode;
-      pv.pts_out = direct ? pts : nullptr;
-      pv.stride = P.stride;
-      pv.ctype = P.ctype;
-      {
-        Prof pf(K_PIVOT, (double)(x.nact << l) * 20, 1, st);
-        KDB_CK(launch_pivots(pv, st));
-      }
+      if (!(fold && l == 0)) KDB_CK(pivots_of(l));  // level 0's: taken while the lists were sorted
       // every list follows the level (sets leaving hand their lists over)
       if (!lazy)
         for (int d = 0; d < k; ++d) KDB_CK(lift(d, l, l + 1, false));
@@ -1754,6 +1788,10 @@ kdb_status lean_build(unsigned char* pts, int64_t n, int k, int stride, int mode
 // not fit the device memory free now (free memory plus what the library's
 // pool holds unused), less a margin.
 bool lean_needed(size_t ws_bytes) {
+  if (g_fault == KDB_FAULT_LOW_MEMORY) {  // tests: as if only g_fault_arg bytes were free
+    g_fault = KDB_FAULT_NONE;
+    return ws_bytes + ((size_t)256 << 20) > (size_t)std::max<int64_t>(g_fault_arg, 0);
+  }
   int dev, sms;
   cudaMemPool_t pool;
   if (device_setup(&dev, &pool, &sms) != KDB_OK) return false;

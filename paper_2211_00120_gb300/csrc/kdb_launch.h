@@ -139,12 +139,28 @@ struct PartArgs {
   uint32_t out_base0;       // the set's first position in the list on level p + b
 };
 size_t partition_smem(int shape);
+// The first pass of list D1 can also count, for the tagged last pass of that
+// list (rec_tag_pass), every entry's (side of the root's pivot, last digit)
+// into thist[512]; the root itself is not counted.
+struct RecCount {
+  const uint2* piv;   // the root's pivot (key in dimension pdim, index)
+  int pdim;           // the root's split dimension
+  uint32_t* thist;    // [2][256], added to; nullptr: no counting
+  int tshift;         // bit offset of the last digit
+};
 size_t rec_sort_smem(int shape);
 uint32_t rec_sort_tile();  // entries of the smallest record-sort tile (one look-back word per digit each)
 cudaError_t launch_gather_level0(const ListBuildArgs& a, cudaStream_t st);
 cudaError_t launch_rec_hist(const RecHistArgs& a, cudaStream_t st);
 cudaError_t launch_rec_sort_pass(const uint4* in, uint4* out, const PassCtl& c, const LevelCtx& x,
-                                 const uint32_t* seg_hist, int d, int shape, int bits, cudaStream_t st);
+                                 const uint32_t* seg_hist, int d, int shape, int bits, cudaStream_t st,
+                                 const RecCount* count = nullptr);
+// The last pass of list D1 of one set, sorted by (side of the root's pivot,
+// digit): the list leaves the pass on level 1, the root dropped (n - 1
+// entries out).  c1: the look-back words of the second side (c1.status a
+// region of its own).
+cudaError_t launch_rec_tag_pass(const uint4* in, uint4* out, const PassCtl& c, const PassCtl& c1, const uint2* piv,
+                                int pdim, const uint32_t* thist, int d, int shape, cudaStream_t st);
 cudaError_t launch_pivots(const PivotArgs& a, cudaStream_t st);
 cudaError_t launch_partition(const PartArgs& a, cudaStream_t st);
 

@@ -40,6 +40,7 @@ FAULT_NONE = 0
 FAULT_ALLOC = 1
 FAULT_LOOKBACK = 2
 FAULT_LOOKBACK_PARTITION = 3
+FAULT_LOW_MEMORY = 4
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libkdb.so")

@@ -65,7 +65,9 @@ def test_workspace_size_grows_with_n(lib):
     a = lib.kdb_workspace_size(1000, 3, 12, 0)
     b = lib.kdb_workspace_size(100000, 3, 12, 0)
     c = lib.kdb_workspace_size(100000, 3, 12, 1)
-    assert 0 < a < b <= c
+    # the split rules differ in their extras (round robin: a second set of
+    # look-back words for its tagged pass; widest: the domains)
+    assert 0 < a < b and a < c and abs(b - c) < 0.05 * b
     # linear in N: under 256 bytes per point at these sizes (three lists of
     # 16-byte entries, double-buffered, dominate)
     assert b < 256 * 100000

@@ -100,3 +100,25 @@ def test_lean_workspace_is_small():
     lean = kdb.kdb_lean_workspace_size(n, 3, 12)
     fast = kdb.load().kdb_workspace_size(n, 3, 12, kdb.ROUND_ROBIN)
     assert lean / n <= 40 and fast / lean > 4
+
+
+def test_automatic_mode_goes_lean_when_memory_is_short():
+    """MEMORY_AUTO takes the lean build when the default workspace does not
+    fit the free memory (made short here by the host-side test hook), the
+    default build otherwise; both give the oracle's tree."""
+    kdb.kdb_set_memory_mode(kdb.MEMORY_AUTO)
+    pts = synth.uniform(400_000, 3, seed=56)
+    want, _ = oracle.build(pts, 3, oracle.ROUND_ROBIN)
+    lean_bytes = kdb.kdb_lean_workspace_size(len(pts), 3, 12)
+    fast_bytes = kdb.load().kdb_workspace_size(len(pts), 3, 12, kdb.ROUND_ROBIN)
+    assert lean_bytes < fast_bytes
+    for short, kind in [(True, "lean_top_levels"), (False, "radix_pass")]:
+        if short:  # free memory between the two workspaces
+            kdb.kdb_debug_inject_fault(kdb.FAULT_LOW_MEMORY, (256 << 20) + (lean_bytes + fast_bytes) // 2)
+        d = torch.from_numpy(pts.copy()).cuda()
+        kdb.kdb_profile_start()
+        kdb.kdb_build(d, 3, kdb.ROUND_ROBIN)
+        kinds = {p["name"] for p in kdb.kdb_profile_stop()}
+        assert kind in kinds and (("lean_top_levels" in kinds) == short)
+        assert d.cpu().numpy().view(np.uint32).tobytes() == want.view(np.uint32).tobytes()
+    assert kdb.kdb_debug_inject_fault(kdb.FAULT_NONE, 0) == kdb.FAULT_NONE  # the hook was used up
