@@ -363,3 +363,20 @@ def test_failure_after_first_pivots_leaves_records_untouched(placement):
         assert_same(pts, 3, RR)
     finally:
         kdb.kdb_set_placement(prev)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+@pytest.mark.parametrize("n", [16383, 16384, 24575, 32767, 32768, 49153, 131071, 131072])
+def test_level1_list_from_its_last_pass(n, k):
+    """Round robin over one set with at least two global levels: the list of
+    the level-1 dimension leaves its last digit pass already on level 1
+    (sorted by side of the root, then key), the root dropped.  Sizes around
+    the first ones with two global levels, perfect trees and ragged ones,
+    ties in the root's dimension (the side of equal keys is decided by
+    index)."""
+    pts = synth.uniform(n, k, seed=n + k)
+    pts[::3, 0] = pts[7, 0]  # a third of the points share the root dimension's key
+    assert_same(pts, k, RR)
+    ints = synth.int32_uniform(n, k, seed=n)
+    ints[::5, 0] = -1
+    assert_same(ints, k, RR)
