@@ -150,10 +150,13 @@ cudaEvent_t take_event() {
 
 // Brackets one launcher call: counts its kernel launches and, while
 // profiling is on, records an event pair around it on the launch stream.
+// timed = false: only counted (a launch inside a phase timed as a whole);
+// count = false: only timed (the whole phase, its launches counted inside).
 class Prof {
  public:
-  Prof(int kind, double bytes, int launches, cudaStream_t st) : st_(st) {
-    g_launches += launches;
+  Prof(int kind, double bytes, int launches, cudaStream_t st, bool timed = true, bool count = true) : st_(st) {
+    if (count) g_launches += launches;
+    if (!timed) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_on) return;
     rec_.kind = kind;
@@ -286,6 +289,8 @@ struct Plan {
   // the width).  tag_hist_off: its (side, digit) counts (512 u32).
   bool tag_fold_room = false;
   size_t tag_hist_off = 0;
+  bool side_list = false;  // list dim0 + 2 sorted on a second stream (one set, k >= 3)
+  int rec_regions = 1;     // look-back regions of the level-0 sorts, tiles * 256 words each
   uint32_t max_nseg = 0;
   uint64_t kstride = 0;  // elements between two dimensions' coordinate keys
 };
@@ -450,8 +455,13 @@ void make_plan(Plan& P) {
   const size_t part_tiles = (std::max<uint64_t>(T, P.max_items) + kPartTile - 1) / kPartTile;
   P.tag_fold_room = P.use_lists && P.mode == KDB_SPLIT_ROUND_ROBIN && P.sets.size() == 1 && P.k >= 2 &&
                     levels >= 2;
-  // the tagged pass takes a second set of look-back words (one per side)
-  P.o_status = take(std::max(tiles * kRadixBins * (P.tag_fold_room ? 2 : 1), part_tiles * kLiftBins) * 8);
+  // one set, k = 3: list dim0 + 2 is sorted on a second stream beside the
+  // others, with look-back words of its own
+  P.side_list = P.use_lists && P.sets.size() == 1 && P.k >= 3 && levels >= 1;
+  // regions of look-back words for the level-0 sorts: the tagged pass takes
+  // a second (one per side), the side stream's passes a third
+  P.rec_regions = 1 + (P.tag_fold_room ? 1 : 0) + (P.side_list ? 1 : 0);
+  P.o_status = take(std::max(tiles * kRadixBins * P.rec_regions, part_tiles * kLiftBins) * 8);
   P.o_hist = take(hist_words * 4);
   P.o_tickets = take((size_t)P.total_passes * 4);
   P.o_err = take(4);
@@ -672,6 +682,44 @@ struct HostFeed {
   cudaStream_t cs = nullptr;
   cudaEvent_t ev[8] = {};
   int chunks = 0;
+};
+
+// A second stream for work that may run beside `st`: fork() makes it wait
+// for what `st` has enqueued so far, join() marks the end of its work, and
+// wait() makes `st` wait for that.  The stream and events are released when
+// the object goes (after their work, by the runtime's deferred release).
+struct SideStream {
+  cudaStream_t s = nullptr, st0 = nullptr;
+  cudaEvent_t f = nullptr, j = nullptr;
+  bool joined = false, waited = false;
+  cudaError_t fork(cudaStream_t st) {
+    st0 = st;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(f, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, f, 0);
+    return e;
+  }
+  cudaError_t join(cudaStream_t) {
+    joined = true;
+    return cudaEventRecord(j, s);
+  }
+  cudaError_t wait(cudaStream_t st) {
+    waited = true;
+    return cudaStreamWaitEvent(st, j, 0);
+  }
+  ~SideStream() {
+    // a build left early: `st` still waits for the side stream's work, so
+    // that nothing freed in stream order on `st` is in use there
+    if (s && j && !waited) {
+      if (!joined) cudaEventRecord(j, s);
+      cudaStreamWaitEvent(st0, j, 0);
+    }
+    if (f) cudaEventDestroy(f);
+    if (j) cudaEventDestroy(j);
+    if (s) cudaStreamDestroy(s);
+  }
 };
 
 kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
@@ -1027,7 +1075,34 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       }
       const int d0 = P.dim0 % k, d1 = (P.dim0 + 1) % k;
       uint32_t* thist = hist + P.tag_hist_off;
-      for (int di = 0; di < k; ++di) {
+      // one set, k = 3: list dim0 + 2 is sorted on a second stream, forked
+      // from `st` and joined back before the levels, so that its passes run
+      // beside the other lists' (each pass is bound by its own latency, not
+      // by bandwidth).  Not while `st` is being captured into a graph.
+      cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+      if (P.side_list) KDB_CK(cudaStreamIsCapturing(st, &cap));
+      const bool side = P.side_list && cap == cudaStreamCaptureStatusNone;
+      const uint64_t region = (P.o_hist - P.o_status) / 8 / P.rec_regions;  // look-back words of one region
+      // the passes run side by side, so the phase is timed as a whole
+      Prof phase(K_RADIX, (double)n0 * 32 * rec_np * k, rec_np * k, st, side, false);
+      SideStream aux;
+      if (side) {
+        KDB_CK(aux.fork(st));
+        const int d = (P.dim0 + 2) % k;
+        const uint4* in = l0;
+        for (int p = 0; p < rec_np; ++p) {
+          uint4* out = ((rec_np - 1 - p) & 1) ? lnext[d] : lcur[d];
+          PassCtl c = ctl(n0, rec_bits * p, nullptr);
+          c.status += (P.rec_regions - 1) * region;  // the last region
+          c.status_words = region;
+          const uint32_t* sh = rh.hist + ((size_t)(d * rec_np + p) * x0.nact) * kRadixBins;
+          Prof pf(K_RADIX, (double)n0 * 32, 1, aux.s, false);
+          KDB_CK(launch_rec_sort_pass(in, out, c, x0, sh, d, rec_shape, rec_bits, aux.s));
+          in = out;
+        }
+        KDB_CK(aux.join(st));
+      }
+      for (int di = 0; di < (side ? k - 1 : k); ++di) {
         const int d = (P.dim0 + di) % k;
         const bool tagged = fold && d == d1;
         const uint4* in = l0;
@@ -1035,14 +1110,14 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
           // ping-pong between the dimension's two list buffers, ending in lcur
           uint4* out = ((rec_np - 1 - p) & 1) ? lnext[d] : lcur[d];
           PassCtl c = ctl(n0, rec_bits * p, nullptr);
+          c.status_words = region;
           const uint32_t* sh = rh.hist + ((size_t)(d * rec_np + p) * x0.nact) * kRadixBins;
-          Prof pf(K_RADIX, (double)n0 * 32, 1, st);
+          Prof pf(K_RADIX, (double)n0 * 32, 1, st, !side);
           if (tagged && p + 1 == rec_np) {
-            // the last digit with the side of the root: the list leaves on level 1
+            // the last digit with the side of the root: the list leaves on
+            // level 1 (the second region holds the right side's words)
             PassCtl c1 = c;
-            c.status_words /= 2;
-            c1.status_words = c.status_words;
-            c1.status = c.status + c.status_words;
+            c1.status = c.status + region;
             KDB_CK(launch_rec_tag_pass(in, out, c, c1, piv_ring[0], d0, thist, d, rec_shape, st));
           } else if (tagged && p == 0) {
             const RecCount rc{piv_ring[0], d0, thist, rec_bits * (rec_np - 1)};
@@ -1055,6 +1130,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
         if (fold && d == d0) KDB_CK(pivots_of(0));  // the root, before list d1's passes need its side
         if (tagged) lat[d] = 1;
       }
+      if (side) KDB_CK(aux.wait(st));
     }
   }
   for (int l = 0; l < levels; ++l) {
