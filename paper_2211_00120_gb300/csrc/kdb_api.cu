@@ -967,8 +967,16 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
   };
   // advance list d from level p to level q (the local finish's level if
   // handoff), with the pivots of levels p .. q-1
-  auto lift = [&](int d, int p, int q, bool handoff) -> cudaError_t {
+  // (ls, soff, swords: the stream, and the look-back words, of a lift that
+  // runs beside others; timed: whether its own time is recorded)
+  auto lift = [&](int d, int p, int q, bool handoff, cudaStream_t ls = nullptr, uint64_t soff = 0,
+                  uint64_t swords = 0, bool timed = true) -> cudaError_t {
+    if (!ls) ls = st;
     PassCtl c = ctl(P.items[p], 0, nullptr);
+    if (swords) {
+      c.status += soff;
+      c.status_words = swords;
+    }
     if (fault_part) c.wait_epoch = c.epoch + 0x10000000u;
     PartArgs pa{};
     pa.x = level_ctx(p);
@@ -1006,15 +1014,15 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     // written as entries, or (hand-over) as original indices, list 0 as
     // entries when it is handed over whole
     const double wbytes = !handoff ? 16.0 : (lents && d == 0 ? 16.0 : 4.0);
-    Prof pf(K_PARTITION, (double)P.items[p] * (16.0 + wbytes), 1, st);
+    Prof pf(K_PARTITION, (double)P.items[p] * (16.0 + wbytes), 1, ls, timed);
     pa.shape = part_shape;
-    cudaError_t e = launch_partition(pa, st);
+    cudaError_t e = launch_partition(pa, ls);
     std::swap(lcur[d], lnext[d]);
     lat[d] = q;
     return e;
   };
   // pivots of level l (Observation 1), from the list of its split dimension
-  auto pivots_of = [&](int l) -> cudaError_t {
+  auto pivots_of = [&](int l, bool timed = true) -> cudaError_t {
     PivotArgs pv{};
     pv.x = level_ctx(l);
     for (int d = 0; d < k; ++d) pv.lists[d] = lcur[d];
@@ -1027,7 +1035,7 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     pv.pts_out = direct ? pts : nullptr;
     pv.stride = P.stride;
     pv.ctype = P.ctype;
-    Prof pf(K_PIVOT, (double)(pv.x.nact << l) * 20, 1, st);
+    Prof pf(K_PIVOT, (double)(pv.x.nact << l) * 20, 1, st, timed);
     return launch_pivots(pv, st);
   };
   // list dim0 + 1 arrives on level 1 from its last digit pass (one set,
@@ -1127,7 +1135,9 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
           }
           in = out;
         }
-        if (fold && d == d0) KDB_CK(pivots_of(0));  // the root, before list d1's passes need its side
+        // the root, before list d1's passes need its side (inside the list
+        // phase, and timed with it when that runs beside the side stream)
+        if (fold && d == d0) KDB_CK(pivots_of(0, !side));
         if (tagged) lat[d] = 1;
       }
       if (side) KDB_CK(aux.wait(st));
@@ -1272,8 +1282,30 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
     }
   }
 
-  if (lazy && levels > 0)  // hand every list over to the local finish
-    for (int d = 0; d < k; ++d) KDB_CK(lift(d, lat[d], levels, true));
+  if (lazy && levels > 0) {
+    // hand every list over to the local finish: the lists are independent,
+    // so lists 1 .. k-1 go on side streams beside list 0, each with
+    // look-back words of its own (not while `st` is being captured)
+    const uint64_t words = ((uint64_t)std::max(T, P.max_items) + kPartTile - 1) / kPartTile * kLiftBins;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    KDB_CK(cudaStreamIsCapturing(st, &cap));
+    const bool par = k > 1 && cap == cudaStreamCaptureStatusNone && (uint64_t)k * words <= (P.o_hist - P.o_status) / 8;
+    if (!par) {
+      for (int d = 0; d < k; ++d) KDB_CK(lift(d, lat[d], levels, true));
+    } else {
+      double bytes = 0.0;
+      for (int d = 0; d < k; ++d) bytes += (double)P.items[lat[d]] * (16.0 + (lents && d == 0 ? 16.0 : 4.0));
+      Prof phase(K_PARTITION, bytes, k, st, true, false);  // the lifts run side by side: timed as a whole
+      SideStream side[2];
+      for (int d = 1; d < k; ++d) {
+        KDB_CK(side[d - 1].fork(st));
+        KDB_CK(lift(d, lat[d], levels, true, side[d - 1].s, d * words, words, false));
+        KDB_CK(side[d - 1].join(st));
+      }
+      KDB_CK(lift(0, lat[0], levels, true, st, 0, words, false));
+      for (int d = 1; d < k; ++d) KDB_CK(side[d - 1].wait(st));
+    }
+  }
 
   // ---- subtrees small enough for one block: all remaining levels on chip
   if (P.use_local && !P.work.empty()) {
