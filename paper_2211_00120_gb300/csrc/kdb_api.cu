@@ -460,7 +460,7 @@ void make_plan(Plan& P) {
   P.side_list = P.use_lists && P.sets.size() == 1 && P.k >= 3 && levels >= 1;
   // regions of look-back words for the level-0 sorts: the tagged pass takes
   // a second (one per side), the side stream's passes a third
-  P.rec_regions = 1 + (P.tag_fold_room ? 1 : 0) + (P.side_list ? 1 : 0);
+  P.rec_regions = (P.side_list ? P.k : 1) + (P.tag_fold_room ? 1 : 0);
   P.o_status = take(std::max(tiles * kRadixBins * P.rec_regions, part_tiles * kLiftBins) * 8);
   P.o_hist = take(hist_words * 4);
   P.o_tickets = take((size_t)P.total_passes * 4);
@@ -1083,64 +1083,83 @@ kdb_status enqueue_build(const Plan& P, unsigned char* pts, void* ws, int sms,
       }
       const int d0 = P.dim0 % k, d1 = (P.dim0 + 1) % k;
       uint32_t* thist = hist + P.tag_hist_off;
-      // one set, k = 3: list dim0 + 2 is sorted on a second stream, forked
-      // from `st` and joined back before the levels, so that its passes run
-      // beside the other lists' (each pass is bound by its own latency, not
-      // by bandwidth).  Not while `st` is being captured into a graph.
+      // One set, k = 3, `st` not being captured into a graph: every list is
+      // sorted on a stream of its own (lists dim0 + 1 and dim0 + 2 on side
+      // streams forked from `st`, joined back before the levels), so that
+      // their passes run side by side (each pass is bound by its own latency,
+      // not by bandwidth); list dim0 + 1 waits for the root's pivot only
+      // before the passes that need it.  Look-back regions: one per list,
+      // and one more for the right side of the tagged pass.
       cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
       if (P.side_list) KDB_CK(cudaStreamIsCapturing(st, &cap));
       const bool side = P.side_list && cap == cudaStreamCaptureStatusNone;
       const uint64_t region = (P.o_hist - P.o_status) / 8 / P.rec_regions;  // look-back words of one region
       // the passes run side by side, so the phase is timed as a whole
       Prof phase(K_RADIX, (double)n0 * 32 * rec_np * k, rec_np * k, st, side, false);
-      SideStream aux;
-      if (side) {
-        KDB_CK(aux.fork(st));
-        const int d = (P.dim0 + 2) % k;
-        const uint4* in = l0;
-        for (int p = 0; p < rec_np; ++p) {
-          uint4* out = ((rec_np - 1 - p) & 1) ? lnext[d] : lcur[d];
-          PassCtl c = ctl(n0, rec_bits * p, nullptr);
-          c.status += (P.rec_regions - 1) * region;  // the last region
-          c.status_words = region;
-          const uint32_t* sh = rh.hist + ((size_t)(d * rec_np + p) * x0.nact) * kRadixBins;
-          Prof pf(K_RADIX, (double)n0 * 32, 1, aux.s, false);
-          KDB_CK(launch_rec_sort_pass(in, out, c, x0, sh, d, rec_shape, rec_bits, aux.s));
-          in = out;
+      SideStream aux[2];
+      cudaEvent_t root_done = nullptr;  // the root's pivot is taken
+      struct EventGuard {
+        cudaEvent_t* e;
+        ~EventGuard() {
+          if (*e) cudaEventDestroy(*e);
         }
-        KDB_CK(aux.join(st));
-      }
-      for (int di = 0; di < (side ? k - 1 : k); ++di) {
-        const int d = (P.dim0 + di) % k;
+      } root_guard{&root_done};
+      // passes [pa, pb) of list d on stream ls with look-back region reg
+      auto sort_list = [&](int d, int pa, int pb, cudaStream_t ls, int reg) -> cudaError_t {
         const bool tagged = fold && d == d1;
-        const uint4* in = l0;
-        for (int p = 0; p < rec_np; ++p) {
+        for (int p = pa; p < pb; ++p) {
+          const uint4* in = p == 0 ? l0 : (((rec_np - p) & 1) ? lnext[d] : lcur[d]);
           // ping-pong between the dimension's two list buffers, ending in lcur
           uint4* out = ((rec_np - 1 - p) & 1) ? lnext[d] : lcur[d];
           PassCtl c = ctl(n0, rec_bits * p, nullptr);
+          c.status += (uint64_t)reg * region;
           c.status_words = region;
           const uint32_t* sh = rh.hist + ((size_t)(d * rec_np + p) * x0.nact) * kRadixBins;
-          Prof pf(K_RADIX, (double)n0 * 32, 1, st, !side);
+          Prof pf(K_RADIX, (double)n0 * 32, 1, ls, !side);
+          cudaError_t e;
           if (tagged && p + 1 == rec_np) {
             // the last digit with the side of the root: the list leaves on
-            // level 1 (the second region holds the right side's words)
+            // level 1 (the last region holds the right side's words)
             PassCtl c1 = c;
-            c1.status = c.status + region;
-            KDB_CK(launch_rec_tag_pass(in, out, c, c1, piv_ring[0], d0, thist, d, rec_shape, st));
-          } else if (tagged && p == 0) {
+            c1.status = status + (uint64_t)(P.rec_regions - 1) * region;
+            e = launch_rec_tag_pass(in, out, c, c1, piv_ring[0], d0, thist, d, rec_shape, ls);
+          } else if (tagged && p + 2 == rec_np) {
+            // counts (side of the root, last digit) for the tagged pass
             const RecCount rc{piv_ring[0], d0, thist, rec_bits * (rec_np - 1)};
-            KDB_CK(launch_rec_sort_pass(in, out, c, x0, sh, d, rec_shape, rec_bits, st, &rc));
+            e = launch_rec_sort_pass(in, out, c, x0, sh, d, rec_shape, rec_bits, ls, &rc);
           } else {
-            KDB_CK(launch_rec_sort_pass(in, out, c, x0, sh, d, rec_shape, rec_bits, st));
+            e = launch_rec_sort_pass(in, out, c, x0, sh, d, rec_shape, rec_bits, ls);
           }
-          in = out;
+          if (e != cudaSuccess) return e;
         }
-        // the root, before list d1's passes need its side (inside the list
-        // phase, and timed with it when that runs beside the side stream)
-        if (fold && d == d0) KDB_CK(pivots_of(0, !side));
-        if (tagged) lat[d] = 1;
+        return cudaSuccess;
+      };
+      // the passes of list d1 that need the root's pivot: its last two
+      const int np_free = fold ? rec_np - 2 : rec_np;
+      if (side) {
+        for (int j = 0; j < 2; ++j) KDB_CK(aux[j].fork(st));
+        KDB_CK(sort_list((P.dim0 + 2) % k, 0, rec_np, aux[1].s, 2));
+        KDB_CK(sort_list(d1, 0, np_free, aux[0].s, 1));
+        KDB_CK(sort_list(d0, 0, rec_np, st, 0));
+        if (fold) {
+          KDB_CK(pivots_of(0, false));  // the root (timed with the phase)
+          KDB_CK(cudaEventCreateWithFlags(&root_done, cudaEventDisableTiming));
+          KDB_CK(cudaEventRecord(root_done, st));
+          KDB_CK(cudaStreamWaitEvent(aux[0].s, root_done, 0));
+          KDB_CK(sort_list(d1, np_free, rec_np, aux[0].s, 1));
+        }
+        for (int j = 0; j < 2; ++j) {
+          KDB_CK(aux[j].join(st));
+          KDB_CK(aux[j].wait(st));
+        }
+      } else {
+        for (int di = 0; di < k; ++di) {
+          const int d = (P.dim0 + di) % k;
+          KDB_CK(sort_list(d, 0, rec_np, st, 0));
+          if (fold && d == d0) KDB_CK(pivots_of(0));  // the root, before list d1's passes need its side
+        }
       }
-      if (side) KDB_CK(aux.wait(st));
+      if (fold) lat[d1] = 1;
     }
   }
   for (int l = 0; l < levels; ++l) {
