@@ -666,6 +666,8 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     __syncthreads();
     jfirst = 1;
   }
+  // lists already split into the runs of depth kJW's nodes (see below)
+  uint32_t split5 = 0;
   for (int j = jfirst; j < jb; ++j) {
     const Local& y = s_lay[j];
     const uint32_t nodes = 1u << j, nb = nodes - 1;
@@ -689,8 +691,30 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
         __syncthreads();
       }
     }
+    // round robin, the last block depth before the warp phase: an item's
+    // rank in its child follows from its rank in its node (Observation 1:
+    // lower ranks go left in order, higher ones right), so this pass also
+    // writes the list in the runs of depth kJW's nodes, and the split before
+    // the warp phase skips it
+    const bool split_here = !bydim && j == kJW - 1 && D - 1 > kJW;
     for (int d = 0; d < k; ++d) {
       if (!bydim && d != s_drr[j]) continue;
+      if (split_here) {
+        uint16_t* dst = list_of(slots, k);
+        const Local& y5 = s_lay[kJW];
+        block_ranks(list_of(slots, d), j, -1, [&](uint32_t id, uint32_t t, uint32_t r) {
+          const uint32_t pr = s_prb[t];
+          split_item(id, j, t, r, pr, d);
+          if (r != pr) {
+            const uint32_t pos = r < pr ? l_start(y5, 2 * t) + r : l_start(y5, 2 * t + 1) + (r - pr - 1);
+            if (pos < kLocalCap) dst[pos] = (uint16_t)id;
+            else s_bad = 1;
+          }
+        });
+        slots = swap_slots(slots, d, k);
+        split5 |= 1u << d;
+        continue;
+      }
       block_ranks(list_of(slots, d), j, bydim ? d : -1, [&](uint32_t id, uint32_t t, uint32_t r) {
         split_item(id, j, t, r, s_prb[t], d);
       });
@@ -712,7 +736,7 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
       for (int jj = kJW; jj < D - 1; ++jj) need |= 1u << s_drr[jj];
     const Local& y5 = s_lay[kJW];
     for (int d = 0; d < k; ++d) {
-      if (!((need >> d) & 1u)) continue;
+      if (!((need >> d) & 1u) || ((split5 >> d) & 1u)) continue;
       uint16_t* dst = list_of(slots, k);
       block_ranks(list_of(slots, d), kJW, -1, [&](uint32_t id, uint32_t t, uint32_t r) {
         const uint32_t pos = l_start(y5, t) + r;
