@@ -30,8 +30,12 @@
  *     caller; "h_" pointers are host memory.  The library never frees caller
  *     memory and keeps no pointer to it after a call returns.
  *   - Streams: work is ordered on `stream` (a cudaStream_t; NULL = the legacy
- *     default stream).  Calls that return device-detected errors synchronise
- *     the stream before returning, as stated per call.
+ *     default stream).  A build may run parts of its work side by side on
+ *     streams of its own, forked from `stream` and joined back to it before
+ *     anything that follows (not while `stream` is being captured into a
+ *     graph), so the order seen from `stream` is unchanged.  Calls that return
+ *     device-detected errors synchronise the stream before returning, as
+ *     stated per call.
  *   - Errors: argument errors return KDB_ERR_INVALID_ARGUMENT before anything
  *     is enqueued.  If a device error is detected (NaN input, a bounded wait
  *     that ran out, an internal consistency check) the records are left
