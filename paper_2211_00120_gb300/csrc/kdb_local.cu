@@ -381,22 +381,32 @@ __global__ void __launch_bounds__(T, 1) local_finish_kernel(LocalArgs a) {
     for (int d = 1; d < 3; ++d) {
       if (d >= k) break;
       uint16_t* list = s_lists + (size_t)d * kLocalCap;
+      // lookups: every item's first probe is read at once (most keys sit in
+      // their first slot), then each probe runs on to the key or an empty
+      // slot, then the ids are read
+      uint32_t key[PER];
+#pragma unroll
+      for (int r = 0; r < PER; ++r) {
+        hh[r] = (ov[d][r] * 0x9E3779B1u) >> (32 - (kLocalLog + 1));
+        key[r] = s_hkey[hh[r]];
+      }
 #pragma unroll
       for (int r = 0; r < PER; ++r) {
         const uint32_t i = threadIdx.x + (uint32_t)r * T;
         if (i >= m) continue;
         const uint32_t o = ov[d][r];
-        uint32_t h = (o * 0x9E3779B1u) >> (32 - (kLocalLog + 1));
-        uint32_t id = 0xFFFFFFFFu;
-        for (uint32_t probe = 0; probe <= HM; ++probe) {
-          const uint32_t key = s_hkey[h];
-          if (key == o) {
-            id = s_hval[h];
-            break;
-          }
-          if (key == 0xFFFFFFFFu) break;
+        uint32_t h = hh[r], kk = key[r];
+        for (uint32_t probe = 0; probe < HM && kk != o && kk != 0xFFFFFFFFu; ++probe) {
           h = (h + 1) & HM;
+          kk = s_hkey[h];
         }
+        hh[r] = kk == o ? h : 0xFFFFFFFFu;
+      }
+#pragma unroll
+      for (int r = 0; r < PER; ++r) {
+        const uint32_t i = threadIdx.x + (uint32_t)r * T;
+        if (i >= m) continue;
+        uint32_t id = hh[r] != 0xFFFFFFFFu ? (uint32_t)s_hval[hh[r]] : 0xFFFFFFFFu;
         if (id >= m) {
           s_bad = 1;
           id = 0;
