@@ -8,8 +8,8 @@
 //
 // Per tile:
 //   1. load keys (and values) coalesced, warp-striped;
-//   2. rank each key among equal digits inside its warp with __match_any_sync
-//      (warp-level multi-split), per-warp digit counters in shared memory;
+//   2. rank each key among equal digits inside its warp (per-bit ballots, or
+//      __match_any_sync where the epilogue is heavy: warp-level multi-split), per-warp digit counters in shared memory;
 //   3. tile-wide digit counts and offsets by a block scan;
 //   4. publish the tile's digit counts, stage the tile in shared memory in
 //      digit order, then decoupled look-back: add up the counts of earlier
@@ -196,7 +196,12 @@ __global__ void __launch_bounds__(THREADS)
     const uint32_t p = wbase + i * 32 + lane;
     const bool ok = p < tn;
     const uint32_t d = ok ? digit_of(key[i], c.shift) : (uint32_t)kRadix;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    // plain passes: eight ballots (up to 256 digits in a warp, where
+    // match.any is slow); passes with a heavier epilogue: match.any, which
+    // needs fewer registers
+    uint32_t peers;
+    if constexpr (Epi::kBallotRank) peers = warp_peers(d, ok, kRadixBits);
+    else peers = __match_any_sync(0xffffffffu, d);
     uint32_t before = 0;
     if (ok) before = s_whist[warp][d];
     __syncwarp();
@@ -272,6 +277,7 @@ __global__ void __launch_bounds__(THREADS)
 // ---- epilogues ------------------------------------------------------------
 template <typename K>
 struct EpiPingPong {
+  static constexpr bool kBallotRank = true;
   K* keys_out;
   uint32_t* vals_out;
   __device__ void operator()(K k, uint32_t v, uint32_t dest) const {
@@ -284,6 +290,7 @@ struct EpiPingPong {
 // item, less its set's first sorted position, is its rank in that dimension.
 template <typename K>
 struct EpiRank {
+  static constexpr bool kBallotRank = false;
   RankOut out;
   const SetInfo* sets;     // nullptr for a single set starting at 0
   int set_shift;           // set id = key >> set_shift (multi-set keys)

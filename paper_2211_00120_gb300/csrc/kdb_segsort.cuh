@@ -228,7 +228,9 @@ __global__ void __launch_bounds__(THREADS, MINB)
     key[i] = ok ? s_keys[p] : 0u;
     const uint32_t bin =
         ok ? (((p >= bpos) ? (uint32_t)kRadix : 0u) | digit_of(key[i], c.shift)) : (uint32_t)BINS;
-    const uint32_t peers = __match_any_sync(0xffffffffu, bin);
+    uint32_t peers;  // ballots in plain passes, as in onesweep_pass
+    if constexpr (Epi::kBallotRank) peers = warp_peers(bin, ok, kRadixBits + 1);
+    else peers = __match_any_sync(0xffffffffu, bin);
     uint32_t before = 0;
     if (ok) before = s_whist[bin * WARPS + warp];
     __syncwarp();
@@ -325,6 +327,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
 // ---- epilogues ------------------------------------------------------------
 struct SegEpiPingPong {
   static constexpr bool kNeedsUpdateInfo = false;
+  static constexpr bool kBallotRank = true;
   uint32_t* keys_out;
   uint32_t* vals_out;
   __device__ void operator()(uint32_t k, uint32_t v, uint32_t dest, uint32_t, const TileSegs&) const {
@@ -344,6 +347,7 @@ struct SegEpiPingPong {
 // an item is its rank in that dimension.
 struct SegEpiRank {
   static constexpr bool kNeedsUpdateInfo = false;
+  static constexpr bool kBallotRank = false;
   RankOut out;
   __device__ void operator()(uint32_t, uint32_t v, uint32_t dest, uint32_t, const TileSegs&) const {
     out.put(v, dest, dest);
@@ -352,6 +356,7 @@ struct SegEpiRank {
 
 struct SegEpiUpdate {
   static constexpr bool kNeedsUpdateInfo = true;
+  static constexpr bool kBallotRank = false;
   uint32_t* perm;
   uint32_t* vals_next;
   uint32_t* vals_local;

@@ -18,6 +18,7 @@ namespace kdb {
 // by position and never stored.  On a set's last sorted level the children
 // are lowest-level nodes and go to their final slots.
 struct EpiUpdate {
+  static constexpr bool kBallotRank = false;
   LevelCtx x;
   uint32_t* perm;
   uint32_t* vals_next;
