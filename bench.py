@@ -854,14 +854,16 @@ def main():
         h_src = torch.from_numpy(host)
         h = torch.empty_like(h_src).pin_memory()
         times = []
-        # one untimed call first: the device's first accesses to freshly
-        # pinned pages over the host link are slow, as any first use is
-        for s in range(1 + max(1, args.e2e_steps)):
+        # untimed calls first (as many as the device legs' warm-up): the
+        # device's first accesses to freshly pinned pages over the host link
+        # are slow, as any first use is
+        e_warm = max(3, args.warmup)
+        for s in range(e_warm + max(1, args.e2e_steps)):
             h.copy_(h_src)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             kdb.kdb_build_host(h, k, mode)
-            if s > 0:
+            if s >= e_warm:
                 times.append(time.perf_counter() - t0)
         e_ms = 1000.0 * sum(times) / len(times)
         # one more call, not timed, with the library's per-kernel events: which
@@ -881,7 +883,7 @@ def main():
         e2e = {"value": world * n / (e_ms / 1000.0) / 1e6, "unit": "Mpts/s",
                "host_link": link,
                "h2d_bytes_per_step": n * stride, "d2h_bytes_per_step": n * stride,
-               "ms_per_step": e_ms, "steps": len(times), "warmup": 1,
+               "ms_per_step": e_ms, "steps": len(times), "warmup": e_warm,
                "kernel_ms_one_call": e_kernel_ms,
                "api": "kdb_build_host on a pinned host tensor",
                "transfer": ("the kernels read the host records and write the tree into them "
