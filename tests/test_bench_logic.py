@@ -40,6 +40,28 @@ def test_kernel_roofline_of_an_hbm_kind():
         assert r["traffic"] is None  # measured on other sources: not reused
 
 
+def test_kernel_roofline_of_the_issue_bound_local_finish(monkeypatch):
+    """The local finish is rated against the warp-instruction issue peak
+    (four schedulers per SM, one instruction each per cycle): achieved =
+    stored warp instructions per point x points / CUDA-event time; without a
+    stored count for its current sources the fraction is null, not guessed."""
+    steps, n = 20, 10**8
+    row = {"name": "local_finish", "ms": steps * 6.68, "bytes": 0.0, "launches": steps}
+    monkeypatch.setattr(bench, "issue_peak_ginst", lambda device=0: (4 * 152 * 2070e6 / 1e9, "test"))
+    counters = {"warp_instructions_per_point": 53.0, "dram_bytes_per_point": 38.0}
+    monkeypatch.setattr(bench, "stored_counters", lambda name, kind: counters)
+    r = bench.kernel_roofline(row, steps, n, 6799.6, "measured", {})
+    assert r["bound"] == "alu" and r["unit"] == "Gwarp-inst/s"
+    assert r["peak"] == pytest.approx(1258.56)
+    assert r["achieved"] == pytest.approx(53.0 * n / 6.68e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 1258.56)
+    assert 0.6 < r["frac"] < 0.7
+    assert r["ms_per_step"] == pytest.approx(6.68)
+    monkeypatch.setattr(bench, "stored_counters", lambda name, kind: None)
+    r = bench.kernel_roofline(row, steps, n, 6799.6, "measured", {})
+    assert r["achieved"] is None and r["frac"] is None and r["traffic"] is None
+
+
 def test_stored_traffic_only_for_its_tile_shape():
     assert bench.traffic_per_launch("radix_pass", 1e6, {"radix": (999, 1, 1)}) is None
     assert bench.traffic_per_launch("partition_pass", 1e6, {"partition": (999, 1, 1)}) is None
